@@ -1,0 +1,192 @@
+"""Pins of the oracle's fermionic pieces: JW (Eq. 15-16), the Hamiltonian (Eq. 1-2),
+dUCC factors (Eq. 19), the PQE identity (Eq. 25) and Tab. 1's CNOT count."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from oracle import fermion, pauli
+from workloads import integrals, amplitudes
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_jw_ladder_matches_bitstring_action(n):
+    for p in range(n):
+        for dag in (False, True):
+            d = sum(c * fermion.letters_dense(s) for s, c in fermion.jw_ladder(n, p, dag).items())
+            np.testing.assert_allclose(d, fermion.ladder_dense(n, p, dag), atol=1e-15)
+
+
+def test_anticommutation():
+    n = 4
+    a = [fermion.ladder_dense(n, p, False) for p in range(n)]
+    ad = [fermion.ladder_dense(n, p, True) for p in range(n)]
+    for p, q in itertools.product(range(n), repeat=2):
+        np.testing.assert_allclose(a[p] @ ad[q] + ad[q] @ a[p], np.eye(16) * (p == q), atol=1e-15)
+        np.testing.assert_allclose(a[p] @ a[q] + a[q] @ a[p], 0, atol=1e-15)
+
+
+def test_ladder_sign_closed_form():
+    # a+_2 |q0=1,q1=1,q2=0> = (-1)^2 |111>;  a_1 |011> = (-1)^1 |001>
+    n = 3
+    v = np.zeros(8, dtype=complex); v[0b011] = 1
+    assert fermion.create(v, n, 2)[0b111] == 1
+    assert fermion.annihilate(v, n, 1)[0b001] == -1
+    assert fermion.annihilate(v, n, 2).sum() == 0
+
+
+def test_excitation_counts():
+    # spin-conserving singles + doubles at the four molecular sizes
+    expect = {(4, 4): (8, 18), (8, 8): (32, 328), (12, 12): (72, 1746), (2, 2): (2, 1)}
+    for (no, ne), (ns, nd) in expect.items():
+        ex = fermion.excitations(no, ne)
+        assert sum(len(e[0]) == 1 for e in ex) == ns
+        assert sum(len(e[0]) == 2 for e in ex) == nd
+
+
+def test_excitation_order_is_ascending_determinant():
+    ex = fermion.excitations(4, 4)
+    ref = fermion.hf_det(4)
+    dets = []
+    for e in ex:
+        v = np.zeros(256, dtype=complex); v[ref] = 1
+        w = fermion.apply_string(v, 8, fermion.tau_string(e))
+        nz = np.flatnonzero(w)
+        assert len(nz) == 1 and abs(abs(w[nz[0]]) - 1) < 1e-15
+        dets.append(int(nz[0]))
+    assert dets == sorted(dets) and len(set(dets)) == len(dets)
+
+
+@pytest.mark.parametrize("ex", [((1,), (3,)), ((0, 1), (2, 3)), ((0, 3), (4, 7)), ((2, 3), (4, 5))])
+def test_ucc_factor_matches_expm_and_pauli_product(ex):
+    n = 8
+    rng = np.random.default_rng(0)
+    psi = rng.normal(size=256) + 1j * rng.normal(size=256)
+    t = 0.7
+    K = fermion.kappa_dense(n, ex)
+    np.testing.assert_allclose(K, -K.conj().T, atol=1e-15)
+    ref = sl.expm(t * K) @ psi
+    np.testing.assert_allclose(fermion.ucc_factor_apply(psi, n, ex, t), ref, atol=1e-12)
+    # kappa = i sum_k c_k P_k and the commuting product of exp(-i(-c_k t)P_k)
+    rots = fermion.jw_kappa_rotations(n, ex)
+    np.testing.assert_allclose(1j * sum(c * pauli.dense(n, x, z) for x, z, c in rots), K, atol=1e-14)
+    expected_count = 2 if len(ex[0]) == 1 else 8
+    assert len(rots) == expected_count
+    out = psi.copy()
+    for x, z, c in rots:
+        out = pauli.rotate(out, n, x, z, -c * t)
+    np.testing.assert_allclose(out, ref, atol=1e-12)
+
+
+def test_pqe_omega_identity():
+    """Eq. 25: exp(pi/4 kappa)|Phi0> = (|Phi0> + |Phi_mu>)/sqrt2 with |Phi_mu> = tau|Phi0>."""
+    n, ne = 8, 4
+    ref = np.zeros(256, dtype=complex); ref[fermion.hf_det(ne)] = 1
+    for ex in fermion.excitations(4, ne)[::5]:
+        phimu = fermion.apply_string(ref, n, fermion.tau_string(ex))
+        out = fermion.ucc_factor_apply(ref, n, ex, np.pi / 4)
+        np.testing.assert_allclose(out, (ref + phimu) / np.sqrt(2), atol=1e-15)
+
+
+def test_tab1_pduccd_cnot_count():
+    """Tab. 1: the p-dUCCD ansatz for H4 (8 qubits, 4 electrons, 4 paired doubles)
+    has 192 CNOTs; each JW string of weight w costs 2(w-1) CNOTs in the Fig. 4
+    ladder, so this pins the number and weight of the JW strings."""
+    gold = GOLD["pdUCCD_H4_NCNOT"]
+    n, ne = gold["n_qubits"], gold["n_el"]
+    nocc, nvir = ne // 2, (n - ne) // 2
+    total = 0
+    npar = 0
+    for i in range(nocc):
+        for a in range(nvir):
+            ia, ib = 2 * i, 2 * i + 1
+            aa, ab = 2 * nocc + 2 * a, 2 * nocc + 2 * a + 1
+            # tau = a+_{a_b} a+_{a_a} a_{i_a} a_{i_b} as in the p-dUCCD factor
+            tau = [("+", ab), ("+", aa), ("-", ia), ("-", ib)]
+            taud = [("+", ib), ("+", ia), ("-", aa), ("-", ab)]
+            k = fermion.jw_product(n, tau)
+            for s, c in fermion.jw_product(n, taud).items():
+                k[s] = k.get(s, 0) - c
+            for s, c in k.items():
+                if abs(c) > 1e-14:
+                    w = sum(ch != "I" for ch in s)
+                    total += 2 * (w - 1)
+            npar += 1
+    assert npar == gold["n_par"]
+    assert total == gold["value"]
+
+
+@pytest.mark.parametrize("n_orb", [2, 3])
+def test_hamiltonian_three_ways(n_orb):
+    h, g = integrals(n_orb, 11 + n_orb)
+    n = 2 * n_orb
+    Hf = fermion.hamiltonian_dense(n_orb, h, g)
+    np.testing.assert_allclose(Hf, Hf.conj().T, atol=1e-14)
+    Hp = pauli.dense_sum(n, fermion.jw_hamiltonian(n_orb, h, g))
+    np.testing.assert_allclose(Hp, Hf, atol=1e-12)
+    rng = np.random.default_rng(1)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    np.testing.assert_allclose(fermion.hamiltonian_apply(psi, n_orb, h, g), Hf @ psi, atol=1e-12)
+
+
+def test_integral_symmetry():
+    h, g = integrals(4, 0)
+    np.testing.assert_array_equal(h, h.T)
+    assert np.all(np.diag(h) <= 0) and np.all(np.diag(h) >= -2)
+    for perm in [(1, 0, 2, 3), (0, 1, 3, 2), (2, 3, 0, 1)]:
+        np.testing.assert_array_equal(g, g.transpose(perm))
+
+
+def test_hf_energy_slater_condon_and_variational_bound():
+    n_orb, ne = 4, 4
+    h, g = integrals(n_orb, 0)
+    H = fermion.hamiltonian_dense(n_orb, h, g)
+    det = fermion.hf_det(ne)
+    e0 = fermion.hf_energy_closed_form(h, g, ne)
+    assert abs(H[det, det].real - e0) < 1e-12
+    exs = fermion.excitations(n_orb, ne)
+    t = amplitudes(len(exs), 0, 0.1)
+    assert abs(fermion.ucc_energy(n_orb, ne, h, g, np.zeros(len(exs)), exs) - e0) < 1e-12
+    psi = fermion.ucc_state(n_orb, ne, t, exs)
+    e = np.vdot(psi, H @ psi)
+    assert abs(e.imag) < 1e-13
+    # lowest eigenvalue in the 4-electron, S_z = 0 sector bounds E from below
+    b = np.arange(256)
+    na = np.array([bin(v & 0x55).count("1") for v in b]); nb = np.array([bin(v & 0xAA).count("1") for v in b])
+    sec = np.flatnonzero((na == 2) & (nb == 2))
+    efci = np.linalg.eigvalsh(H[np.ix_(sec, sec)].real)[0]
+    assert e.real >= efci - 1e-12
+    # state stays in the sector with unit norm
+    assert abs(np.linalg.norm(psi) - 1) < 1e-13
+    out = np.setdiff1d(b, sec)
+    assert np.abs(psi[out]).max() < 1e-14
+
+
+def test_ucc_adjoint_matches_fd():
+    n_orb, ne = 3, 2
+    h, g = integrals(n_orb, 5)
+    exs = fermion.excitations(n_orb, ne)
+    t = amplitudes(len(exs), 5, 0.3)
+    e, grad = fermion.ucc_gradient_adjoint(n_orb, ne, h, g, t, exs)
+    fd = fermion.ucc_gradient_fd(n_orb, ne, h, g, t, list(range(len(exs))), step=1e-5, exs=exs)
+    np.testing.assert_allclose(grad, fd, atol=1e-8)
+
+
+def test_ucc_pauli_route_equals_fermion_route():
+    """The oracle's two routes to the dUCC state agree: fermionic closed-form
+    factors vs the JW Pauli rotations (each excitation's strings, in order)."""
+    n_orb, ne = 3, 2
+    n = 6
+    exs = fermion.excitations(n_orb, ne)
+    t = amplitudes(len(exs), 9, 0.4)
+    a = fermion.ucc_state(n_orb, ne, t, exs)
+    psi = np.zeros(64, dtype=complex); psi[fermion.hf_det(ne)] = 1
+    for ex, tm in zip(exs, t):
+        for x, z, c in fermion.jw_kappa_rotations(n, ex):
+            psi = pauli.rotate(psi, n, x, z, -c * tm)
+    np.testing.assert_allclose(psi, a, atol=1e-13)
