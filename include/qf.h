@@ -1,0 +1,128 @@
+/*
+ * qf.h -- C ABI of libqf, a GB300 (sm_103a) state-vector engine for products of
+ * Pauli-string exponentials and Pauli-sum expectation values, after the
+ * state-vector simulator of QForte (Stair & Evangelista, arXiv:2108.04413).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Basis (Sec. "The QubitBasis class", Eq. 3): amplitude index b = sum_i q_i 2^i,
+ *   bit i of b is qubit q_i.  A state of n qubits is 2^n complex amplitudes,
+ *   stored interleaved (re, im): 16 bytes each for QF_C128 (two doubles),
+ *   8 bytes each for QF_C64 (two floats), amplitude b at byte offset b*size.
+ * Pauli string (Eq. 10): a pair of bit masks (x, z); qubit i carries X if only
+ *   x_i is set, Z if only z_i is set, Y if both are set.  It is the Hermitian
+ *   operator P with P|b> = i^{popc(x&z)} (-1)^{popc(z&b)} |b xor x>.
+ * Rotation (Eq. 9 with the factor -i*theta of the worked example Eq. 11-13):
+ *   exp(-i theta P) = cos(theta) I - i sin(theta) P.
+ * Circuits are applied in list order: element 0 acts first on the state.
+ *
+ * Streams, ownership, errors
+ * --------------------------
+ * Every call that touches a state runs on the CUDA stream given at creation and
+ * returns once its work is queued, except calls that return host values
+ * (qf_expectation, qf_energy_grad, qf_state_copy_to_host), which synchronise
+ * that stream.  Input arrays are read (and planned) before a call returns, so
+ * the caller may free them afterwards.  Handles are owned by the library and
+ * released with qf_state_destroy; a handle must not be used by two host
+ * threads at once (distinct handles on distinct streams may run concurrently).
+ * Every call returns a qf_status; on failure the state is unchanged unless the
+ * status is QF_ECUDA, and qf_last_error() gives a thread-local message.
+ * Invalid arguments (null pointers, n outside 1..QF_MAX_QUBITS, a mask with a
+ * bit at or above n, a parameter index outside the parameter array, a size
+ * that does not match the state) give QF_EINVAL before any GPU work.
+ */
+#ifndef QF_H
+#define QF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QF_MAX_QUBITS 34
+
+typedef enum { QF_OK = 0, QF_EINVAL = 1, QF_ENOMEM = 2, QF_ECUDA = 3, QF_ETIMEOUT = 4 } qf_status;
+typedef enum { QF_C128 = 0, QF_C64 = 1 } qf_dtype;
+
+/* One rotation exp(-i theta P(x, z)). */
+typedef struct { uint64_t x, z; double theta; } qf_rot;
+/* One Hamiltonian term coeff * P(x, z); real coeff, so the sum is Hermitian (Eq. 2). */
+typedef struct { uint64_t x, z; double coeff; } qf_term;
+/* One ansatz rotation exp(-i theta P(x, z)) with theta = coeff * t[param]. */
+typedef struct { uint64_t x, z; double coeff; int32_t param; int32_t reserved; } qf_arot;
+
+typedef struct qf_state qf_state;
+
+/* Create a state of n qubits (the "Computer" of Eq. 4 / Lst. 1), initialised to
+ * |0...0>.  stream: a cudaStream_t (NULL = legacy default stream).
+ * dev_buf: NULL to let the library allocate the 2^n amplitudes, or caller-owned
+ * device memory of dev_buf_bytes >= 2^n * size bytes, 256-byte aligned, which must
+ * outlive the handle.  Work buffers (reduction partials, and the second state
+ * used by qf_energy_grad) are allocated by the library.  QF_ENOMEM if an
+ * allocation fails. */
+qf_status qf_state_create(int n, qf_dtype dtype, void* stream, void* dev_buf, size_t dev_buf_bytes,
+                          qf_state** out);
+qf_status qf_state_destroy(qf_state* st);
+
+/* Set the state to the basis determinant |det> (Eq. 17's reference |Phi_0>). */
+qf_status qf_set_basis(qf_state* st, uint64_t det);
+
+/* Apply exp(-i theta P(x, z)) (Eq. 9, Lst. 4). */
+qf_status qf_apply_pauli_exp(qf_state* st, uint64_t x, uint64_t z, double theta);
+
+/* Apply the product of n_rot rotations in list order (a Circuit, Sec. "The
+ * Circuit class"; the dUCC product of Eq. 19 once each theta is known).  The
+ * library fuses runs of rotations internally; the result equals applying them
+ * one by one up to rounding. */
+qf_status qf_apply_circuit(qf_state* st, const qf_rot* rots, size_t n_rot);
+
+/* Exact operator averaging <psi|H|psi> for H = sum_l coeff_l P_l (Eq. 18, Lst. 5).
+ * Terms may repeat.  *re receives the value; *im receives 0 (the coefficients
+ * are real, so the value is real; the kernel sums each amplitude pair's two
+ * Hermitian-conjugate contributions together).  Synchronises the stream. */
+qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, double* re, double* im);
+
+/* Energy and gradient of E(t) = <Phi|U(t)^+ H U(t)|Phi> (Eq. 17-18) with
+ * |Phi> = |det> and U(t) the ansatz rotations in list order, theta_k = coeff_k *
+ * t[param_k].  The gradient comes from a reverse (adjoint) sweep:
+ * dE/dtheta_k = 2 Im <lambda_k|P_k|psi_k>, dE/dt_p = sum_{k: param_k = p} coeff_k
+ * dE/dtheta_k.  U(t)|Phi> has unit norm; the returned energy and gradient are
+ * divided by the computed <psi|psi> (FP64), which removes the rounding drift of
+ * the stored norm (it matters for QF_C64 states).  grad has n_par entries.  The
+ * reverse sweep undoes the circuit,
+ * so on return the state holds |det> again up to rounding (call
+ * qf_apply_circuit to rebuild U(t)|Phi>).  A second state-sized device buffer
+ * (lambda = H psi) is allocated on the first call and kept with the handle.
+ * Synchronises the stream. */
+qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                         size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad);
+
+/* Copy the state to / from host memory (bytes must equal 2^n * size).  The
+ * copy to host folds the internal scale into the amplitudes first. */
+qf_status qf_state_copy_to_host(qf_state* st, void* host, size_t bytes);
+qf_status qf_state_copy_from_host(qf_state* st, const void* host, size_t bytes);
+
+/* The library may keep a state as scale * stored amplitudes (a rotation then
+ * costs two fused multiply-adds per amplitude instead of four).  This folds the
+ * scale into the stored amplitudes so that device memory holds the state
+ * itself.  Queued on the stream. */
+qf_status qf_state_fold_scale(qf_state* st);
+
+/* Query a state: qubit count, dtype, device pointer of the amplitudes and the
+ * current scale (amplitudes = scale * stored values).  Any pointer may be NULL. */
+qf_status qf_state_info(const qf_state* st, int* n, qf_dtype* dtype, void** dev_ptr, double* scale);
+
+/* Number of kernels this thread's calls have launched since the last reset
+ * (reset = 1 clears the counter after reading). */
+uint64_t qf_kernel_launches(int reset);
+
+/* Thread-local message describing the last failure. */
+const char* qf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QF_H */

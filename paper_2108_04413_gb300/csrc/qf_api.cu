@@ -1,0 +1,697 @@
+// Host side of libqf: the C ABI declared in include/qf.h, the rotation planner
+// (sparse composites, shared-memory tile fusion, deferred scale) and the
+// X-mask grouping of Pauli sums.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "qf_internal.h"
+
+using cplx = std::complex<double>;
+
+namespace {
+
+thread_local std::string t_err;
+
+qf_status fail(qf_status s, const std::string& msg) {
+  t_err = msg;
+  return s;
+}
+
+#define QF_CUDA(expr)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess) return fail(QF_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int popc(uint64_t v) { return __builtin_popcountll(v); }
+int hibit(uint64_t v) { return v ? 63 - __builtin_clzll(v) : -1; }
+
+struct ExpPlan {
+  qf::ExpGroup* d_groups = nullptr;
+  qf::ExpChunk* d_echunks = nullptr;  // pair-form expectation weights
+  qf::ExpChunk* d_hchunks = nullptr;  // H|psi> weights
+  int ngroups = 0;
+  int nchunks = 0;
+};
+
+uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
+struct qf_state {
+  int n = 0;
+  qf_dtype dt = QF_C128;
+  cudaStream_t stream = nullptr;
+  void* psi = nullptr;
+  bool own_psi = false;
+  void* lam = nullptr;
+  double scale = 1.0;
+  double* d_partials = nullptr;
+  unsigned* d_counter = nullptr;
+  double* d_out = nullptr;
+  size_t out_cap = 0;
+  double* h_out = nullptr;
+  size_t h_cap = 0;
+  std::unordered_map<uint64_t, ExpPlan> plans;
+  size_t elem() const { return dt == QF_C128 ? 16 : 8; }
+  size_t bytes() const { return elem() << n; }
+};
+
+namespace {
+
+constexpr int kPartials = 4096;
+
+// Largest |log2 scale| kept aside before it is folded back into the amplitudes.
+double scale_limit(qf_dtype dt) { return dt == QF_C128 ? 400.0 : 30.0; }
+
+// Coefficients for exp(-i th P) = c I - i s P given the scale kept aside
+// (amplitudes = scale * stored values); updates that scale.  The larger of
+// |c| and |s| is factored out so the kernel needs one FMA per real component.
+void rot_coeffs(qf_dtype dt, double* scale, double th, int* form, double* A, double* B) {
+  const double c = std::cos(th), s = std::sin(th);
+  if (std::fabs(std::log2(std::fabs(*scale))) > scale_limit(dt)) {
+    *form = qf::FORM_AB;
+    *A = c * *scale;
+    *B = s * *scale;
+    *scale = 1.0;
+  } else if (std::fabs(c) >= std::fabs(s)) {
+    *form = qf::FORM_A1;
+    *A = 1.0;
+    *B = s / c;
+    *scale *= c;
+  } else {
+    *form = qf::FORM_B1;
+    *A = c / s;
+    *B = 1.0;
+    *scale *= s;
+  }
+}
+
+qf::RotArgs rot_args(qf_dtype dt, double* scale, uint64_t x, uint64_t z, double th) {
+  qf::RotArgs a{};
+  a.x = x;
+  a.z = z;
+  a.h = hibit(x);
+  a.y = popc(x & z);
+  rot_coeffs(dt, scale, th, &a.form, &a.A, &a.B);
+  return a;
+}
+
+qf_status ensure_out(qf_state* st, size_t n) {
+  if (n <= st->out_cap) return QF_OK;
+  size_t cap = std::max<size_t>(n, 2 * st->out_cap);
+  if (st->d_out) cudaFree(st->d_out);
+  if (st->h_out) cudaFreeHost(st->h_out);
+  st->d_out = nullptr;
+  st->h_out = nullptr;
+  st->out_cap = 0;
+  if (cudaMalloc(&st->d_out, cap * sizeof(double)) != cudaSuccess) return fail(QF_ENOMEM, "cudaMalloc(out) failed");
+  if (cudaMallocHost(&st->h_out, cap * sizeof(double)) != cudaSuccess)
+    return fail(QF_ENOMEM, "cudaMallocHost(out) failed");
+  st->out_cap = cap;
+  return QF_OK;
+}
+
+qf_status validate_masks(const qf_state* st, uint64_t x, uint64_t z) {
+  const uint64_t lim = (st->n >= 64) ? ~0ull : ((1ull << st->n) - 1ull);
+  if ((x & ~lim) || (z & ~lim)) return fail(QF_EINVAL, "Pauli mask has a bit at or above the qubit count");
+  return QF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pauli-sum plan: group by X mask, pack terms four per chunk with sign-pattern
+// tables (Eq. 18 evaluated pair by pair).
+
+qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan** out) {
+  uint64_t key = fnv1a(terms, nt * sizeof(qf_term));
+  key = fnv1a(&st->n, sizeof(int), key);
+  auto it = st->plans.find(key);
+  if (it != st->plans.end()) {
+    *out = &it->second;
+    return QF_OK;
+  }
+  std::map<uint64_t, std::vector<size_t>> byx;
+  for (size_t i = 0; i < nt; ++i) byx[terms[i].x].push_back(i);
+  std::vector<qf::ExpGroup> groups;
+  std::vector<qf::ExpChunk> ech, hch;
+  for (auto& kv : byx) {
+    qf::ExpGroup g{};
+    g.x = kv.first;
+    g.h = hibit(kv.first);
+    g.chunk0 = (int)ech.size();
+    const std::vector<size_t>& idx = kv.second;
+    g.nchunk = (int)((idx.size() + qf::kChunkTerms - 1) / qf::kChunkTerms);
+    g.flags = 0;
+    for (size_t k = 0; k < idx.size(); k += qf::kChunkTerms) {
+      qf::ExpChunk ce{}, ch{};
+      const int cnt = (int)std::min<size_t>(qf::kChunkTerms, idx.size() - k);
+      for (int t = 0; t < qf::kChunkTerms; ++t) ce.z[t] = ch.z[t] = (t < cnt) ? terms[idx[k + t]].z : 0ull;
+      for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat) {
+        double ex = 0, ey = 0, hx = 0, hy = 0;
+        for (int t = 0; t < cnt; ++t) {
+          const qf_term& T = terms[idx[k + t]];
+          const int y = popc(T.x & T.z) & 3;
+          const double sg = ((pat >> t) & 1) ? -1.0 : 1.0;
+          const double c = T.coeff * sg;
+          if ((y & 1) == 0) {
+            const double ph = (y == 2) ? -1.0 : 1.0;  // i^y
+            hx += c * ph;
+            ex += (g.x == 0 ? 1.0 : 2.0) * c * ph;
+          } else {
+            hy += c * ((y == 3) ? -1.0 : 1.0);        // i^y = +-i
+            ey += 2.0 * c * ((y == 1) ? -1.0 : 1.0);  // 2 c (-1)^{(y+1)/2}
+          }
+        }
+        ce.tab[pat] = make_double2(ex, ey);
+        ch.tab[pat] = make_double2(hx, hy);
+      }
+      for (int t = 0; t < cnt; ++t) {
+        const qf_term& T = terms[idx[k + t]];
+        g.flags |= (popc(T.x & T.z) & 1) ? 2 : 1;
+      }
+      ech.push_back(ce);
+      hch.push_back(ch);
+    }
+    groups.push_back(g);
+  }
+  ExpPlan p;
+  p.ngroups = (int)groups.size();
+  p.nchunks = (int)ech.size();
+  if (p.ngroups > 0) {
+    if (cudaMalloc(&p.d_groups, groups.size() * sizeof(qf::ExpGroup)) != cudaSuccess ||
+        cudaMalloc(&p.d_echunks, ech.size() * sizeof(qf::ExpChunk)) != cudaSuccess ||
+        cudaMalloc(&p.d_hchunks, hch.size() * sizeof(qf::ExpChunk)) != cudaSuccess) {
+      cudaFree(p.d_groups);
+      cudaFree(p.d_echunks);
+      cudaFree(p.d_hchunks);
+      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
+    }
+    QF_CUDA(cudaMemcpyAsync(p.d_groups, groups.data(), groups.size() * sizeof(qf::ExpGroup), cudaMemcpyHostToDevice,
+                            st->stream));
+    QF_CUDA(cudaMemcpyAsync(p.d_echunks, ech.data(), ech.size() * sizeof(qf::ExpChunk), cudaMemcpyHostToDevice,
+                            st->stream));
+    QF_CUDA(cudaMemcpyAsync(p.d_hchunks, hch.data(), hch.size() * sizeof(qf::ExpChunk), cudaMemcpyHostToDevice,
+                            st->stream));
+    QF_CUDA(cudaStreamSynchronize(st->stream));
+  }
+  auto res = st->plans.emplace(key, p);
+  *out = &res.first->second;
+  return QF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse composite of a run of commuting rotations sharing one X mask.
+
+struct RotIn {
+  uint64_t x, z;
+  double th;
+  double coeff;  // generator weight for the gradient (coeff of the ansatz rotation)
+};
+
+bool commute(uint64_t x1, uint64_t z1, uint64_t x2, uint64_t z2) {
+  return ((popc(x1 & z2) + popc(z1 & x2)) & 1) == 0;
+}
+
+// Build the composite on the support of x for every sign class.  On success
+// fills a with M - I restricted to the active rows (M the forward composite,
+// or its inverse when `inverse`) and, when `with_gen`, the generator
+// Q = sum_k coeff_k P_k (whose rows then also count as active).
+bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf::SparseArgs* a) {
+  const uint64_t x = r[0].x;
+  const int u = popc(x);
+  if (u == 0 || u > qf::kSparseMaxSupp) return false;
+  std::vector<int> supp;
+  for (int i = 0; i < n; ++i)
+    if ((x >> i) & 1) supp.push_back(i);
+  auto compress = [&](uint64_t v) {
+    uint64_t o = 0;
+    for (int i = 0; i < u; ++i)
+      if ((v >> supp[i]) & 1) o |= 1ull << i;
+    return o;
+  };
+  std::vector<uint64_t> zc;
+  for (int k = 0; k < m; ++k) {
+    const uint64_t zo = r[k].z & ~x;
+    if (zo && std::find(zc.begin(), zc.end(), zo) == zc.end()) zc.push_back(zo);
+  }
+  if (zc.size() > 2) return false;
+  const int ncls = 1 << zc.size();
+  const int D = 1 << u;
+  const uint64_t xl = (uint64_t)D - 1;
+  std::vector<std::vector<cplx>> Ms(ncls, std::vector<cplx>(D * D)), Qs(ncls, std::vector<cplx>(D * D));
+  const cplx iu(0, 1);
+  for (int c = 0; c < ncls; ++c) {
+    std::vector<cplx>& M = Ms[c];
+    std::vector<cplx>& Q = Qs[c];
+    for (int i = 0; i < D; ++i) M[i * D + i] = 1.0;
+    for (int k = 0; k < m; ++k) {
+      const uint64_t zo = r[k].z & ~x;
+      double sig = 1.0;
+      if (zo) {
+        const int j = (int)(std::find(zc.begin(), zc.end(), zo) - zc.begin());
+        if ((c >> j) & 1) sig = -1.0;
+      }
+      const uint64_t zin = compress(r[k].z & x);
+      const int y = popc(x & r[k].z) & 3;
+      const cplx iy = (y == 0) ? cplx(1, 0) : (y == 1) ? cplx(0, 1) : (y == 2) ? cplx(-1, 0) : cplx(0, -1);
+      // P|col> = iy (-1)^{popc(zin & col)} |col ^ xl>, times the class sign.
+      auto pel = [&](int row) {  // coefficient of P in (row, row ^ xl)
+        const int col = row ^ (int)xl;
+        return iy * sig * ((popc(zin & (uint64_t)col) & 1) ? -1.0 : 1.0);
+      };
+      const double th = inverse ? -r[k].th : r[k].th;
+      const double cs = std::cos(th), sn = std::sin(th);
+      std::vector<cplx> N2(D * D);
+      for (int row = 0; row < D; ++row) {
+        const cplx pr = pel(row);
+        const int prow = row ^ (int)xl;
+        for (int col = 0; col < D; ++col) N2[row * D + col] = cs * M[row * D + col] - iu * sn * pr * M[prow * D + col];
+      }
+      M.swap(N2);
+      for (int row = 0; row < D; ++row) Q[row * D + (row ^ (int)xl)] += r[k].coeff * pel(row);
+    }
+  }
+  // For the inverse the product above is R_m(-th_m)...R_1(-th_1); it equals the inverse of the
+  // forward composite because the block's rotations commute.
+  const double tol = 1e-14;
+  std::vector<int> act;
+  for (int row = 0; row < D; ++row) {
+    bool a2 = false;
+    for (int c = 0; c < ncls && !a2; ++c)
+      for (int col = 0; col < D && !a2; ++col) {
+        const cplx d = Ms[c][row * D + col] - ((row == col) ? 1.0 : 0.0);
+        const cplx d2 = Ms[c][col * D + row] - ((row == col) ? 1.0 : 0.0);
+        if (std::abs(d) > tol || std::abs(d2) > tol)
+          a2 = true;
+        else if (with_gen && (Qs[c][row * D + col] != 0.0 || Qs[c][col * D + row] != 0.0))
+          a2 = true;
+      }
+    if (a2) act.push_back(row);
+  }
+  const int nr = (int)act.size();
+  if (nr == 0 || nr > qf::kSparseMaxRows || 2 * nr > D) return false;
+  std::memset(a, 0, sizeof(*a));
+  a->u = u;
+  a->nr = nr;
+  a->ncls = ncls;
+  a->nzc = (int)zc.size();
+  for (int i = 0; i < u; ++i) a->supp[i] = supp[i];
+  for (size_t j = 0; j < zc.size(); ++j) a->zc[j] = zc[j];
+  for (int i = 0; i < nr; ++i) {
+    uint64_t off = 0;
+    for (int b = 0; b < u; ++b)
+      if ((act[i] >> b) & 1) off |= 1ull << supp[b];
+    a->pat[i] = off;
+  }
+  for (int c = 0; c < ncls; ++c)
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < nr; ++j) {
+        const cplx mv = Ms[c][act[i] * D + act[j]] - ((i == j) ? 1.0 : 0.0), qv = Qs[c][act[i] * D + act[j]];
+        a->M[c][i][j] = make_double2(mv.real(), mv.imag());
+        a->Q[c][i][j] = make_double2(qv.real(), qv.imag());
+      }
+  return true;
+}
+
+// Length of the run starting at i that can form one sparse block.
+int sparse_run(const RotIn* r, size_t i, size_t nrot, const int32_t* params) {
+  const uint64_t x = r[i].x;
+  if (x == 0) return 1;
+  size_t j = i + 1;
+  while (j < nrot && r[j].x == x && (!params || params[j] == params[i])) {
+    bool ok = true;
+    for (size_t k = i; k < j && ok; ++k) ok = commute(r[k].x, r[k].z, r[j].x, r[j].z);
+    if (!ok) break;
+    ++j;
+  }
+  return (int)(j - i);
+}
+
+// Fill a TileArgs for rotations [i, j) whose X union fits the tile.
+void build_tile(qf_state* st, const RotIn* r, size_t i, size_t j, uint64_t uni, qf::TileArgs* a) {
+  const int n = st->n;
+  const int s_target = std::min(n, st->dt == QF_C128 ? 11 : 12);
+  uint64_t S = uni;
+  for (int b = 0; b < n && popc(S) < s_target; ++b) S |= 1ull << b;
+  std::memset(a, 0, sizeof(*a));
+  a->s = popc(S);
+  int l = 0;
+  while (l < n && ((S >> l) & 1)) ++l;
+  a->l = l;
+  a->nhi = a->s - l;
+  int k = 0, kh = 0;
+  for (int b = 0; b < n; ++b)
+    if ((S >> b) & 1) {
+      a->sbits[k++] = b;
+      if (b >= l) a->pos[kh++] = b;
+    }
+  auto compress = [&](uint64_t v) {
+    uint32_t o = 0;
+    for (int q = 0; q < a->s; ++q)
+      if ((v >> a->sbits[q]) & 1) o |= 1u << q;
+    return o;
+  };
+  a->m = (int)(j - i);
+  for (size_t t = i; t < j; ++t) {
+    qf::TileRot& R = a->r[t - i];
+    R.xl = compress(r[t].x);
+    R.zl = compress(r[t].z & S);
+    R.zout = r[t].z & ~S;
+    R.hl = r[t].x ? 31 - __builtin_clz(R.xl) : -1;
+    R.y = popc(r[t].x & r[t].z);
+    rot_coeffs(st->dt, &st->scale, r[t].th, &R.form, &R.A, &R.B);
+  }
+}
+
+qf_status apply_rotations(qf_state* st, const RotIn* r, size_t nrot) {
+  const int n = st->n;
+  const int umax = std::min(n, 8);
+  size_t i = 0;
+  while (i < nrot) {
+    const int run = sparse_run(r, i, nrot, nullptr);
+    if (run >= 2) {
+      qf::SparseArgs sa;
+      if (build_sparse(r + i, run, n, false, false, &sa)) {
+        QF_CUDA(qf::launch_sparse(st->psi, n, st->dt, sa, st->stream));
+        i += run;
+        continue;
+      }
+    }
+    // greedy tile fusion over consecutive rotations whose X support union stays small
+    uint64_t uni = r[i].x;
+    size_t j = i + 1;
+    while (j < nrot && (int)(j - i) < qf::kTileMaxRot && popc(uni | r[j].x) <= umax) {
+      // stop before a run that can become a sparse block
+      if (j + 1 < nrot && r[j].x != 0 && r[j + 1].x == r[j].x && r[j].x != r[j - 1].x) break;
+      uni |= r[j].x;
+      ++j;
+    }
+    if (j - i >= 2 && n >= 4) {
+      qf::TileArgs ta;
+      build_tile(st, r, i, j, uni, &ta);
+      QF_CUDA(qf::launch_tile(st->psi, n, st->dt, ta, st->stream));
+      i = j;
+    } else {
+      qf::RotArgs a = rot_args(st->dt, &st->scale, r[i].x, r[i].z, r[i].th);
+      QF_CUDA(qf::launch_rot(st->psi, n, st->dt, a, st->stream));
+      ++i;
+    }
+  }
+  return QF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qf_last_error(void) { return t_err.c_str(); }
+
+qf_status qf_state_create(int n, qf_dtype dtype, void* stream, void* dev_buf, size_t dev_buf_bytes,
+                          qf_state** out) {
+  if (!out) return fail(QF_EINVAL, "out is NULL");
+  if (n < 1 || n > QF_MAX_QUBITS) return fail(QF_EINVAL, "qubit count outside 1..QF_MAX_QUBITS");
+  if (dtype != QF_C128 && dtype != QF_C64) return fail(QF_EINVAL, "unknown dtype");
+  qf_state* st = new qf_state();
+  st->n = n;
+  st->dt = dtype;
+  st->stream = static_cast<cudaStream_t>(stream);
+  if (dev_buf) {
+    if (dev_buf_bytes < st->bytes() || (reinterpret_cast<uintptr_t>(dev_buf) & 255u)) {
+      delete st;
+      return fail(QF_EINVAL, "dev_buf too small or not 256-byte aligned");
+    }
+    st->psi = dev_buf;
+  } else {
+    if (cudaMalloc(&st->psi, st->bytes()) != cudaSuccess) {
+      cudaGetLastError();
+      delete st;
+      return fail(QF_ENOMEM, "cudaMalloc(state) failed");
+    }
+    st->own_psi = true;
+  }
+  if (cudaMalloc(&st->d_partials, kPartials * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&st->d_counter, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    if (st->own_psi) cudaFree(st->psi);
+    cudaFree(st->d_partials);
+    delete st;
+    return fail(QF_ENOMEM, "cudaMalloc(scratch) failed");
+  }
+  if (ensure_out(st, 64) != QF_OK) {
+    if (st->own_psi) cudaFree(st->psi);
+    cudaFree(st->d_partials);
+    cudaFree(st->d_counter);
+    delete st;
+    return QF_ENOMEM;
+  }
+  cudaError_t e = cudaMemsetAsync(st->d_counter, 0, sizeof(unsigned), st->stream);
+  if (e == cudaSuccess) e = qf::launch_zero_and_set(st->psi, n, dtype, 0ull, st->stream);
+  if (e != cudaSuccess) {
+    qf_state_destroy(st);
+    return fail(QF_ECUDA, std::string("state init: ") + cudaGetErrorString(e));
+  }
+  *out = st;
+  return QF_OK;
+}
+
+qf_status qf_state_destroy(qf_state* st) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  cudaStreamSynchronize(st->stream);
+  for (auto& kv : st->plans) {
+    cudaFree(kv.second.d_groups);
+    cudaFree(kv.second.d_echunks);
+    cudaFree(kv.second.d_hchunks);
+  }
+  if (st->own_psi) cudaFree(st->psi);
+  cudaFree(st->lam);
+  cudaFree(st->d_partials);
+  cudaFree(st->d_counter);
+  cudaFree(st->d_out);
+  cudaFreeHost(st->h_out);
+  delete st;
+  return QF_OK;
+}
+
+qf_status qf_set_basis(qf_state* st, uint64_t det) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  if (st->n < 64 && (det >> st->n)) return fail(QF_EINVAL, "determinant has a bit at or above the qubit count");
+  st->scale = 1.0;
+  QF_CUDA(qf::launch_zero_and_set(st->psi, st->n, st->dt, det, st->stream));
+  return QF_OK;
+}
+
+qf_status qf_apply_pauli_exp(qf_state* st, uint64_t x, uint64_t z, double theta) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  qf_status v = validate_masks(st, x, z);
+  if (v != QF_OK) return v;
+  if (!std::isfinite(theta)) return fail(QF_EINVAL, "theta is not finite");
+  qf::RotArgs a = rot_args(st->dt, &st->scale, x, z, theta);
+  QF_CUDA(qf::launch_rot(st->psi, st->n, st->dt, a, st->stream));
+  return QF_OK;
+}
+
+qf_status qf_apply_circuit(qf_state* st, const qf_rot* rots, size_t n_rot) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  if (n_rot == 0) return QF_OK;
+  if (!rots) return fail(QF_EINVAL, "rotation list is NULL");
+  std::vector<RotIn> r(n_rot);
+  for (size_t k = 0; k < n_rot; ++k) {
+    qf_status v = validate_masks(st, rots[k].x, rots[k].z);
+    if (v != QF_OK) return v;
+    if (!std::isfinite(rots[k].theta)) return fail(QF_EINVAL, "theta is not finite");
+    r[k] = RotIn{rots[k].x, rots[k].z, rots[k].theta, 1.0};
+  }
+  return apply_rotations(st, r.data(), n_rot);
+}
+
+qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, double* re, double* im) {
+  if (!st || !re) return fail(QF_EINVAL, "NULL argument");
+  if (n_terms && !terms) return fail(QF_EINVAL, "term list is NULL");
+  for (size_t k = 0; k < n_terms; ++k) {
+    qf_status v = validate_masks(st, terms[k].x, terms[k].z);
+    if (v != QF_OK) return v;
+  }
+  if (im) *im = 0.0;
+  if (n_terms == 0) {
+    *re = 0.0;
+    return QF_OK;
+  }
+  const ExpPlan* p = nullptr;
+  qf_status ps = get_plan(st, terms, n_terms, &p);
+  if (ps != QF_OK) return ps;
+  const int nb = qf::reduce_blocks(st->n, st->dt);
+  QF_CUDA(qf::launch_expect(st->psi, st->n, st->dt, p->d_groups, p->ngroups, p->d_echunks, st->d_partials,
+                            st->d_counter, st->d_out, nb, st->stream));
+  QF_CUDA(cudaMemcpyAsync(st->h_out, st->d_out, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  QF_CUDA(cudaStreamSynchronize(st->stream));
+  *re = st->h_out[0] * st->scale * st->scale;
+  return QF_OK;
+}
+
+qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                         size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad) {
+  if (!st || !energy) return fail(QF_EINVAL, "NULL argument");
+  if ((n_rot && !ansatz) || (n_par && !t) || (n_par && !grad) || (n_terms && !terms))
+    return fail(QF_EINVAL, "NULL array");
+  if (st->n < 64 && (det >> st->n)) return fail(QF_EINVAL, "determinant has a bit at or above the qubit count");
+  std::vector<RotIn> r(n_rot);
+  std::vector<int32_t> par(n_rot);
+  for (size_t k = 0; k < n_rot; ++k) {
+    qf_status v = validate_masks(st, ansatz[k].x, ansatz[k].z);
+    if (v != QF_OK) return v;
+    if (ansatz[k].param < 0 || (size_t)ansatz[k].param >= n_par)
+      return fail(QF_EINVAL, "ansatz parameter index out of range");
+    const double th = ansatz[k].coeff * t[ansatz[k].param];
+    if (!std::isfinite(th)) return fail(QF_EINVAL, "theta is not finite");
+    r[k] = RotIn{ansatz[k].x, ansatz[k].z, th, ansatz[k].coeff};
+    par[k] = ansatz[k].param;
+  }
+  for (size_t k = 0; k < n_terms; ++k) {
+    qf_status v = validate_masks(st, terms[k].x, terms[k].z);
+    if (v != QF_OK) return v;
+  }
+  if (!st->lam && cudaMalloc(&st->lam, st->bytes()) != cudaSuccess) {
+    cudaGetLastError();
+    st->lam = nullptr;
+    return fail(QF_ENOMEM, "cudaMalloc(lambda) failed");
+  }
+  // block structure: sparse composite blocks (same X, same parameter, commuting) or single rotations
+  struct Blk {
+    size_t i, j;
+    bool sparse;
+    qf::SparseArgs fwd, inv;
+  };
+  std::vector<Blk> blocks;
+  for (size_t i = 0; i < n_rot;) {
+    const int run = sparse_run(r.data(), i, n_rot, par.data());
+    Blk b;
+    b.i = i;
+    b.sparse = false;
+    if (run >= 2 && build_sparse(&r[i], run, st->n, false, true, &b.fwd) &&
+        build_sparse(&r[i], run, st->n, true, true, &b.inv) && b.fwd.nr == b.inv.nr) {
+      b.sparse = true;
+      b.j = i + run;
+    } else {
+      b.j = i + 1;
+    }
+    blocks.push_back(b);
+    i = b.j;
+  }
+  qf_status os = ensure_out(st, blocks.size() + 2);
+  if (os != QF_OK) return os;
+  const ExpPlan* p = nullptr;
+  if (n_terms) {
+    qf_status ps = get_plan(st, terms, n_terms, &p);
+    if (ps != QF_OK) return ps;
+  }
+  const int n = st->n;
+  st->scale = 1.0;
+  QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
+  for (const Blk& b : blocks) {
+    if (b.sparse) {
+      QF_CUDA(qf::launch_sparse(st->psi, n, st->dt, b.fwd, st->stream));
+    } else {
+      qf::RotArgs a = rot_args(st->dt, &st->scale, r[b.i].x, r[b.i].z, r[b.i].th);
+      QF_CUDA(qf::launch_rot(st->psi, n, st->dt, a, st->stream));
+    }
+  }
+  const double s_fwd = st->scale;
+  const int nb = qf::reduce_blocks(n, st->dt);
+  double* d_e = st->d_out + blocks.size();
+  if (p) {
+    QF_CUDA(qf::launch_hpsi(st->psi, st->lam, n, st->dt, p->d_groups, p->ngroups, p->d_hchunks, st->d_partials,
+                            st->d_counter, d_e, nb, st->stream));
+  } else {
+    QF_CUDA(cudaMemsetAsync(st->lam, 0, st->bytes(), st->stream));
+    QF_CUDA(cudaMemsetAsync(d_e, 0, 2 * sizeof(double), st->stream));
+  }
+  // reverse sweep; psi and lam share one scale
+  std::vector<double> s2(blocks.size());
+  double sc = s_fwd;
+  for (size_t bi = blocks.size(); bi-- > 0;) {
+    const Blk& b = blocks[bi];
+    s2[bi] = sc * sc;
+    if (b.sparse) {
+      QF_CUDA(qf::launch_adj_sparse(st->psi, st->lam, n, st->dt, b.inv, st->d_partials, st->d_counter,
+                                    st->d_out + bi, nb, st->stream));
+    } else {
+      qf::RotArgs a = rot_args(st->dt, &sc, r[b.i].x, r[b.i].z, -r[b.i].th);
+      QF_CUDA(qf::launch_adj_rot(st->psi, st->lam, n, st->dt, a, st->d_partials, st->d_counter, st->d_out + bi, nb,
+                                 st->stream));
+    }
+  }
+  st->scale = sc;
+  QF_CUDA(cudaMemcpyAsync(st->h_out, st->d_out, (blocks.size() + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                          st->stream));
+  QF_CUDA(cudaStreamSynchronize(st->stream));
+  // U(t)|det> has unit norm; dividing by the computed <psi|psi> (FP64) removes the
+  // rounding drift of the stored norm (the Rayleigh quotient and its gradient;
+  // <psi|P_k|psi> is real, so the gradient needs only the same factor).
+  double nrm = p ? st->h_out[blocks.size() + 1] * s_fwd * s_fwd : 1.0;
+  if (!(nrm > 0.0)) nrm = 1.0;
+  *energy = st->h_out[blocks.size()] * s_fwd * s_fwd / nrm;
+  for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
+  for (size_t bi = 0; bi < blocks.size(); ++bi) {
+    const Blk& b = blocks[bi];
+    const double g = 2.0 * st->h_out[bi] * s2[bi] / nrm;
+    if (b.sparse)
+      grad[par[b.i]] += g;
+    else
+      grad[par[b.i]] += r[b.i].coeff * g;
+  }
+  return QF_OK;
+}
+
+qf_status qf_state_fold_scale(qf_state* st) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  if (st->scale != 1.0) {
+    QF_CUDA(qf::launch_scale(st->psi, st->n, st->dt, st->scale, st->stream));
+    st->scale = 1.0;
+  }
+  return QF_OK;
+}
+
+qf_status qf_state_copy_to_host(qf_state* st, void* host, size_t bytes) {
+  if (!st || !host) return fail(QF_EINVAL, "NULL argument");
+  if (bytes != st->bytes()) return fail(QF_EINVAL, "byte count does not match the state");
+  qf_status f = qf_state_fold_scale(st);
+  if (f != QF_OK) return f;
+  QF_CUDA(cudaMemcpyAsync(host, st->psi, bytes, cudaMemcpyDeviceToHost, st->stream));
+  QF_CUDA(cudaStreamSynchronize(st->stream));
+  return QF_OK;
+}
+
+qf_status qf_state_copy_from_host(qf_state* st, const void* host, size_t bytes) {
+  if (!st || !host) return fail(QF_EINVAL, "NULL argument");
+  if (bytes != st->bytes()) return fail(QF_EINVAL, "byte count does not match the state");
+  QF_CUDA(cudaMemcpyAsync(st->psi, host, bytes, cudaMemcpyHostToDevice, st->stream));
+  st->scale = 1.0;
+  return QF_OK;
+}
+
+qf_status qf_state_info(const qf_state* st, int* n, qf_dtype* dtype, void** dev_ptr, double* scale) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  if (n) *n = st->n;
+  if (dtype) *dtype = st->dt;
+  if (dev_ptr) *dev_ptr = st->psi;
+  if (scale) *scale = st->scale;
+  return QF_OK;
+}
+
+}  // extern "C"

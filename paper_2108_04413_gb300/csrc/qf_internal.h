@@ -1,0 +1,107 @@
+// Internal declarations shared by the kernels (qf_kernels.cu) and the host
+// planner / C ABI (qf_api.cu).  Nothing here is exported.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qf.h"
+
+namespace qf {
+
+// Largest tile / block shapes handled by the fused kernels.
+constexpr int kTileMaxRot = 32;   // rotations fused into one shared-memory tile pass
+constexpr int kTileMaxHiBits = 9; // tile bits above the contiguous low run
+constexpr int kSparseMaxRows = 8; // active rows of a sparse composite block
+constexpr int kSparseMaxCls = 4;  // sign classes (2 distinct outside Z masks)
+constexpr int kSparseMaxSupp = 8; // support qubits of a sparse composite block
+constexpr int kChunkTerms = 4;    // Pauli terms per sign-pattern lookup table
+
+// Rotation coefficient forms.  A rotation exp(-i th P) = c I - i s P is applied
+// as out = A u + B w(v) where w(v) is the quarter-turn/sign image of the
+// partner amplitude.  FORM_AB uses both coefficients (A = c*scale, B =
+// s*scale); FORM_A1 has A = 1, B = tan(th) (the state keeps a factor cos(th)
+// aside); FORM_B1 has A = cot(th), B = 1 (the state keeps sin(th) aside).
+enum { FORM_AB = 0, FORM_A1 = 1, FORM_B1 = 2 };
+
+struct RotArgs {
+  uint64_t x, z;
+  int h;     // highest set bit of x (pair pivot), -1 when x == 0
+  int y;     // popc(x & z)
+  int form;
+  int pad;
+  double A, B;
+};
+
+struct TileRot {
+  uint32_t xl, zl;   // x and the in-tile part of z, in tile-local bit positions
+  uint64_t zout;     // part of z outside the tile bits (a per-tile sign)
+  int hl;            // highest set bit of xl, -1 when xl == 0
+  int y;             // popc(x & z)
+  int form;
+  int pad;
+  double A, B;
+};
+
+struct TileArgs {
+  int m;        // rotations in this pass
+  int s;        // tile bits (2^s amplitudes per tile)
+  int l;        // contiguous low bits 0..l-1 in the tile
+  int nhi;      // s - l tile bits above the low run
+  int pos[kTileMaxHiBits];  // global positions of those bits, ascending
+  int sbits[kTileMaxHiBits + 16];  // all s tile bit positions, ascending
+  TileRot r[kTileMaxRot];
+};
+
+struct SparseArgs {
+  int u;        // support qubits (the common x mask)
+  int nr;       // active rows
+  int ncls;     // sign classes (1, 2 or 4)
+  int nzc;      // distinct outside-Z masks (0, 1 or 2)
+  int supp[kSparseMaxSupp];      // support bit positions, ascending
+  uint64_t pat[kSparseMaxRows];  // global offset of each active row
+  uint64_t zc[2];
+  double2 M[kSparseMaxCls][kSparseMaxRows][kSparseMaxRows];  // composite minus identity (or its inverse's)
+  double2 Q[kSparseMaxCls][kSparseMaxRows][kSparseMaxRows];  // generator sum_k coeff_k P_k
+};
+
+// One X-mask group of Pauli terms for the expectation and H|psi> kernels.
+struct ExpGroup {
+  uint64_t x;
+  int h;        // highest set bit of x, -1 for the diagonal (x = 0) group
+  int nchunk;
+  int chunk0;   // first chunk index
+  int flags;    // bit0: has even-y terms, bit1: has odd-y terms
+};
+
+struct ExpChunk {
+  uint64_t z[kChunkTerms];
+  double2 tab[1 << kChunkTerms];  // (real-part weight, imaginary-part weight) per sign pattern
+};
+
+// Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.
+cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s);
+cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s);
+cudaError_t launch_rot(void* psi, int n, qf_dtype dt, const RotArgs& a, cudaStream_t s);
+cudaError_t launch_tile(void* psi, int n, qf_dtype dt, const TileArgs& a, cudaStream_t s);
+cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, cudaStream_t s);
+// <psi|H|psi> for the grouped plan; writes the sum into out[0] (device).
+cudaError_t launch_expect(const void* psi, int n, qf_dtype dt, const ExpGroup* groups, int ngroups,
+                          const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
+                          int nblocks, cudaStream_t s);
+// lam = H psi, out[0] = Re <psi|lam>, out[1] = <psi|psi>; partials holds 2 * nblocks doubles.
+cudaError_t launch_hpsi(const void* psi, void* lam, int n, qf_dtype dt, const ExpGroup* groups, int ngroups,
+                        const ExpChunk* chunks, double* partials, unsigned* counter, double* out, int nblocks,
+                        cudaStream_t s);
+// Reverse step: out[0] = Im <lam|P|psi> (stored units), then psi, lam <- exp(+i th P).
+cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotArgs& a, double* partials,
+                           unsigned* counter, double* out, int nblocks, cudaStream_t s);
+// Reverse step over a sparse block: out[0] = Im <lam|Q|psi>, then psi, lam <- M psi, M lam
+// (SparseArgs.M holds M - I for the block's inverse M).
+cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, double* partials,
+                              unsigned* counter, double* out, int nblocks, cudaStream_t s);
+
+int reduce_blocks(int n, qf_dtype dt);  // grid size used by the reducing kernels
+void count_launch();
+
+}  // namespace qf

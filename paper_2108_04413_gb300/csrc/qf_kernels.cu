@@ -1,0 +1,771 @@
+// CUDA kernels of libqf for GB300 (sm_103a).
+//
+// Every kernel streams the 2^n-amplitude state vector (interleaved complex,
+// double2 for complex128, float2 for complex64).  The rotation kernels apply
+// exp(-i theta P) (Eq. 9, with the factor -i theta of Eq. 11) as a pair swap
+// b <-> b xor x with the phase i^{popc(x&z)} (-1)^{popc(z&b)} of the Pauli
+// string (Eq. 10); the expectation kernels evaluate exact operator averaging
+// (Eq. 18) with the terms grouped by X mask.  Reductions are FP64 for both
+// state precisions and deterministic (fixed-order second stage).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qf_internal.h"
+
+namespace qf {
+
+namespace {
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using V = double2; };
+template <> struct Cx<float> { using V = float2; };
+
+__device__ __forceinline__ double flip(double v, unsigned neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((unsigned long long)(neg & 1u) << 63));
+}
+__device__ __forceinline__ float flip(float v, unsigned neg) {
+  return __int_as_float(__float_as_int(v) ^ (int)((neg & 1u) << 31));
+}
+
+// i^k * v for k in 0..3, done with component swaps and sign-bit flips only.
+template <typename V>
+__device__ __forceinline__ V qturn(V v, unsigned k) {
+  V o;
+  o.x = flip((k & 1u) ? v.y : v.x, (k ^ (k >> 1)) & 1u);
+  o.y = flip((k & 1u) ? v.x : v.y, (k >> 1) & 1u);
+  return o;
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ V comb(V u, V w, T A, T B, int form) {
+  V o;
+  if (form == FORM_A1) {
+    o.x = fma(B, w.x, u.x);
+    o.y = fma(B, w.y, u.y);
+  } else if (form == FORM_B1) {
+    o.x = fma(A, u.x, w.x);
+    o.y = fma(A, u.y, w.y);
+  } else {
+    o.x = fma(B, w.x, A * u.x);
+    o.y = fma(B, w.y, A * u.y);
+  }
+  return o;
+}
+
+__device__ __forceinline__ uint64_t ins0(uint64_t p, int h) {
+  return ((p >> h) << (h + 1)) | (p & ((1ull << h) - 1ull));
+}
+
+__device__ __forceinline__ unsigned par64(uint64_t v) { return (unsigned)__popcll(v) & 1u; }
+
+// ---------------------------------------------------------------------------
+// deterministic block + grid reduction (the last block to finish sums the
+// per-block partials in index order)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v) {
+  __shared__ double red[32];
+  __syncthreads();
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) v = warp_sum(v);
+  return v;  // valid in thread 0
+}
+
+__device__ void grid_finish(double v, double* partials, unsigned* counter, double* out) {
+  __shared__ bool last;
+  double bs = block_sum(v);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = bs;
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(partials + i);
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+      *out = s;
+      *counter = 0u;
+    }
+  }
+}
+
+// Two sums at once (out[0], out[1]); partials holds 2 * gridDim.x doubles.
+__device__ void grid_finish2(double v0, double v1, double* partials, unsigned* counter, double* out) {
+  __shared__ bool last2;
+  const double b0 = block_sum(v0);
+  const double b1 = block_sum(v1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = b0;
+    partials[2 * blockIdx.x + 1] = b1;
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    last2 = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last2) {
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+      s0 += __ldcg(partials + 2 * i);
+      s1 += __ldcg(partials + 2 * i + 1);
+    }
+    s0 = block_sum(s0);
+    s1 = block_sum(s1);
+    if (threadIdx.x == 0) {
+      out[0] = s0;
+      out[1] = s1;
+      *counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// state preparation
+
+template <typename V>
+__global__ void k_zero_and_set(V* psi, uint64_t N, uint64_t det) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    V v;
+    v.x = (i == det) ? 1 : 0;
+    v.y = 0;
+    psi[i] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_scale(typename Cx<T>::V* psi, uint64_t N, T s) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    auto v = psi[i];
+    v.x *= s;
+    v.y *= s;
+    psi[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// unfused rotation: one read + one write sweep of the state
+//
+// For the pair (b, b' = b xor x) with b's pivot bit h clear and par = popc(z&b) mod 2:
+//   out[b]  = A u + B i^{3+3y+2par} v,     out[b'] = A v + B i^{3+y+2par} u,
+// which is c u - i s (P psi)[b] etc. with A = c, B = s (up to the kept scale).
+// Each thread takes the two pairs (b, b|1) so the partner amplitudes also form
+// an aligned 2-vector (needs h >= 1).
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rot_pair2(typename Cx<T>::V* __restrict__ psi, uint64_t nquads, uint64_t x,
+                                                   uint64_t z, int h, int y, T A, T B, int form) {
+  using V = typename Cx<T>::V;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const unsigned z0 = (unsigned)(z & 1ull);
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nquads; q += stride) {
+    const uint64_t b0 = ins0(q << 1, h);  // even, pivot clear
+    const uint64_t b1 = b0 | 1ull;
+    const uint64_t c0 = b0 ^ x, c1 = b1 ^ x;
+    const V u0 = psi[b0], u1 = psi[b1];
+    const V v0 = psi[c0], v1 = psi[c1];
+    const unsigned p0 = par64(z & b0), p1 = p0 ^ z0;
+    psi[b0] = comb<T, V>(u0, qturn(v0, (3u + 3u * y + 2u * p0) & 3u), A, B, form);
+    psi[b1] = comb<T, V>(u1, qturn(v1, (3u + 3u * y + 2u * p1) & 3u), A, B, form);
+    psi[c0] = comb<T, V>(v0, qturn(u0, (3u + y + 2u * p0) & 3u), A, B, form);
+    psi[c1] = comb<T, V>(v1, qturn(u1, (3u + y + 2u * p1) & 3u), A, B, form);
+  }
+}
+
+// x == 1: the pair is the aligned 2-vector (2q, 2q+1).
+template <typename T>
+__global__ void __launch_bounds__(256) k_rot_pair1(typename Cx<T>::V* __restrict__ psi, uint64_t npairs, uint64_t z,
+                                                   int y, T A, T B, int form) {
+  using V = typename Cx<T>::V;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < npairs; q += stride) {
+    const uint64_t b = q << 1;
+    const V u = psi[b], v = psi[b | 1ull];
+    const unsigned p = par64(z & b);
+    psi[b] = comb<T, V>(u, qturn(v, (3u + 3u * y + 2u * p) & 3u), A, B, form);
+    psi[b | 1ull] = comb<T, V>(v, qturn(u, (3u + y + 2u * p) & 3u), A, B, form);
+  }
+}
+
+// x == 0: diagonal phase, out[b] = A u + B i^{3+2par} u.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rot_diag(typename Cx<T>::V* __restrict__ psi, uint64_t N, uint64_t z, T A,
+                                                  T B, int form) {
+  using V = typename Cx<T>::V;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < N; b += stride) {
+    const V u = psi[b];
+    psi[b] = comb<T, V>(u, qturn(u, (3u + 2u * par64(z & b)) & 3u), A, B, form);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused rotations in a shared-memory tile
+//
+// A tile is the 2^s amplitudes whose bits outside the tile bit set S are fixed
+// (S holds the union of the pass's X supports plus low bits for coalescing).
+// The tile is read once, all m rotations act on it in shared memory (the part
+// of z outside S only flips the sign class of the whole tile), and it is
+// written once.
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tile(typename Cx<T>::V* __restrict__ psi, int n,
+                                              const __grid_constant__ TileArgs a) {
+  using V = typename Cx<T>::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tile = reinterpret_cast<V*>(smem_raw);
+  uint64_t* hitab = reinterpret_cast<uint64_t*>(tile + (1 << a.s));
+  const int s = a.s, l = a.l;
+  const unsigned tsize = 1u << s, lmask = (1u << l) - 1u;
+  for (int j = threadIdx.x; j < (1 << a.nhi); j += blockDim.x) {
+    uint64_t off = 0;
+    for (int i = 0; i < a.nhi; ++i)
+      if ((j >> i) & 1) off |= 1ull << a.pos[i];
+    hitab[j] = off;
+  }
+  const uint64_t ntiles = 1ull << (n - s);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint64_t base = t;
+    for (int i = 0; i < s; ++i) base = ins0(base, a.sbits[i]);
+    __syncthreads();
+    for (unsigned j = threadIdx.x; j < tsize; j += blockDim.x) tile[j] = psi[base | hitab[j >> l] | (j & lmask)];
+    __syncthreads();
+    for (int r = 0; r < a.m; ++r) {
+      const TileRot R = a.r[r];
+      const unsigned pout = par64(R.zout & base);
+      const T A = (T)R.A, B = (T)R.B;
+      if (R.hl < 0) {
+        for (unsigned j = threadIdx.x; j < tsize; j += blockDim.x) {
+          const unsigned p = (__popc(R.zl & j) + pout) & 1u;
+          const V u = tile[j];
+          tile[j] = comb<T, V>(u, qturn(u, (3u + 2u * p) & 3u), A, B, R.form);
+        }
+      } else {
+        const unsigned hmask = (1u << R.hl) - 1u;
+        for (unsigned q = threadIdx.x; q < (tsize >> 1); q += blockDim.x) {
+          const unsigned j = ((q >> R.hl) << (R.hl + 1)) | (q & hmask);
+          const unsigned jp = j ^ R.xl;
+          const unsigned p = (__popc(R.zl & j) + pout) & 1u;
+          const V u = tile[j], v = tile[jp];
+          tile[j] = comb<T, V>(u, qturn(v, (3u + 3u * R.y + 2u * p) & 3u), A, B, R.form);
+          tile[jp] = comb<T, V>(v, qturn(u, (3u + R.y + 2u * p) & 3u), A, B, R.form);
+        }
+      }
+      __syncthreads();
+    }
+    for (unsigned j = threadIdx.x; j < tsize; j += blockDim.x) psi[base | hitab[j >> l] | (j & lmask)] = tile[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sparse composite block
+//
+// The composite of the block's rotations restricted to its support qubits is
+// the identity except on a few "active" support patterns; only those
+// amplitudes are read and written.  One thread per assignment of the
+// non-support bits ("outside index").  SparseArgs.M holds M - I, so each output
+// is v_r + sum_k (M - I)_rk v_k: the rounding then scales with the (small)
+// change rather than with the amplitude, which keeps complex64 states close to
+// unit norm.
+
+template <typename T, bool REAL>
+__global__ void __launch_bounds__(256) k_sparse(typename Cx<T>::V* __restrict__ psi, int n,
+                                                const __grid_constant__ SparseArgs a) {
+  using V = typename Cx<T>::V;
+  __shared__ V M[kSparseMaxCls][kSparseMaxRows][kSparseMaxRows];
+  for (int i = threadIdx.x; i < kSparseMaxCls * kSparseMaxRows * kSparseMaxRows; i += blockDim.x) {
+    const int c = i / (kSparseMaxRows * kSparseMaxRows), r = (i / kSparseMaxRows) % kSparseMaxRows,
+              k = i % kSparseMaxRows;
+    V m;
+    m.x = (T)a.M[c][r][k].x;
+    m.y = (T)a.M[c][r][k].y;
+    M[c][r][k] = m;
+  }
+  __syncthreads();
+  const uint64_t nout = 1ull << (n - a.u);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < nout; o += stride) {
+    uint64_t base = o;
+    for (int i = 0; i < a.u; ++i) base = ins0(base, a.supp[i]);
+    unsigned cls = 0;
+    if (a.nzc > 0) cls = par64(a.zc[0] & base);
+    if (a.nzc > 1) cls |= par64(a.zc[1] & base) << 1;
+    V v[kSparseMaxRows];
+#pragma unroll
+    for (int r = 0; r < kSparseMaxRows; ++r)
+      if (r < a.nr) v[r] = psi[base | a.pat[r]];
+#pragma unroll
+    for (int r = 0; r < kSparseMaxRows; ++r) {
+      if (r < a.nr) {
+        T ox = v[r].x, oy = v[r].y;
+#pragma unroll
+        for (int k = 0; k < kSparseMaxRows; ++k) {
+          if (k < a.nr) {
+            const V m = M[cls][r][k];
+            if (REAL) {
+              ox = fma(m.x, v[k].x, ox);
+              oy = fma(m.x, v[k].y, oy);
+            } else {
+              ox = fma(m.x, v[k].x, fma(-m.y, v[k].y, ox));
+              oy = fma(m.x, v[k].y, fma(m.y, v[k].x, oy));
+            }
+          }
+        }
+        V w;
+        w.x = ox;
+        w.y = oy;
+        psi[base | a.pat[r]] = w;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// expectation value, pair form
+//
+// For an X group g (x != 0) and the pair (b, b xor x) with b's pivot bit clear,
+// w = conj(psi[b xor x]) psi[b]; the pair's contribution from term t is
+//   2 c_t (-1)^{y/2} s_t(b) Re w          (y even)
+//   2 c_t (-1)^{(y+1)/2} s_t(b) Im w      (y odd),
+// s_t(b) = (-1)^{popc(z_t & b)}.  Terms are packed four per chunk with a 16-entry
+// table over their sign pattern, so a chunk costs one lookup and one or two
+// FMAs per pair.  The diagonal group (x = 0) uses |psi_b|^2 and c_t.
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_expect(const typename Cx<T>::V* __restrict__ psi, int n,
+                                                const ExpGroup* __restrict__ groups, int ngroups,
+                                                const ExpChunk* __restrict__ chunks, double* partials,
+                                                unsigned* counter, double* out) {
+  using V = typename Cx<T>::V;
+  const uint64_t hmask = (1ull << (n - 1)) - 1ull;
+  const uint64_t total = (uint64_t)ngroups << (n - 1);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (uint64_t f = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; f < total; f += stride) {
+    const int g = (int)(f >> (n - 1));
+    const uint64_t p = f & hmask;
+    const ExpGroup G = groups[g];
+    if (G.h < 0) {
+      const uint64_t b0 = p << 1;
+      const V u0 = psi[b0], u1 = psi[b0 | 1ull];
+      const double n0 = (double)u0.x * u0.x + (double)u0.y * u0.y;
+      const double n1 = (double)u1.x * u1.x + (double)u1.y * u1.y;
+      for (int c = 0; c < G.nchunk; ++c) {
+        const ExpChunk* C = chunks + G.chunk0 + c;
+        unsigned i0 = 0, i1 = 0;
+#pragma unroll
+        for (int t = 0; t < kChunkTerms; ++t) {
+          const uint64_t zt = C->z[t];
+          const unsigned pb = par64(zt & b0);
+          i0 |= pb << t;
+          i1 |= (pb ^ (unsigned)(zt & 1ull)) << t;
+        }
+        acc = fma(C->tab[i0].x, n0, acc);
+        acc = fma(C->tab[i1].x, n1, acc);
+      }
+    } else {
+      const uint64_t b = ins0(p, G.h);
+      const V u = psi[b], v = psi[b ^ G.x];
+      double rew = 0.0, imw = 0.0;
+      if (G.flags & 1) rew = fma((double)u.x, (double)v.x, (double)u.y * (double)v.y);
+      if (G.flags & 2) imw = fma((double)u.y, (double)v.x, -(double)u.x * (double)v.y);
+      for (int c = 0; c < G.nchunk; ++c) {
+        const ExpChunk* C = chunks + G.chunk0 + c;
+        unsigned idx = 0;
+#pragma unroll
+        for (int t = 0; t < kChunkTerms; ++t) idx |= par64(C->z[t] & b) << t;
+        const double2 D = C->tab[idx];
+        if (G.flags & 1) acc = fma(D.x, rew, acc);
+        if (G.flags & 2) acc = fma(D.y, imw, acc);
+      }
+    }
+  }
+  grid_finish(acc, partials, counter, out);
+}
+
+// ---------------------------------------------------------------------------
+// lam = H psi (gather form) fused with out[0] = Re <psi|lam>, out[1] = <psi|psi>
+//
+// lam[c] = sum_g D_g(c xor x_g) psi[c xor x_g], D_g(b) = sum_t c_t i^{y_t} s_t(b);
+// D is read from the same 16-entry chunk tables (real part from even-y terms,
+// imaginary part from odd-y terms).
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_hpsi(const typename Cx<T>::V* __restrict__ psi,
+                                              typename Cx<T>::V* __restrict__ lam, int n,
+                                              const ExpGroup* __restrict__ groups, int ngroups,
+                                              const ExpChunk* __restrict__ chunks, double* partials,
+                                              unsigned* counter, double* out) {
+  using V = typename Cx<T>::V;
+  const uint64_t N = 1ull << n;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc = 0.0, nrm = 0.0;
+  for (uint64_t cidx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; cidx < N; cidx += stride) {
+    double lx = 0.0, ly = 0.0;
+    for (int g = 0; g < ngroups; ++g) {
+      const ExpGroup G = groups[g];
+      const uint64_t b = cidx ^ G.x;
+      const V v = psi[b];
+      double dx = 0.0, dy = 0.0;
+      for (int c = 0; c < G.nchunk; ++c) {
+        const ExpChunk* C = chunks + G.chunk0 + c;
+        unsigned idx = 0;
+#pragma unroll
+        for (int t = 0; t < kChunkTerms; ++t) idx |= par64(C->z[t] & b) << t;
+        const double2 D = C->tab[idx];
+        dx += D.x;
+        dy += D.y;
+      }
+      const double vx = (double)v.x, vy = (double)v.y;
+      lx = fma(dx, vx, lx);
+      ly = fma(dx, vy, ly);
+      if (G.flags & 2) {
+        lx = fma(-dy, vy, lx);
+        ly = fma(dy, vx, ly);
+      }
+    }
+    const V u = psi[cidx];
+    acc = fma((double)u.x, lx, fma((double)u.y, ly, acc));
+    nrm = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, nrm));
+    V w;
+    w.x = (T)lx;
+    w.y = (T)ly;
+    lam[cidx] = w;
+  }
+  grid_finish2(acc, nrm, partials, counter, out);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint step for one rotation: out = Im <lam|P|psi> (pre-rotation values),
+// then psi and lam both get the rotation given in the arguments (the host passes
+// -theta, i.e. exp(+i theta P)).
+//
+// Over the pair (b, b'): <lam|P|psi> gets i^y s(b) [(-1)^y conj(lam_b) psi_b' +
+// conj(lam_b') psi_b].
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_rot(typename Cx<T>::V* __restrict__ psi,
+                                                 typename Cx<T>::V* __restrict__ lam, int n, uint64_t x, uint64_t z,
+                                                 int h, int y, T A, T B, int form, double* partials, unsigned* counter,
+                                                 double* out) {
+  using V = typename Cx<T>::V;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  const unsigned ym = (unsigned)y & 3u;
+  if (x == 0ull) {
+    const uint64_t N = 1ull << n;
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < N; b += stride) {
+      const V u = psi[b], p = lam[b];
+      const unsigned pb = par64(z & b);
+      // Im(conj(p) s u)
+      const double im = fma((double)p.x, (double)u.y, -(double)p.y * (double)u.x);
+      acc += flip(im, pb);
+      psi[b] = comb<T, V>(u, qturn(u, (3u + 2u * pb) & 3u), A, B, form);
+      lam[b] = comb<T, V>(p, qturn(p, (3u + 2u * pb) & 3u), A, B, form);
+    }
+  } else {
+    const uint64_t npairs = 1ull << (n - 1);
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < npairs; q += stride) {
+      const uint64_t b = ins0(q, h), bp = b ^ x;
+      const V u = psi[b], v = psi[bp], p = lam[b], r = lam[bp];
+      const unsigned pb = par64(z & b);
+      double val;
+      if ((ym & 1u) == 0u) {
+        // Im z1 + Im z2, z1 = conj(p) v, z2 = conj(r) u
+        const double i1 = fma((double)p.x, (double)v.y, -(double)p.y * (double)v.x);
+        const double i2 = fma((double)r.x, (double)u.y, -(double)r.y * (double)u.x);
+        val = flip(i1 + i2, (ym >> 1) ^ pb);
+      } else {
+        // Re z2 - Re z1
+        const double r1 = fma((double)p.x, (double)v.x, (double)p.y * (double)v.y);
+        const double r2 = fma((double)r.x, (double)u.x, (double)r.y * (double)u.y);
+        val = flip(r2 - r1, ((ym >> 1) & 1u) ^ pb);
+      }
+      acc += val;
+      psi[b] = comb<T, V>(u, qturn(v, (3u + 3u * y + 2u * pb) & 3u), A, B, form);
+      psi[bp] = comb<T, V>(v, qturn(u, (3u + y + 2u * pb) & 3u), A, B, form);
+      lam[b] = comb<T, V>(p, qturn(r, (3u + 3u * y + 2u * pb) & 3u), A, B, form);
+      lam[bp] = comb<T, V>(r, qturn(p, (3u + y + 2u * pb) & 3u), A, B, form);
+    }
+  }
+  grid_finish(acc, partials, counter, out);
+}
+
+// adjoint step for a sparse block: out = Im <lam|Q|psi>, then psi <- M psi,
+// lam <- M lam on the active rows (SparseArgs.M holds M - I for the block's
+// inverse composite M).
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_sparse(typename Cx<T>::V* __restrict__ psi,
+                                                    typename Cx<T>::V* __restrict__ lam, int n,
+                                                    const __grid_constant__ SparseArgs a, double* partials,
+                                                    unsigned* counter, double* out) {
+  using V = typename Cx<T>::V;
+  __shared__ V M[kSparseMaxCls][kSparseMaxRows][kSparseMaxRows];
+  __shared__ double2 Q[kSparseMaxCls][kSparseMaxRows][kSparseMaxRows];
+  for (int i = threadIdx.x; i < kSparseMaxCls * kSparseMaxRows * kSparseMaxRows; i += blockDim.x) {
+    const int c = i / (kSparseMaxRows * kSparseMaxRows), r = (i / kSparseMaxRows) % kSparseMaxRows,
+              k = i % kSparseMaxRows;
+    V m;
+    m.x = (T)a.M[c][r][k].x;
+    m.y = (T)a.M[c][r][k].y;
+    M[c][r][k] = m;
+    Q[c][r][k] = a.Q[c][r][k];
+  }
+  __syncthreads();
+  const uint64_t nout = 1ull << (n - a.u);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < nout; o += stride) {
+    uint64_t base = o;
+    for (int i = 0; i < a.u; ++i) base = ins0(base, a.supp[i]);
+    unsigned cls = 0;
+    if (a.nzc > 0) cls = par64(a.zc[0] & base);
+    if (a.nzc > 1) cls |= par64(a.zc[1] & base) << 1;
+    V v[kSparseMaxRows], w[kSparseMaxRows];
+#pragma unroll
+    for (int r = 0; r < kSparseMaxRows; ++r)
+      if (r < a.nr) {
+        v[r] = psi[base | a.pat[r]];
+        w[r] = lam[base | a.pat[r]];
+      }
+#pragma unroll
+    for (int r = 0; r < kSparseMaxRows; ++r) {
+      if (r < a.nr) {
+        double qx = 0.0, qy = 0.0;
+#pragma unroll
+        for (int k = 0; k < kSparseMaxRows; ++k) {
+          if (k < a.nr) {
+            const double2 q = Q[cls][r][k];
+            qx = fma(q.x, (double)v[k].x, fma(-q.y, (double)v[k].y, qx));
+            qy = fma(q.x, (double)v[k].y, fma(q.y, (double)v[k].x, qy));
+          }
+        }
+        acc = fma((double)w[r].x, qy, fma(-(double)w[r].y, qx, acc));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kSparseMaxRows; ++r) {
+      if (r < a.nr) {
+        T ox = v[r].x, oy = v[r].y, px = w[r].x, py = w[r].y;
+#pragma unroll
+        for (int k = 0; k < kSparseMaxRows; ++k) {
+          if (k < a.nr) {
+            const V m = M[cls][r][k];
+            ox = fma(m.x, v[k].x, fma(-m.y, v[k].y, ox));
+            oy = fma(m.x, v[k].y, fma(m.y, v[k].x, oy));
+            px = fma(m.x, w[k].x, fma(-m.y, w[k].y, px));
+            py = fma(m.x, w[k].y, fma(m.y, w[k].x, py));
+          }
+        }
+        V o1, o2;
+        o1.x = ox;
+        o1.y = oy;
+        o2.x = px;
+        o2.y = py;
+        psi[base | a.pat[r]] = o1;
+        lam[base | a.pat[r]] = o2;
+      }
+    }
+  }
+  grid_finish(acc, partials, counter, out);
+}
+
+int g_sms = 0;
+
+int sm_count() {
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 152;
+  }
+  return g_sms;
+}
+
+unsigned grid_for(uint64_t work, int per_sm) {
+  const uint64_t cap = (uint64_t)sm_count() * per_sm;
+  uint64_t g = (work + 255) / 256;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+thread_local uint64_t t_launches = 0;
+
+}  // namespace
+
+void count_launch() { ++t_launches; }
+
+int reduce_blocks(int n, qf_dtype) {
+  const uint64_t cap = (uint64_t)sm_count() * 4;
+  uint64_t g = ((1ull << n) / 2 + 255) / 256;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s) {
+  const uint64_t N = 1ull << n;
+  const unsigned g = grid_for(N, 8);
+  if (dt == QF_C128)
+    k_zero_and_set<double2><<<g, 256, 0, s>>>(static_cast<double2*>(psi), N, det);
+  else
+    k_zero_and_set<float2><<<g, 256, 0, s>>>(static_cast<float2*>(psi), N, det);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s) {
+  const uint64_t N = 1ull << n;
+  const unsigned g = grid_for(N, 8);
+  if (dt == QF_C128)
+    k_scale<double><<<g, 256, 0, s>>>(static_cast<double2*>(psi), N, scale);
+  else
+    k_scale<float><<<g, 256, 0, s>>>(static_cast<float2*>(psi), N, (float)scale);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+static void rot_impl(void* psi, int n, const RotArgs& a, cudaStream_t s) {
+  using V = typename Cx<T>::V;
+  V* p = static_cast<V*>(psi);
+  const uint64_t N = 1ull << n;
+  if (a.x == 0ull) {
+    k_rot_diag<T><<<grid_for(N, 8), 256, 0, s>>>(p, N, a.z, (T)a.A, (T)a.B, a.form);
+  } else if (a.h == 0) {
+    k_rot_pair1<T><<<grid_for(N / 2, 8), 256, 0, s>>>(p, N / 2, a.z, a.y, (T)a.A, (T)a.B, a.form);
+  } else {
+    k_rot_pair2<T><<<grid_for(N / 4, 8), 256, 0, s>>>(p, N / 4, a.x, a.z, a.h, a.y, (T)a.A, (T)a.B, a.form);
+  }
+}
+
+cudaError_t launch_rot(void* psi, int n, qf_dtype dt, const RotArgs& a, cudaStream_t s) {
+  if (dt == QF_C128)
+    rot_impl<double>(psi, n, a, s);
+  else
+    rot_impl<float>(psi, n, a, s);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t tile_impl(void* psi, int n, const TileArgs& a, cudaStream_t s) {
+  using V = typename Cx<T>::V;
+  const size_t smem = (sizeof(V) << a.s) + (sizeof(uint64_t) << a.nhi);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  const uint64_t ntiles = 1ull << (n - a.s);
+  uint64_t g = (uint64_t)sm_count() * 4;
+  if (g > ntiles) g = ntiles;
+  k_tile<T><<<(unsigned)g, 256, smem, s>>>(static_cast<V*>(psi), n, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile(void* psi, int n, qf_dtype dt, const TileArgs& a, cudaStream_t s) {
+  count_launch();
+  return dt == QF_C128 ? tile_impl<double>(psi, n, a, s) : tile_impl<float>(psi, n, a, s);
+}
+
+static bool sparse_is_real(const SparseArgs& a) {
+  for (int c = 0; c < a.ncls; ++c)
+    for (int r = 0; r < a.nr; ++r)
+      for (int k = 0; k < a.nr; ++k)
+        if (a.M[c][r][k].y != 0.0) return false;
+  return true;
+}
+
+cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, cudaStream_t s) {
+  const uint64_t nout = 1ull << (n - a.u);
+  const unsigned g = grid_for(nout, 8);
+  const bool real = sparse_is_real(a);
+  if (dt == QF_C128) {
+    if (real)
+      k_sparse<double, true><<<g, 256, 0, s>>>(static_cast<double2*>(psi), n, a);
+    else
+      k_sparse<double, false><<<g, 256, 0, s>>>(static_cast<double2*>(psi), n, a);
+  } else {
+    if (real)
+      k_sparse<float, true><<<g, 256, 0, s>>>(static_cast<float2*>(psi), n, a);
+    else
+      k_sparse<float, false><<<g, 256, 0, s>>>(static_cast<float2*>(psi), n, a);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expect(const void* psi, int n, qf_dtype dt, const ExpGroup* groups, int ngroups,
+                          const ExpChunk* chunks, double* partials, unsigned* counter, double* out, int nblocks,
+                          cudaStream_t s) {
+  if (dt == QF_C128)
+    k_expect<double><<<nblocks, 256, 0, s>>>(static_cast<const double2*>(psi), n, groups, ngroups, chunks,
+                                             partials, counter, out);
+  else
+    k_expect<float><<<nblocks, 256, 0, s>>>(static_cast<const float2*>(psi), n, groups, ngroups, chunks, partials,
+                                            counter, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hpsi(const void* psi, void* lam, int n, qf_dtype dt, const ExpGroup* groups, int ngroups,
+                        const ExpChunk* chunks, double* partials, unsigned* counter, double* out, int nblocks,
+                        cudaStream_t s) {
+  if (dt == QF_C128)
+    k_hpsi<double><<<nblocks, 256, 0, s>>>(static_cast<const double2*>(psi), static_cast<double2*>(lam), n, groups,
+                                           ngroups, chunks, partials, counter, out);
+  else
+    k_hpsi<float><<<nblocks, 256, 0, s>>>(static_cast<const float2*>(psi), static_cast<float2*>(lam), n, groups,
+                                          ngroups, chunks, partials, counter, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotArgs& a, double* partials,
+                           unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  if (dt == QF_C128)
+    k_adj_rot<double><<<nblocks, 256, 0, s>>>(static_cast<double2*>(psi), static_cast<double2*>(lam), n, a.x, a.z,
+                                              a.h, a.y, a.A, a.B, a.form, partials, counter, out);
+  else
+    k_adj_rot<float><<<nblocks, 256, 0, s>>>(static_cast<float2*>(psi), static_cast<float2*>(lam), n, a.x, a.z, a.h,
+                                             a.y, (float)a.A, (float)a.B, a.form, partials, counter, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, double* partials,
+                              unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  if (dt == QF_C128)
+    k_adj_sparse<double><<<nblocks, 256, 0, s>>>(static_cast<double2*>(psi), static_cast<double2*>(lam), n, a,
+                                                 partials, counter, out);
+  else
+    k_adj_sparse<float><<<nblocks, 256, 0, s>>>(static_cast<float2*>(psi), static_cast<float2*>(lam), n, a,
+                                                partials, counter, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace qf
+
+extern "C" uint64_t qf_kernel_launches(int reset) {
+  const uint64_t v = qf::t_launches;
+  if (reset) qf::t_launches = 0;
+  return v;
+}

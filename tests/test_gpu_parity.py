@@ -1,0 +1,255 @@
+"""GPU vs oracle parity through the C ABI (libqf).
+
+Tolerances (from the accuracy targets of the method's precision options):
+complex128 amplitudes 1e-12 max abs, complex128 energies 1e-10 Eh, complex64
+energies 1e-5 Eh, complex64 gradients 1e-4 relative (in the 2-norm).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import __graft_entry__  # noqa: E402
+
+__graft_entry__.build()
+
+from oracle import fermion, pauli  # noqa: E402
+from paper_2108_04413_gb300 import prep, qf  # noqa: E402
+from workloads import CONFIGS, amplitudes, integrals, random_state  # noqa: E402
+
+TOL_AMP_C128 = 1e-12
+TOL_E_C128 = 1e-10
+TOL_AMP_C64 = 2e-5
+TOL_E_C64 = 1e-5
+TOL_G_C64 = 1e-4
+
+
+def _rots_list(R):
+    return list(zip(R["x"], R["z"], R["theta"]))
+
+
+def _terms_list(T):
+    return list(zip(T["x"], T["z"], T["coeff"]))
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_every_pauli_string_n3(dtype):
+    n = 3
+    tol = TOL_AMP_C128 if dtype == "c128" else TOL_AMP_C64
+    st = qf.State(n, dtype)
+    psi0 = random_state(n, 3)
+    for x in range(8):
+        for z in range(8):
+            th = 0.1 + 0.37 * x - 0.21 * z
+            st.from_numpy(psi0)
+            st.apply_pauli_exp(x, z, th)
+            ref = pauli.rotate(psi0, n, x, z, th)
+            assert np.abs(st.to_numpy() - ref).max() < tol, (x, z)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 2, 5, 12])
+def test_unfused_rotations_random(n, dtype):
+    rng = np.random.default_rng(n)
+    tol = TOL_AMP_C128 if dtype == "c128" else TOL_AMP_C64 * 4
+    st = qf.State(n, dtype)
+    psi = random_state(n, 10 + n)
+    st.from_numpy(psi)
+    for k in range(40):
+        x = int(rng.integers(0, 1 << n)) if k % 5 else (1 if k % 10 else 0)
+        z = int(rng.integers(0, 1 << n))
+        th = float(rng.uniform(-np.pi, np.pi))
+        st.apply_pauli_exp(x, z, th)
+        psi = pauli.rotate(psi, n, x, z, th)
+    assert np.abs(st.to_numpy() - psi).max() < tol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [6, 13, 16])
+def test_circuit_fused_random(n, dtype):
+    """Random weight-2..8 exponentials: exercises tile fusion, diagonal and x=1 cases."""
+    R = prep.random_circuit(n, 120, seed=n)
+    psi0 = np.zeros(1 << n, dtype=complex)
+    psi0[(1 << (n // 2)) - 1] = 1
+    st = qf.State(n, dtype)
+    st.set_basis((1 << (n // 2)) - 1)
+    st.apply_circuit(R)
+    ref = pauli.apply_rotations(psi0, n, _rots_list(R))
+    tol = TOL_AMP_C128 if dtype == "c128" else 1e-4
+    assert np.abs(st.to_numpy() - ref).max() < tol
+
+
+def test_scale_renormalisation_long_circuit():
+    """Many large-angle rotations drive the kept scale through the fold-back path."""
+    n = 7
+    rng = np.random.default_rng(77)
+    R = qf.as_rots(rng.integers(0, 128, 3000), rng.integers(0, 128, 3000), rng.uniform(0.6, 0.97, 3000))
+    st = qf.State(n, "c128")
+    st.set_basis(5)
+    st.apply_circuit(R)
+    ref = pauli.apply_rotations(pauli.basis_state(n, 5), n, _rots_list(R))
+    out = st.to_numpy()
+    assert abs(np.linalg.norm(out) - 1) < 1e-12
+    assert np.abs(out - ref).max() < 1e-11
+
+
+def _ucc_problem(cfg_id):
+    cfg = CONFIGS[cfg_id]
+    h, g = integrals(cfg["n_orb"], cfg["seed"])
+    T = prep.molecular_hamiltonian(h, g)
+    A, exs = prep.uccsd_ansatz(cfg["n_orb"], cfg["n_el"])
+    t = amplitudes(len(exs), cfg["seed"], cfg["t_sigma"])
+    return cfg, h, g, T, A, exs, t
+
+
+@pytest.mark.parametrize("cfg_id", [0, 1])
+def test_ucc_state_and_energy_c128(cfg_id):
+    cfg, h, g, T, A, exs, t = _ucc_problem(cfg_id)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], "c128")
+    st.set_basis(det)
+    st.apply_circuit(prep.bind_thetas(A, t))
+    e, im = st.expectation(T)
+    psi = st.to_numpy()
+    ref = fermion.ucc_state(cfg["n_orb"], cfg["n_el"], t, exs)
+    assert np.abs(psi - ref).max() < TOL_AMP_C128
+    e_ref = np.vdot(ref, fermion.hamiltonian_apply(ref, cfg["n_orb"], h, g)).real
+    assert abs(e - e_ref) < TOL_E_C128
+    assert im == 0.0
+
+
+@pytest.mark.parametrize("cfg_id", [0, 1])
+def test_ucc_energy_c64(cfg_id):
+    cfg, h, g, T, A, exs, t = _ucc_problem(cfg_id)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], "c64")
+    st.set_basis(det)
+    st.apply_circuit(prep.bind_thetas(A, t))
+    e, _ = st.expectation(T)
+    ref = fermion.ucc_state(cfg["n_orb"], cfg["n_el"], t, exs)
+    e_ref = np.vdot(ref, fermion.hamiltonian_apply(ref, cfg["n_orb"], h, g)).real
+    assert abs(e - e_ref) < TOL_E_C64
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_expectation_random_terms_mixed(dtype):
+    """Duplicated terms, x = 0 terms, odd and even Y counts, many groups."""
+    n = 11
+    rng = np.random.default_rng(11)
+    psi = random_state(n, 5)
+    xs = rng.integers(0, 1 << n, 300)
+    xs[:40] = 0
+    xs[40:60] = xs[60:80]
+    zs = rng.integers(0, 1 << n, 300)
+    cs = rng.normal(size=300)
+    T = qf.as_terms(xs, zs, cs)
+    st = qf.State(n, dtype)
+    st.from_numpy(psi)
+    e, _ = st.expectation(T)
+    ref = pauli.expectation(psi, n, _terms_list(T))
+    assert abs(ref.imag) < 1e-12
+    tol = 1e-11 if dtype == "c128" else 1e-5
+    assert abs(e - ref.real) < tol
+
+
+def test_energy_grad_ucc_c128_matches_oracle_adjoint():
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], "c128")
+    e, grad = st.energy_grad(det, A, t, T)
+    e_ref, g_ref = fermion.ucc_gradient_adjoint(cfg["n_orb"], cfg["n_el"], h, g, t, exs)
+    assert abs(e - e_ref) < TOL_E_C128
+    assert np.abs(grad - g_ref).max() < 1e-10
+    # the reverse sweep leaves the reference determinant
+    out = st.to_numpy()
+    assert abs(abs(out[det]) - 1) < 1e-12
+
+
+def test_energy_grad_ucc_16q_fd():
+    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], "c128")
+    e, grad = st.energy_grad(det, A, t, T)
+    rng = np.random.default_rng(1)
+    params = rng.choice(len(t), 20, replace=False)
+    hstep = 1e-4
+    for p in params:
+        tp = t.copy(); tp[p] += hstep
+        tm = t.copy(); tm[p] -= hstep
+        st.set_basis(det); st.apply_circuit(prep.bind_thetas(A, tp)); ep, _ = st.expectation(T)
+        st.set_basis(det); st.apply_circuit(prep.bind_thetas(A, tm)); em, _ = st.expectation(T)
+        fd = (ep - em) / (2 * hstep)
+        assert abs(fd - grad[p]) < 1e-6 * max(1.0, abs(grad[p])), (p, fd, grad[p])
+
+
+def test_energy_grad_generic_ansatz_matches_oracle():
+    """Non-commuting rotations sharing parameters: the unfused adjoint path."""
+    n = 8
+    rng = np.random.default_rng(8)
+    m, npar = 40, 9
+    A = qf.as_arots(rng.integers(0, 256, m), rng.integers(0, 256, m), rng.normal(size=m), rng.integers(0, npar, m))
+    t = rng.normal(size=npar)
+    T = qf.as_terms(rng.integers(0, 256, 60), rng.integers(0, 256, 60), rng.normal(size=60))
+    det = 0b00110101
+    st = qf.State(n, "c128")
+    e, grad = st.energy_grad(det, A, t, T)
+    arots = list(zip(A["x"], A["z"], A["coeff"], A["param"]))
+    e_ref, g_ref, _ = pauli.adjoint_gradient(n, det, arots, t, _terms_list(T))
+    assert abs(e - e_ref) < TOL_E_C128
+    assert np.abs(grad - g_ref).max() < 1e-10
+
+
+def test_energy_grad_c64_relative():
+    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], "c64")
+    e, grad = st.energy_grad(det, A, t, T)
+    ref = qf.State(cfg["n_qubits"], "c128")
+    e_ref, g_ref = ref.energy_grad(det, A, t, T)
+    assert abs(e - e_ref) < TOL_E_C64
+    assert np.linalg.norm(grad - g_ref) / np.linalg.norm(g_ref) < TOL_G_C64
+
+
+def test_invalid_arguments_rejected():
+    st = qf.State(4, "c128")
+    with pytest.raises(qf.QFError) as ei:
+        st.apply_pauli_exp(1 << 4, 0, 0.1)
+    assert ei.value.status == qf.QF_EINVAL
+    with pytest.raises(qf.QFError):
+        st.set_basis(1 << 5)
+    with pytest.raises(qf.QFError):
+        st.expectation(qf.as_terms([0], [1 << 4], [1.0]))
+    A = qf.as_arots([1], [0], [1.0], [3])
+    with pytest.raises(qf.QFError):
+        st.energy_grad(0, A, np.zeros(2), qf.as_terms([0], [1], [1.0]))
+    with pytest.raises(qf.QFError):
+        qf.State(0, "c128")
+    # the state is unchanged by rejected calls
+    st.set_basis(3)
+    assert np.abs(st.to_numpy() - pauli.basis_state(4, 3)).max() == 0
+
+
+def test_empty_inputs():
+    st = qf.State(5, "c128")
+    st.set_basis(7)
+    st.apply_circuit(qf.as_rots([], [], []))
+    assert st.expectation(qf.as_terms([], [], []))[0] == 0.0
+    e, g = st.energy_grad(7, qf.as_arots([], [], [], []), np.zeros(0), qf.as_terms([0], [0], [2.5]))
+    assert abs(e - 2.5) < 1e-15 and len(g) == 0
+
+
+def test_torch_owned_buffer():
+    n = 10
+    buf = torch.empty(2 << n, dtype=torch.float64, device="cuda")
+    st = qf.State(n, "c128", buffer=buf)
+    st.set_basis(3)
+    st.apply_pauli_exp(0b1010, 0b0110, 0.3)
+    st.fold_scale()
+    torch.cuda.synchronize()
+    v = torch.view_as_complex(buf.view(-1, 2)).cpu().numpy()
+    ref = pauli.rotate(pauli.basis_state(n, 3), n, 0b1010, 0b0110, 0.3)
+    assert np.abs(v - ref).max() < 1e-15

@@ -16,7 +16,7 @@ available; the workload shapes follow the hydrogen-chain timings of the
   one draw per canonical quadruple, N(0, 0.05) * exp(-|p-q| - |r-s|);
 * cluster amplitudes t_mu ~ N(0, sigma), drawn as a fixed-length stream so the
   first k values do not depend on how many a caller asks for;
-* random Pauli strings: weight w ~ U{wmin..wmax} distinct qubits, each letter
+* random Pauli strings: weight w ~ U{wmin..min(wmax, n)} distinct qubits, each letter
   uniform in {X, Y, Z}, returned as (x_mask, z_mask) with Y = both bits;
 * random angles theta ~ U(-pi, pi); random Pauli-sum coefficients
   N(0, 1) / sqrt(count);
@@ -66,7 +66,7 @@ def random_pauli_masks(n_qubits: int, count: int, seed: int, wmin: int = 2, wmax
     xs = np.zeros(count, dtype=np.uint64)
     zs = np.zeros(count, dtype=np.uint64)
     for k in range(count):
-        w = int(rng.integers(wmin, wmax + 1))
+        w = int(rng.integers(min(wmin, n_qubits), min(wmax, n_qubits) + 1))
         qubits = rng.choice(n_qubits, size=w, replace=False)
         letters = rng.integers(0, 3, size=w)  # 0 = X, 1 = Y, 2 = Z
         x = 0
