@@ -1,0 +1,510 @@
+#!/usr/bin/env python
+"""Benchmark of the Pauli-exponential state-vector hot path on GB300.
+
+Default workload (one "step" = one energy + full adjoint-gradient evaluation,
+every row of the hot path): 24 qubits (12 spatial orbitals, 12 electrons),
+seeded synthetic molecular integrals -> Jordan-Wigner Hamiltonian (29737 Pauli
+terms in 5479 X-mask groups), dUCCSD ansatz of 1818 excitations (14112 Pauli
+exponentials), t ~ N(0, 0.05), complex128 state (256 MiB, larger than L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload ucc24|ucc16|sweep28] [--dtype c128|c64]
+
+Under torchrun each rank evaluates its own copy of the workload (independent
+problems, no collective); the value is the evaluations of all ranks divided by
+the slowest rank's time.  `--impl reference` times the CPU oracle (the
+reference for this build) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_FMA_PER_CLK_PER_SM = 2  # GB300: 1.25 TFLOP/s nominal FP64 = 152 SMs * 2 FMA * 2 flop * ~2.06 GHz
+N_SMS = 152
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ucc24", choices=["ucc24", "ucc16", "sweep28"])
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the c64 / end-to-end / CPU-baseline legs")
+    return ap.parse_args()
+
+
+def peaks():
+    p = {"hbm_gbs": 6782.8, "bf16_tflops": 1939.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        p.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz") if k in m})
+        p["source"] = "measured"
+    p["fp64_tflops"] = N_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    return p
+
+
+# ----------------------------------------------------------------------------- workloads
+
+
+def ucc_workload(n_orb: int, n_el: int, seed: int, sigma: float):
+    from paper_2108_04413_gb300 import prep
+    from workloads import amplitudes, integrals
+
+    h, g = integrals(n_orb, seed)
+    terms = prep.molecular_hamiltonian(h, g)
+    ansatz, exs = prep.uccsd_ansatz(n_orb, n_el)
+    t = amplitudes(len(exs), seed, sigma)
+    return dict(n=2 * n_orb, det=(1 << n_el) - 1, terms=terms, ansatz=ansatz, exs=exs, t=t, h=h, g=g,
+                n_orb=n_orb, n_el=n_el)
+
+
+def group_stats(terms, n):
+    """Per X-mask group: (terms, chunks of four, has odd-Y terms)."""
+    x = terms["x"]
+    z = terms["z"]
+    y = np.array([bin(int(a) & int(b)).count("1") for a, b in zip(x, z)])
+    order = np.argsort(x, kind="stable")
+    xs = x[order]
+    ys = y[order]
+    starts = np.flatnonzero(np.r_[True, xs[1:] != xs[:-1]])
+    ends = np.r_[starts[1:], len(xs)]
+    out = []
+    for s, e in zip(starts, ends):
+        cnt = e - s
+        out.append((int(cnt), int((cnt + 3) // 4), bool(np.any(ys[s:e] & 1))))
+    return out
+
+
+def hpsi_flops(stats, n):
+    """FP64 flops of one H|psi> launch as written: per group and amplitude a
+    (real or complex) D * psi multiply-add and the chunk-table sums, plus the
+    energy and norm accumulations."""
+    N = 1 << n
+    f = 0
+    for cnt, nch, odd in stats:
+        comps = 2 if odd else 1
+        f += 4 * comps + 2 * (nch - 1) * comps
+    return N * (f + 8)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [c.strip() for c in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax = float(p[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- distributed
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl"
+        import torch
+
+        if not torch.cuda.is_available():
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v: float) -> float:
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+
+
+def oracle_sample_ucc(w, budget_s: float = 15.0):
+    """Time the oracle on a bounded sample of one energy+gradient evaluation:
+    a few rotations and a few Hamiltonian terms on the full state, then scale by
+    the counts of one evaluation (forward rotations, reverse rotations on two
+    states with one overlap each, and one H|psi> term application per term)."""
+    from oracle import pauli
+
+    n = w["n"]
+    psi = pauli.basis_state(n, w["det"])
+    A = w["ansatz"]
+    T = w["terms"]
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    nrot = 0
+    while True:
+        k = int(rng.integers(0, len(A)))
+        psi = pauli.rotate(psi, n, int(A["x"][k]), int(A["z"][k]), 0.01)
+        nrot += 1
+        if time.perf_counter() - t0 > budget_s / 2 or nrot >= 16:
+            break
+    t_rot = (time.perf_counter() - t0) / nrot
+    t1 = time.perf_counter()
+    nterm = 0
+    acc = np.zeros_like(psi)
+    while True:
+        k = int(rng.integers(0, len(T)))
+        acc += T["coeff"][k] * pauli.apply(psi, n, int(T["x"][k]), int(T["z"][k]))
+        nterm += 1
+        if time.perf_counter() - t1 > budget_s / 2 or nterm >= 16:
+            break
+    t_term = (time.perf_counter() - t1) / nterm
+    K = len(A)
+    t_eval = t_rot * (K + 2 * K) + t_term * (len(T) + K)
+    sample = (f"{nrot} Pauli exponentials and {nterm} Hamiltonian terms of the {n}-qubit workload on the full "
+              f"state, scaled to one evaluation ({K} forward + {2 * K} reverse rotations, {K} overlaps, "
+              f"{len(T)} terms)")
+    return t_eval, sample
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args, rank, world, local, pg):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2108_04413_gb300 import prep, qf
+
+    torch.cuda.set_device(local)
+    pk = peaks()
+    if args.workload == "sweep28":
+        return run_sweep28(args, rank, world, local, pg, pk)
+    cfg = {"ucc24": (12, 12, 2, 0.05), "ucc16": (8, 8, 1, 0.1)}[args.workload]
+    w = ucc_workload(*cfg)
+    n = w["n"]
+    stream = torch.cuda.Stream()
+    st = qf.State(n, args.dtype, stream=stream)
+    S = 16 if args.dtype == "c128" else 8
+    N = 1 << n
+    for _ in range(args.warmup):
+        st.energy_grad(w["det"], w["ansatz"], w["t"], w["terms"])
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    qf.profile_begin(qf.K_ALL)
+    qf.kernel_launches(reset=True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    energies = []
+    for _ in range(args.steps):
+        e, g = st.energy_grad(w["det"], w["ansatz"], w["t"], w["terms"])
+        energies.append(e)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms = e0.elapsed_time(e1)
+    launches = qf.kernel_launches(reset=True)
+    per_kind = {}
+    for kbit, name in qf.KIND_NAMES.items():
+        cnt, kms = qf.profile_read(kbit)
+        if cnt:
+            per_kind[name] = {"launches": cnt, "ms": kms}
+    qf.profile_end()
+    clk = clocks.stop()
+    ms_max = max_over_ranks(pg, ms)
+    step_ms = ms_max / args.steps
+    value = world * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel
+    dom = max(per_kind.items(), key=lambda kv: kv[1]["ms"])[0]
+    stats = group_stats(w["terms"], n)
+    roof = roofline_for(dom, per_kind[dom], w, stats, n, S, pk, args.dtype)
+
+    out = {
+        "metric": "energy+grad evals/s",
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.dtype == "c128" else "f32 state, f64 reductions",
+        "data": "synthetic (seeded integrals, dUCCSD amplitudes)",
+        "config": {
+            "workload": f"{n}-qubit dUCCSD energy + adjoint gradient ({args.workload})",
+            "qubits": n, "state": args.dtype, "excitations": len(w["exs"]), "rotations": int(len(w["ansatz"])),
+            "pauli_terms": int(len(w["terms"])), "xmask_groups": len(stats),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": f"state {N * S >> 20} MiB > 129 MB L2 (no flush needed)",
+        },
+        "rotations_amplitudes_per_s": value * 3 * len(w["ansatz"]) * N,
+        "energy": float(energies[-1]),
+        "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps} for k, v in per_kind.items()},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_extras:
+        out["e2e"] = e2e_leg(st, w, args, stats, stream)
+        if args.dtype == "c128":
+            out["c64"] = c64_leg(w, args, value, float(energies[-1]), g)
+        t_eval, sample = oracle_sample_ucc(w)
+        out["cpu_baseline"] = {"value": 1.0 / t_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                               "sample": sample}
+    st.close()
+    return out
+
+
+def roofline_for(kind, rec, w, stats, n, S, pk, dtype):
+    N = 1 << n
+    avg_s = rec["ms"] / rec["launches"] / 1e3
+    if kind in ("hpsi",) and dtype == "c128":
+        fl = hpsi_flops(stats, n)
+        ach = fl / avg_s / 1e12
+        return {"kernel": "k_hpsi", "bound": "alu", "achieved": ach, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": ach / pk["fp64_tflops"], "traffic": None,
+                "algorithmic": f"{fl:.4g} FP64 flop per launch",
+                "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock (derived)",
+                "hbm_gbs_as_issued": (len(stats) + 1) * N * S / avg_s / 1e9 + N * S / avg_s / 1e9}
+    if kind in ("hpsi",):
+        by = (len(stats) + 2) * N * S
+        ach = by / avg_s / 1e9
+        return {"kernel": "k_hpsi", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None}
+    if kind in ("sparse", "adj_sparse"):
+        # each UCC block touches the active rows only: 2 of 16 support patterns (doubles), 2 of 4 (singles)
+        frac_rows = sum((2 / 16 if len(e[0]) == 2 else 2 / 4) for e in w["exs"]) / len(w["exs"])
+        nst = 2 if kind == "adj_sparse" else 1
+        by = 2 * nst * N * S * frac_rows
+        ach = by / avg_s / 1e9
+        return {"kernel": "k_" + kind, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None}
+    by = 2 * N * S
+    ach = by / avg_s / 1e9
+    return {"kernel": "k_" + kind, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / pk["hbm_gbs"], "traffic": None}
+
+
+def e2e_leg(st, w, args, stats, stream):
+    """Through the public call with host buffers: every step re-plans and uploads
+    the Hamiltonian (grouping on the host, H2D copy of the group tables), copies
+    the parameters in and reads energy and gradient back."""
+    import torch
+
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st.clear_plans()
+        st.energy_grad(w["det"], w["ansatz"], w["t"], w["terms"])
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    ngroups = len(stats)
+    nchunks = sum(s[1] for s in stats)
+    h2d = ngroups * 24 + 2 * nchunks * 288 + 8 * len(w["t"])
+    d2h = 8 * (len(w["exs"]) + 2)
+    return {"value": 1.0 / dt, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps}
+
+
+def c64_leg(w, args, value128, e128, g128):
+    import torch
+
+    from paper_2108_04413_gb300 import qf
+
+    stream = torch.cuda.Stream()
+    st = qf.State(w["n"], "c64", stream=stream)
+    for _ in range(2):
+        st.energy_grad(w["det"], w["ansatz"], w["t"], w["terms"])
+    torch.cuda.synchronize()
+    steps = max(2, args.steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        e, g = st.energy_grad(w["det"], w["ansatz"], w["t"], w["terms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    v = steps / (e0.elapsed_time(e1) / 1e3)
+    st.close()
+    return {"value": v, "unit": "evals/s", "speedup_vs_c128": v / value128, "energy_err_vs_c128": abs(e - e128),
+            "grad_rel_err_vs_c128": float(np.linalg.norm(g - g128) / np.linalg.norm(g128))}
+
+
+def run_sweep28(args, rank, world, local, pg, pk):
+    """28-qubit random Pauli exponentials (500, weight 2..8, theta ~ U(-pi, pi)):
+    fused circuit application, rotations*amplitudes/s."""
+    import torch
+
+    from paper_2108_04413_gb300 import prep, qf
+
+    n = 28
+    R = prep.random_circuit(n, 500, 3)
+    stream = torch.cuda.Stream()
+    st = qf.State(n, args.dtype, stream=stream)
+    S = 16 if args.dtype == "c128" else 8
+    N = 1 << n
+    det = (1 << 14) - 1
+    for _ in range(args.warmup):
+        st.set_basis(det)
+        st.apply_circuit(R)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    qf.profile_begin(qf.K_ALL)
+    qf.kernel_launches(reset=True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st.set_basis(det)
+        st.apply_circuit(R)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms = max_over_ranks(pg, e0.elapsed_time(e1))
+    launches = qf.kernel_launches(reset=True)
+    per_kind = {}
+    for kbit, name in qf.KIND_NAMES.items():
+        cnt, kms = qf.profile_read(kbit)
+        if cnt:
+            per_kind[name] = {"launches": cnt, "ms": kms}
+    qf.profile_end()
+    clk = clocks.stop()
+    value = world * args.steps * len(R) * N / (ms / 1e3)
+    dom = max(per_kind.items(), key=lambda kv: kv[1]["ms"])[0]
+    rec = per_kind[dom]
+    avg_s = rec["ms"] / rec["launches"] / 1e3
+    by = 2 * N * S
+    roof = {"kernel": "k_" + dom, "bound": "hbm", "achieved": by / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": by / avg_s / 1e9 / pk["hbm_gbs"], "traffic": None}
+    out = {"metric": "rotations·amplitudes/s", "value": value, "unit": "rotation·amplitudes/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.dtype == "c128" else "f32",
+           "data": "synthetic (seeded random Pauli strings)",
+           "config": {"workload": "28-qubit 500 random Pauli exponentials (sweep28)", "qubits": n,
+                      "state": args.dtype, "l2": f"state {N * S >> 20} MiB > L2"},
+           "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps} for k, v in
+                       per_kind.items()},
+           "roofline": roof, "gpu_launches": int(launches), "clocks": clk}
+    st.close()
+    return out
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    cfg = {"ucc24": (12, 12, 2, 0.05), "ucc16": (8, 8, 1, 0.1), "sweep28": None}[args.workload]
+    if cfg is None:
+        return {"impl": "reference", "unavailable": "the oracle needs hours per 28-qubit step; use ucc24"}
+    w = ucc_workload(*cfg)
+    times = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        t_eval, sample = oracle_sample_ucc(w, budget_s=4.0)
+        if i >= args.warmup:
+            times.append(t_eval)
+    v = 1.0 / statistics.mean(times)
+    return {"impl": "reference", "metric": "energy+grad evals/s", "value": v, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded integrals, dUCCSD amplitudes)",
+            "config": {"workload": f"{w['n']}-qubit dUCCSD energy + adjoint gradient ({args.workload})"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": v, "unit": "evals/s"},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    rank, world, local, pg = dist_setup()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_gpu(args, rank, world, local, pg)
+    if rank == 0 and out is not None:
+        print(json.dumps(out, default=lambda o: o.item() if hasattr(o, "item") else str(o)))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

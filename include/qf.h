@@ -114,9 +114,33 @@ qf_status qf_state_fold_scale(qf_state* st);
  * current scale (amplitudes = scale * stored values).  Any pointer may be NULL. */
 qf_status qf_state_info(const qf_state* st, int* n, qf_dtype* dtype, void** dev_ptr, double* scale);
 
+/* Drop the Pauli-sum plans (X-mask groups and their tables) cached in the
+ * handle, so the next qf_expectation / qf_energy_grad groups and uploads its
+ * terms again. */
+qf_status qf_state_clear_plans(qf_state* st);
+
 /* Number of kernels this thread's calls have launched since the last reset
  * (reset = 1 clears the counter after reading). */
 uint64_t qf_kernel_launches(int reset);
+
+/* Kernel kinds for the timing calls below. */
+#define QF_K_SET 1u          /* basis preparation, scale folding */
+#define QF_K_ROT 2u          /* unfused rotation (one pair sweep) */
+#define QF_K_TILE 4u         /* fused rotations in shared-memory tiles */
+#define QF_K_SPARSE 8u       /* sparse composite block */
+#define QF_K_EXPECT 16u      /* grouped expectation value */
+#define QF_K_HPSI 32u        /* H|psi> with <psi|H|psi> and <psi|psi> */
+#define QF_K_ADJ_ROT 64u     /* adjoint step of one rotation */
+#define QF_K_ADJ_SPARSE 128u /* adjoint step of a sparse block */
+
+/* Kernel timing for this host thread: after qf_profile_begin(mask), every launch
+ * of a kind in mask is bracketed by two CUDA events recorded on its stream.
+ * qf_profile_read waits for the recorded events and returns, for the kinds in
+ * mask, the number of launches and their summed device time in milliseconds.
+ * qf_profile_end stops recording and drops the records. */
+qf_status qf_profile_begin(unsigned kind_mask);
+qf_status qf_profile_read(unsigned kind_mask, uint64_t* launches, double* total_ms);
+qf_status qf_profile_end(void);
 
 /* Thread-local message describing the last failure. */
 const char* qf_last_error(void);

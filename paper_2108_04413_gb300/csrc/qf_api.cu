@@ -685,6 +685,33 @@ qf_status qf_state_copy_from_host(qf_state* st, const void* host, size_t bytes) 
   return QF_OK;
 }
 
+qf_status qf_state_clear_plans(qf_state* st) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  cudaStreamSynchronize(st->stream);
+  for (auto& kv : st->plans) {
+    cudaFree(kv.second.d_groups);
+    cudaFree(kv.second.d_echunks);
+    cudaFree(kv.second.d_hchunks);
+  }
+  st->plans.clear();
+  return QF_OK;
+}
+
+qf_status qf_profile_begin(unsigned kind_mask) {
+  qf::profile_begin(kind_mask);
+  return QF_OK;
+}
+
+qf_status qf_profile_read(unsigned kind_mask, uint64_t* launches, double* total_ms) {
+  QF_CUDA(qf::profile_read(kind_mask, launches, total_ms));
+  return QF_OK;
+}
+
+qf_status qf_profile_end(void) {
+  qf::profile_end();
+  return QF_OK;
+}
+
 qf_status qf_state_info(const qf_state* st, int* n, qf_dtype* dtype, void** dev_ptr, double* scale) {
   if (!st) return fail(QF_EINVAL, "state is NULL");
   if (n) *n = st->n;

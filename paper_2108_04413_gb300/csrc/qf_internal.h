@@ -103,5 +103,8 @@ cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const Sp
 
 int reduce_blocks(int n, qf_dtype dt);  // grid size used by the reducing kernels
 void count_launch();
+int profile_begin(unsigned mask);
+cudaError_t profile_read(unsigned mask, uint64_t* launches, double* total_ms);
+void profile_end();
 
 }  // namespace qf

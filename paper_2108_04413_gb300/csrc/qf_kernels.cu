@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "qf_internal.h"
 
 namespace qf {
@@ -607,9 +609,73 @@ unsigned grid_for(uint64_t work, int per_sm) {
 
 thread_local uint64_t t_launches = 0;
 
+// opt-in per-launch event timing
+struct ProfRec {
+  unsigned kind;
+  cudaEvent_t a, b;
+};
+thread_local unsigned t_prof_mask = 0;
+thread_local std::vector<ProfRec> t_prof;
+thread_local std::vector<cudaEvent_t> t_ev_pool;
+thread_local size_t t_prof_used = 0;
+
+cudaEvent_t pool_event(size_t i) {
+  while (t_ev_pool.size() <= i) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    t_ev_pool.push_back(e);
+  }
+  return t_ev_pool[i];
+}
+
+// Records the start event of a launch of `kind` (if profiled); returns a slot.
+int prof_pre(unsigned kind, cudaStream_t s) {
+  if (!(t_prof_mask & kind)) return -1;
+  ProfRec r{kind, pool_event(2 * t_prof_used), pool_event(2 * t_prof_used + 1)};
+  ++t_prof_used;
+  cudaEventRecord(r.a, s);
+  t_prof.push_back(r);
+  return (int)t_prof.size() - 1;
+}
+
+void prof_post(int slot, cudaStream_t s) {
+  if (slot >= 0) cudaEventRecord(t_prof[slot].b, s);
+}
+
 }  // namespace
 
 void count_launch() { ++t_launches; }
+
+int profile_begin(unsigned mask) {
+  t_prof.clear();
+  t_prof_used = 0;
+  t_prof_mask = mask;
+  return 0;
+}
+
+cudaError_t profile_read(unsigned mask, uint64_t* launches, double* total_ms) {
+  uint64_t n = 0;
+  double ms = 0.0;
+  for (const ProfRec& r : t_prof) {
+    if (!(r.kind & mask)) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return e;
+    float f = 0.f;
+    e = cudaEventElapsedTime(&f, r.a, r.b);
+    if (e != cudaSuccess) return e;
+    ms += f;
+    ++n;
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  return cudaSuccess;
+}
+
+void profile_end() {
+  t_prof_mask = 0;
+  t_prof.clear();
+  t_prof_used = 0;
+}
 
 int reduce_blocks(int n, qf_dtype) {
   const uint64_t cap = (uint64_t)sm_count() * 4;
@@ -620,23 +686,27 @@ int reduce_blocks(int n, qf_dtype) {
 }
 
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_SET, s);
   const uint64_t N = 1ull << n;
   const unsigned g = grid_for(N, 8);
   if (dt == QF_C128)
     k_zero_and_set<double2><<<g, 256, 0, s>>>(static_cast<double2*>(psi), N, det);
   else
     k_zero_and_set<float2><<<g, 256, 0, s>>>(static_cast<float2*>(psi), N, det);
+  prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_SET, s);
   const uint64_t N = 1ull << n;
   const unsigned g = grid_for(N, 8);
   if (dt == QF_C128)
     k_scale<double><<<g, 256, 0, s>>>(static_cast<double2*>(psi), N, scale);
   else
     k_scale<float><<<g, 256, 0, s>>>(static_cast<float2*>(psi), N, (float)scale);
+  prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
 }
@@ -656,10 +726,12 @@ static void rot_impl(void* psi, int n, const RotArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_rot(void* psi, int n, qf_dtype dt, const RotArgs& a, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_ROT, s);
   if (dt == QF_C128)
     rot_impl<double>(psi, n, a, s);
   else
     rot_impl<float>(psi, n, a, s);
+  prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
 }
@@ -681,8 +753,11 @@ static cudaError_t tile_impl(void* psi, int n, const TileArgs& a, cudaStream_t s
 }
 
 cudaError_t launch_tile(void* psi, int n, qf_dtype dt, const TileArgs& a, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_TILE, s);
+  cudaError_t e = dt == QF_C128 ? tile_impl<double>(psi, n, a, s) : tile_impl<float>(psi, n, a, s);
+  prof_post(prof_slot_, s);
   count_launch();
-  return dt == QF_C128 ? tile_impl<double>(psi, n, a, s) : tile_impl<float>(psi, n, a, s);
+  return e;
 }
 
 static bool sparse_is_real(const SparseArgs& a) {
@@ -694,6 +769,7 @@ static bool sparse_is_real(const SparseArgs& a) {
 }
 
 cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_SPARSE, s);
   const uint64_t nout = 1ull << (n - a.u);
   const unsigned g = grid_for(nout, 8);
   const bool real = sparse_is_real(a);
@@ -708,6 +784,7 @@ cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, cu
     else
       k_sparse<float, false><<<g, 256, 0, s>>>(static_cast<float2*>(psi), n, a);
   }
+  prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
 }
@@ -715,12 +792,14 @@ cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, cu
 cudaError_t launch_expect(const void* psi, int n, qf_dtype dt, const ExpGroup* groups, int ngroups,
                           const ExpChunk* chunks, double* partials, unsigned* counter, double* out, int nblocks,
                           cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_EXPECT, s);
   if (dt == QF_C128)
     k_expect<double><<<nblocks, 256, 0, s>>>(static_cast<const double2*>(psi), n, groups, ngroups, chunks,
                                              partials, counter, out);
   else
     k_expect<float><<<nblocks, 256, 0, s>>>(static_cast<const float2*>(psi), n, groups, ngroups, chunks, partials,
                                             counter, out);
+  prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
 }
@@ -728,36 +807,42 @@ cudaError_t launch_expect(const void* psi, int n, qf_dtype dt, const ExpGroup* g
 cudaError_t launch_hpsi(const void* psi, void* lam, int n, qf_dtype dt, const ExpGroup* groups, int ngroups,
                         const ExpChunk* chunks, double* partials, unsigned* counter, double* out, int nblocks,
                         cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_HPSI, s);
   if (dt == QF_C128)
     k_hpsi<double><<<nblocks, 256, 0, s>>>(static_cast<const double2*>(psi), static_cast<double2*>(lam), n, groups,
                                            ngroups, chunks, partials, counter, out);
   else
     k_hpsi<float><<<nblocks, 256, 0, s>>>(static_cast<const float2*>(psi), static_cast<float2*>(lam), n, groups,
                                           ngroups, chunks, partials, counter, out);
+  prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotArgs& a, double* partials,
                            unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_ADJ_ROT, s);
   if (dt == QF_C128)
     k_adj_rot<double><<<nblocks, 256, 0, s>>>(static_cast<double2*>(psi), static_cast<double2*>(lam), n, a.x, a.z,
                                               a.h, a.y, a.A, a.B, a.form, partials, counter, out);
   else
     k_adj_rot<float><<<nblocks, 256, 0, s>>>(static_cast<float2*>(psi), static_cast<float2*>(lam), n, a.x, a.z, a.h,
                                              a.y, (float)a.A, (float)a.B, a.form, partials, counter, out);
+  prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, double* partials,
                               unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_ADJ_SPARSE, s);
   if (dt == QF_C128)
     k_adj_sparse<double><<<nblocks, 256, 0, s>>>(static_cast<double2*>(psi), static_cast<double2*>(lam), n, a,
                                                  partials, counter, out);
   else
     k_adj_sparse<float><<<nblocks, 256, 0, s>>>(static_cast<float2*>(psi), static_cast<float2*>(lam), n, a,
                                                 partials, counter, out);
+  prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
 }

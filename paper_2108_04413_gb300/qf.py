@@ -42,7 +42,11 @@ _SIGS = {
     "qf_state_fold_scale": (ctypes.c_int, [_vp]),
     "qf_state_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(_vp), _dp]),
+    "qf_state_clear_plans": (ctypes.c_int, [_vp]),
     "qf_kernel_launches": (ctypes.c_uint64, [ctypes.c_int]),
+    "qf_profile_begin": (ctypes.c_int, [ctypes.c_uint]),
+    "qf_profile_read": (ctypes.c_int, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint64), _dp]),
+    "qf_profile_end": (ctypes.c_int, []),
     "qf_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -66,6 +70,26 @@ def _check(status: int) -> None:
 
 def kernel_launches(reset: bool = False) -> int:
     return int(_lib.qf_kernel_launches(1 if reset else 0))
+
+
+K_SET, K_ROT, K_TILE, K_SPARSE, K_EXPECT, K_HPSI, K_ADJ_ROT, K_ADJ_SPARSE = (1 << i for i in range(8))
+K_ALL = 255
+KIND_NAMES = {K_SET: "set", K_ROT: "rot", K_TILE: "tile", K_SPARSE: "sparse", K_EXPECT: "expect",
+              K_HPSI: "hpsi", K_ADJ_ROT: "adj_rot", K_ADJ_SPARSE: "adj_sparse"}
+
+
+def profile_begin(mask: int = K_ALL) -> None:
+    _check(_lib.qf_profile_begin(mask))
+
+
+def profile_read(mask: int):
+    n, ms = ctypes.c_uint64(), _d()
+    _check(_lib.qf_profile_read(mask, ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+def profile_end() -> None:
+    _check(_lib.qf_profile_end())
 
 
 def _ptr(a: np.ndarray):
@@ -141,6 +165,9 @@ class State:
         _check(_lib.qf_energy_grad(self._h, int(det), _ptr(ansatz), len(ansatz), _ptr(t), len(t), _ptr(terms),
                                    len(terms), ctypes.byref(e), _ptr(grad)))
         return e.value, grad
+
+    def clear_plans(self):
+        _check(_lib.qf_state_clear_plans(self._h))
 
     def fold_scale(self):
         _check(_lib.qf_state_fold_scale(self._h))
