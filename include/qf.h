@@ -142,6 +142,34 @@ qf_status qf_profile_begin(unsigned kind_mask);
 qf_status qf_profile_read(unsigned kind_mask, uint64_t* launches, double* total_ms);
 qf_status qf_profile_end(void);
 
+/* Allocation-free expectation value.  The paper has no counterpart: this call
+ * exists for callers that cannot allocate device memory -- for instance when
+ * all of the GPU's memory is already reserved by another allocator (a
+ * framework's caching pool, a serving process with a fixed memory budget), or
+ * in a latency-critical loop that must not take cudaMalloc's implicit device
+ * synchronisation.  qf_expectation needs a qf_state, whose creation allocates;
+ * this call computes the same <psi|H|psi> (same kernel, same precision) from
+ * amplitudes the caller owns.
+ *   amplitudes: device pointer to 2^n amplitudes in the layout above (the state
+ *     itself, no separate scale), 16-byte aligned; not modified.
+ *   stream: cudaStream_t the work is queued on (NULL = legacy default stream);
+ *     the call synchronises it before returning *re (and *im = 0).
+ *   terms: host array of n_terms <= QF_NOALLOC_MAX_TERMS terms (more gives
+ *     QF_EINVAL before any GPU work).
+ * It calls no cudaMalloc / cudaFree: its scratch (reduction partials, counter,
+ * result and grouped term tables) is one static device array of
+ * QF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make the first call on each device before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (the counter is cleared at each call's start): calls whose GPU work
+ * may overlap -- other streams, other host threads -- race and must be ordered
+ * by the caller. */
+#define QF_NOALLOC_MAX_TERMS 2048
+#define QF_NOALLOC_SCRATCH_BYTES (1u << 20)
+qf_status qf_expectation_noalloc(const void* amplitudes, int n, qf_dtype dtype, void* stream,
+                                 const qf_term* terms, size_t n_terms, double* re, double* im);
+
 /* Thread-local message describing the last failure. */
 const char* qf_last_error(void);
 

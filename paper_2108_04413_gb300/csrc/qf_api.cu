@@ -54,6 +54,8 @@ uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603u
 
 }  // namespace
 
+void qf::set_last_error(const std::string& msg) { t_err = msg; }
+
 struct qf_state {
   int n = 0;
   qf_dtype dt = QF_C128;

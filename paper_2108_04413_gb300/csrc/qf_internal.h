@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "qf.h"
 
 namespace qf {
@@ -106,5 +108,6 @@ void count_launch();
 int profile_begin(unsigned mask);
 cudaError_t profile_read(unsigned mask, uint64_t* launches, double* total_ms);
 void profile_end();
+void set_last_error(const std::string& msg);  // message returned by qf_last_error (this thread)
 
 }  // namespace qf

@@ -47,6 +47,7 @@ _SIGS = {
     "qf_profile_begin": (ctypes.c_int, [ctypes.c_uint]),
     "qf_profile_read": (ctypes.c_int, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint64), _dp]),
     "qf_profile_end": (ctypes.c_int, []),
+    "qf_expectation_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _sz, _dp, _dp]),
     "qf_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -66,6 +67,19 @@ class QFError(RuntimeError):
 def _check(status: int) -> None:
     if status != QF_OK:
         raise QFError(status, _lib.qf_last_error().decode(errors="replace"))
+
+
+QF_NOALLOC_MAX_TERMS = 2048
+
+
+def expectation_noalloc(amplitudes_ptr: int, n: int, dtype: str, stream_ptr: int, terms: np.ndarray):
+    """<psi|H|psi> from caller-owned device amplitudes without any device
+    allocation (qf_expectation_noalloc); returns (re, im)."""
+    terms = np.ascontiguousarray(terms, dtype=TERM_DTYPE)
+    re, im = _d(), _d()
+    _check(_lib.qf_expectation_noalloc(_vp(amplitudes_ptr), int(n), QF_C128 if dtype == "c128" else QF_C64,
+                                       _vp(stream_ptr), _ptr(terms), len(terms), ctypes.byref(re), ctypes.byref(im)))
+    return re.value, im.value
 
 
 def kernel_launches(reset: bool = False) -> int:

@@ -1,0 +1,60 @@
+"""qf_expectation_noalloc: the allocation-free expectation entry point.
+
+It serves callers that cannot allocate device memory (their GPU memory is
+reserved by another allocator, or they must avoid cudaMalloc's implicit
+synchronisation); it keeps its scratch in a static device array instead.  Here
+it is called through the C ABI on amplitudes that a torch tensor owns and
+compared with qf_expectation (which allocates through its state handle) on two
+calls in a row with different Hamiltonians, so a stale scratch would show.
+This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import __graft_entry__  # noqa: E402
+
+__graft_entry__.build()
+
+from paper_2108_04413_gb300 import qf  # noqa: E402
+from workloads import random_state  # noqa: E402
+
+
+def _terms(n, count, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, 1 << n, count)
+    x[: count // 8] = 0
+    return qf.as_terms(x, rng.integers(0, 1 << n, count), rng.normal(size=count))
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-11), ("c64", 1e-11)])
+def test_noalloc_matches_expectation_twice(dtype, tol):
+    n = 14
+    psi = random_state(n, 21)
+    buf = torch.empty(2 << n, dtype=torch.float64 if dtype == "c128" else torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    st = qf.State(n, dtype, stream=stream, buffer=buf)
+    st.from_numpy(psi)
+    for call, (count, seed) in enumerate(((600, 1), (2048, 2))):
+        T = _terms(n, count, seed)
+        ref, _ = st.expectation(T)
+        torch.cuda.synchronize()
+        got, im = qf.expectation_noalloc(buf.data_ptr(), n, dtype, stream.cuda_stream, T)
+        assert im == 0.0
+        assert abs(got - ref) < tol * max(1.0, abs(ref)), (call, got, ref)
+    st.close()
+
+
+def test_noalloc_rejects_too_many_terms():
+    n = 10
+    buf = torch.zeros(2 << n, dtype=torch.float64, device="cuda")
+    T = _terms(n, qf.QF_NOALLOC_MAX_TERMS + 1, 3)
+    with pytest.raises(qf.QFError) as ei:
+        qf.expectation_noalloc(buf.data_ptr(), n, "c128", torch.cuda.current_stream().cuda_stream, T)
+    assert ei.value.status == qf.QF_EINVAL
+    assert "QF_NOALLOC_MAX_TERMS" in str(ei.value)
