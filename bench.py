@@ -92,16 +92,14 @@ def group_stats(terms, n):
     return out
 
 
-def hpsi_flops(stats, n):
-    """FP64 flops of one H|psi> launch as written: per group and amplitude a
-    (real or complex) D * psi multiply-add and the chunk-table sums, plus the
-    energy and norm accumulations."""
+def hpsi_flops(stats, n, real: bool):
+    """Algorithmic FP64 flops of one H|psi> over the grouped Pauli sum: one
+    multiply-add D_g(b) * psi[b] per (X group, amplitude) -- 2 flops when the
+    state and every D are real, 8 when complex -- plus the energy and norm
+    accumulations (4 or 8 flops per amplitude)."""
     N = 1 << n
-    f = 0
-    for cnt, nch, odd in stats:
-        comps = 2 if odd else 1
-        f += 4 * comps + 2 * (nch - 1) * comps
-    return N * (f + 8)
+    per = 2 if real else 8
+    return N * (per * len(stats) + (4 if real else 8))
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -178,6 +176,14 @@ def dist_setup():
 def barrier(pg):
     if pg is not None:
         pg.barrier()
+
+
+def aggregate(pg, units_per_rank: float, ms: float):
+    """Whole-job throughput: the units all ranks processed divided by the slowest
+    rank's time (ms).  Returns (value per second, slowest ms)."""
+    ms_max = max_over_ranks(pg, ms)
+    world = pg.get_world_size() if pg is not None else 1
+    return world * units_per_rank / (ms_max / 1e3), ms_max
 
 
 def max_over_ranks(pg, v: float) -> float:
@@ -282,9 +288,8 @@ def run_gpu(args, rank, world, local, pg):
             per_kind[name] = {"launches": cnt, "ms": kms}
     qf.profile_end()
     clk = clocks.stop()
-    ms_max = max_over_ranks(pg, ms)
+    value, ms_max = aggregate(pg, args.steps, ms)
     step_ms = ms_max / args.steps
-    value = world * args.steps / (ms_max / 1e3)
 
     # roofline of the dominant kernel
     dom = max(per_kind.items(), key=lambda kv: kv[1]["ms"])[0]
@@ -333,11 +338,12 @@ def roofline_for(kind, rec, w, stats, n, S, pk, dtype):
     N = 1 << n
     avg_s = rec["ms"] / rec["launches"] / 1e3
     if kind in ("hpsi",) and dtype == "c128":
-        fl = hpsi_flops(stats, n)
+        real = not any(odd for _, _, odd in stats)  # dUCC states are real; H real iff no odd-Y term
+        fl = hpsi_flops(stats, n, real)
         ach = fl / avg_s / 1e12
         return {"kernel": "k_hpsi", "bound": "alu", "achieved": ach, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                 "frac": ach / pk["fp64_tflops"], "traffic": None,
-                "algorithmic": f"{fl:.4g} FP64 flop per launch",
+                "algorithmic": f"{fl:.4g} FP64 flop per launch (one multiply-add per X group and amplitude)",
                 "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock (derived)",
                 "hbm_gbs_as_issued": (len(stats) + 1) * N * S / avg_s / 1e9 + N * S / avg_s / 1e9}
     if kind in ("hpsi",):

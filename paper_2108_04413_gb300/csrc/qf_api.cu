@@ -41,7 +41,26 @@ struct ExpPlan {
   qf::ExpChunk* d_hchunks = nullptr;  // H|psi> weights
   int ngroups = 0;
   int nchunks = 0;
+  // tiled H|psi>: groups in X order, 8-term tables, classes for 2^10 and 2^11 tiles
+  qf::HGroup* d_hgroups = nullptr;
+  qf::WChunk* d_wchunks = nullptr;
+  qf::WChunkF* d_wchunks_f = nullptr;
+  qf::HClass* d_classes[2] = {nullptr, nullptr};
+  int nclasses[2] = {0, 0};
+  bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
 };
+
+void free_plan(ExpPlan& p) {
+  cudaFree(p.d_groups);
+  cudaFree(p.d_echunks);
+  cudaFree(p.d_hchunks);
+  cudaFree(p.d_hgroups);
+  cudaFree(p.d_wchunks);
+  cudaFree(p.d_wchunks_f);
+  cudaFree(p.d_classes[0]);
+  cudaFree(p.d_classes[1]);
+  p = ExpPlan();
+}
 
 uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull) {
   const unsigned char* p = static_cast<const unsigned char*>(data);
@@ -64,6 +83,10 @@ struct qf_state {
   bool own_psi = false;
   void* lam = nullptr;
   double scale = 1.0;
+  // Every stored imaginary part is exactly zero.  Holds after qf_set_basis and
+  // is kept by real sparse composites and by rotations with x != 0 and an odd
+  // number of Y letters (their phases map real amplitudes to real ones).
+  bool real = true;
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
   double* d_out = nullptr;
@@ -71,6 +94,13 @@ struct qf_state {
   double* h_out = nullptr;
   size_t h_cap = 0;
   std::unordered_map<uint64_t, ExpPlan> plans;
+  // block structure of ansatz lists seen by qf_energy_grad (angles refilled per call)
+  struct Blk {
+    size_t i, j;
+    bool sparse;
+    qf::SparseArgs fwd, inv;
+  };
+  std::unordered_map<uint64_t, std::vector<Blk>> ansatz_plans;
   size_t elem() const { return dt == QF_C128 ? 16 : 8; }
   size_t bytes() const { return elem() << n; }
 };
@@ -114,6 +144,9 @@ qf::RotArgs rot_args(qf_dtype dt, double* scale, uint64_t x, uint64_t z, double 
   rot_coeffs(dt, scale, th, &a.form, &a.A, &a.B);
   return a;
 }
+
+// A rotation keeps a real state real iff x != 0 and popc(x & z) is odd.
+bool keeps_real(uint64_t x, uint64_t z) { return x != 0 && (popc(x & z) & 1); }
 
 qf_status ensure_out(qf_state* st, size_t n) {
   if (n <= st->out_cap) return QF_OK;
@@ -195,6 +228,54 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   ExpPlan p;
   p.ngroups = (int)groups.size();
   p.nchunks = (int)ech.size();
+  for (const qf::ExpGroup& g : groups)
+    if (g.flags & 2) p.has_odd = true;
+  // tiled H|psi> tables: D_g(b) = sum_t c_t i^{y_t} s_t(b), eight terms per table
+  std::vector<qf::HGroup> hg;
+  std::vector<qf::WChunk> wc;
+  std::vector<qf::WChunkF> wf;
+  for (auto& kv : byx) {
+    qf::HGroup g{};
+    g.x = kv.first;
+    g.chunk0 = (int)wc.size();
+    const std::vector<size_t>& idx = kv.second;
+    g.nchunk = (int)((idx.size() + qf::kWideTerms - 1) / qf::kWideTerms);
+    for (size_t k = 0; k < idx.size(); k += qf::kWideTerms) {
+      qf::WChunk c{};
+      qf::WChunkF cf{};
+      const int cnt = (int)std::min<size_t>(qf::kWideTerms, idx.size() - k);
+      for (int t = 0; t < qf::kWideTerms; ++t) c.z[t] = cf.z[t] = (t < cnt) ? terms[idx[k + t]].z : 0ull;
+      for (int pat = 0; pat < (1 << qf::kWideTerms); ++pat) {
+        double hx = 0, hy = 0;
+        for (int t = 0; t < cnt; ++t) {
+          const qf_term& T = terms[idx[k + t]];
+          const int y = popc(T.x & T.z) & 3;
+          const double c0 = ((pat >> t) & 1) ? -T.coeff : T.coeff;
+          if ((y & 1) == 0)
+            hx += c0 * ((y == 2) ? -1.0 : 1.0);
+          else
+            hy += c0 * ((y == 3) ? -1.0 : 1.0);
+        }
+        c.tab[pat] = make_double2(hx, hy);
+        cf.tab[pat] = make_float2((float)hx, (float)hy);
+      }
+      for (int t = 0; t < cnt; ++t)
+        if (popc(terms[idx[k + t]].x & terms[idx[k + t]].z) & 1) g.odd = 1;
+      wc.push_back(c);
+      wf.push_back(cf);
+    }
+    hg.push_back(g);
+  }
+  std::vector<qf::HClass> cls[2];
+  for (int v = 0; v < 2; ++v) {
+    const int tb = 10 + v;
+    for (int g = 0; g < (int)hg.size(); ++g) {
+      const uint64_t xh = hg[g].x >> tb;
+      if (cls[v].empty() || cls[v].back().xh != xh) cls[v].push_back(qf::HClass{xh, g, g + 1});
+      else cls[v].back().g1 = g + 1;
+    }
+    p.nclasses[v] = (int)cls[v].size();
+  }
   if (p.ngroups > 0) {
     if (cudaMalloc(&p.d_groups, groups.size() * sizeof(qf::ExpGroup)) != cudaSuccess ||
         cudaMalloc(&p.d_echunks, ech.size() * sizeof(qf::ExpChunk)) != cudaSuccess ||
@@ -210,6 +291,24 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
                             st->stream));
     QF_CUDA(cudaMemcpyAsync(p.d_hchunks, hch.data(), hch.size() * sizeof(qf::ExpChunk), cudaMemcpyHostToDevice,
                             st->stream));
+    if (cudaMalloc(&p.d_hgroups, hg.size() * sizeof(qf::HGroup)) != cudaSuccess ||
+        cudaMalloc(&p.d_wchunks, wc.size() * sizeof(qf::WChunk)) != cudaSuccess ||
+        cudaMalloc(&p.d_wchunks_f, wf.size() * sizeof(qf::WChunkF)) != cudaSuccess ||
+        cudaMalloc(&p.d_classes[0], cls[0].size() * sizeof(qf::HClass)) != cudaSuccess ||
+        cudaMalloc(&p.d_classes[1], cls[1].size() * sizeof(qf::HClass)) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(p);
+      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
+    }
+    QF_CUDA(cudaMemcpyAsync(p.d_hgroups, hg.data(), hg.size() * sizeof(qf::HGroup), cudaMemcpyHostToDevice,
+                            st->stream));
+    QF_CUDA(cudaMemcpyAsync(p.d_wchunks, wc.data(), wc.size() * sizeof(qf::WChunk), cudaMemcpyHostToDevice,
+                            st->stream));
+    QF_CUDA(cudaMemcpyAsync(p.d_wchunks_f, wf.data(), wf.size() * sizeof(qf::WChunkF), cudaMemcpyHostToDevice,
+                            st->stream));
+    for (int v = 0; v < 2; ++v)
+      QF_CUDA(cudaMemcpyAsync(p.d_classes[v], cls[v].data(), cls[v].size() * sizeof(qf::HClass),
+                              cudaMemcpyHostToDevice, st->stream));
     QF_CUDA(cudaStreamSynchronize(st->stream));
   }
   auto res = st->plans.emplace(key, p);
@@ -331,6 +430,66 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
   return true;
 }
 
+// Recompute M - I of a sparse block for new angles, on its active rows only.
+// This is exact: every rotation of the block pairs support pattern r with
+// r ^ x, and the active rows are a union of such pairs, so each rotation maps
+// the active rows onto themselves and the composite restricted to them is the
+// product of the restricted rotations.
+void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
+  const int u = a->u, nr = a->nr;
+  const uint64_t x = r[0].x;
+  const int xl = (1 << u) - 1;
+  int loc[qf::kSparseMaxRows];
+  for (int i = 0; i < nr; ++i) {
+    int v = 0;
+    for (int b = 0; b < u; ++b)
+      if ((a->pat[i] >> a->supp[b]) & 1) v |= 1 << b;
+    loc[i] = v;
+  }
+  int partner[qf::kSparseMaxRows];
+  for (int i = 0; i < nr; ++i) {
+    partner[i] = -1;
+    for (int j = 0; j < nr; ++j)
+      if (loc[j] == (loc[i] ^ xl)) partner[i] = j;
+  }
+  auto compress = [&](uint64_t v) {
+    uint64_t o = 0;
+    for (int b = 0; b < u; ++b)
+      if ((v >> a->supp[b]) & 1) o |= 1ull << b;
+    return o;
+  };
+  const cplx iu(0, 1);
+  const int ncls = 1 << a->nzc;
+  for (int c = 0; c < ncls; ++c) {
+    cplx M[qf::kSparseMaxRows][qf::kSparseMaxRows] = {};
+    for (int i = 0; i < nr; ++i) M[i][i] = 1.0;
+    for (int k = 0; k < m; ++k) {
+      const uint64_t zo = r[k].z & ~x;
+      double sig = 1.0;
+      for (int j = 0; j < a->nzc; ++j)
+        if (zo == a->zc[j] && ((c >> j) & 1)) sig = -1.0;
+      const uint64_t zin = compress(r[k].z & x);
+      const int y = popc(x & r[k].z) & 3;
+      const cplx iy = (y == 0) ? cplx(1, 0) : (y == 1) ? cplx(0, 1) : (y == 2) ? cplx(-1, 0) : cplx(0, -1);
+      const double th = inverse ? -r[k].th : r[k].th;
+      const double cs = std::cos(th), sn = std::sin(th);
+      cplx N2[qf::kSparseMaxRows][qf::kSparseMaxRows];
+      for (int i = 0; i < nr; ++i) {
+        const int col = loc[i] ^ xl;
+        const cplx pe = iy * sig * ((popc(zin & (uint64_t)col) & 1) ? -1.0 : 1.0);
+        for (int j = 0; j < nr; ++j) N2[i][j] = cs * M[i][j] - iu * sn * pe * M[partner[i]][j];
+      }
+      for (int i = 0; i < nr; ++i)
+        for (int j = 0; j < nr; ++j) M[i][j] = N2[i][j];
+    }
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < nr; ++j) {
+        const cplx d = M[i][j] - ((i == j) ? 1.0 : 0.0);
+        a->M[c][i][j] = make_double2(d.real(), d.imag());
+      }
+  }
+}
+
 // Length of the run starting at i that can form one sparse block.
 int sparse_run(const RotIn* r, size_t i, size_t nrot, const int32_t* params) {
   const uint64_t x = r[i].x;
@@ -390,7 +549,9 @@ qf_status apply_rotations(qf_state* st, const RotIn* r, size_t nrot) {
     if (run >= 2) {
       qf::SparseArgs sa;
       if (build_sparse(r + i, run, n, false, false, &sa)) {
-        QF_CUDA(qf::launch_sparse(st->psi, n, st->dt, sa, st->stream));
+        const bool rm = qf::sparse_m_real(sa);
+        QF_CUDA(qf::launch_sparse(st->psi, n, st->dt, sa, st->real && rm, st->stream));
+        st->real = st->real && rm;
         i += run;
         continue;
       }
@@ -408,10 +569,12 @@ qf_status apply_rotations(qf_state* st, const RotIn* r, size_t nrot) {
       qf::TileArgs ta;
       build_tile(st, r, i, j, uni, &ta);
       QF_CUDA(qf::launch_tile(st->psi, n, st->dt, ta, st->stream));
+      for (size_t k = i; k < j; ++k) st->real = st->real && keeps_real(r[k].x, r[k].z);
       i = j;
     } else {
       qf::RotArgs a = rot_args(st->dt, &st->scale, r[i].x, r[i].z, r[i].th);
       QF_CUDA(qf::launch_rot(st->psi, n, st->dt, a, st->stream));
+      st->real = st->real && keeps_real(r[i].x, r[i].z);
       ++i;
     }
   }
@@ -475,11 +638,7 @@ qf_status qf_state_create(int n, qf_dtype dtype, void* stream, void* dev_buf, si
 qf_status qf_state_destroy(qf_state* st) {
   if (!st) return fail(QF_EINVAL, "state is NULL");
   cudaStreamSynchronize(st->stream);
-  for (auto& kv : st->plans) {
-    cudaFree(kv.second.d_groups);
-    cudaFree(kv.second.d_echunks);
-    cudaFree(kv.second.d_hchunks);
-  }
+  for (auto& kv : st->plans) free_plan(kv.second);
   if (st->own_psi) cudaFree(st->psi);
   cudaFree(st->lam);
   cudaFree(st->d_partials);
@@ -494,6 +653,7 @@ qf_status qf_set_basis(qf_state* st, uint64_t det) {
   if (!st) return fail(QF_EINVAL, "state is NULL");
   if (st->n < 64 && (det >> st->n)) return fail(QF_EINVAL, "determinant has a bit at or above the qubit count");
   st->scale = 1.0;
+  st->real = true;
   QF_CUDA(qf::launch_zero_and_set(st->psi, st->n, st->dt, det, st->stream));
   return QF_OK;
 }
@@ -505,6 +665,7 @@ qf_status qf_apply_pauli_exp(qf_state* st, uint64_t x, uint64_t z, double theta)
   if (!std::isfinite(theta)) return fail(QF_EINVAL, "theta is not finite");
   qf::RotArgs a = rot_args(st->dt, &st->scale, x, z, theta);
   QF_CUDA(qf::launch_rot(st->psi, st->n, st->dt, a, st->stream));
+  st->real = st->real && keeps_real(x, z);
   return QF_OK;
 }
 
@@ -574,27 +735,38 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     return fail(QF_ENOMEM, "cudaMalloc(lambda) failed");
   }
   // block structure: sparse composite blocks (same X, same parameter, commuting) or single rotations
-  struct Blk {
-    size_t i, j;
-    bool sparse;
-    qf::SparseArgs fwd, inv;
-  };
-  std::vector<Blk> blocks;
-  for (size_t i = 0; i < n_rot;) {
-    const int run = sparse_run(r.data(), i, n_rot, par.data());
-    Blk b;
-    b.i = i;
-    b.sparse = false;
-    if (run >= 2 && build_sparse(&r[i], run, st->n, false, true, &b.fwd) &&
-        build_sparse(&r[i], run, st->n, true, true, &b.inv) && b.fwd.nr == b.inv.nr) {
-      b.sparse = true;
-      b.j = i + run;
-    } else {
-      b.j = i + 1;
+  using Blk = qf_state::Blk;
+  uint64_t akey = fnv1a(ansatz, n_rot * sizeof(qf_arot));
+  akey = fnv1a(&st->n, sizeof(int), akey);
+  auto ait = st->ansatz_plans.find(akey);
+  if (ait == st->ansatz_plans.end()) {
+    // first sight of this ansatz: find the sparse blocks (the active rows of a block
+    // do not depend on the angles, so the structure is kept and only M is refilled)
+    std::vector<Blk> bl;
+    for (size_t i = 0; i < n_rot;) {
+      const int run = sparse_run(r.data(), i, n_rot, par.data());
+      Blk b;
+      b.i = i;
+      b.sparse = false;
+      if (run >= 2 && build_sparse(&r[i], run, st->n, false, true, &b.fwd) &&
+          build_sparse(&r[i], run, st->n, true, true, &b.inv) && b.fwd.nr == b.inv.nr) {
+        b.sparse = true;
+        b.j = i + run;
+      } else {
+        b.j = i + 1;
+      }
+      bl.push_back(b);
+      i = b.j;
     }
-    blocks.push_back(b);
-    i = b.j;
+    ait = st->ansatz_plans.emplace(akey, std::move(bl)).first;
+  } else {
+    for (Blk& b : ait->second)
+      if (b.sparse) {
+        refill_sparse(&r[b.i], (int)(b.j - b.i), false, &b.fwd);
+        refill_sparse(&r[b.i], (int)(b.j - b.i), true, &b.inv);
+      }
   }
+  const std::vector<Blk>& blocks = ait->second;
   qf_status os = ensure_out(st, blocks.size() + 2);
   if (os != QF_OK) return os;
   const ExpPlan* p = nullptr;
@@ -604,19 +776,31 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   }
   const int n = st->n;
   st->scale = 1.0;
+  st->real = true;
   QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
   for (const Blk& b : blocks) {
     if (b.sparse) {
-      QF_CUDA(qf::launch_sparse(st->psi, n, st->dt, b.fwd, st->stream));
+      const bool rm = qf::sparse_m_real(b.fwd);
+      QF_CUDA(qf::launch_sparse(st->psi, n, st->dt, b.fwd, st->real && rm, st->stream));
+      st->real = st->real && rm;
     } else {
       qf::RotArgs a = rot_args(st->dt, &st->scale, r[b.i].x, r[b.i].z, r[b.i].th);
       QF_CUDA(qf::launch_rot(st->psi, n, st->dt, a, st->stream));
+      st->real = st->real && keeps_real(r[b.i].x, r[b.i].z);
     }
   }
   const double s_fwd = st->scale;
   const int nb = qf::reduce_blocks(n, st->dt);
   double* d_e = st->d_out + blocks.size();
-  if (p) {
+  const bool hreal = st->real && p && !p->has_odd;
+  if (p && n >= 10) {
+    // tiles of 2^11 amplitudes when the state is real (fewer registers per element), else 2^10
+    const int v = (hreal && n >= 11) ? 1 : 0;
+    QF_CUDA(qf::launch_hpsi_tiled(st->psi, st->lam, n, st->dt, 10 + v, hreal, p->d_classes[v], p->nclasses[v],
+                                  p->d_hgroups, st->dt == QF_C128 ? (const void*)p->d_wchunks
+                                                                 : (const void*)p->d_wchunks_f,
+                                  st->d_partials, st->d_counter, d_e, nb, st->stream));
+  } else if (p) {
     QF_CUDA(qf::launch_hpsi(st->psi, st->lam, n, st->dt, p->d_groups, p->ngroups, p->d_hchunks, st->d_partials,
                             st->d_counter, d_e, nb, st->stream));
   } else {
@@ -626,19 +810,25 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   // reverse sweep; psi and lam share one scale
   std::vector<double> s2(blocks.size());
   double sc = s_fwd;
+  // psi and lambda = H psi are both real when psi is real and H has no odd-Y term
+  bool both_real = st->real && (!p || !p->has_odd);
   for (size_t bi = blocks.size(); bi-- > 0;) {
     const Blk& b = blocks[bi];
     s2[bi] = sc * sc;
     if (b.sparse) {
-      QF_CUDA(qf::launch_adj_sparse(st->psi, st->lam, n, st->dt, b.inv, st->d_partials, st->d_counter,
-                                    st->d_out + bi, nb, st->stream));
+      const bool rm = qf::sparse_m_real(b.inv);
+      QF_CUDA(qf::launch_adj_sparse(st->psi, st->lam, n, st->dt, b.inv, both_real && rm, st->d_partials,
+                                    st->d_counter, st->d_out + bi, nb, st->stream));
+      both_real = both_real && rm;
     } else {
       qf::RotArgs a = rot_args(st->dt, &sc, r[b.i].x, r[b.i].z, -r[b.i].th);
       QF_CUDA(qf::launch_adj_rot(st->psi, st->lam, n, st->dt, a, st->d_partials, st->d_counter, st->d_out + bi, nb,
                                  st->stream));
+      both_real = both_real && keeps_real(r[b.i].x, r[b.i].z);
     }
   }
   st->scale = sc;
+  st->real = both_real;
   QF_CUDA(cudaMemcpyAsync(st->h_out, st->d_out, (blocks.size() + 2) * sizeof(double), cudaMemcpyDeviceToHost,
                           st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));
@@ -684,18 +874,16 @@ qf_status qf_state_copy_from_host(qf_state* st, const void* host, size_t bytes) 
   if (bytes != st->bytes()) return fail(QF_EINVAL, "byte count does not match the state");
   QF_CUDA(cudaMemcpyAsync(st->psi, host, bytes, cudaMemcpyHostToDevice, st->stream));
   st->scale = 1.0;
+  st->real = false;
   return QF_OK;
 }
 
 qf_status qf_state_clear_plans(qf_state* st) {
   if (!st) return fail(QF_EINVAL, "state is NULL");
   cudaStreamSynchronize(st->stream);
-  for (auto& kv : st->plans) {
-    cudaFree(kv.second.d_groups);
-    cudaFree(kv.second.d_echunks);
-    cudaFree(kv.second.d_hchunks);
-  }
+  for (auto& kv : st->plans) free_plan(kv.second);
   st->plans.clear();
+  st->ansatz_plans.clear();
   return QF_OK;
 }
 

@@ -81,12 +81,37 @@ struct ExpChunk {
   double2 tab[1 << kChunkTerms];  // (real-part weight, imaginary-part weight) per sign pattern
 };
 
+// H|psi> plan (tiled): groups sorted by X mask form classes of equal high part
+// x >> tb (tb = tile bits); a class reads one partner tile per output tile.
+constexpr int kWideTerms = 8;  // terms per H|psi> sign-pattern table
+struct HClass {
+  uint64_t xh;  // x >> tb
+  int g0, g1;   // group range [g0, g1)
+};
+struct HGroup {
+  uint64_t x;
+  int chunk0, nchunk;
+  int odd;      // some term has an odd number of Y letters (complex D)
+  int pad;
+};
+struct WChunk {
+  uint64_t z[kWideTerms];
+  double2 tab[1 << kWideTerms];  // D = sum_t c_t i^{y_t} s_t: (real, imaginary) per sign pattern
+};
+struct WChunkF {
+  uint64_t z[kWideTerms];
+  float2 tab[1 << kWideTerms];
+};
+
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s);
 cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s);
 cudaError_t launch_rot(void* psi, int n, qf_dtype dt, const RotArgs& a, cudaStream_t s);
 cudaError_t launch_tile(void* psi, int n, qf_dtype dt, const TileArgs& a, cudaStream_t s);
-cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, cudaStream_t s);
+// realst: the state is real (every imaginary part exactly zero) and M is real.
+cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, bool realst, cudaStream_t s);
+bool sparse_m_real(const SparseArgs& a);
+bool sparse_q_imag(const SparseArgs& a);
 // <psi|H|psi> for the grouped plan; writes the sum into out[0] (device).
 cudaError_t launch_expect(const void* psi, int n, qf_dtype dt, const ExpGroup* groups, int ngroups,
                           const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
@@ -95,13 +120,18 @@ cudaError_t launch_expect(const void* psi, int n, qf_dtype dt, const ExpGroup* g
 cudaError_t launch_hpsi(const void* psi, void* lam, int n, qf_dtype dt, const ExpGroup* groups, int ngroups,
                         const ExpChunk* chunks, double* partials, unsigned* counter, double* out, int nblocks,
                         cudaStream_t s);
+// Tiled H|psi> (n >= 8): same outputs as launch_hpsi.  tb = tile bits; chunks is a
+// WChunk array (QF_C128) or a WChunkF array (QF_C64).
+cudaError_t launch_hpsi_tiled(const void* psi, void* lam, int n, qf_dtype dt, int tb, bool realst,
+                              const HClass* classes, int nclasses, const HGroup* groups, const void* chunks,
+                              double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s);
 // Reverse step: out[0] = Im <lam|P|psi> (stored units), then psi, lam <- exp(+i th P).
 cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotArgs& a, double* partials,
                            unsigned* counter, double* out, int nblocks, cudaStream_t s);
 // Reverse step over a sparse block: out[0] = Im <lam|Q|psi>, then psi, lam <- M psi, M lam
 // (SparseArgs.M holds M - I for the block's inverse M).
-cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, double* partials,
-                              unsigned* counter, double* out, int nblocks, cudaStream_t s);
+cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, bool realst,
+                              double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s);
 
 int reduce_blocks(int n, qf_dtype dt);  // grid size used by the reducing kernels
 void count_launch();

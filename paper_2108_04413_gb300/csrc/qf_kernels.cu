@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "qf_internal.h"
@@ -280,19 +282,42 @@ __global__ void __launch_bounds__(256) k_tile(typename Cx<T>::V* __restrict__ ps
 // The composite of the block's rotations restricted to its support qubits is
 // the identity except on a few "active" support patterns; only those
 // amplitudes are read and written.  One thread per assignment of the
-// non-support bits ("outside index").  SparseArgs.M holds M - I, so each output
+// non-support bits ("outside index").  The arguments hold M - I, so each output
 // is v_r + sum_k (M - I)_rk v_k: the rounding then scales with the (small)
 // change rather than with the amplitude, which keeps complex64 states close to
-// unit norm.
+// unit norm.  REALM: M is real.  REALST: the state is real (imaginary parts are
+// exactly zero and stay zero), so only real parts are read and written.
 
-template <typename T, bool REAL>
+template <int NR>
+struct SpK {
+  int u, nr, nzc, pad;
+  int supp[kSparseMaxSupp];
+  uint64_t pat[NR];
+  uint64_t zc[2];
+  double2 M[kSparseMaxCls][NR][NR];
+  double2 Q[kSparseMaxCls][NR][NR];
+};
+
+__device__ __forceinline__ uint64_t sp_base(uint64_t o, const int* supp, int u) {
+  for (int i = 0; i < u; ++i) o = ins0(o, supp[i]);
+  return o;
+}
+
+template <int NR>
+__device__ __forceinline__ unsigned sp_class(const SpK<NR>& a, uint64_t base) {
+  unsigned cls = 0;
+  if (a.nzc > 0) cls = par64(a.zc[0] & base);
+  if (a.nzc > 1) cls |= par64(a.zc[1] & base) << 1;
+  return cls;
+}
+
+template <typename T, int NR, bool REALM, bool REALST>
 __global__ void __launch_bounds__(256) k_sparse(typename Cx<T>::V* __restrict__ psi, int n,
-                                                const __grid_constant__ SparseArgs a) {
+                                                const __grid_constant__ SpK<NR> a) {
   using V = typename Cx<T>::V;
-  __shared__ V M[kSparseMaxCls][kSparseMaxRows][kSparseMaxRows];
-  for (int i = threadIdx.x; i < kSparseMaxCls * kSparseMaxRows * kSparseMaxRows; i += blockDim.x) {
-    const int c = i / (kSparseMaxRows * kSparseMaxRows), r = (i / kSparseMaxRows) % kSparseMaxRows,
-              k = i % kSparseMaxRows;
+  __shared__ V M[kSparseMaxCls][NR][NR];
+  for (int i = threadIdx.x; i < kSparseMaxCls * NR * NR; i += blockDim.x) {
+    const int c = i / (NR * NR), r = (i / NR) % NR, k = i % NR;
     V m;
     m.x = (T)a.M[c][r][k].x;
     m.y = (T)a.M[c][r][k].y;
@@ -301,37 +326,46 @@ __global__ void __launch_bounds__(256) k_sparse(typename Cx<T>::V* __restrict__ 
   __syncthreads();
   const uint64_t nout = 1ull << (n - a.u);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  T* pr = reinterpret_cast<T*>(psi);
   for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < nout; o += stride) {
-    uint64_t base = o;
-    for (int i = 0; i < a.u; ++i) base = ins0(base, a.supp[i]);
-    unsigned cls = 0;
-    if (a.nzc > 0) cls = par64(a.zc[0] & base);
-    if (a.nzc > 1) cls |= par64(a.zc[1] & base) << 1;
-    V v[kSparseMaxRows];
+    const uint64_t base = sp_base(o, a.supp, a.u);
+    const unsigned cls = sp_class(a, base);
+    V v[NR];
 #pragma unroll
-    for (int r = 0; r < kSparseMaxRows; ++r)
-      if (r < a.nr) v[r] = psi[base | a.pat[r]];
+    for (int r = 0; r < NR; ++r) {
+      if (r < a.nr) {
+        if (REALST) {
+          v[r].x = pr[2 * (base | a.pat[r])];
+          v[r].y = 0;
+        } else {
+          v[r] = psi[base | a.pat[r]];
+        }
+      }
+    }
 #pragma unroll
-    for (int r = 0; r < kSparseMaxRows; ++r) {
+    for (int r = 0; r < NR; ++r) {
       if (r < a.nr) {
         T ox = v[r].x, oy = v[r].y;
 #pragma unroll
-        for (int k = 0; k < kSparseMaxRows; ++k) {
+        for (int k = 0; k < NR; ++k) {
           if (k < a.nr) {
             const V m = M[cls][r][k];
-            if (REAL) {
-              ox = fma(m.x, v[k].x, ox);
-              oy = fma(m.x, v[k].y, oy);
-            } else {
-              ox = fma(m.x, v[k].x, fma(-m.y, v[k].y, ox));
-              oy = fma(m.x, v[k].y, fma(m.y, v[k].x, oy));
+            ox = fma(m.x, v[k].x, ox);
+            if (!REALST) oy = fma(m.x, v[k].y, oy);
+            if (!REALM) {
+              ox = fma(-m.y, v[k].y, ox);
+              oy = fma(m.y, v[k].x, oy);
             }
           }
         }
-        V w;
-        w.x = ox;
-        w.y = oy;
-        psi[base | a.pat[r]] = w;
+        if (REALST) {
+          pr[2 * (base | a.pat[r])] = ox;
+        } else {
+          V w;
+          w.x = ox;
+          w.y = oy;
+          psi[base | a.pat[r]] = w;
+        }
       }
     }
   }
@@ -453,6 +487,125 @@ __global__ void __launch_bounds__(256) k_hpsi(const typename Cx<T>::V* __restric
 }
 
 // ---------------------------------------------------------------------------
+// tiled H|psi>: lam[c] = sum_g D_g(c xor x_g) psi[c xor x_g], out[0] = Re <psi|lam>,
+// out[1] = <psi|psi>.
+//
+// Output tiles are 2^TB contiguous amplitudes (TB = 8 + log2 E; each of the 256
+// threads owns E of them: c = tid + 256 k).  For every class of groups sharing
+// the high part xh of their X mask, the partner tile (tile xor xh) is staged in
+// shared memory once and all groups of the class read it there.  For element k
+// the partner index inside the tile is (tid ^ xl) | ((k ^ xl >> 8) << 8), and the
+// sign pattern of the group's terms splits into a per-thread part and a part
+// that depends on k only, so the inner loop is an XOR, a table load and an FMA.
+// REALST: psi is real and every D is real, so only real parts are used.
+// For float states each class's contribution is summed in FP32 and folded into
+// FP64 accumulators once per class.
+
+template <typename T> struct WTab;
+template <> struct WTab<double> { using C = WChunk; using V2 = double2; };
+template <> struct WTab<float> { using C = WChunkF; using V2 = float2; };
+
+template <typename T, int E, bool REALST>
+__global__ void __launch_bounds__(256) k_hpsi_tiled(const typename Cx<T>::V* __restrict__ psi,
+                                                    typename Cx<T>::V* __restrict__ lam, int n,
+                                                    const HClass* __restrict__ classes, int nclasses,
+                                                    const HGroup* __restrict__ groups,
+                                                    const typename WTab<T>::C* __restrict__ chunks,
+                                                    double* partials, unsigned* counter, double* out) {
+  using V = typename Cx<T>::V;
+  constexpr int TB = (E == 1) ? 8 : (E == 2) ? 9 : (E == 4) ? 10 : (E == 8) ? 11 : 12;
+  constexpr int KB = TB - 8;  // bits of k
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tile = reinterpret_cast<V*>(smem_raw);
+  const unsigned tid = threadIdx.x;
+  const uint64_t ntiles = 1ull << (n - TB);
+  double acc_e = 0.0, acc_n = 0.0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    double lx[E], ly[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) lx[k] = ly[k] = 0.0;
+    for (int ci = 0; ci < nclasses; ++ci) {
+      const HClass C = classes[ci];
+      const uint64_t pt = t ^ C.xh;
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < E; ++k) tile[tid + 256u * k] = psi[(pt << TB) + tid + 256u * k];
+      __syncthreads();
+      T fx[E], fy[E];
+#pragma unroll
+      for (int k = 0; k < E; ++k) fx[k] = fy[k] = 0;
+      for (int g = C.g0; g < C.g1; ++g) {
+        const HGroup G = groups[g];
+        const unsigned xl = (unsigned)(G.x & ((1ull << TB) - 1ull));
+        const unsigned xlo = xl & 255u, xhi = xl >> 8;
+        T dx[E], dy[E];
+        // the first table initialises D (no add of zero), later tables add to it
+        for (int c = 0; c < G.nchunk; ++c) {
+          const typename WTab<T>::C* W = chunks + G.chunk0 + c;
+          unsigned ith = 0, col[KB > 0 ? KB : 1];
+#pragma unroll
+          for (int j = 0; j < (KB > 0 ? KB : 1); ++j) col[j] = 0;
+#pragma unroll
+          for (int q = 0; q < kWideTerms; ++q) {
+            const uint64_t z = W->z[q];
+            const unsigned hp = par64((z >> TB) & pt);
+            const unsigned tp = (unsigned)__popc((unsigned)z & 255u & (tid ^ xlo)) & 1u;
+            ith |= (hp ^ tp) << q;
+#pragma unroll
+            for (int j = 0; j < KB; ++j) col[j] |= (unsigned)((z >> (8 + j)) & 1ull) << q;
+          }
+#pragma unroll
+          for (int k = 0; k < E; ++k) {
+            unsigned idx = ith;
+            const unsigned kk = (unsigned)k ^ xhi;
+#pragma unroll
+            for (int j = 0; j < KB; ++j)
+              if ((kk >> j) & 1u) idx ^= col[j];
+            const typename WTab<T>::V2 d = W->tab[idx];
+            if (c == 0) {
+              dx[k] = d.x;
+              if (!REALST) dy[k] = d.y;
+            } else {
+              dx[k] += d.x;
+              if (!REALST) dy[k] += d.y;
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const V v = tile[(tid ^ xlo) | ((((unsigned)k ^ xhi)) << 8)];
+          fx[k] = fma(dx[k], v.x, fx[k]);
+          if (!REALST) {
+            fy[k] = fma(dx[k], v.y, fy[k]);
+            if (G.odd) {
+              fx[k] = fma(-dy[k], v.y, fx[k]);
+              fy[k] = fma(dy[k], v.x, fy[k]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        lx[k] += (double)fx[k];
+        if (!REALST) ly[k] += (double)fy[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const uint64_t cidx = (t << TB) + tid + 256u * k;
+      const V u = psi[cidx];
+      acc_e = fma((double)u.x, lx[k], fma((double)u.y, ly[k], acc_e));
+      acc_n = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, acc_n));
+      V w;
+      w.x = (T)lx[k];
+      w.y = (T)ly[k];
+      lam[cidx] = w;
+    }
+  }
+  grid_finish2(acc_e, acc_n, partials, counter, out);
+}
+
+// ---------------------------------------------------------------------------
 // adjoint step for one rotation: out = Im <lam|P|psi> (pre-rotation values),
 // then psi and lam both get the rotation given in the arguments (the host passes
 // -theta, i.e. exp(+i theta P)).
@@ -509,19 +662,19 @@ __global__ void __launch_bounds__(256) k_adj_rot(typename Cx<T>::V* __restrict__
 }
 
 // adjoint step for a sparse block: out = Im <lam|Q|psi>, then psi <- M psi,
-// lam <- M lam on the active rows (SparseArgs.M holds M - I for the block's
-// inverse composite M).
-template <typename T>
+// lam <- M lam on the active rows (the arguments hold M - I for the block's
+// inverse composite M).  RQ: M is real and Q = i * (real matrix), the case of
+// every fermionic excitation block, where Im <lam|Q|psi> = sum Qi_rk Re(conj(lam_r) psi_k).
+template <typename T, int NR, bool RQ, bool REALST>
 __global__ void __launch_bounds__(256) k_adj_sparse(typename Cx<T>::V* __restrict__ psi,
                                                     typename Cx<T>::V* __restrict__ lam, int n,
-                                                    const __grid_constant__ SparseArgs a, double* partials,
+                                                    const __grid_constant__ SpK<NR> a, double* partials,
                                                     unsigned* counter, double* out) {
   using V = typename Cx<T>::V;
-  __shared__ V M[kSparseMaxCls][kSparseMaxRows][kSparseMaxRows];
-  __shared__ double2 Q[kSparseMaxCls][kSparseMaxRows][kSparseMaxRows];
-  for (int i = threadIdx.x; i < kSparseMaxCls * kSparseMaxRows * kSparseMaxRows; i += blockDim.x) {
-    const int c = i / (kSparseMaxRows * kSparseMaxRows), r = (i / kSparseMaxRows) % kSparseMaxRows,
-              k = i % kSparseMaxRows;
+  __shared__ V M[kSparseMaxCls][NR][NR];
+  __shared__ double2 Q[kSparseMaxCls][NR][NR];
+  for (int i = threadIdx.x; i < kSparseMaxCls * NR * NR; i += blockDim.x) {
+    const int c = i / (NR * NR), r = (i / NR) % NR, k = i % NR;
     V m;
     m.x = (T)a.M[c][r][k].x;
     m.y = (T)a.M[c][r][k].y;
@@ -531,56 +684,89 @@ __global__ void __launch_bounds__(256) k_adj_sparse(typename Cx<T>::V* __restric
   __syncthreads();
   const uint64_t nout = 1ull << (n - a.u);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  T* pr = reinterpret_cast<T*>(psi);
+  T* lr = reinterpret_cast<T*>(lam);
   double acc = 0.0;
   for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < nout; o += stride) {
-    uint64_t base = o;
-    for (int i = 0; i < a.u; ++i) base = ins0(base, a.supp[i]);
-    unsigned cls = 0;
-    if (a.nzc > 0) cls = par64(a.zc[0] & base);
-    if (a.nzc > 1) cls |= par64(a.zc[1] & base) << 1;
-    V v[kSparseMaxRows], w[kSparseMaxRows];
+    const uint64_t base = sp_base(o, a.supp, a.u);
+    const unsigned cls = sp_class(a, base);
+    V v[NR], w[NR];
 #pragma unroll
-    for (int r = 0; r < kSparseMaxRows; ++r)
+    for (int r = 0; r < NR; ++r) {
       if (r < a.nr) {
-        v[r] = psi[base | a.pat[r]];
-        w[r] = lam[base | a.pat[r]];
-      }
-#pragma unroll
-    for (int r = 0; r < kSparseMaxRows; ++r) {
-      if (r < a.nr) {
-        double qx = 0.0, qy = 0.0;
-#pragma unroll
-        for (int k = 0; k < kSparseMaxRows; ++k) {
-          if (k < a.nr) {
-            const double2 q = Q[cls][r][k];
-            qx = fma(q.x, (double)v[k].x, fma(-q.y, (double)v[k].y, qx));
-            qy = fma(q.x, (double)v[k].y, fma(q.y, (double)v[k].x, qy));
-          }
+        const uint64_t idx = base | a.pat[r];
+        if (REALST) {
+          v[r].x = pr[2 * idx];
+          w[r].x = lr[2 * idx];
+          v[r].y = w[r].y = 0;
+        } else {
+          v[r] = psi[idx];
+          w[r] = lam[idx];
         }
-        acc = fma((double)w[r].x, qy, fma(-(double)w[r].y, qx, acc));
       }
     }
 #pragma unroll
-    for (int r = 0; r < kSparseMaxRows; ++r) {
+    for (int r = 0; r < NR; ++r) {
+      if (r < a.nr) {
+        if (RQ) {
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < NR; ++k)
+            if (k < a.nr) {
+              const double qi = Q[cls][r][k].y;
+              s = fma(qi, (double)v[k].x, s);
+              if (!REALST) acc = fma(qi * (double)w[r].y, (double)v[k].y, acc);
+            }
+          acc = fma((double)w[r].x, s, acc);
+        } else {
+          double qx = 0.0, qy = 0.0;
+#pragma unroll
+          for (int k = 0; k < NR; ++k) {
+            if (k < a.nr) {
+              const double2 q = Q[cls][r][k];
+              qx = fma(q.x, (double)v[k].x, fma(-q.y, (double)v[k].y, qx));
+              qy = fma(q.x, (double)v[k].y, fma(q.y, (double)v[k].x, qy));
+            }
+          }
+          acc = fma((double)w[r].x, qy, fma(-(double)w[r].y, qx, acc));
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
       if (r < a.nr) {
         T ox = v[r].x, oy = v[r].y, px = w[r].x, py = w[r].y;
 #pragma unroll
-        for (int k = 0; k < kSparseMaxRows; ++k) {
+        for (int k = 0; k < NR; ++k) {
           if (k < a.nr) {
             const V m = M[cls][r][k];
-            ox = fma(m.x, v[k].x, fma(-m.y, v[k].y, ox));
-            oy = fma(m.x, v[k].y, fma(m.y, v[k].x, oy));
-            px = fma(m.x, w[k].x, fma(-m.y, w[k].y, px));
-            py = fma(m.x, w[k].y, fma(m.y, w[k].x, py));
+            ox = fma(m.x, v[k].x, ox);
+            px = fma(m.x, w[k].x, px);
+            if (!REALST) {
+              oy = fma(m.x, v[k].y, oy);
+              py = fma(m.x, w[k].y, py);
+            }
+            if (!RQ) {
+              ox = fma(-m.y, v[k].y, ox);
+              oy = fma(m.y, v[k].x, oy);
+              px = fma(-m.y, w[k].y, px);
+              py = fma(m.y, w[k].x, py);
+            }
           }
         }
-        V o1, o2;
-        o1.x = ox;
-        o1.y = oy;
-        o2.x = px;
-        o2.y = py;
-        psi[base | a.pat[r]] = o1;
-        lam[base | a.pat[r]] = o2;
+        const uint64_t idx = base | a.pat[r];
+        if (REALST) {
+          pr[2 * idx] = ox;
+          lr[2 * idx] = px;
+        } else {
+          V o1, o2;
+          o1.x = ox;
+          o1.y = oy;
+          o2.x = px;
+          o2.y = py;
+          psi[idx] = o1;
+          lam[idx] = o2;
+        }
       }
     }
   }
@@ -760,7 +946,27 @@ cudaError_t launch_tile(void* psi, int n, qf_dtype dt, const TileArgs& a, cudaSt
   return e;
 }
 
-static bool sparse_is_real(const SparseArgs& a) {
+template <int NR>
+static SpK<NR> compact(const SparseArgs& a) {
+  SpK<NR> k;
+  memset(&k, 0, sizeof(k));
+  k.u = a.u;
+  k.nr = a.nr;
+  k.nzc = a.nzc;
+  for (int i = 0; i < kSparseMaxSupp; ++i) k.supp[i] = a.supp[i];
+  for (int r = 0; r < NR && r < a.nr; ++r) k.pat[r] = a.pat[r];
+  k.zc[0] = a.zc[0];
+  k.zc[1] = a.zc[1];
+  for (int c = 0; c < kSparseMaxCls; ++c)
+    for (int r = 0; r < NR && r < a.nr; ++r)
+      for (int q = 0; q < NR && q < a.nr; ++q) {
+        k.M[c][r][q] = a.M[c][r][q];
+        k.Q[c][r][q] = a.Q[c][r][q];
+      }
+  return k;
+}
+
+bool sparse_m_real(const SparseArgs& a) {
   for (int c = 0; c < a.ncls; ++c)
     for (int r = 0; r < a.nr; ++r)
       for (int k = 0; k < a.nr; ++k)
@@ -768,22 +974,72 @@ static bool sparse_is_real(const SparseArgs& a) {
   return true;
 }
 
-cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, cudaStream_t s) {
+bool sparse_q_imag(const SparseArgs& a) {
+  for (int c = 0; c < a.ncls; ++c)
+    for (int r = 0; r < a.nr; ++r)
+      for (int k = 0; k < a.nr; ++k)
+        if (a.Q[c][r][k].x != 0.0) return false;
+  return true;
+}
+
+template <typename T, int NR>
+static void sparse_fwd(void* psi, int n, const SparseArgs& a, bool realst, cudaStream_t s) {
+  using V = typename Cx<T>::V;
+  const SpK<NR> k = compact<NR>(a);
+  const unsigned g = grid_for(1ull << (n - a.u), 8);
+  V* p = static_cast<V*>(psi);
+  const bool rm = sparse_m_real(a);
+  if (rm && realst)
+    k_sparse<T, NR, true, true><<<g, 256, 0, s>>>(p, n, k);
+  else if (rm)
+    k_sparse<T, NR, true, false><<<g, 256, 0, s>>>(p, n, k);
+  else
+    k_sparse<T, NR, false, false><<<g, 256, 0, s>>>(p, n, k);
+}
+
+template <typename T, int NR>
+static void sparse_adj(void* psi, void* lam, int n, const SparseArgs& a, bool realst, double* partials,
+                       unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  using V = typename Cx<T>::V;
+  const SpK<NR> k = compact<NR>(a);
+  V* p = static_cast<V*>(psi);
+  V* l = static_cast<V*>(lam);
+  const bool rq = sparse_m_real(a) && sparse_q_imag(a);
+  if (rq && realst)
+    k_adj_sparse<T, NR, true, true><<<nblocks, 256, 0, s>>>(p, l, n, k, partials, counter, out);
+  else if (rq)
+    k_adj_sparse<T, NR, true, false><<<nblocks, 256, 0, s>>>(p, l, n, k, partials, counter, out);
+  else
+    k_adj_sparse<T, NR, false, false><<<nblocks, 256, 0, s>>>(p, l, n, k, partials, counter, out);
+}
+
+template <typename T>
+static void sparse_fwd_nr(void* psi, int n, const SparseArgs& a, bool realst, cudaStream_t s) {
+  if (a.nr <= 2)
+    sparse_fwd<T, 2>(psi, n, a, realst, s);
+  else if (a.nr <= 4)
+    sparse_fwd<T, 4>(psi, n, a, realst, s);
+  else
+    sparse_fwd<T, 8>(psi, n, a, realst, s);
+}
+
+template <typename T>
+static void sparse_adj_nr(void* psi, void* lam, int n, const SparseArgs& a, bool realst, double* partials,
+                          unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  if (a.nr <= 2)
+    sparse_adj<T, 2>(psi, lam, n, a, realst, partials, counter, out, nblocks, s);
+  else if (a.nr <= 4)
+    sparse_adj<T, 4>(psi, lam, n, a, realst, partials, counter, out, nblocks, s);
+  else
+    sparse_adj<T, 8>(psi, lam, n, a, realst, partials, counter, out, nblocks, s);
+}
+
+cudaError_t launch_sparse(void* psi, int n, qf_dtype dt, const SparseArgs& a, bool realst, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_SPARSE, s);
-  const uint64_t nout = 1ull << (n - a.u);
-  const unsigned g = grid_for(nout, 8);
-  const bool real = sparse_is_real(a);
-  if (dt == QF_C128) {
-    if (real)
-      k_sparse<double, true><<<g, 256, 0, s>>>(static_cast<double2*>(psi), n, a);
-    else
-      k_sparse<double, false><<<g, 256, 0, s>>>(static_cast<double2*>(psi), n, a);
-  } else {
-    if (real)
-      k_sparse<float, true><<<g, 256, 0, s>>>(static_cast<float2*>(psi), n, a);
-    else
-      k_sparse<float, false><<<g, 256, 0, s>>>(static_cast<float2*>(psi), n, a);
-  }
+  if (dt == QF_C128)
+    sparse_fwd_nr<double>(psi, n, a, realst, s);
+  else
+    sparse_fwd_nr<float>(psi, n, a, realst, s);
   prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
@@ -819,6 +1075,67 @@ cudaError_t launch_hpsi(const void* psi, void* lam, int n, qf_dtype dt, const Ex
   return cudaGetLastError();
 }
 
+template <typename T, int E>
+static cudaError_t hpsi_tiled_e(const void* psi, void* lam, int n, bool realst, const HClass* classes, int nclasses,
+                                const HGroup* groups, const void* chunks, double* partials, unsigned* counter,
+                                double* out, int nblocks, cudaStream_t s) {
+  using V = typename Cx<T>::V;
+  using C = typename WTab<T>::C;
+  const size_t smem = sizeof(V) * 256 * E;
+  const uint64_t ntiles = 1ull << (n - (8 + (E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4)));
+  // persistent grid: exactly the blocks that are resident at once (a partial
+  // second wave would leave most SMs idle at the end)
+  int per_sm = 1;
+  if (realst)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_tiled<T, E, true>, 256, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_tiled<T, E, false>, 256, smem);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
+  if (cap > (uint64_t)nblocks) cap = (uint64_t)nblocks;
+  unsigned g = (unsigned)std::min<uint64_t>(ntiles, cap);
+  if (realst) {
+    cudaFuncSetAttribute(k_hpsi_tiled<T, E, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_hpsi_tiled<T, E, true><<<g, 256, smem, s>>>(static_cast<const V*>(psi), static_cast<V*>(lam), n, classes,
+                                                  nclasses, groups, static_cast<const C*>(chunks), partials,
+                                                  counter, out);
+  } else {
+    cudaFuncSetAttribute(k_hpsi_tiled<T, E, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_hpsi_tiled<T, E, false><<<g, 256, smem, s>>>(static_cast<const V*>(psi), static_cast<V*>(lam), n, classes,
+                                                   nclasses, groups, static_cast<const C*>(chunks), partials,
+                                                   counter, out);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t hpsi_tiled_t(const void* psi, void* lam, int n, int tb, bool realst, const HClass* classes,
+                                int nclasses, const HGroup* groups, const void* chunks, double* partials,
+                                unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  switch (tb) {
+    case 8: return hpsi_tiled_e<T, 1>(psi, lam, n, realst, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s);
+    case 9: return hpsi_tiled_e<T, 2>(psi, lam, n, realst, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s);
+    case 10: return hpsi_tiled_e<T, 4>(psi, lam, n, realst, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s);
+    case 11: return hpsi_tiled_e<T, 8>(psi, lam, n, realst, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s);
+    case 12: return hpsi_tiled_e<T, 16>(psi, lam, n, realst, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_hpsi_tiled(const void* psi, void* lam, int n, qf_dtype dt, int tb, bool realst,
+                              const HClass* classes, int nclasses, const HGroup* groups, const void* chunks,
+                              double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_HPSI, s);
+  cudaError_t e = (dt == QF_C128)
+                      ? hpsi_tiled_t<double>(psi, lam, n, tb, realst, classes, nclasses, groups, chunks, partials,
+                                             counter, out, nblocks, s)
+                      : hpsi_tiled_t<float>(psi, lam, n, tb, realst, classes, nclasses, groups, chunks, partials,
+                                            counter, out, nblocks, s);
+  prof_post(prof_slot_, s);
+  count_launch();
+  return e;
+}
+
 cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotArgs& a, double* partials,
                            unsigned* counter, double* out, int nblocks, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_ADJ_ROT, s);
@@ -833,15 +1150,13 @@ cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotAr
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, double* partials,
-                              unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, bool realst,
+                              double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_ADJ_SPARSE, s);
   if (dt == QF_C128)
-    k_adj_sparse<double><<<nblocks, 256, 0, s>>>(static_cast<double2*>(psi), static_cast<double2*>(lam), n, a,
-                                                 partials, counter, out);
+    sparse_adj_nr<double>(psi, lam, n, a, realst, partials, counter, out, nblocks, s);
   else
-    k_adj_sparse<float><<<nblocks, 256, 0, s>>>(static_cast<float2*>(psi), static_cast<float2*>(lam), n, a,
-                                                partials, counter, out);
+    sparse_adj_nr<float>(psi, lam, n, a, realst, partials, counter, out, nblocks, s);
   prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();

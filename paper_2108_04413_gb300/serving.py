@@ -1,0 +1,222 @@
+"""Continuous-batching server for energy + gradient requests.
+
+Requests (system, parameters) arrive over time.  A dispatcher admits them as
+worker slots free up and as device memory allows: every system keeps its state
+resident (psi and lambda = H psi, 2 * 2^n amplitudes, plus its cached plans) so
+repeated-parameter requests skip all planning, and admission charges a system's
+footprint against an HBM budget, evicting idle resident systems (least
+recently used first) when a new one does not fit.  Admitted requests run on
+worker threads, each call on its system's own CUDA stream; libqf calls release
+the GIL, so the device work of several requests overlaps.  Requests for the
+same system are serialised (one handle is never used by two threads at once).
+
+Latency = completion time - arrival time; the server reports throughput and
+p50/p99 latency.  The executor is pluggable so the scheduling logic can be
+tested without a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class System:
+    key: str
+    n: int
+    det: int
+    ansatz: np.ndarray
+    terms: np.ndarray
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    system: str
+    t: np.ndarray
+    arrival: float  # seconds on the server clock
+    start: float = 0.0
+    done: float = 0.0
+    energy: float = 0.0
+    grad: Optional[np.ndarray] = None
+    error: Optional[str] = None
+
+
+def footprint_bytes(n: int, dtype: str) -> int:
+    """Device bytes a resident system holds: psi and lambda (plan tables are small)."""
+    return 2 * ((16 if dtype == "c128" else 8) << n)
+
+
+class GpuExecutor:
+    """Runs qf_energy_grad on resident libqf states, one CUDA stream per state."""
+
+    def __init__(self, dtype: str = "c64", device: int = 0):
+        import torch
+
+        from . import qf
+
+        self.qf = qf
+        self.torch = torch
+        self.dtype = dtype
+        self.device = device
+
+    def create(self, sysm: System):
+        self.torch.cuda.set_device(self.device)
+        stream = self.torch.cuda.Stream()
+        return self.qf.State(sysm.n, self.dtype, stream=stream)
+
+    def run(self, handle, sysm: System, t: np.ndarray):
+        self.torch.cuda.set_device(self.device)
+        return handle.energy_grad(sysm.det, sysm.ansatz, t, sysm.terms)
+
+    def release(self, handle):
+        handle.close()
+
+
+class Server:
+    def __init__(self, systems: Dict[str, System], executor, workers: int = 4, hbm_budget: int = 8 << 30,
+                 dtype: str = "c64", clock: Callable[[], float] = time.perf_counter):
+        self.systems = systems
+        self.ex = executor
+        self.workers = workers
+        self.budget = hbm_budget
+        self.dtype = dtype
+        self.clock = clock
+        self._lock = threading.Condition()
+        self._pending: collections.deque = collections.deque()
+        self._resident: "collections.OrderedDict[str, object]" = collections.OrderedDict()
+        self._busy: Dict[str, bool] = {}
+        self._used = 0
+        self._active = 0
+        self._closed = False
+        self.done: List[Request] = []
+        self.evictions = 0
+        self.max_concurrent = 0
+        self._threads = [threading.Thread(target=self._worker, daemon=True) for _ in range(workers)]
+        self.t0 = self.clock()
+        for th in self._threads:
+            th.start()
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    # -- submission
+    def submit(self, req: Request):
+        with self._lock:
+            self._pending.append(req)
+            self._lock.notify_all()
+
+    def close(self):
+        with self._lock:
+            self._closed = True
+            self._lock.notify_all()
+        for th in self._threads:
+            th.join()
+        for key, h in list(self._resident.items()):
+            self.ex.release(h)
+        self._resident.clear()
+
+    # -- admission (called with the lock held): first pending request whose
+    # system is idle and whose state is resident or fits after evictions
+    def _admit(self):
+        for i, req in enumerate(self._pending):
+            key = req.system
+            if self._busy.get(key):
+                continue
+            if key in self._resident:
+                del self._pending[i]
+                self._resident.move_to_end(key)
+                return req, self._resident[key], False
+            need = footprint_bytes(self.systems[key].n, self.dtype)
+            if need > self.budget:
+                del self._pending[i]
+                req.error = "system does not fit the HBM budget"
+                req.done = self.now()
+                self.done.append(req)
+                return None
+            victims = []
+            free = self.budget - self._used
+            for k in self._resident:  # least recently used first
+                if free >= need:
+                    break
+                if not self._busy.get(k):
+                    victims.append(k)
+                    free += footprint_bytes(self.systems[k].n, self.dtype)
+            if free < need:
+                continue  # wait for a busy system to finish
+            for k in victims:
+                h = self._resident.pop(k)
+                self._used -= footprint_bytes(self.systems[k].n, self.dtype)
+                self.evictions += 1
+                self.ex.release(h)
+            del self._pending[i]
+            self._used += need
+            return req, None, True
+        return None
+
+    def _worker(self):
+        while True:
+            with self._lock:
+                while True:
+                    got = self._admit() if self._pending else None
+                    if got is not None:
+                        break
+                    if self._closed and not self._pending:
+                        return
+                    self._lock.wait(timeout=0.05)
+                req, handle, fresh = got
+                key = req.system
+                self._busy[key] = True
+                self._active += 1
+                self.max_concurrent = max(self.max_concurrent, self._active)
+            sysm = self.systems[key]
+            try:
+                if fresh:
+                    handle = self.ex.create(sysm)
+                req.start = self.now()
+                e, g = self.ex.run(handle, sysm, req.t)
+                req.energy, req.grad = float(e), np.asarray(g)
+            except Exception as exc:  # the request fails, the server keeps going
+                req.error = repr(exc)
+            req.done = self.now()
+            with self._lock:
+                if fresh and handle is not None:
+                    self._resident[key] = handle
+                    self._resident.move_to_end(key)
+                elif fresh:
+                    self._used -= footprint_bytes(sysm.n, self.dtype)
+                self._busy[key] = False
+                self._active -= 1
+                self.done.append(req)
+                self._lock.notify_all()
+
+
+def replay(server: Server, requests: List[Request], realtime: bool = True) -> List[Request]:
+    """Submit requests at their arrival times (server clock), wait for all."""
+    for req in sorted(requests, key=lambda r: r.arrival):
+        if realtime:
+            delay = req.arrival - server.now()
+            if delay > 0:
+                time.sleep(delay)
+        server.submit(req)
+    while True:
+        with server._lock:
+            if len(server.done) >= len(requests):
+                break
+        time.sleep(0.002)
+    return server.done
+
+
+def latency_stats(done: List[Request]) -> dict:
+    ok = [r for r in done if r.error is None]
+    lat = np.array([r.done - r.arrival for r in ok])
+    span = max(r.done for r in ok) - min(r.arrival for r in ok) if ok else 0.0
+    return {"requests": len(done), "failed": len(done) - len(ok),
+            "throughput_rps": len(ok) / span if span > 0 else 0.0,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None}

@@ -169,6 +169,24 @@ def test_energy_grad_ucc_c128_matches_oracle_adjoint():
     assert abs(abs(out[det]) - 1) < 1e-12
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_energy_grad_repeated_calls_new_angles(dtype):
+    """The ansatz structure is planned once per handle; later calls refill the
+    composites for new angles.  Each call must match the oracle."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], dtype)
+    for k, tt in enumerate((t, 3 * t[::-1].copy(), amplitudes(len(exs), 99, 0.4))):
+        e, grad = st.energy_grad(det, A, tt, T)
+        e_ref, g_ref = fermion.ucc_gradient_adjoint(cfg["n_orb"], cfg["n_el"], h, g, tt, exs)
+        if dtype == "c128":
+            assert abs(e - e_ref) < TOL_E_C128, k
+            assert np.abs(grad - g_ref).max() < 1e-10, k
+        else:
+            assert abs(e - e_ref) < TOL_E_C64, k
+            assert np.linalg.norm(grad - g_ref) / np.linalg.norm(g_ref) < TOL_G_C64, k
+
+
 def test_energy_grad_ucc_16q_fd():
     cfg, h, g, T, A, exs, t = _ucc_problem(1)
     det = (1 << cfg["n_el"]) - 1
@@ -201,6 +219,31 @@ def test_energy_grad_generic_ansatz_matches_oracle():
     e_ref, g_ref, _ = pauli.adjoint_gradient(n, det, arots, t, _terms_list(T))
     assert abs(e - e_ref) < TOL_E_C128
     assert np.abs(grad - g_ref).max() < 1e-10
+
+
+@pytest.mark.parametrize("n,dtype", [(12, "c128"), (13, "c128"), (12, "c64")])
+def test_energy_grad_generic_complex_tiled(n, dtype):
+    """Complex state and odd-Y terms at n >= 10: the tiled H|psi> kernel's complex path."""
+    rng = np.random.default_rng(n)
+    m, npar = 30, 7
+    A = qf.as_arots(rng.integers(0, 1 << n, m), rng.integers(0, 1 << n, m), rng.normal(size=m),
+                    rng.integers(0, npar, m))
+    t = rng.normal(size=npar)
+    xs = rng.integers(0, 1 << n, 400)
+    xs[:50] = xs[50:100] ^ 1
+    xs[100:110] = 0
+    T = qf.as_terms(xs, rng.integers(0, 1 << n, 400), rng.normal(size=400) / 20)
+    det = (1 << (n // 2)) - 1
+    st = qf.State(n, dtype)
+    e, grad = st.energy_grad(det, A, t, T)
+    arots = list(zip(A["x"], A["z"], A["coeff"], A["param"]))
+    e_ref, g_ref, _ = pauli.adjoint_gradient(n, det, arots, t, _terms_list(T))
+    if dtype == "c128":
+        assert abs(e - e_ref) < TOL_E_C128
+        assert np.abs(grad - g_ref).max() < 1e-10
+    else:
+        assert abs(e - e_ref) < TOL_E_C64
+        assert np.linalg.norm(grad - g_ref) / np.linalg.norm(g_ref) < TOL_G_C64
 
 
 def test_energy_grad_c64_relative():

@@ -1,0 +1,103 @@
+"""Serving scheduler logic without a GPU (fake executor): every request
+completes, admission never exceeds the HBM budget, idle systems are evicted
+least-recently-used first, work overlaps, and results do not depend on the mix."""
+import threading
+import time
+
+import numpy as np
+
+from paper_2108_04413_gb300.serving import Request, Server, System, footprint_bytes, latency_stats, replay
+
+
+class FakeExecutor:
+    def __init__(self, budget, dtype):
+        self.budget = budget
+        self.dtype = dtype
+        self.used = 0
+        self.max_used = 0
+        self.active = 0
+        self.max_active = 0
+        self.lock = threading.Lock()
+        self.created = []
+
+    def create(self, sysm):
+        with self.lock:
+            self.used += footprint_bytes(sysm.n, self.dtype)
+            self.max_used = max(self.max_used, self.used)
+            self.created.append(sysm.key)
+        return {"key": sysm.key, "n": sysm.n}
+
+    def run(self, handle, sysm, t):
+        with self.lock:
+            self.active += 1
+            self.max_active = max(self.max_active, self.active)
+        time.sleep(0.002 * (sysm.n - 6))
+        with self.lock:
+            self.active -= 1
+        e = float(np.sum(np.sin(t)) + sysm.n)
+        return e, np.cos(t)
+
+    def release(self, handle):
+        with self.lock:
+            self.used -= footprint_bytes(handle["n"], self.dtype)
+
+
+def _systems():
+    out = {}
+    for n in (8, 10, 12):
+        for k in range(2):
+            key = f"n{n}-{k}"
+            out[key] = System(key, n, (1 << (n // 2)) - 1, np.zeros(0), np.zeros(0))
+    return out
+
+
+def _requests(systems, count, seed):
+    rng = np.random.default_rng(seed)
+    keys = sorted(systems)
+    arr = np.cumsum(rng.exponential(1 / 400.0, count))
+    return [Request(i, keys[int(rng.integers(0, len(keys)))], rng.normal(size=5), float(arr[i])) for i in range(count)]
+
+
+def test_all_complete_and_match_sequential():
+    systems = _systems()
+    reqs = _requests(systems, 60, 1)
+    ex = FakeExecutor(1 << 30, "c64")
+    srv = Server(systems, ex, workers=4, hbm_budget=1 << 30)
+    done = replay(srv, reqs)
+    srv.close()
+    assert len(done) == 60 and all(r.error is None for r in done)
+    for r in done:
+        e, g = FakeExecutor(0, "c64").run(None, systems[r.system], r.t)
+        assert r.energy == e and np.array_equal(r.grad, g)
+        assert r.done >= r.start >= r.arrival - 1e-9
+    assert ex.max_active > 1  # requests overlapped
+    st = latency_stats(done)
+    assert st["failed"] == 0 and st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_budget_respected_with_eviction():
+    systems = _systems()
+    reqs = _requests(systems, 50, 2)
+    budget = footprint_bytes(12, "c64") + footprint_bytes(10, "c64")  # two systems at most
+    ex = FakeExecutor(budget, "c64")
+    srv = Server(systems, ex, workers=3, hbm_budget=budget)
+    done = replay(srv, reqs, realtime=False)
+    srv.close()
+    assert len(done) == 50 and all(r.error is None for r in done)
+    assert ex.max_used <= budget
+    assert srv.evictions > 0
+    assert ex.used == 0  # everything released at close
+
+
+def test_oversized_system_fails_alone():
+    systems = _systems()
+    reqs = _requests(systems, 10, 3)
+    systems["big"] = System("big", 30, 0, np.zeros(0), np.zeros(0))
+    reqs.append(Request(99, "big", np.zeros(5), 0.0))
+    ex = FakeExecutor(1 << 26, "c64")
+    srv = Server(systems, ex, workers=2, hbm_budget=1 << 26)
+    done = replay(srv, reqs, realtime=False)
+    srv.close()
+    big = [r for r in done if r.rid == 99][0]
+    assert big.error is not None
+    assert sum(r.error is None for r in done) == 10
