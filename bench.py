@@ -307,7 +307,8 @@ def run_gpu(args, rank, world, local, pg):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.dtype == "c128" else "f32 state, f64 reductions",
+        "dtype": ("f64 (H|psi> multiply-adds in double-single, ~2^-46; see hpsi_fp64_mode)"
+                  if args.dtype == "c128" else "f32 state, f64 reductions"),
         "data": "synthetic (seeded integrals, dUCCSD amplitudes)",
         "config": {
             "workload": f"{n}-qubit dUCCSD energy + adjoint gradient ({args.workload})",
@@ -327,6 +328,7 @@ def run_gpu(args, rank, world, local, pg):
         out["e2e"] = e2e_leg(st, w, args, stats, stream)
         if args.dtype == "c128":
             out["c64"] = c64_leg(w, args, value, float(energies[-1]), g)
+            out["hpsi_fp64_mode"] = fp64_mode_leg(w, args, value, float(energies[-1]), g)
         t_eval, sample = oracle_sample_ucc(w)
         out["cpu_baseline"] = {"value": 1.0 / t_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
                                "sample": sample}
@@ -385,6 +387,32 @@ def e2e_leg(st, w, args, stats, stream):
     d2h = 8 * (len(w["exs"]) + 2)
     return {"value": 1.0 / dt, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "steps": steps}
+
+
+def fp64_mode_leg(w, args, value_ds, e_ds, g_ds):
+    """The same c128 evaluation with H|psi> in plain FP64 multiply-adds: its
+    throughput, and how far the default double-single result is from it."""
+    import torch
+
+    from paper_2108_04413_gb300 import qf
+
+    stream = torch.cuda.Stream()
+    st = qf.State(w["n"], "c128", stream=stream)
+    st.set_hpsi_mode(qf.QF_HPSI_FP64)
+    st.energy_grad(w["det"], w["ansatz"], w["t"], w["terms"])
+    torch.cuda.synchronize()
+    steps = max(2, min(args.steps, 3))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        e, g = st.energy_grad(w["det"], w["ansatz"], w["t"], w["terms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    v = steps / (e0.elapsed_time(e1) / 1e3)
+    st.close()
+    return {"value": v, "unit": "evals/s", "default_speedup": value_ds / v,
+            "default_energy_diff": abs(e - e_ds), "default_grad_max_diff": float(np.abs(g - g_ds).max())}
 
 
 def c64_leg(w, args, value128, e128, g128):

@@ -114,6 +114,19 @@ qf_status qf_state_fold_scale(qf_state* st);
  * current scale (amplitudes = scale * stored values).  Any pointer may be NULL. */
 qf_status qf_state_info(const qf_state* st, int* n, qf_dtype* dtype, void** dev_ptr, double* scale);
 
+/* Arithmetic of qf_energy_grad's H|psi> for QF_C128 states that are exactly
+ * real with a Hamiltonian whose strings all have an even number of Y letters
+ * (every dUCC state of a real Hamiltonian).  GB300 runs FP64 multiply-adds at
+ * 1/58 of its FP32 rate, and this step needs one per (X group, amplitude).
+ * QF_HPSI_FP64: FP64 multiply-adds.  QF_HPSI_DS (default): double-single
+ * multiply-adds on the FP32 pipe -- values and tables split into (hi, lo) float
+ * pairs (~48 bits), products formed exactly in their leading part, error-free
+ * TwoSum accumulation, FP64 for the energy, norm and overlaps; relative error
+ * per operation ~2^-46.  Other states always use FP64. */
+#define QF_HPSI_FP64 0
+#define QF_HPSI_DS 1
+qf_status qf_state_set_hpsi_mode(qf_state* st, int mode);
+
 /* Drop the Pauli-sum plans (X-mask groups and their tables) cached in the
  * handle, so the next qf_expectation / qf_energy_grad groups and uploads its
  * terms again. */

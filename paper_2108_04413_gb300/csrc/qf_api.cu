@@ -45,6 +45,7 @@ struct ExpPlan {
   qf::HGroup* d_hgroups = nullptr;
   qf::WChunk* d_wchunks = nullptr;
   qf::WChunkF* d_wchunks_f = nullptr;
+  qf::WChunkS* d_wchunks_s = nullptr;  // real D as (hi, lo) floats for double-single H|psi>
   qf::HClass* d_classes[2] = {nullptr, nullptr};
   int nclasses[2] = {0, 0};
   bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
@@ -57,6 +58,7 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_hgroups);
   cudaFree(p.d_wchunks);
   cudaFree(p.d_wchunks_f);
+  cudaFree(p.d_wchunks_s);
   cudaFree(p.d_classes[0]);
   cudaFree(p.d_classes[1]);
   p = ExpPlan();
@@ -87,6 +89,7 @@ struct qf_state {
   // is kept by real sparse composites and by rotations with x != 0 and an odd
   // number of Y letters (their phases map real amplitudes to real ones).
   bool real = true;
+  int hpsi_mode = QF_HPSI_DS;
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
   double* d_out = nullptr;
@@ -234,6 +237,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   std::vector<qf::HGroup> hg;
   std::vector<qf::WChunk> wc;
   std::vector<qf::WChunkF> wf;
+  std::vector<qf::WChunkS> ws;
   for (auto& kv : byx) {
     qf::HGroup g{};
     g.x = kv.first;
@@ -243,8 +247,9 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     for (size_t k = 0; k < idx.size(); k += qf::kWideTerms) {
       qf::WChunk c{};
       qf::WChunkF cf{};
+      qf::WChunkS cs{};
       const int cnt = (int)std::min<size_t>(qf::kWideTerms, idx.size() - k);
-      for (int t = 0; t < qf::kWideTerms; ++t) c.z[t] = cf.z[t] = (t < cnt) ? terms[idx[k + t]].z : 0ull;
+      for (int t = 0; t < qf::kWideTerms; ++t) c.z[t] = cf.z[t] = cs.z[t] = (t < cnt) ? terms[idx[k + t]].z : 0ull;
       for (int pat = 0; pat < (1 << qf::kWideTerms); ++pat) {
         double hx = 0, hy = 0;
         for (int t = 0; t < cnt; ++t) {
@@ -258,11 +263,14 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
         }
         c.tab[pat] = make_double2(hx, hy);
         cf.tab[pat] = make_float2((float)hx, (float)hy);
+        const float hh = (float)hx;
+        cs.tab[pat] = make_float2(hh, (float)(hx - (double)hh));
       }
       for (int t = 0; t < cnt; ++t)
         if (popc(terms[idx[k + t]].x & terms[idx[k + t]].z) & 1) g.odd = 1;
       wc.push_back(c);
       wf.push_back(cf);
+      ws.push_back(cs);
     }
     hg.push_back(g);
   }
@@ -294,6 +302,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     if (cudaMalloc(&p.d_hgroups, hg.size() * sizeof(qf::HGroup)) != cudaSuccess ||
         cudaMalloc(&p.d_wchunks, wc.size() * sizeof(qf::WChunk)) != cudaSuccess ||
         cudaMalloc(&p.d_wchunks_f, wf.size() * sizeof(qf::WChunkF)) != cudaSuccess ||
+        cudaMalloc(&p.d_wchunks_s, ws.size() * sizeof(qf::WChunkS)) != cudaSuccess ||
         cudaMalloc(&p.d_classes[0], cls[0].size() * sizeof(qf::HClass)) != cudaSuccess ||
         cudaMalloc(&p.d_classes[1], cls[1].size() * sizeof(qf::HClass)) != cudaSuccess) {
       cudaGetLastError();
@@ -305,6 +314,8 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks, wc.data(), wc.size() * sizeof(qf::WChunk), cudaMemcpyHostToDevice,
                             st->stream));
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks_f, wf.data(), wf.size() * sizeof(qf::WChunkF), cudaMemcpyHostToDevice,
+                            st->stream));
+    QF_CUDA(cudaMemcpyAsync(p.d_wchunks_s, ws.data(), ws.size() * sizeof(qf::WChunkS), cudaMemcpyHostToDevice,
                             st->stream));
     for (int v = 0; v < 2; ++v)
       QF_CUDA(cudaMemcpyAsync(p.d_classes[v], cls[v].data(), cls[v].size() * sizeof(qf::HClass),
@@ -793,7 +804,10 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   const int nb = qf::reduce_blocks(n, st->dt);
   double* d_e = st->d_out + blocks.size();
   const bool hreal = st->real && p && !p->has_odd;
-  if (p && n >= 10) {
+  if (p && n >= 11 && hreal && st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS) {
+    QF_CUDA(qf::launch_hpsi_ds(st->psi, st->lam, n, 11, p->d_classes[1], p->nclasses[1], p->d_hgroups,
+                               p->d_wchunks_s, st->d_partials, st->d_counter, d_e, nb, st->stream));
+  } else if (p && n >= 10) {
     // tiles of 2^11 amplitudes when the state is real (fewer registers per element), else 2^10
     const int v = (hreal && n >= 11) ? 1 : 0;
     QF_CUDA(qf::launch_hpsi_tiled(st->psi, st->lam, n, st->dt, 10 + v, hreal, p->d_classes[v], p->nclasses[v],
@@ -875,6 +889,13 @@ qf_status qf_state_copy_from_host(qf_state* st, const void* host, size_t bytes) 
   QF_CUDA(cudaMemcpyAsync(st->psi, host, bytes, cudaMemcpyHostToDevice, st->stream));
   st->scale = 1.0;
   st->real = false;
+  return QF_OK;
+}
+
+qf_status qf_state_set_hpsi_mode(qf_state* st, int mode) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  if (mode != QF_HPSI_FP64 && mode != QF_HPSI_DS) return fail(QF_EINVAL, "unknown H|psi> mode");
+  st->hpsi_mode = mode;
   return QF_OK;
 }
 

@@ -103,6 +103,11 @@ struct WChunkF {
   float2 tab[1 << kWideTerms];
 };
 
+struct WChunkS {
+  uint64_t z[kWideTerms];
+  float2 tab[1 << kWideTerms];  // real D split as (hi, lo) floats: D = hi + lo to ~2^-48
+};
+
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s);
 cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s);
@@ -125,6 +130,11 @@ cudaError_t launch_hpsi(const void* psi, void* lam, int n, qf_dtype dt, const Ex
 cudaError_t launch_hpsi_tiled(const void* psi, void* lam, int n, qf_dtype dt, int tb, bool realst,
                               const HClass* classes, int nclasses, const HGroup* groups, const void* chunks,
                               double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s);
+// Tiled H|psi> for a real complex128 state and real D with double-single
+// multiply-adds on the FP32 pipe (same outputs as launch_hpsi_tiled).
+cudaError_t launch_hpsi_ds(const void* psi, void* lam, int n, int tb, const HClass* classes, int nclasses,
+                           const HGroup* groups, const WChunkS* chunks, double* partials, unsigned* counter,
+                           double* out, int nblocks, cudaStream_t s);
 // Reverse step: out[0] = Im <lam|P|psi> (stored units), then psi, lam <- exp(+i th P).
 cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotArgs& a, double* partials,
                            unsigned* counter, double* out, int nblocks, cudaStream_t s);

@@ -606,6 +606,112 @@ __global__ void __launch_bounds__(256) k_hpsi_tiled(const typename Cx<T>::V* __r
 }
 
 // ---------------------------------------------------------------------------
+// tiled H|psi> for a real complex128 state and real D_g, double-single arithmetic
+//
+// GB300 executes FP64 FMAs at 1/58 of the FP32 rate, and this gather needs one
+// multiply-add per (X group, amplitude).  Here each staged partner amplitude
+// and each table value is split into a pair of floats (hi + lo, ~48 bits), the
+// product D * v is formed exactly in its leading part (p = dh*vh and its FMA
+// residual) plus the cross terms dh*vl + dl*vh, and it is accumulated with an
+// error-free TwoSum into a (hi, lo) float pair per output amplitude.  Per
+// operation the relative error is about 2^-46; the pair is renormalised once per
+// class and converted to FP64 when the tile is written.  Groups with more than
+// eight terms contribute one product per eight-term table.
+
+// The _rn intrinsics keep the compiler from contracting or reassociating the
+// error-free transformations.
+__device__ __forceinline__ void ds_mad(float& ah, float& al, float dh, float dl, float vh, float vl) {
+  const float p = __fmul_rn(dh, vh);
+  float e = fmaf(dh, vh, -p);
+  e = fmaf(dh, vl, e);
+  e = fmaf(dl, vh, e);
+  const float s = __fadd_rn(ah, p);
+  const float bp = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  al = __fadd_rn(al, __fadd_rn(err, e));
+  ah = s;
+}
+
+template <int E>
+__global__ void __launch_bounds__(256) k_hpsi_ds(const double2* __restrict__ psi, double2* __restrict__ lam, int n,
+                                                 const HClass* __restrict__ classes, int nclasses,
+                                                 const HGroup* __restrict__ groups,
+                                                 const WChunkS* __restrict__ chunks, double* partials,
+                                                 unsigned* counter, double* out) {
+  constexpr int TB = (E == 1) ? 8 : (E == 2) ? 9 : (E == 4) ? 10 : (E == 8) ? 11 : 12;
+  constexpr int KB = TB - 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tile = reinterpret_cast<float2*>(smem_raw);
+  const unsigned tid = threadIdx.x;
+  const uint64_t ntiles = 1ull << (n - TB);
+  double acc_e = 0.0, acc_n = 0.0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    float ah[E], al[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) ah[k] = al[k] = 0.f;
+    for (int ci = 0; ci < nclasses; ++ci) {
+      const HClass C = classes[ci];
+      const uint64_t pt = t ^ C.xh;
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const double v = psi[(pt << TB) + tid + 256u * k].x;
+        const float vh = __double2float_rn(v);
+        tile[tid + 256u * k] = make_float2(vh, __double2float_rn(v - (double)vh));
+      }
+      __syncthreads();
+      for (int g = C.g0; g < C.g1; ++g) {
+        const HGroup G = groups[g];
+        const unsigned xl = (unsigned)(G.x & ((1ull << TB) - 1ull));
+        const unsigned xlo = xl & 255u, xhi = xl >> 8;
+        for (int c = 0; c < G.nchunk; ++c) {
+          const WChunkS* W = chunks + G.chunk0 + c;
+          unsigned ith = 0, col[KB > 0 ? KB : 1];
+#pragma unroll
+          for (int j = 0; j < (KB > 0 ? KB : 1); ++j) col[j] = 0;
+#pragma unroll
+          for (int q = 0; q < kWideTerms; ++q) {
+            const uint64_t z = W->z[q];
+            const unsigned hp = par64((z >> TB) & pt);
+            const unsigned tp = (unsigned)__popc((unsigned)z & 255u & (tid ^ xlo)) & 1u;
+            ith |= (hp ^ tp) << q;
+#pragma unroll
+            for (int j = 0; j < KB; ++j) col[j] |= (unsigned)((z >> (8 + j)) & 1ull) << q;
+          }
+#pragma unroll
+          for (int k = 0; k < E; ++k) {
+            unsigned idx = ith;
+            const unsigned kk = (unsigned)k ^ xhi;
+#pragma unroll
+            for (int j = 0; j < KB; ++j)
+              if ((kk >> j) & 1u) idx ^= col[j];
+            const float2 d = W->tab[idx];
+            const float2 v = tile[(tid ^ xlo) | (kk << 8)];
+            ds_mad(ah[k], al[k], d.x, d.y, v.x, v.y);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < E; ++k) {  // renormalise the pair once per class
+        const float s = __fadd_rn(ah[k], al[k]);
+        al[k] = __fsub_rn(al[k], __fsub_rn(s, ah[k]));
+        ah[k] = s;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const uint64_t cidx = (t << TB) + tid + 256u * k;
+      const double lx = (double)ah[k] + (double)al[k];
+      const double2 u = psi[cidx];
+      acc_e = fma(u.x, lx, acc_e);
+      acc_n = fma(u.x, u.x, acc_n);
+      lam[cidx] = make_double2(lx, 0.0);
+    }
+  }
+  grid_finish2(acc_e, acc_n, partials, counter, out);
+}
+
+// ---------------------------------------------------------------------------
 // adjoint step for one rotation: out = Im <lam|P|psi> (pre-rotation values),
 // then psi and lam both get the rotation given in the arguments (the host passes
 // -theta, i.e. exp(+i theta P)).
@@ -1131,6 +1237,39 @@ cudaError_t launch_hpsi_tiled(const void* psi, void* lam, int n, qf_dtype dt, in
                                              counter, out, nblocks, s)
                       : hpsi_tiled_t<float>(psi, lam, n, tb, realst, classes, nclasses, groups, chunks, partials,
                                             counter, out, nblocks, s);
+  prof_post(prof_slot_, s);
+  count_launch();
+  return e;
+}
+
+template <int E>
+static cudaError_t hpsi_ds_e(const void* psi, void* lam, int n, const HClass* classes, int nclasses,
+                             const HGroup* groups, const WChunkS* chunks, double* partials, unsigned* counter,
+                             double* out, int nblocks, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * 256 * E;
+  const int tb = 8 + (E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4);
+  const uint64_t ntiles = 1ull << (n - tb);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_ds<E>, 256, smem);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
+  if (cap > (uint64_t)nblocks) cap = (uint64_t)nblocks;
+  const unsigned g = (unsigned)std::min<uint64_t>(ntiles, cap);
+  k_hpsi_ds<E><<<g, 256, smem, s>>>(static_cast<const double2*>(psi), static_cast<double2*>(lam), n, classes,
+                                    nclasses, groups, chunks, partials, counter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hpsi_ds(const void* psi, void* lam, int n, int tb, const HClass* classes, int nclasses,
+                           const HGroup* groups, const WChunkS* chunks, double* partials, unsigned* counter,
+                           double* out, int nblocks, cudaStream_t s) {
+  const int prof_slot_ = prof_pre(QF_K_HPSI, s);
+  cudaError_t e;
+  switch (tb) {
+    case 10: e = hpsi_ds_e<4>(psi, lam, n, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s); break;
+    case 11: e = hpsi_ds_e<8>(psi, lam, n, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s); break;
+    default: e = cudaErrorInvalidValue;
+  }
   prof_post(prof_slot_, s);
   count_launch();
   return e;

@@ -19,6 +19,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 QF_OK, QF_EINVAL, QF_ENOMEM, QF_ECUDA, QF_ETIMEOUT = range(5)
 QF_C128, QF_C64 = 0, 1
+QF_HPSI_FP64, QF_HPSI_DS = 0, 1
 QF_MAX_QUBITS = 34
 
 from .abi import AROT_DTYPE, ROT_DTYPE, TERM_DTYPE, as_arots, as_rots, as_terms  # noqa: F401
@@ -43,6 +44,7 @@ _SIGS = {
     "qf_state_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(_vp), _dp]),
     "qf_state_clear_plans": (ctypes.c_int, [_vp]),
+    "qf_state_set_hpsi_mode": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qf_kernel_launches": (ctypes.c_uint64, [ctypes.c_int]),
     "qf_profile_begin": (ctypes.c_int, [ctypes.c_uint]),
     "qf_profile_read": (ctypes.c_int, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint64), _dp]),
@@ -179,6 +181,9 @@ class State:
         _check(_lib.qf_energy_grad(self._h, int(det), _ptr(ansatz), len(ansatz), _ptr(t), len(t), _ptr(terms),
                                    len(terms), ctypes.byref(e), _ptr(grad)))
         return e.value, grad
+
+    def set_hpsi_mode(self, mode: int):
+        _check(_lib.qf_state_set_hpsi_mode(self._h, int(mode)))
 
     def clear_plans(self):
         _check(_lib.qf_state_clear_plans(self._h))

@@ -187,6 +187,20 @@ def test_energy_grad_repeated_calls_new_angles(dtype):
             assert np.linalg.norm(grad - g_ref) / np.linalg.norm(g_ref) < TOL_G_C64, k
 
 
+@pytest.mark.parametrize("mode", ["fp64", "ds"])
+def test_energy_grad_ucc_16q_matches_oracle_both_hpsi_modes(mode):
+    """16-qubit dUCCSD energy and full gradient with the H|psi> step in FP64 and
+    in double-single arithmetic, against the oracle's fermionic adjoint."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], "c128")
+    st.set_hpsi_mode(qf.QF_HPSI_FP64 if mode == "fp64" else qf.QF_HPSI_DS)
+    e, grad = st.energy_grad(det, A, t, T)
+    e_ref, g_ref = fermion.ucc_gradient_adjoint(cfg["n_orb"], cfg["n_el"], h, g, t, exs)
+    assert abs(e - e_ref) < TOL_E_C128
+    assert np.abs(grad - g_ref).max() < 1e-10
+
+
 def test_energy_grad_ucc_16q_fd():
     cfg, h, g, T, A, exs, t = _ucc_problem(1)
     det = (1 << cfg["n_el"]) - 1
