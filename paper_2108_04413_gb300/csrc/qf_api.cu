@@ -46,8 +46,8 @@ struct ExpPlan {
   qf::WChunk* d_wchunks = nullptr;
   qf::WChunkF* d_wchunks_f = nullptr;
   qf::WChunkS* d_wchunks_s = nullptr;  // real D as (hi, lo) floats for double-single H|psi>
-  qf::HClass* d_classes[2] = {nullptr, nullptr};
-  int nclasses[2] = {0, 0};
+  qf::HClass* d_classes[qf::kClassTbN] = {};  // classes for tile bits 10, 11, 12
+  int nclasses[qf::kClassTbN] = {};
   bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
 };
 
@@ -59,8 +59,7 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_wchunks);
   cudaFree(p.d_wchunks_f);
   cudaFree(p.d_wchunks_s);
-  cudaFree(p.d_classes[0]);
-  cudaFree(p.d_classes[1]);
+  for (int v = 0; v < qf::kClassTbN; ++v) cudaFree(p.d_classes[v]);
   p = ExpPlan();
 }
 
@@ -84,6 +83,7 @@ struct qf_state {
   void* psi = nullptr;
   bool own_psi = false;
   void* lam = nullptr;
+  void* split = nullptr;  // (hi, lo) float copy of psi's real parts for double-single H|psi>
   double scale = 1.0;
   // Every stored imaginary part is exactly zero.  Holds after qf_set_basis and
   // is kept by real sparse composites and by rotations with x != 0 and an odd
@@ -249,7 +249,25 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
       qf::WChunkF cf{};
       qf::WChunkS cs{};
       const int cnt = (int)std::min<size_t>(qf::kWideTerms, idx.size() - k);
-      for (int t = 0; t < qf::kWideTerms; ++t) c.z[t] = cf.z[t] = cs.z[t] = (t < cnt) ? terms[idx[k + t]].z : 0ull;
+      for (int t = 0; t < qf::kWideTerms; ++t) c.z[t] = cf.z[t] = (t < cnt) ? terms[idx[k + t]].z : 0ull;
+      // double-single tables (tiles of 2^12): split each term's pattern bit into a
+      // tile part (z >> 12), a thread-nibble part and an element part.
+      {
+        const unsigned xhi = (unsigned)((kv.first >> 8) & 15u);
+        for (int t = 0; t < qf::kWideTerms; ++t) cs.zh[t] = c.z[t] >> 12;
+        for (int v = 0; v < 16; ++v) {
+          unsigned bl = 0, bh = 0, bk = 0;
+          for (int t = 0; t < qf::kWideTerms; ++t) {
+            const uint64_t z = c.z[t];
+            bl |= (unsigned)(popc(z & 15u & (uint64_t)v) & 1) << t;
+            bh |= (unsigned)(popc(z & 0xF0u & ((uint64_t)v << 4)) & 1) << t;
+            bk |= (unsigned)(popc((z >> 8) & 15u & (uint64_t)(v ^ xhi)) & 1) << t;
+          }
+          cs.nl[v] = (uint8_t)bl;
+          cs.nh[v] = (uint8_t)bh;
+          cs.kx[v] = (uint8_t)bk;
+        }
+      }
       for (int pat = 0; pat < (1 << qf::kWideTerms); ++pat) {
         double hx = 0, hy = 0;
         for (int t = 0; t < cnt; ++t) {
@@ -274,9 +292,9 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     }
     hg.push_back(g);
   }
-  std::vector<qf::HClass> cls[2];
-  for (int v = 0; v < 2; ++v) {
-    const int tb = 10 + v;
+  std::vector<qf::HClass> cls[qf::kClassTbN];
+  for (int v = 0; v < qf::kClassTbN; ++v) {
+    const int tb = qf::kClassTb0 + v;
     for (int g = 0; g < (int)hg.size(); ++g) {
       const uint64_t xh = hg[g].x >> tb;
       if (cls[v].empty() || cls[v].back().xh != xh) cls[v].push_back(qf::HClass{xh, g, g + 1});
@@ -304,7 +322,8 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
         cudaMalloc(&p.d_wchunks_f, wf.size() * sizeof(qf::WChunkF)) != cudaSuccess ||
         cudaMalloc(&p.d_wchunks_s, ws.size() * sizeof(qf::WChunkS)) != cudaSuccess ||
         cudaMalloc(&p.d_classes[0], cls[0].size() * sizeof(qf::HClass)) != cudaSuccess ||
-        cudaMalloc(&p.d_classes[1], cls[1].size() * sizeof(qf::HClass)) != cudaSuccess) {
+        cudaMalloc(&p.d_classes[1], cls[1].size() * sizeof(qf::HClass)) != cudaSuccess ||
+        cudaMalloc(&p.d_classes[2], cls[2].size() * sizeof(qf::HClass)) != cudaSuccess) {
       cudaGetLastError();
       free_plan(p);
       return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
@@ -317,7 +336,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
                             st->stream));
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks_s, ws.data(), ws.size() * sizeof(qf::WChunkS), cudaMemcpyHostToDevice,
                             st->stream));
-    for (int v = 0; v < 2; ++v)
+    for (int v = 0; v < qf::kClassTbN; ++v)
       QF_CUDA(cudaMemcpyAsync(p.d_classes[v], cls[v].data(), cls[v].size() * sizeof(qf::HClass),
                               cudaMemcpyHostToDevice, st->stream));
     QF_CUDA(cudaStreamSynchronize(st->stream));
@@ -652,6 +671,7 @@ qf_status qf_state_destroy(qf_state* st) {
   for (auto& kv : st->plans) free_plan(kv.second);
   if (st->own_psi) cudaFree(st->psi);
   cudaFree(st->lam);
+  cudaFree(st->split);
   cudaFree(st->d_partials);
   cudaFree(st->d_counter);
   cudaFree(st->d_out);
@@ -804,8 +824,13 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   const int nb = qf::reduce_blocks(n, st->dt);
   double* d_e = st->d_out + blocks.size();
   const bool hreal = st->real && p && !p->has_odd;
-  if (p && n >= 11 && hreal && st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS) {
-    QF_CUDA(qf::launch_hpsi_ds(st->psi, st->lam, n, 11, p->d_classes[1], p->nclasses[1], p->d_hgroups,
+  if (p && n >= 12 && hreal && st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS) {
+    if (!st->split && cudaMalloc(&st->split, sizeof(float2) << n) != cudaSuccess) {
+      cudaGetLastError();
+      st->split = nullptr;
+      return fail(QF_ENOMEM, "cudaMalloc(double-single split) failed");
+    }
+    QF_CUDA(qf::launch_hpsi_ds(st->psi, st->lam, st->split, n, p->d_classes[2], p->nclasses[2], p->d_hgroups,
                                p->d_wchunks_s, st->d_partials, st->d_counter, d_e, nb, st->stream));
   } else if (p && n >= 10) {
     // tiles of 2^11 amplitudes when the state is real (fewer registers per element), else 2^10

@@ -84,6 +84,8 @@ struct ExpChunk {
 // H|psi> plan (tiled): groups sorted by X mask form classes of equal high part
 // x >> tb (tb = tile bits); a class reads one partner tile per output tile.
 constexpr int kWideTerms = 8;  // terms per H|psi> sign-pattern table
+constexpr int kClassTb0 = 10;  // class tables exist for tile bits 10, 11, 12
+constexpr int kClassTbN = 3;
 struct HClass {
   uint64_t xh;  // x >> tb
   int g0, g1;   // group range [g0, g1)
@@ -103,8 +105,13 @@ struct WChunkF {
   float2 tab[1 << kWideTerms];
 };
 
+// Double-single H|psi> table for tiles of 2^12 amplitudes (thread t owns
+// c = t + 256 k, k < 16): everything about the sign pattern that does not depend
+// on the tile is precomputed here.
 struct WChunkS {
-  uint64_t z[kWideTerms];
+  uint64_t zh[kWideTerms];   // z >> 12: the tile-index part of each term's z
+  uint8_t nl[16], nh[16];    // pattern bits from the low / high nibble of (thread ^ x)
+  uint8_t kx[16];            // pattern bits from element k's bits 8..11, for k ^ (x >> 8)
   float2 tab[1 << kWideTerms];  // real D split as (hi, lo) floats: D = hi + lo to ~2^-48
 };
 
@@ -132,7 +139,8 @@ cudaError_t launch_hpsi_tiled(const void* psi, void* lam, int n, qf_dtype dt, in
                               double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s);
 // Tiled H|psi> for a real complex128 state and real D with double-single
 // multiply-adds on the FP32 pipe (same outputs as launch_hpsi_tiled).
-cudaError_t launch_hpsi_ds(const void* psi, void* lam, int n, int tb, const HClass* classes, int nclasses,
+// split: a scratch array of 2^n float2 receiving (hi, lo) of each real part.
+cudaError_t launch_hpsi_ds(const void* psi, void* lam, void* split, int n, const HClass* classes, int nclasses,
                            const HGroup* groups, const WChunkS* chunks, double* partials, unsigned* counter,
                            double* out, int nblocks, cudaStream_t s);
 // Reverse step: out[0] = Im <lam|P|psi> (stored units), then psi, lam <- exp(+i th P).

@@ -632,16 +632,28 @@ __device__ __forceinline__ void ds_mad(float& ah, float& al, float dh, float dl,
   ah = s;
 }
 
-template <int E>
-__global__ void __launch_bounds__(256) k_hpsi_ds(const double2* __restrict__ psi, double2* __restrict__ lam, int n,
+__global__ void __launch_bounds__(256) k_split_ds(const double2* __restrict__ psi, float2* __restrict__ out,
+                                                  uint64_t N) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const double v = psi[i].x;
+    const float h = __double2float_rn(v);
+    out[i] = make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+
+// Tiles of 2^12 amplitudes; thread t owns c = t + 256 k (k < 16).  For group
+// g with low X bits xl = xlo + 256 xhi the partner of element k is
+// (t ^ xlo) + 256 (k ^ xhi), and the sign-pattern index of a table is
+//   hp (tile part, uniform) ^ nl[(t^xlo) & 15] ^ nh[(t^xlo) >> 4] ^ kx[k].
+__global__ void __launch_bounds__(256) k_hpsi_ds(const double2* __restrict__ psi, const float2* __restrict__ split,
+                                                 double2* __restrict__ lam, int n,
                                                  const HClass* __restrict__ classes, int nclasses,
                                                  const HGroup* __restrict__ groups,
                                                  const WChunkS* __restrict__ chunks, double* partials,
                                                  unsigned* counter, double* out) {
-  constexpr int TB = (E == 1) ? 8 : (E == 2) ? 9 : (E == 4) ? 10 : (E == 8) ? 11 : 12;
-  constexpr int KB = TB - 8;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tile = reinterpret_cast<float2*>(smem_raw);
+  constexpr int TB = 12, E = 16;
+  __shared__ float2 tile[1 << TB];
   const unsigned tid = threadIdx.x;
   const uint64_t ntiles = 1ull << (n - TB);
   double acc_e = 0.0, acc_n = 0.0;
@@ -654,39 +666,25 @@ __global__ void __launch_bounds__(256) k_hpsi_ds(const double2* __restrict__ psi
       const uint64_t pt = t ^ C.xh;
       __syncthreads();
 #pragma unroll
-      for (int k = 0; k < E; ++k) {
-        const double v = psi[(pt << TB) + tid + 256u * k].x;
-        const float vh = __double2float_rn(v);
-        tile[tid + 256u * k] = make_float2(vh, __double2float_rn(v - (double)vh));
-      }
+      for (int k = 0; k < E; ++k) tile[tid + 256u * k] = split[(pt << TB) + tid + 256u * k];
       __syncthreads();
       for (int g = C.g0; g < C.g1; ++g) {
         const HGroup G = groups[g];
-        const unsigned xl = (unsigned)(G.x & ((1ull << TB) - 1ull));
-        const unsigned xlo = xl & 255u, xhi = xl >> 8;
+        const unsigned xlo = (unsigned)G.x & 255u;
+        const unsigned tx = tid ^ xlo;
         for (int c = 0; c < G.nchunk; ++c) {
           const WChunkS* W = chunks + G.chunk0 + c;
-          unsigned ith = 0, col[KB > 0 ? KB : 1];
+          unsigned ith = (unsigned)W->nl[tx & 15u] ^ (unsigned)W->nh[tx >> 4];
 #pragma unroll
-          for (int j = 0; j < (KB > 0 ? KB : 1); ++j) col[j] = 0;
-#pragma unroll
-          for (int q = 0; q < kWideTerms; ++q) {
-            const uint64_t z = W->z[q];
-            const unsigned hp = par64((z >> TB) & pt);
-            const unsigned tp = (unsigned)__popc((unsigned)z & 255u & (tid ^ xlo)) & 1u;
-            ith |= (hp ^ tp) << q;
-#pragma unroll
-            for (int j = 0; j < KB; ++j) col[j] |= (unsigned)((z >> (8 + j)) & 1ull) << q;
-          }
+          for (int q = 0; q < kWideTerms; ++q) ith ^= par64(W->zh[q] & pt) << q;
+          const uint4 kxw = *reinterpret_cast<const uint4*>(W->kx);
+          const unsigned kw[4] = {kxw.x, kxw.y, kxw.z, kxw.w};
+          const unsigned xhi = ((unsigned)G.x >> 8) & 15u;
 #pragma unroll
           for (int k = 0; k < E; ++k) {
-            unsigned idx = ith;
-            const unsigned kk = (unsigned)k ^ xhi;
-#pragma unroll
-            for (int j = 0; j < KB; ++j)
-              if ((kk >> j) & 1u) idx ^= col[j];
+            const unsigned idx = ith ^ ((kw[k >> 2] >> (8 * (k & 3))) & 255u);
             const float2 d = W->tab[idx];
-            const float2 v = tile[(tid ^ xlo) | (kk << 8)];
+            const float2 v = tile[tx | (((unsigned)k ^ xhi) << 8)];
             ds_mad(ah[k], al[k], d.x, d.y, v.x, v.y);
           }
         }
@@ -1242,37 +1240,25 @@ cudaError_t launch_hpsi_tiled(const void* psi, void* lam, int n, qf_dtype dt, in
   return e;
 }
 
-template <int E>
-static cudaError_t hpsi_ds_e(const void* psi, void* lam, int n, const HClass* classes, int nclasses,
-                             const HGroup* groups, const WChunkS* chunks, double* partials, unsigned* counter,
-                             double* out, int nblocks, cudaStream_t s) {
-  const size_t smem = sizeof(float2) * 256 * E;
-  const int tb = 8 + (E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4);
-  const uint64_t ntiles = 1ull << (n - tb);
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_ds<E>, 256, smem);
-  if (per_sm < 1) per_sm = 1;
-  uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
-  if (cap > (uint64_t)nblocks) cap = (uint64_t)nblocks;
-  const unsigned g = (unsigned)std::min<uint64_t>(ntiles, cap);
-  k_hpsi_ds<E><<<g, 256, smem, s>>>(static_cast<const double2*>(psi), static_cast<double2*>(lam), n, classes,
-                                    nclasses, groups, chunks, partials, counter, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_hpsi_ds(const void* psi, void* lam, int n, int tb, const HClass* classes, int nclasses,
+cudaError_t launch_hpsi_ds(const void* psi, void* lam, void* split, int n, const HClass* classes, int nclasses,
                            const HGroup* groups, const WChunkS* chunks, double* partials, unsigned* counter,
                            double* out, int nblocks, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_HPSI, s);
-  cudaError_t e;
-  switch (tb) {
-    case 10: e = hpsi_ds_e<4>(psi, lam, n, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s); break;
-    case 11: e = hpsi_ds_e<8>(psi, lam, n, classes, nclasses, groups, chunks, partials, counter, out, nblocks, s); break;
-    default: e = cudaErrorInvalidValue;
-  }
+  const uint64_t N = 1ull << n;
+  k_split_ds<<<grid_for(N, 8), 256, 0, s>>>(static_cast<const double2*>(psi), static_cast<float2*>(split), N);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hpsi_ds, 256, 0);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
+  if (cap > (uint64_t)nblocks) cap = (uint64_t)nblocks;
+  const unsigned g = (unsigned)std::min<uint64_t>(1ull << (n - 12), cap);
+  k_hpsi_ds<<<g, 256, 0, s>>>(static_cast<const double2*>(psi), static_cast<const float2*>(split),
+                              static_cast<double2*>(lam), n, classes, nclasses, groups, chunks, partials, counter,
+                              out);
   prof_post(prof_slot_, s);
   count_launch();
-  return e;
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotArgs& a, double* partials,
