@@ -329,6 +329,8 @@ def run_gpu(args, rank, world, local, pg):
         if args.dtype == "c128":
             out["c64"] = c64_leg(w, args, value, float(energies[-1]), g)
             out["hpsi_fp64_mode"] = fp64_mode_leg(w, args, value, float(energies[-1]), g)
+        out["serving"] = serving_leg(args)
+        out["sweep28"] = sweep28_leg()
         t_eval, sample = oracle_sample_ucc(w)
         out["cpu_baseline"] = {"value": 1.0 / t_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
                                "sample": sample}
@@ -414,6 +416,107 @@ def fp64_mode_leg(w, args, value_ds, e_ds, g_ds):
     st.close()
     return {"value": v, "unit": "evals/s", "default_speedup": value_ds / v,
             "default_energy_diff": abs(e - e_ds), "default_grad_max_diff": float(np.abs(g - g_ds).max())}
+
+
+def serving_systems(qubit_counts=(10, 12, 14, 16, 18, 20, 22)):
+    from paper_2108_04413_gb300 import prep
+    from paper_2108_04413_gb300.serving import System
+    from workloads import integrals
+
+    systems, npar = {}, {}
+    for n in qubit_counts:
+        no, ne = n // 2, n // 2
+        h, g = integrals(no, 100 + n)
+        A, exs = prep.uccsd_ansatz(no, ne)
+        key = f"n{n}"
+        systems[key] = System(key, n, (1 << ne) - 1, A, prep.molecular_hamiltonian(h, g))
+        npar[key] = len(exs)
+    return systems, npar
+
+
+def serving_leg(args, count: int = 240, rate: float = 200.0):
+    """Poisson stream (seeded, `rate` requests/s) of energy+gradient requests with
+    qubit counts uniform in {10,...,22}, t ~ N(0, 0.1): the complex64 continuous-
+    batching server (4 workers, resident states, HBM-budget admission) against
+    one-at-a-time complex128 solves of the same stream (one worker)."""
+    from paper_2108_04413_gb300.serving import GpuExecutor, Request, Server, latency_stats, replay
+    from workloads import poisson_arrivals
+
+    systems, npar = serving_systems()
+    keys = sorted(systems)
+    rng = np.random.default_rng(4)
+    arrivals = poisson_arrivals(rate, count, 4)
+    picks = rng.integers(0, len(keys), count)
+    ts = [rng.normal(0.0, 0.1, npar[keys[k]]) for k in picks]
+
+    def stream():
+        return [Request(i, keys[picks[i]], ts[i], float(arrivals[i])) for i in range(count)]
+
+    out = {"requests": count, "arrival_rate_rps": rate, "qubits": "uniform in {10,...,22}"}
+    for label, dtype, workers in (("continuous_batching_c64", "c64", 4), ("one_at_a_time_c128", "c128", 1)):
+        srv = Server(systems, GpuExecutor(dtype), workers=workers, hbm_budget=32 << 30, dtype=dtype)
+        replay(srv, [Request(-1 - i, k, np.zeros(npar[k]), 0.0) for i, k in enumerate(keys)], realtime=False)
+        srv.done.clear()  # warm-up: one request per system plans and allocates its state
+        srv.t0 = srv.clock()
+        done = replay(srv, stream())
+        srv.close()
+        st = latency_stats(done)
+        st["max_concurrent"] = srv.max_concurrent
+        out[label] = st
+    b = out["one_at_a_time_c128"]
+    c = out["continuous_batching_c64"]
+    out["throughput_multiple"] = c["throughput_rps"] / b["throughput_rps"] if b["throughput_rps"] else None
+    return out
+
+
+def sweep28_leg(n: int = 28, n_rot: int = 500, n_terms: int = 1000):
+    """28-qubit random Pauli exponentials (weight 2..8, theta ~ U(-pi, pi)):
+    fused circuit vs one launch per rotation, complex128 and complex64, and the
+    grouped expectation of a random Hermitian sum (first n_terms of 20000)."""
+    import torch
+
+    from paper_2108_04413_gb300 import prep, qf
+
+    R = prep.random_circuit(n, n_rot, 3)
+    T = prep.random_hamiltonian(n, 20000, 3)[:n_terms]
+    N = 1 << n
+    det = (1 << 14) - 1
+    out = {"qubits": n, "rotations": n_rot}
+    for dtype in ("c128", "c64"):
+        S = 16 if dtype == "c128" else 8
+        stream = torch.cuda.Stream()
+        st = qf.State(n, dtype, stream=stream)
+        res = {}
+        for label in ("fused", "unfused"):
+            def run():
+                st.set_basis(det)
+                if label == "fused":
+                    st.apply_circuit(R)
+                else:
+                    for r in R:
+                        st.apply_pauli_exp(int(r["x"]), int(r["z"]), float(r["theta"]))
+            run()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s_ = e0.elapsed_time(e1) / 1e3
+            res[label] = {"ms": s_ * 1e3, "rotations_amplitudes_per_s": n_rot * N / s_}
+        # unfused: every rotation is one read+write sweep of the state
+        res["unfused"]["hbm_gbs"] = n_rot * 2 * N * S / (res["unfused"]["ms"] / 1e3) / 1e9
+        res["unfused"]["frac_of_measured_hbm"] = res["unfused"]["hbm_gbs"] / peaks()["hbm_gbs"]
+        st.expectation(T)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.expectation(T)
+        dt = time.perf_counter() - t0
+        res["expectation"] = {"terms": n_terms, "ms": dt * 1e3, "terms_amplitudes_per_s": n_terms * N / dt}
+        out[dtype] = res
+        st.close()
+    return out
 
 
 def c64_leg(w, args, value128, e128, g128):

@@ -33,6 +33,7 @@ qf_status fail(qf_status s, const std::string& msg) {
   } while (0)
 
 int popc(uint64_t v) { return __builtin_popcountll(v); }
+constexpr uint64_t kEvenMask = 0x5555555555555555ull;  // alpha spin orbitals (even qubits)
 int hibit(uint64_t v) { return v ? 63 - __builtin_clzll(v) : -1; }
 
 struct ExpPlan {
@@ -46,6 +47,8 @@ struct ExpPlan {
   qf::WChunk* d_wchunks = nullptr;
   qf::WChunkF* d_wchunks_f = nullptr;
   qf::WChunkS* d_wchunks_s = nullptr;  // real D as (hi, lo) floats for double-single H|psi>
+  qf::SecGroup* d_secgroups = nullptr;  // groups that can connect two members of a sector
+  int nsecgroups = 0;
   qf::HClass* d_classes[qf::kClassTbN] = {};  // classes for tile bits 10, 11, 12
   int nclasses[qf::kClassTbN] = {};
   bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
@@ -59,6 +62,7 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_wchunks);
   cudaFree(p.d_wchunks_f);
   cudaFree(p.d_wchunks_s);
+  cudaFree(p.d_secgroups);
   for (int v = 0; v < qf::kClassTbN; ++v) cudaFree(p.d_classes[v]);
   p = ExpPlan();
 }
@@ -89,6 +93,15 @@ struct qf_state {
   // is kept by real sparse composites and by rotations with x != 0 and an odd
   // number of Y letters (their phases map real amplitudes to real ones).
   bool real = true;
+  // Numbers of occupied even (alpha) and odd (beta) qubits when every nonzero
+  // amplitude has them (set by qf_set_basis, kept by sector-preserving blocks);
+  // -1 when unknown.
+  int sec_a = -1, sec_b = -1;
+  qf::SecBlk* d_secblk = nullptr;  // sector block descriptors (forward, then reverse)
+  size_t secblk_cap = 0;
+  double* d_sec_partial = nullptr;  // reverse-sweep overlaps per block and CTA
+  size_t sec_partial_cap = 0;
+  unsigned* d_bar = nullptr;        // grid barrier words
   int hpsi_mode = QF_HPSI_DS;
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
@@ -292,6 +305,15 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     }
     hg.push_back(g);
   }
+  // sector groups: a group flips popc(x & even) even qubits; it links two members of
+  // one sector only when that count (and the odd one) is even
+  std::vector<qf::SecGroup> sg;
+  for (const qf::ExpGroup& g : groups) {
+    const int xe = popc(g.x & kEvenMask), xo = popc(g.x & ~kEvenMask);
+    if ((xe & 1) || (xo & 1)) continue;
+    sg.push_back(qf::SecGroup{g.x, xe, xo, g.chunk0, g.nchunk});
+  }
+  p.nsecgroups = (int)sg.size();
   std::vector<qf::HClass> cls[qf::kClassTbN];
   for (int v = 0; v < qf::kClassTbN; ++v) {
     const int tb = qf::kClassTb0 + v;
@@ -330,6 +352,15 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     }
     QF_CUDA(cudaMemcpyAsync(p.d_hgroups, hg.data(), hg.size() * sizeof(qf::HGroup), cudaMemcpyHostToDevice,
                             st->stream));
+    if (!sg.empty()) {
+      if (cudaMalloc(&p.d_secgroups, sg.size() * sizeof(qf::SecGroup)) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
+      }
+      QF_CUDA(cudaMemcpyAsync(p.d_secgroups, sg.data(), sg.size() * sizeof(qf::SecGroup), cudaMemcpyHostToDevice,
+                              st->stream));
+    }
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks, wc.data(), wc.size() * sizeof(qf::WChunk), cudaMemcpyHostToDevice,
                             st->stream));
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks_f, wf.data(), wf.size() * sizeof(qf::WChunkF), cudaMemcpyHostToDevice,
@@ -520,6 +551,113 @@ void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
   }
 }
 
+uint32_t binom(int m, int k) {
+  if (k < 0 || k > m) return 0;
+  uint64_t c = 1;
+  for (int j = 1; j <= k; ++j) c = c * (uint64_t)(m - k + j) / (uint64_t)j;
+  return (uint32_t)c;
+}
+
+// A two-row sparse block as a sector block for a state with (na, nb) occupied
+// even/odd qubits.  Requires a real composite, two active patterns with equal
+// even and odd occupation (so the block maps the sector onto itself) and, for
+// the reverse sweep, a purely imaginary generator.
+bool to_secblk(const qf::SparseArgs& a, int n, int na, int nb, bool need_q, qf::SecBlk* o) {
+  if (a.nr != 2 || n > 2 * qf::kSecMaxPos) return false;
+  const uint64_t p0 = a.pat[0], p1 = a.pat[1];
+  const int e0 = popc(p0 & kEvenMask), o0 = popc(p0 & ~kEvenMask);
+  if (e0 != popc(p1 & kEvenMask) || o0 != popc(p1 & ~kEvenMask)) return false;
+  const int ncls = 1 << a.nzc;
+  for (int c = 0; c < ncls; ++c)
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        if (a.M[c][i][j].y != 0.0) return false;
+        if (need_q && a.Q[c][i][j].x != 0.0) return false;
+      }
+  uint64_t U = 0;
+  for (int i = 0; i < a.u; ++i) U |= 1ull << a.supp[i];
+  std::memset(o, 0, sizeof(*o));
+  for (int q = 0; q < n; ++q) {
+    if ((U >> q) & 1) continue;
+    if ((q & 1) == 0)
+      o->epos[o->ne++] = (uint8_t)q;
+    else
+      o->opos[o->no++] = (uint8_t)q;
+  }
+  o->ke = na - e0;
+  o->ko = nb - o0;
+  if (o->ke < 0 || o->ke > o->ne || o->ko < 0 || o->ko > o->no) return false;
+  o->cnt_e = binom(o->ne, o->ke);
+  o->cnt_o = binom(o->no, o->ko);
+  o->pat[0] = p0;
+  o->pat[1] = p1;
+  o->zc[0] = a.zc[0];
+  o->zc[1] = a.zc[1];
+  o->nzc = a.nzc;
+  for (int c = 0; c < qf::kSparseMaxCls; ++c)
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        const int cc = c < ncls ? c : 0;
+        o->m[c][i][j] = a.M[cc][i][j].x;
+        o->q[c][i][j] = need_q ? a.Q[cc][i][j].y : 0.0;
+      }
+  return true;
+}
+
+qf::SecSpace sector_space(int n, int na, int nb) {
+  qf::SecSpace sp{};
+  for (int q = 0; q < n; ++q) {
+    if ((q & 1) == 0)
+      sp.epos[sp.ne++] = (uint8_t)q;
+    else
+      sp.opos[sp.no++] = (uint8_t)q;
+  }
+  sp.ke = na;
+  sp.ko = nb;
+  sp.cnt_e = binom(sp.ne, na);
+  sp.cnt_o = binom(sp.no, nb);
+  return sp;
+}
+
+qf_status ensure_sector_buffers(qf_state* st, size_t nblk, size_t partials) {
+  if (nblk > st->secblk_cap) {
+    cudaFree(st->d_secblk);
+    st->d_secblk = nullptr;
+    st->secblk_cap = 0;
+    if (cudaMalloc(&st->d_secblk, nblk * sizeof(qf::SecBlk)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QF_ENOMEM, "cudaMalloc(sector blocks) failed");
+    }
+    st->secblk_cap = nblk;
+  }
+  if (partials > st->sec_partial_cap) {
+    cudaFree(st->d_sec_partial);
+    st->d_sec_partial = nullptr;
+    st->sec_partial_cap = 0;
+    if (cudaMalloc(&st->d_sec_partial, partials * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QF_ENOMEM, "cudaMalloc(sector partials) failed");
+    }
+    st->sec_partial_cap = partials;
+  }
+  if (!st->d_bar) {
+    if (cudaMalloc(&st->d_bar, 4 * sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QF_ENOMEM, "cudaMalloc(barrier) failed");
+    }
+  }
+  return QF_OK;
+}
+
+// Reads the sweep's error flag (grid barrier timeout) after the stream synchronised.
+qf_status check_barrier(qf_state* st) {
+  unsigned flags[3] = {0, 0, 0};
+  QF_CUDA(cudaMemcpyAsync(flags, st->d_bar, sizeof(flags), cudaMemcpyDeviceToHost, st->stream));
+  QF_CUDA(cudaStreamSynchronize(st->stream));
+  if (flags[2]) return fail(QF_ETIMEOUT, "sector sweep: grid barrier wait exceeded its limit");
+  return QF_OK;
+}
+
 // Length of the run starting at i that can form one sparse block.
 int sparse_run(const RotIn* r, size_t i, size_t nrot, const int32_t* params) {
   const uint64_t x = r[i].x;
@@ -570,18 +708,45 @@ void build_tile(qf_state* st, const RotIn* r, size_t i, size_t j, uint64_t uni, 
   }
 }
 
+qf_status flush_sector(qf_state* st, std::vector<qf::SecBlk>& pend) {
+  if (pend.empty()) return QF_OK;
+  const int grid = qf::sector_sweep_grid(st->dt, false, true);
+  qf_status bs = ensure_sector_buffers(st, pend.size(), 1);
+  if (bs != QF_OK) return bs;
+  QF_CUDA(cudaMemcpyAsync(st->d_secblk, pend.data(), pend.size() * sizeof(qf::SecBlk), cudaMemcpyHostToDevice,
+                          st->stream));
+  QF_CUDA(qf::launch_sector_sweep(st->psi, nullptr, st->dt, false, st->real, st->d_secblk, (int)pend.size(),
+                                  st->d_bar, st->d_sec_partial, nullptr, grid, st->stream));
+  QF_CUDA(cudaStreamSynchronize(st->stream));  // the descriptor buffer is reused by the next flush
+  pend.clear();
+  return check_barrier(st);
+}
+
 qf_status apply_rotations(qf_state* st, const RotIn* r, size_t nrot) {
   const int n = st->n;
   const int umax = std::min(n, 8);
+  std::vector<qf::SecBlk> pend;  // sector blocks waiting for one sweep launch
   size_t i = 0;
   while (i < nrot) {
     const int run = sparse_run(r, i, nrot, nullptr);
+    if (run >= 2 && st->sec_a >= 0 && st->real) {
+      qf::SparseArgs sa;
+      qf::SecBlk sb;
+      if (build_sparse(r + i, run, n, false, false, &sa) && to_secblk(sa, n, st->sec_a, st->sec_b, false, &sb)) {
+        pend.push_back(sb);
+        i += run;
+        continue;
+      }
+    }
+    qf_status fs = flush_sector(st, pend);
+    if (fs != QF_OK) return fs;
     if (run >= 2) {
       qf::SparseArgs sa;
       if (build_sparse(r + i, run, n, false, false, &sa)) {
         const bool rm = qf::sparse_m_real(sa);
         QF_CUDA(qf::launch_sparse(st->psi, n, st->dt, sa, st->real && rm, st->stream));
         st->real = st->real && rm;
+        st->sec_a = st->sec_b = -1;
         i += run;
         continue;
       }
@@ -600,15 +765,17 @@ qf_status apply_rotations(qf_state* st, const RotIn* r, size_t nrot) {
       build_tile(st, r, i, j, uni, &ta);
       QF_CUDA(qf::launch_tile(st->psi, n, st->dt, ta, st->stream));
       for (size_t k = i; k < j; ++k) st->real = st->real && keeps_real(r[k].x, r[k].z);
+      st->sec_a = st->sec_b = -1;
       i = j;
     } else {
       qf::RotArgs a = rot_args(st->dt, &st->scale, r[i].x, r[i].z, r[i].th);
       QF_CUDA(qf::launch_rot(st->psi, n, st->dt, a, st->stream));
       st->real = st->real && keeps_real(r[i].x, r[i].z);
+      if (r[i].x != 0) st->sec_a = st->sec_b = -1;  // a diagonal rotation keeps every occupation
       ++i;
     }
   }
-  return QF_OK;
+  return flush_sector(st, pend);
 }
 
 }  // namespace
@@ -672,6 +839,9 @@ qf_status qf_state_destroy(qf_state* st) {
   if (st->own_psi) cudaFree(st->psi);
   cudaFree(st->lam);
   cudaFree(st->split);
+  cudaFree(st->d_secblk);
+  cudaFree(st->d_sec_partial);
+  cudaFree(st->d_bar);
   cudaFree(st->d_partials);
   cudaFree(st->d_counter);
   cudaFree(st->d_out);
@@ -685,6 +855,8 @@ qf_status qf_set_basis(qf_state* st, uint64_t det) {
   if (st->n < 64 && (det >> st->n)) return fail(QF_EINVAL, "determinant has a bit at or above the qubit count");
   st->scale = 1.0;
   st->real = true;
+  st->sec_a = popc(det & kEvenMask);
+  st->sec_b = popc(det & ~kEvenMask);
   QF_CUDA(qf::launch_zero_and_set(st->psi, st->n, st->dt, det, st->stream));
   return QF_OK;
 }
@@ -697,6 +869,7 @@ qf_status qf_apply_pauli_exp(qf_state* st, uint64_t x, uint64_t z, double theta)
   qf::RotArgs a = rot_args(st->dt, &st->scale, x, z, theta);
   QF_CUDA(qf::launch_rot(st->psi, st->n, st->dt, a, st->stream));
   st->real = st->real && keeps_real(x, z);
+  if (x != 0) st->sec_a = st->sec_b = -1;
   return QF_OK;
 }
 
@@ -730,8 +903,16 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
   qf_status ps = get_plan(st, terms, n_terms, &p);
   if (ps != QF_OK) return ps;
   const int nb = qf::reduce_blocks(st->n, st->dt);
-  QF_CUDA(qf::launch_expect(st->psi, st->n, st->dt, p->d_groups, p->ngroups, p->d_echunks, st->d_partials,
-                            st->d_counter, st->d_out, nb, st->stream));
+  if (st->sec_a >= 0 && st->n <= 2 * qf::kSecMaxPos) {
+    // every nonzero amplitude is in one (alpha, beta) sector: sum over its members only
+    const qf::SecSpace sp = sector_space(st->n, st->sec_a, st->sec_b);
+    QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, p->d_secgroups,
+                                   p->nsecgroups, p->d_hchunks, st->d_partials, st->d_counter, st->d_out, nb,
+                                   st->stream));
+  } else {
+    QF_CUDA(qf::launch_expect(st->psi, st->n, st->dt, p->d_groups, p->ngroups, p->d_echunks, st->d_partials,
+                              st->d_counter, st->d_out, nb, st->stream));
+  }
   QF_CUDA(cudaMemcpyAsync(st->h_out, st->d_out, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));
   *re = st->h_out[0] * st->scale * st->scale;
@@ -806,8 +987,59 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     if (ps != QF_OK) return ps;
   }
   const int n = st->n;
+  // Sector path: every block is a two-row excitation that keeps the reference's
+  // numbers of occupied even and odd qubits, so the whole evaluation runs on the
+  // members of that sector (five launches).
+  {
+    const int na = popc(det & kEvenMask), nbeta = popc(det & ~kEvenMask);
+    std::vector<qf::SecBlk> sec(2 * blocks.size());
+    bool ok = !blocks.empty() && n <= 2 * qf::kSecMaxPos;
+    for (size_t bi = 0; ok && bi < blocks.size(); ++bi)
+      ok = blocks[bi].sparse && to_secblk(blocks[bi].fwd, n, na, nbeta, false, &sec[bi]) &&
+           to_secblk(blocks[bi].inv, n, na, nbeta, true, &sec[blocks.size() + bi]);
+    if (ok) {
+      const size_t nblk = blocks.size();
+      const bool lreal = !p || !p->has_odd;
+      const int grid_f = qf::sector_sweep_grid(st->dt, false, true);
+      const int grid_r = qf::sector_sweep_grid(st->dt, true, lreal);
+      qf_status bs = ensure_sector_buffers(st, 2 * nblk, nblk * (size_t)grid_r);
+      if (bs != QF_OK) return bs;
+      st->scale = 1.0;
+      st->real = true;
+      st->sec_a = na;
+      st->sec_b = nbeta;
+      QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
+      QF_CUDA(cudaMemcpyAsync(st->d_secblk, sec.data(), sec.size() * sizeof(qf::SecBlk), cudaMemcpyHostToDevice,
+                              st->stream));
+      QF_CUDA(qf::launch_sector_sweep(st->psi, nullptr, st->dt, false, true, st->d_secblk, (int)nblk, st->d_bar,
+                                      st->d_sec_partial, nullptr, grid_f, st->stream));
+      double* d_e = st->d_out + nblk;
+      const int nbk = qf::reduce_blocks(n, st->dt);
+      if (p) {
+        const qf::SecSpace sp = sector_space(n, na, nbeta);
+        QF_CUDA(qf::launch_sector_hpsi(st->psi, st->lam, st->dt, lreal, sp, p->d_secgroups, p->nsecgroups,
+                                       p->d_hchunks, st->d_partials, st->d_counter, d_e, nbk, st->stream));
+        QF_CUDA(qf::launch_sector_sweep(st->psi, st->lam, st->dt, true, lreal, st->d_secblk + nblk, (int)nblk,
+                                        st->d_bar, st->d_sec_partial, st->d_out, grid_r, st->stream));
+      } else {
+        QF_CUDA(cudaMemsetAsync(st->d_out, 0, (nblk + 2) * sizeof(double), st->stream));
+      }
+      QF_CUDA(cudaMemcpyAsync(st->h_out, st->d_out, (nblk + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                              st->stream));
+      QF_CUDA(cudaStreamSynchronize(st->stream));
+      qf_status bc = check_barrier(st);
+      if (bc != QF_OK) return bc;
+      double nrm = p ? st->h_out[nblk + 1] : 1.0;
+      if (!(nrm > 0.0)) nrm = 1.0;
+      *energy = st->h_out[nblk] / nrm;
+      for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
+      for (size_t bi = 0; bi < nblk; ++bi) grad[par[blocks[bi].i]] += 2.0 * st->h_out[bi] / nrm;
+      return QF_OK;
+    }
+  }
   st->scale = 1.0;
   st->real = true;
+  st->sec_a = st->sec_b = -1;
   QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
   for (const Blk& b : blocks) {
     if (b.sparse) {
@@ -914,6 +1146,7 @@ qf_status qf_state_copy_from_host(qf_state* st, const void* host, size_t bytes) 
   QF_CUDA(cudaMemcpyAsync(st->psi, host, bytes, cudaMemcpyHostToDevice, st->stream));
   st->scale = 1.0;
   st->real = false;
+  st->sec_a = st->sec_b = -1;
   return QF_OK;
 }
 

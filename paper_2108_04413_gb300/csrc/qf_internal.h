@@ -115,6 +115,28 @@ struct WChunkS {
   float2 tab[1 << kWideTerms];  // real D split as (hi, lo) floats: D = hi + lo to ~2^-48
 };
 
+// Sector-restricted kernels (qf_sector.cu): states with fixed numbers of
+// occupied even (alpha) and odd (beta) qubits.
+constexpr int kSecMaxPos = 17;  // positions per parity (34 qubits)
+struct SecBlk {                 // one two-row excitation block
+  uint64_t pat[2];              // global offsets of the two active support patterns
+  uint64_t zc[2];               // outside-Z class masks
+  int nzc, ne, no, ke, ko;      // outside even/odd positions and electrons to place there
+  uint32_t cnt_e, cnt_o;        // C(ne, ke), C(no, ko)
+  uint8_t epos[kSecMaxPos], opos[kSecMaxPos];
+  double m[kSparseMaxCls][2][2];  // composite minus identity (real), per sign class
+  double q[kSparseMaxCls][2][2];  // Qi with generator Q = i Qi (reverse sweep)
+};
+struct SecSpace {               // all determinants of one sector
+  uint32_t cnt_e, cnt_o;
+  int ne, no, ke, ko;
+  uint8_t epos[kSecMaxPos], opos[kSecMaxPos];
+};
+struct SecGroup {               // X group with its even/odd flip counts
+  uint64_t x;
+  int xe, xo, chunk0, nchunk;
+};
+
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s);
 cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s);
@@ -151,7 +173,20 @@ cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotAr
 cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, bool realst,
                               double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s);
 
+// Sector sweep over nblk blocks in one cooperative launch (reverse when adj:
+// out[b] = Im <lam|Q_b|psi> of block b, from partial[nblk * grid]).  bar: 3
+// device words.  grid from sector_sweep_grid.
+int sector_sweep_grid(qf_dtype dt, bool adj, bool realst);
+cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const SecBlk* blks,
+                                int nblk, unsigned* bar, double* partial, double* out, int grid, cudaStream_t s);
+// lam = H psi on the sector (lam may be NULL), out[0] = <psi|H psi>, out[1] = <psi|psi>.
+cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
+                               const SecGroup* groups, int ngroups, const ExpChunk* chunks, double* partials,
+                               unsigned* counter, double* out, int nblocks, cudaStream_t s);
+
 int reduce_blocks(int n, qf_dtype dt);  // grid size used by the reducing kernels
+int prof_pre(unsigned kind, cudaStream_t s);  // kernel timing hooks (see qf_profile_begin)
+void prof_post(int slot, cudaStream_t s);
 void count_launch();
 int profile_begin(unsigned mask);
 cudaError_t profile_read(unsigned mask, uint64_t* launches, double* total_ms);

@@ -918,6 +918,10 @@ cudaEvent_t pool_event(size_t i) {
   return t_ev_pool[i];
 }
 
+}  // namespace
+
+void count_launch() { ++t_launches; }
+
 // Records the start event of a launch of `kind` (if profiled); returns a slot.
 int prof_pre(unsigned kind, cudaStream_t s) {
   if (!(t_prof_mask & kind)) return -1;
@@ -931,10 +935,6 @@ int prof_pre(unsigned kind, cudaStream_t s) {
 void prof_post(int slot, cudaStream_t s) {
   if (slot >= 0) cudaEventRecord(t_prof[slot].b, s);
 }
-
-}  // namespace
-
-void count_launch() { ++t_launches; }
 
 int profile_begin(unsigned mask) {
   t_prof.clear();

@@ -136,6 +136,52 @@ def test_ucc_energy_c64(cfg_id):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_ucc_general_sparse_path_unknown_sector(dtype):
+    """A determinant loaded from the host has no tracked sector, so the dUCC
+    blocks run on the general sparse kernels; same state and energy as the oracle."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], dtype)
+    st.from_numpy(pauli.basis_state(cfg["n_qubits"], det))
+    st.apply_circuit(prep.bind_thetas(A, t))
+    e, _ = st.expectation(T)
+    ref = fermion.ucc_state(cfg["n_orb"], cfg["n_el"], t, exs)
+    e_ref = np.vdot(ref, fermion.hamiltonian_apply(ref, cfg["n_orb"], h, g)).real
+    if dtype == "c128":
+        assert np.abs(st.to_numpy() - ref).max() < TOL_AMP_C128
+        assert abs(e - e_ref) < TOL_E_C128
+    else:
+        assert abs(e - e_ref) < TOL_E_C64
+
+
+def test_energy_grad_particle_changing_blocks():
+    """Pair-creation blocks kappa = a+_a a+_b - h.c. are sparse but change the
+    particle number, so they take the general sparse adjoint path."""
+    n = 10
+    rows = []
+    pairs = [(0, 5), (2, 7), (1, 3), (4, 9), (6, 8)]
+    for mu, (a, b) in enumerate(pairs):
+        k = fermion.jw_product(n, [("+", a), ("+", b)])
+        for s_, c in fermion.jw_product(n, [("-", b), ("-", a)]).items():
+            k[s_] = k.get(s_, 0) - c
+        for s_, c in sorted(k.items()):
+            if abs(c) > 1e-14:
+                x, z = fermion.letters_to_masks(s_)
+                rows.append((x, z, -(c / 1j).real, mu))
+    A = qf.as_arots([r[0] for r in rows], [r[1] for r in rows], [r[2] for r in rows], [r[3] for r in rows])
+    t = np.array([0.3, -0.2, 0.5, 0.1, -0.4])
+    rng = np.random.default_rng(3)
+    T = qf.as_terms(rng.integers(0, 1 << n, 80), rng.integers(0, 1 << n, 80), rng.normal(size=80))
+    det = 0b0000110011
+    st = qf.State(n, "c128")
+    e, grad = st.energy_grad(det, A, t, T)
+    arots = list(zip(A["x"], A["z"], A["coeff"], A["param"]))
+    e_ref, g_ref, _ = pauli.adjoint_gradient(n, det, arots, t, _terms_list(T))
+    assert abs(e - e_ref) < TOL_E_C128
+    assert np.abs(grad - g_ref).max() < 1e-10
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_expectation_random_terms_mixed(dtype):
     """Duplicated terms, x = 0 terms, odd and even Y counts, many groups."""
     n = 11
