@@ -92,6 +92,24 @@ def group_stats(terms, n):
     return out
 
 
+def sector_pairs(terms, n: int, na: int, nb: int):
+    """Connected (sector member c, X group g) pairs of the sector H|psi>: group x
+    links c to c ^ x inside the sector iff x flips as many occupied as empty even
+    qubits of c, and likewise odd ones.  Counted in closed form per group."""
+    from math import comb
+
+    ne, no = (n + 1) // 2, n // 2
+    ev = int(sum(1 << q for q in range(0, n, 2)))
+    total = 0
+    for x in np.unique(terms["x"]):
+        x = int(x)
+        xe, xo = bin(x & ev).count("1"), bin(x & ~ev).count("1")
+        if xe % 2 or xo % 2:
+            continue
+        total += (comb(xe, xe // 2) * comb(ne - xe, na - xe // 2) * comb(xo, xo // 2) * comb(no - xo, nb - xo // 2))
+    return total, comb(ne, na) * comb(no, nb)
+
+
 def hpsi_flops(stats, n, real: bool):
     """Algorithmic FP64 flops of one H|psi> over the grouped Pauli sum: one
     multiply-add D_g(b) * psi[b] per (X group, amplitude) -- 2 flops when the
@@ -295,6 +313,42 @@ def run_gpu(args, rank, world, local, pg):
     dom = max(per_kind.items(), key=lambda kv: kv[1]["ms"])[0]
     stats = group_stats(w["terms"], n)
     roof = roofline_for(dom, per_kind[dom], w, stats, n, S, pk, args.dtype)
+    if dom in ("sparse", "adj_sparse"):
+        # sector sweeps: every excitation moves its two active amplitudes of each
+        # sector member pair once (read + write), for psi (and lambda in reverse)
+        from math import comb
+
+        ev = int(sum(1 << q for q in range(0, n, 2)))
+        na = bin(w["det"] & ev).count("1")
+        nb_ = bin(w["det"]).count("1") - na
+        ne, no = (n + 1) // 2, n // 2
+        items = 0
+        for occ, vir in w["exs"]:
+            sup = list(occ) + list(vir)
+            ea = sum(1 for q in occ if q % 2 == 0)
+            eb = len(occ) - ea
+            ce = sum(1 for q in sup if q % 2 == 0)
+            items += comb(ne - ce, na - ea) * comb(no - (len(sup) - ce), nb_ - eb)
+        nst = 2 if dom == "adj_sparse" else 1
+        by = items * 2 * 2 * nst * S
+        avg_s = per_kind[dom]["ms"] / per_kind[dom]["launches"] / 1e3
+        roof = {"kernel": "k_sector_sweep (" + ("reverse" if nst == 2 else "forward") + ")", "bound": "hbm",
+                "achieved": by / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": by / avg_s / 1e9 / pk["hbm_gbs"], "traffic": None,
+                "algorithmic": (f"{by:.4g} B per launch: {items} (member, excitation) items x 2 amplitudes x "
+                                f"read+write x {nst} state(s) x {S} B"),
+                "note": "one persistent launch over all excitations; time is set by the grid-barrier chain"}
+    if dom == "hpsi":
+        # the dUCC state stays in one (alpha, beta) sector, where H|psi> runs on members only
+        na = bin(w["det"] & int(sum(1 << q for q in range(0, n, 2)))).count("1")
+        pairs, members = sector_pairs(w["terms"], n, na, bin(w["det"]).count("1") - na)
+        avg_s = per_kind[dom]["ms"] / per_kind[dom]["launches"] / 1e3
+        fl = 2 * pairs + 4 * members
+        roof = {"kernel": "k_sector_hpsi", "bound": "alu", "achieved": fl / avg_s / 1e12, "peak": pk["fp64_tflops"],
+                "unit": "TFLOP/s", "frac": fl / avg_s / 1e12 / pk["fp64_tflops"], "traffic": None,
+                "algorithmic": (f"{fl:.4g} FP64 flop per launch: one multiply-add per connected (sector member, "
+                                f"X group) pair ({pairs} pairs, {members} members)"),
+                "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock (derived)"}
 
     out = {
         "metric": "energy+grad evals/s",

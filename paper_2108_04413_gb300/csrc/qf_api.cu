@@ -49,6 +49,11 @@ struct ExpPlan {
   qf::WChunkS* d_wchunks_s = nullptr;  // real D as (hi, lo) floats for double-single H|psi>
   qf::SecGroup* d_secgroups = nullptr;  // groups that can connect two members of a sector
   int nsecgroups = 0;
+  qf::SecGroup* d_seclarge = nullptr;   // those flipping more than four qubits
+  int nseclarge = 0;
+  int* d_rank2 = nullptr;               // group index by rank of a 2-set of flipped qubits
+  int* d_rank4 = nullptr;               // ... of a 4-set
+  int sec_diag = -1;
   qf::HClass* d_classes[qf::kClassTbN] = {};  // classes for tile bits 10, 11, 12
   int nclasses[qf::kClassTbN] = {};
   bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
@@ -63,6 +68,9 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_wchunks_f);
   cudaFree(p.d_wchunks_s);
   cudaFree(p.d_secgroups);
+  cudaFree(p.d_seclarge);
+  cudaFree(p.d_rank2);
+  cudaFree(p.d_rank4);
   for (int v = 0; v < qf::kClassTbN; ++v) cudaFree(p.d_classes[v]);
   p = ExpPlan();
 }
@@ -231,6 +239,8 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
         }
         ce.tab[pat] = make_double2(ex, ey);
         ch.tab[pat] = make_double2(hx, hy);
+        ce.ftab[pat] = make_float2((float)ex, (float)ey);
+        ch.ftab[pat] = make_float2((float)hx, (float)hy);
       }
       for (int t = 0; t < cnt; ++t) {
         const qf_term& T = terms[idx[k + t]];
@@ -314,6 +324,33 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     sg.push_back(qf::SecGroup{g.x, xe, xo, g.chunk0, g.nchunk});
   }
   p.nsecgroups = (int)sg.size();
+  // rank tables: colex rank of the sorted flip set, sum_i C(p_i, i + 1)
+  const int nq = st->n;
+  auto bin = [](int m, int k) -> int64_t {
+    if (k < 0 || k > m) return 0;
+    int64_t c = 1;
+    for (int j = 1; j <= k; ++j) c = c * (m - k + j) / j;
+    return c;
+  };
+  std::vector<int> r2((size_t)std::max<int64_t>(1, bin(nq, 2)), -1), r4((size_t)std::max<int64_t>(1, bin(nq, 4)), -1);
+  std::vector<qf::SecGroup> lg;
+  for (size_t gi = 0; gi < sg.size(); ++gi) {
+    const uint64_t x = sg[gi].x;
+    const int w = popc(x);
+    if (w == 0) {
+      p.sec_diag = (int)gi;
+    } else if (w == 2 || w == 4) {
+      int pos[4], k = 0;
+      for (int q = 0; q < nq; ++q)
+        if ((x >> q) & 1) pos[k++] = q;
+      int64_t r = 0;
+      for (int i2 = 0; i2 < k; ++i2) r += bin(pos[i2], i2 + 1);
+      (w == 2 ? r2 : r4)[(size_t)r] = (int)gi;
+    } else {
+      lg.push_back(sg[gi]);
+    }
+  }
+  p.nseclarge = (int)lg.size();
   std::vector<qf::HClass> cls[qf::kClassTbN];
   for (int v = 0; v < qf::kClassTbN; ++v) {
     const int tb = qf::kClassTb0 + v;
@@ -352,15 +389,22 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     }
     QF_CUDA(cudaMemcpyAsync(p.d_hgroups, hg.data(), hg.size() * sizeof(qf::HGroup), cudaMemcpyHostToDevice,
                             st->stream));
-    if (!sg.empty()) {
-      if (cudaMalloc(&p.d_secgroups, sg.size() * sizeof(qf::SecGroup)) != cudaSuccess) {
-        cudaGetLastError();
-        free_plan(p);
-        return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
-      }
+    if (cudaMalloc(&p.d_secgroups, std::max<size_t>(1, sg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
+        cudaMalloc(&p.d_seclarge, std::max<size_t>(1, lg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
+        cudaMalloc(&p.d_rank2, r2.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p.d_rank4, r4.size() * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(p);
+      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
+    }
+    if (!sg.empty())
       QF_CUDA(cudaMemcpyAsync(p.d_secgroups, sg.data(), sg.size() * sizeof(qf::SecGroup), cudaMemcpyHostToDevice,
                               st->stream));
-    }
+    if (!lg.empty())
+      QF_CUDA(cudaMemcpyAsync(p.d_seclarge, lg.data(), lg.size() * sizeof(qf::SecGroup), cudaMemcpyHostToDevice,
+                              st->stream));
+    QF_CUDA(cudaMemcpyAsync(p.d_rank2, r2.data(), r2.size() * sizeof(int), cudaMemcpyHostToDevice, st->stream));
+    QF_CUDA(cudaMemcpyAsync(p.d_rank4, r4.data(), r4.size() * sizeof(int), cudaMemcpyHostToDevice, st->stream));
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks, wc.data(), wc.size() * sizeof(qf::WChunk), cudaMemcpyHostToDevice,
                             st->stream));
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks_f, wf.data(), wf.size() * sizeof(qf::WChunkF), cudaMemcpyHostToDevice,
@@ -906,9 +950,10 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
   if (st->sec_a >= 0 && st->n <= 2 * qf::kSecMaxPos) {
     // every nonzero amplitude is in one (alpha, beta) sector: sum over its members only
     const qf::SecSpace sp = sector_space(st->n, st->sec_a, st->sec_b);
-    QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, p->d_secgroups,
-                                   p->nsecgroups, p->d_hchunks, st->d_partials, st->d_counter, st->d_out, nb,
-                                   st->stream));
+    const qf::SecRank rk{p->d_rank2, p->d_rank4, p->sec_diag};
+    QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, rk, p->d_secgroups,
+                                   p->d_seclarge, p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter,
+                                   st->d_out, nb, st->stream));
   } else {
     QF_CUDA(qf::launch_expect(st->psi, st->n, st->dt, p->d_groups, p->ngroups, p->d_echunks, st->d_partials,
                               st->d_counter, st->d_out, nb, st->stream));
@@ -1017,8 +1062,10 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
       const int nbk = qf::reduce_blocks(n, st->dt);
       if (p) {
         const qf::SecSpace sp = sector_space(n, na, nbeta);
-        QF_CUDA(qf::launch_sector_hpsi(st->psi, st->lam, st->dt, lreal, sp, p->d_secgroups, p->nsecgroups,
-                                       p->d_hchunks, st->d_partials, st->d_counter, d_e, nbk, st->stream));
+        const qf::SecRank rk{p->d_rank2, p->d_rank4, p->sec_diag};
+        QF_CUDA(qf::launch_sector_hpsi(st->psi, st->lam, st->dt, lreal, sp, rk, p->d_secgroups, p->d_seclarge,
+                                       p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, nbk,
+                                       st->stream));
         QF_CUDA(qf::launch_sector_sweep(st->psi, st->lam, st->dt, true, lreal, st->d_secblk + nblk, (int)nblk,
                                         st->d_bar, st->d_sec_partial, st->d_out, grid_r, st->stream));
       } else {

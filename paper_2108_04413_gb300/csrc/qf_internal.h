@@ -79,6 +79,7 @@ struct ExpGroup {
 struct ExpChunk {
   uint64_t z[kChunkTerms];
   double2 tab[1 << kChunkTerms];  // (real-part weight, imaginary-part weight) per sign pattern
+  float2 ftab[1 << kChunkTerms];  // the same weights in FP32 (complex64 states)
 };
 
 // H|psi> plan (tiled): groups sorted by X mask form classes of equal high part
@@ -136,6 +137,13 @@ struct SecGroup {               // X group with its even/odd flip counts
   uint64_t x;
   int xe, xo, chunk0, nchunk;
 };
+// Groups of at most four flipped qubits, looked up by the colex rank of their X
+// set: rank2 has C(n,2) entries, rank4 C(n,4); -1 where no group exists.
+struct SecRank {
+  const int* rank2;
+  const int* rank4;
+  int diag;                     // the x = 0 group, or -1
+};
 
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s);
@@ -180,9 +188,12 @@ int sector_sweep_grid(qf_dtype dt, bool adj, bool realst);
 cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const SecBlk* blks,
                                 int nblk, unsigned* bar, double* partial, double* out, int grid, cudaStream_t s);
 // lam = H psi on the sector (lam may be NULL), out[0] = <psi|H psi>, out[1] = <psi|psi>.
+// Groups with <= 4 flipped qubits are reached by enumerating each member's
+// single and double flips (rk, indexing into `all`); `large` lists the others.
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
-                               const SecGroup* groups, int ngroups, const ExpChunk* chunks, double* partials,
-                               unsigned* counter, double* out, int nblocks, cudaStream_t s);
+                               const SecRank& rk, const SecGroup* all, const SecGroup* large, int nlarge,
+                               const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
+                               int nblocks, cudaStream_t s);
 
 int reduce_blocks(int n, qf_dtype dt);  // grid size used by the reducing kernels
 int prof_pre(unsigned kind, cudaStream_t s);  // kernel timing hooks (see qf_profile_begin)

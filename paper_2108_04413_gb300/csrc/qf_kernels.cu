@@ -392,6 +392,10 @@ __global__ void __launch_bounds__(256) k_expect(const typename Cx<T>::V* __restr
   const uint64_t total = (uint64_t)ngroups << (n - 1);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
+  // complex64: pair products and table weights in FP32, folded into the FP64
+  // accumulator every 32 pairs (no per-pair FP64 conversions)
+  float facc = 0.f;
+  int nf = 0;
   for (uint64_t f = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; f < total; f += stride) {
     const int g = (int)(f >> (n - 1));
     const uint64_t p = f & hmask;
@@ -399,8 +403,6 @@ __global__ void __launch_bounds__(256) k_expect(const typename Cx<T>::V* __restr
     if (G.h < 0) {
       const uint64_t b0 = p << 1;
       const V u0 = psi[b0], u1 = psi[b0 | 1ull];
-      const double n0 = (double)u0.x * u0.x + (double)u0.y * u0.y;
-      const double n1 = (double)u1.x * u1.x + (double)u1.y * u1.y;
       for (int c = 0; c < G.nchunk; ++c) {
         const ExpChunk* C = chunks + G.chunk0 + c;
         unsigned i0 = 0, i1 = 0;
@@ -411,26 +413,45 @@ __global__ void __launch_bounds__(256) k_expect(const typename Cx<T>::V* __restr
           i0 |= pb << t;
           i1 |= (pb ^ (unsigned)(zt & 1ull)) << t;
         }
-        acc = fma(C->tab[i0].x, n0, acc);
-        acc = fma(C->tab[i1].x, n1, acc);
+        if constexpr (sizeof(T) == 4) {
+          facc = fmaf(C->ftab[i0].x, fmaf(u0.x, u0.x, u0.y * u0.y), facc);
+          facc = fmaf(C->ftab[i1].x, fmaf(u1.x, u1.x, u1.y * u1.y), facc);
+        } else {
+          acc = fma(C->tab[i0].x, fma((double)u0.x, u0.x, (double)u0.y * u0.y), acc);
+          acc = fma(C->tab[i1].x, fma((double)u1.x, u1.x, (double)u1.y * u1.y), acc);
+        }
       }
     } else {
       const uint64_t b = ins0(p, G.h);
       const V u = psi[b], v = psi[b ^ G.x];
-      double rew = 0.0, imw = 0.0;
-      if (G.flags & 1) rew = fma((double)u.x, (double)v.x, (double)u.y * (double)v.y);
-      if (G.flags & 2) imw = fma((double)u.y, (double)v.x, -(double)u.x * (double)v.y);
+      T rew = 0, imw = 0;
+      if (G.flags & 1) rew = fma(u.x, v.x, u.y * v.y);
+      if (G.flags & 2) imw = fma(u.y, v.x, -u.x * v.y);
       for (int c = 0; c < G.nchunk; ++c) {
         const ExpChunk* C = chunks + G.chunk0 + c;
         unsigned idx = 0;
 #pragma unroll
         for (int t = 0; t < kChunkTerms; ++t) idx |= par64(C->z[t] & b) << t;
-        const double2 D = C->tab[idx];
-        if (G.flags & 1) acc = fma(D.x, rew, acc);
-        if (G.flags & 2) acc = fma(D.y, imw, acc);
+        if constexpr (sizeof(T) == 4) {
+          const float2 D = C->ftab[idx];
+          if (G.flags & 1) facc = fmaf(D.x, rew, facc);
+          if (G.flags & 2) facc = fmaf(D.y, imw, facc);
+        } else {
+          const double2 D = C->tab[idx];
+          if (G.flags & 1) acc = fma(D.x, rew, acc);
+          if (G.flags & 2) acc = fma(D.y, imw, acc);
+        }
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (++nf == 32) {
+        acc += (double)facc;
+        facc = 0.f;
+        nf = 0;
       }
     }
   }
+  acc += (double)facc;
   grid_finish(acc, partials, counter, out);
 }
 
@@ -813,15 +834,16 @@ __global__ void __launch_bounds__(256) k_adj_sparse(typename Cx<T>::V* __restric
     for (int r = 0; r < NR; ++r) {
       if (r < a.nr) {
         if (RQ) {
-          double s = 0.0;
+          // Re <lam_r|Qi v>, in the state's precision (FP64 accumulation across items)
+          T sx = 0, sy = 0;
 #pragma unroll
           for (int k = 0; k < NR; ++k)
             if (k < a.nr) {
-              const double qi = Q[cls][r][k].y;
-              s = fma(qi, (double)v[k].x, s);
-              if (!REALST) acc = fma(qi * (double)w[r].y, (double)v[k].y, acc);
+              const T qi = (T)Q[cls][r][k].y;
+              sx = fma(qi, v[k].x, sx);
+              if (!REALST) sy = fma(qi, v[k].y, sy);
             }
-          acc = fma((double)w[r].x, s, acc);
+          acc += (double)fma(w[r].x, sx, REALST ? (T)0 : w[r].y * sy);
         } else {
           double qx = 0.0, qy = 0.0;
 #pragma unroll

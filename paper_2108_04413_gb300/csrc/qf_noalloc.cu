@@ -118,6 +118,7 @@ void build_tables(const qf_term* terms, size_t nt, int* ngroups, int* nchunks) {
             ey += 2.0 * cv * ((y == 1) ? -1.0 : 1.0);
         }
         c.tab[pat] = make_double2(ex, ey);
+        c.ftab[pat] = make_float2((float)ex, (float)ey);
       }
       for (int t = 0; t < cnt; ++t) {
         const qf_term& T = terms[h_order[k + t]];

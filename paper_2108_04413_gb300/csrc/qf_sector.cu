@@ -82,7 +82,6 @@ __device__ bool grid_barrier(unsigned* bar) {
           atomicExch(bar + 2, 1u);
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -109,7 +108,8 @@ __device__ void sector_block(typename SCx<T>::V* psi, typename SCx<T>::V* lam, c
   T* pr = reinterpret_cast<T*>(psi);
   T* lr = reinterpret_cast<T*>(lam);
   for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items; it += stride) {
-    const uint32_t ie = (uint32_t)(it / B.cnt_o), io = (uint32_t)(it % B.cnt_o);
+    const uint32_t i32 = (uint32_t)it;  // items < 2^32 (at most C(17,8)^2)
+    const uint32_t ie = i32 / B.cnt_o, io = i32 - ie * B.cnt_o;
     const uint64_t base = unrank(ie, B.epos, B.ne, B.ke, C) | unrank(io, B.opos, B.no, B.ko, C);
     unsigned cls = 0;
     if (B.nzc > 0) cls = par64s(B.zc[0] & base);
@@ -176,8 +176,10 @@ __device__ double block_sum_s(double v) {
 // Persistent sweep over blocks [0, nblk) (forward: in order; reverse: from the
 // last).  Reverse: partial[b * gridDim.x + blockIdx.x] receives block b's
 // overlap summed over this CTA.
+constexpr int kSweepThreads = 1024;
+
 template <bool ADJ, bool REALST, typename T>
-__global__ void __launch_bounds__(256) k_sector_sweep(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
+__global__ void __launch_bounds__(kSweepThreads) k_sector_sweep(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
                                                       const SecBlk* __restrict__ blks, int nblk, unsigned* bar,
                                                       double* partial) {
   __shared__ uint32_t C[kBinom][kBinom];
@@ -211,77 +213,148 @@ __global__ void k_sector_reduce_rows(const double* __restrict__ partial, int nct
   out[b] = s;
 }
 
-// lambda = H psi on the sector members; out[0] = <psi|lambda>, out[1] = <psi|psi>
-// (block partials reduced by the last block, in order).
+// D_g(b) psi[b] added to (lx, ly) for one connected group.
+template <typename T, bool REALST>
+__device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict__ psi,
+                                            const ExpChunk* __restrict__ chunks, int chunk0, int nchunk, uint64_t b,
+                                            double& lx, double& ly) {
+  using V = typename SCx<T>::V;
+  double dx = 0.0, dy = 0.0;
+  for (int k = 0; k < nchunk; ++k) {
+    const ExpChunk* W = chunks + chunk0 + k;
+    unsigned idx = 0;
+#pragma unroll
+    for (int t = 0; t < kChunkTerms; ++t) idx |= par64s(W->z[t] & b) << t;
+    const double2 d = W->tab[idx];
+    dx += d.x;
+    dy += d.y;
+  }
+  const V v = psi[b];
+  lx = fma(dx, (double)v.x, lx);
+  if (!REALST) {
+    lx = fma(-dy, (double)v.y, lx);
+    ly = fma(dx, (double)v.y, fma(dy, (double)v.x, ly));
+  }
+}
+
+__device__ __forceinline__ void sort4(int& a, int& b, int& c, int& d) {
+  int t;
+#define QF_CSWAP(x, y) if (x > y) { t = x; x = y; y = t; }
+  QF_CSWAP(a, b) QF_CSWAP(c, d) QF_CSWAP(a, c) QF_CSWAP(b, d) QF_CSWAP(b, c)
+#undef QF_CSWAP
+}
+
+// lambda = H psi on the sector members; out[0] = <psi|lambda>, out[1] = <psi|psi>.
+// For member c every group that links c to another member flips as many
+// occupied as empty alpha (even) and beta (odd) spin orbitals.  Groups of at
+// most four flips are reached by enumerating exactly those flips (singles and
+// doubles of c) and looking the group up by the rank of its flip set; larger
+// groups are tested one by one.
 template <typename T, bool REALST>
 __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* __restrict__ psi,
-                                                     typename SCx<T>::V* __restrict__ lam, SecSpace sp,
-                                                     const SecGroup* __restrict__ groups, int ngroups,
+                                                     typename SCx<T>::V* __restrict__ lam, SecSpace sp, SecRank rk,
+                                                     const SecGroup* __restrict__ all,
+                                                     const SecGroup* __restrict__ large, int nlarge,
                                                      const ExpChunk* __restrict__ chunks, double* partials,
                                                      unsigned* counter, double* out) {
   using V = typename SCx<T>::V;
   __shared__ uint32_t C[kBinom][kBinom];
-  constexpr int kBatch = 512;
-  __shared__ SecGroup sg[kBatch];
+  __shared__ uint32_t C34[2 * kSecMaxPos + 1][5];  // C(m, k), k <= 4, for ranking flip sets
   __shared__ SecSpace ssp;
   fill_binom(C);
+  for (int i = threadIdx.x; i < (2 * kSecMaxPos + 1) * 5; i += blockDim.x) {
+    const int m = i / 5, k = i % 5;
+    uint64_t c = (k > m) ? 0 : 1;
+    for (int j = 1; j <= k && k <= m; ++j) c = c * (uint64_t)(m - k + j) / (uint64_t)j;
+    C34[m][k] = (uint32_t)c;
+  }
   if (threadIdx.x == 0) ssp = sp;
   __syncthreads();
   const uint64_t items = (uint64_t)sp.cnt_e * (uint64_t)sp.cnt_o;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t EVEN = 0x5555555555555555ull, ODD = 0xAAAAAAAAAAAAAAAAull;
   double acc_e = 0.0, acc_n = 0.0;
-  // every thread runs the same number of item rounds so the group batches stay in step
-  const uint64_t rounds = (items + stride - 1) / stride;
-  for (uint64_t rd = 0; rd < rounds; ++rd) {
-    const uint64_t it = rd * stride + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const bool live = it < items;
-    uint64_t c = 0;
-    if (live) {
-      const uint32_t ie = (uint32_t)(it / ssp.cnt_o), io = (uint32_t)(it % ssp.cnt_o);
-      c = unrank(ie, ssp.epos, ssp.ne, ssp.ke, C) | unrank(io, ssp.opos, ssp.no, ssp.ko, C);
+  for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items; it += stride) {
+    const uint32_t i32 = (uint32_t)it;
+    const uint32_t ie = i32 / ssp.cnt_o, io = i32 - ie * ssp.cnt_o;
+    const uint64_t c = unrank(ie, ssp.epos, ssp.ne, ssp.ke, C) | unrank(io, ssp.opos, ssp.no, ssp.ko, C);
+    // occupied / empty positions of each parity
+    uint8_t oa[kSecMaxPos], va[kSecMaxPos], ob[kSecMaxPos], vb[kSecMaxPos];
+    int noa = 0, nva = 0, nob = 0, nvb = 0;
+    for (int q = 0; q < ssp.ne; ++q) {
+      const int p = ssp.epos[q];
+      if ((c >> p) & 1ull) oa[noa++] = (uint8_t)p; else va[nva++] = (uint8_t)p;
+    }
+    for (int q = 0; q < ssp.no; ++q) {
+      const int p = ssp.opos[q];
+      if ((c >> p) & 1ull) ob[nob++] = (uint8_t)p; else vb[nvb++] = (uint8_t)p;
     }
     double lx = 0.0, ly = 0.0;
-    for (int g0 = 0; g0 < ngroups; g0 += kBatch) {
-      const int nb = min(kBatch, ngroups - g0);
-      __syncthreads();
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) sg[i] = groups[g0 + i];
-      __syncthreads();
-      if (!live) continue;
-      for (int i = 0; i < nb; ++i) {
-        const SecGroup G = sg[i];
-        // the partner c ^ x is in the sector iff x flips as many occupied as empty
-        // even (and odd) qubits of c
-        if (2 * __popcll(c & G.x & EVEN) != G.xe || 2 * __popcll(c & G.x & ODD) != G.xo) continue;
-        const uint64_t b = c ^ G.x;
-        double dx = 0.0, dy = 0.0;
-        for (int k = 0; k < G.nchunk; ++k) {
-          const ExpChunk* W = chunks + G.chunk0 + k;
-          unsigned idx = 0;
-#pragma unroll
-          for (int t = 0; t < kChunkTerms; ++t) idx |= par64s(W->z[t] & b) << t;
-          const double2 d = W->tab[idx];
-          dx += d.x;
-          dy += d.y;
-        }
-        const V v = psi[b];
-        lx = fma(dx, (double)v.x, lx);
-        if (!REALST) {
-          lx = fma(-dy, (double)v.y, lx);
-          ly = fma(dx, (double)v.y, fma(dy, (double)v.x, ly));
-        }
-      }
+    if (rk.diag >= 0) {
+      const SecGroup G = all[rk.diag];
+      sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c, lx, ly);
     }
-    if (live) {
-      const V u = psi[c];
-      acc_e = fma((double)u.x, lx, fma((double)u.y, ly, acc_e));
-      acc_n = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, acc_n));
-      if (lam) {
-        V w;
-        w.x = (T)lx;
-        w.y = (T)ly;
-        lam[c] = w;
-      }
+    // singles (both spins): flip set {i, a}
+    for (int s = 0; s < 2; ++s) {
+      const uint8_t* oc = s ? ob : oa;
+      const uint8_t* vc = s ? vb : va;
+      const int no_ = s ? nob : noa, nv_ = s ? nvb : nva;
+      for (int x1 = 0; x1 < no_; ++x1)
+        for (int x2 = 0; x2 < nv_; ++x2) {
+          int p = oc[x1], q = vc[x2];
+          if (p > q) { const int t = p; p = q; q = t; }
+          const int g = rk.rank2[p + (int)C34[q][2]];
+          if (g >= 0) {
+            const SecGroup G = all[g];
+            sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
+          }
+        }
+    }
+    // same-spin doubles: {i, j} occupied, {a, b} empty
+    for (int s = 0; s < 2; ++s) {
+      const uint8_t* oc = s ? ob : oa;
+      const uint8_t* vc = s ? vb : va;
+      const int no_ = s ? nob : noa, nv_ = s ? nvb : nva;
+      for (int x1 = 0; x1 < no_; ++x1)
+        for (int x2 = x1 + 1; x2 < no_; ++x2)
+          for (int y1 = 0; y1 < nv_; ++y1)
+            for (int y2 = y1 + 1; y2 < nv_; ++y2) {
+              int p0 = oc[x1], p1 = oc[x2], p2 = vc[y1], p3 = vc[y2];
+              sort4(p0, p1, p2, p3);
+              const int g = rk.rank4[p0 + (int)C34[p1][2] + (int)C34[p2][3] + (int)C34[p3][4]];
+              if (g >= 0) {
+                const SecGroup G = all[g];
+                sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
+              }
+            }
+    }
+    // opposite-spin doubles: one alpha and one beta flip pair
+    for (int x1 = 0; x1 < noa; ++x1)
+      for (int y1 = 0; y1 < nva; ++y1)
+        for (int x2 = 0; x2 < nob; ++x2)
+          for (int y2 = 0; y2 < nvb; ++y2) {
+            int p0 = oa[x1], p1 = va[y1], p2 = ob[x2], p3 = vb[y2];
+            sort4(p0, p1, p2, p3);
+            const int g = rk.rank4[p0 + (int)C34[p1][2] + (int)C34[p2][3] + (int)C34[p3][4]];
+            if (g >= 0) {
+              const SecGroup G = all[g];
+              sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
+            }
+          }
+    // groups flipping more than four qubits: test each
+    for (int gi = 0; gi < nlarge; ++gi) {
+      const SecGroup G = large[gi];
+      if (2 * __popcll(c & G.x & EVEN) != G.xe || 2 * __popcll(c & G.x & ODD) != G.xo) continue;
+      sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
+    }
+    const V u = psi[c];
+    acc_e = fma((double)u.x, lx, fma((double)u.y, ly, acc_e));
+    acc_n = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, acc_n));
+    if (lam) {
+      V w;
+      w.x = (T)lx;
+      w.y = (T)ly;
+      lam[c] = w;
     }
   }
   // deterministic two-value grid reduction
@@ -320,8 +393,9 @@ static int sweep_grid() {
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sector_sweep<ADJ, REALST, T>, 256, 0);
-  return std::max(1, std::min(per_sm, 4)) * std::max(1, sms);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sector_sweep<ADJ, REALST, T>, kSweepThreads, 0);
+  // one CTA per SM: the grid barrier then has one arrival per SM
+  return std::max(1, std::min(per_sm, 1)) * std::max(1, sms);
 }
 
 template <bool ADJ, bool REALST, typename T>
@@ -331,7 +405,8 @@ static cudaError_t sweep_t(void* psi, void* lam, const SecBlk* blks, int nblk, u
   V* p = static_cast<V*>(psi);
   V* l = static_cast<V*>(lam);
   void* args[] = {&p, &l, &blks, &nblk, &bar, &partial};
-  return cudaLaunchCooperativeKernel((const void*)k_sector_sweep<ADJ, REALST, T>, dim3(grid), dim3(256), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_sector_sweep<ADJ, REALST, T>, dim3(grid), dim3(kSweepThreads),
+                                     args, 0, s);
 }
 
 int sector_sweep_grid(qf_dtype dt, bool adj, bool realst) {
@@ -376,26 +451,21 @@ cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, boo
 }
 
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
-                               const SecGroup* groups, int ngroups, const ExpChunk* chunks, double* partials,
-                               unsigned* counter, double* out, int nblocks, cudaStream_t s) {
+                               const SecRank& rk, const SecGroup* all, const SecGroup* large, int nlarge,
+                               const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
+                               int nblocks, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_HPSI, s);
   const uint64_t items = (uint64_t)sp.cnt_e * sp.cnt_o;
   const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, (uint64_t)nblocks));
+#define QF_SECTOR_HPSI(TT, VV, RR)                                                                           \
+  k_sector_hpsi<TT, RR><<<g, 256, 0, s>>>(static_cast<const VV*>(psi), static_cast<VV*>(lam), sp, rk, all, large, \
+                                          nlarge, chunks, partials, counter, out)
   if (dt == QF_C128) {
-    if (realst)
-      k_sector_hpsi<double, true><<<g, 256, 0, s>>>(static_cast<const double2*>(psi), static_cast<double2*>(lam), sp,
-                                                    groups, ngroups, chunks, partials, counter, out);
-    else
-      k_sector_hpsi<double, false><<<g, 256, 0, s>>>(static_cast<const double2*>(psi), static_cast<double2*>(lam),
-                                                     sp, groups, ngroups, chunks, partials, counter, out);
+    if (realst) QF_SECTOR_HPSI(double, double2, true); else QF_SECTOR_HPSI(double, double2, false);
   } else {
-    if (realst)
-      k_sector_hpsi<float, true><<<g, 256, 0, s>>>(static_cast<const float2*>(psi), static_cast<float2*>(lam), sp,
-                                                   groups, ngroups, chunks, partials, counter, out);
-    else
-      k_sector_hpsi<float, false><<<g, 256, 0, s>>>(static_cast<const float2*>(psi), static_cast<float2*>(lam), sp,
-                                                    groups, ngroups, chunks, partials, counter, out);
+    if (realst) QF_SECTOR_HPSI(float, float2, true); else QF_SECTOR_HPSI(float, float2, false);
   }
+#undef QF_SECTOR_HPSI
   prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
