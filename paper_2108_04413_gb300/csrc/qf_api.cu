@@ -752,9 +752,16 @@ void build_tile(qf_state* st, const RotIn* r, size_t i, size_t j, uint64_t uni, 
   }
 }
 
+uint64_t typical_items(const qf::SecBlk* b, size_t n) {
+  std::vector<uint64_t> v(n);
+  for (size_t i = 0; i < n; ++i) v[i] = (uint64_t)b[i].cnt_e * b[i].cnt_o;
+  std::nth_element(v.begin(), v.begin() + n / 2, v.end());
+  return n ? v[n / 2] : 1;
+}
+
 qf_status flush_sector(qf_state* st, std::vector<qf::SecBlk>& pend) {
   if (pend.empty()) return QF_OK;
-  const int grid = qf::sector_sweep_grid(st->dt, false, true);
+  const int grid = qf::sector_sweep_grid(st->dt, false, true, typical_items(pend.data(), pend.size()));
   qf_status bs = ensure_sector_buffers(st, pend.size(), 1);
   if (bs != QF_OK) return bs;
   QF_CUDA(cudaMemcpyAsync(st->d_secblk, pend.data(), pend.size() * sizeof(qf::SecBlk), cudaMemcpyHostToDevice,
@@ -1045,9 +1052,10 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     if (ok) {
       const size_t nblk = blocks.size();
       const bool lreal = !p || !p->has_odd;
-      const int grid_f = qf::sector_sweep_grid(st->dt, false, true);
-      const int grid_r = qf::sector_sweep_grid(st->dt, true, lreal);
-      qf_status bs = ensure_sector_buffers(st, 2 * nblk, nblk * (size_t)grid_r);
+      const uint64_t typ = typical_items(sec.data(), nblk);
+      const int grid_f = qf::sector_sweep_grid(st->dt, false, true, typ);
+      const int grid_r = qf::sector_sweep_grid(st->dt, true, lreal, typ);
+      qf_status bs = ensure_sector_buffers(st, 2 * nblk, nblk * (size_t)grid_r * 32);
       if (bs != QF_OK) return bs;
       st->scale = 1.0;
       st->real = true;

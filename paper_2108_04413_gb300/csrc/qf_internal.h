@@ -182,9 +182,9 @@ cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const Sp
                               double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s);
 
 // Sector sweep over nblk blocks in one cooperative launch (reverse when adj:
-// out[b] = Im <lam|Q_b|psi> of block b, from partial[nblk * grid]).  bar: 3
-// device words.  grid from sector_sweep_grid.
-int sector_sweep_grid(qf_dtype dt, bool adj, bool realst);
+// out[b] = Im <lam|Q_b|psi> of block b, from partial[nblk * grid * 32]).  bar: 3
+// device words.  grid from sector_sweep_grid (typical_items: items of a typical block).
+int sector_sweep_grid(qf_dtype dt, bool adj, bool realst, uint64_t typical_items);
 cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const SecBlk* blks,
                                 int nblk, unsigned* bar, double* partial, double* out, int grid, cudaStream_t s);
 // lam = H psi on the sector (lam may be NULL), out[0] = <psi|H psi>, out[1] = <psi|psi>.

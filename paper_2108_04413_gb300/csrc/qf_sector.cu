@@ -59,6 +59,7 @@ __device__ __forceinline__ uint64_t unrank(uint32_t r, const uint8_t* pos, int m
 }
 
 constexpr long long kSpinLimit = 1ll << 26;
+constexpr int kSweepThreads = 1024;
 
 // Grid-wide barrier with a bounded wait.  bar[0] = arrivals, bar[1] = generation,
 // bar[2] = error flag.  Returns false when the grid must stop (error raised).
@@ -174,42 +175,53 @@ __device__ double block_sum_s(double v) {
 }
 
 // Persistent sweep over blocks [0, nblk) (forward: in order; reverse: from the
-// last).  Reverse: partial[b * gridDim.x + blockIdx.x] receives block b's
-// overlap summed over this CTA.
-constexpr int kSweepThreads = 1024;
+// last).  The next block's descriptor is loaded while the current one runs.
+// Reverse: partial[(b * gridDim.x + cta) * 32 + warp] receives block b's overlap
+// summed over one warp (reduced in a fixed order afterwards).  A one-CTA grid
+// needs no grid barrier.
+constexpr int kDescWords = sizeof(SecBlk) / 4;
+static_assert(sizeof(SecBlk) % 4 == 0 && kDescWords <= 1024, "descriptor copy layout");
 
 template <bool ADJ, bool REALST, typename T>
 __global__ void __launch_bounds__(kSweepThreads) k_sector_sweep(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
                                                       const SecBlk* __restrict__ blks, int nblk, unsigned* bar,
                                                       double* partial) {
   __shared__ uint32_t C[kBinom][kBinom];
-  __shared__ SecBlk sb;  // the current block's description, read by every thread
+  __shared__ SecBlk sb[2];  // current and next block descriptions
   fill_binom(C);
+  const int tid = threadIdx.x;
+  auto block_of = [&](int s) { return ADJ ? (nblk - 1 - s) : s; };
+  if (tid < kDescWords) reinterpret_cast<uint32_t*>(&sb[0])[tid] = __ldcg(reinterpret_cast<const uint32_t*>(blks + block_of(0)) + tid);
+  __syncthreads();
   for (int s = 0; s < nblk; ++s) {
-    const int b = ADJ ? (nblk - 1 - s) : s;
-    __syncthreads();
-    {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(blks + b);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(&sb);
-      for (int i = threadIdx.x; i < (int)(sizeof(SecBlk) / 4); i += blockDim.x) dst[i] = __ldcg(src + i);
-    }
-    __syncthreads();
+    const int b = block_of(s);
+    uint32_t nxt = 0;
+    if (s + 1 < nblk && tid < kDescWords)
+      nxt = __ldcg(reinterpret_cast<const uint32_t*>(blks + block_of(s + 1)) + tid);
     double acc = 0.0;
-    sector_block<ADJ, REALST, T>(psi, lam, sb, C, &acc);
+    sector_block<ADJ, REALST, T>(psi, lam, sb[s & 1], C, &acc);
     if (ADJ) {
-      acc = block_sum_s(acc);
-      if (threadIdx.x == 0) partial[(size_t)b * gridDim.x + blockIdx.x] = acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if ((tid & 31) == 0) partial[((size_t)b * gridDim.x + blockIdx.x) * 32 + (tid >> 5)] = acc;
     }
-    if (s + 1 < nblk && !grid_barrier(bar)) return;
+    if (s + 1 < nblk) {
+      if (tid < kDescWords) reinterpret_cast<uint32_t*>(&sb[(s + 1) & 1])[tid] = nxt;
+      if (gridDim.x == 1) {
+        __syncthreads();
+      } else if (!grid_barrier(bar)) {
+        return;
+      }
+    }
   }
 }
 
-// out[b] = sum over CTAs of partial[b * ncta + cta], in CTA order.
-__global__ void k_sector_reduce_rows(const double* __restrict__ partial, int ncta, int nblk, double* out) {
+// out[b] = sum of partial[b * nslot .. b * nslot + nslot), in slot order.
+__global__ void k_sector_reduce_rows(const double* __restrict__ partial, int nslot, int nblk, double* out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblk) return;
   double s = 0.0;
-  for (int c = 0; c < ncta; ++c) s += partial[(size_t)b * ncta + c];
+  for (int c = 0; c < nslot; ++c) s += partial[(size_t)b * nslot + c];
   out[b] = s;
 }
 
@@ -387,15 +399,17 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
 
 }  // namespace
 
-// Largest grid the cooperative sweep can use (every CTA resident at once).
+// Grid of the cooperative sweep: about one item per thread for a typical block,
+// at most one CTA per SM (all CTAs must be resident at once).
 template <bool ADJ, bool REALST, typename T>
-static int sweep_grid() {
+static int sweep_grid(uint64_t typical_items) {
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sector_sweep<ADJ, REALST, T>, kSweepThreads, 0);
-  // one CTA per SM: the grid barrier then has one arrival per SM
-  return std::max(1, std::min(per_sm, 1)) * std::max(1, sms);
+  const uint64_t want = (typical_items + kSweepThreads - 1) / kSweepThreads;
+  const uint64_t cap = (uint64_t)std::max(1, std::min(per_sm, 1)) * (uint64_t)std::max(1, sms);
+  return (int)std::max<uint64_t>(1, std::min(want, cap));
 }
 
 template <bool ADJ, bool REALST, typename T>
@@ -409,13 +423,14 @@ static cudaError_t sweep_t(void* psi, void* lam, const SecBlk* blks, int nblk, u
                                      args, 0, s);
 }
 
-int sector_sweep_grid(qf_dtype dt, bool adj, bool realst) {
+int sector_sweep_grid(qf_dtype dt, bool adj, bool realst, uint64_t typical_items) {
+  const uint64_t t = typical_items;
   if (dt == QF_C128) {
-    if (adj) return realst ? sweep_grid<true, true, double>() : sweep_grid<true, false, double>();
-    return realst ? sweep_grid<false, true, double>() : sweep_grid<false, false, double>();
+    if (adj) return realst ? sweep_grid<true, true, double>(t) : sweep_grid<true, false, double>(t);
+    return realst ? sweep_grid<false, true, double>(t) : sweep_grid<false, false, double>(t);
   }
-  if (adj) return realst ? sweep_grid<true, true, float>() : sweep_grid<true, false, float>();
-  return realst ? sweep_grid<false, true, float>() : sweep_grid<false, false, float>();
+  if (adj) return realst ? sweep_grid<true, true, float>(t) : sweep_grid<true, false, float>(t);
+  return realst ? sweep_grid<false, true, float>(t) : sweep_grid<false, false, float>(t);
 }
 
 cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const SecBlk* blks,
@@ -442,7 +457,7 @@ cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, boo
   }
   count_launch();
   if (e == cudaSuccess && adj) {
-    k_sector_reduce_rows<<<(nblk + 255) / 256, 256, 0, s>>>(partial, grid, nblk, out);
+    k_sector_reduce_rows<<<(nblk + 255) / 256, 256, 0, s>>>(partial, grid * (kSweepThreads / 32), nblk, out);
     e = cudaGetLastError();
     count_launch();
   }
