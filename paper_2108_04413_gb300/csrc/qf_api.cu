@@ -51,9 +51,8 @@ struct ExpPlan {
   int nsecgroups = 0;
   qf::SecGroup* d_seclarge = nullptr;   // those flipping more than four qubits
   int nseclarge = 0;
-  int* d_rank2 = nullptr;               // group index by rank of a 2-set of flipped qubits
-  int* d_rank4 = nullptr;               // ... of a 4-set
-  int sec_diag = -1;
+  int* d_rk = nullptr;                  // group index tables by flipped spin orbitals (see SecRank)
+  qf::SecRank rk{};
   qf::HClass* d_classes[qf::kClassTbN] = {};  // classes for tile bits 10, 11, 12
   int nclasses[qf::kClassTbN] = {};
   bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
@@ -69,8 +68,7 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_wchunks_s);
   cudaFree(p.d_secgroups);
   cudaFree(p.d_seclarge);
-  cudaFree(p.d_rank2);
-  cudaFree(p.d_rank4);
+  cudaFree(p.d_rk);
   for (int v = 0; v < qf::kClassTbN; ++v) cudaFree(p.d_classes[v]);
   p = ExpPlan();
 }
@@ -324,28 +322,47 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     sg.push_back(qf::SecGroup{g.x, xe, xo, g.chunk0, g.nchunk});
   }
   p.nsecgroups = (int)sg.size();
-  // rank tables: colex rank of the sorted flip set, sum_i C(p_i, i + 1)
-  const int nq = st->n;
-  auto bin = [](int m, int k) -> int64_t {
-    if (k < 0 || k > m) return 0;
-    int64_t c = 1;
-    for (int j = 1; j <= k; ++j) c = c * (m - k + j) / j;
-    return c;
-  };
-  std::vector<int> r2((size_t)std::max<int64_t>(1, bin(nq, 2)), -1), r4((size_t)std::max<int64_t>(1, bin(nq, 4)), -1);
+  // lookup tables by flipped spin orbitals (local index i of qubit 2i or 2i+1)
+  const int nq = st->n, ne = (nq + 1) / 2, no = nq / 2;
+  const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
+  const size_t o_sa = 0, o_sb = o_sa + (size_t)ne * ne, o_aa = o_sb + (size_t)no * no,
+               o_bb = o_aa + (size_t)pe * pe, o_ab = o_bb + (size_t)po * po,
+               n_rk = o_ab + (size_t)ne * ne * no * no;
+  std::vector<int> rkt(std::max<size_t>(1, n_rk), -1);
   std::vector<qf::SecGroup> lg;
+  int diag = -1;
+  auto pr = [](int i, int j) { return i + j * (j - 1) / 2; };  // i < j
   for (size_t gi = 0; gi < sg.size(); ++gi) {
     const uint64_t x = sg[gi].x;
     const int w = popc(x);
+    std::vector<int> ev, od;
+    for (int q = 0; q < nq; ++q)
+      if ((x >> q) & 1) ((q & 1) ? od : ev).push_back(q >> 1);
     if (w == 0) {
-      p.sec_diag = (int)gi;
-    } else if (w == 2 || w == 4) {
-      int pos[4], k = 0;
-      for (int q = 0; q < nq; ++q)
-        if ((x >> q) & 1) pos[k++] = q;
-      int64_t r = 0;
-      for (int i2 = 0; i2 < k; ++i2) r += bin(pos[i2], i2 + 1);
-      (w == 2 ? r2 : r4)[(size_t)r] = (int)gi;
+      diag = (int)gi;
+      continue;
+    }
+    // each flip set is recorded under every occupied/empty split that a member can present
+    if (w == 2 && ev.size() == 2) {
+      rkt[o_sa + ev[0] * ne + ev[1]] = (int)gi;
+      rkt[o_sa + ev[1] * ne + ev[0]] = (int)gi;
+    } else if (w == 2 && od.size() == 2) {
+      rkt[o_sb + od[0] * no + od[1]] = (int)gi;
+      rkt[o_sb + od[1] * no + od[0]] = (int)gi;
+    } else if (w == 4 && (ev.size() == 4 || od.size() == 4)) {
+      const std::vector<int>& v = ev.size() == 4 ? ev : od;
+      const size_t off = ev.size() == 4 ? o_aa : o_bb;
+      const int P = ev.size() == 4 ? pe : po;
+      const int pairs[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
+      for (const auto& q : pairs) {
+        const int r1 = pr(v[q[0]], v[q[1]]), r2 = pr(v[q[2]], v[q[3]]);
+        rkt[off + (size_t)r1 * P + r2] = (int)gi;
+        rkt[off + (size_t)r2 * P + r1] = (int)gi;
+      }
+    } else if (w == 4 && ev.size() == 2) {
+      for (int s0 = 0; s0 < 2; ++s0)
+        for (int s1 = 0; s1 < 2; ++s1)
+          rkt[o_ab + (((size_t)ev[s0] * ne + ev[1 - s0]) * no + od[s1]) * no + od[1 - s1]] = (int)gi;
     } else {
       lg.push_back(sg[gi]);
     }
@@ -391,8 +408,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
                             st->stream));
     if (cudaMalloc(&p.d_secgroups, std::max<size_t>(1, sg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
         cudaMalloc(&p.d_seclarge, std::max<size_t>(1, lg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
-        cudaMalloc(&p.d_rank2, r2.size() * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&p.d_rank4, r4.size() * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&p.d_rk, rkt.size() * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       free_plan(p);
       return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
@@ -403,8 +419,8 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     if (!lg.empty())
       QF_CUDA(cudaMemcpyAsync(p.d_seclarge, lg.data(), lg.size() * sizeof(qf::SecGroup), cudaMemcpyHostToDevice,
                               st->stream));
-    QF_CUDA(cudaMemcpyAsync(p.d_rank2, r2.data(), r2.size() * sizeof(int), cudaMemcpyHostToDevice, st->stream));
-    QF_CUDA(cudaMemcpyAsync(p.d_rank4, r4.data(), r4.size() * sizeof(int), cudaMemcpyHostToDevice, st->stream));
+    QF_CUDA(cudaMemcpyAsync(p.d_rk, rkt.data(), rkt.size() * sizeof(int), cudaMemcpyHostToDevice, st->stream));
+    p.rk = qf::SecRank{p.d_rk + o_sa, p.d_rk + o_sb, p.d_rk + o_aa, p.d_rk + o_bb, p.d_rk + o_ab, diag, ne, no};
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks, wc.data(), wc.size() * sizeof(qf::WChunk), cudaMemcpyHostToDevice,
                             st->stream));
     QF_CUDA(cudaMemcpyAsync(p.d_wchunks_f, wf.data(), wf.size() * sizeof(qf::WChunkF), cudaMemcpyHostToDevice,
@@ -957,8 +973,7 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
   if (st->sec_a >= 0 && st->n <= 2 * qf::kSecMaxPos) {
     // every nonzero amplitude is in one (alpha, beta) sector: sum over its members only
     const qf::SecSpace sp = sector_space(st->n, st->sec_a, st->sec_b);
-    const qf::SecRank rk{p->d_rank2, p->d_rank4, p->sec_diag};
-    QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, rk, p->d_secgroups,
+    QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, p->rk, p->d_secgroups,
                                    p->d_seclarge, p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter,
                                    st->d_out, nb, st->stream));
   } else {
@@ -1070,8 +1085,7 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
       const int nbk = qf::reduce_blocks(n, st->dt);
       if (p) {
         const qf::SecSpace sp = sector_space(n, na, nbeta);
-        const qf::SecRank rk{p->d_rank2, p->d_rank4, p->sec_diag};
-        QF_CUDA(qf::launch_sector_hpsi(st->psi, st->lam, st->dt, lreal, sp, rk, p->d_secgroups, p->d_seclarge,
+        QF_CUDA(qf::launch_sector_hpsi(st->psi, st->lam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
                                        p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, nbk,
                                        st->stream));
         QF_CUDA(qf::launch_sector_sweep(st->psi, st->lam, st->dt, true, lreal, st->d_secblk + nblk, (int)nblk,

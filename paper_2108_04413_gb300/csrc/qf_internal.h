@@ -137,12 +137,21 @@ struct SecGroup {               // X group with its even/odd flip counts
   uint64_t x;
   int xe, xo, chunk0, nchunk;
 };
-// Groups of at most four flipped qubits, looked up by the colex rank of their X
-// set: rank2 has C(n,2) entries, rank4 C(n,4); -1 where no group exists.
+// Groups of at most four flipped qubits, looked up by the spin orbitals they
+// flip, in local indices of each parity (alpha = even qubit 2i -> i, beta = odd
+// qubit 2i+1 -> i); -1 where no group exists.
+//   sa[i * ne + a], sb[j * no + b]                      singles
+//   aa[pr(i, j) * C(ne, 2) + pr(a, b)], bb likewise     same-spin doubles, i < j, a < b
+//   ab[((i * ne + a) * no + j) * no + b]                opposite-spin doubles
+// with pr(i, j) = i + j (j - 1) / 2.
 struct SecRank {
-  const int* rank2;
-  const int* rank4;
+  const int* sa;
+  const int* sb;
+  const int* aa;
+  const int* bb;
+  const int* ab;
   int diag;                     // the x = 0 group, or -1
+  int ne, no;
 };
 
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.

@@ -226,7 +226,7 @@ __global__ void k_sector_reduce_rows(const double* __restrict__ partial, int nsl
 }
 
 // D_g(b) psi[b] added to (lx, ly) for one connected group.
-template <typename T, bool REALST>
+template <typename T, bool REALST, bool NARROW>
 __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict__ psi,
                                             const ExpChunk* __restrict__ chunks, int chunk0, int nchunk, uint64_t b,
                                             double& lx, double& ly) {
@@ -235,25 +235,31 @@ __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict
   for (int k = 0; k < nchunk; ++k) {
     const ExpChunk* W = chunks + chunk0 + k;
     unsigned idx = 0;
+    if (NARROW) {  // n <= 32: one 32-bit popcount per term
+      const uint32_t b32 = (uint32_t)b;
 #pragma unroll
-    for (int t = 0; t < kChunkTerms; ++t) idx |= par64s(W->z[t] & b) << t;
+      for (int t = 0; t < kChunkTerms; ++t) idx |= ((unsigned)__popc((uint32_t)W->z[t] & b32) & 1u) << t;
+    } else {
+#pragma unroll
+      for (int t = 0; t < kChunkTerms; ++t) idx |= par64s(W->z[t] & b) << t;
+    }
     const double2 d = W->tab[idx];
-    dx += d.x;
-    dy += d.y;
+    if (k == 0) {
+      dx = d.x;
+      dy = d.y;
+    } else {
+      dx += d.x;
+      dy += d.y;
+    }
   }
-  const V v = psi[b];
-  lx = fma(dx, (double)v.x, lx);
-  if (!REALST) {
+  if (REALST) {
+    lx = fma(dx, (double)reinterpret_cast<const T*>(psi)[2 * b], lx);
+  } else {
+    const V v = psi[b];
+    lx = fma(dx, (double)v.x, lx);
     lx = fma(-dy, (double)v.y, lx);
     ly = fma(dx, (double)v.y, fma(dy, (double)v.x, ly));
   }
-}
-
-__device__ __forceinline__ void sort4(int& a, int& b, int& c, int& d) {
-  int t;
-#define QF_CSWAP(x, y) if (x > y) { t = x; x = y; y = t; }
-  QF_CSWAP(a, b) QF_CSWAP(c, d) QF_CSWAP(a, c) QF_CSWAP(b, d) QF_CSWAP(b, c)
-#undef QF_CSWAP
 }
 
 // lambda = H psi on the sector members; out[0] = <psi|lambda>, out[1] = <psi|psi>.
@@ -262,7 +268,7 @@ __device__ __forceinline__ void sort4(int& a, int& b, int& c, int& d) {
 // most four flips are reached by enumerating exactly those flips (singles and
 // doubles of c) and looking the group up by the rank of its flip set; larger
 // groups are tested one by one.
-template <typename T, bool REALST>
+template <typename T, bool REALST, bool NARROW>
 __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* __restrict__ psi,
                                                      typename SCx<T>::V* __restrict__ lam, SecSpace sp, SecRank rk,
                                                      const SecGroup* __restrict__ all,
@@ -271,15 +277,8 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
                                                      unsigned* counter, double* out) {
   using V = typename SCx<T>::V;
   __shared__ uint32_t C[kBinom][kBinom];
-  __shared__ uint32_t C34[2 * kSecMaxPos + 1][5];  // C(m, k), k <= 4, for ranking flip sets
   __shared__ SecSpace ssp;
   fill_binom(C);
-  for (int i = threadIdx.x; i < (2 * kSecMaxPos + 1) * 5; i += blockDim.x) {
-    const int m = i / 5, k = i % 5;
-    uint64_t c = (k > m) ? 0 : 1;
-    for (int j = 1; j <= k && k <= m; ++j) c = c * (uint64_t)(m - k + j) / (uint64_t)j;
-    C34[m][k] = (uint32_t)c;
-  }
   if (threadIdx.x == 0) ssp = sp;
   __syncthreads();
   const uint64_t items = (uint64_t)sp.cnt_e * (uint64_t)sp.cnt_o;
@@ -290,74 +289,54 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
     const uint32_t i32 = (uint32_t)it;
     const uint32_t ie = i32 / ssp.cnt_o, io = i32 - ie * ssp.cnt_o;
     const uint64_t c = unrank(ie, ssp.epos, ssp.ne, ssp.ke, C) | unrank(io, ssp.opos, ssp.no, ssp.ko, C);
-    // occupied / empty positions of each parity
+    // occupied / empty spin orbitals of each parity, as local indices (qubit 2i -> i, 2i+1 -> i)
     uint8_t oa[kSecMaxPos], va[kSecMaxPos], ob[kSecMaxPos], vb[kSecMaxPos];
     int noa = 0, nva = 0, nob = 0, nvb = 0;
     for (int q = 0; q < ssp.ne; ++q) {
-      const int p = ssp.epos[q];
-      if ((c >> p) & 1ull) oa[noa++] = (uint8_t)p; else va[nva++] = (uint8_t)p;
+      if ((c >> ssp.epos[q]) & 1ull) oa[noa++] = (uint8_t)q; else va[nva++] = (uint8_t)q;
     }
     for (int q = 0; q < ssp.no; ++q) {
-      const int p = ssp.opos[q];
-      if ((c >> p) & 1ull) ob[nob++] = (uint8_t)p; else vb[nvb++] = (uint8_t)p;
+      if ((c >> ssp.opos[q]) & 1ull) ob[nob++] = (uint8_t)q; else vb[nvb++] = (uint8_t)q;
     }
     double lx = 0.0, ly = 0.0;
-    if (rk.diag >= 0) {
-      const SecGroup G = all[rk.diag];
-      sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c, lx, ly);
-    }
-    // singles (both spins): flip set {i, a}
-    for (int s = 0; s < 2; ++s) {
-      const uint8_t* oc = s ? ob : oa;
-      const uint8_t* vc = s ? vb : va;
-      const int no_ = s ? nob : noa, nv_ = s ? nvb : nva;
-      for (int x1 = 0; x1 < no_; ++x1)
-        for (int x2 = 0; x2 < nv_; ++x2) {
-          int p = oc[x1], q = vc[x2];
-          if (p > q) { const int t = p; p = q; q = t; }
-          const int g = rk.rank2[p + (int)C34[q][2]];
-          if (g >= 0) {
-            const SecGroup G = all[g];
-            sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
-          }
-        }
-    }
-    // same-spin doubles: {i, j} occupied, {a, b} empty
-    for (int s = 0; s < 2; ++s) {
-      const uint8_t* oc = s ? ob : oa;
-      const uint8_t* vc = s ? vb : va;
-      const int no_ = s ? nob : noa, nv_ = s ? nvb : nva;
-      for (int x1 = 0; x1 < no_; ++x1)
-        for (int x2 = x1 + 1; x2 < no_; ++x2)
-          for (int y1 = 0; y1 < nv_; ++y1)
-            for (int y2 = y1 + 1; y2 < nv_; ++y2) {
-              int p0 = oc[x1], p1 = oc[x2], p2 = vc[y1], p3 = vc[y2];
-              sort4(p0, p1, p2, p3);
-              const int g = rk.rank4[p0 + (int)C34[p1][2] + (int)C34[p2][3] + (int)C34[p3][4]];
-              if (g >= 0) {
-                const SecGroup G = all[g];
-                sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
-              }
-            }
-    }
-    // opposite-spin doubles: one alpha and one beta flip pair
+    auto visit = [&](int g) {
+      if (g >= 0) {
+        const SecGroup G = all[g];
+        sector_term<T, REALST, NARROW>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
+      }
+    };
+    if (rk.diag >= 0) visit(rk.diag);
+    const int ne = rk.ne, no = rk.no;
+    const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
     for (int x1 = 0; x1 < noa; ++x1)
-      for (int y1 = 0; y1 < nva; ++y1)
-        for (int x2 = 0; x2 < nob; ++x2)
-          for (int y2 = 0; y2 < nvb; ++y2) {
-            int p0 = oa[x1], p1 = va[y1], p2 = ob[x2], p3 = vb[y2];
-            sort4(p0, p1, p2, p3);
-            const int g = rk.rank4[p0 + (int)C34[p1][2] + (int)C34[p2][3] + (int)C34[p3][4]];
-            if (g >= 0) {
-              const SecGroup G = all[g];
-              sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
-            }
-          }
+      for (int y1 = 0; y1 < nva; ++y1) visit(__ldg(rk.sa + oa[x1] * ne + va[y1]));
+    for (int x1 = 0; x1 < nob; ++x1)
+      for (int y1 = 0; y1 < nvb; ++y1) visit(__ldg(rk.sb + ob[x1] * no + vb[y1]));
+    for (int x2 = 1; x2 < noa; ++x2)
+      for (int x1 = 0; x1 < x2; ++x1) {
+        const int rij = oa[x1] + oa[x2] * (oa[x2] - 1) / 2;
+        for (int y2 = 1; y2 < nva; ++y2)
+          for (int y1 = 0; y1 < y2; ++y1) visit(__ldg(rk.aa + rij * pe + va[y1] + va[y2] * (va[y2] - 1) / 2));
+      }
+    for (int x2 = 1; x2 < nob; ++x2)
+      for (int x1 = 0; x1 < x2; ++x1) {
+        const int rij = ob[x1] + ob[x2] * (ob[x2] - 1) / 2;
+        for (int y2 = 1; y2 < nvb; ++y2)
+          for (int y1 = 0; y1 < y2; ++y1) visit(__ldg(rk.bb + rij * po + vb[y1] + vb[y2] * (vb[y2] - 1) / 2));
+      }
+    for (int x1 = 0; x1 < noa; ++x1)
+      for (int y1 = 0; y1 < nva; ++y1) {
+        const int ia = (oa[x1] * ne + va[y1]) * no;
+        for (int x2 = 0; x2 < nob; ++x2) {
+          const int iab = (ia + ob[x2]) * no;
+          for (int y2 = 0; y2 < nvb; ++y2) visit(__ldg(rk.ab + iab + vb[y2]));
+        }
+      }
     // groups flipping more than four qubits: test each
     for (int gi = 0; gi < nlarge; ++gi) {
       const SecGroup G = large[gi];
       if (2 * __popcll(c & G.x & EVEN) != G.xe || 2 * __popcll(c & G.x & ODD) != G.xo) continue;
-      sector_term<T, REALST>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
+      sector_term<T, REALST, NARROW>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
     }
     const V u = psi[c];
     acc_e = fma((double)u.x, lx, fma((double)u.y, ly, acc_e));
@@ -472,13 +451,22 @@ cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool rea
   const int prof_slot_ = prof_pre(QF_K_HPSI, s);
   const uint64_t items = (uint64_t)sp.cnt_e * sp.cnt_o;
   const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, (uint64_t)nblocks));
-#define QF_SECTOR_HPSI(TT, VV, RR)                                                                           \
-  k_sector_hpsi<TT, RR><<<g, 256, 0, s>>>(static_cast<const VV*>(psi), static_cast<VV*>(lam), sp, rk, all, large, \
-                                          nlarge, chunks, partials, counter, out)
+  const bool narrow = sp.ne + sp.no <= 32;
+#define QF_SECTOR_HPSI(TT, VV, RR, NN)                                                                       \
+  k_sector_hpsi<TT, RR, NN><<<g, 256, 0, s>>>(static_cast<const VV*>(psi), static_cast<VV*>(lam), sp, rk, all,    \
+                                              large, nlarge, chunks, partials, counter, out)
   if (dt == QF_C128) {
-    if (realst) QF_SECTOR_HPSI(double, double2, true); else QF_SECTOR_HPSI(double, double2, false);
+    if (realst) {
+      if (narrow) QF_SECTOR_HPSI(double, double2, true, true); else QF_SECTOR_HPSI(double, double2, true, false);
+    } else {
+      if (narrow) QF_SECTOR_HPSI(double, double2, false, true); else QF_SECTOR_HPSI(double, double2, false, false);
+    }
   } else {
-    if (realst) QF_SECTOR_HPSI(float, float2, true); else QF_SECTOR_HPSI(float, float2, false);
+    if (realst) {
+      if (narrow) QF_SECTOR_HPSI(float, float2, true, true); else QF_SECTOR_HPSI(float, float2, true, false);
+    } else {
+      if (narrow) QF_SECTOR_HPSI(float, float2, false, true); else QF_SECTOR_HPSI(float, float2, false, false);
+    }
   }
 #undef QF_SECTOR_HPSI
   prof_post(prof_slot_, s);
