@@ -84,6 +84,10 @@ qf_status qf_apply_circuit(qf_state* st, const qf_rot* rots, size_t n_rot);
  * Hermitian-conjugate contributions together).  Synchronises the stream. */
 qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, double* re, double* im);
 
+/* (Calls that run a persistent kernel with grid barriers -- qf_energy_grad and
+ * qf_apply_circuit on sector states -- return QF_ETIMEOUT if a barrier wait
+ * exceeds 2 s.) */
+
 /* Energy and gradient of E(t) = <Phi|U(t)^+ H U(t)|Phi> (Eq. 17-18) with
  * |Phi> = |det> and U(t) the ansatz rotations in list order, theta_k = coeff_k *
  * t[param_k].  The gradient comes from a reverse (adjoint) sweep:
@@ -182,6 +186,12 @@ qf_status qf_profile_end(void);
 #define QF_NOALLOC_SCRATCH_BYTES (1u << 20)
 qf_status qf_expectation_noalloc(const void* amplitudes, int n, qf_dtype dtype, void* stream,
                                  const qf_term* terms, size_t n_terms, double* re, double* im);
+
+/* Self-test of the bounded device wait used by the grid barriers of the
+ * persistent kernels: one thread waits up to limit_s seconds (0 < limit_s <= 10)
+ * on a word that nothing changes.  Returns QF_ETIMEOUT when the wait gave up as
+ * designed (the context stays usable), QF_ECUDA otherwise. */
+qf_status qf_selftest_bounded_wait(void* stream, double limit_s);
 
 /* Thread-local message describing the last failure. */
 const char* qf_last_error(void);

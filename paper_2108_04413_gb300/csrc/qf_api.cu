@@ -1235,6 +1235,25 @@ qf_status qf_state_clear_plans(qf_state* st) {
   return QF_OK;
 }
 
+qf_status qf_selftest_bounded_wait(void* stream, double limit_s) {
+  if (!(limit_s > 0.0) || limit_s > 10.0) return fail(QF_EINVAL, "limit_s must be in (0, 10]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned* w = nullptr;
+  if (cudaMalloc(&w, 4 * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QF_ENOMEM, "cudaMalloc(self-test words) failed");
+  }
+  unsigned h[3] = {0, 0, 0};
+  cudaError_t e = cudaMemsetAsync(w, 0, 4 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = qf::launch_wait_selftest(w, limit_s, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, w, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(w);
+  if (e != cudaSuccess) return fail(QF_ECUDA, std::string("bounded-wait self-test: ") + cudaGetErrorString(e));
+  if (h[2]) return fail(QF_ETIMEOUT, "bounded wait gave up after its limit (expected)");
+  return fail(QF_ECUDA, "bounded wait returned without a timeout");
+}
+
 qf_status qf_profile_begin(unsigned kind_mask) {
   qf::profile_begin(kind_mask);
   return QF_OK;

@@ -204,6 +204,10 @@ cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool rea
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
                                int nblocks, cudaStream_t s);
 
+// Bounded-wait self-test: words (3 device words, zeroed) -- waits on words[1]
+// for limit_s seconds, then raises words[2].
+cudaError_t launch_wait_selftest(unsigned* words, double limit_s, cudaStream_t s);
+
 int reduce_blocks(int n, qf_dtype dt);  // grid size used by the reducing kernels
 int prof_pre(unsigned kind, cudaStream_t s);  // kernel timing hooks (see qf_profile_begin)
 void prof_post(int slot, cudaStream_t s);

@@ -58,8 +58,29 @@ __device__ __forceinline__ uint64_t unrank(uint32_t r, const uint8_t* pos, int m
   return bits;
 }
 
-constexpr long long kSpinLimit = 1ll << 26;
 constexpr int kSweepThreads = 1024;
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // a grid barrier gives up after 2 s
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits (one thread) until *gen differs from `old`, *err is raised, or limit_ns
+// passes; on timeout raises *err.  Returns true when the generation changed.
+__device__ bool bounded_wait(volatile unsigned* gen, unsigned old, unsigned* err, uint64_t limit_ns) {
+  volatile unsigned* verr = err;
+  const uint64_t t0 = global_ns();
+  while (*gen == old) {
+    if (*verr != 0u) return false;
+    if (global_ns() - t0 > limit_ns) {
+      atomicExch(err, 1u);
+      return false;
+    }
+  }
+  return true;
+}
 
 // Grid-wide barrier with a bounded wait.  bar[0] = arrivals, bar[1] = generation,
 // bar[2] = error flag.  Returns false when the grid must stop (error raised).
@@ -68,7 +89,6 @@ __device__ bool grid_barrier(unsigned* bar) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = bar + 1;
-    volatile unsigned* verr = bar + 2;
     const unsigned gen = *vgen;
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u);
@@ -77,19 +97,19 @@ __device__ bool grid_barrier(unsigned* bar) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
-      long long it = 0;
-      while (*vgen == gen && *verr == 0u) {
-        if (++it > kSpinLimit) {
-          atomicExch(bar + 2, 1u);
-          break;
-        }
-      }
+      bounded_wait(vgen, gen, bar + 2, kBarrierLimitNs);
     }
     __threadfence();
-    stop = (*verr != 0u);
+    stop = (*(volatile unsigned*)(bar + 2) != 0u);
   }
   __syncthreads();
   return !stop;
+}
+
+// Self-test of the bounded wait: waits on a generation word that nothing
+// changes; words[2] must come back raised.
+__global__ void k_wait_selftest(unsigned* words, uint64_t limit_ns) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) bounded_wait(words + 1, words[1], words + 2, limit_ns);
 }
 
 template <typename T> struct SCx;
@@ -400,6 +420,12 @@ static cudaError_t sweep_t(void* psi, void* lam, const SecBlk* blks, int nblk, u
   void* args[] = {&p, &l, &blks, &nblk, &bar, &partial};
   return cudaLaunchCooperativeKernel((const void*)k_sector_sweep<ADJ, REALST, T>, dim3(grid), dim3(kSweepThreads),
                                      args, 0, s);
+}
+
+cudaError_t launch_wait_selftest(unsigned* words, double limit_s, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(words, (uint64_t)(limit_s * 1e9));
+  count_launch();
+  return cudaGetLastError();
 }
 
 int sector_sweep_grid(qf_dtype dt, bool adj, bool realst, uint64_t typical_items) {

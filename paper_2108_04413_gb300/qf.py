@@ -50,6 +50,7 @@ _SIGS = {
     "qf_profile_read": (ctypes.c_int, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint64), _dp]),
     "qf_profile_end": (ctypes.c_int, []),
     "qf_expectation_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _sz, _dp, _dp]),
+    "qf_selftest_bounded_wait": (ctypes.c_int, [_vp, ctypes.c_double]),
     "qf_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -92,6 +93,11 @@ K_SET, K_ROT, K_TILE, K_SPARSE, K_EXPECT, K_HPSI, K_ADJ_ROT, K_ADJ_SPARSE = (1 <
 K_ALL = 255
 KIND_NAMES = {K_SET: "set", K_ROT: "rot", K_TILE: "tile", K_SPARSE: "sparse", K_EXPECT: "expect",
               K_HPSI: "hpsi", K_ADJ_ROT: "adj_rot", K_ADJ_SPARSE: "adj_sparse"}
+
+
+def selftest_bounded_wait(stream_ptr: int, limit_s: float) -> int:
+    """Runs the bounded-wait self-test; returns the status (QF_ETIMEOUT expected)."""
+    return int(_lib.qf_selftest_bounded_wait(_vp(stream_ptr), float(limit_s)))
 
 
 def profile_begin(mask: int = K_ALL) -> None:

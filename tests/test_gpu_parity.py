@@ -356,3 +356,19 @@ def test_torch_owned_buffer():
     v = torch.view_as_complex(buf.view(-1, 2)).cpu().numpy()
     ref = pauli.rotate(pauli.basis_state(n, 3), n, 0b1010, 0b0110, 0.3)
     assert np.abs(v - ref).max() < 1e-15
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait on a word that nothing sets gives up after its limit and the
+    host reads QF_ETIMEOUT; the context keeps working afterwards."""
+    import time
+
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    assert qf.selftest_bounded_wait(stream, 0.25) == qf.QF_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    st = qf.State(6, "c128")
+    st.set_basis(3)
+    st.apply_pauli_exp(0b101, 0b010, 0.4)
+    ref = pauli.rotate(pauli.basis_state(6, 3), 6, 0b101, 0b010, 0.4)
+    assert np.abs(st.to_numpy() - ref).max() < 1e-15
