@@ -40,13 +40,15 @@ __device__ __forceinline__ V qturn(V v, unsigned k) {
   return o;
 }
 
-template <typename T, typename V>
-__device__ __forceinline__ V comb(V u, V w, T A, T B, int form) {
+// The form is a compile-time parameter: with a runtime form the compiler
+// evaluates every branch, tripling the FP64 work of the one-FMA forms.
+template <int F, typename T, typename V>
+__device__ __forceinline__ V comb(V u, V w, T A, T B) {
   V o;
-  if (form == FORM_A1) {
+  if (F == FORM_A1) {
     o.x = fma(B, w.x, u.x);
     o.y = fma(B, w.y, u.y);
-  } else if (form == FORM_B1) {
+  } else if (F == FORM_B1) {
     o.x = fma(A, u.x, w.x);
     o.y = fma(A, u.y, w.y);
   } else {
@@ -171,9 +173,9 @@ __global__ void k_scale(typename Cx<T>::V* psi, uint64_t N, T s) {
 // Each thread takes the two pairs (b, b|1) so the partner amplitudes also form
 // an aligned 2-vector (needs h >= 1).
 
-template <typename T>
+template <typename T, int F>
 __global__ void __launch_bounds__(256) k_rot_pair2(typename Cx<T>::V* __restrict__ psi, uint64_t nquads, uint64_t x,
-                                                   uint64_t z, int h, int y, T A, T B, int form) {
+                                                   uint64_t z, int h, int y, T A, T B) {
   using V = typename Cx<T>::V;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const unsigned z0 = (unsigned)(z & 1ull);
@@ -184,37 +186,37 @@ __global__ void __launch_bounds__(256) k_rot_pair2(typename Cx<T>::V* __restrict
     const V u0 = psi[b0], u1 = psi[b1];
     const V v0 = psi[c0], v1 = psi[c1];
     const unsigned p0 = par64(z & b0), p1 = p0 ^ z0;
-    psi[b0] = comb<T, V>(u0, qturn(v0, (3u + 3u * y + 2u * p0) & 3u), A, B, form);
-    psi[b1] = comb<T, V>(u1, qturn(v1, (3u + 3u * y + 2u * p1) & 3u), A, B, form);
-    psi[c0] = comb<T, V>(v0, qturn(u0, (3u + y + 2u * p0) & 3u), A, B, form);
-    psi[c1] = comb<T, V>(v1, qturn(u1, (3u + y + 2u * p1) & 3u), A, B, form);
+    psi[b0] = comb<F, T, V>(u0, qturn(v0, (3u + 3u * y + 2u * p0) & 3u), A, B);
+    psi[b1] = comb<F, T, V>(u1, qturn(v1, (3u + 3u * y + 2u * p1) & 3u), A, B);
+    psi[c0] = comb<F, T, V>(v0, qturn(u0, (3u + y + 2u * p0) & 3u), A, B);
+    psi[c1] = comb<F, T, V>(v1, qturn(u1, (3u + y + 2u * p1) & 3u), A, B);
   }
 }
 
 // x == 1: the pair is the aligned 2-vector (2q, 2q+1).
-template <typename T>
+template <typename T, int F>
 __global__ void __launch_bounds__(256) k_rot_pair1(typename Cx<T>::V* __restrict__ psi, uint64_t npairs, uint64_t z,
-                                                   int y, T A, T B, int form) {
+                                                   int y, T A, T B) {
   using V = typename Cx<T>::V;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < npairs; q += stride) {
     const uint64_t b = q << 1;
     const V u = psi[b], v = psi[b | 1ull];
     const unsigned p = par64(z & b);
-    psi[b] = comb<T, V>(u, qturn(v, (3u + 3u * y + 2u * p) & 3u), A, B, form);
-    psi[b | 1ull] = comb<T, V>(v, qturn(u, (3u + y + 2u * p) & 3u), A, B, form);
+    psi[b] = comb<F, T, V>(u, qturn(v, (3u + 3u * y + 2u * p) & 3u), A, B);
+    psi[b | 1ull] = comb<F, T, V>(v, qturn(u, (3u + y + 2u * p) & 3u), A, B);
   }
 }
 
 // x == 0: diagonal phase, out[b] = A u + B i^{3+2par} u.
-template <typename T>
+template <typename T, int F>
 __global__ void __launch_bounds__(256) k_rot_diag(typename Cx<T>::V* __restrict__ psi, uint64_t N, uint64_t z, T A,
-                                                  T B, int form) {
+                                                  T B) {
   using V = typename Cx<T>::V;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < N; b += stride) {
     const V u = psi[b];
-    psi[b] = comb<T, V>(u, qturn(u, (3u + 2u * par64(z & b)) & 3u), A, B, form);
+    psi[b] = comb<F, T, V>(u, qturn(u, (3u + 2u * par64(z & b)) & 3u), A, B);
   }
 }
 
@@ -226,6 +228,30 @@ __global__ void __launch_bounds__(256) k_rot_diag(typename Cx<T>::V* __restrict_
 // The tile is read once, all m rotations act on it in shared memory (the part
 // of z outside S only flips the sign class of the whole tile), and it is
 // written once.
+
+// One rotation of a fused pass on the staged tile.
+template <int F, typename T>
+__device__ __forceinline__ void tile_rot(typename Cx<T>::V* tile, const TileRot& R, unsigned pout, unsigned tsize, T A,
+                                         T B) {
+  using V = typename Cx<T>::V;
+  if (R.hl < 0) {
+    for (unsigned j = threadIdx.x; j < tsize; j += blockDim.x) {
+      const unsigned p = (__popc(R.zl & j) + pout) & 1u;
+      const V u = tile[j];
+      tile[j] = comb<F, T, V>(u, qturn(u, (3u + 2u * p) & 3u), A, B);
+    }
+  } else {
+    const unsigned hmask = (1u << R.hl) - 1u;
+    for (unsigned q = threadIdx.x; q < (tsize >> 1); q += blockDim.x) {
+      const unsigned j = ((q >> R.hl) << (R.hl + 1)) | (q & hmask);
+      const unsigned jp = j ^ R.xl;
+      const unsigned p = (__popc(R.zl & j) + pout) & 1u;
+      const V u = tile[j], v = tile[jp];
+      tile[j] = comb<F, T, V>(u, qturn(v, (3u + 3u * R.y + 2u * p) & 3u), A, B);
+      tile[jp] = comb<F, T, V>(v, qturn(u, (3u + R.y + 2u * p) & 3u), A, B);
+    }
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_tile(typename Cx<T>::V* __restrict__ psi, int n,
@@ -247,29 +273,19 @@ __global__ void __launch_bounds__(256) k_tile(typename Cx<T>::V* __restrict__ ps
     uint64_t base = t;
     for (int i = 0; i < s; ++i) base = ins0(base, a.sbits[i]);
     __syncthreads();
+#pragma unroll 8
     for (unsigned j = threadIdx.x; j < tsize; j += blockDim.x) tile[j] = psi[base | hitab[j >> l] | (j & lmask)];
     __syncthreads();
     for (int r = 0; r < a.m; ++r) {
       const TileRot R = a.r[r];
       const unsigned pout = par64(R.zout & base);
       const T A = (T)R.A, B = (T)R.B;
-      if (R.hl < 0) {
-        for (unsigned j = threadIdx.x; j < tsize; j += blockDim.x) {
-          const unsigned p = (__popc(R.zl & j) + pout) & 1u;
-          const V u = tile[j];
-          tile[j] = comb<T, V>(u, qturn(u, (3u + 2u * p) & 3u), A, B, R.form);
-        }
-      } else {
-        const unsigned hmask = (1u << R.hl) - 1u;
-        for (unsigned q = threadIdx.x; q < (tsize >> 1); q += blockDim.x) {
-          const unsigned j = ((q >> R.hl) << (R.hl + 1)) | (q & hmask);
-          const unsigned jp = j ^ R.xl;
-          const unsigned p = (__popc(R.zl & j) + pout) & 1u;
-          const V u = tile[j], v = tile[jp];
-          tile[j] = comb<T, V>(u, qturn(v, (3u + 3u * R.y + 2u * p) & 3u), A, B, R.form);
-          tile[jp] = comb<T, V>(v, qturn(u, (3u + R.y + 2u * p) & 3u), A, B, R.form);
-        }
-      }
+      if (R.form == FORM_A1)
+        tile_rot<FORM_A1, T>(tile, R, pout, tsize, A, B);
+      else if (R.form == FORM_B1)
+        tile_rot<FORM_B1, T>(tile, R, pout, tsize, A, B);
+      else
+        tile_rot<FORM_AB, T>(tile, R, pout, tsize, A, B);
       __syncthreads();
     }
     for (unsigned j = threadIdx.x; j < tsize; j += blockDim.x) psi[base | hitab[j >> l] | (j & lmask)] = tile[j];
@@ -738,10 +754,10 @@ __global__ void __launch_bounds__(256) k_hpsi_ds(const double2* __restrict__ psi
 // Over the pair (b, b'): <lam|P|psi> gets i^y s(b) [(-1)^y conj(lam_b) psi_b' +
 // conj(lam_b') psi_b].
 
-template <typename T>
+template <typename T, int F>
 __global__ void __launch_bounds__(256) k_adj_rot(typename Cx<T>::V* __restrict__ psi,
                                                  typename Cx<T>::V* __restrict__ lam, int n, uint64_t x, uint64_t z,
-                                                 int h, int y, T A, T B, int form, double* partials, unsigned* counter,
+                                                 int h, int y, T A, T B, double* partials, unsigned* counter,
                                                  double* out) {
   using V = typename Cx<T>::V;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -755,8 +771,8 @@ __global__ void __launch_bounds__(256) k_adj_rot(typename Cx<T>::V* __restrict__
       // Im(conj(p) s u)
       const double im = fma((double)p.x, (double)u.y, -(double)p.y * (double)u.x);
       acc += flip(im, pb);
-      psi[b] = comb<T, V>(u, qturn(u, (3u + 2u * pb) & 3u), A, B, form);
-      lam[b] = comb<T, V>(p, qturn(p, (3u + 2u * pb) & 3u), A, B, form);
+      psi[b] = comb<F, T, V>(u, qturn(u, (3u + 2u * pb) & 3u), A, B);
+      lam[b] = comb<F, T, V>(p, qturn(p, (3u + 2u * pb) & 3u), A, B);
     }
   } else {
     const uint64_t npairs = 1ull << (n - 1);
@@ -777,10 +793,10 @@ __global__ void __launch_bounds__(256) k_adj_rot(typename Cx<T>::V* __restrict__
         val = flip(r2 - r1, ((ym >> 1) & 1u) ^ pb);
       }
       acc += val;
-      psi[b] = comb<T, V>(u, qturn(v, (3u + 3u * y + 2u * pb) & 3u), A, B, form);
-      psi[bp] = comb<T, V>(v, qturn(u, (3u + y + 2u * pb) & 3u), A, B, form);
-      lam[b] = comb<T, V>(p, qturn(r, (3u + 3u * y + 2u * pb) & 3u), A, B, form);
-      lam[bp] = comb<T, V>(r, qturn(p, (3u + y + 2u * pb) & 3u), A, B, form);
+      psi[b] = comb<F, T, V>(u, qturn(v, (3u + 3u * y + 2u * pb) & 3u), A, B);
+      psi[bp] = comb<F, T, V>(v, qturn(u, (3u + y + 2u * pb) & 3u), A, B);
+      lam[b] = comb<F, T, V>(p, qturn(r, (3u + 3u * y + 2u * pb) & 3u), A, B);
+      lam[bp] = comb<F, T, V>(r, qturn(p, (3u + y + 2u * pb) & 3u), A, B);
     }
   }
   grid_finish(acc, partials, counter, out);
@@ -1023,18 +1039,28 @@ cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream
   return cudaGetLastError();
 }
 
-template <typename T>
-static void rot_impl(void* psi, int n, const RotArgs& a, cudaStream_t s) {
+template <typename T, int F>
+static void rot_impl_f(void* psi, int n, const RotArgs& a, cudaStream_t s) {
   using V = typename Cx<T>::V;
   V* p = static_cast<V*>(psi);
   const uint64_t N = 1ull << n;
   if (a.x == 0ull) {
-    k_rot_diag<T><<<grid_for(N, 8), 256, 0, s>>>(p, N, a.z, (T)a.A, (T)a.B, a.form);
+    k_rot_diag<T, F><<<grid_for(N, 8), 256, 0, s>>>(p, N, a.z, (T)a.A, (T)a.B);
   } else if (a.h == 0) {
-    k_rot_pair1<T><<<grid_for(N / 2, 8), 256, 0, s>>>(p, N / 2, a.z, a.y, (T)a.A, (T)a.B, a.form);
+    k_rot_pair1<T, F><<<grid_for(N / 2, 8), 256, 0, s>>>(p, N / 2, a.z, a.y, (T)a.A, (T)a.B);
   } else {
-    k_rot_pair2<T><<<grid_for(N / 4, 8), 256, 0, s>>>(p, N / 4, a.x, a.z, a.h, a.y, (T)a.A, (T)a.B, a.form);
+    k_rot_pair2<T, F><<<grid_for(N / 4, 8), 256, 0, s>>>(p, N / 4, a.x, a.z, a.h, a.y, (T)a.A, (T)a.B);
   }
+}
+
+template <typename T>
+static void rot_impl(void* psi, int n, const RotArgs& a, cudaStream_t s) {
+  if (a.form == FORM_A1)
+    rot_impl_f<T, FORM_A1>(psi, n, a, s);
+  else if (a.form == FORM_B1)
+    rot_impl_f<T, FORM_B1>(psi, n, a, s);
+  else
+    rot_impl_f<T, FORM_AB>(psi, n, a, s);
 }
 
 cudaError_t launch_rot(void* psi, int n, qf_dtype dt, const RotArgs& a, cudaStream_t s) {
@@ -1058,7 +1084,9 @@ static cudaError_t tile_impl(void* psi, int n, const TileArgs& a, cudaStream_t s
     attr_set = true;
   }
   const uint64_t ntiles = 1ull << (n - a.s);
-  uint64_t g = (uint64_t)sm_count() * 4;
+  int per_sm = 4;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<T>, 256, smem);
+  uint64_t g = (uint64_t)sm_count() * (uint64_t)std::max(1, per_sm);
   if (g > ntiles) g = ntiles;
   k_tile<T><<<(unsigned)g, 256, smem, s>>>(static_cast<V*>(psi), n, a);
   return cudaGetLastError();
@@ -1283,15 +1311,32 @@ cudaError_t launch_hpsi_ds(const void* psi, void* lam, void* split, int n, const
   return cudaGetLastError();
 }
 
+template <typename T, int F>
+static void adj_rot_f(void* psi, void* lam, int n, const RotArgs& a, double* partials, unsigned* counter, double* out,
+                      int nblocks, cudaStream_t s) {
+  using V = typename Cx<T>::V;
+  k_adj_rot<T, F><<<nblocks, 256, 0, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), n, a.x, a.z, a.h, a.y, (T)a.A,
+                                          (T)a.B, partials, counter, out);
+}
+
+template <typename T>
+static void adj_rot_t(void* psi, void* lam, int n, const RotArgs& a, double* partials, unsigned* counter, double* out,
+                      int nblocks, cudaStream_t s) {
+  if (a.form == FORM_A1)
+    adj_rot_f<T, FORM_A1>(psi, lam, n, a, partials, counter, out, nblocks, s);
+  else if (a.form == FORM_B1)
+    adj_rot_f<T, FORM_B1>(psi, lam, n, a, partials, counter, out, nblocks, s);
+  else
+    adj_rot_f<T, FORM_AB>(psi, lam, n, a, partials, counter, out, nblocks, s);
+}
+
 cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotArgs& a, double* partials,
                            unsigned* counter, double* out, int nblocks, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_ADJ_ROT, s);
   if (dt == QF_C128)
-    k_adj_rot<double><<<nblocks, 256, 0, s>>>(static_cast<double2*>(psi), static_cast<double2*>(lam), n, a.x, a.z,
-                                              a.h, a.y, a.A, a.B, a.form, partials, counter, out);
+    adj_rot_t<double>(psi, lam, n, a, partials, counter, out, nblocks, s);
   else
-    k_adj_rot<float><<<nblocks, 256, 0, s>>>(static_cast<float2*>(psi), static_cast<float2*>(lam), n, a.x, a.z, a.h,
-                                             a.y, (float)a.A, (float)a.B, a.form, partials, counter, out);
+    adj_rot_t<float>(psi, lam, n, a, partials, counter, out, nblocks, s);
   prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();
