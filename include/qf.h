@@ -140,6 +140,12 @@ qf_status qf_state_clear_plans(qf_state* st);
  * (reset = 1 clears the counter after reading). */
 uint64_t qf_kernel_launches(int reset);
 
+/* Bytes this thread's calls have copied host-to-device (state uploads, plan
+ * tables, block descriptors) and device-to-host (results, state downloads)
+ * since the last reset (reset = 1 clears after reading).  Either pointer may be
+ * NULL. */
+void qf_transfer_bytes(int reset, uint64_t* h2d_bytes, uint64_t* d2h_bytes);
+
 /* Kernel kinds for the timing calls below. */
 #define QF_K_SET 1u          /* basis preparation, scale folding */
 #define QF_K_ROT 2u          /* unfused rotation (one pair sweep) */

@@ -44,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and out:
             sys.stdout.write(out.decode(errors="replace"))
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed: " + r.stdout.decode(errors="replace"))

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -20,6 +21,17 @@ using cplx = std::complex<double>;
 namespace {
 
 thread_local std::string t_err;
+thread_local uint64_t t_h2d = 0, t_d2h = 0;  // bytes this thread's calls copied each way
+
+cudaError_t h2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  t_h2d += bytes;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t d2h(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  t_d2h += bytes;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+}
 
 qf_status fail(qf_status s, const std::string& msg) {
   t_err = msg;
@@ -55,6 +67,8 @@ struct ExpPlan {
   qf::SecRank rk{};
   qf::HClass* d_classes[qf::kClassTbN] = {};  // classes for tile bits 10, 11, 12
   int nclasses[qf::kClassTbN] = {};
+  bool tiled = false;                // tiled H|psi> tables built (on first use)
+  std::vector<qf_term> terms;        // the plan's terms, for building the tiled tables later
   bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
 };
 
@@ -254,6 +268,99 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   p.nchunks = (int)ech.size();
   for (const qf::ExpGroup& g : groups)
     if (g.flags & 2) p.has_odd = true;
+  // sector groups: a group flips popc(x & even) even qubits; it links two members of
+  // one sector only when that count (and the odd one) is even
+  std::vector<qf::SecGroup> sg;
+  for (const qf::ExpGroup& g : groups) {
+    const int xe = popc(g.x & kEvenMask), xo = popc(g.x & ~kEvenMask);
+    if ((xe & 1) || (xo & 1)) continue;
+    sg.push_back(qf::SecGroup{g.x, xe, xo, g.chunk0, g.nchunk});
+  }
+  p.nsecgroups = (int)sg.size();
+  // lookup tables by flipped spin orbitals (local index i of qubit 2i or 2i+1)
+  const int nq = st->n, ne = (nq + 1) / 2, no = nq / 2;
+  const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
+  const size_t o_sa = 0, o_sb = o_sa + (size_t)ne * ne, o_aa = o_sb + (size_t)no * no,
+               o_bb = o_aa + (size_t)pe * pe, o_ab = o_bb + (size_t)po * po,
+               n_rk = o_ab + (size_t)ne * ne * no * no;
+  std::vector<int> rkt(std::max<size_t>(1, n_rk), -1);
+  std::vector<qf::SecGroup> lg;
+  int diag = -1;
+  auto pr = [](int i, int j) { return i + j * (j - 1) / 2; };  // i < j
+  for (size_t gi = 0; gi < sg.size(); ++gi) {
+    const uint64_t x = sg[gi].x;
+    const int w = popc(x);
+    std::vector<int> ev, od;
+    for (int q = 0; q < nq; ++q)
+      if ((x >> q) & 1) ((q & 1) ? od : ev).push_back(q >> 1);
+    if (w == 0) {
+      diag = (int)gi;
+      continue;
+    }
+    // each flip set is recorded under every occupied/empty split that a member can present
+    if (w == 2 && ev.size() == 2) {
+      rkt[o_sa + ev[0] * ne + ev[1]] = (int)gi;
+      rkt[o_sa + ev[1] * ne + ev[0]] = (int)gi;
+    } else if (w == 2 && od.size() == 2) {
+      rkt[o_sb + od[0] * no + od[1]] = (int)gi;
+      rkt[o_sb + od[1] * no + od[0]] = (int)gi;
+    } else if (w == 4 && (ev.size() == 4 || od.size() == 4)) {
+      const std::vector<int>& v = ev.size() == 4 ? ev : od;
+      const size_t off = ev.size() == 4 ? o_aa : o_bb;
+      const int P = ev.size() == 4 ? pe : po;
+      const int pairs[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
+      for (const auto& q : pairs) {
+        const int r1 = pr(v[q[0]], v[q[1]]), r2 = pr(v[q[2]], v[q[3]]);
+        rkt[off + (size_t)r1 * P + r2] = (int)gi;
+        rkt[off + (size_t)r2 * P + r1] = (int)gi;
+      }
+    } else if (w == 4 && ev.size() == 2) {
+      for (int s0 = 0; s0 < 2; ++s0)
+        for (int s1 = 0; s1 < 2; ++s1)
+          rkt[o_ab + (((size_t)ev[s0] * ne + ev[1 - s0]) * no + od[s1]) * no + od[1 - s1]] = (int)gi;
+    } else {
+      lg.push_back(sg[gi]);
+    }
+  }
+  p.nseclarge = (int)lg.size();
+  if (p.ngroups > 0) {
+    if (cudaMalloc(&p.d_groups, groups.size() * sizeof(qf::ExpGroup)) != cudaSuccess ||
+        cudaMalloc(&p.d_echunks, ech.size() * sizeof(qf::ExpChunk)) != cudaSuccess ||
+        cudaMalloc(&p.d_hchunks, hch.size() * sizeof(qf::ExpChunk)) != cudaSuccess) {
+      cudaFree(p.d_groups);
+      cudaFree(p.d_echunks);
+      cudaFree(p.d_hchunks);
+      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
+    }
+    QF_CUDA(h2d(p.d_groups, groups.data(), groups.size() * sizeof(qf::ExpGroup), st->stream));
+    QF_CUDA(h2d(p.d_echunks, ech.data(), ech.size() * sizeof(qf::ExpChunk), st->stream));
+    QF_CUDA(h2d(p.d_hchunks, hch.data(), hch.size() * sizeof(qf::ExpChunk), st->stream));
+    if (cudaMalloc(&p.d_secgroups, std::max<size_t>(1, sg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
+        cudaMalloc(&p.d_seclarge, std::max<size_t>(1, lg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
+        cudaMalloc(&p.d_rk, rkt.size() * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(p);
+      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
+    }
+    if (!sg.empty()) QF_CUDA(h2d(p.d_secgroups, sg.data(), sg.size() * sizeof(qf::SecGroup), st->stream));
+    if (!lg.empty()) QF_CUDA(h2d(p.d_seclarge, lg.data(), lg.size() * sizeof(qf::SecGroup), st->stream));
+    QF_CUDA(h2d(p.d_rk, rkt.data(), rkt.size() * sizeof(int), st->stream));
+    p.rk = qf::SecRank{p.d_rk + o_sa, p.d_rk + o_sb, p.d_rk + o_aa, p.d_rk + o_bb, p.d_rk + o_ab, diag, ne, no};
+    QF_CUDA(cudaStreamSynchronize(st->stream));
+  }
+  p.terms.assign(terms, terms + nt);
+  auto res = st->plans.emplace(key, std::move(p));
+  *out = &res.first->second;
+  return QF_OK;
+}
+
+// Tables of the tiled H|psi> kernels, built the first time a plan needs them.
+qf_status ensure_tiled(qf_state* st, ExpPlan* pp) {
+  if (pp->tiled) return QF_OK;
+  ExpPlan& p = *pp;
+  const qf_term* terms = p.terms.data();
+  std::map<uint64_t, std::vector<size_t>> byx;
+  for (size_t i = 0; i < p.terms.size(); ++i) byx[terms[i].x].push_back(i);
   // tiled H|psi> tables: D_g(b) = sum_t c_t i^{y_t} s_t(b), eight terms per table
   std::vector<qf::HGroup> hg;
   std::vector<qf::WChunk> wc;
@@ -313,61 +420,6 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     }
     hg.push_back(g);
   }
-  // sector groups: a group flips popc(x & even) even qubits; it links two members of
-  // one sector only when that count (and the odd one) is even
-  std::vector<qf::SecGroup> sg;
-  for (const qf::ExpGroup& g : groups) {
-    const int xe = popc(g.x & kEvenMask), xo = popc(g.x & ~kEvenMask);
-    if ((xe & 1) || (xo & 1)) continue;
-    sg.push_back(qf::SecGroup{g.x, xe, xo, g.chunk0, g.nchunk});
-  }
-  p.nsecgroups = (int)sg.size();
-  // lookup tables by flipped spin orbitals (local index i of qubit 2i or 2i+1)
-  const int nq = st->n, ne = (nq + 1) / 2, no = nq / 2;
-  const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
-  const size_t o_sa = 0, o_sb = o_sa + (size_t)ne * ne, o_aa = o_sb + (size_t)no * no,
-               o_bb = o_aa + (size_t)pe * pe, o_ab = o_bb + (size_t)po * po,
-               n_rk = o_ab + (size_t)ne * ne * no * no;
-  std::vector<int> rkt(std::max<size_t>(1, n_rk), -1);
-  std::vector<qf::SecGroup> lg;
-  int diag = -1;
-  auto pr = [](int i, int j) { return i + j * (j - 1) / 2; };  // i < j
-  for (size_t gi = 0; gi < sg.size(); ++gi) {
-    const uint64_t x = sg[gi].x;
-    const int w = popc(x);
-    std::vector<int> ev, od;
-    for (int q = 0; q < nq; ++q)
-      if ((x >> q) & 1) ((q & 1) ? od : ev).push_back(q >> 1);
-    if (w == 0) {
-      diag = (int)gi;
-      continue;
-    }
-    // each flip set is recorded under every occupied/empty split that a member can present
-    if (w == 2 && ev.size() == 2) {
-      rkt[o_sa + ev[0] * ne + ev[1]] = (int)gi;
-      rkt[o_sa + ev[1] * ne + ev[0]] = (int)gi;
-    } else if (w == 2 && od.size() == 2) {
-      rkt[o_sb + od[0] * no + od[1]] = (int)gi;
-      rkt[o_sb + od[1] * no + od[0]] = (int)gi;
-    } else if (w == 4 && (ev.size() == 4 || od.size() == 4)) {
-      const std::vector<int>& v = ev.size() == 4 ? ev : od;
-      const size_t off = ev.size() == 4 ? o_aa : o_bb;
-      const int P = ev.size() == 4 ? pe : po;
-      const int pairs[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
-      for (const auto& q : pairs) {
-        const int r1 = pr(v[q[0]], v[q[1]]), r2 = pr(v[q[2]], v[q[3]]);
-        rkt[off + (size_t)r1 * P + r2] = (int)gi;
-        rkt[off + (size_t)r2 * P + r1] = (int)gi;
-      }
-    } else if (w == 4 && ev.size() == 2) {
-      for (int s0 = 0; s0 < 2; ++s0)
-        for (int s1 = 0; s1 < 2; ++s1)
-          rkt[o_ab + (((size_t)ev[s0] * ne + ev[1 - s0]) * no + od[s1]) * no + od[1 - s1]] = (int)gi;
-    } else {
-      lg.push_back(sg[gi]);
-    }
-  }
-  p.nseclarge = (int)lg.size();
   std::vector<qf::HClass> cls[qf::kClassTbN];
   for (int v = 0; v < qf::kClassTbN; ++v) {
     const int tb = qf::kClassTb0 + v;
@@ -378,62 +430,24 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     }
     p.nclasses[v] = (int)cls[v].size();
   }
-  if (p.ngroups > 0) {
-    if (cudaMalloc(&p.d_groups, groups.size() * sizeof(qf::ExpGroup)) != cudaSuccess ||
-        cudaMalloc(&p.d_echunks, ech.size() * sizeof(qf::ExpChunk)) != cudaSuccess ||
-        cudaMalloc(&p.d_hchunks, hch.size() * sizeof(qf::ExpChunk)) != cudaSuccess) {
-      cudaFree(p.d_groups);
-      cudaFree(p.d_echunks);
-      cudaFree(p.d_hchunks);
-      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
-    }
-    QF_CUDA(cudaMemcpyAsync(p.d_groups, groups.data(), groups.size() * sizeof(qf::ExpGroup), cudaMemcpyHostToDevice,
-                            st->stream));
-    QF_CUDA(cudaMemcpyAsync(p.d_echunks, ech.data(), ech.size() * sizeof(qf::ExpChunk), cudaMemcpyHostToDevice,
-                            st->stream));
-    QF_CUDA(cudaMemcpyAsync(p.d_hchunks, hch.data(), hch.size() * sizeof(qf::ExpChunk), cudaMemcpyHostToDevice,
-                            st->stream));
-    if (cudaMalloc(&p.d_hgroups, hg.size() * sizeof(qf::HGroup)) != cudaSuccess ||
-        cudaMalloc(&p.d_wchunks, wc.size() * sizeof(qf::WChunk)) != cudaSuccess ||
-        cudaMalloc(&p.d_wchunks_f, wf.size() * sizeof(qf::WChunkF)) != cudaSuccess ||
-        cudaMalloc(&p.d_wchunks_s, ws.size() * sizeof(qf::WChunkS)) != cudaSuccess ||
-        cudaMalloc(&p.d_classes[0], cls[0].size() * sizeof(qf::HClass)) != cudaSuccess ||
-        cudaMalloc(&p.d_classes[1], cls[1].size() * sizeof(qf::HClass)) != cudaSuccess ||
-        cudaMalloc(&p.d_classes[2], cls[2].size() * sizeof(qf::HClass)) != cudaSuccess) {
-      cudaGetLastError();
-      free_plan(p);
-      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
-    }
-    QF_CUDA(cudaMemcpyAsync(p.d_hgroups, hg.data(), hg.size() * sizeof(qf::HGroup), cudaMemcpyHostToDevice,
-                            st->stream));
-    if (cudaMalloc(&p.d_secgroups, std::max<size_t>(1, sg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
-        cudaMalloc(&p.d_seclarge, std::max<size_t>(1, lg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
-        cudaMalloc(&p.d_rk, rkt.size() * sizeof(int)) != cudaSuccess) {
-      cudaGetLastError();
-      free_plan(p);
-      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
-    }
-    if (!sg.empty())
-      QF_CUDA(cudaMemcpyAsync(p.d_secgroups, sg.data(), sg.size() * sizeof(qf::SecGroup), cudaMemcpyHostToDevice,
-                              st->stream));
-    if (!lg.empty())
-      QF_CUDA(cudaMemcpyAsync(p.d_seclarge, lg.data(), lg.size() * sizeof(qf::SecGroup), cudaMemcpyHostToDevice,
-                              st->stream));
-    QF_CUDA(cudaMemcpyAsync(p.d_rk, rkt.data(), rkt.size() * sizeof(int), cudaMemcpyHostToDevice, st->stream));
-    p.rk = qf::SecRank{p.d_rk + o_sa, p.d_rk + o_sb, p.d_rk + o_aa, p.d_rk + o_bb, p.d_rk + o_ab, diag, ne, no};
-    QF_CUDA(cudaMemcpyAsync(p.d_wchunks, wc.data(), wc.size() * sizeof(qf::WChunk), cudaMemcpyHostToDevice,
-                            st->stream));
-    QF_CUDA(cudaMemcpyAsync(p.d_wchunks_f, wf.data(), wf.size() * sizeof(qf::WChunkF), cudaMemcpyHostToDevice,
-                            st->stream));
-    QF_CUDA(cudaMemcpyAsync(p.d_wchunks_s, ws.data(), ws.size() * sizeof(qf::WChunkS), cudaMemcpyHostToDevice,
-                            st->stream));
-    for (int v = 0; v < qf::kClassTbN; ++v)
-      QF_CUDA(cudaMemcpyAsync(p.d_classes[v], cls[v].data(), cls[v].size() * sizeof(qf::HClass),
-                              cudaMemcpyHostToDevice, st->stream));
-    QF_CUDA(cudaStreamSynchronize(st->stream));
+  if (cudaMalloc(&p.d_hgroups, std::max<size_t>(1, hg.size()) * sizeof(qf::HGroup)) != cudaSuccess ||
+      cudaMalloc(&p.d_wchunks, std::max<size_t>(1, wc.size()) * sizeof(qf::WChunk)) != cudaSuccess ||
+      cudaMalloc(&p.d_wchunks_f, std::max<size_t>(1, wf.size()) * sizeof(qf::WChunkF)) != cudaSuccess ||
+      cudaMalloc(&p.d_wchunks_s, std::max<size_t>(1, ws.size()) * sizeof(qf::WChunkS)) != cudaSuccess ||
+      cudaMalloc(&p.d_classes[0], std::max<size_t>(1, cls[0].size()) * sizeof(qf::HClass)) != cudaSuccess ||
+      cudaMalloc(&p.d_classes[1], std::max<size_t>(1, cls[1].size()) * sizeof(qf::HClass)) != cudaSuccess ||
+      cudaMalloc(&p.d_classes[2], std::max<size_t>(1, cls[2].size()) * sizeof(qf::HClass)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QF_ENOMEM, "cudaMalloc(tiled plan) failed");
   }
-  auto res = st->plans.emplace(key, p);
-  *out = &res.first->second;
+  QF_CUDA(h2d(p.d_hgroups, hg.data(), hg.size() * sizeof(qf::HGroup), st->stream));
+  QF_CUDA(h2d(p.d_wchunks, wc.data(), wc.size() * sizeof(qf::WChunk), st->stream));
+  QF_CUDA(h2d(p.d_wchunks_f, wf.data(), wf.size() * sizeof(qf::WChunkF), st->stream));
+  QF_CUDA(h2d(p.d_wchunks_s, ws.data(), ws.size() * sizeof(qf::WChunkS), st->stream));
+  for (int v = 0; v < qf::kClassTbN; ++v)
+    QF_CUDA(h2d(p.d_classes[v], cls[v].data(), cls[v].size() * sizeof(qf::HClass), st->stream));
+  QF_CUDA(cudaStreamSynchronize(st->stream));
+  p.tiled = true;
   return QF_OK;
 }
 
@@ -780,8 +794,7 @@ qf_status flush_sector(qf_state* st, std::vector<qf::SecBlk>& pend) {
   const int grid = qf::sector_sweep_grid(st->dt, false, true, typical_items(pend.data(), pend.size()));
   qf_status bs = ensure_sector_buffers(st, pend.size(), 1);
   if (bs != QF_OK) return bs;
-  QF_CUDA(cudaMemcpyAsync(st->d_secblk, pend.data(), pend.size() * sizeof(qf::SecBlk), cudaMemcpyHostToDevice,
-                          st->stream));
+  QF_CUDA(h2d(st->d_secblk, pend.data(), pend.size() * sizeof(qf::SecBlk), st->stream));
   QF_CUDA(qf::launch_sector_sweep(st->psi, nullptr, st->dt, false, st->real, st->d_secblk, (int)pend.size(),
                                   st->d_bar, st->d_sec_partial, nullptr, grid, st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));  // the descriptor buffer is reused by the next flush
@@ -980,7 +993,7 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
     QF_CUDA(qf::launch_expect(st->psi, st->n, st->dt, p->d_groups, p->ngroups, p->d_echunks, st->d_partials,
                               st->d_counter, st->d_out, nb, st->stream));
   }
-  QF_CUDA(cudaMemcpyAsync(st->h_out, st->d_out, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  QF_CUDA(d2h(st->h_out, st->d_out, sizeof(double), st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));
   *re = st->h_out[0] * st->scale * st->scale;
   return QF_OK;
@@ -1021,21 +1034,57 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   if (ait == st->ansatz_plans.end()) {
     // first sight of this ansatz: find the sparse blocks (the active rows of a block
     // do not depend on the angles, so the structure is kept and only M is refilled)
-    std::vector<Blk> bl;
+    // candidate runs (assuming every run becomes a block), built in parallel
+    std::vector<std::pair<size_t, int>> runs;
     for (size_t i = 0; i < n_rot;) {
       const int run = sparse_run(r.data(), i, n_rot, par.data());
-      Blk b;
-      b.i = i;
-      b.sparse = false;
-      if (run >= 2 && build_sparse(&r[i], run, st->n, false, true, &b.fwd) &&
-          build_sparse(&r[i], run, st->n, true, true, &b.inv) && b.fwd.nr == b.inv.nr) {
-        b.sparse = true;
+      runs.emplace_back(i, run);
+      i += run;
+    }
+    std::vector<Blk> cand(runs.size());
+    std::vector<char> ok(runs.size(), 0);
+    auto work = [&](size_t t0, size_t step) {
+      for (size_t k = t0; k < runs.size(); k += step) {
+        const size_t i = runs[k].first;
+        const int run = runs[k].second;
+        Blk& b = cand[k];
+        b.i = i;
         b.j = i + run;
-      } else {
-        b.j = i + 1;
+        b.sparse = run >= 2 && build_sparse(&r[i], run, st->n, false, true, &b.fwd) &&
+                   build_sparse(&r[i], run, st->n, true, true, &b.inv) && b.fwd.nr == b.inv.nr;
+        ok[k] = b.sparse;
       }
-      bl.push_back(b);
-      i = b.j;
+    };
+    const size_t nth = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
+    if (runs.size() >= 64 && nth > 1) {
+      std::vector<std::thread> th;
+      for (size_t t = 0; t < nth; ++t) th.emplace_back(work, t, nth);
+      for (auto& x : th) x.join();
+    } else {
+      work(0, 1);
+    }
+    // assemble in order; a run that is not a sparse block is walked rotation by rotation
+    std::vector<Blk> bl;
+    for (size_t k = 0; k < runs.size(); ++k) {
+      if (ok[k]) {
+        bl.push_back(cand[k]);
+        continue;
+      }
+      for (size_t i = runs[k].first; i < runs[k].first + runs[k].second;) {
+        const int run = sparse_run(r.data(), i, runs[k].first + runs[k].second, par.data());
+        Blk b;
+        b.i = i;
+        b.sparse = false;
+        if (run >= 2 && build_sparse(&r[i], run, st->n, false, true, &b.fwd) &&
+            build_sparse(&r[i], run, st->n, true, true, &b.inv) && b.fwd.nr == b.inv.nr) {
+          b.sparse = true;
+          b.j = i + run;
+        } else {
+          b.j = i + 1;
+        }
+        bl.push_back(b);
+        i = b.j;
+      }
     }
     ait = st->ansatz_plans.emplace(akey, std::move(bl)).first;
   } else {
@@ -1077,8 +1126,7 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
       st->sec_a = na;
       st->sec_b = nbeta;
       QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
-      QF_CUDA(cudaMemcpyAsync(st->d_secblk, sec.data(), sec.size() * sizeof(qf::SecBlk), cudaMemcpyHostToDevice,
-                              st->stream));
+      QF_CUDA(h2d(st->d_secblk, sec.data(), sec.size() * sizeof(qf::SecBlk), st->stream));
       QF_CUDA(qf::launch_sector_sweep(st->psi, nullptr, st->dt, false, true, st->d_secblk, (int)nblk, st->d_bar,
                                       st->d_sec_partial, nullptr, grid_f, st->stream));
       double* d_e = st->d_out + nblk;
@@ -1093,8 +1141,7 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
       } else {
         QF_CUDA(cudaMemsetAsync(st->d_out, 0, (nblk + 2) * sizeof(double), st->stream));
       }
-      QF_CUDA(cudaMemcpyAsync(st->h_out, st->d_out, (nblk + 2) * sizeof(double), cudaMemcpyDeviceToHost,
-                              st->stream));
+      QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2) * sizeof(double), st->stream));
       QF_CUDA(cudaStreamSynchronize(st->stream));
       qf_status bc = check_barrier(st);
       if (bc != QF_OK) return bc;
@@ -1125,6 +1172,10 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   const int nb = qf::reduce_blocks(n, st->dt);
   double* d_e = st->d_out + blocks.size();
   const bool hreal = st->real && p && !p->has_odd;
+  if (p && n >= 10) {
+    qf_status ts = ensure_tiled(st, const_cast<ExpPlan*>(p));
+    if (ts != QF_OK) return ts;
+  }
   if (p && n >= 12 && hreal && st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS) {
     if (!st->split && cudaMalloc(&st->split, sizeof(float2) << n) != cudaSuccess) {
       cudaGetLastError();
@@ -1169,8 +1220,7 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   }
   st->scale = sc;
   st->real = both_real;
-  QF_CUDA(cudaMemcpyAsync(st->h_out, st->d_out, (blocks.size() + 2) * sizeof(double), cudaMemcpyDeviceToHost,
-                          st->stream));
+  QF_CUDA(d2h(st->h_out, st->d_out, (blocks.size() + 2) * sizeof(double), st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));
   // U(t)|det> has unit norm; dividing by the computed <psi|psi> (FP64) removes the
   // rounding drift of the stored norm (the Rayleigh quotient and its gradient;
@@ -1204,7 +1254,7 @@ qf_status qf_state_copy_to_host(qf_state* st, void* host, size_t bytes) {
   if (bytes != st->bytes()) return fail(QF_EINVAL, "byte count does not match the state");
   qf_status f = qf_state_fold_scale(st);
   if (f != QF_OK) return f;
-  QF_CUDA(cudaMemcpyAsync(host, st->psi, bytes, cudaMemcpyDeviceToHost, st->stream));
+  QF_CUDA(d2h(host, st->psi, bytes, st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));
   return QF_OK;
 }
@@ -1212,7 +1262,7 @@ qf_status qf_state_copy_to_host(qf_state* st, void* host, size_t bytes) {
 qf_status qf_state_copy_from_host(qf_state* st, const void* host, size_t bytes) {
   if (!st || !host) return fail(QF_EINVAL, "NULL argument");
   if (bytes != st->bytes()) return fail(QF_EINVAL, "byte count does not match the state");
-  QF_CUDA(cudaMemcpyAsync(st->psi, host, bytes, cudaMemcpyHostToDevice, st->stream));
+  QF_CUDA(h2d(st->psi, host, bytes, st->stream));
   st->scale = 1.0;
   st->real = false;
   st->sec_a = st->sec_b = -1;
@@ -1252,6 +1302,12 @@ qf_status qf_selftest_bounded_wait(void* stream, double limit_s) {
   if (e != cudaSuccess) return fail(QF_ECUDA, std::string("bounded-wait self-test: ") + cudaGetErrorString(e));
   if (h[2]) return fail(QF_ETIMEOUT, "bounded wait gave up after its limit (expected)");
   return fail(QF_ECUDA, "bounded wait returned without a timeout");
+}
+
+void qf_transfer_bytes(int reset, uint64_t* h2d_bytes, uint64_t* d2h_bytes) {
+  if (h2d_bytes) *h2d_bytes = t_h2d;
+  if (d2h_bytes) *d2h_bytes = t_d2h;
+  if (reset) t_h2d = t_d2h = 0;
 }
 
 qf_status qf_profile_begin(unsigned kind_mask) {

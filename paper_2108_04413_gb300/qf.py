@@ -46,6 +46,7 @@ _SIGS = {
     "qf_state_clear_plans": (ctypes.c_int, [_vp]),
     "qf_state_set_hpsi_mode": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qf_kernel_launches": (ctypes.c_uint64, [ctypes.c_int]),
+    "qf_transfer_bytes": (None, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "qf_profile_begin": (ctypes.c_int, [ctypes.c_uint]),
     "qf_profile_read": (ctypes.c_int, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint64), _dp]),
     "qf_profile_end": (ctypes.c_int, []),
@@ -70,6 +71,13 @@ class QFError(RuntimeError):
 def _check(status: int) -> None:
     if status != QF_OK:
         raise QFError(status, _lib.qf_last_error().decode(errors="replace"))
+
+
+def transfer_bytes(reset: bool = False):
+    """(host-to-device, device-to-host) bytes copied by this thread's calls."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _lib.qf_transfer_bytes(1 if reset else 0, ctypes.byref(a), ctypes.byref(b))
+    return int(a.value), int(b.value)
 
 
 QF_NOALLOC_MAX_TERMS = 2048
