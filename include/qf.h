@@ -95,10 +95,12 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
  * dE/dtheta_k.  U(t)|Phi> has unit norm; the returned energy and gradient are
  * divided by the computed <psi|psi> (FP64), which removes the rounding drift of
  * the stored norm (it matters for QF_C64 states).  grad has n_par entries.  The
- * reverse sweep undoes the circuit,
- * so on return the state holds |det> again up to rounding (call
- * qf_apply_circuit to rebuild U(t)|Phi>).  A second state-sized device buffer
- * (lambda = H psi) is allocated on the first call and kept with the handle.
+ * reverse sweep undoes the circuit, so on return the state holds |det> again
+ * up to rounding (call qf_apply_circuit to rebuild U(t)|Phi>); when every
+ * block keeps the reference's alpha and beta occupation counts it holds |det>
+ * exactly.  A second state-sized device buffer (lambda = H psi) is allocated
+ * on the first call that needs one and kept with the handle; a real lambda on
+ * that sector path is kept in psi's imaginary slots and needs none.
  * Synchronises the stream. */
 qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
                          size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad);

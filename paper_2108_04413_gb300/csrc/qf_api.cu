@@ -122,6 +122,12 @@ struct qf_state {
   double* d_sec_partial = nullptr;  // reverse-sweep overlaps per block and CTA
   size_t sec_partial_cap = 0;
   unsigned* d_bar = nullptr;        // grid barrier words
+  // compact sector layout of qf_energy_grad: rank tables of sector (rank_n,
+  // rank_a, rank_b) and the compact psi / lambda buffer
+  uint16_t* d_rank = nullptr;
+  int rank_n = -1, rank_a = -1, rank_b = -1;
+  void* d_cstate = nullptr;
+  size_t cstate_cap = 0;
   int hpsi_mode = QF_HPSI_DS;
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
@@ -144,6 +150,15 @@ struct qf_state {
 namespace {
 
 constexpr int kPartials = 4096;
+
+// Bits of mask on qubits of parity par (0 even / alpha, 1 odd / beta), as local
+// spin-orbital indices: qubit q -> bit q >> 1.
+uint32_t local_bits(uint64_t mask, int par) {
+  uint32_t out = 0;
+  for (int q = par; q < 64; q += 2)
+    if ((mask >> q) & 1ull) out |= 1u << (q >> 1);
+  return out;
+}
 
 // Largest |log2 scale| kept aside before it is folded back into the amplitudes.
 double scale_limit(qf_dtype dt) { return dt == QF_C128 ? 400.0 : 30.0; }
@@ -274,7 +289,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   for (const qf::ExpGroup& g : groups) {
     const int xe = popc(g.x & kEvenMask), xo = popc(g.x & ~kEvenMask);
     if ((xe & 1) || (xo & 1)) continue;
-    sg.push_back(qf::SecGroup{g.x, xe, xo, g.chunk0, g.nchunk});
+    sg.push_back(qf::SecGroup{g.x, xe, xo, g.chunk0, g.nchunk, local_bits(g.x, 0), local_bits(g.x, 1)});
   }
   p.nsecgroups = (int)sg.size();
   // lookup tables by flipped spin orbitals (local index i of qubit 2i or 2i+1)
@@ -668,6 +683,11 @@ bool to_secblk(const qf::SparseArgs& a, int n, int na, int nb, bool need_q, qf::
   o->zc[0] = a.zc[0];
   o->zc[1] = a.zc[1];
   o->nzc = a.nzc;
+  for (int i = 0; i < 2; ++i)
+    for (int par = 0; par < 2; ++par) {
+      o->pl[i][par] = local_bits(o->pat[i], par);
+      o->zl[i][par] = local_bits(o->zc[i], par);
+    }
   for (int c = 0; c < qf::kSparseMaxCls; ++c)
     for (int i = 0; i < 2; ++i)
       for (int j = 0; j < 2; ++j) {
@@ -691,6 +711,61 @@ qf::SecSpace sector_space(int n, int na, int nb) {
   sp.cnt_e = binom(sp.ne, na);
   sp.cnt_o = binom(sp.no, nb);
   return sp;
+}
+
+// Colex rank of a k-subset mask among all k-subsets: sum over its set bits,
+// taken in increasing position p_1 < p_2 < ..., of C(p_i, i).
+uint32_t colex_rank(uint32_t mask) {
+  uint32_t r = 0;
+  int i = 0;
+  for (int p = 0; p < 32; ++p)
+    if ((mask >> p) & 1u) r += binom(p, ++i);
+  return r;
+}
+
+// Compact index of basis state det in its sector (SecCompact ordering).
+uint64_t compact_of(uint64_t det, const qf::SecSpace& sp) {
+  return (uint64_t)colex_rank(local_bits(det, 0)) * sp.cnt_o + colex_rank(local_bits(det, 1));
+}
+
+// Rank tables of sector (na, nb) and a compact buffer of 2 * members amplitudes.
+qf_status ensure_compact(qf_state* st, const qf::SecSpace& sp, int na, int nb, qf::SecCompact* cm) {
+  const size_t ea = (size_t)1 << sp.ne, eb = (size_t)1 << sp.no;
+  if (st->rank_n != st->n || st->rank_a != na || st->rank_b != nb) {
+    std::vector<uint16_t> t(ea + eb, 0xFFFFu);  // entries of other popcounts are never read
+    for (size_t m = 0; m < ea; ++m)
+      if (popc(m) == na) t[m] = (uint16_t)colex_rank((uint32_t)m);
+    for (size_t m = 0; m < eb; ++m)
+      if (popc(m) == nb) t[ea + m] = (uint16_t)colex_rank((uint32_t)m);
+    cudaFree(st->d_rank);
+    st->d_rank = nullptr;
+    st->rank_n = -1;
+    if (cudaMalloc(&st->d_rank, t.size() * sizeof(uint16_t)) != cudaSuccess) {
+      cudaGetLastError();
+      st->d_rank = nullptr;
+      return fail(QF_ENOMEM, "cudaMalloc(sector rank tables) failed");
+    }
+    QF_CUDA(h2d(st->d_rank, t.data(), t.size() * sizeof(uint16_t), st->stream));
+    st->rank_n = st->n;
+    st->rank_a = na;
+    st->rank_b = nb;
+  }
+  const size_t need = 2 * (size_t)sp.cnt_e * sp.cnt_o * st->elem();
+  if (need > st->cstate_cap) {
+    cudaFree(st->d_cstate);
+    st->d_cstate = nullptr;
+    st->cstate_cap = 0;
+    if (cudaMalloc(&st->d_cstate, need) != cudaSuccess) {
+      cudaGetLastError();
+      st->d_cstate = nullptr;
+      return fail(QF_ENOMEM, "cudaMalloc(compact sector state) failed");
+    }
+    st->cstate_cap = need;
+  }
+  cm->ra = st->d_rank;
+  cm->rb = st->d_rank + ea;
+  cm->cnt_o = sp.cnt_o;
+  return QF_OK;
 }
 
 qf_status ensure_sector_buffers(qf_state* st, size_t nblk, size_t partials) {
@@ -796,7 +871,7 @@ qf_status flush_sector(qf_state* st, std::vector<qf::SecBlk>& pend) {
   if (bs != QF_OK) return bs;
   QF_CUDA(h2d(st->d_secblk, pend.data(), pend.size() * sizeof(qf::SecBlk), st->stream));
   QF_CUDA(qf::launch_sector_sweep(st->psi, nullptr, st->dt, false, st->real, st->d_secblk, (int)pend.size(),
-                                  st->d_bar, st->d_sec_partial, nullptr, grid, st->stream));
+                                  st->d_bar, st->d_sec_partial, nullptr, grid, qf::SecCompact{}, st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));  // the descriptor buffer is reused by the next flush
   pend.clear();
   return check_barrier(st);
@@ -922,6 +997,8 @@ qf_status qf_state_destroy(qf_state* st) {
   cudaFree(st->d_secblk);
   cudaFree(st->d_sec_partial);
   cudaFree(st->d_bar);
+  cudaFree(st->d_rank);
+  cudaFree(st->d_cstate);
   cudaFree(st->d_partials);
   cudaFree(st->d_counter);
   cudaFree(st->d_out);
@@ -988,7 +1065,7 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
     const qf::SecSpace sp = sector_space(st->n, st->sec_a, st->sec_b);
     QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, p->rk, p->d_secgroups,
                                    p->d_seclarge, p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter,
-                                   st->d_out, nb, st->stream));
+                                   st->d_out, nb, qf::SecCompact{}, st->stream));
   } else {
     QF_CUDA(qf::launch_expect(st->psi, st->n, st->dt, p->d_groups, p->ngroups, p->d_echunks, st->d_partials,
                               st->d_counter, st->d_out, nb, st->stream));
@@ -996,6 +1073,16 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
   QF_CUDA(d2h(st->h_out, st->d_out, sizeof(double), st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));
   *re = st->h_out[0] * st->scale * st->scale;
+  return QF_OK;
+}
+
+// The lambda buffer, allocated on first need and kept with the handle.
+static qf_status ensure_lam(qf_state* st) {
+  if (!st->lam && cudaMalloc(&st->lam, st->bytes()) != cudaSuccess) {
+    cudaGetLastError();
+    st->lam = nullptr;
+    return fail(QF_ENOMEM, "cudaMalloc(lambda) failed");
+  }
   return QF_OK;
 }
 
@@ -1020,11 +1107,6 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   for (size_t k = 0; k < n_terms; ++k) {
     qf_status v = validate_masks(st, terms[k].x, terms[k].z);
     if (v != QF_OK) return v;
-  }
-  if (!st->lam && cudaMalloc(&st->lam, st->bytes()) != cudaSuccess) {
-    cudaGetLastError();
-    st->lam = nullptr;
-    return fail(QF_ENOMEM, "cudaMalloc(lambda) failed");
   }
   // block structure: sparse composite blocks (same X, same parameter, commuting) or single rotations
   using Blk = qf_state::Blk;
@@ -1105,7 +1187,8 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   const int n = st->n;
   // Sector path: every block is a two-row excitation that keeps the reference's
   // numbers of occupied even and odd qubits, so the whole evaluation runs on the
-  // members of that sector (five launches).
+  // members of that sector, stored contiguously (compact layout) in a buffer of
+  // the handle; psi itself is only reset to |det> at the end.
   {
     const int na = popc(det & kEvenMask), nbeta = popc(det & ~kEvenMask);
     std::vector<qf::SecBlk> sec(2 * blocks.size());
@@ -1115,37 +1198,48 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
            to_secblk(blocks[bi].inv, n, na, nbeta, true, &sec[blocks.size() + bi]);
     if (ok) {
       const size_t nblk = blocks.size();
-      const bool lreal = !p || !p->has_odd;
+      st->scale = 1.0;
+      st->real = true;
+      st->sec_a = na;
+      st->sec_b = nbeta;
+      if (!p) {  // no Hamiltonian terms: E = 0 and a zero gradient
+        QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
+        QF_CUDA(cudaStreamSynchronize(st->stream));
+        *energy = 0.0;
+        for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
+        return QF_OK;
+      }
+      const bool lreal = !p->has_odd;
       const uint64_t typ = typical_items(sec.data(), nblk);
       const int grid_f = qf::sector_sweep_grid(st->dt, false, true, typ);
       const int grid_r = qf::sector_sweep_grid(st->dt, true, lreal, typ);
       qf_status bs = ensure_sector_buffers(st, 2 * nblk, nblk * (size_t)grid_r * 32);
       if (bs != QF_OK) return bs;
-      st->scale = 1.0;
-      st->real = true;
-      st->sec_a = na;
-      st->sec_b = nbeta;
-      QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
+      const qf::SecSpace sp = sector_space(n, na, nbeta);
+      qf::SecCompact cm{};
+      qf_status cs = ensure_compact(st, sp, na, nbeta, &cm);
+      if (cs != QF_OK) return cs;
+      const uint64_t members = (uint64_t)sp.cnt_e * sp.cnt_o;
+      // a real lambda shares psi's slots (psi real parts, lambda imaginary parts)
+      void* cpsi = st->d_cstate;
+      void* clam = lreal ? cpsi : static_cast<char*>(cpsi) + members * st->elem();
+      QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
       QF_CUDA(h2d(st->d_secblk, sec.data(), sec.size() * sizeof(qf::SecBlk), st->stream));
-      QF_CUDA(qf::launch_sector_sweep(st->psi, nullptr, st->dt, false, true, st->d_secblk, (int)nblk, st->d_bar,
-                                      st->d_sec_partial, nullptr, grid_f, st->stream));
+      QF_CUDA(qf::launch_sector_sweep(cpsi, nullptr, st->dt, false, true, st->d_secblk, (int)nblk, st->d_bar,
+                                      st->d_sec_partial, nullptr, grid_f, cm, st->stream));
       double* d_e = st->d_out + nblk;
       const int nbk = qf::reduce_blocks(n, st->dt);
-      if (p) {
-        const qf::SecSpace sp = sector_space(n, na, nbeta);
-        QF_CUDA(qf::launch_sector_hpsi(st->psi, st->lam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
-                                       p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, nbk,
-                                       st->stream));
-        QF_CUDA(qf::launch_sector_sweep(st->psi, st->lam, st->dt, true, lreal, st->d_secblk + nblk, (int)nblk,
-                                        st->d_bar, st->d_sec_partial, st->d_out, grid_r, st->stream));
-      } else {
-        QF_CUDA(cudaMemsetAsync(st->d_out, 0, (nblk + 2) * sizeof(double), st->stream));
-      }
+      QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
+                                     p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, nbk, cm,
+                                     st->stream));
+      QF_CUDA(qf::launch_sector_sweep(cpsi, clam, st->dt, true, lreal, st->d_secblk + nblk, (int)nblk, st->d_bar,
+                                      st->d_sec_partial, st->d_out, grid_r, cm, st->stream));
+      QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
       QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2) * sizeof(double), st->stream));
       QF_CUDA(cudaStreamSynchronize(st->stream));
       qf_status bc = check_barrier(st);
       if (bc != QF_OK) return bc;
-      double nrm = p ? st->h_out[nblk + 1] : 1.0;
+      double nrm = st->h_out[nblk + 1];
       if (!(nrm > 0.0)) nrm = 1.0;
       *energy = st->h_out[nblk] / nrm;
       for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
@@ -1153,6 +1247,8 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
       return QF_OK;
     }
   }
+  qf_status ls = ensure_lam(st);
+  if (ls != QF_OK) return ls;
   st->scale = 1.0;
   st->real = true;
   st->sec_a = st->sec_b = -1;

@@ -125,6 +125,9 @@ struct SecBlk {                 // one two-row excitation block
   int nzc, ne, no, ke, ko;      // outside even/odd positions and electrons to place there
   uint32_t cnt_e, cnt_o;        // C(ne, ke), C(no, ko)
   uint8_t epos[kSecMaxPos], opos[kSecMaxPos];
+  // The same masks in per-spin local form (qubit q -> bit q >> 1 of its parity):
+  // pl[i][0] / pl[i][1] = even / odd bits of pat[i]; zl[j][0] / zl[j][1] likewise for zc[j].
+  uint32_t pl[2][2], zl[2][2];
   double m[kSparseMaxCls][2][2];  // composite minus identity (real), per sign class
   double q[kSparseMaxCls][2][2];  // Qi with generator Q = i Qi (reverse sweep)
 };
@@ -136,6 +139,17 @@ struct SecSpace {               // all determinants of one sector
 struct SecGroup {               // X group with its even/odd flip counts
   uint64_t x;
   int xe, xo, chunk0, nchunk;
+  uint32_t xa, xb;              // x in per-spin local form (even / odd bits)
+};
+// Compact sector layout: member (alpha string a, beta string b), both as local
+// masks, sits at index ra[a] * cnt_o + rb[b], where ra / rb give a string's
+// colex rank among the strings with the sector's electron count (2^ne / 2^no
+// entries; other entries unused).  This is the ordering the sector kernels
+// enumerate members in, so member number `it` sits at index `it`.
+struct SecCompact {
+  const uint16_t* ra;
+  const uint16_t* rb;
+  uint32_t cnt_o;
 };
 // Groups of at most four flipped qubits, looked up by the spin orbitals they
 // flip, in local indices of each parity (alpha = even qubit 2i -> i, beta = odd
@@ -156,6 +170,8 @@ struct SecRank {
 
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s);
+// count amplitudes set to the unit vector e_idx.
+cudaError_t launch_zero_and_set_count(void* psi, uint64_t count, qf_dtype dt, uint64_t idx, cudaStream_t s);
 cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s);
 cudaError_t launch_rot(void* psi, int n, qf_dtype dt, const RotArgs& a, cudaStream_t s);
 cudaError_t launch_tile(void* psi, int n, qf_dtype dt, const TileArgs& a, cudaStream_t s);
@@ -190,19 +206,25 @@ cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotAr
 cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, bool realst,
                               double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s);
 
-// Sector sweep over nblk blocks in one cooperative launch (reverse when adj:
+// Sector sweep over nblk blocks in one cooperative launch (reverse when adj;
+// a reverse sweep with realst reads lambda from psi's imaginary slots:
 // out[b] = Im <lam|Q_b|psi> of block b, from partial[nblk * grid * 32]).  bar: 3
 // device words.  grid from sector_sweep_grid (typical_items: items of a typical block).
+// With cm.ra != NULL psi and lam are in the compact layout (SecCompact).
 int sector_sweep_grid(qf_dtype dt, bool adj, bool realst, uint64_t typical_items);
 cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const SecBlk* blks,
-                                int nblk, unsigned* bar, double* partial, double* out, int grid, cudaStream_t s);
+                                int nblk, unsigned* bar, double* partial, double* out, int grid,
+                                const SecCompact& cm, cudaStream_t s);
 // lam = H psi on the sector (lam may be NULL), out[0] = <psi|H psi>, out[1] = <psi|psi>.
+// With realst and lam == psi, lambda's real part is written into psi's
+// imaginary slots (the packed form the reverse sweep of a real state reads).
 // Groups with <= 4 flipped qubits are reached by enumerating each member's
 // single and double flips (rk, indexing into `all`); `large` lists the others.
+// With cm.ra != NULL psi and lam are in the compact layout.
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
                                const SecRank& rk, const SecGroup* all, const SecGroup* large, int nlarge,
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
-                               int nblocks, cudaStream_t s);
+                               int nblocks, const SecCompact& cm, cudaStream_t s);
 
 // Bounded-wait self-test: words (3 device words, zeroed) -- waits on words[1]
 // for limit_s seconds, then raises words[2].

@@ -1014,8 +1014,11 @@ int reduce_blocks(int n, qf_dtype) {
 }
 
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s) {
+  return launch_zero_and_set_count(psi, 1ull << n, dt, det, s);
+}
+
+cudaError_t launch_zero_and_set_count(void* psi, uint64_t N, qf_dtype dt, uint64_t det, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_SET, s);
-  const uint64_t N = 1ull << n;
   const unsigned g = grid_for(N, 8);
   if (dt == QF_C128)
     k_zero_and_set<double2><<<g, 256, 0, s>>>(static_cast<double2*>(psi), N, det);

@@ -6,9 +6,12 @@
 // qubits (alpha spin orbitals) and odd qubits (beta): C(n/2, N_a) * C(n/2, N_b)
 // of the 2^n basis states, 5 % at 24 qubits.  Restricting the state to that
 // sector is the speed-up the paper's conclusion proposes for larger systems.
-// The state keeps its full 2^n layout here; these kernels simply enumerate the
+// Two layouts: in the state's own full 2^n layout these kernels enumerate the
 // sector members by combinatorial unranking and never touch the (exactly zero)
-// amplitudes outside it.
+// amplitudes outside it; in the compact layout (SecCompact) the members are
+// stored contiguously by rank, which keeps a 24-qubit sector (0.85 M members,
+// 13.7 MB complex) resident in L2 where the full layout scatters it over
+// 0.85 M separate cache lines.
 //
 // * k_sector_sweep: every excitation block of a circuit in one persistent
 //   cooperative launch, with a grid barrier between consecutive blocks; for the
@@ -56,6 +59,29 @@ __device__ __forceinline__ uint64_t unrank(uint32_t r, const uint8_t* pos, int m
     }
   }
   return bits;
+}
+
+// The same subset as a mask of local indices (position p -> bit p >> 1, the
+// spin-orbital index of qubit p).
+__device__ __forceinline__ uint32_t unrank_l(uint32_t r, const uint8_t* pos, int m, int k,
+                                            const uint32_t (*C)[kBinom]) {
+  uint32_t bits = 0;
+  for (int j = m - 1; j >= 0 && k > 0; --j) {
+    const uint32_t c = C[j][k];
+    if (r >= c) {
+      bits |= 1u << (pos[j] >> 1);
+      r -= c;
+      --k;
+    }
+  }
+  return bits;
+}
+
+__device__ __forceinline__ unsigned par32s(uint32_t v) { return (unsigned)__popc(v) & 1u; }
+
+// Compact index of the member with local alpha / beta strings la, lb.
+__device__ __forceinline__ uint64_t compact_index(const SecCompact& cm, uint32_t la, uint32_t lb) {
+  return (uint64_t)__ldg(cm.ra + la) * cm.cnt_o + __ldg(cm.rb + lb);
 }
 
 constexpr int kSweepThreads = 1024;
@@ -119,9 +145,11 @@ template <> struct SCx<float> { using V = float2; };
 // One excitation block of a sector sweep (forward or reverse): the real 2x2
 // composite minus identity per sign class and, for the reverse sweep, the real
 // matrix Qi with Q = i Qi.
-template <bool ADJ, bool REALST, typename T>
+// PACKED (reverse sweep of a real state): lambda's real part lives in psi's
+// (otherwise zero) imaginary slot, so one access reads or writes both states.
+template <bool ADJ, bool REALST, typename T, bool PACKED, bool COMPACT>
 __device__ void sector_block(typename SCx<T>::V* psi, typename SCx<T>::V* lam, const SecBlk& B,
-                             const uint32_t (*C)[kBinom], double* acc_out) {
+                             const uint32_t (*C)[kBinom], double* acc_out, const SecCompact& cm) {
   using V = typename SCx<T>::V;
   const uint64_t items = (uint64_t)B.cnt_e * (uint64_t)B.cnt_o;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -131,14 +159,35 @@ __device__ void sector_block(typename SCx<T>::V* psi, typename SCx<T>::V* lam, c
   for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items; it += stride) {
     const uint32_t i32 = (uint32_t)it;  // items < 2^32 (at most C(17,8)^2)
     const uint32_t ie = i32 / B.cnt_o, io = i32 - ie * B.cnt_o;
-    const uint64_t base = unrank(ie, B.epos, B.ne, B.ke, C) | unrank(io, B.opos, B.no, B.ko, C);
     unsigned cls = 0;
-    if (B.nzc > 0) cls = par64s(B.zc[0] & base);
-    if (B.nzc > 1) cls |= par64s(B.zc[1] & base) << 1;
-    const uint64_t i0 = base | B.pat[0], i1 = base | B.pat[1];
+    uint64_t i0, i1;
+    if (COMPACT) {
+      const uint32_t la = unrank_l(ie, B.epos, B.ne, B.ke, C), lb = unrank_l(io, B.opos, B.no, B.ko, C);
+      if (B.nzc > 0) cls = par32s(B.zl[0][0] & la) ^ par32s(B.zl[0][1] & lb);
+      if (B.nzc > 1) cls |= (par32s(B.zl[1][0] & la) ^ par32s(B.zl[1][1] & lb)) << 1;
+      i0 = compact_index(cm, la | B.pl[0][0], lb | B.pl[0][1]);
+      i1 = compact_index(cm, la | B.pl[1][0], lb | B.pl[1][1]);
+    } else {
+      const uint64_t base = unrank(ie, B.epos, B.ne, B.ke, C) | unrank(io, B.opos, B.no, B.ko, C);
+      if (B.nzc > 0) cls = par64s(B.zc[0] & base);
+      if (B.nzc > 1) cls |= par64s(B.zc[1] & base) << 1;
+      i0 = base | B.pat[0];
+      i1 = base | B.pat[1];
+    }
     const T a00 = (T)B.m[cls][0][0], a01 = (T)B.m[cls][0][1], a10 = (T)B.m[cls][1][0], a11 = (T)B.m[cls][1][1];
     // L2-coherent accesses: other SMs wrote these amplitudes before the last grid barrier
-    if (REALST) {
+    if (PACKED) {
+      const V p0 = __ldcg(psi + i0), p1 = __ldcg(psi + i1);  // (psi, lambda) real parts
+      acc = fma((double)p0.y, fma(B.q[cls][0][0], (double)p0.x, B.q[cls][0][1] * (double)p1.x), acc);
+      acc = fma((double)p1.y, fma(B.q[cls][1][0], (double)p0.x, B.q[cls][1][1] * (double)p1.x), acc);
+      V o0, o1;
+      o0.x = fma(a00, p0.x, fma(a01, p1.x, p0.x));
+      o0.y = fma(a00, p0.y, fma(a01, p1.y, p0.y));
+      o1.x = fma(a10, p0.x, fma(a11, p1.x, p1.x));
+      o1.y = fma(a10, p0.y, fma(a11, p1.y, p1.y));
+      __stcg(psi + i0, o0);
+      __stcg(psi + i1, o1);
+    } else if (REALST) {
       const T v0 = __ldcg(pr + 2 * i0), v1 = __ldcg(pr + 2 * i1);
       if (ADJ) {
         const T w0 = __ldcg(lr + 2 * i0), w1 = __ldcg(lr + 2 * i1);
@@ -202,10 +251,10 @@ __device__ double block_sum_s(double v) {
 constexpr int kDescWords = sizeof(SecBlk) / 4;
 static_assert(sizeof(SecBlk) % 4 == 0 && kDescWords <= 1024, "descriptor copy layout");
 
-template <bool ADJ, bool REALST, typename T>
+template <bool ADJ, bool REALST, typename T, bool PACKED, bool COMPACT>
 __global__ void __launch_bounds__(kSweepThreads) k_sector_sweep(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
                                                       const SecBlk* __restrict__ blks, int nblk, unsigned* bar,
-                                                      double* partial) {
+                                                      double* partial, SecCompact cm) {
   __shared__ uint32_t C[kBinom][kBinom];
   __shared__ SecBlk sb[2];  // current and next block descriptions
   fill_binom(C);
@@ -219,7 +268,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sector_sweep(typename SCx<T>:
     if (s + 1 < nblk && tid < kDescWords)
       nxt = __ldcg(reinterpret_cast<const uint32_t*>(blks + block_of(s + 1)) + tid);
     double acc = 0.0;
-    sector_block<ADJ, REALST, T>(psi, lam, sb[s & 1], C, &acc);
+    sector_block<ADJ, REALST, T, PACKED, COMPACT>(psi, lam, sb[s & 1], C, &acc, cm);
     if (ADJ) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -245,11 +294,11 @@ __global__ void k_sector_reduce_rows(const double* __restrict__ partial, int nsl
   out[b] = s;
 }
 
-// D_g(b) psi[b] added to (lx, ly) for one connected group.
+// D_g(b) psi(b) added to (lx, ly) for one connected group; psi(b) is stored at psi[a].
 template <typename T, bool REALST, bool NARROW>
 __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict__ psi,
                                             const ExpChunk* __restrict__ chunks, int chunk0, int nchunk, uint64_t b,
-                                            double& lx, double& ly) {
+                                            uint64_t a, double& lx, double& ly) {
   using V = typename SCx<T>::V;
   double dx = 0.0, dy = 0.0;
   for (int k = 0; k < nchunk; ++k) {
@@ -273,9 +322,9 @@ __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict
     }
   }
   if (REALST) {
-    lx = fma(dx, (double)reinterpret_cast<const T*>(psi)[2 * b], lx);
+    lx = fma(dx, (double)reinterpret_cast<const T*>(psi)[2 * a], lx);
   } else {
-    const V v = psi[b];
+    const V v = psi[a];
     lx = fma(dx, (double)v.x, lx);
     lx = fma(-dy, (double)v.y, lx);
     ly = fma(dx, (double)v.y, fma(dy, (double)v.x, ly));
@@ -288,13 +337,13 @@ __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict
 // most four flips are reached by enumerating exactly those flips (singles and
 // doubles of c) and looking the group up by the rank of its flip set; larger
 // groups are tested one by one.
-template <typename T, bool REALST, bool NARROW>
+template <typename T, bool REALST, bool NARROW, bool LAMY, bool COMPACT>
 __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* __restrict__ psi,
                                                      typename SCx<T>::V* __restrict__ lam, SecSpace sp, SecRank rk,
                                                      const SecGroup* __restrict__ all,
                                                      const SecGroup* __restrict__ large, int nlarge,
                                                      const ExpChunk* __restrict__ chunks, double* partials,
-                                                     unsigned* counter, double* out) {
+                                                     unsigned* counter, double* out, SecCompact cm) {
   using V = typename SCx<T>::V;
   __shared__ uint32_t C[kBinom][kBinom];
   __shared__ SecSpace ssp;
@@ -312,18 +361,31 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
     // occupied / empty spin orbitals of each parity, as local indices (qubit 2i -> i, 2i+1 -> i)
     uint8_t oa[kSecMaxPos], va[kSecMaxPos], ob[kSecMaxPos], vb[kSecMaxPos];
     int noa = 0, nva = 0, nob = 0, nvb = 0;
+    uint32_t la = 0, lb = 0;  // local alpha / beta strings (compact addressing)
     for (int q = 0; q < ssp.ne; ++q) {
-      if ((c >> ssp.epos[q]) & 1ull) oa[noa++] = (uint8_t)q; else va[nva++] = (uint8_t)q;
+      if ((c >> ssp.epos[q]) & 1ull) {
+        oa[noa++] = (uint8_t)q;
+        la |= 1u << q;
+      } else {
+        va[nva++] = (uint8_t)q;
+      }
     }
     for (int q = 0; q < ssp.no; ++q) {
-      if ((c >> ssp.opos[q]) & 1ull) ob[nob++] = (uint8_t)q; else vb[nvb++] = (uint8_t)q;
+      if ((c >> ssp.opos[q]) & 1ull) {
+        ob[nob++] = (uint8_t)q;
+        lb |= 1u << q;
+      } else {
+        vb[nvb++] = (uint8_t)q;
+      }
     }
     double lx = 0.0, ly = 0.0;
+    auto term = [&](const SecGroup& G) {
+      const uint64_t b = c ^ G.x;
+      const uint64_t a = COMPACT ? compact_index(cm, la ^ G.xa, lb ^ G.xb) : b;
+      sector_term<T, REALST, NARROW>(psi, chunks, G.chunk0, G.nchunk, b, a, lx, ly);
+    };
     auto visit = [&](int g) {
-      if (g >= 0) {
-        const SecGroup G = all[g];
-        sector_term<T, REALST, NARROW>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
-      }
+      if (g >= 0) term(all[g]);
     };
     if (rk.diag >= 0) visit(rk.diag);
     const int ne = rk.ne, no = rk.no;
@@ -356,16 +418,25 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
     for (int gi = 0; gi < nlarge; ++gi) {
       const SecGroup G = large[gi];
       if (2 * __popcll(c & G.x & EVEN) != G.xe || 2 * __popcll(c & G.x & ODD) != G.xo) continue;
-      sector_term<T, REALST, NARROW>(psi, chunks, G.chunk0, G.nchunk, c ^ G.x, lx, ly);
+      term(G);
     }
-    const V u = psi[c];
-    acc_e = fma((double)u.x, lx, fma((double)u.y, ly, acc_e));
-    acc_n = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, acc_n));
-    if (lam) {
+    const uint64_t self = COMPACT ? it : c;
+    if (REALST) {  // real parts only: with LAMY the imaginary slots are lambda's
+      const double ux = (double)reinterpret_cast<const T*>(psi)[2 * self];
+      acc_e = fma(ux, lx, acc_e);
+      acc_n = fma(ux, ux, acc_n);
+    } else {
+      const V u = psi[self];
+      acc_e = fma((double)u.x, lx, fma((double)u.y, ly, acc_e));
+      acc_n = fma((double)u.x, (double)u.x, fma((double)u.y, (double)u.y, acc_n));
+    }
+    if (LAMY) {  // lambda's real part into psi's imaginary slot (real states)
+      reinterpret_cast<T*>(lam)[2 * self + 1] = (T)lx;
+    } else if (lam) {
       V w;
       w.x = (T)lx;
       w.y = (T)ly;
-      lam[c] = w;
+      lam[self] = w;
     }
   }
   // deterministic two-value grid reduction
@@ -399,27 +470,43 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
 }  // namespace
 
 // Grid of the cooperative sweep: about one item per thread for a typical block,
-// at most one CTA per SM (all CTAs must be resident at once).
-template <bool ADJ, bool REALST, typename T>
-static int sweep_grid(uint64_t typical_items) {
-  int per_sm = 0, dev = 0, sms = 0;
+// at most one CTA per SM (all CTAs must be resident at once; a 1024-thread CTA
+// under __launch_bounds__ always fits one per SM).
+int sector_sweep_grid(qf_dtype, bool, bool, uint64_t typical_items) {
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sector_sweep<ADJ, REALST, T>, kSweepThreads, 0);
   const uint64_t want = (typical_items + kSweepThreads - 1) / kSweepThreads;
-  const uint64_t cap = (uint64_t)std::max(1, std::min(per_sm, 1)) * (uint64_t)std::max(1, sms);
-  return (int)std::max<uint64_t>(1, std::min(want, cap));
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(1, sms)));
 }
 
-template <bool ADJ, bool REALST, typename T>
+template <bool ADJ, bool REALST, typename T, bool COMPACT>
 static cudaError_t sweep_t(void* psi, void* lam, const SecBlk* blks, int nblk, unsigned* bar, double* partial,
-                           int grid, cudaStream_t s) {
+                           int grid, SecCompact cm, cudaStream_t s) {
   using V = typename SCx<T>::V;
   V* p = static_cast<V*>(psi);
   V* l = static_cast<V*>(lam);
-  void* args[] = {&p, &l, &blks, &nblk, &bar, &partial};
-  return cudaLaunchCooperativeKernel((const void*)k_sector_sweep<ADJ, REALST, T>, dim3(grid), dim3(kSweepThreads),
-                                     args, 0, s);
+  void* args[] = {&p, &l, &blks, &nblk, &bar, &partial, &cm};
+  // reverse sweeps of real states keep lambda in psi's imaginary slots
+  constexpr bool PK = ADJ && REALST;
+  return cudaLaunchCooperativeKernel((const void*)k_sector_sweep<ADJ, REALST, T, PK, COMPACT>, dim3(grid),
+                                     dim3(kSweepThreads), args, 0, s);
+}
+
+template <typename T>
+static cudaError_t sweep_dispatch(void* psi, void* lam, bool adj, bool realst, const SecBlk* blks, int nblk,
+                                  unsigned* bar, double* partial, int grid, const SecCompact& cm, cudaStream_t s) {
+  if (!cm.ra) {  // full layout: forward sweeps only
+    if (adj) return cudaErrorInvalidValue;
+    return realst ? sweep_t<false, true, T, false>(psi, lam, blks, nblk, bar, partial, grid, cm, s)
+                  : sweep_t<false, false, T, false>(psi, lam, blks, nblk, bar, partial, grid, cm, s);
+  }
+  if (!adj) {  // compact forward: the real state of an energy evaluation
+    if (!realst) return cudaErrorInvalidValue;
+    return sweep_t<false, true, T, true>(psi, lam, blks, nblk, bar, partial, grid, cm, s);
+  }
+  return realst ? sweep_t<true, true, T, true>(psi, lam, blks, nblk, bar, partial, grid, cm, s)
+                : sweep_t<true, false, T, true>(psi, lam, blks, nblk, bar, partial, grid, cm, s);
 }
 
 cudaError_t launch_wait_selftest(unsigned* words, double limit_s, cudaStream_t s) {
@@ -428,37 +515,15 @@ cudaError_t launch_wait_selftest(unsigned* words, double limit_s, cudaStream_t s
   return cudaGetLastError();
 }
 
-int sector_sweep_grid(qf_dtype dt, bool adj, bool realst, uint64_t typical_items) {
-  const uint64_t t = typical_items;
-  if (dt == QF_C128) {
-    if (adj) return realst ? sweep_grid<true, true, double>(t) : sweep_grid<true, false, double>(t);
-    return realst ? sweep_grid<false, true, double>(t) : sweep_grid<false, false, double>(t);
-  }
-  if (adj) return realst ? sweep_grid<true, true, float>(t) : sweep_grid<true, false, float>(t);
-  return realst ? sweep_grid<false, true, float>(t) : sweep_grid<false, false, float>(t);
-}
-
 cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const SecBlk* blks,
-                                int nblk, unsigned* bar, double* partial, double* out, int grid, cudaStream_t s) {
+                                int nblk, unsigned* bar, double* partial, double* out, int grid,
+                                const SecCompact& cm, cudaStream_t s) {
   if (nblk <= 0) return cudaSuccess;
   const int prof_slot_ = prof_pre(adj ? QF_K_ADJ_SPARSE : QF_K_SPARSE, s);
   cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s);
   if (e == cudaSuccess) {
-    if (dt == QF_C128) {
-      if (adj)
-        e = realst ? sweep_t<true, true, double>(psi, lam, blks, nblk, bar, partial, grid, s)
-                   : sweep_t<true, false, double>(psi, lam, blks, nblk, bar, partial, grid, s);
-      else
-        e = realst ? sweep_t<false, true, double>(psi, lam, blks, nblk, bar, partial, grid, s)
-                   : sweep_t<false, false, double>(psi, lam, blks, nblk, bar, partial, grid, s);
-    } else {
-      if (adj)
-        e = realst ? sweep_t<true, true, float>(psi, lam, blks, nblk, bar, partial, grid, s)
-                   : sweep_t<true, false, float>(psi, lam, blks, nblk, bar, partial, grid, s);
-      else
-        e = realst ? sweep_t<false, true, float>(psi, lam, blks, nblk, bar, partial, grid, s)
-                   : sweep_t<false, false, float>(psi, lam, blks, nblk, bar, partial, grid, s);
-    }
+    e = (dt == QF_C128) ? sweep_dispatch<double>(psi, lam, adj, realst, blks, nblk, bar, partial, grid, cm, s)
+                        : sweep_dispatch<float>(psi, lam, adj, realst, blks, nblk, bar, partial, grid, cm, s);
   }
   count_launch();
   if (e == cudaSuccess && adj) {
@@ -470,34 +535,65 @@ cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, boo
   return e;
 }
 
+template <typename T, bool REALST, bool LAMY, bool COMPACT>
+static void hpsi_t(const void* psi, void* lam, bool narrow, unsigned g, const SecSpace& sp, const SecRank& rk,
+                   const SecGroup* all, const SecGroup* large, int nlarge, const ExpChunk* chunks, double* partials,
+                   unsigned* counter, double* out, const SecCompact& cm, cudaStream_t s) {
+  using V = typename SCx<T>::V;
+  const V* p = static_cast<const V*>(psi);
+  V* l = static_cast<V*>(lam);
+  if (narrow)
+    k_sector_hpsi<T, REALST, true, LAMY, COMPACT><<<g, 256, 0, s>>>(p, l, sp, rk, all, large, nlarge, chunks,
+                                                                     partials, counter, out, cm);
+  else
+    k_sector_hpsi<T, REALST, false, LAMY, COMPACT><<<g, 256, 0, s>>>(p, l, sp, rk, all, large, nlarge, chunks,
+                                                                      partials, counter, out, cm);
+}
+
+template <typename T>
+static cudaError_t hpsi_dispatch(const void* psi, void* lam, bool realst, bool narrow, unsigned g,
+                                 const SecSpace& sp, const SecRank& rk, const SecGroup* all,
+                                 const SecGroup* large, int nlarge, const ExpChunk* chunks, double* partials,
+                                 unsigned* counter, double* out, const SecCompact& cm, cudaStream_t s) {
+  const bool lamy = realst && lam == psi;  // packed: lambda into psi's imaginary slots
+  if (!cm.ra) {  // full layout (expectation values): no packed lambda
+    if (lamy) return cudaErrorInvalidValue;
+    if (realst)
+      hpsi_t<T, true, false, false>(psi, lam, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter, out,
+                                    cm, s);
+    else
+      hpsi_t<T, false, false, false>(psi, lam, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter,
+                                     out, cm, s);
+    return cudaGetLastError();
+  }
+  // compact layout (energy and gradient): a real lambda is always packed
+  if (realst != lamy) return cudaErrorInvalidValue;
+  if (lamy)
+    hpsi_t<T, true, true, true>(psi, lam, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter, out, cm,
+                                s);
+  else
+    hpsi_t<T, false, false, true>(psi, lam, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter, out,
+                                  cm, s);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
                                const SecRank& rk, const SecGroup* all, const SecGroup* large, int nlarge,
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
-                               int nblocks, cudaStream_t s) {
+                               int nblocks, const SecCompact& cm, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_HPSI, s);
   const uint64_t items = (uint64_t)sp.cnt_e * sp.cnt_o;
   const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, (uint64_t)nblocks));
   const bool narrow = sp.ne + sp.no <= 32;
-#define QF_SECTOR_HPSI(TT, VV, RR, NN)                                                                       \
-  k_sector_hpsi<TT, RR, NN><<<g, 256, 0, s>>>(static_cast<const VV*>(psi), static_cast<VV*>(lam), sp, rk, all,    \
-                                              large, nlarge, chunks, partials, counter, out)
-  if (dt == QF_C128) {
-    if (realst) {
-      if (narrow) QF_SECTOR_HPSI(double, double2, true, true); else QF_SECTOR_HPSI(double, double2, true, false);
-    } else {
-      if (narrow) QF_SECTOR_HPSI(double, double2, false, true); else QF_SECTOR_HPSI(double, double2, false, false);
-    }
-  } else {
-    if (realst) {
-      if (narrow) QF_SECTOR_HPSI(float, float2, true, true); else QF_SECTOR_HPSI(float, float2, true, false);
-    } else {
-      if (narrow) QF_SECTOR_HPSI(float, float2, false, true); else QF_SECTOR_HPSI(float, float2, false, false);
-    }
-  }
-#undef QF_SECTOR_HPSI
+  const cudaError_t e =
+      (dt == QF_C128)
+          ? hpsi_dispatch<double>(psi, lam, realst, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter,
+                                  out, cm, s)
+          : hpsi_dispatch<float>(psi, lam, realst, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter,
+                                 out, cm, s);
   prof_post(prof_slot_, s);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace qf

@@ -210,9 +210,12 @@ def test_energy_grad_ucc_c128_matches_oracle_adjoint():
     e_ref, g_ref = fermion.ucc_gradient_adjoint(cfg["n_orb"], cfg["n_el"], h, g, t, exs)
     assert abs(e - e_ref) < TOL_E_C128
     assert np.abs(grad - g_ref).max() < 1e-10
-    # the reverse sweep leaves the reference determinant
+    # the sector path leaves exactly the reference determinant (lambda, kept in
+    # psi's imaginary slots for a real Hamiltonian, is cleared)
     out = st.to_numpy()
-    assert abs(abs(out[det]) - 1) < 1e-12
+    ref = np.zeros_like(out)
+    ref[det] = 1.0
+    assert np.array_equal(out, ref)
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
@@ -231,6 +234,8 @@ def test_energy_grad_repeated_calls_new_angles(dtype):
         else:
             assert abs(e - e_ref) < TOL_E_C64, k
             assert np.linalg.norm(grad - g_ref) / np.linalg.norm(g_ref) < TOL_G_C64, k
+        out = st.to_numpy()
+        assert out[det] == 1.0 and np.count_nonzero(out) == 1, k
 
 
 @pytest.mark.parametrize("mode", ["fp64", "ds"])
