@@ -128,6 +128,8 @@ struct qf_state {
   int rank_n = -1, rank_a = -1, rank_b = -1;
   void* d_cstate = nullptr;
   size_t cstate_cap = 0;
+  void* d_runblk = nullptr;  // part-local sweep descriptors (blocks, then parts)
+  size_t runblk_cap = 0;
   int hpsi_mode = QF_HPSI_DS;
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
@@ -150,6 +152,9 @@ struct qf_state {
 namespace {
 
 constexpr int kPartials = 4096;
+// Target part size (members) of the part-local sector sweeps: ~40 KB of shared
+// memory per part, so several parts run on each SM.
+constexpr uint64_t kRunPartTarget = 4096;
 
 // Bits of mask on qubits of parity par (0 even / alpha, 1 odd / beta), as local
 // spin-orbital indices: qubit q -> bit q >> 1.
@@ -732,11 +737,11 @@ uint64_t compact_of(uint64_t det, const qf::SecSpace& sp) {
 qf_status ensure_compact(qf_state* st, const qf::SecSpace& sp, int na, int nb, qf::SecCompact* cm) {
   const size_t ea = (size_t)1 << sp.ne, eb = (size_t)1 << sp.no;
   if (st->rank_n != st->n || st->rank_a != na || st->rank_b != nb) {
-    std::vector<uint16_t> t(ea + eb, 0xFFFFu);  // entries of other popcounts are never read
-    for (size_t m = 0; m < ea; ++m)
-      if (popc(m) == na) t[m] = (uint16_t)colex_rank((uint32_t)m);
-    for (size_t m = 0; m < eb; ++m)
-      if (popc(m) == nb) t[ea + m] = (uint16_t)colex_rank((uint32_t)m);
+    // every mask's colex rank among the masks of its own popcount (the part-local
+    // sweeps rank strings of other electron counts with the same table)
+    std::vector<uint16_t> t(ea + eb);
+    for (size_t m = 0; m < ea; ++m) t[m] = (uint16_t)colex_rank((uint32_t)m);
+    for (size_t m = 0; m < eb; ++m) t[ea + m] = (uint16_t)colex_rank((uint32_t)m);
     cudaFree(st->d_rank);
     st->d_rank = nullptr;
     st->rank_n = -1;
@@ -765,6 +770,163 @@ qf_status ensure_compact(qf_state* st, const qf::SecSpace& sp, int na, int nb, q
   cm->ra = st->d_rank;
   cm->rb = st->d_rank + ea;
   cm->cnt_o = sp.cnt_o;
+  return QF_OK;
+}
+
+// Part-local runs (qf::RunInfo) for sector blocks sec[0..nblk) (forward) and
+// sec[nblk..2 nblk) (their inverses) of an n-qubit state in sector (na, nb):
+// consecutive blocks are grouped while the largest part of the union of their
+// supports stays within cap members (and a run holds at most kRunMaxBlocks).
+struct SectorRuns {
+  std::vector<qf::RunInfo> runs;
+  std::vector<qf::RunPart> parts;
+  std::vector<qf::RunBlk> blks;  // forward blocks, then inverse blocks
+  int pmax = 0;
+};
+
+// Largest part of a run touching ua of the ne alpha and ub of the no beta orbitals.
+uint64_t run_maxpart(int ua, int ub, int ne, int no, int na, int nb) {
+  uint64_t ba = 0, bb = 0;
+  for (int ka = std::max(0, na - (ne - ua)); ka <= std::min(ua, na); ++ka) ba = std::max<uint64_t>(ba, binom(ua, ka));
+  for (int kb = std::max(0, nb - (no - ub)); kb <= std::min(ub, nb); ++kb) bb = std::max<uint64_t>(bb, binom(ub, kb));
+  return ba * bb;
+}
+
+bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint64_t cap, SectorRuns* out) {
+  const int ne = (n + 1) / 2, no = n / 2;
+  const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+  std::vector<uint64_t> supp(nblk);
+  for (size_t b = 0; b < nblk; ++b) {
+    uint64_t outside = 0;
+    for (int i = 0; i < sec[b].ne; ++i) outside |= 1ull << sec[b].epos[i];
+    for (int i = 0; i < sec[b].no; ++i) outside |= 1ull << sec[b].opos[i];
+    supp[b] = all & ~outside;
+  }
+  out->runs.clear();
+  out->parts.clear();
+  out->blks.assign(2 * nblk, qf::RunBlk{});
+  out->pmax = 0;
+  size_t b0 = 0;
+  while (b0 < nblk) {
+    uint64_t U = supp[b0];
+    size_t b1 = b0 + 1;
+    while (b1 < nblk && b1 - b0 < (size_t)qf::kRunMaxBlocks) {
+      const uint64_t U2 = U | supp[b1];
+      if (run_maxpart(popc(U2 & kEvenMask), popc(U2 & ~kEvenMask), ne, no, na, nb) > cap) break;
+      U = U2;
+      ++b1;
+    }
+    const int ua = popc(U & kEvenMask), ub = popc(U & ~kEvenMask);
+    if (run_maxpart(ua, ub, ne, no, na, nb) > cap) return false;  // one block's own part too large
+    qf::RunInfo R{};
+    R.b0 = (int)b0;
+    R.b1 = (int)b1;
+    R.ua = ua;
+    R.ub = ub;
+    int loca[32] = {0}, locb[32] = {0};  // spin-local orbital -> run-local index
+    uint32_t Ga = 0, Gb = 0;             // spin-local masks of G
+    {
+      int ia = 0, ib = 0;
+      for (int q = 0; q < n; ++q) {
+        const int orb = q >> 1;
+        if ((U >> q) & 1ull) {
+          if ((q & 1) == 0) {
+            R.apos[ia] = (uint8_t)orb;
+            loca[orb] = ia++;
+          } else {
+            R.bpos[ib] = (uint8_t)orb;
+            locb[orb] = ib++;
+          }
+        } else if ((q & 1) == 0) {
+          Ga |= 1u << orb;
+        } else {
+          Gb |= 1u << orb;
+        }
+      }
+    }
+    // parts: every occupation of G that leaves a feasible count on U, largest first
+    std::vector<uint32_t> gas, gbs;
+    for (uint32_t m = Ga;; m = (m - 1) & Ga) {
+      const int ka = na - popc(m);
+      if (ka >= 0 && ka <= ua) gas.push_back(m);
+      if (m == 0) break;
+    }
+    for (uint32_t m = Gb;; m = (m - 1) & Gb) {
+      const int kb = nb - popc(m);
+      if (kb >= 0 && kb <= ub) gbs.push_back(m);
+      if (m == 0) break;
+    }
+    std::vector<qf::RunPart> ps;
+    ps.reserve(gas.size() * gbs.size());
+    for (uint32_t ga : gas)
+      for (uint32_t gb : gbs) {
+        qf::RunPart P{};
+        P.ga = ga;
+        P.gb = gb;
+        P.ka = na - popc(ga);
+        P.kb = nb - popc(gb);
+        P.cnta = binom(ua, P.ka);
+        P.cntb = binom(ub, P.kb);
+        ps.push_back(P);
+      }
+    std::stable_sort(ps.begin(), ps.end(), [](const qf::RunPart& a, const qf::RunPart& b) {
+      return (uint64_t)a.cnta * a.cntb > (uint64_t)b.cnta * b.cntb;
+    });
+    R.part0 = (int)out->parts.size();
+    R.nparts = (int)ps.size();
+    R.maxsize = ps.empty() ? 0u : ps[0].cnta * ps[0].cntb;
+    out->parts.insert(out->parts.end(), ps.begin(), ps.end());
+    out->pmax = std::max(out->pmax, R.nparts);
+    // the run's blocks in run-local coordinates (forward and inverse share the geometry)
+    auto runlocal = [&](uint64_t mask, int par) {
+      uint32_t o = 0;
+      for (int q = par; q < n; q += 2)
+        if (((mask >> q) & 1ull) && ((U >> q) & 1ull)) o |= 1u << (par ? locb[q >> 1] : loca[q >> 1]);
+      return o;
+    };
+    for (size_t b = b0; b < b1; ++b)
+      for (int dir = 0; dir < 2; ++dir) {
+        const qf::SecBlk& S = sec[dir * nblk + b];
+        qf::RunBlk& B = out->blks[dir * nblk + b];
+        const uint64_t sp = supp[b];
+        for (int q = 0; q < n; ++q) {
+          if (!((U >> q) & 1ull) || ((sp >> q) & 1ull)) continue;
+          if ((q & 1) == 0)
+            B.epos[B.ne++] = (uint8_t)loca[q >> 1];
+          else
+            B.opos[B.no++] = (uint8_t)locb[q >> 1];
+        }
+        B.e0 = popc(S.pat[0] & kEvenMask);
+        B.o0 = popc(S.pat[0] & ~kEvenMask);
+        B.nzc = S.nzc;
+        B.np = R.nparts;
+        for (int i = 0; i < 2; ++i)
+          for (int par = 0; par < 2; ++par) {
+            B.pu[i][par] = runlocal(S.pat[i], par);
+            B.zu[i][par] = runlocal(S.zc[i] & ~sp, par);
+            B.zg[i][par] = local_bits(S.zc[i] & ~U, par);
+          }
+        std::memcpy(B.m, S.m, sizeof(B.m));
+        std::memcpy(B.q, S.q, sizeof(B.q));
+      }
+    out->runs.push_back(R);
+    b0 = b1;
+  }
+  return true;
+}
+
+// A device buffer of at least `bytes`, kept with the handle.
+qf_status ensure_buf(void** p, size_t* cap, size_t bytes, const char* what) {
+  if (bytes <= *cap) return QF_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(QF_ENOMEM, std::string("cudaMalloc(") + what + ") failed");
+  }
+  *cap = bytes;
   return QF_OK;
 }
 
@@ -999,6 +1161,7 @@ qf_status qf_state_destroy(qf_state* st) {
   cudaFree(st->d_bar);
   cudaFree(st->d_rank);
   cudaFree(st->d_cstate);
+  cudaFree(st->d_runblk);
   cudaFree(st->d_partials);
   cudaFree(st->d_counter);
   cudaFree(st->d_out);
@@ -1210,35 +1373,46 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
         return QF_OK;
       }
       const bool lreal = !p->has_odd;
-      const uint64_t typ = typical_items(sec.data(), nblk);
-      const int grid_f = qf::sector_sweep_grid(st->dt, false, true, typ);
-      const int grid_r = qf::sector_sweep_grid(st->dt, true, lreal, typ);
-      qf_status bs = ensure_sector_buffers(st, 2 * nblk, nblk * (size_t)grid_r * 32);
-      if (bs != QF_OK) return bs;
       const qf::SecSpace sp = sector_space(n, na, nbeta);
       qf::SecCompact cm{};
       qf_status cs = ensure_compact(st, sp, na, nbeta, &cm);
       if (cs != QF_OK) return cs;
+      // part-local runs: parts of at most kRunPartTarget members (and what shared memory holds)
+      const uint64_t cap = std::min<uint64_t>(
+          kRunPartTarget, std::min(qf::sector_run_capacity(st->dt, false, true), qf::sector_run_capacity(st->dt, true, lreal)));
+      SectorRuns rs;
+      if (!build_runs(sec.data(), nblk, n, na, nbeta, cap, &rs))
+        return fail(QF_EINVAL, "sector block support too large for a part-local sweep");
+      qf_status bs = ensure_sector_buffers(st, 1, nblk * (size_t)rs.pmax);
+      if (bs != QF_OK) return bs;
+      const size_t blk_bytes = rs.blks.size() * sizeof(qf::RunBlk);
+      bs = ensure_buf(&st->d_runblk, &st->runblk_cap, blk_bytes + rs.parts.size() * sizeof(qf::RunPart),
+                      "sector run descriptors");
+      if (bs != QF_OK) return bs;
+      const qf::RunBlk* d_blks = static_cast<const qf::RunBlk*>(st->d_runblk);
+      const qf::RunPart* d_parts =
+          reinterpret_cast<const qf::RunPart*>(static_cast<const char*>(st->d_runblk) + blk_bytes);
+      QF_CUDA(h2d(st->d_runblk, rs.blks.data(), blk_bytes, st->stream));
+      QF_CUDA(h2d(static_cast<char*>(st->d_runblk) + blk_bytes, rs.parts.data(),
+                  rs.parts.size() * sizeof(qf::RunPart), st->stream));
       const uint64_t members = (uint64_t)sp.cnt_e * sp.cnt_o;
       // a real lambda shares psi's slots (psi real parts, lambda imaginary parts)
       void* cpsi = st->d_cstate;
       void* clam = lreal ? cpsi : static_cast<char*>(cpsi) + members * st->elem();
+      const int nruns = (int)rs.runs.size();
       QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
-      QF_CUDA(h2d(st->d_secblk, sec.data(), sec.size() * sizeof(qf::SecBlk), st->stream));
-      QF_CUDA(qf::launch_sector_sweep(cpsi, nullptr, st->dt, false, true, st->d_secblk, (int)nblk, st->d_bar,
-                                      st->d_sec_partial, nullptr, grid_f, cm, st->stream));
+      QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
+                                     (int)nblk, nullptr, rs.pmax, nullptr, cm, st->stream));
       double* d_e = st->d_out + nblk;
       const int nbk = qf::reduce_blocks(n, st->dt);
       QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
                                      p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, nbk, cm,
                                      st->stream));
-      QF_CUDA(qf::launch_sector_sweep(cpsi, clam, st->dt, true, lreal, st->d_secblk + nblk, (int)nblk, st->d_bar,
-                                      st->d_sec_partial, st->d_out, grid_r, cm, st->stream));
+      QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
+                                     (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, st->stream));
       QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
       QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2) * sizeof(double), st->stream));
       QF_CUDA(cudaStreamSynchronize(st->stream));
-      qf_status bc = check_barrier(st);
-      if (bc != QF_OK) return bc;
       double nrm = st->h_out[nblk + 1];
       if (!(nrm > 0.0)) nrm = 1.0;
       *energy = st->h_out[nblk] / nrm;

@@ -141,6 +141,41 @@ struct SecGroup {               // X group with its even/odd flip counts
   int xe, xo, chunk0, nchunk;
   uint32_t xa, xb;              // x in per-spin local form (even / odd bits)
 };
+// Part-local sweeps.  A run is a stretch of consecutive excitation blocks whose
+// supports avoid a set G of spin orbitals; the rest, U, is what the run acts
+// on.  Every block of the run maps a sector member onto one with the same
+// occupation of G, so the sector splits into independent parts (one per
+// occupation pattern of G), and each part can take the whole run in shared
+// memory, with no grid-wide synchronisation between the run's blocks.
+// Inside a part, members are numbered by (alpha string on U, beta string on
+// U) in "run-local" coordinates: U's alpha orbitals renumbered 0..ua-1 and its
+// beta orbitals 0..ub-1.
+constexpr int kRunMaxBlocks = 256;  // blocks per run (per-warp overlap slots in shared memory)
+struct RunBlk {                     // one excitation block inside its run
+  uint8_t epos[kSecMaxPos], opos[kSecMaxPos];  // run-local U orbitals outside the support
+  int ne, no;                       // their counts
+  int e0, o0;                       // alpha / beta electrons of the active patterns
+  int nzc;
+  int np;                           // parts of the run (overlap partials to reduce)
+  uint32_t pu[2][2];                // pattern i on U (run-local), [i][0] alpha, [i][1] beta
+  uint32_t zu[2][2];                // class mask j on U (run-local)
+  uint32_t zg[2][2];                // class mask j on G (spin-local: orbital index)
+  double m[kSparseMaxCls][2][2];    // composite minus identity (real), per sign class
+  double q[kSparseMaxCls][2][2];    // Qi with generator Q = i Qi (reverse)
+};
+struct RunPart {                    // one occupation pattern of G
+  uint32_t ga, gb;                  // occupied G orbitals (spin-local masks)
+  int ka, kb;                       // electrons left for U's alpha / beta orbitals
+  uint32_t cnta, cntb;              // C(ua, ka), C(ub, kb): size = cnta * cntb
+};
+struct RunInfo {
+  int b0, b1;                       // blocks [b0, b1)
+  int part0, nparts;                // parts [part0, part0 + nparts), largest first
+  int ua, ub;
+  uint8_t apos[kSecMaxPos], bpos[kSecMaxPos];  // spin-local orbital of each run-local index
+  uint32_t maxsize;                 // largest part
+};
+
 // Compact sector layout: member (alpha string a, beta string b), both as local
 // masks, sits at index ra[a] * cnt_o + rb[b], where ra / rb give a string's
 // colex rank among the strings with the sector's electron count (2^ne / 2^no
@@ -220,6 +255,17 @@ cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, boo
 // imaginary slots (the packed form the reverse sweep of a real state reads).
 // Groups with <= 4 flipped qubits are reached by enumerating each member's
 // single and double flips (rk, indexing into `all`); `large` lists the others.
+// Part-local sweep of all runs over a compact-layout state (forward: runs and
+// blocks in order, psi real; reverse: from the last, psi real and lam real
+// packed in psi's imaginary slots when realst, else separate complex states).
+// Reverse: out[b] = Im <lam|Q_b|psi> of block b, via partial[b * pmax + part].
+// runs is a host array; parts and blks are device arrays.  Returns an error
+// when a part does not fit in shared memory.
+cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
+                               int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
+                               int pmax, double* out, const SecCompact& cm, cudaStream_t s);
+// Largest part (members) launch_sector_runs accepts for this dtype and direction.
+uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst);
 // With cm.ra != NULL psi and lam are in the compact layout.
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
                                const SecRank& rk, const SecGroup* all, const SecGroup* large, int nlarge,

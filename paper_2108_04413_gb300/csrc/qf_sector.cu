@@ -108,25 +108,33 @@ __device__ bool bounded_wait(volatile unsigned* gen, unsigned old, unsigned* err
   return true;
 }
 
-// Grid-wide barrier with a bounded wait.  bar[0] = arrivals, bar[1] = generation,
-// bar[2] = error flag.  Returns false when the grid must stop (error raised).
-__device__ bool grid_barrier(unsigned* bar) {
+// Grid-wide barrier with a bounded wait.  bar[0] counts arrivals and is never
+// reset within a launch: the k-th barrier of a grid of G CTAs is passed once it
+// reaches k * G, so each CTA pays one fire-and-forget increment and one polling
+// loop.  bar[2] is the error flag.  Returns false when the grid must stop.
+__device__ bool grid_barrier(unsigned* bar, unsigned target) {
   __shared__ int stop;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      bounded_wait(vgen, gen, bar + 2, kBarrierLimitNs);
+    __threadfence();  // release this CTA's writes (ordered after the CTA barrier)
+    atomicAdd(bar, 1u);
+    volatile unsigned* vcount = bar;
+    volatile unsigned* verr = bar + 2;
+    const uint64_t t0 = global_ns();
+    int st = 0;
+    while (*vcount < target) {
+      if (*verr != 0u) {
+        st = 1;
+        break;
+      }
+      if (global_ns() - t0 > kBarrierLimitNs) {
+        atomicExch(bar + 2, 1u);
+        st = 1;
+        break;
+      }
     }
-    __threadfence();
-    stop = (*(volatile unsigned*)(bar + 2) != 0u);
+    __threadfence();  // acquire the other CTAs' writes
+    stop = st;
   }
   __syncthreads();
   return !stop;
@@ -278,11 +286,194 @@ __global__ void __launch_bounds__(kSweepThreads) k_sector_sweep(typename SCx<T>:
       if (tid < kDescWords) reinterpret_cast<uint32_t*>(&sb[(s + 1) & 1])[tid] = nxt;
       if (gridDim.x == 1) {
         __syncthreads();
-      } else if (!grid_barrier(bar)) {
+      } else if (!grid_barrier(bar, (unsigned)(s + 1) * gridDim.x)) {
         return;
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Part-local sweeps (RunInfo / RunPart / RunBlk): one launch per run, one CTA
+// per part.  The CTA gathers its part's members from the compact state into
+// shared memory, applies every block of the run there (a CTA barrier between
+// blocks), and scatters them back.
+
+// The r-th k-subset (colex order) of positions pos[0..m), as a mask of the
+// position values.
+__device__ __forceinline__ uint32_t unrank_m(uint32_t r, const uint8_t* pos, int m, int k,
+                                            const uint32_t (*C)[kBinom]) {
+  uint32_t bits = 0;
+  for (int j = m - 1; j >= 0 && k > 0; --j) {
+    const uint32_t c = C[j][k];
+    if (r >= c) {
+      bits |= 1u << pos[j];
+      r -= c;
+      --k;
+    }
+  }
+  return bits;
+}
+
+constexpr int kRunThreads = 256;
+constexpr int kRunWarps = kRunThreads / 32;
+constexpr int kRunBlkWords = sizeof(RunBlk) / 4;
+static_assert(sizeof(RunBlk) % 4 == 0 && kRunBlkWords <= kRunThreads, "run descriptor copy layout");
+
+// Shared-memory bytes per member: psi real parts (forward), (psi, lam) packed
+// real pairs (reverse, real), or psi and lam complex (reverse, complex); plus
+// the member's compact index.
+template <int MODE, typename T>
+__host__ __device__ constexpr size_t run_member_bytes() {
+  return (MODE == 0 ? sizeof(T) : MODE == 1 ? 2 * sizeof(T) : 4 * sizeof(T)) + sizeof(uint32_t);
+}
+__host__ __device__ constexpr size_t run_ws_bytes() { return (size_t)kRunMaxBlocks * kRunWarps * sizeof(double); }
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// MODE 0: forward, psi real.  MODE 1: reverse, psi and lam real, packed as
+// (psi, lam) in one complex slot.  MODE 2: reverse, psi and lam complex.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
+                                                             RunInfo run, const RunPart* __restrict__ parts,
+                                                             const RunBlk* __restrict__ blks, double* partial,
+                                                             int pmax, SecCompact cm) {
+  using V = typename SCx<T>::V;
+  constexpr bool ADJ = MODE != 0;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ uint32_t C[kBinom][kBinom];
+  __shared__ RunBlk sb[2];
+  __shared__ RunInfo R;
+  __shared__ RunPart P;
+  const int tid = threadIdx.x;
+  fill_binom(C);
+  if (tid == 0) {
+    R = run;
+    P = parts[run.part0 + blockIdx.x];
+  }
+  const int nb = run.b1 - run.b0;
+  auto blk_of = [&](int s) { return ADJ ? run.b1 - 1 - s : run.b0 + s; };
+  if (tid < kRunBlkWords)
+    reinterpret_cast<uint32_t*>(&sb[0])[tid] = __ldg(reinterpret_cast<const uint32_t*>(blks + blk_of(0)) + tid);
+  __syncthreads();
+  // shared memory: amplitudes, then compact indices, then (reverse) overlap slots
+  const uint32_t cap = R.maxsize;
+  T* ar = reinterpret_cast<T*>(dsm);   // MODE 0
+  V* av = reinterpret_cast<V*>(dsm);   // MODE 1, 2 (psi)
+  V* lv = av + cap;                    // MODE 2 (lam)
+  const size_t amp_bytes = align16((run_member_bytes<MODE, T>() - sizeof(uint32_t)) * cap);
+  uint32_t* gi = reinterpret_cast<uint32_t*>(dsm + amp_bytes);
+  double* ws = reinterpret_cast<double*>(dsm + align16(amp_bytes + sizeof(uint32_t) * cap));
+  const uint32_t size = P.cnta * P.cntb;
+  const T* pr = reinterpret_cast<const T*>(psi);
+  for (uint32_t m = tid; m < size; m += kRunThreads) {
+    const uint32_t ia = m / P.cntb, ib = m - ia * P.cntb;
+    const uint32_t sa = unrank_m(ia, R.apos, R.ua, P.ka, C) | P.ga;
+    const uint32_t sbm = unrank_m(ib, R.bpos, R.ub, P.kb, C) | P.gb;
+    const uint32_t g = (uint32_t)compact_index(cm, sa, sbm);
+    gi[m] = g;
+    if (MODE == 0) {
+      ar[m] = __ldcg(pr + 2 * (size_t)g);
+    } else {
+      av[m] = __ldcg(psi + g);
+      if (MODE == 2) lv[m] = __ldcg(lam + g);
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < nb; ++s) {
+    uint32_t nxt = 0;
+    if (s + 1 < nb && tid < kRunBlkWords)
+      nxt = __ldg(reinterpret_cast<const uint32_t*>(blks + blk_of(s + 1)) + tid);
+    const RunBlk& B = sb[s & 1];
+    double acc = 0.0;
+    const int ke = P.ka - B.e0, ko = P.kb - B.o0;
+    if (ke >= 0 && ke <= B.ne && ko >= 0 && ko <= B.no) {
+      const uint32_t co = C[B.no][ko];
+      const uint32_t items = C[B.ne][ke] * co;
+      unsigned cg = 0;  // sign-class bits from the part's occupation of G
+      if (B.nzc > 0) cg = par32s(B.zg[0][0] & P.ga) ^ par32s(B.zg[0][1] & P.gb);
+      if (B.nzc > 1) cg |= (par32s(B.zg[1][0] & P.ga) ^ par32s(B.zg[1][1] & P.gb)) << 1;
+      for (uint32_t it = tid; it < items; it += kRunThreads) {
+        const uint32_t ie = it / co, io = it - ie * co;
+        const uint32_t la = unrank_m(ie, B.epos, B.ne, ke, C), lb = unrank_m(io, B.opos, B.no, ko, C);
+        unsigned cls = cg;
+        if (B.nzc > 0) cls ^= par32s(B.zu[0][0] & la) ^ par32s(B.zu[0][1] & lb);
+        if (B.nzc > 1) cls ^= (par32s(B.zu[1][0] & la) ^ par32s(B.zu[1][1] & lb)) << 1;
+        // ranks of run-local strings: the general colex rank table
+        const uint32_t i0 = (uint32_t)__ldg(cm.ra + (la | B.pu[0][0])) * P.cntb + __ldg(cm.ra + (lb | B.pu[0][1]));
+        const uint32_t i1 = (uint32_t)__ldg(cm.ra + (la | B.pu[1][0])) * P.cntb + __ldg(cm.ra + (lb | B.pu[1][1]));
+        const T a00 = (T)B.m[cls][0][0], a01 = (T)B.m[cls][0][1], a10 = (T)B.m[cls][1][0], a11 = (T)B.m[cls][1][1];
+        if (MODE == 0) {
+          const T v0 = ar[i0], v1 = ar[i1];
+          ar[i0] = fma(a00, v0, fma(a01, v1, v0));
+          ar[i1] = fma(a10, v0, fma(a11, v1, v1));
+        } else if (MODE == 1) {
+          const V p0 = av[i0], p1 = av[i1];  // (psi, lambda)
+          acc = fma((double)p0.y, fma(B.q[cls][0][0], (double)p0.x, B.q[cls][0][1] * (double)p1.x), acc);
+          acc = fma((double)p1.y, fma(B.q[cls][1][0], (double)p0.x, B.q[cls][1][1] * (double)p1.x), acc);
+          V o0, o1;
+          o0.x = fma(a00, p0.x, fma(a01, p1.x, p0.x));
+          o0.y = fma(a00, p0.y, fma(a01, p1.y, p0.y));
+          o1.x = fma(a10, p0.x, fma(a11, p1.x, p1.x));
+          o1.y = fma(a10, p0.y, fma(a11, p1.y, p1.y));
+          av[i0] = o0;
+          av[i1] = o1;
+        } else {
+          const V v0 = av[i0], v1 = av[i1], w0 = lv[i0], w1 = lv[i1];
+          const double q00 = B.q[cls][0][0], q01 = B.q[cls][0][1], q10 = B.q[cls][1][0], q11 = B.q[cls][1][1];
+          acc += (double)w0.x * (q00 * v0.x + q01 * v1.x) + (double)w0.y * (q00 * v0.y + q01 * v1.y);
+          acc += (double)w1.x * (q10 * v0.x + q11 * v1.x) + (double)w1.y * (q10 * v0.y + q11 * v1.y);
+          V o0, o1;
+          o0.x = fma(a00, w0.x, fma(a01, w1.x, w0.x));
+          o0.y = fma(a00, w0.y, fma(a01, w1.y, w0.y));
+          o1.x = fma(a10, w0.x, fma(a11, w1.x, w1.x));
+          o1.y = fma(a10, w0.y, fma(a11, w1.y, w1.y));
+          lv[i0] = o0;
+          lv[i1] = o1;
+          o0.x = fma(a00, v0.x, fma(a01, v1.x, v0.x));
+          o0.y = fma(a00, v0.y, fma(a01, v1.y, v0.y));
+          o1.x = fma(a10, v0.x, fma(a11, v1.x, v1.x));
+          o1.y = fma(a10, v0.y, fma(a11, v1.y, v1.y));
+          av[i0] = o0;
+          av[i1] = o1;
+        }
+      }
+    }
+    if (ADJ) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if ((tid & 31) == 0) ws[s * kRunWarps + (tid >> 5)] = acc;
+    }
+    if (s + 1 < nb && tid < kRunBlkWords) reinterpret_cast<uint32_t*>(&sb[(s + 1) & 1])[tid] = nxt;
+    __syncthreads();
+  }
+  if (ADJ) {  // this part's overlap with each block: its warps' sums in warp order
+    for (int s = tid; s < nb; s += kRunThreads) {
+      double v = 0.0;
+      for (int w = 0; w < kRunWarps; ++w) v += ws[s * kRunWarps + w];
+      partial[(size_t)blk_of(s) * pmax + blockIdx.x] = v;
+    }
+  }
+  T* pw = reinterpret_cast<T*>(psi);
+  for (uint32_t m = tid; m < size; m += kRunThreads) {
+    const uint32_t g = gi[m];
+    if (MODE == 0) {
+      __stcg(pw + 2 * (size_t)g, ar[m]);
+    } else {
+      __stcg(psi + g, av[m]);
+      if (MODE == 2) __stcg(lam + g, lv[m]);
+    }
+  }
+}
+
+// out[b] = sum over the parts of block b's run of partial[b * pmax + part], in part order.
+__global__ void k_sector_reduce_parts(const double* __restrict__ partial, int pmax, const RunBlk* __restrict__ blks,
+                                      int nblk, double* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  const int np = blks[b].np;
+  double s = 0.0;
+  for (int p = 0; p < np; ++p) s += partial[(size_t)b * pmax + p];
+  out[b] = s;
 }
 
 // out[b] = sum of partial[b * nslot .. b * nslot + nslot), in slot order.
@@ -528,6 +719,86 @@ cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, boo
   count_launch();
   if (e == cudaSuccess && adj) {
     k_sector_reduce_rows<<<(nblk + 255) / 256, 256, 0, s>>>(partial, grid * (kSweepThreads / 32), nblk, out);
+    e = cudaGetLastError();
+    count_launch();
+  }
+  prof_post(prof_slot_, s);
+  return e;
+}
+
+static size_t run_smem_max() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  // the kernel's static shared memory (binomials, two descriptors, run, part) and a margin
+  return (size_t)std::max(0, v - 4096);
+}
+
+template <int MODE, typename T>
+static size_t run_smem_bytes(uint32_t maxsize) {
+  const size_t amp = align16((run_member_bytes<MODE, T>() - sizeof(uint32_t)) * maxsize);
+  return align16(amp + sizeof(uint32_t) * maxsize) + (MODE != 0 ? run_ws_bytes() : 0);
+}
+
+template <int MODE, typename T>
+static uint32_t run_capacity_t() {
+  const size_t avail = run_smem_max();
+  const size_t fixed = 64 + (MODE != 0 ? run_ws_bytes() : 0);
+  return avail > fixed ? (uint32_t)((avail - fixed) / run_member_bytes<MODE, T>()) : 0u;
+}
+
+uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst) {
+  const int mode = !adj ? 0 : realst ? 1 : 2;
+  if (dt == QF_C128)
+    return mode == 0 ? run_capacity_t<0, double>() : mode == 1 ? run_capacity_t<1, double>() : run_capacity_t<2, double>();
+  return mode == 0 ? run_capacity_t<0, float>() : mode == 1 ? run_capacity_t<1, float>() : run_capacity_t<2, float>();
+}
+
+template <int MODE, typename T>
+static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, const RunPart* parts,
+                          const RunBlk* blks, double* partial, int pmax, const SecCompact& cm, cudaStream_t s) {
+  using V = typename SCx<T>::V;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_sector_run<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)run_smem_max());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  for (int r = 0; r < nruns; ++r) {
+    const RunInfo& R = runs[MODE != 0 ? nruns - 1 - r : r];
+    const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
+    if (smem > run_smem_max() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
+    k_sector_run<MODE, T><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
+                                                              blks, partial, pmax, cm);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
+                               int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
+                               int pmax, double* out, const SecCompact& cm, cudaStream_t s) {
+  if (nblk <= 0 || nruns <= 0) return cudaSuccess;
+  if (!cm.ra) return cudaErrorInvalidValue;
+  const int prof_slot_ = prof_pre(adj ? QF_K_ADJ_SPARSE : QF_K_SPARSE, s);
+  const int mode = !adj ? 0 : realst ? 1 : 2;
+  cudaError_t e;
+  if (dt == QF_C128)
+    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s)
+      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s)
+                  : runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s);
+  else
+    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s)
+      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s)
+                  : runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s);
+  if (e == cudaSuccess && adj) {
+    k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
     count_launch();
   }
