@@ -1228,7 +1228,7 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
     const qf::SecSpace sp = sector_space(st->n, st->sec_a, st->sec_b);
     QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, p->rk, p->d_secgroups,
                                    p->d_seclarge, p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter,
-                                   st->d_out, nb, qf::SecCompact{}, st->stream));
+                                   st->d_out, kPartials / 2, qf::SecCompact{}, st->stream));
   } else {
     QF_CUDA(qf::launch_expect(st->psi, st->n, st->dt, p->d_groups, p->ngroups, p->d_echunks, st->d_partials,
                               st->d_counter, st->d_out, nb, st->stream));
@@ -1404,9 +1404,8 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
       QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
                                      (int)nblk, nullptr, rs.pmax, nullptr, cm, st->stream));
       double* d_e = st->d_out + nblk;
-      const int nbk = qf::reduce_blocks(n, st->dt);
       QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
-                                     p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, nbk, cm,
+                                     p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
                                      st->stream));
       QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
                                      (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, st->stream));

@@ -266,7 +266,8 @@ cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool
                                int pmax, double* out, const SecCompact& cm, cudaStream_t s);
 // Largest part (members) launch_sector_runs accepts for this dtype and direction.
 uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst);
-// With cm.ra != NULL psi and lam are in the compact layout.
+// With cm.ra != NULL psi and lam are in the compact layout.  nblocks: the
+// most CTAs the reduction may use (partials holds 2 * nblocks doubles).
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
                                const SecRank& rk, const SecGroup* all, const SecGroup* large, int nlarge,
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,

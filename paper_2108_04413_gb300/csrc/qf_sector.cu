@@ -806,23 +806,43 @@ cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool
   return e;
 }
 
+// Grid of the sector H|psi>: every CTA the SMs hold at once (grid-stride loop
+// over members), at most max_blocks (the reduction's partial slots).
+template <typename K>
+static unsigned hpsi_grid(K kernel, uint64_t items, int max_blocks) {
+  static int resident = -1;  // one per kernel instantiation
+  if (resident < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+    resident = std::max(1, sms) * std::max(1, per_sm);
+  }
+  const uint64_t want = (items + 255) / 256;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::min(resident, max_blocks)));
+}
+
 template <typename T, bool REALST, bool LAMY, bool COMPACT>
-static void hpsi_t(const void* psi, void* lam, bool narrow, unsigned g, const SecSpace& sp, const SecRank& rk,
+static void hpsi_t(const void* psi, void* lam, bool narrow, int max_blocks, const SecSpace& sp, const SecRank& rk,
                    const SecGroup* all, const SecGroup* large, int nlarge, const ExpChunk* chunks, double* partials,
                    unsigned* counter, double* out, const SecCompact& cm, cudaStream_t s) {
   using V = typename SCx<T>::V;
   const V* p = static_cast<const V*>(psi);
   V* l = static_cast<V*>(lam);
-  if (narrow)
-    k_sector_hpsi<T, REALST, true, LAMY, COMPACT><<<g, 256, 0, s>>>(p, l, sp, rk, all, large, nlarge, chunks,
-                                                                     partials, counter, out, cm);
-  else
-    k_sector_hpsi<T, REALST, false, LAMY, COMPACT><<<g, 256, 0, s>>>(p, l, sp, rk, all, large, nlarge, chunks,
-                                                                      partials, counter, out, cm);
+  const uint64_t items = (uint64_t)sp.cnt_e * sp.cnt_o;
+  if (narrow) {
+    const auto k = k_sector_hpsi<T, REALST, true, LAMY, COMPACT>;
+    k<<<hpsi_grid(k, items, max_blocks), 256, 0, s>>>(p, l, sp, rk, all, large, nlarge, chunks, partials, counter,
+                                                      out, cm);
+  } else {
+    const auto k = k_sector_hpsi<T, REALST, false, LAMY, COMPACT>;
+    k<<<hpsi_grid(k, items, max_blocks), 256, 0, s>>>(p, l, sp, rk, all, large, nlarge, chunks, partials, counter,
+                                                      out, cm);
+  }
 }
 
 template <typename T>
-static cudaError_t hpsi_dispatch(const void* psi, void* lam, bool realst, bool narrow, unsigned g,
+static cudaError_t hpsi_dispatch(const void* psi, void* lam, bool realst, bool narrow, int g,
                                  const SecSpace& sp, const SecRank& rk, const SecGroup* all,
                                  const SecGroup* large, int nlarge, const ExpChunk* chunks, double* partials,
                                  unsigned* counter, double* out, const SecCompact& cm, cudaStream_t s) {
@@ -853,8 +873,7 @@ cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool rea
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
                                int nblocks, const SecCompact& cm, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_HPSI, s);
-  const uint64_t items = (uint64_t)sp.cnt_e * sp.cnt_o;
-  const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, (uint64_t)nblocks));
+  const int g = nblocks;  // partial slots available: the grid's upper bound
   const bool narrow = sp.ne + sp.no <= 32;
   const cudaError_t e =
       (dt == QF_C128)
