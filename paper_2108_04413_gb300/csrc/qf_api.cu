@@ -246,37 +246,90 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     g.x = kv.first;
     g.h = hibit(kv.first);
     g.chunk0 = (int)ech.size();
-    const std::vector<size_t>& idx = kv.second;
-    g.nchunk = (int)((idx.size() + qf::kChunkTerms - 1) / qf::kChunkTerms);
     g.flags = 0;
-    for (size_t k = 0; k < idx.size(); k += qf::kChunkTerms) {
+    const std::vector<size_t>& idx = kv.second;
+    for (size_t i : idx) g.flags |= (popc(terms[i].x & terms[i].z) & 1) ? 2 : 1;
+    // A chunk holds terms whose Z masks are combinations (over GF(2)) of at most
+    // kChunkTerms basis masks: the table entry for the basis parities `pat` sums
+    // the terms with the sign (-1)^{popc(a_t & pat)}, a_t the term's coordinates.
+    // When the whole group spans at most kChunkTerms dimensions it is one chunk;
+    // otherwise each chunk takes kChunkTerms terms as its own basis.
+    std::vector<std::vector<size_t>> parts;
+    std::vector<std::vector<uint32_t>> coords;
+    std::vector<std::vector<uint64_t>> bases;
+    {
+      std::vector<uint64_t> B, E;  // basis (term masks), echelon copies (pivot = highest bit, descending)
+      std::vector<uint32_t> Cb;    // E[i] as a combination of B
+      std::vector<uint32_t> a(idx.size());
+      bool fits = true;
+      for (size_t t = 0; t < idx.size() && fits; ++t) {
+        uint64_t v = terms[idx[t]].z;
+        uint32_t comb = 0;
+        for (size_t i = 0; i < E.size(); ++i)
+          if ((v >> hibit(E[i])) & 1ull) {
+            v ^= E[i];
+            comb ^= Cb[i];
+          }
+        if (v == 0) {
+          a[t] = comb;
+          continue;
+        }
+        if ((int)B.size() == qf::kChunkTerms) {
+          fits = false;
+          break;
+        }
+        const uint32_t j = (uint32_t)B.size();
+        B.push_back(terms[idx[t]].z);
+        size_t pos = 0;  // keep E sorted by pivot, descending
+        while (pos < E.size() && hibit(E[pos]) > hibit(v)) ++pos;
+        E.insert(E.begin() + pos, v);
+        Cb.insert(Cb.begin() + pos, comb ^ (1u << j));
+        a[t] = 1u << j;
+      }
+      if (fits) {
+        parts.push_back(idx);
+        coords.push_back(a);
+        bases.push_back(B);
+      } else {
+        for (size_t k = 0; k < idx.size(); k += qf::kChunkTerms) {
+          const size_t cnt = std::min<size_t>(qf::kChunkTerms, idx.size() - k);
+          std::vector<size_t> ps(idx.begin() + k, idx.begin() + k + cnt);
+          std::vector<uint32_t> cs(cnt);
+          std::vector<uint64_t> bs(cnt);
+          for (size_t t = 0; t < cnt; ++t) {
+            cs[t] = 1u << t;
+            bs[t] = terms[ps[t]].z;
+          }
+          parts.push_back(ps);
+          coords.push_back(cs);
+          bases.push_back(bs);
+        }
+      }
+    }
+    g.nchunk = (int)parts.size();
+    for (size_t c = 0; c < parts.size(); ++c) {
       qf::ExpChunk ce{}, ch{};
-      const int cnt = (int)std::min<size_t>(qf::kChunkTerms, idx.size() - k);
-      for (int t = 0; t < qf::kChunkTerms; ++t) ce.z[t] = ch.z[t] = (t < cnt) ? terms[idx[k + t]].z : 0ull;
+      for (int t = 0; t < qf::kChunkTerms; ++t) ce.z[t] = ch.z[t] = (t < (int)bases[c].size()) ? bases[c][t] : 0ull;
       for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat) {
         double ex = 0, ey = 0, hx = 0, hy = 0;
-        for (int t = 0; t < cnt; ++t) {
-          const qf_term& T = terms[idx[k + t]];
+        for (size_t t = 0; t < parts[c].size(); ++t) {
+          const qf_term& T = terms[parts[c][t]];
           const int y = popc(T.x & T.z) & 3;
-          const double sg = ((pat >> t) & 1) ? -1.0 : 1.0;
-          const double c = T.coeff * sg;
+          const double sg = (popc(coords[c][t] & (uint32_t)pat) & 1) ? -1.0 : 1.0;
+          const double cf = T.coeff * sg;
           if ((y & 1) == 0) {
             const double ph = (y == 2) ? -1.0 : 1.0;  // i^y
-            hx += c * ph;
-            ex += (g.x == 0 ? 1.0 : 2.0) * c * ph;
+            hx += cf * ph;
+            ex += (g.x == 0 ? 1.0 : 2.0) * cf * ph;
           } else {
-            hy += c * ((y == 3) ? -1.0 : 1.0);        // i^y = +-i
-            ey += 2.0 * c * ((y == 1) ? -1.0 : 1.0);  // 2 c (-1)^{(y+1)/2}
+            hy += cf * ((y == 3) ? -1.0 : 1.0);        // i^y = +-i
+            ey += 2.0 * cf * ((y == 1) ? -1.0 : 1.0);  // 2 c (-1)^{(y+1)/2}
           }
         }
         ce.tab[pat] = make_double2(ex, ey);
         ch.tab[pat] = make_double2(hx, hy);
         ce.ftab[pat] = make_float2((float)ex, (float)ey);
         ch.ftab[pat] = make_float2((float)hx, (float)hy);
-      }
-      for (int t = 0; t < cnt; ++t) {
-        const qf_term& T = terms[idx[k + t]];
-        g.flags |= (popc(T.x & T.z) & 1) ? 2 : 1;
       }
       ech.push_back(ce);
       hch.push_back(ch);
@@ -668,6 +721,11 @@ bool to_secblk(const qf::SparseArgs& a, int n, int na, int nb, bool need_q, qf::
         if (a.M[c][i][j].y != 0.0) return false;
         if (need_q && a.Q[c][i][j].x != 0.0) return false;
       }
+  // the reverse sweep takes Qi = [[0, q01], [-q01, 0]] (the generator only links
+  // the two active patterns)
+  if (need_q)
+    for (int c = 0; c < ncls; ++c)
+      if (a.Q[c][0][0].y != 0.0 || a.Q[c][1][1].y != 0.0 || a.Q[c][1][0].y != -a.Q[c][0][1].y) return false;
   uint64_t U = 0;
   for (int i = 0; i < a.u; ++i) U |= 1ull << a.supp[i];
   std::memset(o, 0, sizeof(*o));
@@ -1028,12 +1086,12 @@ uint64_t typical_items(const qf::SecBlk* b, size_t n) {
 
 qf_status flush_sector(qf_state* st, std::vector<qf::SecBlk>& pend) {
   if (pend.empty()) return QF_OK;
-  const int grid = qf::sector_sweep_grid(st->dt, false, true, typical_items(pend.data(), pend.size()));
+  const int grid = qf::sector_sweep_grid(typical_items(pend.data(), pend.size()));
   qf_status bs = ensure_sector_buffers(st, pend.size(), 1);
   if (bs != QF_OK) return bs;
   QF_CUDA(h2d(st->d_secblk, pend.data(), pend.size() * sizeof(qf::SecBlk), st->stream));
-  QF_CUDA(qf::launch_sector_sweep(st->psi, nullptr, st->dt, false, st->real, st->d_secblk, (int)pend.size(),
-                                  st->d_bar, st->d_sec_partial, nullptr, grid, qf::SecCompact{}, st->stream));
+  QF_CUDA(qf::launch_sector_sweep(st->psi, st->dt, st->real, st->d_secblk, (int)pend.size(), st->d_bar, grid,
+                                  st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));  // the descriptor buffer is reused by the next flush
   pend.clear();
   return check_barrier(st);

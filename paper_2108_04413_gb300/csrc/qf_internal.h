@@ -241,20 +241,12 @@ cudaError_t launch_adj_rot(void* psi, void* lam, int n, qf_dtype dt, const RotAr
 cudaError_t launch_adj_sparse(void* psi, void* lam, int n, qf_dtype dt, const SparseArgs& a, bool realst,
                               double* partials, unsigned* counter, double* out, int nblocks, cudaStream_t s);
 
-// Sector sweep over nblk blocks in one cooperative launch (reverse when adj;
-// a reverse sweep with realst reads lambda from psi's imaginary slots:
-// out[b] = Im <lam|Q_b|psi> of block b, from partial[nblk * grid * 32]).  bar: 3
-// device words.  grid from sector_sweep_grid (typical_items: items of a typical block).
-// With cm.ra != NULL psi and lam are in the compact layout (SecCompact).
-int sector_sweep_grid(qf_dtype dt, bool adj, bool realst, uint64_t typical_items);
-cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const SecBlk* blks,
-                                int nblk, unsigned* bar, double* partial, double* out, int grid,
-                                const SecCompact& cm, cudaStream_t s);
-// lam = H psi on the sector (lam may be NULL), out[0] = <psi|H psi>, out[1] = <psi|psi>.
-// With realst and lam == psi, lambda's real part is written into psi's
-// imaginary slots (the packed form the reverse sweep of a real state reads).
-// Groups with <= 4 flipped qubits are reached by enumerating each member's
-// single and double flips (rk, indexing into `all`); `large` lists the others.
+// Forward sector sweep over nblk blocks in one cooperative launch, full
+// layout.  bar: 3 device words.  grid from sector_sweep_grid (typical_items:
+// items of a typical block).
+int sector_sweep_grid(uint64_t typical_items);
+cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBlk* blks, int nblk, unsigned* bar,
+                                int grid, cudaStream_t s);
 // Part-local sweep of all runs over a compact-layout state (forward: runs and
 // blocks in order, psi real; reverse: from the last, psi real and lam real
 // packed in psi's imaginary slots when realst, else separate complex states).

@@ -14,8 +14,10 @@
 // 0.85 M separate cache lines.
 //
 // * k_sector_sweep: every excitation block of a circuit in one persistent
-//   cooperative launch, with a grid barrier between consecutive blocks; for the
-//   reverse sweep it also records each block's gradient overlap per CTA.
+//   cooperative launch over the full layout, with a grid barrier between
+//   consecutive blocks (qf_apply_circuit).
+// * k_sector_run: the part-local sweeps of an energy and gradient evaluation
+//   (compact layout, forward and reverse with the gradient overlaps).
 // * k_sector_hpsi: lambda = H psi on the sector members only (the only part
 //   that enters <psi|lambda>, the gradient overlaps and the reverse sweep, since
 //   psi and every block stay in the sector), with <psi|lambda> and <psi|psi>.
@@ -54,22 +56,6 @@ __device__ __forceinline__ uint64_t unrank(uint32_t r, const uint8_t* pos, int m
     const uint32_t c = C[j][k];
     if (r >= c) {
       bits |= 1ull << pos[j];
-      r -= c;
-      --k;
-    }
-  }
-  return bits;
-}
-
-// The same subset as a mask of local indices (position p -> bit p >> 1, the
-// spin-orbital index of qubit p).
-__device__ __forceinline__ uint32_t unrank_l(uint32_t r, const uint8_t* pos, int m, int k,
-                                            const uint32_t (*C)[kBinom]) {
-  uint32_t bits = 0;
-  for (int j = m - 1; j >= 0 && k > 0; --j) {
-    const uint32_t c = C[j][k];
-    if (r >= c) {
-      bits |= 1u << (pos[j] >> 1);
       r -= c;
       --k;
     }
@@ -150,78 +136,31 @@ template <typename T> struct SCx;
 template <> struct SCx<double> { using V = double2; };
 template <> struct SCx<float> { using V = float2; };
 
-// One excitation block of a sector sweep (forward or reverse): the real 2x2
-// composite minus identity per sign class and, for the reverse sweep, the real
-// matrix Qi with Q = i Qi.
-// PACKED (reverse sweep of a real state): lambda's real part lives in psi's
-// (otherwise zero) imaginary slot, so one access reads or writes both states.
-template <bool ADJ, bool REALST, typename T, bool PACKED, bool COMPACT>
-__device__ void sector_block(typename SCx<T>::V* psi, typename SCx<T>::V* lam, const SecBlk& B,
-                             const uint32_t (*C)[kBinom], double* acc_out, const SecCompact& cm) {
+// One block on every sector member its outside positions allow (forward
+// sweep in the full layout): the two active rows take psi <- psi + (M - I) psi
+// with M chosen by the sign class.
+template <bool REALST, typename T>
+__device__ void sector_block(typename SCx<T>::V* psi, const SecBlk& B, const uint32_t (*C)[kBinom]) {
   using V = typename SCx<T>::V;
   const uint64_t items = (uint64_t)B.cnt_e * (uint64_t)B.cnt_o;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  double acc = 0.0;
   T* pr = reinterpret_cast<T*>(psi);
-  T* lr = reinterpret_cast<T*>(lam);
   for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items; it += stride) {
     const uint32_t i32 = (uint32_t)it;  // items < 2^32 (at most C(17,8)^2)
     const uint32_t ie = i32 / B.cnt_o, io = i32 - ie * B.cnt_o;
+    const uint64_t base = unrank(ie, B.epos, B.ne, B.ke, C) | unrank(io, B.opos, B.no, B.ko, C);
     unsigned cls = 0;
-    uint64_t i0, i1;
-    if (COMPACT) {
-      const uint32_t la = unrank_l(ie, B.epos, B.ne, B.ke, C), lb = unrank_l(io, B.opos, B.no, B.ko, C);
-      if (B.nzc > 0) cls = par32s(B.zl[0][0] & la) ^ par32s(B.zl[0][1] & lb);
-      if (B.nzc > 1) cls |= (par32s(B.zl[1][0] & la) ^ par32s(B.zl[1][1] & lb)) << 1;
-      i0 = compact_index(cm, la | B.pl[0][0], lb | B.pl[0][1]);
-      i1 = compact_index(cm, la | B.pl[1][0], lb | B.pl[1][1]);
-    } else {
-      const uint64_t base = unrank(ie, B.epos, B.ne, B.ke, C) | unrank(io, B.opos, B.no, B.ko, C);
-      if (B.nzc > 0) cls = par64s(B.zc[0] & base);
-      if (B.nzc > 1) cls |= par64s(B.zc[1] & base) << 1;
-      i0 = base | B.pat[0];
-      i1 = base | B.pat[1];
-    }
+    if (B.nzc > 0) cls = par64s(B.zc[0] & base);
+    if (B.nzc > 1) cls |= par64s(B.zc[1] & base) << 1;
+    const uint64_t i0 = base | B.pat[0], i1 = base | B.pat[1];
     const T a00 = (T)B.m[cls][0][0], a01 = (T)B.m[cls][0][1], a10 = (T)B.m[cls][1][0], a11 = (T)B.m[cls][1][1];
     // L2-coherent accesses: other SMs wrote these amplitudes before the last grid barrier
-    if (PACKED) {
-      const V p0 = __ldcg(psi + i0), p1 = __ldcg(psi + i1);  // (psi, lambda) real parts
-      acc = fma((double)p0.y, fma(B.q[cls][0][0], (double)p0.x, B.q[cls][0][1] * (double)p1.x), acc);
-      acc = fma((double)p1.y, fma(B.q[cls][1][0], (double)p0.x, B.q[cls][1][1] * (double)p1.x), acc);
-      V o0, o1;
-      o0.x = fma(a00, p0.x, fma(a01, p1.x, p0.x));
-      o0.y = fma(a00, p0.y, fma(a01, p1.y, p0.y));
-      o1.x = fma(a10, p0.x, fma(a11, p1.x, p1.x));
-      o1.y = fma(a10, p0.y, fma(a11, p1.y, p1.y));
-      __stcg(psi + i0, o0);
-      __stcg(psi + i1, o1);
-    } else if (REALST) {
+    if (REALST) {
       const T v0 = __ldcg(pr + 2 * i0), v1 = __ldcg(pr + 2 * i1);
-      if (ADJ) {
-        const T w0 = __ldcg(lr + 2 * i0), w1 = __ldcg(lr + 2 * i1);
-        // Im <lam|Q|psi> = Re <lam|Qi|psi> for real Qi
-        acc = fma((double)w0, fma(B.q[cls][0][0], (double)v0, B.q[cls][0][1] * (double)v1), acc);
-        acc = fma((double)w1, fma(B.q[cls][1][0], (double)v0, B.q[cls][1][1] * (double)v1), acc);
-        __stcg(lr + 2 * i0, fma(a00, w0, fma(a01, w1, w0)));
-        __stcg(lr + 2 * i1, fma(a10, w0, fma(a11, w1, w1)));
-      }
       __stcg(pr + 2 * i0, fma(a00, v0, fma(a01, v1, v0)));
       __stcg(pr + 2 * i1, fma(a10, v0, fma(a11, v1, v1)));
     } else {
       const V v0 = __ldcg(psi + i0), v1 = __ldcg(psi + i1);
-      if (ADJ) {
-        const V w0 = __ldcg(lam + i0), w1 = __ldcg(lam + i1);
-        const double q00 = B.q[cls][0][0], q01 = B.q[cls][0][1], q10 = B.q[cls][1][0], q11 = B.q[cls][1][1];
-        acc += (double)w0.x * (q00 * v0.x + q01 * v1.x) + (double)w0.y * (q00 * v0.y + q01 * v1.y);
-        acc += (double)w1.x * (q10 * v0.x + q11 * v1.x) + (double)w1.y * (q10 * v0.y + q11 * v1.y);
-        V o0, o1;
-        o0.x = fma(a00, w0.x, fma(a01, w1.x, w0.x));
-        o0.y = fma(a00, w0.y, fma(a01, w1.y, w0.y));
-        o1.x = fma(a10, w0.x, fma(a11, w1.x, w1.x));
-        o1.y = fma(a10, w0.y, fma(a11, w1.y, w1.y));
-        __stcg(lam + i0, o0);
-        __stcg(lam + i1, o1);
-      }
       V o0, o1;
       o0.x = fma(a00, v0.x, fma(a01, v1.x, v0.x));
       o0.y = fma(a00, v0.y, fma(a01, v1.y, v0.y));
@@ -231,7 +170,6 @@ __device__ void sector_block(typename SCx<T>::V* psi, typename SCx<T>::V* lam, c
       __stcg(psi + i1, o1);
     }
   }
-  if (ADJ) *acc_out = acc;
 }
 
 __device__ double block_sum_s(double v) {
@@ -251,37 +189,26 @@ __device__ double block_sum_s(double v) {
   return v;
 }
 
-// Persistent sweep over blocks [0, nblk) (forward: in order; reverse: from the
-// last).  The next block's descriptor is loaded while the current one runs.
-// Reverse: partial[(b * gridDim.x + cta) * 32 + warp] receives block b's overlap
-// summed over one warp (reduced in a fixed order afterwards).  A one-CTA grid
+// Persistent forward sweep over blocks [0, nblk) in the full layout.  The next
+// block's descriptor is loaded while the current one runs.  A one-CTA grid
 // needs no grid barrier.
 constexpr int kDescWords = sizeof(SecBlk) / 4;
 static_assert(sizeof(SecBlk) % 4 == 0 && kDescWords <= 1024, "descriptor copy layout");
 
-template <bool ADJ, bool REALST, typename T, bool PACKED, bool COMPACT>
-__global__ void __launch_bounds__(kSweepThreads) k_sector_sweep(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
-                                                      const SecBlk* __restrict__ blks, int nblk, unsigned* bar,
-                                                      double* partial, SecCompact cm) {
+template <bool REALST, typename T>
+__global__ void __launch_bounds__(kSweepThreads) k_sector_sweep(typename SCx<T>::V* psi,
+                                                                const SecBlk* __restrict__ blks, int nblk,
+                                                                unsigned* bar) {
   __shared__ uint32_t C[kBinom][kBinom];
   __shared__ SecBlk sb[2];  // current and next block descriptions
   fill_binom(C);
   const int tid = threadIdx.x;
-  auto block_of = [&](int s) { return ADJ ? (nblk - 1 - s) : s; };
-  if (tid < kDescWords) reinterpret_cast<uint32_t*>(&sb[0])[tid] = __ldcg(reinterpret_cast<const uint32_t*>(blks + block_of(0)) + tid);
+  if (tid < kDescWords) reinterpret_cast<uint32_t*>(&sb[0])[tid] = __ldcg(reinterpret_cast<const uint32_t*>(blks) + tid);
   __syncthreads();
   for (int s = 0; s < nblk; ++s) {
-    const int b = block_of(s);
     uint32_t nxt = 0;
-    if (s + 1 < nblk && tid < kDescWords)
-      nxt = __ldcg(reinterpret_cast<const uint32_t*>(blks + block_of(s + 1)) + tid);
-    double acc = 0.0;
-    sector_block<ADJ, REALST, T, PACKED, COMPACT>(psi, lam, sb[s & 1], C, &acc, cm);
-    if (ADJ) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if ((tid & 31) == 0) partial[((size_t)b * gridDim.x + blockIdx.x) * 32 + (tid >> 5)] = acc;
-    }
+    if (s + 1 < nblk && tid < kDescWords) nxt = __ldcg(reinterpret_cast<const uint32_t*>(blks + s + 1) + tid);
+    sector_block<REALST, T>(psi, sb[s & 1], C);
     if (s + 1 < nblk) {
       if (tid < kDescWords) reinterpret_cast<uint32_t*>(&sb[(s + 1) & 1])[tid] = nxt;
       if (gridDim.x == 1) {
@@ -408,8 +335,8 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
           ar[i1] = fma(a10, v0, fma(a11, v1, v1));
         } else if (MODE == 1) {
           const V p0 = av[i0], p1 = av[i1];  // (psi, lambda)
-          acc = fma((double)p0.y, fma(B.q[cls][0][0], (double)p0.x, B.q[cls][0][1] * (double)p1.x), acc);
-          acc = fma((double)p1.y, fma(B.q[cls][1][0], (double)p0.x, B.q[cls][1][1] * (double)p1.x), acc);
+          // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
+          acc = fma(B.q[cls][0][1], fma((double)p0.y, (double)p1.x, -(double)p1.y * (double)p0.x), acc);
           V o0, o1;
           o0.x = fma(a00, p0.x, fma(a01, p1.x, p0.x));
           o0.y = fma(a00, p0.y, fma(a01, p1.y, p0.y));
@@ -476,14 +403,6 @@ __global__ void k_sector_reduce_parts(const double* __restrict__ partial, int pm
   out[b] = s;
 }
 
-// out[b] = sum of partial[b * nslot .. b * nslot + nslot), in slot order.
-__global__ void k_sector_reduce_rows(const double* __restrict__ partial, int nslot, int nblk, double* out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nblk) return;
-  double s = 0.0;
-  for (int c = 0; c < nslot; ++c) s += partial[(size_t)b * nslot + c];
-  out[b] = s;
-}
 
 // D_g(b) psi(b) added to (lx, ly) for one connected group; psi(b) is stored at psi[a].
 template <typename T, bool REALST, bool NARROW>
@@ -663,7 +582,7 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
 // Grid of the cooperative sweep: about one item per thread for a typical block,
 // at most one CTA per SM (all CTAs must be resident at once; a 1024-thread CTA
 // under __launch_bounds__ always fits one per SM).
-int sector_sweep_grid(qf_dtype, bool, bool, uint64_t typical_items) {
+int sector_sweep_grid(uint64_t typical_items) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -671,33 +590,13 @@ int sector_sweep_grid(qf_dtype, bool, bool, uint64_t typical_items) {
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(1, sms)));
 }
 
-template <bool ADJ, bool REALST, typename T, bool COMPACT>
-static cudaError_t sweep_t(void* psi, void* lam, const SecBlk* blks, int nblk, unsigned* bar, double* partial,
-                           int grid, SecCompact cm, cudaStream_t s) {
+template <bool REALST, typename T>
+static cudaError_t sweep_t(void* psi, const SecBlk* blks, int nblk, unsigned* bar, int grid, cudaStream_t s) {
   using V = typename SCx<T>::V;
   V* p = static_cast<V*>(psi);
-  V* l = static_cast<V*>(lam);
-  void* args[] = {&p, &l, &blks, &nblk, &bar, &partial, &cm};
-  // reverse sweeps of real states keep lambda in psi's imaginary slots
-  constexpr bool PK = ADJ && REALST;
-  return cudaLaunchCooperativeKernel((const void*)k_sector_sweep<ADJ, REALST, T, PK, COMPACT>, dim3(grid),
-                                     dim3(kSweepThreads), args, 0, s);
-}
-
-template <typename T>
-static cudaError_t sweep_dispatch(void* psi, void* lam, bool adj, bool realst, const SecBlk* blks, int nblk,
-                                  unsigned* bar, double* partial, int grid, const SecCompact& cm, cudaStream_t s) {
-  if (!cm.ra) {  // full layout: forward sweeps only
-    if (adj) return cudaErrorInvalidValue;
-    return realst ? sweep_t<false, true, T, false>(psi, lam, blks, nblk, bar, partial, grid, cm, s)
-                  : sweep_t<false, false, T, false>(psi, lam, blks, nblk, bar, partial, grid, cm, s);
-  }
-  if (!adj) {  // compact forward: the real state of an energy evaluation
-    if (!realst) return cudaErrorInvalidValue;
-    return sweep_t<false, true, T, true>(psi, lam, blks, nblk, bar, partial, grid, cm, s);
-  }
-  return realst ? sweep_t<true, true, T, true>(psi, lam, blks, nblk, bar, partial, grid, cm, s)
-                : sweep_t<true, false, T, true>(psi, lam, blks, nblk, bar, partial, grid, cm, s);
+  void* args[] = {&p, &blks, &nblk, &bar};
+  return cudaLaunchCooperativeKernel((const void*)k_sector_sweep<REALST, T>, dim3(grid), dim3(kSweepThreads), args,
+                                     0, s);
 }
 
 cudaError_t launch_wait_selftest(unsigned* words, double limit_s, cudaStream_t s) {
@@ -706,22 +605,20 @@ cudaError_t launch_wait_selftest(unsigned* words, double limit_s, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_sector_sweep(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const SecBlk* blks,
-                                int nblk, unsigned* bar, double* partial, double* out, int grid,
-                                const SecCompact& cm, cudaStream_t s) {
+cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBlk* blks, int nblk, unsigned* bar,
+                                int grid, cudaStream_t s) {
   if (nblk <= 0) return cudaSuccess;
-  const int prof_slot_ = prof_pre(adj ? QF_K_ADJ_SPARSE : QF_K_SPARSE, s);
+  const int prof_slot_ = prof_pre(QF_K_SPARSE, s);
   cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s);
   if (e == cudaSuccess) {
-    e = (dt == QF_C128) ? sweep_dispatch<double>(psi, lam, adj, realst, blks, nblk, bar, partial, grid, cm, s)
-                        : sweep_dispatch<float>(psi, lam, adj, realst, blks, nblk, bar, partial, grid, cm, s);
+    if (dt == QF_C128)
+      e = realst ? sweep_t<true, double>(psi, blks, nblk, bar, grid, s)
+                 : sweep_t<false, double>(psi, blks, nblk, bar, grid, s);
+    else
+      e = realst ? sweep_t<true, float>(psi, blks, nblk, bar, grid, s)
+                 : sweep_t<false, float>(psi, blks, nblk, bar, grid, s);
   }
   count_launch();
-  if (e == cudaSuccess && adj) {
-    k_sector_reduce_rows<<<(nblk + 255) / 256, 256, 0, s>>>(partial, grid * (kSweepThreads / 32), nblk, out);
-    e = cudaGetLastError();
-    count_launch();
-  }
   prof_post(prof_slot_, s);
   return e;
 }
