@@ -52,6 +52,7 @@ struct ExpPlan {
   qf::ExpGroup* d_groups = nullptr;
   qf::ExpChunk* d_echunks = nullptr;  // pair-form expectation weights
   qf::ExpChunk* d_hchunks = nullptr;  // H|psi> weights
+  long long* d_hfix = nullptr;        // their real parts in fixed point (SecRank::itab)
   int ngroups = 0;
   int nchunks = 0;
   // tiled H|psi>: groups in X order, 8-term tables, classes for 2^10 and 2^11 tiles
@@ -76,6 +77,7 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_groups);
   cudaFree(p.d_echunks);
   cudaFree(p.d_hchunks);
+  cudaFree(p.d_hfix);
   cudaFree(p.d_hgroups);
   cudaFree(p.d_wchunks);
   cudaFree(p.d_wchunks_f);
@@ -336,6 +338,26 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     }
     groups.push_back(g);
   }
+  // fixed-point real weights for groups of several chunks: the largest |D| such a
+  // group can reach, times 2^e, stays below 2^61
+  double maxabs = 0.0;
+  for (const qf::ExpGroup& g : groups) {
+    if (g.nchunk < 2) continue;
+    double m = 0.0;
+    for (int c = 0; c < g.nchunk; ++c) {
+      double cm = 0.0;
+      for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat) cm = std::max(cm, std::fabs(hch[g.chunk0 + c].tab[pat].x));
+      m += cm;
+    }
+    maxabs = std::max(maxabs, m);
+  }
+  int fix_e = 0;
+  if (maxabs > 0.0) fix_e = std::min(1000, 61 - (int)std::ceil(std::log2(maxabs)));
+  const double inv_fix = std::ldexp(1.0, -fix_e);
+  std::vector<long long> hfix(hch.size() << qf::kChunkTerms);
+  for (size_t c = 0; c < hch.size(); ++c)
+    for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat)
+      hfix[(c << qf::kChunkTerms) + pat] = std::llrint(std::ldexp(hch[c].tab[pat].x, fix_e));
   ExpPlan p;
   p.ngroups = (int)groups.size();
   p.nchunks = (int)ech.size();
@@ -408,6 +430,13 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     QF_CUDA(h2d(p.d_groups, groups.data(), groups.size() * sizeof(qf::ExpGroup), st->stream));
     QF_CUDA(h2d(p.d_echunks, ech.data(), ech.size() * sizeof(qf::ExpChunk), st->stream));
     QF_CUDA(h2d(p.d_hchunks, hch.data(), hch.size() * sizeof(qf::ExpChunk), st->stream));
+    if (cudaMalloc(&p.d_hfix, std::max<size_t>(1, hfix.size()) * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      p.d_hfix = nullptr;
+      free_plan(p);
+      return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
+    }
+    if (!hfix.empty()) QF_CUDA(h2d(p.d_hfix, hfix.data(), hfix.size() * sizeof(long long), st->stream));
     if (cudaMalloc(&p.d_secgroups, std::max<size_t>(1, sg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
         cudaMalloc(&p.d_seclarge, std::max<size_t>(1, lg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
         cudaMalloc(&p.d_rk, rkt.size() * sizeof(int)) != cudaSuccess) {
@@ -418,7 +447,8 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     if (!sg.empty()) QF_CUDA(h2d(p.d_secgroups, sg.data(), sg.size() * sizeof(qf::SecGroup), st->stream));
     if (!lg.empty()) QF_CUDA(h2d(p.d_seclarge, lg.data(), lg.size() * sizeof(qf::SecGroup), st->stream));
     QF_CUDA(h2d(p.d_rk, rkt.data(), rkt.size() * sizeof(int), st->stream));
-    p.rk = qf::SecRank{p.d_rk + o_sa, p.d_rk + o_sb, p.d_rk + o_aa, p.d_rk + o_bb, p.d_rk + o_ab, diag, ne, no};
+    p.rk = qf::SecRank{p.d_rk + o_sa, p.d_rk + o_sb, p.d_rk + o_aa, p.d_rk + o_bb, p.d_rk + o_ab, diag, ne, no,
+                       p.d_hfix, inv_fix};
     QF_CUDA(cudaStreamSynchronize(st->stream));
   }
   p.terms.assign(terms, terms + nt);

@@ -150,7 +150,7 @@ struct SecGroup {               // X group with its even/odd flip counts
 // Inside a part, members are numbered by (alpha string on U, beta string on
 // U) in "run-local" coordinates: U's alpha orbitals renumbered 0..ua-1 and its
 // beta orbitals 0..ub-1.
-constexpr int kRunMaxBlocks = 256;  // blocks per run (per-warp overlap slots in shared memory)
+constexpr int kRunMaxBlocks = 256;  // blocks per run (bounds one launch's length)
 struct RunBlk {                     // one excitation block inside its run
   uint8_t epos[kSecMaxPos], opos[kSecMaxPos];  // run-local U orbitals outside the support
   int ne, no;                       // their counts
@@ -201,6 +201,11 @@ struct SecRank {
   const int* ab;
   int diag;                     // the x = 0 group, or -1
   int ne, no;
+  // Real-part H|psi> weights in fixed point: itab[16 c + pat] = round(tab.x * 2^e)
+  // of chunk c, inv_fix = 2^-e.  Groups of several chunks sum them exactly in
+  // integer arithmetic.
+  const long long* itab;
+  double inv_fix;
 };
 
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.

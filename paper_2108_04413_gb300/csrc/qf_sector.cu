@@ -254,7 +254,6 @@ template <int MODE, typename T>
 __host__ __device__ constexpr size_t run_member_bytes() {
   return (MODE == 0 ? sizeof(T) : MODE == 1 ? 2 * sizeof(T) : 4 * sizeof(T)) + sizeof(uint32_t);
 }
-__host__ __device__ constexpr size_t run_ws_bytes() { return (size_t)kRunMaxBlocks * kRunWarps * sizeof(double); }
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // MODE 0: forward, psi real.  MODE 1: reverse, psi and lam real, packed as
@@ -289,7 +288,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   V* lv = av + cap;                    // MODE 2 (lam)
   const size_t amp_bytes = align16((run_member_bytes<MODE, T>() - sizeof(uint32_t)) * cap);
   uint32_t* gi = reinterpret_cast<uint32_t*>(dsm + amp_bytes);
-  double* ws = reinterpret_cast<double*>(dsm + align16(amp_bytes + sizeof(uint32_t) * cap));
+  __shared__ double ws[2][kRunWarps];  // per-warp overlaps of the current and the previous block
   const uint32_t size = P.cnta * P.cntb;
   const T* pr = reinterpret_cast<const T*>(psi);
   for (uint32_t m = tid; m < size; m += kRunThreads) {
@@ -368,15 +367,15 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     if (ADJ) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if ((tid & 31) == 0) ws[s * kRunWarps + (tid >> 5)] = acc;
+      if ((tid & 31) == 0) ws[s & 1][tid >> 5] = acc;
     }
     if (s + 1 < nb && tid < kRunBlkWords) reinterpret_cast<uint32_t*>(&sb[(s + 1) & 1])[tid] = nxt;
     __syncthreads();
-  }
-  if (ADJ) {  // this part's overlap with each block: its warps' sums in warp order
-    for (int s = tid; s < nb; s += kRunThreads) {
+    // this part's overlap with block s: its warps' sums in warp order (ws[s & 1] is
+    // rewritten only after the next barrier)
+    if (ADJ && tid == kRunThreads - 1) {
       double v = 0.0;
-      for (int w = 0; w < kRunWarps; ++w) v += ws[s * kRunWarps + w];
+      for (int w = 0; w < kRunWarps; ++w) v += ws[s & 1][w];
       partial[(size_t)blk_of(s) * pmax + blockIdx.x] = v;
     }
   }
@@ -405,24 +404,41 @@ __global__ void k_sector_reduce_parts(const double* __restrict__ partial, int pm
 
 
 // D_g(b) psi(b) added to (lx, ly) for one connected group; psi(b) is stored at psi[a].
+// A real state's groups of several chunks add their fixed-point weights exactly
+// and accumulate into lxs (in units of 2^-e).
+template <typename T, bool NARROW>
+__device__ __forceinline__ unsigned chunk_index(const ExpChunk* W, uint64_t b) {
+  unsigned idx = 0;
+  if (NARROW) {  // n <= 32: one 32-bit popcount per term
+    const uint32_t b32 = (uint32_t)b;
+#pragma unroll
+    for (int t = 0; t < kChunkTerms; ++t) idx |= ((unsigned)__popc((uint32_t)W->z[t] & b32) & 1u) << t;
+  } else {
+#pragma unroll
+    for (int t = 0; t < kChunkTerms; ++t) idx |= par64s(W->z[t] & b) << t;
+  }
+  return idx;
+}
+
 template <typename T, bool REALST, bool NARROW>
 __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict__ psi,
-                                            const ExpChunk* __restrict__ chunks, int chunk0, int nchunk, uint64_t b,
-                                            uint64_t a, double& lx, double& ly) {
+                                            const ExpChunk* __restrict__ chunks,
+                                            const long long* __restrict__ itab, int chunk0, int nchunk, uint64_t b,
+                                            uint64_t a, double& lx, double& ly, double& lxs) {
   using V = typename SCx<T>::V;
+  if (REALST && nchunk > 1) {
+    long long is = 0;
+    for (int k = 0; k < nchunk; ++k) {
+      const ExpChunk* W = chunks + chunk0 + k;
+      is += __ldg(itab + ((size_t)(chunk0 + k) << kChunkTerms) + chunk_index<T, NARROW>(W, b));
+    }
+    lxs = fma(__ll2double_rn(is), (double)reinterpret_cast<const T*>(psi)[2 * a], lxs);
+    return;
+  }
   double dx = 0.0, dy = 0.0;
   for (int k = 0; k < nchunk; ++k) {
     const ExpChunk* W = chunks + chunk0 + k;
-    unsigned idx = 0;
-    if (NARROW) {  // n <= 32: one 32-bit popcount per term
-      const uint32_t b32 = (uint32_t)b;
-#pragma unroll
-      for (int t = 0; t < kChunkTerms; ++t) idx |= ((unsigned)__popc((uint32_t)W->z[t] & b32) & 1u) << t;
-    } else {
-#pragma unroll
-      for (int t = 0; t < kChunkTerms; ++t) idx |= par64s(W->z[t] & b) << t;
-    }
-    const double2 d = W->tab[idx];
+    const double2 d = W->tab[chunk_index<T, NARROW>(W, b)];
     if (k == 0) {
       dx = d.x;
       dy = d.y;
@@ -488,11 +504,11 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
         vb[nvb++] = (uint8_t)q;
       }
     }
-    double lx = 0.0, ly = 0.0;
+    double lx = 0.0, ly = 0.0, lxs = 0.0;
     auto term = [&](const SecGroup& G) {
       const uint64_t b = c ^ G.x;
       const uint64_t a = COMPACT ? compact_index(cm, la ^ G.xa, lb ^ G.xb) : b;
-      sector_term<T, REALST, NARROW>(psi, chunks, G.chunk0, G.nchunk, b, a, lx, ly);
+      sector_term<T, REALST, NARROW>(psi, chunks, rk.itab, G.chunk0, G.nchunk, b, a, lx, ly, lxs);
     };
     auto visit = [&](int g) {
       if (g >= 0) term(all[g]);
@@ -531,6 +547,7 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
       term(G);
     }
     const uint64_t self = COMPACT ? it : c;
+    if (REALST) lx = fma(lxs, rk.inv_fix, lx);
     if (REALST) {  // real parts only: with LAMY the imaginary slots are lambda's
       const double ux = (double)reinterpret_cast<const T*>(psi)[2 * self];
       acc_e = fma(ux, lx, acc_e);
@@ -637,13 +654,13 @@ static size_t run_smem_max() {
 template <int MODE, typename T>
 static size_t run_smem_bytes(uint32_t maxsize) {
   const size_t amp = align16((run_member_bytes<MODE, T>() - sizeof(uint32_t)) * maxsize);
-  return align16(amp + sizeof(uint32_t) * maxsize) + (MODE != 0 ? run_ws_bytes() : 0);
+  return align16(amp + sizeof(uint32_t) * maxsize);
 }
 
 template <int MODE, typename T>
 static uint32_t run_capacity_t() {
   const size_t avail = run_smem_max();
-  const size_t fixed = 64 + (MODE != 0 ? run_ws_bytes() : 0);
+  const size_t fixed = 64;
   return avail > fixed ? (uint32_t)((avail - fixed) / run_member_bytes<MODE, T>()) : 0u;
 }
 
