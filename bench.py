@@ -333,8 +333,11 @@ def run_gpu(args, rank, world, local, pg):
     stats = group_stats(w["terms"], n)
     roof = roofline_for(dom, per_kind[dom], w, stats, n, S, pk, args.dtype)
     if dom in ("sparse", "adj_sparse"):
-        # sector sweeps: every excitation moves its two active amplitudes of each
-        # sector member pair once (read + write), for psi (and lambda in reverse)
+        # part-local sector sweeps: every excitation rotates the two active
+        # amplitudes of each sector member pair it touches (a real 2x2 rotation,
+        # 4 multiply-adds), for psi and, in reverse, lambda, plus the gradient
+        # overlap (2 multiply-adds).  The compact sector state is L2-resident, so
+        # the bound is the FP64 pipe.
         from math import comb
 
         ev = int(sum(1 << q for q in range(0, n, 2)))
@@ -348,16 +351,17 @@ def run_gpu(args, rank, world, local, pg):
             eb = len(occ) - ea
             ce = sum(1 for q in sup if q % 2 == 0)
             items += comb(ne - ce, na - ea) * comb(no - (len(sup) - ce), nb_ - eb)
-        nst = 2 if dom == "adj_sparse" else 1
-        s_eff = S // 2  # dUCC states are real: only the real part of each amplitude moves
-        by = items * 2 * 2 * nst * s_eff
+        rev = dom == "adj_sparse"
+        fl = items * (2 * (4 + 4 + 2) if rev else 2 * 4)
         avg_s = per_kind[dom]["ms"] / per_kind[dom]["launches"] / 1e3
-        roof = {"kernel": "k_sector_sweep (" + ("reverse" if nst == 2 else "forward") + ")", "bound": "hbm",
-                "achieved": by / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": by / avg_s / 1e9 / pk["hbm_gbs"], "traffic": None,
-                "algorithmic": (f"{by:.4g} B per launch: {items} (member, excitation) items x 2 amplitudes x "
-                                f"read+write x {nst} state(s) x {s_eff} B (real part)"),
-                "note": "one persistent launch over all excitations; time is set by the grid-barrier chain"}
+        roof = {"kernel": "k_sector_run (" + ("reverse" if rev else "forward") + ")", "bound": "alu",
+                "achieved": fl / avg_s / 1e12, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": fl / avg_s / 1e12 / pk["fp64_tflops"], "traffic": None,
+                "algorithmic": (f"{fl:.4g} FP64 flop per sweep: {items} (member pair, excitation) items x "
+                                + ("(4 + 4 multiply-adds rotating psi and lambda + 2 for the overlap)"
+                                   if rev else "4 multiply-adds rotating psi") + " x 2 flop"),
+                "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock (derived)",
+                "note": "one launch per run of excitations; the compact sector state stays in L2"}
     if dom == "hpsi":
         # the dUCC state stays in one (alpha, beta) sector, where H|psi> runs on members only
         na = bin(w["det"] & int(sum(1 << q for q in range(0, n, 2)))).count("1")
@@ -382,7 +386,7 @@ def run_gpu(args, rank, world, local, pg):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f64 (H|psi> multiply-adds in double-single, ~2^-46; see hpsi_fp64_mode)"
+        "dtype": ("f64 (sector H|psi> weight sums in exact 64-bit fixed point)"
                   if args.dtype == "c128" else "f32 state, f64 reductions"),
         "data": "synthetic (seeded integrals, dUCCSD amplitudes)",
         "config": {
@@ -392,7 +396,6 @@ def run_gpu(args, rank, world, local, pg):
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "l2": f"state {N * S >> 20} MiB > 129 MB L2 (no flush needed)",
         },
-        "rotations_amplitudes_per_s": value * 3 * len(w["ansatz"]) * N,
         "energy": float(energies[-1]),
         "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps} for k, v in per_kind.items()},
         "roofline": roof,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "qf_internal.h"
+#include "qf_pool.h"
 
 using cplx = std::complex<double>;
 
@@ -89,18 +91,43 @@ void free_plan(ExpPlan& p) {
   p = ExpPlan();
 }
 
-uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull) {
+// Content key of a host array: four independent multiply-rotate lanes over
+// 8-byte words (the tail byte-wise), then a xor-shift-multiply finish.  Used to
+// recognise a term list or an ansatz seen before; a different array colliding
+// has probability ~2^-64.
+inline uint64_t rotl64(uint64_t v, int s) { return (v << s) | (v >> (64 - s)); }
+uint64_t content_key(const void* data, size_t bytes, uint64_t seed = 0x243F6A8885A308D3ull) {
   const unsigned char* p = static_cast<const unsigned char*>(data);
-  for (size_t i = 0; i < bytes; ++i) {
-    h ^= p[i];
-    h *= 1099511628211ull;
-  }
-  return h;
+  const uint64_t K1 = 0x9E3779B97F4A7C15ull, K2 = 0xC2B2AE3D27D4EB4Full;
+  uint64_t h[4] = {seed, seed ^ K1, seed ^ K2, seed + bytes};
+  size_t i = 0;
+  for (; i + 32 <= bytes; i += 32)
+    for (int l = 0; l < 4; ++l) {
+      uint64_t w;
+      std::memcpy(&w, p + i + 8 * l, 8);
+      h[l] = rotl64(h[l] ^ (w * K2), 31) * K1;
+    }
+  uint64_t v = h[0] ^ rotl64(h[1], 17) ^ rotl64(h[2], 33) ^ rotl64(h[3], 49);
+  for (; i < bytes; ++i) v = (v ^ p[i]) * K1;
+  v ^= v >> 32;
+  v *= 0xD6E8FEB86659FD93ull;
+  v ^= v >> 32;
+  v *= 0xD6E8FEB86659FD93ull;
+  v ^= v >> 32;
+  return v;
 }
 
 }  // namespace
 
 void qf::set_last_error(const std::string& msg) { t_err = msg; }
+
+// The part-local run plan of an ansatz in one sector (see build_runs).
+struct SectorRuns {
+  std::vector<qf::RunInfo> runs;
+  std::vector<qf::RunPart> parts;
+  std::vector<qf::RunBlk> blks;  // forward blocks, then inverse blocks (m, q refilled per call)
+  int pmax = 0;
+};
 
 struct qf_state {
   int n = 0;
@@ -146,7 +173,16 @@ struct qf_state {
     bool sparse;
     qf::SparseArgs fwd, inv;
   };
-  std::unordered_map<uint64_t, std::vector<Blk>> ansatz_plans;
+  struct AnsatzPlan {
+    std::vector<Blk> blocks;
+    // sector run plan, built for (sec_n, sec_na, sec_nb) on first use there
+    int sec_n = -1, sec_na = -1, sec_nb = -1;
+    uint64_t sec_cap = 0;
+    bool sec_ok = false;
+    SectorRuns runs;
+  };
+  std::unordered_map<uint64_t, AnsatzPlan> ansatz_plans;
+  uint64_t parts_key = 0;  // the ansatz plan and sector whose run parts sit in d_runblk
   size_t elem() const { return dt == QF_C128 ? 16 : 8; }
   size_t bytes() const { return elem() << n; }
 };
@@ -232,8 +268,7 @@ qf_status validate_masks(const qf_state* st, uint64_t x, uint64_t z) {
 // tables (Eq. 18 evaluated pair by pair).
 
 qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan** out) {
-  uint64_t key = fnv1a(terms, nt * sizeof(qf_term));
-  key = fnv1a(&st->n, sizeof(int), key);
+  const uint64_t key = content_key(terms, nt * sizeof(qf_term), 0x243F6A8885A308D3ull ^ (uint64_t)st->n);
   auto it = st->plans.find(key);
   if (it != st->plans.end()) {
     *out = &it->second;
@@ -698,6 +733,22 @@ void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
   };
   const cplx iu(0, 1);
   const int ncls = 1 << a->nzc;
+  // one sine and cosine per rotation (a block's runs are short; longer ones spill to the heap)
+  double cs_buf[32], sn_buf[32];
+  std::vector<double> cs_heap, sn_heap;
+  double* csv = cs_buf;
+  double* snv = sn_buf;
+  if (m > 32) {
+    cs_heap.resize(m);
+    sn_heap.resize(m);
+    csv = cs_heap.data();
+    snv = sn_heap.data();
+  }
+  for (int k = 0; k < m; ++k) {
+    const double th = inverse ? -r[k].th : r[k].th;
+    csv[k] = std::cos(th);
+    snv[k] = std::sin(th);
+  }
   for (int c = 0; c < ncls; ++c) {
     cplx M[qf::kSparseMaxRows][qf::kSparseMaxRows] = {};
     for (int i = 0; i < nr; ++i) M[i][i] = 1.0;
@@ -709,8 +760,7 @@ void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
       const uint64_t zin = compress(r[k].z & x);
       const int y = popc(x & r[k].z) & 3;
       const cplx iy = (y == 0) ? cplx(1, 0) : (y == 1) ? cplx(0, 1) : (y == 2) ? cplx(-1, 0) : cplx(0, -1);
-      const double th = inverse ? -r[k].th : r[k].th;
-      const double cs = std::cos(th), sn = std::sin(th);
+      const double cs = csv[k], sn = snv[k];
       cplx N2[qf::kSparseMaxRows][qf::kSparseMaxRows];
       for (int i = 0; i < nr; ++i) {
         const int col = loc[i] ^ xl;
@@ -735,15 +785,12 @@ uint32_t binom(int m, int k) {
   return (uint32_t)c;
 }
 
-// A two-row sparse block as a sector block for a state with (na, nb) occupied
-// even/odd qubits.  Requires a real composite, two active patterns with equal
-// even and odd occupation (so the block maps the sector onto itself) and, for
-// the reverse sweep, a purely imaginary generator.
-bool to_secblk(const qf::SparseArgs& a, int n, int na, int nb, bool need_q, qf::SecBlk* o) {
-  if (a.nr != 2 || n > 2 * qf::kSecMaxPos) return false;
-  const uint64_t p0 = a.pat[0], p1 = a.pat[1];
-  const int e0 = popc(p0 & kEvenMask), o0 = popc(p0 & ~kEvenMask);
-  if (e0 != popc(p1 & kEvenMask) || o0 != popc(p1 & ~kEvenMask)) return false;
+// The real composite-minus-identity m and, for an inverse block, the real Qi of
+// its generator Q = i Qi, per sign class, of a two-row block; false when the
+// block is not of that form.  The reverse sweep takes Qi = [[0, q01], [-q01, 0]]
+// (the generator only links the two active patterns).
+bool sector_mq(const qf::SparseArgs& a, bool need_q, double (*m)[2][2], double (*q)[2][2]) {
+  if (a.nr != 2) return false;
   const int ncls = 1 << a.nzc;
   for (int c = 0; c < ncls; ++c)
     for (int i = 0; i < 2; ++i)
@@ -751,14 +798,33 @@ bool to_secblk(const qf::SparseArgs& a, int n, int na, int nb, bool need_q, qf::
         if (a.M[c][i][j].y != 0.0) return false;
         if (need_q && a.Q[c][i][j].x != 0.0) return false;
       }
-  // the reverse sweep takes Qi = [[0, q01], [-q01, 0]] (the generator only links
-  // the two active patterns)
   if (need_q)
     for (int c = 0; c < ncls; ++c)
       if (a.Q[c][0][0].y != 0.0 || a.Q[c][1][1].y != 0.0 || a.Q[c][1][0].y != -a.Q[c][0][1].y) return false;
+  for (int c = 0; c < qf::kSparseMaxCls; ++c)
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        const int cc = c < ncls ? c : 0;
+        m[c][i][j] = a.M[cc][i][j].x;
+        q[c][i][j] = need_q ? a.Q[cc][i][j].y : 0.0;
+      }
+  return true;
+}
+
+// A two-row sparse block as a sector block for a state with (na, nb) occupied
+// even/odd qubits.  Requires a real composite, two active patterns with equal
+// even and odd occupation (so the block maps the sector onto itself) and, for
+// the reverse sweep, a purely imaginary generator.  A block that no member can
+// carry is accepted with zero items (it acts as the identity on the sector).
+bool to_secblk(const qf::SparseArgs& a, int n, int na, int nb, bool need_q, qf::SecBlk* o) {
+  if (a.nr != 2 || n > 2 * qf::kSecMaxPos) return false;
+  const uint64_t p0 = a.pat[0], p1 = a.pat[1];
+  const int e0 = popc(p0 & kEvenMask), o0 = popc(p0 & ~kEvenMask);
+  if (e0 != popc(p1 & kEvenMask) || o0 != popc(p1 & ~kEvenMask)) return false;
+  std::memset(o, 0, sizeof(*o));
+  if (!sector_mq(a, need_q, o->m, o->q)) return false;
   uint64_t U = 0;
   for (int i = 0; i < a.u; ++i) U |= 1ull << a.supp[i];
-  std::memset(o, 0, sizeof(*o));
   for (int q = 0; q < n; ++q) {
     if ((U >> q) & 1) continue;
     if ((q & 1) == 0)
@@ -766,9 +832,10 @@ bool to_secblk(const qf::SparseArgs& a, int n, int na, int nb, bool need_q, qf::
     else
       o->opos[o->no++] = (uint8_t)q;
   }
+  // a block whose patterns no member of the sector can carry (too few or too
+  // many electrons left for the outside positions) touches nothing: zero items
   o->ke = na - e0;
   o->ko = nb - o0;
-  if (o->ke < 0 || o->ke > o->ne || o->ko < 0 || o->ko > o->no) return false;
   o->cnt_e = binom(o->ne, o->ke);
   o->cnt_o = binom(o->no, o->ko);
   o->pat[0] = p0;
@@ -776,18 +843,6 @@ bool to_secblk(const qf::SparseArgs& a, int n, int na, int nb, bool need_q, qf::
   o->zc[0] = a.zc[0];
   o->zc[1] = a.zc[1];
   o->nzc = a.nzc;
-  for (int i = 0; i < 2; ++i)
-    for (int par = 0; par < 2; ++par) {
-      o->pl[i][par] = local_bits(o->pat[i], par);
-      o->zl[i][par] = local_bits(o->zc[i], par);
-    }
-  for (int c = 0; c < qf::kSparseMaxCls; ++c)
-    for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) {
-        const int cc = c < ncls ? c : 0;
-        o->m[c][i][j] = a.M[cc][i][j].x;
-        o->q[c][i][j] = need_q ? a.Q[cc][i][j].y : 0.0;
-      }
   return true;
 }
 
@@ -865,12 +920,6 @@ qf_status ensure_compact(qf_state* st, const qf::SecSpace& sp, int na, int nb, q
 // sec[nblk..2 nblk) (their inverses) of an n-qubit state in sector (na, nb):
 // consecutive blocks are grouped while the largest part of the union of their
 // supports stays within cap members (and a run holds at most kRunMaxBlocks).
-struct SectorRuns {
-  std::vector<qf::RunInfo> runs;
-  std::vector<qf::RunPart> parts;
-  std::vector<qf::RunBlk> blks;  // forward blocks, then inverse blocks
-  int pmax = 0;
-};
 
 // Largest part of a run touching ua of the ne alpha and ub of the no beta orbitals.
 uint64_t run_maxpart(int ua, int ub, int ne, int no, int na, int nb) {
@@ -1361,9 +1410,9 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   }
   // block structure: sparse composite blocks (same X, same parameter, commuting) or single rotations
   using Blk = qf_state::Blk;
-  uint64_t akey = fnv1a(ansatz, n_rot * sizeof(qf_arot));
-  akey = fnv1a(&st->n, sizeof(int), akey);
+  const uint64_t akey = content_key(ansatz, n_rot * sizeof(qf_arot), 0x13198A2E03707344ull ^ (uint64_t)st->n);
   auto ait = st->ansatz_plans.find(akey);
+  bool fresh = false;
   if (ait == st->ansatz_plans.end()) {
     // first sight of this ansatz: find the sparse blocks (the active rows of a block
     // do not depend on the angles, so the structure is kept and only M is refilled)
@@ -1419,16 +1468,15 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
         i = b.j;
       }
     }
-    ait = st->ansatz_plans.emplace(akey, std::move(bl)).first;
-  } else {
-    for (Blk& b : ait->second)
-      if (b.sparse) {
-        refill_sparse(&r[b.i], (int)(b.j - b.i), false, &b.fwd);
-        refill_sparse(&r[b.i], (int)(b.j - b.i), true, &b.inv);
-      }
+    qf_state::AnsatzPlan plan;
+    plan.blocks = std::move(bl);
+    ait = st->ansatz_plans.emplace(akey, std::move(plan)).first;
+    fresh = true;
   }
-  const std::vector<Blk>& blocks = ait->second;
-  qf_status os = ensure_out(st, blocks.size() + 2);
+  qf_state::AnsatzPlan& ap = ait->second;
+  std::vector<Blk>& blocks = ap.blocks;
+  const size_t nblk = blocks.size();
+  qf_status os = ensure_out(st, nblk + 2);
   if (os != QF_OK) return os;
   const ExpPlan* p = nullptr;
   if (n_terms) {
@@ -1436,77 +1484,110 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     if (ps != QF_OK) return ps;
   }
   const int n = st->n;
+  const int na = popc(det & kEvenMask), nbeta = popc(det & ~kEvenMask);
+  const bool lreal = !p || !p->has_odd;
+  // part-local runs: parts of at most kRunPartTarget members (and what shared memory holds)
+  const uint64_t cap = std::min<uint64_t>(
+      kRunPartTarget, std::min(qf::sector_run_capacity(st->dt, false, true), qf::sector_run_capacity(st->dt, true, lreal)));
+  const bool sec_cached =
+      ap.sec_ok && ap.sec_n == n && ap.sec_na == na && ap.sec_nb == nbeta && ap.sec_cap == cap;
+  // new angles: refill every block's composites (and, with a cached run plan, its
+  // sector form), spread over the host pool
+  std::atomic<bool> sec_good(true);
+  if (!fresh || sec_cached) {
+    qf::HostPool::get().parallel_for(nblk, 32, [&](size_t k) {
+      Blk& b = blocks[k];
+      if (!b.sparse) return;
+      if (!fresh) {
+        refill_sparse(&r[b.i], (int)(b.j - b.i), false, &b.fwd);
+        refill_sparse(&r[b.i], (int)(b.j - b.i), true, &b.inv);
+      }
+      if (sec_cached) {
+        qf::RunBlk& F = ap.runs.blks[k];
+        qf::RunBlk& I = ap.runs.blks[nblk + k];
+        if (!sector_mq(b.fwd, false, F.m, F.q) || !sector_mq(b.inv, true, I.m, I.q)) sec_good = false;
+      }
+    });
+  }
   // Sector path: every block is a two-row excitation that keeps the reference's
   // numbers of occupied even and odd qubits, so the whole evaluation runs on the
   // members of that sector, stored contiguously (compact layout) in a buffer of
   // the handle; psi itself is only reset to |det> at the end.
-  {
-    const int na = popc(det & kEvenMask), nbeta = popc(det & ~kEvenMask);
-    std::vector<qf::SecBlk> sec(2 * blocks.size());
-    bool ok = !blocks.empty() && n <= 2 * qf::kSecMaxPos;
-    for (size_t bi = 0; ok && bi < blocks.size(); ++bi)
-      ok = blocks[bi].sparse && to_secblk(blocks[bi].fwd, n, na, nbeta, false, &sec[bi]) &&
-           to_secblk(blocks[bi].inv, n, na, nbeta, true, &sec[blocks.size() + bi]);
-    if (ok) {
-      const size_t nblk = blocks.size();
-      st->scale = 1.0;
-      st->real = true;
-      st->sec_a = na;
-      st->sec_b = nbeta;
-      if (!p) {  // no Hamiltonian terms: E = 0 and a zero gradient
-        QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
-        QF_CUDA(cudaStreamSynchronize(st->stream));
-        *energy = 0.0;
-        for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
-        return QF_OK;
-      }
-      const bool lreal = !p->has_odd;
-      const qf::SecSpace sp = sector_space(n, na, nbeta);
-      qf::SecCompact cm{};
-      qf_status cs = ensure_compact(st, sp, na, nbeta, &cm);
-      if (cs != QF_OK) return cs;
-      // part-local runs: parts of at most kRunPartTarget members (and what shared memory holds)
-      const uint64_t cap = std::min<uint64_t>(
-          kRunPartTarget, std::min(qf::sector_run_capacity(st->dt, false, true), qf::sector_run_capacity(st->dt, true, lreal)));
-      SectorRuns rs;
-      if (!build_runs(sec.data(), nblk, n, na, nbeta, cap, &rs))
-        return fail(QF_EINVAL, "sector block support too large for a part-local sweep");
-      qf_status bs = ensure_sector_buffers(st, 1, nblk * (size_t)rs.pmax);
-      if (bs != QF_OK) return bs;
-      const size_t blk_bytes = rs.blks.size() * sizeof(qf::RunBlk);
-      bs = ensure_buf(&st->d_runblk, &st->runblk_cap, blk_bytes + rs.parts.size() * sizeof(qf::RunPart),
-                      "sector run descriptors");
-      if (bs != QF_OK) return bs;
-      const qf::RunBlk* d_blks = static_cast<const qf::RunBlk*>(st->d_runblk);
-      const qf::RunPart* d_parts =
-          reinterpret_cast<const qf::RunPart*>(static_cast<const char*>(st->d_runblk) + blk_bytes);
-      QF_CUDA(h2d(st->d_runblk, rs.blks.data(), blk_bytes, st->stream));
-      QF_CUDA(h2d(static_cast<char*>(st->d_runblk) + blk_bytes, rs.parts.data(),
-                  rs.parts.size() * sizeof(qf::RunPart), st->stream));
-      const uint64_t members = (uint64_t)sp.cnt_e * sp.cnt_o;
-      // a real lambda shares psi's slots (psi real parts, lambda imaginary parts)
-      void* cpsi = st->d_cstate;
-      void* clam = lreal ? cpsi : static_cast<char*>(cpsi) + members * st->elem();
-      const int nruns = (int)rs.runs.size();
-      QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
-      QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
-                                     (int)nblk, nullptr, rs.pmax, nullptr, cm, st->stream));
-      double* d_e = st->d_out + nblk;
-      QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
-                                     p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
-                                     st->stream));
-      QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
-                                     (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, st->stream));
+  bool sector = !blocks.empty() && n <= 2 * qf::kSecMaxPos;
+  if (sector && !sec_cached) {
+    // first evaluation of this ansatz in this sector: the run plan
+    std::vector<qf::SecBlk> sec(2 * nblk);
+    for (size_t bi = 0; sector && bi < nblk; ++bi)
+      sector = blocks[bi].sparse && to_secblk(blocks[bi].fwd, n, na, nbeta, false, &sec[bi]) &&
+               to_secblk(blocks[bi].inv, n, na, nbeta, true, &sec[nblk + bi]);
+    ap.sec_ok = sector && build_runs(sec.data(), nblk, n, na, nbeta, cap, &ap.runs);
+    ap.sec_n = n;
+    ap.sec_na = na;
+    ap.sec_nb = nbeta;
+    ap.sec_cap = cap;
+    st->parts_key = 0;
+    sector = ap.sec_ok;
+  } else if (sector) {
+    sector = sec_good.load();  // a block that lost the sector form this time: general path
+  }
+  if (sector) {
+    st->scale = 1.0;
+    st->real = true;
+    st->sec_a = na;
+    st->sec_b = nbeta;
+    if (!p) {  // no Hamiltonian terms: E = 0 and a zero gradient
       QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
-      QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2) * sizeof(double), st->stream));
       QF_CUDA(cudaStreamSynchronize(st->stream));
-      double nrm = st->h_out[nblk + 1];
-      if (!(nrm > 0.0)) nrm = 1.0;
-      *energy = st->h_out[nblk] / nrm;
+      *energy = 0.0;
       for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
-      for (size_t bi = 0; bi < nblk; ++bi) grad[par[blocks[bi].i]] += 2.0 * st->h_out[bi] / nrm;
       return QF_OK;
     }
+    const SectorRuns& rs = ap.runs;
+    const qf::SecSpace sp = sector_space(n, na, nbeta);
+    qf::SecCompact cm{};
+    qf_status cs = ensure_compact(st, sp, na, nbeta, &cm);
+    if (cs != QF_OK) return cs;
+    qf_status bs = ensure_sector_buffers(st, 1, nblk * (size_t)rs.pmax);
+    if (bs != QF_OK) return bs;
+    const size_t blk_bytes = rs.blks.size() * sizeof(qf::RunBlk);
+    const void* before = st->d_runblk;
+    bs = ensure_buf(&st->d_runblk, &st->runblk_cap, blk_bytes + rs.parts.size() * sizeof(qf::RunPart),
+                    "sector run descriptors");
+    if (bs != QF_OK) return bs;
+    const qf::RunBlk* d_blks = static_cast<const qf::RunBlk*>(st->d_runblk);
+    const qf::RunPart* d_parts =
+        reinterpret_cast<const qf::RunPart*>(static_cast<const char*>(st->d_runblk) + blk_bytes);
+    QF_CUDA(h2d(st->d_runblk, rs.blks.data(), blk_bytes, st->stream));
+    // the parts depend only on the plan and the sector: upload them when those change
+    const uint64_t pkey = content_key(nullptr, 0, akey ^ ((uint64_t)na << 40) ^ ((uint64_t)nbeta << 48) ^ cap) | 1ull;
+    if (st->parts_key != pkey || st->d_runblk != before) {
+      QF_CUDA(h2d(static_cast<char*>(st->d_runblk) + blk_bytes, rs.parts.data(),
+                  rs.parts.size() * sizeof(qf::RunPart), st->stream));
+      st->parts_key = pkey;
+    }
+    const uint64_t members = (uint64_t)sp.cnt_e * sp.cnt_o;
+    // a real lambda shares psi's slots (psi real parts, lambda imaginary parts)
+    void* cpsi = st->d_cstate;
+    void* clam = lreal ? cpsi : static_cast<char*>(cpsi) + members * st->elem();
+    const int nruns = (int)rs.runs.size();
+    QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
+    QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
+                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, st->stream));
+    double* d_e = st->d_out + nblk;
+    QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
+                                   p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
+                                   st->stream));
+    QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
+                                   (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, st->stream));
+    QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
+    QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2) * sizeof(double), st->stream));
+    QF_CUDA(cudaStreamSynchronize(st->stream));
+    double nrm = st->h_out[nblk + 1];
+    if (!(nrm > 0.0)) nrm = 1.0;
+    *energy = st->h_out[nblk] / nrm;
+    for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
+    for (size_t bi = 0; bi < nblk; ++bi) grad[par[blocks[bi].i]] += 2.0 * st->h_out[bi] / nrm;
+    return QF_OK;
   }
   qf_status ls = ensure_lam(st);
   if (ls != QF_OK) return ls;

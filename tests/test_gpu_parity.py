@@ -269,6 +269,33 @@ def test_energy_grad_ucc_16q_fd():
         assert abs(fd - grad[p]) < 1e-6 * max(1.0, abs(grad[p])), (p, fd, grad[p])
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_energy_grad_same_ansatz_across_sectors(dtype):
+    """One handle evaluates one dUCC ansatz from determinants in different
+    (alpha, beta) sectors and back: the cached part-local run plan of each
+    sector must be rebuilt or reused correctly (oracle: plain Pauli adjoint)."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    n = cfg["n_qubits"]
+    hf = (1 << cfg["n_el"]) - 1
+    # sectors (2, 2); (3, 2) and (1, 2), where the alpha-alpha doubles touch no
+    # member (identity blocks); (2, 2) from another determinant; (2, 2) again
+    dets = [hf, hf | 0b10000, hf ^ 0b11 ^ 0b1100000, hf ^ 0b1, hf]
+    st = qf.State(n, dtype)
+    arots = list(zip(A["x"], A["z"], A["coeff"], A["param"]))
+    for k, det in enumerate(dets):
+        tt = t * (1 + 0.3 * k)
+        e, grad = st.energy_grad(det, A, tt, T)
+        e_ref, g_ref, _ = pauli.adjoint_gradient(n, det, arots, tt, _terms_list(T))
+        if dtype == "c128":
+            assert abs(e - e_ref) < TOL_E_C128, k
+            assert np.abs(grad - g_ref).max() < 1e-10, k
+        else:
+            assert abs(e - e_ref) < TOL_E_C64, k
+            assert np.linalg.norm(grad - g_ref) <= TOL_G_C64 * max(1.0, np.linalg.norm(g_ref)), k
+        out = st.to_numpy()  # the sector path leaves exactly |det>
+        assert out[det] == 1.0 and np.count_nonzero(out) == 1, k
+
+
 def test_energy_grad_generic_ansatz_matches_oracle():
     """Non-commuting rotations sharing parameters: the unfused adjoint path."""
     n = 8
