@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <complex>
@@ -127,6 +128,8 @@ struct SectorRuns {
   std::vector<qf::RunPart> parts;
   std::vector<qf::RunBlk> blks;  // forward blocks, then inverse blocks (m, q refilled per call)
   int pmax = 0;
+  uint64_t logitems = 0;         // (member pair, block) items of one sweep: the forward log's length
+  bool log_ok = true;            // every inverse block lists its two patterns in the forward order
 };
 
 struct qf_state {
@@ -159,6 +162,9 @@ struct qf_state {
   size_t cstate_cap = 0;
   void* d_runblk = nullptr;  // part-local sweep descriptors (blocks, then parts)
   size_t runblk_cap = 0;
+  void* d_log = nullptr;     // forward log of the part-local sweeps (psi pairs after each block)
+  size_t log_cap = 0;
+  bool log_failed = false;   // the log did not fit: later calls un-rotate psi instead
   int hpsi_mode = QF_HPSI_DS;
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
@@ -193,6 +199,9 @@ constexpr int kPartials = 4096;
 // Target part size (members) of the part-local sector sweeps: ~40 KB of shared
 // memory per part, so several parts run on each SM.
 constexpr uint64_t kRunPartTarget = 4096;
+// Largest forward log of the part-local sweeps a handle allocates (24 qubits,
+// complex128: 2.1 GB).
+constexpr size_t kLogMaxBytes = (size_t)16 << 30;
 
 // Bits of mask on qubits of parity par (0 even / alpha, 1 odd / beta), as local
 // spin-orbital indices: qubit q -> bit q >> 1.
@@ -943,6 +952,10 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
   out->parts.clear();
   out->blks.assign(2 * nblk, qf::RunBlk{});
   out->pmax = 0;
+  out->logitems = 0;
+  out->log_ok = true;
+  for (size_t b = 0; b < nblk; ++b)
+    if (sec[b].pat[0] != sec[nblk + b].pat[0] || sec[b].pat[1] != sec[nblk + b].pat[1]) out->log_ok = false;
   size_t b0 = 0;
   while (b0 < nblk) {
     uint64_t U = supp[b0];
@@ -1046,6 +1059,23 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
         std::memcpy(B.m, S.m, sizeof(B.m));
         std::memcpy(B.q, S.q, sizeof(B.q));
       }
+    // forward-log layout: each part's items, block after block, parts in order.
+    // Blocks of equal shape (outside counts, pattern electrons) share their count.
+    std::map<std::array<int, 4>, uint64_t> shapes;
+    for (size_t b = b0; b < b1; ++b) {
+      const qf::RunBlk& B = out->blks[b];
+      ++shapes[{B.ne, B.no, B.e0, B.o0}];
+    }
+    for (int k = 0; k < R.nparts; ++k) {
+      qf::RunPart& P = out->parts[R.part0 + k];
+      uint64_t tot = 0;
+      for (const auto& sh : shapes) {
+        const auto& f = sh.first;
+        tot += sh.second * (uint64_t)binom(f[0], P.ka - f[2]) * binom(f[1], P.kb - f[3]);
+      }
+      P.logbase = out->logitems;
+      out->logitems += tot;
+    }
     out->runs.push_back(R);
     b0 = b1;
   }
@@ -1299,6 +1329,7 @@ qf_status qf_state_destroy(qf_state* st) {
   cudaFree(st->d_rank);
   cudaFree(st->d_cstate);
   cudaFree(st->d_runblk);
+  cudaFree(st->d_log);
   cudaFree(st->d_partials);
   cudaFree(st->d_counter);
   cudaFree(st->d_out);
@@ -1488,7 +1519,8 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   const bool lreal = !p || !p->has_odd;
   // part-local runs: parts of at most kRunPartTarget members (and what shared memory holds)
   const uint64_t cap = std::min<uint64_t>(
-      kRunPartTarget, std::min(qf::sector_run_capacity(st->dt, false, true), qf::sector_run_capacity(st->dt, true, lreal)));
+      kRunPartTarget, std::min(qf::sector_run_capacity(st->dt, false, true, false),
+                               qf::sector_run_capacity(st->dt, true, lreal, false)));
   const bool sec_cached =
       ap.sec_ok && ap.sec_n == n && ap.sec_na == na && ap.sec_nb == nbeta && ap.sec_cap == cap;
   // new angles: refill every block's composites (and, with a cached run plan, its
@@ -1569,16 +1601,27 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     // a real lambda shares psi's slots (psi real parts, lambda imaginary parts)
     void* cpsi = st->d_cstate;
     void* clam = lreal ? cpsi : static_cast<char*>(cpsi) + members * st->elem();
+    // forward log (real lambda only): psi after each block, so that the reverse need
+    // not un-rotate psi; up to kLogMaxBytes, else (or when it does not fit) the
+    // reverse un-rotates psi
+    void* log = nullptr;
+    const size_t log_bytes = (size_t)rs.logitems * st->elem();  // one (psi_i0, psi_i1) pair per item
+    if (lreal && rs.log_ok && !st->log_failed && log_bytes <= kLogMaxBytes) {
+      if (ensure_buf(&st->d_log, &st->log_cap, log_bytes, "sector log") == QF_OK)
+        log = st->d_log;
+      else
+        st->log_failed = true;
+    }
     const int nruns = (int)rs.runs.size();
     QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
     QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
-                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, st->stream));
+                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, st->stream));
     double* d_e = st->d_out + nblk;
     QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
                                    p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
                                    st->stream));
     QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
-                                   (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, st->stream));
+                                   (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, st->stream));
     QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
     QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2) * sizeof(double), st->stream));
     QF_CUDA(cudaStreamSynchronize(st->stream));

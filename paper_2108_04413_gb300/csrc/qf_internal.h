@@ -167,6 +167,7 @@ struct RunPart {                    // one occupation pattern of G
   uint32_t ga, gb;                  // occupied G orbitals (spin-local masks)
   int ka, kb;                       // electrons left for U's alpha / beta orbitals
   uint32_t cnta, cntb;              // C(ua, ka), C(ub, kb): size = cnta * cntb
+  uint64_t logbase;                 // first forward-log item of this part (its blocks' items follow in order)
 };
 struct RunInfo {
   int b0, b1;                       // blocks [b0, b1)
@@ -256,13 +257,16 @@ cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBl
 // blocks in order, psi real; reverse: from the last, psi real and lam real
 // packed in psi's imaginary slots when realst, else separate complex states).
 // Reverse: out[b] = Im <lam|Q_b|psi> of block b, via partial[b * pmax + part].
+// log (optional; realst only): the forward writes each item's rotated psi pair
+// there (RunPart::logbase) and the reverse reads psi back from it instead of
+// un-rotating psi; both sweeps of one evaluation must use the same log.
 // runs is a host array; parts and blks are device arrays.  Returns an error
 // when a part does not fit in shared memory.
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
-                               int pmax, double* out, const SecCompact& cm, cudaStream_t s);
-// Largest part (members) launch_sector_runs accepts for this dtype and direction.
-uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst);
+                               int pmax, double* out, const SecCompact& cm, void* log, cudaStream_t s);
+// Largest part (members) launch_sector_runs accepts for this dtype, direction and log use.
+uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged);
 // With cm.ra != NULL psi and lam are in the compact layout.  nblocks: the
 // most CTAs the reduction may use (partials holds 2 * nblocks doubles).
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,

@@ -248,21 +248,27 @@ constexpr int kRunBlkWords = sizeof(RunBlk) / 4;
 static_assert(sizeof(RunBlk) % 4 == 0 && kRunBlkWords <= kRunThreads, "run descriptor copy layout");
 
 // Shared-memory bytes per member: psi real parts (forward), (psi, lam) packed
-// real pairs (reverse, real), or psi and lam complex (reverse, complex); plus
-// the member's compact index.
+// real pairs (reverse, real), psi and lam complex (reverse, complex), or lam's
+// real parts (reverse, real, psi read from the forward log); plus the member's
+// compact index.
 template <int MODE, typename T>
 __host__ __device__ constexpr size_t run_member_bytes() {
-  return (MODE == 0 ? sizeof(T) : MODE == 1 ? 2 * sizeof(T) : 4 * sizeof(T)) + sizeof(uint32_t);
+  return (MODE == 0 || MODE == 3 ? sizeof(T) : MODE == 1 ? 2 * sizeof(T) : 4 * sizeof(T)) + sizeof(uint32_t);
 }
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// MODE 0: forward, psi real.  MODE 1: reverse, psi and lam real, packed as
-// (psi, lam) in one complex slot.  MODE 2: reverse, psi and lam complex.
+// MODE 0: forward, psi real; with a log, each item's rotated pair (psi_i0,
+// psi_i1) is also written to log[P.logbase + offset of the block + item].
+// MODE 1: reverse, psi and lam real, packed as (psi, lam) in one complex slot;
+// psi is un-rotated block by block.
+// MODE 2: reverse, psi and lam complex.
+// MODE 3: reverse, lam real (psi's imaginary slots); psi after each block is
+// read back from the forward log instead of being un-rotated.
 template <int MODE, typename T>
 __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
                                                              RunInfo run, const RunPart* __restrict__ parts,
                                                              const RunBlk* __restrict__ blks, double* partial,
-                                                             int pmax, SecCompact cm) {
+                                                             int pmax, SecCompact cm, typename SCx<T>::V* log) {
   using V = typename SCx<T>::V;
   constexpr bool ADJ = MODE != 0;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -270,6 +276,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   __shared__ RunBlk sb[2];
   __shared__ RunInfo R;
   __shared__ RunPart P;
+  __shared__ double ws[2][kRunWarps];  // per-warp overlaps of the current and the previous block
   const int tid = threadIdx.x;
   fill_binom(C);
   if (tid == 0) {
@@ -281,15 +288,16 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   if (tid < kRunBlkWords)
     reinterpret_cast<uint32_t*>(&sb[0])[tid] = __ldg(reinterpret_cast<const uint32_t*>(blks + blk_of(0)) + tid);
   __syncthreads();
-  // shared memory: amplitudes, then compact indices, then (reverse) overlap slots
+  // shared memory: amplitudes, then compact indices
   const uint32_t cap = R.maxsize;
-  T* ar = reinterpret_cast<T*>(dsm);   // MODE 0
+  T* ar = reinterpret_cast<T*>(dsm);   // MODE 0 (psi), MODE 3 (lam)
   V* av = reinterpret_cast<V*>(dsm);   // MODE 1, 2 (psi)
   V* lv = av + cap;                    // MODE 2 (lam)
   const size_t amp_bytes = align16((run_member_bytes<MODE, T>() - sizeof(uint32_t)) * cap);
   uint32_t* gi = reinterpret_cast<uint32_t*>(dsm + amp_bytes);
-  __shared__ double ws[2][kRunWarps];  // per-warp overlaps of the current and the previous block
   const uint32_t size = P.cnta * P.cntb;
+  // the real slot each member moves: psi's real part (MODE 0), lam's in psi's imaginary slot (MODE 3)
+  const int slot = MODE == 3 ? 1 : 0;
   const T* pr = reinterpret_cast<const T*>(psi);
   for (uint32_t m = tid; m < size; m += kRunThreads) {
     const uint32_t ia = m / P.cntb, ib = m - ia * P.cntb;
@@ -297,11 +305,27 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     const uint32_t sbm = unrank_m(ib, R.bpos, R.ub, P.kb, C) | P.gb;
     const uint32_t g = (uint32_t)compact_index(cm, sa, sbm);
     gi[m] = g;
-    if (MODE == 0) {
-      ar[m] = __ldcg(pr + 2 * (size_t)g);
+    if (MODE == 0 || MODE == 3) {
+      ar[m] = __ldcg(pr + 2 * (size_t)g + slot);
     } else {
       av[m] = __ldcg(psi + g);
       if (MODE == 2) lv[m] = __ldcg(lam + g);
+    }
+  }
+  // items of a block in this part (uniform over the CTA)
+  auto items_of = [&](const RunBlk& B) -> uint64_t {
+    const int ke = P.ka - B.e0, ko = P.kb - B.o0;
+    if (ke < 0 || ke > B.ne || ko < 0 || ko > B.no) return 0;
+    return (uint64_t)C[B.ne][ke] * C[B.no][ko];
+  };
+  // log offset of the current block within this part's log
+  uint64_t logoff = 0;
+  if (MODE == 3) {  // the reverse starts past the part's last block
+    for (int s = 0; s < nb; ++s) {
+      const RunBlk* Bg = blks + run.b0 + s;
+      const int ne = __ldg(&Bg->ne), no = __ldg(&Bg->no);
+      const int ke = P.ka - __ldg(&Bg->e0), ko = P.kb - __ldg(&Bg->o0);
+      if (ke >= 0 && ke <= ne && ko >= 0 && ko <= no) logoff += (uint64_t)C[ne][ke] * C[no][ko];
     }
   }
   __syncthreads();
@@ -312,12 +336,15 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     const RunBlk& B = sb[s & 1];
     double acc = 0.0;
     const int ke = P.ka - B.e0, ko = P.kb - B.o0;
-    if (ke >= 0 && ke <= B.ne && ko >= 0 && ko <= B.no) {
+    const uint64_t nitems = items_of(B);
+    if (MODE == 3) logoff -= nitems;
+    if (nitems) {
       const uint32_t co = C[B.no][ko];
-      const uint32_t items = C[B.ne][ke] * co;
+      const uint32_t items = (uint32_t)nitems;
       unsigned cg = 0;  // sign-class bits from the part's occupation of G
       if (B.nzc > 0) cg = par32s(B.zg[0][0] & P.ga) ^ par32s(B.zg[0][1] & P.gb);
       if (B.nzc > 1) cg |= (par32s(B.zg[1][0] & P.ga) ^ par32s(B.zg[1][1] & P.gb)) << 1;
+      V* lg = ((MODE == 0 || MODE == 3) && log) ? log + P.logbase + logoff : nullptr;
       for (uint32_t it = tid; it < items; it += kRunThreads) {
         const uint32_t ie = it / co, io = it - ie * co;
         const uint32_t la = unrank_m(ie, B.epos, B.ne, ke, C), lb = unrank_m(io, B.opos, B.no, ko, C);
@@ -330,8 +357,22 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
         const T a00 = (T)B.m[cls][0][0], a01 = (T)B.m[cls][0][1], a10 = (T)B.m[cls][1][0], a11 = (T)B.m[cls][1][1];
         if (MODE == 0) {
           const T v0 = ar[i0], v1 = ar[i1];
-          ar[i0] = fma(a00, v0, fma(a01, v1, v0));
-          ar[i1] = fma(a10, v0, fma(a11, v1, v1));
+          const T o0 = fma(a00, v0, fma(a01, v1, v0)), o1 = fma(a10, v0, fma(a11, v1, v1));
+          ar[i0] = o0;
+          ar[i1] = o1;
+          if (lg) {
+            V w;
+            w.x = o0;
+            w.y = o1;
+            __stcs(lg + it, w);  // streamed: read back once by the reverse sweep
+          }
+        } else if (MODE == 3) {
+          const V pp = __ldcs(lg + it);  // psi on the pair after this block (forward log)
+          const T w0 = ar[i0], w1 = ar[i1];
+          // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
+          acc = fma(B.q[cls][0][1], fma((double)w0, (double)pp.y, -(double)w1 * (double)pp.x), acc);
+          ar[i0] = fma(a00, w0, fma(a01, w1, w0));
+          ar[i1] = fma(a10, w0, fma(a11, w1, w1));
         } else if (MODE == 1) {
           const V p0 = av[i0], p1 = av[i1];  // (psi, lambda)
           // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
@@ -364,6 +405,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
         }
       }
     }
+    if (MODE == 0) logoff += nitems;
     if (ADJ) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -382,8 +424,8 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   T* pw = reinterpret_cast<T*>(psi);
   for (uint32_t m = tid; m < size; m += kRunThreads) {
     const uint32_t g = gi[m];
-    if (MODE == 0) {
-      __stcg(pw + 2 * (size_t)g, ar[m]);
+    if (MODE == 0 || MODE == 3) {
+      __stcg(pw + 2 * (size_t)g + slot, ar[m]);
     } else {
       __stcg(psi + g, av[m]);
       if (MODE == 2) __stcg(lam + g, lv[m]);
@@ -664,16 +706,19 @@ static uint32_t run_capacity_t() {
   return avail > fixed ? (uint32_t)((avail - fixed) / run_member_bytes<MODE, T>()) : 0u;
 }
 
-uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst) {
-  const int mode = !adj ? 0 : realst ? 1 : 2;
+uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged) {
+  const int mode = !adj ? 0 : !realst ? 2 : logged ? 3 : 1;
   if (dt == QF_C128)
-    return mode == 0 ? run_capacity_t<0, double>() : mode == 1 ? run_capacity_t<1, double>() : run_capacity_t<2, double>();
-  return mode == 0 ? run_capacity_t<0, float>() : mode == 1 ? run_capacity_t<1, float>() : run_capacity_t<2, float>();
+    return mode == 0 ? run_capacity_t<0, double>() : mode == 1 ? run_capacity_t<1, double>()
+         : mode == 2 ? run_capacity_t<2, double>() : run_capacity_t<3, double>();
+  return mode == 0 ? run_capacity_t<0, float>() : mode == 1 ? run_capacity_t<1, float>()
+       : mode == 2 ? run_capacity_t<2, float>() : run_capacity_t<3, float>();
 }
 
 template <int MODE, typename T>
 static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, const RunPart* parts,
-                          const RunBlk* blks, double* partial, int pmax, const SecCompact& cm, cudaStream_t s) {
+                          const RunBlk* blks, double* partial, int pmax, const SecCompact& cm, void* log,
+                          cudaStream_t s) {
   using V = typename SCx<T>::V;
   static bool attr = false;
   if (!attr) {
@@ -687,7 +732,7 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
     if (smem > run_smem_max() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
     k_sector_run<MODE, T><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
-                                                              blks, partial, pmax, cm);
+                                                              blks, partial, pmax, cm, static_cast<V*>(log));
     count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -697,20 +742,22 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
 
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
-                               int pmax, double* out, const SecCompact& cm, cudaStream_t s) {
+                               int pmax, double* out, const SecCompact& cm, void* log, cudaStream_t s) {
   if (nblk <= 0 || nruns <= 0) return cudaSuccess;
-  if (!cm.ra) return cudaErrorInvalidValue;
+  if (!cm.ra || (log && !realst)) return cudaErrorInvalidValue;
   const int prof_slot_ = prof_pre(adj ? QF_K_ADJ_SPARSE : QF_K_SPARSE, s);
-  const int mode = !adj ? 0 : realst ? 1 : 2;
+  const int mode = !adj ? 0 : !realst ? 2 : log ? 3 : 1;
   cudaError_t e;
   if (dt == QF_C128)
-    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s)
-      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s)
-                  : runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s);
+    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
+      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
+      : mode == 2 ? runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
+                  : runs_t<3, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s);
   else
-    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s)
-      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s)
-                  : runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, s);
+    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
+      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
+      : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
+                  : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s);
   if (e == cudaSuccess && adj) {
     k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
