@@ -63,8 +63,6 @@ struct ExpPlan {
   qf::WChunk* d_wchunks = nullptr;
   qf::WChunkF* d_wchunks_f = nullptr;
   qf::WChunkS* d_wchunks_s = nullptr;  // real D as (hi, lo) floats for double-single H|psi>
-  qf::SecGroup* d_secgroups = nullptr;  // groups that can connect two members of a sector
-  int nsecgroups = 0;
   qf::SecGroup* d_seclarge = nullptr;   // those flipping more than four qubits
   int nseclarge = 0;
   int* d_rk = nullptr;                  // group index tables by flipped spin orbitals (see SecRank)
@@ -85,7 +83,6 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_wchunks);
   cudaFree(p.d_wchunks_f);
   cudaFree(p.d_wchunks_s);
-  cudaFree(p.d_secgroups);
   cudaFree(p.d_seclarge);
   cudaFree(p.d_rk);
   for (int v = 0; v < qf::kClassTbN; ++v) cudaFree(p.d_classes[v]);
@@ -415,7 +412,6 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     if ((xe & 1) || (xo & 1)) continue;
     sg.push_back(qf::SecGroup{g.x, xe, xo, g.chunk0, g.nchunk, local_bits(g.x, 0), local_bits(g.x, 1)});
   }
-  p.nsecgroups = (int)sg.size();
   // lookup tables by flipped spin orbitals (local index i of qubit 2i or 2i+1)
   const int nq = st->n, ne = (nq + 1) / 2, no = nq / 2;
   const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
@@ -429,20 +425,27 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   for (size_t gi = 0; gi < sg.size(); ++gi) {
     const uint64_t x = sg[gi].x;
     const int w = popc(x);
+    // table entries hold the group's chunk0 | nchunk << 24; a group that does not
+    // fit that code is tested one by one with the large groups
+    if (sg[gi].chunk0 >= (1 << 24) || sg[gi].nchunk > 127) {
+      lg.push_back(sg[gi]);
+      continue;
+    }
+    const int code = sg[gi].chunk0 | (sg[gi].nchunk << 24);
     std::vector<int> ev, od;
     for (int q = 0; q < nq; ++q)
       if ((x >> q) & 1) ((q & 1) ? od : ev).push_back(q >> 1);
     if (w == 0) {
-      diag = (int)gi;
+      diag = code;
       continue;
     }
     // each flip set is recorded under every occupied/empty split that a member can present
     if (w == 2 && ev.size() == 2) {
-      rkt[o_sa + ev[0] * ne + ev[1]] = (int)gi;
-      rkt[o_sa + ev[1] * ne + ev[0]] = (int)gi;
+      rkt[o_sa + ev[0] * ne + ev[1]] = code;
+      rkt[o_sa + ev[1] * ne + ev[0]] = code;
     } else if (w == 2 && od.size() == 2) {
-      rkt[o_sb + od[0] * no + od[1]] = (int)gi;
-      rkt[o_sb + od[1] * no + od[0]] = (int)gi;
+      rkt[o_sb + od[0] * no + od[1]] = code;
+      rkt[o_sb + od[1] * no + od[0]] = code;
     } else if (w == 4 && (ev.size() == 4 || od.size() == 4)) {
       const std::vector<int>& v = ev.size() == 4 ? ev : od;
       const size_t off = ev.size() == 4 ? o_aa : o_bb;
@@ -450,13 +453,13 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
       const int pairs[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
       for (const auto& q : pairs) {
         const int r1 = pr(v[q[0]], v[q[1]]), r2 = pr(v[q[2]], v[q[3]]);
-        rkt[off + (size_t)r1 * P + r2] = (int)gi;
-        rkt[off + (size_t)r2 * P + r1] = (int)gi;
+        rkt[off + (size_t)r1 * P + r2] = code;
+        rkt[off + (size_t)r2 * P + r1] = code;
       }
     } else if (w == 4 && ev.size() == 2) {
       for (int s0 = 0; s0 < 2; ++s0)
         for (int s1 = 0; s1 < 2; ++s1)
-          rkt[o_ab + (((size_t)ev[s0] * ne + ev[1 - s0]) * no + od[s1]) * no + od[1 - s1]] = (int)gi;
+          rkt[o_ab + (((size_t)ev[s0] * ne + ev[1 - s0]) * no + od[s1]) * no + od[1 - s1]] = code;
     } else {
       lg.push_back(sg[gi]);
     }
@@ -481,14 +484,12 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
       return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
     }
     if (!hfix.empty()) QF_CUDA(h2d(p.d_hfix, hfix.data(), hfix.size() * sizeof(long long), st->stream));
-    if (cudaMalloc(&p.d_secgroups, std::max<size_t>(1, sg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
-        cudaMalloc(&p.d_seclarge, std::max<size_t>(1, lg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
+    if (cudaMalloc(&p.d_seclarge, std::max<size_t>(1, lg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
         cudaMalloc(&p.d_rk, rkt.size() * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       free_plan(p);
       return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
     }
-    if (!sg.empty()) QF_CUDA(h2d(p.d_secgroups, sg.data(), sg.size() * sizeof(qf::SecGroup), st->stream));
     if (!lg.empty()) QF_CUDA(h2d(p.d_seclarge, lg.data(), lg.size() * sizeof(qf::SecGroup), st->stream));
     QF_CUDA(h2d(p.d_rk, rkt.data(), rkt.size() * sizeof(int), st->stream));
     p.rk = qf::SecRank{p.d_rk + o_sa, p.d_rk + o_sb, p.d_rk + o_aa, p.d_rk + o_bb, p.d_rk + o_ab, diag, ne, no,
@@ -1394,7 +1395,7 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
   if (st->sec_a >= 0 && st->n <= 2 * qf::kSecMaxPos) {
     // every nonzero amplitude is in one (alpha, beta) sector: sum over its members only
     const qf::SecSpace sp = sector_space(st->n, st->sec_a, st->sec_b);
-    QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, p->rk, p->d_secgroups,
+    QF_CUDA(qf::launch_sector_hpsi(st->psi, nullptr, st->dt, st->real && !p->has_odd, sp, p->rk,
                                    p->d_seclarge, p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter,
                                    st->d_out, kPartials / 2, qf::SecCompact{}, st->stream));
   } else {
@@ -1617,7 +1618,7 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
                                    (int)nblk, nullptr, rs.pmax, nullptr, cm, log, st->stream));
     double* d_e = st->d_out + nblk;
-    QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_secgroups, p->d_seclarge,
+    QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_seclarge,
                                    p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
                                    st->stream));
     QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,

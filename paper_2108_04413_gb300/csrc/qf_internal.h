@@ -189,7 +189,9 @@ struct SecCompact {
 };
 // Groups of at most four flipped qubits, looked up by the spin orbitals they
 // flip, in local indices of each parity (alpha = even qubit 2i -> i, beta = odd
-// qubit 2i+1 -> i); -1 where no group exists.
+// qubit 2i+1 -> i).  An entry is the group's first chunk | its chunk count << 24,
+// or -1 where no group exists (groups whose chunks do not fit that code are
+// listed with the large groups instead).
 //   sa[i * ne + a], sb[j * no + b]                      singles
 //   aa[pr(i, j) * C(ne, 2) + pr(a, b)], bb likewise     same-spin doubles, i < j, a < b
 //   ab[((i * ne + a) * no + j) * no + b]                opposite-spin doubles
@@ -200,7 +202,7 @@ struct SecRank {
   const int* aa;
   const int* bb;
   const int* ab;
-  int diag;                     // the x = 0 group, or -1
+  int diag;                     // the x = 0 group's code, or -1
   int ne, no;
   // Real-part H|psi> weights in fixed point: itab[16 c + pat] = round(tab.x * 2^e)
   // of chunk c, inv_fix = 2^-e.  Groups of several chunks sum them exactly in
@@ -270,7 +272,7 @@ uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged);
 // With cm.ra != NULL psi and lam are in the compact layout.  nblocks: the
 // most CTAs the reduction may use (partials holds 2 * nblocks doubles).
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
-                               const SecRank& rk, const SecGroup* all, const SecGroup* large, int nlarge,
+                               const SecRank& rk, const SecGroup* large, int nlarge,
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
                                int nblocks, const SecCompact& cm, cudaStream_t s);
 

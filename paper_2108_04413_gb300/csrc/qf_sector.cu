@@ -508,7 +508,6 @@ __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict
 template <typename T, bool REALST, bool NARROW, bool LAMY, bool COMPACT>
 __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* __restrict__ psi,
                                                      typename SCx<T>::V* __restrict__ lam, SecSpace sp, SecRank rk,
-                                                     const SecGroup* __restrict__ all,
                                                      const SecGroup* __restrict__ large, int nlarge,
                                                      const ExpChunk* __restrict__ chunks, double* partials,
                                                      unsigned* counter, double* out, SecCompact cm) {
@@ -547,46 +546,64 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
       }
     }
     double lx = 0.0, ly = 0.0, lxs = 0.0;
-    auto term = [&](const SecGroup& G) {
-      const uint64_t b = c ^ G.x;
-      const uint64_t a = COMPACT ? compact_index(cm, la ^ G.xa, lb ^ G.xb) : b;
-      sector_term<T, REALST, NARROW>(psi, chunks, rk.itab, G.chunk0, G.nchunk, b, a, lx, ly, lxs);
+    // one connected group: flip x (qubits), xa / xb (local alpha / beta orbitals)
+    auto term = [&](int chunk0, int nchunk, uint64_t x, uint32_t xa, uint32_t xb) {
+      const uint64_t b = c ^ x;
+      const uint64_t a = COMPACT ? compact_index(cm, la ^ xa, lb ^ xb) : b;
+      sector_term<T, REALST, NARROW>(psi, chunks, rk.itab, chunk0, nchunk, b, a, lx, ly, lxs);
     };
-    auto visit = [&](int g) {
-      if (g >= 0) term(all[g]);
+    // a lookup-table entry: the group's chunk0 | nchunk << 24, or -1 (no group)
+    auto visit = [&](int code, uint64_t x, uint32_t xa, uint32_t xb) {
+      if (code >= 0) term(code & 0xFFFFFF, code >> 24, x, xa, xb);
     };
-    if (rk.diag >= 0) visit(rk.diag);
+    // alpha orbital q is qubit 2q, beta orbital q is qubit 2q + 1
+    auto qa = [](int q) { return 1ull << (2 * q); };
+    auto qb = [](int q) { return 1ull << (2 * q + 1); };
+    visit(rk.diag, 0ull, 0u, 0u);
     const int ne = rk.ne, no = rk.no;
     const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
     for (int x1 = 0; x1 < noa; ++x1)
-      for (int y1 = 0; y1 < nva; ++y1) visit(__ldg(rk.sa + oa[x1] * ne + va[y1]));
+      for (int y1 = 0; y1 < nva; ++y1)
+        visit(__ldg(rk.sa + oa[x1] * ne + va[y1]), qa(oa[x1]) | qa(va[y1]), (1u << oa[x1]) | (1u << va[y1]), 0u);
     for (int x1 = 0; x1 < nob; ++x1)
-      for (int y1 = 0; y1 < nvb; ++y1) visit(__ldg(rk.sb + ob[x1] * no + vb[y1]));
+      for (int y1 = 0; y1 < nvb; ++y1)
+        visit(__ldg(rk.sb + ob[x1] * no + vb[y1]), qb(ob[x1]) | qb(vb[y1]), 0u, (1u << ob[x1]) | (1u << vb[y1]));
     for (int x2 = 1; x2 < noa; ++x2)
       for (int x1 = 0; x1 < x2; ++x1) {
         const int rij = oa[x1] + oa[x2] * (oa[x2] - 1) / 2;
+        const uint64_t xo = qa(oa[x1]) | qa(oa[x2]);
+        const uint32_t lo = (1u << oa[x1]) | (1u << oa[x2]);
         for (int y2 = 1; y2 < nva; ++y2)
-          for (int y1 = 0; y1 < y2; ++y1) visit(__ldg(rk.aa + rij * pe + va[y1] + va[y2] * (va[y2] - 1) / 2));
+          for (int y1 = 0; y1 < y2; ++y1)
+            visit(__ldg(rk.aa + rij * pe + va[y1] + va[y2] * (va[y2] - 1) / 2), xo | qa(va[y1]) | qa(va[y2]),
+                  lo | (1u << va[y1]) | (1u << va[y2]), 0u);
       }
     for (int x2 = 1; x2 < nob; ++x2)
       for (int x1 = 0; x1 < x2; ++x1) {
         const int rij = ob[x1] + ob[x2] * (ob[x2] - 1) / 2;
+        const uint64_t xo = qb(ob[x1]) | qb(ob[x2]);
+        const uint32_t lo = (1u << ob[x1]) | (1u << ob[x2]);
         for (int y2 = 1; y2 < nvb; ++y2)
-          for (int y1 = 0; y1 < y2; ++y1) visit(__ldg(rk.bb + rij * po + vb[y1] + vb[y2] * (vb[y2] - 1) / 2));
+          for (int y1 = 0; y1 < y2; ++y1)
+            visit(__ldg(rk.bb + rij * po + vb[y1] + vb[y2] * (vb[y2] - 1) / 2), xo | qb(vb[y1]) | qb(vb[y2]), 0u,
+                  lo | (1u << vb[y1]) | (1u << vb[y2]));
       }
     for (int x1 = 0; x1 < noa; ++x1)
       for (int y1 = 0; y1 < nva; ++y1) {
         const int ia = (oa[x1] * ne + va[y1]) * no;
+        const uint64_t xa_q = qa(oa[x1]) | qa(va[y1]);
+        const uint32_t xa_l = (1u << oa[x1]) | (1u << va[y1]);
         for (int x2 = 0; x2 < nob; ++x2) {
           const int iab = (ia + ob[x2]) * no;
-          for (int y2 = 0; y2 < nvb; ++y2) visit(__ldg(rk.ab + iab + vb[y2]));
+          for (int y2 = 0; y2 < nvb; ++y2)
+            visit(__ldg(rk.ab + iab + vb[y2]), xa_q | qb(ob[x2]) | qb(vb[y2]), xa_l, (1u << ob[x2]) | (1u << vb[y2]));
         }
       }
     // groups flipping more than four qubits: test each
     for (int gi = 0; gi < nlarge; ++gi) {
       const SecGroup G = large[gi];
       if (2 * __popcll(c & G.x & EVEN) != G.xe || 2 * __popcll(c & G.x & ODD) != G.xo) continue;
-      term(G);
+      term(G.chunk0, G.nchunk, G.x, G.xa, G.xb);
     }
     const uint64_t self = COMPACT ? it : c;
     if (REALST) lx = fma(lxs, rk.inv_fix, lx);
@@ -785,7 +802,7 @@ static unsigned hpsi_grid(K kernel, uint64_t items, int max_blocks) {
 
 template <typename T, bool REALST, bool LAMY, bool COMPACT>
 static void hpsi_t(const void* psi, void* lam, bool narrow, int max_blocks, const SecSpace& sp, const SecRank& rk,
-                   const SecGroup* all, const SecGroup* large, int nlarge, const ExpChunk* chunks, double* partials,
+                   const SecGroup* large, int nlarge, const ExpChunk* chunks, double* partials,
                    unsigned* counter, double* out, const SecCompact& cm, cudaStream_t s) {
   using V = typename SCx<T>::V;
   const V* p = static_cast<const V*>(psi);
@@ -793,44 +810,44 @@ static void hpsi_t(const void* psi, void* lam, bool narrow, int max_blocks, cons
   const uint64_t items = (uint64_t)sp.cnt_e * sp.cnt_o;
   if (narrow) {
     const auto k = k_sector_hpsi<T, REALST, true, LAMY, COMPACT>;
-    k<<<hpsi_grid(k, items, max_blocks), 256, 0, s>>>(p, l, sp, rk, all, large, nlarge, chunks, partials, counter,
+    k<<<hpsi_grid(k, items, max_blocks), 256, 0, s>>>(p, l, sp, rk, large, nlarge, chunks, partials, counter,
                                                       out, cm);
   } else {
     const auto k = k_sector_hpsi<T, REALST, false, LAMY, COMPACT>;
-    k<<<hpsi_grid(k, items, max_blocks), 256, 0, s>>>(p, l, sp, rk, all, large, nlarge, chunks, partials, counter,
+    k<<<hpsi_grid(k, items, max_blocks), 256, 0, s>>>(p, l, sp, rk, large, nlarge, chunks, partials, counter,
                                                       out, cm);
   }
 }
 
 template <typename T>
 static cudaError_t hpsi_dispatch(const void* psi, void* lam, bool realst, bool narrow, int g,
-                                 const SecSpace& sp, const SecRank& rk, const SecGroup* all,
+                                 const SecSpace& sp, const SecRank& rk,
                                  const SecGroup* large, int nlarge, const ExpChunk* chunks, double* partials,
                                  unsigned* counter, double* out, const SecCompact& cm, cudaStream_t s) {
   const bool lamy = realst && lam == psi;  // packed: lambda into psi's imaginary slots
   if (!cm.ra) {  // full layout (expectation values): no packed lambda
     if (lamy) return cudaErrorInvalidValue;
     if (realst)
-      hpsi_t<T, true, false, false>(psi, lam, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter, out,
+      hpsi_t<T, true, false, false>(psi, lam, narrow, g, sp, rk, large, nlarge, chunks, partials, counter, out,
                                     cm, s);
     else
-      hpsi_t<T, false, false, false>(psi, lam, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter,
+      hpsi_t<T, false, false, false>(psi, lam, narrow, g, sp, rk, large, nlarge, chunks, partials, counter,
                                      out, cm, s);
     return cudaGetLastError();
   }
   // compact layout (energy and gradient): a real lambda is always packed
   if (realst != lamy) return cudaErrorInvalidValue;
   if (lamy)
-    hpsi_t<T, true, true, true>(psi, lam, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter, out, cm,
+    hpsi_t<T, true, true, true>(psi, lam, narrow, g, sp, rk, large, nlarge, chunks, partials, counter, out, cm,
                                 s);
   else
-    hpsi_t<T, false, false, true>(psi, lam, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter, out,
+    hpsi_t<T, false, false, true>(psi, lam, narrow, g, sp, rk, large, nlarge, chunks, partials, counter, out,
                                   cm, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
-                               const SecRank& rk, const SecGroup* all, const SecGroup* large, int nlarge,
+                               const SecRank& rk, const SecGroup* large, int nlarge,
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
                                int nblocks, const SecCompact& cm, cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_HPSI, s);
@@ -838,9 +855,9 @@ cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool rea
   const bool narrow = sp.ne + sp.no <= 32;
   const cudaError_t e =
       (dt == QF_C128)
-          ? hpsi_dispatch<double>(psi, lam, realst, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter,
+          ? hpsi_dispatch<double>(psi, lam, realst, narrow, g, sp, rk, large, nlarge, chunks, partials, counter,
                                   out, cm, s)
-          : hpsi_dispatch<float>(psi, lam, realst, narrow, g, sp, rk, all, large, nlarge, chunks, partials, counter,
+          : hpsi_dispatch<float>(psi, lam, realst, narrow, g, sp, rk, large, nlarge, chunks, partials, counter,
                                  out, cm, s);
   prof_post(prof_slot_, s);
   count_launch();
