@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "qf_internal.h"
 
@@ -700,12 +701,12 @@ cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBl
 }
 
 static size_t run_smem_max() {
-  static int v = -1;
-  if (v < 0) {
-    int dev = 0;
+  static const int v = [] {  // thread-safe one-time initialisation
+    int dev = 0, bytes = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  }
+    cudaDeviceGetAttribute(&bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return bytes;
+  }();
   // the kernel's static shared memory (binomials, two descriptors, run, part) and a margin
   return (size_t)std::max(0, v - 4096);
 }
@@ -737,13 +738,13 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
                           const RunBlk* blks, double* partial, int pmax, const SecCompact& cm, void* log,
                           cudaStream_t s) {
   using V = typename SCx<T>::V;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_sector_run<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)run_smem_max());
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::once_flag once;  // allow the opt-in shared memory size, once per process
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_sector_run<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)run_smem_max());
+  });
+  if (attr != cudaSuccess) return attr;
   for (int r = 0; r < nruns; ++r) {
     const RunInfo& R = runs[MODE != 0 ? nruns - 1 - r : r];
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
@@ -788,14 +789,13 @@ cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool
 // over members), at most max_blocks (the reduction's partial slots).
 template <typename K>
 static unsigned hpsi_grid(K kernel, uint64_t items, int max_blocks) {
-  static int resident = -1;  // one per kernel instantiation
-  if (resident < 0) {
+  static const int resident = [&] {  // one per kernel instantiation, initialised once
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
-    resident = std::max(1, sms) * std::max(1, per_sm);
-  }
+    return std::max(1, sms) * std::max(1, per_sm);
+  }();
   const uint64_t want = (items + 255) / 256;
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::min(resident, max_blocks)));
 }
