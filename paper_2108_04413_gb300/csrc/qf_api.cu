@@ -126,6 +126,7 @@ struct SectorRuns {
   std::vector<qf::RunBlk> blks;  // forward blocks, then inverse blocks (m, q refilled per call)
   int pmax = 0;
   uint64_t logitems = 0;         // (member pair, block) items of one sweep: the forward log's length
+  std::vector<uint16_t> strs;    // the blocks' outside strings (RunBlk::lsa / lsb); empty when not tabulated
   bool log_ok = true;            // every inverse block lists its two patterns in the forward order
 };
 
@@ -196,6 +197,8 @@ constexpr int kPartials = 4096;
 // Target part size (members) of the part-local sector sweeps: ~40 KB of shared
 // memory per part, so several parts run on each SM.
 constexpr uint64_t kRunPartTarget = 4096;
+// Largest outside-string table of a run plan (uint16 entries: 64 MB).
+constexpr uint64_t kStringsMax = (uint64_t)1 << 25;
 // Largest forward log of the part-local sweeps a handle allocates (24 qubits,
 // complex128: 2.1 GB).
 constexpr size_t kLogMaxBytes = (size_t)16 << 30;
@@ -954,6 +957,7 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
   out->blks.assign(2 * nblk, qf::RunBlk{});
   out->pmax = 0;
   out->logitems = 0;
+  out->strs.clear();
   out->log_ok = true;
   for (size_t b = 0; b < nblk; ++b)
     if (sec[b].pat[0] != sec[nblk + b].pat[0] || sec[b].pat[1] != sec[nblk + b].pat[1]) out->log_ok = false;
@@ -963,12 +967,14 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
     size_t b1 = b0 + 1;
     while (b1 < nblk && b1 - b0 < (size_t)qf::kRunMaxBlocks) {
       const uint64_t U2 = U | supp[b1];
-      if (run_maxpart(popc(U2 & kEvenMask), popc(U2 & ~kEvenMask), ne, no, na, nb) > cap) break;
+      const int ua2 = popc(U2 & kEvenMask), ub2 = popc(U2 & ~kEvenMask);
+      if (ua2 > qf::kRunMaxOrb || ub2 > qf::kRunMaxOrb || run_maxpart(ua2, ub2, ne, no, na, nb) > cap) break;
       U = U2;
       ++b1;
     }
     const int ua = popc(U & kEvenMask), ub = popc(U & ~kEvenMask);
-    if (run_maxpart(ua, ub, ne, no, na, nb) > cap) return false;  // one block's own part too large
+    if (ua > qf::kRunMaxOrb || ub > qf::kRunMaxOrb || run_maxpart(ua, ub, ne, no, na, nb) > cap)
+      return false;  // one block's own part too large
     qf::RunInfo R{};
     R.b0 = (int)b0;
     R.b1 = (int)b1;
@@ -1079,6 +1085,41 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
     }
     out->runs.push_back(R);
     b0 = b1;
+  }
+  // outside strings of every block: all subsets of its outside positions, by size,
+  // each size in colex order (= increasing mask), as run-local masks; shared by a
+  // block and its inverse.  Left out when the table would pass kStringsMax entries.
+  uint64_t total = 0;
+  for (size_t b = 0; b < nblk; ++b) total += (1ull << out->blks[b].ne) + (1ull << out->blks[b].no);
+  const bool tab = total <= kStringsMax;
+  if (tab) out->strs.reserve(total);
+  for (size_t b = 0; b < nblk; ++b) {
+    qf::RunBlk& F = out->blks[b];
+    qf::RunBlk& I = out->blks[nblk + b];
+    if (!tab) {
+      F.lsa = F.lsb = I.lsa = I.lsb = qf::kNoStrings;
+      continue;
+    }
+    for (int spin = 0; spin < 2; ++spin) {
+      const int m = spin ? F.no : F.ne;
+      const uint8_t* pos = spin ? F.opos : F.epos;
+      const uint32_t base = (uint32_t)out->strs.size();
+      out->strs.resize(base + (1u << m));
+      uint32_t next[qf::kSecMaxPos + 1];  // next slot of each size
+      uint32_t acc = base;
+      for (int k = 0; k <= m; ++k) {
+        next[k] = acc;
+        acc += binom(m, k);
+      }
+      for (uint32_t mask = 0; mask < (1u << m); ++mask) {
+        uint32_t dep = 0;
+        for (int j = 0; j < m; ++j)
+          if ((mask >> j) & 1u) dep |= 1u << pos[j];
+        out->strs[next[popc(mask)]++] = (uint16_t)dep;
+      }
+      (spin ? F.lsb : F.lsa) = base;
+      (spin ? I.lsb : I.lsa) = base;
+    }
   }
   return true;
 }
@@ -1583,8 +1624,9 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     qf_status bs = ensure_sector_buffers(st, 1, nblk * (size_t)rs.pmax);
     if (bs != QF_OK) return bs;
     const size_t blk_bytes = rs.blks.size() * sizeof(qf::RunBlk);
+    const size_t part_bytes = rs.parts.size() * sizeof(qf::RunPart);
     const void* before = st->d_runblk;
-    bs = ensure_buf(&st->d_runblk, &st->runblk_cap, blk_bytes + rs.parts.size() * sizeof(qf::RunPart),
+    bs = ensure_buf(&st->d_runblk, &st->runblk_cap, blk_bytes + part_bytes + rs.strs.size() * sizeof(uint16_t),
                     "sector run descriptors");
     if (bs != QF_OK) return bs;
     const qf::RunBlk* d_blks = static_cast<const qf::RunBlk*>(st->d_runblk);
@@ -1594,8 +1636,10 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     // the parts depend only on the plan and the sector: upload them when those change
     const uint64_t pkey = content_key(nullptr, 0, akey ^ ((uint64_t)na << 40) ^ ((uint64_t)nbeta << 48) ^ cap) | 1ull;
     if (st->parts_key != pkey || st->d_runblk != before) {
-      QF_CUDA(h2d(static_cast<char*>(st->d_runblk) + blk_bytes, rs.parts.data(),
-                  rs.parts.size() * sizeof(qf::RunPart), st->stream));
+      QF_CUDA(h2d(static_cast<char*>(st->d_runblk) + blk_bytes, rs.parts.data(), part_bytes, st->stream));
+      if (!rs.strs.empty())
+        QF_CUDA(h2d(static_cast<char*>(st->d_runblk) + blk_bytes + part_bytes, rs.strs.data(),
+                    rs.strs.size() * sizeof(uint16_t), st->stream));
       st->parts_key = pkey;
     }
     const uint64_t members = (uint64_t)sp.cnt_e * sp.cnt_o;
@@ -1614,15 +1658,20 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
         st->log_failed = true;
     }
     const int nruns = (int)rs.runs.size();
+    const uint16_t* d_strs =
+        rs.strs.empty() ? nullptr
+                        : reinterpret_cast<const uint16_t*>(static_cast<const char*>(st->d_runblk) + blk_bytes +
+                                                            part_bytes);
     QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
     QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
-                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, st->stream));
+                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, d_strs, st->stream));
     double* d_e = st->d_out + nblk;
     QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_seclarge,
                                    p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
                                    st->stream));
     QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
-                                   (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, st->stream));
+                                   (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, d_strs,
+                                   st->stream));
     QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
     QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2) * sizeof(double), st->stream));
     QF_CUDA(cudaStreamSynchronize(st->stream));

@@ -160,9 +160,16 @@ struct RunBlk {                     // one excitation block inside its run
   uint32_t pu[2][2];                // pattern i on U (run-local), [i][0] alpha, [i][1] beta
   uint32_t zu[2][2];                // class mask j on U (run-local)
   uint32_t zg[2][2];                // class mask j on G (spin-local: orbital index)
+  // Offsets into the run strings table (launch_sector_runs' strs) of this block's
+  // outside alpha / beta strings: every subset of epos (opos), as run-local masks,
+  // grouped by size k (group k starts after the C(ne, k') subsets of each k' < k),
+  // each group in colex order; kNoStrings when there is no table.
+  uint32_t lsa, lsb;
   double m[kSparseMaxCls][2][2];    // composite minus identity (real), per sign class
   double q[kSparseMaxCls][2][2];    // Qi with generator Q = i Qi (reverse)
 };
+constexpr uint32_t kNoStrings = 0xFFFFFFFFu;
+constexpr int kRunMaxOrb = 16;      // U orbitals per spin (run-local strings fit 16 bits)
 struct RunPart {                    // one occupation pattern of G
   uint32_t ga, gb;                  // occupied G orbitals (spin-local masks)
   int ka, kb;                       // electrons left for U's alpha / beta orbitals
@@ -262,11 +269,13 @@ cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBl
 // log (optional; realst only): the forward writes each item's rotated psi pair
 // there (RunPart::logbase) and the reverse reads psi back from it instead of
 // un-rotating psi; both sweeps of one evaluation must use the same log.
+// strs: the blocks' outside strings (RunBlk::lsa / lsb), or NULL to unrank them.
 // runs is a host array; parts and blks are device arrays.  Returns an error
 // when a part does not fit in shared memory.
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
-                               int pmax, double* out, const SecCompact& cm, void* log, cudaStream_t s);
+                               int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
+                               cudaStream_t s);
 // Largest part (members) launch_sector_runs accepts for this dtype, direction and log use.
 uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged);
 // With cm.ra != NULL psi and lam are in the compact layout.  nblocks: the

@@ -269,7 +269,8 @@ template <int MODE, typename T>
 __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
                                                              RunInfo run, const RunPart* __restrict__ parts,
                                                              const RunBlk* __restrict__ blks, double* partial,
-                                                             int pmax, SecCompact cm, typename SCx<T>::V* log) {
+                                                             int pmax, SecCompact cm, typename SCx<T>::V* log,
+                                                             const uint16_t* __restrict__ strs) {
   using V = typename SCx<T>::V;
   constexpr bool ADJ = MODE != 0;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -346,9 +347,23 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       if (B.nzc > 0) cg = par32s(B.zg[0][0] & P.ga) ^ par32s(B.zg[0][1] & P.gb);
       if (B.nzc > 1) cg |= (par32s(B.zg[1][0] & P.ga) ^ par32s(B.zg[1][1] & P.gb)) << 1;
       V* lg = ((MODE == 0 || MODE == 3) && log) ? log + P.logbase + logoff : nullptr;
+      // the block's outside strings of sizes ke and ko, when tabulated
+      const bool tab = strs && B.lsa != kNoStrings;
+      uint32_t sa0 = 0, sb0 = 0;
+      if (tab) {
+        sa0 = B.lsa;
+        for (int k = 0; k < ke; ++k) sa0 += C[B.ne][k];
+        sb0 = B.lsb;
+        for (int k = 0; k < ko; ++k) sb0 += C[B.no][k];
+      }
+      const float inv_co = 1.0f / (float)co;  // items < 2^24: the estimate is off by at most one
       for (uint32_t it = tid; it < items; it += kRunThreads) {
-        const uint32_t ie = it / co, io = it - ie * co;
-        const uint32_t la = unrank_m(ie, B.epos, B.ne, ke, C), lb = unrank_m(io, B.opos, B.no, ko, C);
+        uint32_t ie = (uint32_t)((float)it * inv_co);
+        if (ie * co > it) --ie;
+        else if ((ie + 1) * co <= it) ++ie;
+        const uint32_t io = it - ie * co;
+        const uint32_t la = tab ? (uint32_t)__ldg(strs + sa0 + ie) : unrank_m(ie, B.epos, B.ne, ke, C);
+        const uint32_t lb = tab ? (uint32_t)__ldg(strs + sb0 + io) : unrank_m(io, B.opos, B.no, ko, C);
         unsigned cls = cg;
         if (B.nzc > 0) cls ^= par32s(B.zu[0][0] & la) ^ par32s(B.zu[0][1] & lb);
         if (B.nzc > 1) cls ^= (par32s(B.zu[1][0] & la) ^ par32s(B.zu[1][1] & lb)) << 1;
@@ -736,7 +751,7 @@ uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged) {
 template <int MODE, typename T>
 static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, const RunPart* parts,
                           const RunBlk* blks, double* partial, int pmax, const SecCompact& cm, void* log,
-                          cudaStream_t s) {
+                          const uint16_t* strs, cudaStream_t s) {
   using V = typename SCx<T>::V;
   static std::once_flag once;  // allow the opt-in shared memory size, once per process
   static cudaError_t attr = cudaSuccess;
@@ -750,7 +765,7 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
     if (smem > run_smem_max() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
     k_sector_run<MODE, T><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
-                                                              blks, partial, pmax, cm, static_cast<V*>(log));
+                                                              blks, partial, pmax, cm, static_cast<V*>(log), strs);
     count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -760,22 +775,23 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
 
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
-                               int pmax, double* out, const SecCompact& cm, void* log, cudaStream_t s) {
+                               int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
+                               cudaStream_t s) {
   if (nblk <= 0 || nruns <= 0) return cudaSuccess;
   if (!cm.ra || (log && !realst)) return cudaErrorInvalidValue;
   const int prof_slot_ = prof_pre(adj ? QF_K_ADJ_SPARSE : QF_K_SPARSE, s);
   const int mode = !adj ? 0 : !realst ? 2 : log ? 3 : 1;
   cudaError_t e;
   if (dt == QF_C128)
-    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
-      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
-      : mode == 2 ? runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
-                  : runs_t<3, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s);
+    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
+      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
+      : mode == 2 ? runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
+                  : runs_t<3, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s);
   else
-    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
-      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
-      : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s)
-                  : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, s);
+    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
+      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
+      : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
+                  : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s);
   if (e == cudaSuccess && adj) {
     k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
