@@ -56,6 +56,7 @@ struct ExpPlan {
   qf::ExpChunk* d_echunks = nullptr;  // pair-form expectation weights
   qf::ExpChunk* d_hchunks = nullptr;  // H|psi> weights
   long long* d_hfix = nullptr;        // their real parts in fixed point (SecRank::itab)
+  qf::RealChunk* d_hreal = nullptr;   // their masks and real parts packed (n <= 32; SecRank::rch)
   int ngroups = 0;
   int nchunks = 0;
   // tiled H|psi>: groups in X order, 8-term tables, classes for 2^10 and 2^11 tiles
@@ -79,6 +80,7 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_echunks);
   cudaFree(p.d_hchunks);
   cudaFree(p.d_hfix);
+  cudaFree(p.d_hreal);
   cudaFree(p.d_hgroups);
   cudaFree(p.d_wchunks);
   cudaFree(p.d_wchunks_f);
@@ -487,6 +489,20 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
       return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
     }
     if (!hfix.empty()) QF_CUDA(h2d(p.d_hfix, hfix.data(), hfix.size() * sizeof(long long), st->stream));
+    if (st->n <= 32 && !hch.empty()) {
+      std::vector<qf::RealChunk> rc(hch.size());
+      for (size_t c = 0; c < hch.size(); ++c) {
+        for (int t = 0; t < qf::kChunkTerms; ++t) rc[c].z[t] = (uint32_t)hch[c].z[t];
+        for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat) rc[c].t[pat] = hch[c].tab[pat].x;
+      }
+      if (cudaMalloc(&p.d_hreal, rc.size() * sizeof(qf::RealChunk)) != cudaSuccess) {
+        cudaGetLastError();
+        p.d_hreal = nullptr;
+        free_plan(p);
+        return fail(QF_ENOMEM, "cudaMalloc(plan) failed");
+      }
+      QF_CUDA(h2d(p.d_hreal, rc.data(), rc.size() * sizeof(qf::RealChunk), st->stream));
+    }
     if (cudaMalloc(&p.d_seclarge, std::max<size_t>(1, lg.size()) * sizeof(qf::SecGroup)) != cudaSuccess ||
         cudaMalloc(&p.d_rk, rkt.size() * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
@@ -496,7 +512,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     if (!lg.empty()) QF_CUDA(h2d(p.d_seclarge, lg.data(), lg.size() * sizeof(qf::SecGroup), st->stream));
     QF_CUDA(h2d(p.d_rk, rkt.data(), rkt.size() * sizeof(int), st->stream));
     p.rk = qf::SecRank{p.d_rk + o_sa, p.d_rk + o_sb, p.d_rk + o_aa, p.d_rk + o_bb, p.d_rk + o_ab, diag, ne, no,
-                       p.d_hfix, inv_fix};
+                       p.d_hfix, inv_fix, p.d_hreal};
     QF_CUDA(cudaStreamSynchronize(st->stream));
   }
   p.terms.assign(terms, terms + nt);

@@ -81,6 +81,12 @@ struct ExpChunk {
   double2 tab[1 << kChunkTerms];  // (real-part weight, imaginary-part weight) per sign pattern
   float2 ftab[1 << kChunkTerms];  // the same weights in FP32 (complex64 states)
 };
+// A chunk's masks and real-part weights packed for n <= 32: the masks and the
+// first 14 weights share one 128-byte line (one chunk per 256 bytes).
+struct __align__(256) RealChunk {
+  uint32_t z[kChunkTerms];
+  double t[1 << kChunkTerms];
+};
 
 // H|psi> plan (tiled): groups sorted by X mask form classes of equal high part
 // x >> tb (tb = tile bits); a class reads one partner tile per output tile.
@@ -216,6 +222,7 @@ struct SecRank {
   // integer arithmetic.
   const long long* itab;
   double inv_fix;
+  const RealChunk* rch;         // the chunks as RealChunk (n <= 32), else NULL
 };
 
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.

@@ -478,12 +478,33 @@ __device__ __forceinline__ unsigned chunk_index(const ExpChunk* W, uint64_t b) {
   return idx;
 }
 
+// Sign pattern of b (n <= 32) against a packed chunk's masks.
+__device__ __forceinline__ unsigned real_index(const RealChunk* __restrict__ R, uint32_t b) {
+  const uint4 z = __ldg(reinterpret_cast<const uint4*>(R->z));
+  return ((unsigned)__popc(z.x & b) & 1u) | (((unsigned)__popc(z.y & b) & 1u) << 1) |
+         (((unsigned)__popc(z.z & b) & 1u) << 2) | (((unsigned)__popc(z.w & b) & 1u) << 3);
+}
+
 template <typename T, bool REALST, bool NARROW>
 __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict__ psi,
                                             const ExpChunk* __restrict__ chunks,
-                                            const long long* __restrict__ itab, int chunk0, int nchunk, uint64_t b,
-                                            uint64_t a, double& lx, double& ly, double& lxs) {
+                                            const long long* __restrict__ itab, const RealChunk* __restrict__ rch,
+                                            int chunk0, int nchunk, uint64_t b, uint64_t a, double& lx, double& ly,
+                                            double& lxs) {
   using V = typename SCx<T>::V;
+  if (REALST && NARROW && rch) {  // packed real tables
+    const double v = (double)reinterpret_cast<const T*>(psi)[2 * a];
+    if (nchunk == 1) {
+      const RealChunk* R = rch + chunk0;
+      lx = fma(__ldg(&R->t[real_index(R, (uint32_t)b)]), v, lx);
+    } else {
+      long long is = 0;
+      for (int k = 0; k < nchunk; ++k)
+        is += __ldg(itab + ((size_t)(chunk0 + k) << kChunkTerms) + real_index(rch + chunk0 + k, (uint32_t)b));
+      lxs = fma(__ll2double_rn(is), v, lxs);
+    }
+    return;
+  }
   if (REALST && nchunk > 1) {
     long long is = 0;
     for (int k = 0; k < nchunk; ++k) {
@@ -566,7 +587,7 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
     auto term = [&](int chunk0, int nchunk, uint64_t x, uint32_t xa, uint32_t xb) {
       const uint64_t b = c ^ x;
       const uint64_t a = COMPACT ? compact_index(cm, la ^ xa, lb ^ xb) : b;
-      sector_term<T, REALST, NARROW>(psi, chunks, rk.itab, chunk0, nchunk, b, a, lx, ly, lxs);
+      sector_term<T, REALST, NARROW>(psi, chunks, rk.itab, rk.rch, chunk0, nchunk, b, a, lx, ly, lxs);
     };
     // a lookup-table entry: the group's chunk0 | nchunk << 24, or -1 (no group)
     auto visit = [&](int code, uint64_t x, uint32_t xa, uint32_t xb) {
