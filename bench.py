@@ -352,14 +352,16 @@ def run_gpu(args, rank, world, local, pg):
             ce = sum(1 for q in sup if q % 2 == 0)
             items += comb(ne - ce, na - ea) * comb(no - (len(sup) - ce), nb_ - eb)
         rev = dom == "adj_sparse"
-        fl = items * (2 * (4 + 4 + 2) if rev else 2 * 4)
+        # reverse: psi after each block comes back from the forward log, so its work
+        # is lambda's rotation and the overlap
+        fl = items * (2 * (4 + 2) if rev else 2 * 4)
         avg_s = per_kind[dom]["ms"] / per_kind[dom]["launches"] / 1e3
         roof = {"kernel": "k_sector_run (" + ("reverse" if rev else "forward") + ")", "bound": "alu",
                 "achieved": fl / avg_s / 1e12, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                 "frac": fl / avg_s / 1e12 / pk["fp64_tflops"], "traffic": None,
                 "algorithmic": (f"{fl:.4g} FP64 flop per sweep: {items} (member pair, excitation) items x "
-                                + ("(4 + 4 multiply-adds rotating psi and lambda + 2 for the overlap)"
-                                   if rev else "4 multiply-adds rotating psi") + " x 2 flop"),
+                                + ("(4 multiply-adds rotating lambda + 2 for the overlap; psi read from the "
+                                   "forward log)" if rev else "4 multiply-adds rotating psi") + " x 2 flop"),
                 "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock (derived)",
                 "note": "one launch per run of excitations; the compact sector state stays in L2"}
     if dom == "hpsi":
@@ -394,7 +396,9 @@ def run_gpu(args, rank, world, local, pg):
             "qubits": n, "state": args.dtype, "excitations": len(w["exs"]), "rotations": int(len(w["ansatz"])),
             "pauli_terms": int(len(w["terms"])), "xmask_groups": len(stats),
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": f"state {N * S >> 20} MiB > 129 MB L2 (no flush needed)",
+            "l2": (f"no explicit flush: every step rewrites the {N * S >> 20} MiB state (reset to |det>) and "
+                   "streams the 2 GB sweep log, more than the 129 MB L2; the 13.7 MB compact sector state "
+                   "is L2-resident within a step"),
         },
         "energy": float(energies[-1]),
         "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps} for k, v in per_kind.items()},

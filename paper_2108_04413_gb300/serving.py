@@ -2,7 +2,8 @@
 
 Requests (system, parameters) arrive over time.  A dispatcher admits them as
 worker slots free up and as device memory allows: every system keeps its state
-resident (psi and lambda = H psi, 2 * 2^n amplitudes, plus its cached plans) so
+resident (psi, lambda or the sector path's compact copy and forward log, plus its
+cached plans; see footprint_bytes) so
 repeated-parameter requests skip all planning, and admission charges a system's
 footprint against an HBM budget, evicting idle resident systems (least
 recently used first) when a new one does not fit.  Admitted requests run on
@@ -47,9 +48,37 @@ class Request:
     error: Optional[str] = None
 
 
-def footprint_bytes(n: int, dtype: str) -> int:
-    """Device bytes a resident system holds: psi and lambda (plan tables are small)."""
-    return 2 * ((16 if dtype == "c128" else 8) << n)
+def _popc(v: int) -> int:
+    return bin(v).count("1")
+
+
+def footprint_bytes(n: int, dtype: str, det: Optional[int] = None, ansatz: Optional[np.ndarray] = None) -> int:
+    """Device bytes a resident system holds: psi and lambda (2 * 2^n amplitudes).
+    Given the determinant and the ansatz, also the sector path's compact copy
+    (2 * members amplitudes) and forward log (one amplitude pair per (member
+    pair, excitation) item, at most 16 GB): an excitation whose flips cover sa
+    alpha and sb beta spin orbitals, half of each occupied, moves
+    C(ne - sa, na - sa/2) * C(no - sb, nb - sb/2) items.  Plan tables are small."""
+    from math import comb
+
+    size = 16 if dtype == "c128" else 8
+    total = 2 * (size << n)
+    if det is None or ansatz is None or len(ansatz) == 0:
+        return total
+    ne, no = (n + 1) // 2, n // 2
+    even = sum(1 << q for q in range(0, n, 2))
+    na, nb = _popc(det & even), _popc(det & ~even)
+    members = comb(ne, na) * comb(no, nb)
+    flips = {}
+    for x, p in zip(ansatz["x"].tolist(), ansatz["param"].tolist()):
+        flips.setdefault(int(p), int(x))
+    items = 0
+    for x in flips.values():
+        sa, sb = _popc(x & even), _popc(x & ~even)
+        ka, kb = na - sa // 2, nb - sb // 2
+        if 0 <= ka <= ne - sa and 0 <= kb <= no - sb:
+            items += comb(ne - sa, ka) * comb(no - sb, kb)
+    return total + 2 * members * size + min(items * size, 16 << 30)
 
 
 class GpuExecutor:
@@ -97,6 +126,7 @@ class Server:
         self.done: List[Request] = []
         self.evictions = 0
         self.max_concurrent = 0
+        self._fp: Dict[str, int] = {}
         self._threads = [threading.Thread(target=self._worker, daemon=True) for _ in range(workers)]
         self.t0 = self.clock()
         for th in self._threads:
@@ -104,6 +134,14 @@ class Server:
 
     def now(self) -> float:
         return self.clock() - self.t0
+
+    def _footprint(self, key: str) -> int:
+        """Device bytes charged for a resident system (cached per system)."""
+        fp = self._fp.get(key)
+        if fp is None:
+            sysm = self.systems[key]
+            fp = self._fp[key] = footprint_bytes(sysm.n, self.dtype, sysm.det, sysm.ansatz)
+        return fp
 
     # -- submission
     def submit(self, req: Request):
@@ -132,7 +170,7 @@ class Server:
                 del self._pending[i]
                 self._resident.move_to_end(key)
                 return req, self._resident[key], False
-            need = footprint_bytes(self.systems[key].n, self.dtype)
+            need = self._footprint(key)
             if need > self.budget:
                 del self._pending[i]
                 req.error = "system does not fit the HBM budget"
@@ -146,12 +184,12 @@ class Server:
                     break
                 if not self._busy.get(k):
                     victims.append(k)
-                    free += footprint_bytes(self.systems[k].n, self.dtype)
+                    free += self._footprint(k)
             if free < need:
                 continue  # wait for a busy system to finish
             for k in victims:
                 h = self._resident.pop(k)
-                self._used -= footprint_bytes(self.systems[k].n, self.dtype)
+                self._used -= self._footprint(k)
                 self.evictions += 1
                 self.ex.release(h)
             del self._pending[i]
@@ -189,7 +227,7 @@ class Server:
                     self._resident[key] = handle
                     self._resident.move_to_end(key)
                 elif fresh:
-                    self._used -= footprint_bytes(sysm.n, self.dtype)
+                    self._used -= self._footprint(sysm.key)
                 self._busy[key] = False
                 self._active -= 1
                 self.done.append(req)

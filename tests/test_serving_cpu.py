@@ -101,3 +101,29 @@ def test_oversized_system_fails_alone():
     big = [r for r in done if r.rid == 99][0]
     assert big.error is not None
     assert sum(r.error is None for r in done) == 10
+
+
+def test_footprint_counts_sector_log_items_by_brute_force():
+    """The sector part of footprint_bytes: 2 * members amplitudes for the compact
+    copy plus one amplitude pair per (member pair, excitation) for the forward
+    log.  A pair is a sector member carrying the excitation's annihilated
+    orbitals on its support; count those directly."""
+    from paper_2108_04413_gb300 import prep
+
+    n_orb, n_el = 4, 4
+    n = 2 * n_orb
+    A, exs = prep.uccsd_ansatz(n_orb, n_el)
+    det = (1 << n_el) - 1
+    even = sum(1 << q for q in range(0, n, 2))
+    na, nb = bin(det & even).count("1"), bin(det & ~even).count("1")
+    members = [c for c in range(1 << n) if bin(c & even).count("1") == na and bin(c & ~even).count("1") == nb]
+    items = 0
+    for occ, vir in exs:
+        p0 = sum(1 << q for q in occ)
+        sup = p0 | sum(1 << q for q in vir)
+        items += sum(1 for c in members if c & sup == p0)
+    for dtype, size in (("c128", 16), ("c64", 8)):
+        base = footprint_bytes(n, dtype)
+        assert base == 2 * (size << n)
+        got = footprint_bytes(n, dtype, det, A) - base
+        assert got == 2 * len(members) * size + items * size
