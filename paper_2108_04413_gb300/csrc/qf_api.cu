@@ -493,7 +493,10 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
       std::vector<qf::RealChunk> rc(hch.size());
       for (size_t c = 0; c < hch.size(); ++c) {
         for (int t = 0; t < qf::kChunkTerms; ++t) rc[c].z[t] = (uint32_t)hch[c].z[t];
-        for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat) rc[c].t[pat] = hch[c].tab[pat].x;
+        for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat) {
+          rc[c].t[pat] = hch[c].tab[pat].x;
+          rc[c].tf[pat] = (float)hch[c].tab[pat].x;
+        }
       }
       if (cudaMalloc(&p.d_hreal, rc.size() * sizeof(qf::RealChunk)) != cudaSuccess) {
         cudaGetLastError();

@@ -86,6 +86,7 @@ struct ExpChunk {
 struct __align__(256) RealChunk {
   uint32_t z[kChunkTerms];
   double t[1 << kChunkTerms];
+  float tf[1 << kChunkTerms];  // the same weights in FP32 (complex64 states)
 };
 
 // H|psi> plan (tiled): groups sorted by X mask form classes of equal high part

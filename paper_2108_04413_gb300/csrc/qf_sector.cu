@@ -385,8 +385,11 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
         } else if (MODE == 3) {
           const V pp = __ldcs(lg + it);  // psi on the pair after this block (forward log)
           const T w0 = ar[i0], w1 = ar[i1];
-          // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
-          acc = fma(B.q[cls][0][1], fma((double)w0, (double)pp.y, -(double)w1 * (double)pp.x), acc);
+          // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host); a
+          // complex64 state forms the pair's product in FP32
+          const double t01 = (sizeof(T) == 4) ? (double)fmaf((float)w0, (float)pp.y, -(float)w1 * (float)pp.x)
+                                              : fma((double)w0, (double)pp.y, -(double)w1 * (double)pp.x);
+          acc = fma(B.q[cls][0][1], t01, acc);
           ar[i0] = fma(a00, w0, fma(a01, w1, w0));
           ar[i1] = fma(a10, w0, fma(a11, w1, w1));
         } else if (MODE == 1) {
@@ -485,19 +488,40 @@ __device__ __forceinline__ unsigned real_index(const RealChunk* __restrict__ R, 
          (((unsigned)__popc(z.z & b) & 1u) << 2) | (((unsigned)__popc(z.w & b) & 1u) << 3);
 }
 
+// FP32 partial sums of a complex64 state's H|psi>, folded into the FP64 sum
+// every kFoldTerms terms.
+constexpr int kFoldTerms = 32;
+struct F32Acc {
+  float s = 0.0f;
+  int k = 0;
+  __device__ __forceinline__ void add(float w, float v, double& lx) {
+    s = fmaf(w, v, s);
+    if (++k == kFoldTerms) {
+      lx += (double)s;
+      s = 0.0f;
+      k = 0;
+    }
+  }
+};
+
 template <typename T, bool REALST, bool NARROW>
 __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict__ psi,
                                             const ExpChunk* __restrict__ chunks,
                                             const long long* __restrict__ itab, const RealChunk* __restrict__ rch,
                                             int chunk0, int nchunk, uint64_t b, uint64_t a, double& lx, double& ly,
-                                            double& lxs) {
+                                            double& lxs, F32Acc& fac) {
   using V = typename SCx<T>::V;
   if (REALST && NARROW && rch) {  // packed real tables
-    const double v = (double)reinterpret_cast<const T*>(psi)[2 * a];
+    const T vt = reinterpret_cast<const T*>(psi)[2 * a];
     if (nchunk == 1) {
       const RealChunk* R = rch + chunk0;
-      lx = fma(__ldg(&R->t[real_index(R, (uint32_t)b)]), v, lx);
+      const unsigned idx = real_index(R, (uint32_t)b);
+      if (sizeof(T) == 4)  // complex64: FP32 products, folded into the FP64 sum
+        fac.add(__ldg(&R->tf[idx]), (float)vt, lx);
+      else
+        lx = fma(__ldg(&R->t[idx]), (double)vt, lx);
     } else {
+      const double v = (double)vt;
       long long is = 0;
       for (int k = 0; k < nchunk; ++k)
         is += __ldg(itab + ((size_t)(chunk0 + k) << kChunkTerms) + real_index(rch + chunk0 + k, (uint32_t)b));
@@ -583,11 +607,12 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
       }
     }
     double lx = 0.0, ly = 0.0, lxs = 0.0;
+    F32Acc fac;
     // one connected group: flip x (qubits), xa / xb (local alpha / beta orbitals)
     auto term = [&](int chunk0, int nchunk, uint64_t x, uint32_t xa, uint32_t xb) {
       const uint64_t b = c ^ x;
       const uint64_t a = COMPACT ? compact_index(cm, la ^ xa, lb ^ xb) : b;
-      sector_term<T, REALST, NARROW>(psi, chunks, rk.itab, rk.rch, chunk0, nchunk, b, a, lx, ly, lxs);
+      sector_term<T, REALST, NARROW>(psi, chunks, rk.itab, rk.rch, chunk0, nchunk, b, a, lx, ly, lxs, fac);
     };
     // a lookup-table entry: the group's chunk0 | nchunk << 24, or -1 (no group)
     auto visit = [&](int code, uint64_t x, uint32_t xa, uint32_t xb) {
@@ -643,6 +668,7 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
       term(G.chunk0, G.nchunk, G.x, G.xa, G.xb);
     }
     const uint64_t self = COMPACT ? it : c;
+    lx += (double)fac.s;
     if (REALST) lx = fma(lxs, rk.inv_fix, lx);
     if (REALST) {  // real parts only: with LAMY the imaginary slots are lambda's
       const double ux = (double)reinterpret_cast<const T*>(psi)[2 * self];
