@@ -268,6 +268,54 @@ def ucc_gradient_adjoint(n_orb, n_el, h, g, t, exs=None):
     return e, grad
 
 
+def excited_state(n: int, n_el: int, ex) -> np.ndarray:
+    """|Phi_mu> = tau_mu |Phi_HF> (with its fermionic sign)."""
+    phi = np.zeros(1 << n, dtype=complex)
+    phi[hf_det(n_el)] = 1.0
+    return apply_string(phi, n, tau_string(ex))
+
+
+def pqe_residuals(n_orb, n_el, h, g, t, exs=None):
+    """r_mu(t) = <Phi_mu| U^dagger(t) H U(t) |Phi_0> (Eq. 23) for every excitation:
+    sigma = H U Phi_0 (direct fermionic action), U^dagger applied factor by factor
+    in reverse order, then projected on tau_mu Phi_0.  Returns (E, r)."""
+    n = 2 * n_orb
+    if exs is None:
+        exs = excitations(n_orb, n_el)
+    psi = ucc_state(n_orb, n_el, t, exs)
+    sig = hamiltonian_apply(psi, n_orb, h, g)
+    e = np.vdot(psi, sig).real
+    for mu in range(len(exs) - 1, -1, -1):
+        sig = ucc_factor_apply(sig, n, exs[mu], -float(t[mu]))
+    r = np.array([np.vdot(excited_state(n, n_el, ex), sig) for ex in exs])
+    return e, r
+
+
+def pqe_residuals_from_energies(n_orb, n_el, h, g, t, exs=None):
+    """The same residuals from three energies each (Eq. 24): with
+    Omega_mu = exp(pi/4 kappa_mu) Phi_0 (Eq. 25),
+        r_mu = <Omega_mu|Ubar|Omega_mu> - <Phi_0|Ubar|Phi_0>/2 - <Phi_mu|Ubar|Phi_mu>/2,
+    Ubar = U^dagger H U; valid for real H and real amplitudes."""
+    n = 2 * n_orb
+    if exs is None:
+        exs = excitations(n_orb, n_el)
+
+    def ubar_energy(start):
+        psi = start
+        for ex, tm in zip(exs, t):
+            psi = ucc_factor_apply(psi, n, ex, float(tm))
+        return np.vdot(psi, hamiltonian_apply(psi, n_orb, h, g)).real
+
+    phi0 = np.zeros(1 << n, dtype=complex)
+    phi0[hf_det(n_el)] = 1.0
+    e0 = ubar_energy(phi0)
+    out = []
+    for ex in exs:
+        omega = ucc_factor_apply(phi0, n, ex, np.pi / 4)
+        out.append(ubar_energy(omega) - 0.5 * e0 - 0.5 * ubar_energy(excited_state(n, n_el, ex)))
+    return np.array(out)
+
+
 # ----------------------------------------------------------------------------
 # Jordan-Wigner by Pauli-letter multiplication
 

@@ -144,6 +144,26 @@ def adjoint_gradient(n: int, det: int, arots, t, terms):
     return e, g, g_theta
 
 
+def residuals(n: int, det: int, arots, t, terms, dets):
+    """<b|U(t)^dagger H U(t)|Phi> for each basis index b in dets, with E(t).
+
+    These are the projective residuals of Eq. 23 (Sec. PQE) on basis
+    determinants; the residual of an excited determinant tau_mu|Phi> carries its
+    fermionic sign on top.  Plainly: psi = U Phi, sigma = H psi, then U^dagger
+    applied as the inverse rotations in reverse order, and sigma read at b.
+    Returns (E, complex array over dets)."""
+    psi = basis_state(n, det)
+    thetas = [coeff * t[param] for (_, _, coeff, param) in arots]
+    for (x, z, _, _), th in zip(arots, thetas):
+        psi = rotate(psi, n, int(x), int(z), th)
+    sig = apply_sum(psi, n, terms)
+    e = np.vdot(psi, sig).real
+    for k in range(len(arots) - 1, -1, -1):
+        x, z, _, _ = arots[k]
+        sig = rotate(sig, n, int(x), int(z), -thetas[k])
+    return e, np.array([sig[int(b)] for b in dets], dtype=complex)
+
+
 def fd_gradient(n: int, det: int, arots, t, terms, params, h: float = 1e-4):
     """Central finite differences of E(t) for the listed parameter indices."""
     t = np.asarray(t, dtype=float)

@@ -170,6 +170,28 @@ def uccsd_ansatz(n_orb: int, n_el: int):
     return as_arots(np.concatenate(xs), np.concatenate(zs), np.concatenate(cs), np.concatenate(ps)), exs
 
 
+def excited_determinants(excitations, det: int):
+    """The excited determinants tau_mu |det> of the PQE residuals (Eq. 23) as
+    (basis indices, signs): tau = a+_a a+_b a_j a_i acts right to left, each
+    ladder operator on spin orbital p contributing (-1)^{(occupied orbitals
+    below p)} (Eq. 15-16).  r_mu = sign_mu * <index_mu| U^dagger H U |det>."""
+    idx = np.zeros(len(excitations), dtype=np.uint64)
+    sgn = np.zeros(len(excitations))
+    for k, (occ, vir) in enumerate(excitations):
+        d, s = int(det), 1.0
+        ops = [(True, a) for a in vir] + [(False, i) for i in reversed(occ)]  # left to right
+        for create, p in reversed(ops):
+            occupied = (d >> p) & 1
+            if occupied == create:
+                raise ValueError("excitation does not act on this determinant")
+            if bin(d & ((1 << p) - 1)).count("1") & 1:
+                s = -s
+            d ^= 1 << p
+        idx[k] = d
+        sgn[k] = s
+    return idx, sgn
+
+
 def bind_thetas(ansatz: np.ndarray, t) -> np.ndarray:
     """Plain rotation list (ROT_DTYPE) for parameters t."""
     t = np.asarray(t, dtype=np.float64)

@@ -190,3 +190,74 @@ def test_ucc_pauli_route_equals_fermion_route():
         for x, z, c in fermion.jw_kappa_rotations(n, ex):
             psi = pauli.rotate(psi, n, x, z, -c * tm)
     np.testing.assert_allclose(psi, a, atol=1e-13)
+
+
+@pytest.mark.parametrize("n_orb,ne,seed", [(3, 2, 11), (4, 4, 12)])
+def test_pqe_residuals_projection_equals_energy_form(n_orb, ne, seed):
+    """Eq. 23 (projection of U^dagger H U Phi_0 on tau_mu Phi_0) and Eq. 24 (three
+    energies with Omega_mu of Eq. 25) give the same residuals."""
+    h, g = integrals(n_orb, seed)
+    exs = fermion.excitations(n_orb, ne)
+    t = amplitudes(len(exs), seed, 0.3)
+    e, r = fermion.pqe_residuals(n_orb, ne, h, g, t, exs)
+    assert np.abs(r.imag).max() < 1e-14
+    np.testing.assert_allclose(r.real, fermion.pqe_residuals_from_energies(n_orb, ne, h, g, t, exs), atol=1e-12)
+    assert abs(e - fermion.ucc_energy(n_orb, ne, h, g, t, exs)) < 1e-12
+
+
+def test_pqe_residuals_at_reference_are_half_the_gradient_and_hamiltonian_elements():
+    """At t = 0: r_mu = <Phi_mu|H|Phi_0> (a Hamiltonian matrix element), and
+    dE/dt_mu = <Phi_0|[H, kappa_mu]|Phi_0> = 2 r_mu for real H."""
+    n_orb, ne = 3, 2
+    n = 2 * n_orb
+    h, g = integrals(n_orb, 13)
+    exs = fermion.excitations(n_orb, ne)
+    t = np.zeros(len(exs))
+    _, r = fermion.pqe_residuals(n_orb, ne, h, g, t, exs)
+    _, grad = fermion.ucc_gradient_adjoint(n_orb, ne, h, g, t, exs)
+    np.testing.assert_allclose(2 * r.real, grad, atol=1e-12)
+    H = fermion.hamiltonian_dense(n_orb, h, g)
+    ref = np.zeros(1 << n, dtype=complex)
+    ref[fermion.hf_det(ne)] = 1.0
+    for ex, rm in zip(exs, r):
+        assert abs(rm - np.vdot(fermion.excited_state(n, ne, ex), H @ ref)) < 1e-12
+
+
+def test_pqe_residuals_pauli_route_equals_fermion_route():
+    """The Pauli route (JW rotations and Hamiltonian, residual read at the excited
+    determinant's index times its fermionic sign) equals the fermionic route."""
+    from paper_2108_04413_gb300 import prep
+
+    n_orb, ne = 3, 2
+    n = 2 * n_orb
+    h, g = integrals(n_orb, 14)
+    exs = fermion.excitations(n_orb, ne)
+    t = amplitudes(len(exs), 14, 0.4)
+    _, r_f = fermion.pqe_residuals(n_orb, ne, h, g, t, exs)
+    A, exs_p = prep.uccsd_ansatz(n_orb, ne)
+    T = prep.molecular_hamiltonian(h, g)
+    assert [tuple(map(tuple, e)) for e in exs_p] == [tuple(map(tuple, e)) for e in exs]
+    dets, signs = [], []
+    for ex in exs:
+        v = fermion.excited_state(n, ne, ex)
+        b = int(np.flatnonzero(v)[0])
+        dets.append(b)
+        signs.append(v[b].real)
+    arots = list(zip(A["x"], A["z"], A["coeff"], A["param"]))
+    _, r_p = pauli.residuals(n, fermion.hf_det(ne), arots, t, list(zip(T["x"], T["z"], T["coeff"])), dets)
+    np.testing.assert_allclose(np.array(signs) * r_p, r_f, atol=1e-12)
+
+
+def test_prep_excited_determinants_match_ladder_action():
+    """Host prep's excited determinants and signs against the oracle's tau_mu |Phi_0>."""
+    from paper_2108_04413_gb300 import prep
+
+    n_orb, ne = 4, 4
+    n = 2 * n_orb
+    exs = fermion.excitations(n_orb, ne)
+    idx, sgn = prep.excited_determinants(exs, fermion.hf_det(ne))
+    for ex, b, s in zip(exs, idx, sgn):
+        v = fermion.excited_state(n, ne, ex)
+        ref = np.zeros_like(v)
+        ref[int(b)] = s
+        np.testing.assert_array_equal(v, ref)

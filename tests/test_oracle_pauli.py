@@ -135,3 +135,24 @@ def test_planted_sign_error_is_caught():
     zero = np.array([1, 0], dtype=complex)
     wrong = np.cos(th) * zero + 1j * np.sin(th) * pauli.apply(zero, 1, 1, 0)
     assert np.abs(wrong - np.array([np.cos(th), -1j * np.sin(th)])).max() > 0.5
+
+
+def test_residuals_match_dense_transformed_hamiltonian():
+    """<b|U^dagger H U|Phi> (Eq. 23 on basis determinants) against the dense
+    matrices: U as the product of expm(-i theta P) built from Kronecker
+    products, H as the dense Pauli sum."""
+    n = 5
+    rng = np.random.default_rng(23)
+    arots = [(int(rng.integers(1, 32)), int(rng.integers(0, 32)), float(rng.normal()), k % 4) for k in range(10)]
+    t = rng.normal(size=4)
+    terms = [(int(rng.integers(0, 32)), int(rng.integers(0, 32)), float(rng.normal())) for _ in range(15)]
+    det = 0b00101
+    dets = list(range(32))
+    e, r = pauli.residuals(n, det, arots, t, terms, dets)
+    U = np.eye(32, dtype=complex)
+    for (x, z, c, p) in arots:
+        U = sl.expm(-1j * c * t[p] * pauli.dense(n, x, z)) @ U
+    Hbar = U.conj().T @ pauli.dense_sum(n, terms) @ U
+    np.testing.assert_allclose(r, Hbar[:, det], atol=1e-12)
+    assert abs(e - Hbar[det, det].real) < 1e-12
+    assert abs(e - pauli.energy(n, det, arots, t, terms)) < 1e-12
