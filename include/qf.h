@@ -109,6 +109,21 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
 qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
                          size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad);
 
+/* PQE residuals (Sec. PQE, Eq. 23): for each of the n_dets basis determinants b,
+ * res[2k] + i res[2k+1] = <b| U(t)^+ H U(t) |det> / |U(t) det|, with the energy
+ * and, when grad is not NULL, the gradient of qf_energy_grad (same arguments,
+ * same pass).  The residual of an excited determinant tau_mu|det> is its
+ * fermionic sign times the value at tau_mu's basis index (the host prep module
+ * gives both).  res holds 2 * n_dets doubles.  The value is read from
+ * lambda = U^+ H U |det> at the end of the reverse sweep.  When every b shares
+ * the reference's alpha and beta occupation counts the compact sector path
+ * computes it; otherwise the call takes the general path, since H may connect
+ * sectors.  A bit of b at or above n gives QF_EINVAL.  Synchronises the stream;
+ * leaves the state as qf_energy_grad does. */
+qf_status qf_residuals(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                       size_t n_par, const qf_term* terms, size_t n_terms, const uint64_t* dets, size_t n_dets,
+                       double* energy, double* grad, double* res);
+
 /* Copy the state to / from host memory (bytes must equal 2^n * size).  The
  * copy to host folds the internal scale into the amplitudes first. */
 qf_status qf_state_copy_to_host(qf_state* st, void* host, size_t bytes);

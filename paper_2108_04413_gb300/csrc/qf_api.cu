@@ -162,6 +162,8 @@ struct qf_state {
   size_t cstate_cap = 0;
   void* d_runblk = nullptr;  // part-local sweep descriptors (blocks, then parts)
   size_t runblk_cap = 0;
+  void* d_idx = nullptr;     // residual read-out indices
+  size_t idx_cap = 0;
   void* d_log = nullptr;     // forward log of the part-local sweeps (psi pairs after each block)
   size_t log_cap = 0;
   bool log_failed = false;   // the log did not fit: later calls un-rotate psi instead
@@ -1158,6 +1160,17 @@ qf_status ensure_buf(void** p, size_t* cap, size_t bytes, const char* what) {
   return QF_OK;
 }
 
+// Residual read-out: out[2k], out[2k + 1] = the amplitude of lam at idx[k].
+cudaError_t gather_residuals(qf_state* st, const void* lam, bool packed, const std::vector<int64_t>& idx,
+                             double* out) {
+  if (ensure_buf(&st->d_idx, &st->idx_cap, idx.size() * sizeof(int64_t), "residual indices") != QF_OK)
+    return cudaErrorMemoryAllocation;
+  cudaError_t e = h2d(st->d_idx, idx.data(), idx.size() * sizeof(int64_t), st->stream);
+  if (e != cudaSuccess) return e;
+  return qf::launch_gather(lam, st->dt, static_cast<const int64_t*>(st->d_idx), (int)idx.size(), packed, out,
+                           st->stream);
+}
+
 qf_status ensure_sector_buffers(qf_state* st, size_t nblk, size_t partials) {
   if (nblk > st->secblk_cap) {
     cudaFree(st->d_secblk);
@@ -1391,6 +1404,7 @@ qf_status qf_state_destroy(qf_state* st) {
   cudaFree(st->d_cstate);
   cudaFree(st->d_runblk);
   cudaFree(st->d_log);
+  cudaFree(st->d_idx);
   cudaFree(st->d_partials);
   cudaFree(st->d_counter);
   cudaFree(st->d_out);
@@ -1478,11 +1492,16 @@ static qf_status ensure_lam(qf_state* st) {
   return QF_OK;
 }
 
-qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
-                         size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad) {
+// Energy, gradient (grad may be NULL) and, for n_dets basis indices, the
+// residuals <b|U^dagger H U|det> / |psi| as (re, im) pairs in res.
+static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                                  size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad,
+                                  const uint64_t* dets, size_t n_dets, double* res) {
   if (!st || !energy) return fail(QF_EINVAL, "NULL argument");
-  if ((n_rot && !ansatz) || (n_par && !t) || (n_par && !grad) || (n_terms && !terms))
+  if ((n_rot && !ansatz) || (n_par && !t) || (n_terms && !terms) || (n_dets && (!dets || !res)))
     return fail(QF_EINVAL, "NULL array");
+  for (size_t k = 0; k < n_dets; ++k)
+    if (st->n < 64 && (dets[k] >> st->n)) return fail(QF_EINVAL, "residual determinant has a bit at or above the qubit count");
   if (st->n < 64 && (det >> st->n)) return fail(QF_EINVAL, "determinant has a bit at or above the qubit count");
   std::vector<RotIn> r(n_rot);
   std::vector<int32_t> par(n_rot);
@@ -1568,7 +1587,7 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   qf_state::AnsatzPlan& ap = ait->second;
   std::vector<Blk>& blocks = ap.blocks;
   const size_t nblk = blocks.size();
-  qf_status os = ensure_out(st, nblk + 2);
+  qf_status os = ensure_out(st, nblk + 2 + 2 * n_dets);
   if (os != QF_OK) return os;
   const ExpPlan* p = nullptr;
   if (n_terms) {
@@ -1607,6 +1626,9 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   // members of that sector, stored contiguously (compact layout) in a buffer of
   // the handle; psi itself is only reset to |det> at the end.
   bool sector = !blocks.empty() && n <= 2 * qf::kSecMaxPos;
+  // residuals outside the sector need H psi off the sector too: general path
+  for (size_t k = 0; sector && k < n_dets; ++k)
+    sector = popc(dets[k] & kEvenMask) == na && popc(dets[k] & ~kEvenMask) == nbeta;
   if (sector && !sec_cached) {
     // first evaluation of this ansatz in this sector: the run plan
     std::vector<qf::SecBlk> sec(2 * nblk);
@@ -1628,11 +1650,13 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     st->real = true;
     st->sec_a = na;
     st->sec_b = nbeta;
-    if (!p) {  // no Hamiltonian terms: E = 0 and a zero gradient
+    if (!p) {  // no Hamiltonian terms: E = 0, a zero gradient and zero residuals
       QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
       QF_CUDA(cudaStreamSynchronize(st->stream));
       *energy = 0.0;
-      for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
+      if (grad)
+        for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
+      for (size_t k = 0; k < 2 * n_dets; ++k) res[k] = 0.0;
       return QF_OK;
     }
     const SectorRuns& rs = ap.runs;
@@ -1691,14 +1715,23 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
     QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
                                    (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, d_strs,
                                    st->stream));
+    if (n_dets) {  // residuals: lambda after the reverse sweep is U^dagger H psi
+      std::vector<int64_t> idx(n_dets);
+      for (size_t k = 0; k < n_dets; ++k) idx[k] = (int64_t)compact_of(dets[k], sp);
+      QF_CUDA(gather_residuals(st, lreal ? cpsi : clam, lreal, idx, st->d_out + nblk + 2));
+    }
     QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
-    QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2) * sizeof(double), st->stream));
+    QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2 + 2 * n_dets) * sizeof(double), st->stream));
     QF_CUDA(cudaStreamSynchronize(st->stream));
     double nrm = st->h_out[nblk + 1];
     if (!(nrm > 0.0)) nrm = 1.0;
     *energy = st->h_out[nblk] / nrm;
-    for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
-    for (size_t bi = 0; bi < nblk; ++bi) grad[par[blocks[bi].i]] += 2.0 * st->h_out[bi] / nrm;
+    if (grad) {
+      for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
+      for (size_t bi = 0; bi < nblk; ++bi) grad[par[blocks[bi].i]] += 2.0 * st->h_out[bi] / nrm;
+    }
+    const double rs_scale = 1.0 / std::sqrt(nrm);  // residuals scale with |psi|
+    for (size_t k = 0; k < 2 * n_dets; ++k) res[k] = st->h_out[nblk + 2 + k] * rs_scale;
     return QF_OK;
   }
   qf_status ls = ensure_lam(st);
@@ -1770,7 +1803,11 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   }
   st->scale = sc;
   st->real = both_real;
-  QF_CUDA(d2h(st->h_out, st->d_out, (blocks.size() + 2) * sizeof(double), st->stream));
+  if (n_dets) {  // residuals: lambda after the reverse sweep is U^dagger H psi (scale sc)
+    std::vector<int64_t> idx(dets, dets + n_dets);
+    QF_CUDA(gather_residuals(st, st->lam, false, idx, st->d_out + blocks.size() + 2));
+  }
+  QF_CUDA(d2h(st->h_out, st->d_out, (blocks.size() + 2 + 2 * n_dets) * sizeof(double), st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));
   // U(t)|det> has unit norm; dividing by the computed <psi|psi> (FP64) removes the
   // rounding drift of the stored norm (the Rayleigh quotient and its gradient;
@@ -1778,16 +1815,32 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
   double nrm = p ? st->h_out[blocks.size() + 1] * s_fwd * s_fwd : 1.0;
   if (!(nrm > 0.0)) nrm = 1.0;
   *energy = st->h_out[blocks.size()] * s_fwd * s_fwd / nrm;
-  for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
-  for (size_t bi = 0; bi < blocks.size(); ++bi) {
-    const Blk& b = blocks[bi];
-    const double g = 2.0 * st->h_out[bi] * s2[bi] / nrm;
-    if (b.sparse)
-      grad[par[b.i]] += g;
-    else
-      grad[par[b.i]] += r[b.i].coeff * g;
+  if (grad) {
+    for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
+    for (size_t bi = 0; bi < blocks.size(); ++bi) {
+      const Blk& b = blocks[bi];
+      const double g = 2.0 * st->h_out[bi] * s2[bi] / nrm;
+      if (b.sparse)
+        grad[par[b.i]] += g;
+      else
+        grad[par[b.i]] += r[b.i].coeff * g;
+    }
   }
+  const double rs_scale = sc / std::sqrt(nrm);  // stored lambda times the shared scale, over |psi|
+  for (size_t k = 0; k < 2 * n_dets; ++k) res[k] = st->h_out[blocks.size() + 2 + k] * rs_scale;
   return QF_OK;
+}
+
+qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                         size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad) {
+  if (n_par && !grad) return fail(QF_EINVAL, "NULL array");
+  return energy_grad_impl(st, det, ansatz, n_rot, t, n_par, terms, n_terms, energy, grad, nullptr, 0, nullptr);
+}
+
+qf_status qf_residuals(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                       size_t n_par, const qf_term* terms, size_t n_terms, const uint64_t* dets, size_t n_dets,
+                       double* energy, double* grad, double* res) {
+  return energy_grad_impl(st, det, ansatz, n_rot, t, n_par, terms, n_terms, energy, grad, dets, n_dets, res);
 }
 
 qf_status qf_state_fold_scale(qf_state* st) {

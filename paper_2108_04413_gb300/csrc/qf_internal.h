@@ -230,6 +230,10 @@ struct SecRank {
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s);
 // count amplitudes set to the unit vector e_idx.
 cudaError_t launch_zero_and_set_count(void* psi, uint64_t count, qf_dtype dt, uint64_t idx, cudaStream_t s);
+// out[2k], out[2k + 1] = (re, im) of src[idx[k]] (zeros where idx[k] < 0); packed: a
+// real value kept in the imaginary slot.
+cudaError_t launch_gather(const void* src, qf_dtype dt, const int64_t* idx, int count, bool packed, double* out,
+                          cudaStream_t s);
 cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s);
 cudaError_t launch_rot(void* psi, int n, qf_dtype dt, const RotArgs& a, cudaStream_t s);
 cudaError_t launch_tile(void* psi, int n, qf_dtype dt, const TileArgs& a, cudaStream_t s);

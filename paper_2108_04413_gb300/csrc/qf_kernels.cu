@@ -153,6 +153,28 @@ __global__ void k_zero_and_set(V* psi, uint64_t N, uint64_t det) {
   }
 }
 
+// out[2k], out[2k + 1] = the amplitude at idx[k] (0 where idx[k] < 0); packed:
+// the real value stored in the imaginary slot, imaginary part 0.
+template <typename V>
+__global__ void k_gather(const V* __restrict__ src, const int64_t* __restrict__ idx, int count, int packed,
+                         double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int64_t i = idx[k];
+  double re = 0.0, im = 0.0;
+  if (i >= 0) {
+    const V v = src[i];
+    if (packed) {
+      re = (double)v.y;
+    } else {
+      re = (double)v.x;
+      im = (double)v.y;
+    }
+  }
+  out[2 * k] = re;
+  out[2 * k + 1] = im;
+}
+
 template <typename T>
 __global__ void k_scale(typename Cx<T>::V* psi, uint64_t N, T s) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -1025,6 +1047,18 @@ cudaError_t launch_zero_and_set_count(void* psi, uint64_t N, qf_dtype dt, uint64
   else
     k_zero_and_set<float2><<<g, 256, 0, s>>>(static_cast<float2*>(psi), N, det);
   prof_post(prof_slot_, s);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void* src, qf_dtype dt, const int64_t* idx, int count, bool packed, double* out,
+                          cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)((count + 255) / 256);
+  if (dt == QF_C128)
+    k_gather<double2><<<g, 256, 0, s>>>(static_cast<const double2*>(src), idx, count, packed ? 1 : 0, out);
+  else
+    k_gather<float2><<<g, 256, 0, s>>>(static_cast<const float2*>(src), idx, count, packed ? 1 : 0, out);
   count_launch();
   return cudaGetLastError();
 }

@@ -38,6 +38,7 @@ _SIGS = {
     "qf_apply_circuit": (ctypes.c_int, [_vp, _vp, _sz]),
     "qf_expectation": (ctypes.c_int, [_vp, _vp, _sz, _dp, _dp]),
     "qf_energy_grad": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _dp, _vp]),
+    "qf_residuals": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _dp, _vp, _vp]),
     "qf_state_copy_to_host": (ctypes.c_int, [_vp, _vp, _sz]),
     "qf_state_copy_from_host": (ctypes.c_int, [_vp, _vp, _sz]),
     "qf_state_fold_scale": (ctypes.c_int, [_vp]),
@@ -195,6 +196,22 @@ class State:
         _check(_lib.qf_energy_grad(self._h, int(det), _ptr(ansatz), len(ansatz), _ptr(t), len(t), _ptr(terms),
                                    len(terms), ctypes.byref(e), _ptr(grad)))
         return e.value, grad
+
+    def residuals(self, det: int, ansatz: np.ndarray, t, terms: np.ndarray, dets, grad: bool = False):
+        """PQE residuals <b|U^dagger H U|det> for the basis indices dets (complex
+        array), with the energy and, if grad, the gradient."""
+        ansatz = np.ascontiguousarray(ansatz, dtype=AROT_DTYPE)
+        terms = np.ascontiguousarray(terms, dtype=TERM_DTYPE)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        dets = np.ascontiguousarray(dets, dtype=np.uint64)
+        res = np.zeros(2 * len(dets), dtype=np.float64)
+        g = np.zeros(len(t), dtype=np.float64) if grad else None
+        e = _d()
+        _check(_lib.qf_residuals(self._h, int(det), _ptr(ansatz), len(ansatz), _ptr(t), len(t), _ptr(terms),
+                                 len(terms), _ptr(dets), len(dets), ctypes.byref(e),
+                                 _ptr(g) if grad else None, _ptr(res)))
+        r = res[0::2] + 1j * res[1::2]
+        return (e.value, r, g) if grad else (e.value, r)
 
     def set_hpsi_mode(self, mode: int):
         _check(_lib.qf_state_set_hpsi_mode(self._h, int(mode)))

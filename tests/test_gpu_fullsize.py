@@ -128,3 +128,20 @@ def test_sweep28_fused_equals_unfused(dtype, tol):
     assert im1 == 0.0 and abs(e1 - e2) < (1e-11 if dtype == "c128" else 1e-5)
     s1.close()
     s2.close()
+
+
+def test_ucc24_residuals_at_reference_are_half_the_gradient(ucc24):
+    """At t = 0, dE/dt_mu = <Phi_0|[H, kappa_mu]|Phi_0> = 2 r_mu for every one of
+    the 1818 excitations (a property that holds at any size; the oracle pins it
+    at small sizes)."""
+    cfg, h, g, T, A, exs, t = ucc24
+    det = (1 << cfg["n_el"]) - 1
+    idx, sgn = prep.excited_determinants(exs, det)
+    t0 = np.zeros(len(exs))
+    st = qf.State(cfg["n_qubits"], "c128")
+    e, r, grad = st.residuals(det, A, t0, T, idx, grad=True)
+    assert np.abs(r.imag).max() == 0.0
+    assert np.abs(2 * sgn * r.real - grad).max() < 1e-10
+    e1, r1 = st.residuals(det, A, t, T, idx)
+    assert abs(e1 - st.energy_grad(det, A, t, T)[0]) < 1e-12
+    assert np.isfinite(r1).all()

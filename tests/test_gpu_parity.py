@@ -404,3 +404,54 @@ def test_bounded_wait_times_out_and_context_survives():
     st.apply_pauli_exp(0b101, 0b010, 0.4)
     ref = pauli.rotate(pauli.basis_state(6, 3), 6, 0b101, 0b010, 0.4)
     assert np.abs(st.to_numpy() - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("cfg_id,dtype", [(0, "c128"), (1, "c128"), (0, "c64"), (1, "c64")])
+def test_pqe_residuals_match_oracle(cfg_id, dtype):
+    """PQE residuals r_mu = <Phi_mu|U^dagger H U|Phi_0> (Eq. 23) of every dUCCSD
+    excitation, through qf_residuals on the compact sector path, against the
+    oracle's fermionic route; the energy and gradient that come along match
+    qf_energy_grad."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(cfg_id)
+    det = (1 << cfg["n_el"]) - 1
+    idx, sgn = prep.excited_determinants(exs, det)
+    st = qf.State(cfg["n_qubits"], dtype)
+    e, r, gr = st.residuals(det, A, t, T, idx, grad=True)
+    e_ref, r_ref = fermion.pqe_residuals(cfg["n_orb"], cfg["n_el"], h, g, t, exs)
+    tol = TOL_E_C128 if dtype == "c128" else TOL_E_C64
+    assert abs(e - e_ref) < tol
+    assert np.abs(sgn * r - r_ref).max() < tol
+    e2, g2 = st.energy_grad(det, A, t, T)
+    assert e2 == e and np.array_equal(g2, gr)
+    out = st.to_numpy()  # the sector path leaves exactly |det>
+    assert out[det] == 1.0 and np.count_nonzero(out) == 1
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_residuals_general_path_match_oracle(dtype):
+    """Determinants outside the reference's sector send qf_residuals down the
+    general path (H may connect sectors); a non-commuting generic ansatz always
+    takes it.  Every basis index of 8 qubits, against the Pauli oracle."""
+    n = 8
+    rng = np.random.default_rng(31)
+    T = qf.as_terms(rng.integers(0, 256, 50), rng.integers(0, 256, 50), rng.normal(size=50))
+    terms = _terms_list(T)
+    cfg, h, g, Tu, A, exs, t = _ucc_problem(0)
+    det = (1 << cfg["n_el"]) - 1
+    dets = np.arange(256, dtype=np.uint64)
+    tol = 1e-10 if dtype == "c128" else 1e-5
+    st = qf.State(n, dtype)
+    for ans, tt in ((A, t), (qf.as_arots(rng.integers(0, 256, 30), rng.integers(0, 256, 30), rng.normal(size=30),
+                                          rng.integers(0, 7, 30)), rng.normal(size=7))):
+        e, r = st.residuals(det, ans, tt, T, dets)
+        arots = list(zip(ans["x"], ans["z"], ans["coeff"], ans["param"]))
+        e_ref, r_ref = pauli.residuals(n, det, arots, tt, terms, dets)
+        assert abs(e - e_ref) < tol
+        assert np.abs(r - r_ref).max() < tol
+
+
+def test_residuals_invalid_determinant_rejected():
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    st = qf.State(cfg["n_qubits"], "c128")
+    with pytest.raises(qf.QFError):
+        st.residuals(15, A, t, T, np.array([1 << cfg["n_qubits"]], dtype=np.uint64))
