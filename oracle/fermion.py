@@ -268,6 +268,16 @@ def ucc_gradient_adjoint(n_orb, n_el, h, g, t, exs=None):
     return e, grad
 
 
+def adapt_gradients(n_orb, n_el, h, g, t, exs, pool):
+    """g_nu = <Psi| [H, kappa_nu] |Psi> (Eq. 21) = 2 Re <H Psi| kappa_nu Psi> for
+    each pool excitation, with Psi the dUCC state of exs and t.  Returns (E, g)."""
+    n = 2 * n_orb
+    psi = ucc_state(n_orb, n_el, t, exs)
+    lam = hamiltonian_apply(psi, n_orb, h, g)
+    out = np.array([2.0 * np.vdot(lam, kappa_apply(psi, n, ex)).real for ex in pool])
+    return np.vdot(psi, lam).real, out
+
+
 def excited_state(n: int, n_el: int, ex) -> np.ndarray:
     """|Phi_mu> = tau_mu |Phi_HF> (with its fermionic sign)."""
     phi = np.zeros(1 << n, dtype=complex)

@@ -164,6 +164,21 @@ def residuals(n: int, det: int, arots, t, terms, dets):
     return e, np.array([sig[int(b)] for b in dets], dtype=complex)
 
 
+def pool_gradients(n: int, det: int, arots, t, terms, pool, n_pool: int):
+    """Gradients of a pool of operators at the state U(t)|Phi> (Eq. 21, Sec.
+    ADAPT): appending the pool's rotations exp(-i coeff_k s_p P_k) at s = 0,
+        dE/ds_p = sum_{k in p} coeff_k * 2 Im <H psi | P_k | psi>.
+    pool lists (x, z, coeff, param) with param in [0, n_pool).  Returns (E, g)."""
+    psi = basis_state(n, det)
+    for (x, z, coeff, param) in arots:
+        psi = rotate(psi, n, int(x), int(z), coeff * t[param])
+    lam = apply_sum(psi, n, terms)
+    g = np.zeros(n_pool)
+    for (x, z, coeff, param) in pool:
+        g[param] += coeff * 2.0 * np.vdot(lam, apply(psi, n, int(x), int(z))).imag
+    return np.vdot(psi, lam).real, g
+
+
 def fd_gradient(n: int, det: int, arots, t, terms, params, h: float = 1e-4):
     """Central finite differences of E(t) for the listed parameter indices."""
     t = np.asarray(t, dtype=float)

@@ -261,3 +261,34 @@ def test_prep_excited_determinants_match_ladder_action():
         ref = np.zeros_like(v)
         ref[int(b)] = s
         np.testing.assert_array_equal(v, ref)
+
+
+def test_adapt_gradients_dense_commutator_and_pauli_route():
+    """Eq. 21: g_nu = <Psi|[H, kappa_nu]|Psi> against the dense commutator, against
+    the Pauli route with the JW pool, and, for the ansatz's own operators at
+    t = 0, against the dUCC gradient."""
+    from paper_2108_04413_gb300 import prep
+
+    n_orb, ne = 3, 2
+    n = 2 * n_orb
+    h, g = integrals(n_orb, 21)
+    exs = fermion.excitations(n_orb, ne)
+    t = amplitudes(len(exs), 21, 0.3)
+    pool = exs[::-1]
+    e, gp = fermion.adapt_gradients(n_orb, ne, h, g, t, exs, pool)
+    psi = fermion.ucc_state(n_orb, ne, t, exs)
+    H = fermion.hamiltonian_dense(n_orb, h, g)
+    for ex, gv in zip(pool, gp):
+        K = fermion.kappa_dense(n, ex)
+        assert abs(np.vdot(psi, (H @ K - K @ H) @ psi) - gv) < 1e-12
+    A, _ = prep.uccsd_ansatz(n_orb, ne)
+    T = prep.molecular_hamiltonian(h, g)
+    # the pool is the excitation list reversed: ansatz parameter p is pool operator len - 1 - p
+    pool_rots = [(x, z, c, len(pool) - 1 - p) for x, z, c, p in zip(A["x"], A["z"], A["coeff"], A["param"])]
+    e2, g2 = pauli.pool_gradients(n, fermion.hf_det(ne), list(zip(A["x"], A["z"], A["coeff"], A["param"])), t,
+                                  list(zip(T["x"], T["z"], T["coeff"])), pool_rots, len(pool))
+    assert abs(e - e2) < 1e-12
+    np.testing.assert_allclose(g2, gp, atol=1e-12)
+    _, g0 = fermion.adapt_gradients(n_orb, ne, h, g, np.zeros(len(exs)), exs, exs)
+    _, gref = fermion.ucc_gradient_adjoint(n_orb, ne, h, g, np.zeros(len(exs)), exs)
+    np.testing.assert_allclose(g0, gref, atol=1e-12)

@@ -156,3 +156,25 @@ def test_residuals_match_dense_transformed_hamiltonian():
     np.testing.assert_allclose(r, Hbar[:, det], atol=1e-12)
     assert abs(e - Hbar[det, det].real) < 1e-12
     assert abs(e - pauli.energy(n, det, arots, t, terms)) < 1e-12
+
+
+def test_pool_gradients_match_finite_differences_of_the_appended_block():
+    """Eq. 21 on Pauli rotations: the pool gradient equals the derivative of the
+    energy with the pool operator's rotations appended, at zero angle."""
+    n = 5
+    rng = np.random.default_rng(21)
+    arots = [(int(rng.integers(1, 32)), int(rng.integers(0, 32)), float(rng.normal()), k % 3) for k in range(8)]
+    t = rng.normal(size=3)
+    terms = [(int(rng.integers(0, 32)), int(rng.integers(0, 32)), float(rng.normal())) for _ in range(15)]
+    pool = [(int(rng.integers(1, 32)), int(rng.integers(0, 32)), float(rng.normal()), k % 4) for k in range(9)]
+    det = 0b01011
+    e, g = pauli.pool_gradients(n, det, arots, t, terms, pool, 4)
+    assert abs(e - pauli.energy(n, det, arots, t, terms)) < 1e-13
+    for p in range(4):
+        block = [(x, z, c, 3) for (x, z, c, q) in pool if q == p]  # the pool operator as parameter 3 of an extension
+        ext = list(arots) + block
+        fd = []
+        for s in (1e-5, -1e-5):
+            tt = np.r_[t, s]
+            fd.append(pauli.energy(n, det, ext, tt, terms))
+        assert abs((fd[0] - fd[1]) / 2e-5 - g[p]) < 1e-8
