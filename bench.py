@@ -413,6 +413,7 @@ def run_gpu(args, rank, world, local, pg):
             out["c64"] = c64_leg(w, args, value, float(energies[-1]), g)
             out["hpsi_fp64_mode"] = fp64_mode_leg(w, args, value, float(energies[-1]), g)
             out["pqe"] = pqe_leg(w, args, value, g)
+            out["adapt"] = adapt_leg(w, args, value)
         out["serving"] = serving_leg(args)
         out["sweep28"] = sweep28_leg()
         t_eval, sample = oracle_sample_ucc(w)
@@ -657,6 +658,34 @@ def pqe_leg(w, args, value128, g128):
     return {"value": v, "unit": "residual evals/s (1818 residuals + energy + gradient each)",
             "relative_to_energy_grad": v / value128, "max_abs_residual": float(np.abs(rr).max()),
             "grad_same_as_energy_grad": bool(np.array_equal(g, g128))}
+
+
+def adapt_leg(w, args, value128):
+    """ADAPT pool gradients (Eq. 21) of the full spin-conserving singles-and-doubles
+    pool (1818 operators) at the 24-qubit dUCCSD state, complex128."""
+    import torch
+
+    from paper_2108_04413_gb300 import qf
+
+    pool = w["ansatz"].copy()
+    npool = len(w["exs"])
+    stream = torch.cuda.Stream()
+    st = qf.State(w["n"], "c128", stream=stream)
+    for _ in range(2):
+        st.pool_gradients(w["det"], w["ansatz"], w["t"], w["terms"], pool, npool)
+    torch.cuda.synchronize()
+    steps = max(2, args.steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        e, gp = st.pool_gradients(w["det"], w["ansatz"], w["t"], w["terms"], pool, npool)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    v = steps / (e0.elapsed_time(e1) / 1e3)
+    st.close()
+    return {"value": v, "unit": f"pool-gradient evals/s ({npool} operators + energy each)",
+            "relative_to_energy_grad": v / value128, "max_abs_pool_gradient": float(np.abs(gp).max())}
 
 
 def run_sweep28(args, rank, world, local, pg, pk):

@@ -124,6 +124,21 @@ qf_status qf_residuals(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t
                        size_t n_par, const qf_term* terms, size_t n_terms, const uint64_t* dets, size_t n_dets,
                        double* energy, double* grad, double* res);
 
+/* Operator-pool gradients of ADAPT (Sec. ADAPT, Eq. 21): for the state
+ * psi = U(t)|det>, pool_grad[p] = <psi|[H, kappa_p]|psi> for each pool operator p,
+ * where the pool is a rotation list like an ansatz (pool[k].param in [0, n_pool)
+ * names its operator, exp(s_p kappa_p) = prod_{k in p} exp(-i s_p coeff_k P_k)).
+ * Equivalently, the derivative at s = 0 of the energy with the operator
+ * appended to the ansatz.  Also returns the energy.  On the compact sector path
+ * (every ansatz and pool block a sector block, real H) one overlap pass on the
+ * final (psi, H psi) gives every pool gradient and no reverse sweep is run.
+ * Otherwise the pool is appended to the ansatz at zero angle and differentiated
+ * with qf_energy_grad's general path.  The pool's block structure is planned
+ * once per handle.  Synchronises the stream. */
+qf_status qf_pool_gradients(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                            size_t n_par, const qf_term* terms, size_t n_terms, const qf_arot* pool, size_t n_pool_rot,
+                            size_t n_pool, double* energy, double* pool_grad);
+
 /* Copy the state to / from host memory (bytes must equal 2^n * size).  The
  * copy to host folds the internal scale into the amplitudes first. */
 qf_status qf_state_copy_to_host(qf_state* st, void* host, size_t bytes);

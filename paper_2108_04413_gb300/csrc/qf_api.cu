@@ -164,6 +164,9 @@ struct qf_state {
   size_t runblk_cap = 0;
   void* d_idx = nullptr;     // residual read-out indices
   size_t idx_cap = 0;
+  void* d_poolblk = nullptr; // operator-pool run descriptors (blocks, parts, strings)
+  size_t poolblk_cap = 0;
+  uint64_t pool_key = 0;     // the pool plan and sector whose descriptors sit in d_poolblk
   void* d_log = nullptr;     // forward log of the part-local sweeps (psi pairs after each block)
   size_t log_cap = 0;
   bool log_failed = false;   // the log did not fit: later calls un-rotate psi instead
@@ -1405,6 +1408,7 @@ qf_status qf_state_destroy(qf_state* st) {
   cudaFree(st->d_runblk);
   cudaFree(st->d_log);
   cudaFree(st->d_idx);
+  cudaFree(st->d_poolblk);
   cudaFree(st->d_partials);
   cudaFree(st->d_counter);
   cudaFree(st->d_out);
@@ -1482,6 +1486,67 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
   return QF_OK;
 }
 
+// Block structure of a rotation list: runs of same-X, same-parameter, mutually
+// commuting rotations become sparse composite blocks (their active rows do not
+// depend on the angles, so the structure is kept and only M is refilled);
+// anything else is walked rotation by rotation.
+std::vector<qf_state::Blk> plan_blocks(const RotIn* r, const int32_t* par, size_t n_rot, int n) {
+  using Blk = qf_state::Blk;
+  // candidate runs (assuming every run becomes a block), built in parallel
+  std::vector<std::pair<size_t, int>> runs;
+  for (size_t i = 0; i < n_rot;) {
+    const int run = sparse_run(r, i, n_rot, par);
+    runs.emplace_back(i, run);
+    i += run;
+  }
+  std::vector<Blk> cand(runs.size());
+  std::vector<char> ok(runs.size(), 0);
+  auto work = [&](size_t t0, size_t step) {
+    for (size_t k = t0; k < runs.size(); k += step) {
+      const size_t i = runs[k].first;
+      const int run = runs[k].second;
+      Blk& b = cand[k];
+      b.i = i;
+      b.j = i + run;
+      b.sparse = run >= 2 && build_sparse(r + i, run, n, false, true, &b.fwd) &&
+                 build_sparse(r + i, run, n, true, true, &b.inv) && b.fwd.nr == b.inv.nr;
+      ok[k] = b.sparse;
+    }
+  };
+  const size_t nth = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
+  if (runs.size() >= 64 && nth > 1) {
+    std::vector<std::thread> th;
+    for (size_t t = 0; t < nth; ++t) th.emplace_back(work, t, nth);
+    for (auto& x : th) x.join();
+  } else {
+    work(0, 1);
+  }
+  // assemble in order; a run that is not a sparse block is walked rotation by rotation
+  std::vector<Blk> bl;
+  for (size_t k = 0; k < runs.size(); ++k) {
+    if (ok[k]) {
+      bl.push_back(cand[k]);
+      continue;
+    }
+    for (size_t i = runs[k].first; i < runs[k].first + runs[k].second;) {
+      const int run = sparse_run(r, i, runs[k].first + runs[k].second, par);
+      Blk b;
+      b.i = i;
+      b.sparse = false;
+      if (run >= 2 && build_sparse(r + i, run, n, false, true, &b.fwd) &&
+          build_sparse(r + i, run, n, true, true, &b.inv) && b.fwd.nr == b.inv.nr) {
+        b.sparse = true;
+        b.j = i + run;
+      } else {
+        b.j = i + 1;
+      }
+      bl.push_back(b);
+      i = b.j;
+    }
+  }
+  return bl;
+}
+
 // The lambda buffer, allocated on first need and kept with the handle.
 static qf_status ensure_lam(qf_state* st) {
   if (!st->lam && cudaMalloc(&st->lam, st->bytes()) != cudaSuccess) {
@@ -1494,14 +1559,32 @@ static qf_status ensure_lam(qf_state* st) {
 
 // Energy, gradient (grad may be NULL) and, for n_dets basis indices, the
 // residuals <b|U^dagger H U|det> / |psi| as (re, im) pairs in res.
+// With a pool (n_pool_rot rotations at zero angle, parameters in [0, n_pool)):
+// its gradients (Eq. 21) into pool_grad on the compact sector path; when that
+// path cannot take the pool, *pool_fallback is set before any GPU work and the
+// caller evaluates the pool another way.
 static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
                                   size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad,
-                                  const uint64_t* dets, size_t n_dets, double* res) {
+                                  const uint64_t* dets, size_t n_dets, double* res, const qf_arot* pool = nullptr,
+                                  size_t n_pool_rot = 0, size_t n_pool = 0, double* pool_grad = nullptr,
+                                  bool* pool_fallback = nullptr) {
   if (!st || !energy) return fail(QF_EINVAL, "NULL argument");
   if ((n_rot && !ansatz) || (n_par && !t) || (n_terms && !terms) || (n_dets && (!dets || !res)))
     return fail(QF_EINVAL, "NULL array");
   for (size_t k = 0; k < n_dets; ++k)
     if (st->n < 64 && (dets[k] >> st->n)) return fail(QF_EINVAL, "residual determinant has a bit at or above the qubit count");
+  const bool want_pool = pool_fallback != nullptr;
+  if (want_pool) {
+    *pool_fallback = false;
+    if ((n_pool_rot && !pool) || (n_pool && !pool_grad)) return fail(QF_EINVAL, "NULL array");
+    for (size_t k = 0; k < n_pool_rot; ++k) {
+      qf_status v = validate_masks(st, pool[k].x, pool[k].z);
+      if (v != QF_OK) return v;
+      if (pool[k].param < 0 || (size_t)pool[k].param >= n_pool)
+        return fail(QF_EINVAL, "pool parameter index out of range");
+      if (!std::isfinite(pool[k].coeff)) return fail(QF_EINVAL, "pool coefficient is not finite");
+    }
+  }
   if (st->n < 64 && (det >> st->n)) return fail(QF_EINVAL, "determinant has a bit at or above the qubit count");
   std::vector<RotIn> r(n_rot);
   std::vector<int32_t> par(n_rot);
@@ -1525,60 +1608,8 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
   auto ait = st->ansatz_plans.find(akey);
   bool fresh = false;
   if (ait == st->ansatz_plans.end()) {
-    // first sight of this ansatz: find the sparse blocks (the active rows of a block
-    // do not depend on the angles, so the structure is kept and only M is refilled)
-    // candidate runs (assuming every run becomes a block), built in parallel
-    std::vector<std::pair<size_t, int>> runs;
-    for (size_t i = 0; i < n_rot;) {
-      const int run = sparse_run(r.data(), i, n_rot, par.data());
-      runs.emplace_back(i, run);
-      i += run;
-    }
-    std::vector<Blk> cand(runs.size());
-    std::vector<char> ok(runs.size(), 0);
-    auto work = [&](size_t t0, size_t step) {
-      for (size_t k = t0; k < runs.size(); k += step) {
-        const size_t i = runs[k].first;
-        const int run = runs[k].second;
-        Blk& b = cand[k];
-        b.i = i;
-        b.j = i + run;
-        b.sparse = run >= 2 && build_sparse(&r[i], run, st->n, false, true, &b.fwd) &&
-                   build_sparse(&r[i], run, st->n, true, true, &b.inv) && b.fwd.nr == b.inv.nr;
-        ok[k] = b.sparse;
-      }
-    };
-    const size_t nth = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
-    if (runs.size() >= 64 && nth > 1) {
-      std::vector<std::thread> th;
-      for (size_t t = 0; t < nth; ++t) th.emplace_back(work, t, nth);
-      for (auto& x : th) x.join();
-    } else {
-      work(0, 1);
-    }
-    // assemble in order; a run that is not a sparse block is walked rotation by rotation
-    std::vector<Blk> bl;
-    for (size_t k = 0; k < runs.size(); ++k) {
-      if (ok[k]) {
-        bl.push_back(cand[k]);
-        continue;
-      }
-      for (size_t i = runs[k].first; i < runs[k].first + runs[k].second;) {
-        const int run = sparse_run(r.data(), i, runs[k].first + runs[k].second, par.data());
-        Blk b;
-        b.i = i;
-        b.sparse = false;
-        if (run >= 2 && build_sparse(&r[i], run, st->n, false, true, &b.fwd) &&
-            build_sparse(&r[i], run, st->n, true, true, &b.inv) && b.fwd.nr == b.inv.nr) {
-          b.sparse = true;
-          b.j = i + run;
-        } else {
-          b.j = i + 1;
-        }
-        bl.push_back(b);
-        i = b.j;
-      }
-    }
+    // first sight of this ansatz: find its block structure
+    std::vector<Blk> bl = plan_blocks(r.data(), par.data(), n_rot, st->n);
     qf_state::AnsatzPlan plan;
     plan.blocks = std::move(bl);
     ait = st->ansatz_plans.emplace(akey, std::move(plan)).first;
@@ -1589,6 +1620,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
   const size_t nblk = blocks.size();
   qf_status os = ensure_out(st, nblk + 2 + 2 * n_dets);
   if (os != QF_OK) return os;
+  const bool need_reverse = !want_pool || grad || n_dets;
   const ExpPlan* p = nullptr;
   if (n_terms) {
     qf_status ps = get_plan(st, terms, n_terms, &p);
@@ -1657,14 +1689,60 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
       if (grad)
         for (size_t k = 0; k < n_par; ++k) grad[k] = 0.0;
       for (size_t k = 0; k < 2 * n_dets; ++k) res[k] = 0.0;
+      for (size_t k = 0; k < n_pool; ++k) pool_grad[k] = 0.0;
       return QF_OK;
+    }
+    // the pool (its blocks at zero angle) as sector blocks, planned once per handle
+    qf_state::AnsatzPlan* pp = nullptr;
+    if (want_pool) {
+      if (!lreal) {  // overlaps on the packed (psi, lambda) need a real lambda
+        *pool_fallback = true;
+        return QF_OK;
+      }
+      const uint64_t pkey0 = content_key(pool, n_pool_rot * sizeof(qf_arot), 0x452821E638D01377ull ^ (uint64_t)n);
+      auto pit = st->ansatz_plans.find(pkey0);
+      if (pit == st->ansatz_plans.end()) {
+        std::vector<RotIn> rp(n_pool_rot);
+        std::vector<int32_t> ppar(n_pool_rot);
+        for (size_t k = 0; k < n_pool_rot; ++k) {
+          rp[k] = RotIn{pool[k].x, pool[k].z, 0.0, pool[k].coeff};
+          ppar[k] = pool[k].param;
+        }
+        qf_state::AnsatzPlan plan;
+        plan.blocks = plan_blocks(rp.data(), ppar.data(), n_pool_rot, n);
+        pit = st->ansatz_plans.emplace(pkey0, std::move(plan)).first;
+      }
+      pp = &pit->second;
+      if (!(pp->sec_ok && pp->sec_n == n && pp->sec_na == na && pp->sec_nb == nbeta && pp->sec_cap == cap)) {
+        const size_t nbp = pp->blocks.size();
+        std::vector<qf::SecBlk> sec(2 * nbp);
+        bool ok = nbp > 0;
+        for (size_t bi = 0; ok && bi < nbp; ++bi)
+          ok = pp->blocks[bi].sparse && to_secblk(pp->blocks[bi].fwd, n, na, nbeta, false, &sec[bi]) &&
+               to_secblk(pp->blocks[bi].inv, n, na, nbeta, true, &sec[nbp + bi]);
+        pp->sec_ok = ok && build_runs(sec.data(), nbp, n, na, nbeta, cap, &pp->runs);
+        pp->sec_n = n;
+        pp->sec_na = na;
+        pp->sec_nb = nbeta;
+        pp->sec_cap = cap;
+        st->pool_key = 0;
+      }
+      if (!pp->sec_ok) {
+        *pool_fallback = true;
+        return QF_OK;
+      }
+      const size_t nbp = pp->blocks.size();
+      qf_status po = ensure_out(st, nblk + 2 + 2 * n_dets + nbp);
+      if (po != QF_OK) return po;
     }
     const SectorRuns& rs = ap.runs;
     const qf::SecSpace sp = sector_space(n, na, nbeta);
     qf::SecCompact cm{};
     qf_status cs = ensure_compact(st, sp, na, nbeta, &cm);
     if (cs != QF_OK) return cs;
-    qf_status bs = ensure_sector_buffers(st, 1, nblk * (size_t)rs.pmax);
+    size_t partials = nblk * (size_t)rs.pmax;
+    if (pp) partials = std::max(partials, pp->blocks.size() * (size_t)pp->runs.pmax);
+    qf_status bs = ensure_sector_buffers(st, 1, partials);
     if (bs != QF_OK) return bs;
     const size_t blk_bytes = rs.blks.size() * sizeof(qf::RunBlk);
     const size_t part_bytes = rs.parts.size() * sizeof(qf::RunPart);
@@ -1694,7 +1772,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     // reverse un-rotates psi
     void* log = nullptr;
     const size_t log_bytes = (size_t)rs.logitems * st->elem();  // one (psi_i0, psi_i1) pair per item
-    if (lreal && rs.log_ok && !st->log_failed && log_bytes <= kLogMaxBytes) {
+    if (need_reverse && lreal && rs.log_ok && !st->log_failed && log_bytes <= kLogMaxBytes) {
       if (ensure_buf(&st->d_log, &st->log_cap, log_bytes, "sector log") == QF_OK)
         log = st->d_log;
       else
@@ -1712,16 +1790,41 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_seclarge,
                                    p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
                                    st->stream));
-    QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
-                                   (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, d_strs,
-                                   st->stream));
+    const size_t npool_blk = pp ? pp->blocks.size() : 0;
+    double* d_pool = st->d_out + nblk + 2 + 2 * n_dets;
+    if (pp) {  // every pool operator's overlap with the final (psi, lambda): nothing rotated
+      const SectorRuns& pr = pp->runs;
+      const size_t pblk = pr.blks.size() * sizeof(qf::RunBlk), ppart = pr.parts.size() * sizeof(qf::RunPart);
+      const void* pbefore = st->d_poolblk;
+      bs = ensure_buf(&st->d_poolblk, &st->poolblk_cap, pblk + ppart + pr.strs.size() * sizeof(uint16_t),
+                      "pool run descriptors");
+      if (bs != QF_OK) return bs;
+      const uint64_t key = content_key(nullptr, 0, (uint64_t)(uintptr_t)pp ^ ((uint64_t)na << 40) ^
+                                                       ((uint64_t)nbeta << 48) ^ cap) | 1ull;
+      if (st->pool_key != key || st->d_poolblk != pbefore) {  // zero angle: the descriptors never change
+        char* base = static_cast<char*>(st->d_poolblk);
+        QF_CUDA(h2d(base, pr.blks.data(), pblk, st->stream));
+        QF_CUDA(h2d(base + pblk, pr.parts.data(), ppart, st->stream));
+        if (!pr.strs.empty()) QF_CUDA(h2d(base + pblk + ppart, pr.strs.data(), pr.strs.size() * 2, st->stream));
+        st->pool_key = key;
+      }
+      const char* base = static_cast<const char*>(st->d_poolblk);
+      QF_CUDA(qf::launch_sector_overlaps(
+          cpsi, st->dt, pr.runs.data(), (int)pr.runs.size(), reinterpret_cast<const qf::RunPart*>(base + pblk),
+          reinterpret_cast<const qf::RunBlk*>(base) + npool_blk, (int)npool_blk, st->d_sec_partial, pr.pmax, d_pool,
+          cm, pr.strs.empty() ? nullptr : reinterpret_cast<const uint16_t*>(base + pblk + ppart), st->stream));
+    }
+    if (need_reverse)
+      QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
+                                     (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, d_strs,
+                                     st->stream));
     if (n_dets) {  // residuals: lambda after the reverse sweep is U^dagger H psi
       std::vector<int64_t> idx(n_dets);
       for (size_t k = 0; k < n_dets; ++k) idx[k] = (int64_t)compact_of(dets[k], sp);
       QF_CUDA(gather_residuals(st, lreal ? cpsi : clam, lreal, idx, st->d_out + nblk + 2));
     }
     QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
-    QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2 + 2 * n_dets) * sizeof(double), st->stream));
+    QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2 + 2 * n_dets + npool_blk) * sizeof(double), st->stream));
     QF_CUDA(cudaStreamSynchronize(st->stream));
     double nrm = st->h_out[nblk + 1];
     if (!(nrm > 0.0)) nrm = 1.0;
@@ -1732,6 +1835,15 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     }
     const double rs_scale = 1.0 / std::sqrt(nrm);  // residuals scale with |psi|
     for (size_t k = 0; k < 2 * n_dets; ++k) res[k] = st->h_out[nblk + 2 + k] * rs_scale;
+    if (pp) {
+      for (size_t k = 0; k < n_pool; ++k) pool_grad[k] = 0.0;
+      for (size_t bi = 0; bi < npool_blk; ++bi)
+        pool_grad[pool[pp->blocks[bi].i].param] += 2.0 * st->h_out[nblk + 2 + 2 * n_dets + bi] / nrm;
+    }
+    return QF_OK;
+  }
+  if (want_pool) {  // the general path takes no pool
+    *pool_fallback = true;
     return QF_OK;
   }
   qf_status ls = ensure_lam(st);
@@ -1835,6 +1947,31 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
                          size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad) {
   if (n_par && !grad) return fail(QF_EINVAL, "NULL array");
   return energy_grad_impl(st, det, ansatz, n_rot, t, n_par, terms, n_terms, energy, grad, nullptr, 0, nullptr);
+}
+
+qf_status qf_pool_gradients(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                            size_t n_par, const qf_term* terms, size_t n_terms, const qf_arot* pool, size_t n_pool_rot,
+                            size_t n_pool, double* energy, double* pool_grad) {
+  bool fallback = false;
+  qf_status s = energy_grad_impl(st, det, ansatz, n_rot, t, n_par, terms, n_terms, energy, nullptr, nullptr, 0,
+                                 nullptr, pool, n_pool_rot, n_pool, pool_grad, &fallback);
+  if (s != QF_OK || !fallback) return s;
+  // general route: the pool appended to the ansatz at zero angle, whose gradient
+  // with respect to the appended parameters is the pool gradient
+  if (n_pool && !pool_grad) return fail(QF_EINVAL, "NULL array");
+  std::vector<qf_arot> all(ansatz, ansatz + n_rot);
+  for (size_t k = 0; k < n_pool_rot; ++k) {
+    qf_arot a = pool[k];
+    a.param += (int32_t)n_par;
+    all.push_back(a);
+  }
+  std::vector<double> tt(t, t + n_par), g(n_par + n_pool);
+  tt.resize(n_par + n_pool, 0.0);
+  s = energy_grad_impl(st, det, all.data(), all.size(), tt.data(), n_par + n_pool, terms, n_terms, energy, g.data(),
+                       nullptr, 0, nullptr);
+  if (s != QF_OK) return s;
+  for (size_t k = 0; k < n_pool; ++k) pool_grad[k] = g[n_par + k];
+  return QF_OK;
 }
 
 qf_status qf_residuals(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,

@@ -288,6 +288,12 @@ cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
                                int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
                                cudaStream_t s);
+// Overlaps only: out[b] = Im <lam|Q_b|psi> of every block b on the same compact
+// state (psi real parts, lam real parts in psi's imaginary slots); nothing is
+// rotated.  Same descriptors as launch_sector_runs.
+cudaError_t launch_sector_overlaps(void* psi, qf_dtype dt, const RunInfo* runs, int nruns, const RunPart* parts,
+                                  const RunBlk* blks, int nblk, double* partial, int pmax, double* out,
+                                  const SecCompact& cm, const uint16_t* strs, cudaStream_t s);
 // Largest part (members) launch_sector_runs accepts for this dtype, direction and log use.
 uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged);
 // With cm.ra != NULL psi and lam are in the compact layout.  nblocks: the

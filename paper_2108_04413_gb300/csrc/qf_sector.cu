@@ -254,7 +254,8 @@ static_assert(sizeof(RunBlk) % 4 == 0 && kRunBlkWords <= kRunThreads, "run descr
 // compact index.
 template <int MODE, typename T>
 __host__ __device__ constexpr size_t run_member_bytes() {
-  return (MODE == 0 || MODE == 3 ? sizeof(T) : MODE == 1 ? 2 * sizeof(T) : 4 * sizeof(T)) + sizeof(uint32_t);
+  return (MODE == 0 || MODE == 3 ? sizeof(T) : (MODE == 1 || MODE == 4) ? 2 * sizeof(T) : 4 * sizeof(T)) +
+         sizeof(uint32_t);
 }
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -265,6 +266,8 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t
 // MODE 2: reverse, psi and lam complex.
 // MODE 3: reverse, lam real (psi's imaginary slots); psi after each block is
 // read back from the forward log instead of being un-rotated.
+// MODE 4: overlaps only, psi and lam real and packed: every block's overlap on
+// the same (psi, lam), nothing rotated or written back (operator-pool gradients).
 template <int MODE, typename T>
 __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
                                                              RunInfo run, const RunPart* __restrict__ parts,
@@ -392,6 +395,11 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
           acc = fma(B.q[cls][0][1], t01, acc);
           ar[i0] = fma(a00, w0, fma(a01, w1, w0));
           ar[i1] = fma(a10, w0, fma(a11, w1, w1));
+        } else if (MODE == 4) {
+          const V p0 = av[i0], p1 = av[i1];  // (psi, lambda)
+          const double t01 = (sizeof(T) == 4) ? (double)fmaf((float)p0.y, (float)p1.x, -(float)p1.y * (float)p0.x)
+                                              : fma((double)p0.y, (double)p1.x, -(double)p1.y * (double)p0.x);
+          acc = fma(B.q[cls][0][1], t01, acc);
         } else if (MODE == 1) {
           const V p0 = av[i0], p1 = av[i1];  // (psi, lambda)
           // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
@@ -440,6 +448,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       partial[(size_t)blk_of(s) * pmax + blockIdx.x] = v;
     }
   }
+  if (MODE == 4) return;  // read only
   T* pw = reinterpret_cast<T*>(psi);
   for (uint32_t m = tid; m < size; m += kRunThreads) {
     const uint32_t g = gi[m];
@@ -840,6 +849,24 @@ cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool
       : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
                   : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s);
   if (e == cudaSuccess && adj) {
+    k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
+    e = cudaGetLastError();
+    count_launch();
+  }
+  prof_post(prof_slot_, s);
+  return e;
+}
+
+cudaError_t launch_sector_overlaps(void* psi, qf_dtype dt, const RunInfo* runs, int nruns, const RunPart* parts,
+                                  const RunBlk* blks, int nblk, double* partial, int pmax, double* out,
+                                  const SecCompact& cm, const uint16_t* strs, cudaStream_t s) {
+  if (nblk <= 0 || nruns <= 0) return cudaSuccess;
+  if (!cm.ra) return cudaErrorInvalidValue;
+  const int prof_slot_ = prof_pre(QF_K_ADJ_SPARSE, s);
+  cudaError_t e = (dt == QF_C128)
+                      ? runs_t<4, double>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, s)
+                      : runs_t<4, float>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, s);
+  if (e == cudaSuccess) {
     k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
     count_launch();

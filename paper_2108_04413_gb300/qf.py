@@ -39,6 +39,7 @@ _SIGS = {
     "qf_expectation": (ctypes.c_int, [_vp, _vp, _sz, _dp, _dp]),
     "qf_energy_grad": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _dp, _vp]),
     "qf_residuals": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _dp, _vp, _vp]),
+    "qf_pool_gradients": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _sz, _dp, _vp]),
     "qf_state_copy_to_host": (ctypes.c_int, [_vp, _vp, _sz]),
     "qf_state_copy_from_host": (ctypes.c_int, [_vp, _vp, _sz]),
     "qf_state_fold_scale": (ctypes.c_int, [_vp]),
@@ -212,6 +213,19 @@ class State:
                                  _ptr(g) if grad else None, _ptr(res)))
         r = res[0::2] + 1j * res[1::2]
         return (e.value, r, g) if grad else (e.value, r)
+
+    def pool_gradients(self, det: int, ansatz: np.ndarray, t, terms: np.ndarray, pool: np.ndarray, n_pool: int):
+        """Gradients of a pool of operators at U(t)|det> (ADAPT, Eq. 21); pool is an
+        ansatz-style rotation list whose params index the n_pool operators."""
+        ansatz = np.ascontiguousarray(ansatz, dtype=AROT_DTYPE)
+        terms = np.ascontiguousarray(terms, dtype=TERM_DTYPE)
+        pool = np.ascontiguousarray(pool, dtype=AROT_DTYPE)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        g = np.zeros(int(n_pool), dtype=np.float64)
+        e = _d()
+        _check(_lib.qf_pool_gradients(self._h, int(det), _ptr(ansatz), len(ansatz), _ptr(t), len(t), _ptr(terms),
+                                      len(terms), _ptr(pool), len(pool), int(n_pool), ctypes.byref(e), _ptr(g)))
+        return e.value, g
 
     def set_hpsi_mode(self, mode: int):
         _check(_lib.qf_state_set_hpsi_mode(self._h, int(mode)))

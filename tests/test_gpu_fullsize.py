@@ -145,3 +145,16 @@ def test_ucc24_residuals_at_reference_are_half_the_gradient(ucc24):
     e1, r1 = st.residuals(det, A, t, T, idx)
     assert abs(e1 - st.energy_grad(det, A, t, T)[0]) < 1e-12
     assert np.isfinite(r1).all()
+
+
+def test_ucc24_pool_gradients_of_the_ansatz_at_reference_equal_the_gradient(ucc24):
+    """With the ansatz's own operators as the pool and t = 0 the pool gradients are
+    the energy gradient (both are <Phi_0|[H, kappa_mu]|Phi_0>), for all 1818."""
+    cfg, h, g, T, A, exs, t = ucc24
+    det = (1 << cfg["n_el"]) - 1
+    t0 = np.zeros(len(exs))
+    st = qf.State(cfg["n_qubits"], "c128")
+    e, gp = st.pool_gradients(det, A, t0, T, A, len(exs))
+    e2, grad = st.energy_grad(det, A, t0, T)
+    assert abs(e - e2) < 1e-12
+    assert np.abs(gp - grad).max() < 1e-10

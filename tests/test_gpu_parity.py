@@ -455,3 +455,49 @@ def test_residuals_invalid_determinant_rejected():
     st = qf.State(cfg["n_qubits"], "c128")
     with pytest.raises(qf.QFError):
         st.residuals(15, A, t, T, np.array([1 << cfg["n_qubits"]], dtype=np.uint64))
+
+
+@pytest.mark.parametrize("cfg_id,dtype", [(0, "c128"), (1, "c128"), (0, "c64"), (1, "c64")])
+def test_pool_gradients_match_oracle(cfg_id, dtype):
+    """ADAPT pool gradients (Eq. 21) of every spin-conserving single and double
+    excitation at the dUCCSD state: the overlap pass on the compact sector path,
+    against the oracle's fermionic commutator route."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(cfg_id)
+    det = (1 << cfg["n_el"]) - 1
+    pool = A.copy()
+    pool["param"] = len(exs) - 1 - A["param"]  # operators numbered in reverse
+    st = qf.State(cfg["n_qubits"], dtype)
+    e, gp = st.pool_gradients(det, A, t, T, pool, len(exs))
+    e_ref, g_ref = fermion.adapt_gradients(cfg["n_orb"], cfg["n_el"], h, g, t, exs, exs[::-1])
+    if dtype == "c128":
+        assert abs(e - e_ref) < TOL_E_C128
+        assert np.abs(gp - g_ref).max() < 1e-10
+    else:
+        assert abs(e - e_ref) < TOL_E_C64
+        assert np.linalg.norm(gp - g_ref) <= TOL_G_C64 * np.linalg.norm(g_ref)
+    # a second call reuses the pool plan
+    e2, gp2 = st.pool_gradients(det, A, 1.5 * t, T, pool, len(exs))
+    e_ref2, g_ref2 = fermion.adapt_gradients(cfg["n_orb"], cfg["n_el"], h, g, 1.5 * t, exs, exs[::-1])
+    tol = 1e-10 if dtype == "c128" else TOL_G_C64 * np.linalg.norm(g_ref2)
+    assert np.abs(gp2 - g_ref2).max() < tol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_pool_gradients_general_route_match_oracle(dtype):
+    """A pool of arbitrary Pauli rotations (not sector blocks) and a Hamiltonian
+    with odd-Y terms go through the appended-at-zero route; against the Pauli oracle."""
+    n = 8
+    rng = np.random.default_rng(41)
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    det = (1 << cfg["n_el"]) - 1
+    pool = qf.as_arots(rng.integers(1, 256, 12), rng.integers(0, 256, 12), rng.normal(size=12), rng.integers(0, 5, 12))
+    arots = list(zip(A["x"], A["z"], A["coeff"], A["param"]))
+    pr = list(zip(pool["x"], pool["z"], pool["coeff"], pool["param"]))
+    Tr = qf.as_terms(rng.integers(0, 256, 40), rng.integers(0, 256, 40), rng.normal(size=40))
+    tol = 1e-10 if dtype == "c128" else 1e-5
+    st = qf.State(n, dtype)
+    for TT in (T, Tr):
+        e, gp = st.pool_gradients(det, A, t, TT, pool, 5)
+        e_ref, g_ref = pauli.pool_gradients(n, det, arots, t, _terms_list(TT), pr, 5)
+        assert abs(e - e_ref) < tol
+        assert np.abs(gp - g_ref).max() < (tol if dtype == "c128" else 1e-4 * max(1.0, np.abs(g_ref).max()))
