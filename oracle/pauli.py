@@ -179,6 +179,15 @@ def pool_gradients(n: int, det: int, arots, t, terms, pool, n_pool: int):
     return np.vdot(psi, lam).real, g
 
 
+def trotter(psi: np.ndarray, n: int, terms, time: float, steps: int) -> np.ndarray:
+    """Trotterized time evolution (Eq. 39): (prod_l exp(-i time c_l P_l / r))^r psi
+    with r = steps, the terms applied in list order within each step."""
+    for _ in range(steps):
+        for (x, z, c) in terms:
+            psi = rotate(psi, n, int(x), int(z), c * time / steps)
+    return psi
+
+
 def fd_gradient(n: int, det: int, arots, t, terms, params, h: float = 1e-4):
     """Central finite differences of E(t) for the listed parameter indices."""
     t = np.asarray(t, dtype=float)

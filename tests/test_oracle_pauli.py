@@ -178,3 +178,37 @@ def test_pool_gradients_match_finite_differences_of_the_appended_block():
             tt = np.r_[t, s]
             fd.append(pauli.energy(n, det, ext, tt, terms))
         assert abs((fd[0] - fd[1]) / 2e-5 - g[p]) < 1e-8
+
+
+def test_trotter_exact_for_commuting_terms():
+    """Diagonal (Z-only) terms commute, so the Trotter product (Eq. 39) equals
+    exp(-i t H) for every step count."""
+    n = 4
+    rng = np.random.default_rng(39)
+    terms = [(0, int(z), float(rng.normal())) for z in rng.integers(0, 16, 8)]
+    psi = rng.normal(size=16) + 1j * rng.normal(size=16)
+    psi /= np.linalg.norm(psi)
+    exact = sl.expm(-1j * 0.7 * pauli.dense_sum(n, terms)) @ psi
+    for r in (1, 3):
+        np.testing.assert_allclose(pauli.trotter(psi, n, terms, 0.7, r), exact, atol=1e-12)
+
+
+def test_trotter_first_order_error_bound_and_rate():
+    """Non-commuting terms: the first-order product error stays within
+    (t^2 / 2r) sum_{j<k} ||[h_j P_j, h_k P_k]|| and halves when r doubles."""
+    n = 4
+    rng = np.random.default_rng(40)
+    terms = [(int(rng.integers(0, 16)), int(rng.integers(0, 16)), float(rng.normal())) for _ in range(6)]
+    psi = rng.normal(size=16) + 1j * rng.normal(size=16)
+    psi /= np.linalg.norm(psi)
+    t = 0.3
+    exact = sl.expm(-1j * t * pauli.dense_sum(n, terms)) @ psi
+    mats = [c * pauli.dense(n, x, z) for (x, z, c) in terms]
+    comm = sum(np.linalg.norm(mats[j] @ mats[k] - mats[k] @ mats[j], 2)
+               for j in range(len(mats)) for k in range(j + 1, len(mats)))
+    errs = []
+    for r in (8, 16, 32):
+        err = np.linalg.norm(pauli.trotter(psi, n, terms, t, r) - exact)
+        assert err <= t * t / (2 * r) * comm + 1e-12
+        errs.append(err)
+    assert 0.4 < errs[1] / errs[0] < 0.6 and 0.4 < errs[2] / errs[1] < 0.6
