@@ -416,6 +416,7 @@ def run_gpu(args, rank, world, local, pg):
             out["adapt"] = adapt_leg(w, args, value)
         out["serving"] = serving_leg(args)
         out["sweep28"] = sweep28_leg()
+        out["trotter"] = trotter_leg()
         t_eval, sample = oracle_sample_ucc(w)
         out["cpu_baseline"] = {"value": 1.0 / t_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
                                "sample": sample}
@@ -686,6 +687,39 @@ def adapt_leg(w, args, value128):
     st.close()
     return {"value": v, "unit": f"pool-gradient evals/s ({npool} operators + energy each)",
             "relative_to_energy_grad": v / value128, "max_abs_pool_gradient": float(np.abs(gp).max())}
+
+
+def trotter_leg():
+    """Trotterized time evolution (Eq. 39) of the 24-qubit molecular Hamiltonian
+    (29737 terms, one rotation each per step) from the Hartree-Fock determinant,
+    complex128, one step: rotations * amplitudes / s and the equivalent HBM rate
+    of one read and one write of the state per rotation."""
+    import torch
+
+    from paper_2108_04413_gb300 import prep, qf
+    from workloads import integrals
+
+    n_orb, n_el = 12, 12
+    n = 2 * n_orb
+    h, g = integrals(n_orb, 2)
+    T = prep.molecular_hamiltonian(h, g)
+    stream = torch.cuda.Stream()
+    st = qf.State(n, "c128", stream=stream)
+    st.set_basis((1 << n_el) - 1)
+    st.trotter(T, 0.05, 1)  # warm-up (plans)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st.trotter(T, 0.05, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    norm = float(np.linalg.norm(st.to_numpy()))
+    st.close()
+    ra = len(T) * (1 << n) / (ms / 1e3)
+    return {"qubits": n, "terms": int(len(T)), "steps": 1, "ms_per_step": ms, "rotations_amplitudes_per_s": ra,
+            "unfused_equivalent_gbs": ra * 2 * 16 / 1e9, "norm_after": norm}
 
 
 def run_sweep28(args, rank, world, local, pg, pk):

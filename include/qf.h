@@ -139,6 +139,12 @@ qf_status qf_pool_gradients(qf_state* st, uint64_t det, const qf_arot* ansatz, s
                             size_t n_par, const qf_term* terms, size_t n_terms, const qf_arot* pool, size_t n_pool_rot,
                             size_t n_pool, double* energy, double* pool_grad);
 
+/* Trotterized time evolution (Eq. 39, used by the quantum Krylov methods): apply
+ * (prod_l exp(-i time coeff_l P_l / steps))^steps, the terms in list order
+ * within each step, through the fused rotation path of qf_apply_circuit.
+ * steps < 1 or a non-finite time gives QF_EINVAL. */
+qf_status qf_trotter(qf_state* st, const qf_term* terms, size_t n_terms, double time, int steps);
+
 /* Copy the state to / from host memory (bytes must equal 2^n * size).  The
  * copy to host folds the internal scale into the amplitudes first. */
 qf_status qf_state_copy_to_host(qf_state* st, void* host, size_t bytes);

@@ -1454,6 +1454,27 @@ qf_status qf_apply_circuit(qf_state* st, const qf_rot* rots, size_t n_rot) {
   return apply_rotations(st, r.data(), n_rot);
 }
 
+qf_status qf_trotter(qf_state* st, const qf_term* terms, size_t n_terms, double time, int steps) {
+  if (!st) return fail(QF_EINVAL, "state is NULL");
+  if (steps < 1) return fail(QF_EINVAL, "Trotter step count must be at least 1");
+  if (!std::isfinite(time)) return fail(QF_EINVAL, "time is not finite");
+  if (n_terms == 0) return QF_OK;
+  if (!terms) return fail(QF_EINVAL, "term list is NULL");
+  std::vector<RotIn> r(n_terms);
+  for (size_t k = 0; k < n_terms; ++k) {
+    qf_status v = validate_masks(st, terms[k].x, terms[k].z);
+    if (v != QF_OK) return v;
+    const double th = terms[k].coeff * time / steps;
+    if (!std::isfinite(th)) return fail(QF_EINVAL, "coefficient is not finite");
+    r[k] = RotIn{terms[k].x, terms[k].z, th, 1.0};
+  }
+  for (int s = 0; s < steps; ++s) {
+    qf_status a = apply_rotations(st, r.data(), n_terms);
+    if (a != QF_OK) return a;
+  }
+  return QF_OK;
+}
+
 qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, double* re, double* im) {
   if (!st || !re) return fail(QF_EINVAL, "NULL argument");
   if (n_terms && !terms) return fail(QF_EINVAL, "term list is NULL");

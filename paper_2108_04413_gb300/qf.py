@@ -40,6 +40,7 @@ _SIGS = {
     "qf_energy_grad": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _dp, _vp]),
     "qf_residuals": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _dp, _vp, _vp]),
     "qf_pool_gradients": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _sz, _dp, _vp]),
+    "qf_trotter": (ctypes.c_int, [_vp, _vp, _sz, _d, ctypes.c_int]),
     "qf_state_copy_to_host": (ctypes.c_int, [_vp, _vp, _sz]),
     "qf_state_copy_from_host": (ctypes.c_int, [_vp, _vp, _sz]),
     "qf_state_fold_scale": (ctypes.c_int, [_vp]),
@@ -226,6 +227,11 @@ class State:
         _check(_lib.qf_pool_gradients(self._h, int(det), _ptr(ansatz), len(ansatz), _ptr(t), len(t), _ptr(terms),
                                       len(terms), _ptr(pool), len(pool), int(n_pool), ctypes.byref(e), _ptr(g)))
         return e.value, g
+
+    def trotter(self, terms: np.ndarray, time: float, steps: int):
+        """Trotterized exp(-i time H) with the given number of steps (Eq. 39)."""
+        terms = np.ascontiguousarray(terms, dtype=TERM_DTYPE)
+        _check(_lib.qf_trotter(self._h, _ptr(terms), len(terms), float(time), int(steps)))
 
     def set_hpsi_mode(self, mode: int):
         _check(_lib.qf_state_set_hpsi_mode(self._h, int(mode)))

@@ -501,3 +501,34 @@ def test_pool_gradients_general_route_match_oracle(dtype):
         e_ref, g_ref = pauli.pool_gradients(n, det, arots, t, _terms_list(TT), pr, 5)
         assert abs(e - e_ref) < tol
         assert np.abs(gp - g_ref).max() < (tol if dtype == "c128" else 1e-4 * max(1.0, np.abs(g_ref).max()))
+
+
+@pytest.mark.parametrize("n,dtype", [(10, "c128"), (13, "c128"), (10, "c64")])
+def test_trotter_matches_oracle(n, dtype):
+    """Trotterized time evolution (Eq. 39) of a random Pauli Hamiltonian from a
+    random state, through qf_trotter, against the oracle's product."""
+    rng = np.random.default_rng(100 + n)
+    T = qf.as_terms(rng.integers(0, 1 << n, 120), rng.integers(0, 1 << n, 120), rng.normal(size=120) / 5)
+    psi0 = random_state(n, n)
+    st = qf.State(n, dtype)
+    st.from_numpy(psi0.astype(np.complex128 if dtype == "c128" else np.complex64))
+    st.trotter(T, 0.8, 3)
+    ref = pauli.trotter(psi0, n, _terms_list(T), 0.8, 3)
+    tol = TOL_AMP_C128 if dtype == "c128" else TOL_AMP_C64
+    assert np.abs(st.to_numpy() - ref).max() < tol
+
+
+def test_trotter_molecular_hamiltonian_from_reference():
+    """The molecular Hamiltonian's evolution of the Hartree-Fock determinant (the
+    time-evolved basis states of the quantum Krylov method): against the oracle,
+    and the energy is conserved up to the Trotter error."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    n = cfg["n_qubits"]
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(n, "c128")
+    st.set_basis(det)
+    st.trotter(T, 0.5, 4)
+    ref = pauli.trotter(pauli.basis_state(n, det), n, _terms_list(T), 0.5, 4)
+    assert np.abs(st.to_numpy() - ref).max() < TOL_AMP_C128
+    with pytest.raises(qf.QFError):
+        st.trotter(T, 0.5, 0)
