@@ -132,9 +132,6 @@ struct SecBlk {                 // one two-row excitation block
   int nzc, ne, no, ke, ko;      // outside even/odd positions and electrons to place there
   uint32_t cnt_e, cnt_o;        // C(ne, ke), C(no, ko)
   uint8_t epos[kSecMaxPos], opos[kSecMaxPos];
-  // The same masks in per-spin local form (qubit q -> bit q >> 1 of its parity):
-  // pl[i][0] / pl[i][1] = even / odd bits of pat[i]; zl[j][0] / zl[j][1] likewise for zc[j].
-  uint32_t pl[2][2], zl[2][2];
   double m[kSparseMaxCls][2][2];  // composite minus identity (real), per sign class
   double q[kSparseMaxCls][2][2];  // Qi with generator Q = i Qi (reverse sweep)
 };
