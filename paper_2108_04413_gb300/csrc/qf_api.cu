@@ -1715,12 +1715,13 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     }
     // the pool (its blocks at zero angle) as sector blocks, planned once per handle
     qf_state::AnsatzPlan* pp = nullptr;
+    uint64_t pkey0 = 0;  // the pool's content key
     if (want_pool) {
       if (!lreal) {  // overlaps on the packed (psi, lambda) need a real lambda
         *pool_fallback = true;
         return QF_OK;
       }
-      const uint64_t pkey0 = content_key(pool, n_pool_rot * sizeof(qf_arot), 0x452821E638D01377ull ^ (uint64_t)n);
+      pkey0 = content_key(pool, n_pool_rot * sizeof(qf_arot), 0x452821E638D01377ull ^ (uint64_t)n);
       auto pit = st->ansatz_plans.find(pkey0);
       if (pit == st->ansatz_plans.end()) {
         std::vector<RotIn> rp(n_pool_rot);
@@ -1820,8 +1821,8 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
       bs = ensure_buf(&st->d_poolblk, &st->poolblk_cap, pblk + ppart + pr.strs.size() * sizeof(uint16_t),
                       "pool run descriptors");
       if (bs != QF_OK) return bs;
-      const uint64_t key = content_key(nullptr, 0, (uint64_t)(uintptr_t)pp ^ ((uint64_t)na << 40) ^
-                                                       ((uint64_t)nbeta << 48) ^ cap) | 1ull;
+      const uint64_t key =
+          content_key(nullptr, 0, pkey0 ^ ((uint64_t)na << 40) ^ ((uint64_t)nbeta << 48) ^ cap) | 1ull;
       if (st->pool_key != key || st->d_poolblk != pbefore) {  // zero angle: the descriptors never change
         char* base = static_cast<char*>(st->d_poolblk);
         QF_CUDA(h2d(base, pr.blks.data(), pblk, st->stream));
@@ -2043,6 +2044,7 @@ qf_status qf_state_clear_plans(qf_state* st) {
   for (auto& kv : st->plans) free_plan(kv.second);
   st->plans.clear();
   st->ansatz_plans.clear();
+  st->parts_key = st->pool_key = 0;  // descriptors on the device belong to no plan now
   return QF_OK;
 }
 

@@ -532,3 +532,21 @@ def test_trotter_molecular_hamiltonian_from_reference():
     assert np.abs(st.to_numpy() - ref).max() < TOL_AMP_C128
     with pytest.raises(qf.QFError):
         st.trotter(T, 0.5, 0)
+
+
+def test_pool_gradients_different_pools_across_clear_plans():
+    """Two different pools on one handle, with the plans cleared in between: each
+    call must use its own pool's descriptors (oracle: fermionic commutators)."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], "c128")
+    doubles = [k for k, ex in enumerate(exs) if len(ex[0]) == 2]
+    sub = np.isin(A["param"], doubles)
+    pool2 = A[sub].copy()
+    remap = {p: k for k, p in enumerate(doubles)}
+    pool2["param"] = [remap[int(p)] for p in pool2["param"]]
+    for pool, pexs in ((A, exs), (pool2, [exs[k] for k in doubles])):
+        _, gp = st.pool_gradients(det, A, t, T, pool, len(pexs))
+        _, g_ref = fermion.adapt_gradients(cfg["n_orb"], cfg["n_el"], h, g, t, exs, pexs)
+        assert np.abs(gp - g_ref).max() < 1e-10
+        st.clear_plans()
