@@ -84,8 +84,8 @@ qf_status qf_apply_circuit(qf_state* st, const qf_rot* rots, size_t n_rot);
  * Hermitian-conjugate contributions together).  Synchronises the stream. */
 qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, double* re, double* im);
 
-/* (Calls that run a persistent kernel with grid barriers -- qf_energy_grad and
- * qf_apply_circuit on sector states -- return QF_ETIMEOUT if a barrier wait
+/* (Calls that run a persistent kernel with grid barriers -- qf_apply_circuit
+ * and qf_trotter on sector states -- return QF_ETIMEOUT if a barrier wait
  * exceeds 2 s.) */
 
 /* Energy and gradient of E(t) = <Phi|U(t)^+ H U(t)|Phi> (Eq. 17-18) with
