@@ -619,6 +619,7 @@ def c64_leg(w, args, value128, e128, g128):
         st.energy_grad(w["det"], w["ansatz"], w["t"], w["terms"])
     torch.cuda.synchronize()
     steps = max(2, args.steps)
+    qf.profile_begin(qf.K_ALL)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -627,9 +628,15 @@ def c64_leg(w, args, value128, e128, g128):
     e1.record(stream)
     torch.cuda.synchronize()
     v = steps / (e0.elapsed_time(e1) / 1e3)
+    kernels = {}
+    for kbit, name in qf.KIND_NAMES.items():
+        cnt, kms = qf.profile_read(kbit)
+        if cnt:
+            kernels[name] = {"launches": cnt, "ms_per_step": kms / steps}
+    qf.profile_end()
     st.close()
     return {"value": v, "unit": "evals/s", "speedup_vs_c128": v / value128, "energy_err_vs_c128": abs(e - e128),
-            "grad_rel_err_vs_c128": float(np.linalg.norm(g - g128) / np.linalg.norm(g128))}
+            "grad_rel_err_vs_c128": float(np.linalg.norm(g - g128) / np.linalg.norm(g128)), "kernels": kernels}
 
 
 def pqe_leg(w, args, value128, g128):

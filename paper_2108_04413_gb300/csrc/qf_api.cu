@@ -1089,6 +1089,7 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
           }
         std::memcpy(B.m, S.m, sizeof(B.m));
         std::memcpy(B.q, S.q, sizeof(B.q));
+        qf::runblk_f32(B);
       }
     // forward-log layout: each part's items, block after block, parts in order.
     // Blocks of equal shape (outside counts, pattern electrons) share their count.
@@ -1671,6 +1672,8 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
         qf::RunBlk& F = ap.runs.blks[k];
         qf::RunBlk& I = ap.runs.blks[nblk + k];
         if (!sector_mq(b.fwd, false, F.m, F.q) || !sector_mq(b.inv, true, I.m, I.q)) sec_good = false;
+        qf::runblk_f32(F);
+        qf::runblk_f32(I);
       }
     });
   }

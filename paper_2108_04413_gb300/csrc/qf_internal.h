@@ -171,7 +171,17 @@ struct RunBlk {                     // one excitation block inside its run
   uint32_t lsa, lsb;
   double m[kSparseMaxCls][2][2];    // composite minus identity (real), per sign class
   double q[kSparseMaxCls][2][2];    // Qi with generator Q = i Qi (reverse)
+  float mf[kSparseMaxCls][2][2];    // m rounded to FP32 (complex64 sweeps)
+  float qf[kSparseMaxCls];          // q[c][0][1] rounded to FP32 (complex64 overlaps)
 };
+// Fills a run block's FP32 coefficients from its FP64 ones.
+inline void runblk_f32(RunBlk& B) {
+  for (int c = 0; c < kSparseMaxCls; ++c) {
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) B.mf[c][i][j] = (float)B.m[c][i][j];
+    B.qf[c] = (float)B.q[c][0][1];
+  }
+}
 constexpr uint32_t kNoStrings = 0xFFFFFFFFu;
 constexpr int kRunMaxOrb = 16;      // U orbitals per spin (run-local strings fit 16 bits)
 struct RunPart {                    // one occupation pattern of G

@@ -251,13 +251,27 @@ static_assert(sizeof(RunBlk) % 4 == 0 && kRunBlkWords <= kRunThreads, "run descr
 // Shared-memory bytes per member: psi real parts (forward), (psi, lam) packed
 // real pairs (reverse, real), psi and lam complex (reverse, complex), or lam's
 // real parts (reverse, real, psi read from the forward log); plus the member's
-// compact index.
+// compact index, kept for the scatter (the read-only MODE 4 has none).
 template <int MODE, typename T>
 __host__ __device__ constexpr size_t run_member_bytes() {
   return (MODE == 0 || MODE == 3 ? sizeof(T) : (MODE == 1 || MODE == 4) ? 2 * sizeof(T) : 4 * sizeof(T)) +
-         sizeof(uint32_t);
+         (MODE == 4 ? 0 : sizeof(uint32_t));
 }
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Cs[m][k] = sum of C(m, k') over k' < k: where the size-k group of the subsets
+// of m positions starts in a strings table ordered by size.
+__device__ void fill_binom_prefix(uint32_t (*Cs)[kBinom]) {
+  for (int i = threadIdx.x; i < kBinom * kBinom; i += blockDim.x) {
+    const int m = i / kBinom, k = i % kBinom;
+    uint64_t s = 0, c = 1;  // c = C(m, j), exact in 64-bit for m < 18
+    for (int j = 0; j < k && j <= m; ++j) {
+      s += c;
+      c = c * (uint64_t)(m - j) / (uint64_t)(j + 1);
+    }
+    Cs[m][k] = (uint32_t)s;
+  }
+}
 
 // MODE 0: forward, psi real; with a log, each item's rotated pair (psi_i0,
 // psi_i1) is also written to log[P.logbase + offset of the block + item].
@@ -268,6 +282,8 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t
 // read back from the forward log instead of being un-rotated.
 // MODE 4: overlaps only, psi and lam real and packed: every block's overlap on
 // the same (psi, lam), nothing rotated or written back (operator-pool gradients).
+// Overlaps accumulate in the state's precision (FP64 for complex128, FP32 for
+// complex64); each part's overlap with a block is written to partial in FP64.
 template <int MODE, typename T>
 __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
                                                              RunInfo run, const RunPart* __restrict__ parts,
@@ -276,14 +292,19 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
                                                              const uint16_t* __restrict__ strs) {
   using V = typename SCx<T>::V;
   constexpr bool ADJ = MODE != 0;
+  constexpr bool F32 = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ uint32_t C[kBinom][kBinom];
+  __shared__ uint32_t Cs[kBinom][kBinom];
   __shared__ RunBlk sb[2];
   __shared__ RunInfo R;
   __shared__ RunPart P;
-  __shared__ double ws[2][kRunWarps];  // per-warp overlaps of the current and the previous block
-  const int tid = threadIdx.x;
+  // every thread's overlap with the last two blocks: block s's values are summed
+  // by one warp during block s + 1 and rewritten after block s + 1's barrier
+  __shared__ T red[ADJ ? 2 : 1][kRunThreads];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   fill_binom(C);
+  fill_binom_prefix(Cs);
   if (tid == 0) {
     R = run;
     P = parts[run.part0 + blockIdx.x];
@@ -296,9 +317,10 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   // shared memory: amplitudes, then compact indices
   const uint32_t cap = R.maxsize;
   T* ar = reinterpret_cast<T*>(dsm);   // MODE 0 (psi), MODE 3 (lam)
-  V* av = reinterpret_cast<V*>(dsm);   // MODE 1, 2 (psi)
+  V* av = reinterpret_cast<V*>(dsm);   // MODE 1, 2, 4 (psi)
   V* lv = av + cap;                    // MODE 2 (lam)
-  const size_t amp_bytes = align16((run_member_bytes<MODE, T>() - sizeof(uint32_t)) * cap);
+  constexpr size_t idx_bytes = MODE == 4 ? 0 : sizeof(uint32_t);
+  const size_t amp_bytes = align16((run_member_bytes<MODE, T>() - idx_bytes) * cap);
   uint32_t* gi = reinterpret_cast<uint32_t*>(dsm + amp_bytes);
   const uint32_t size = P.cnta * P.cntb;
   // the real slot each member moves: psi's real part (MODE 0), lam's in psi's imaginary slot (MODE 3)
@@ -309,7 +331,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     const uint32_t sa = unrank_m(ia, R.apos, R.ua, P.ka, C) | P.ga;
     const uint32_t sbm = unrank_m(ib, R.bpos, R.ub, P.kb, C) | P.gb;
     const uint32_t g = (uint32_t)compact_index(cm, sa, sbm);
-    gi[m] = g;
+    if (MODE != 4) gi[m] = g;
     if (MODE == 0 || MODE == 3) {
       ar[m] = __ldcg(pr + 2 * (size_t)g + slot);
     } else {
@@ -334,12 +356,30 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     }
   }
   __syncthreads();
+  // The overlap of block ps with this part: the threads' values in red[ps & 1],
+  // summed by one warp (rotating over the upper warps, which hold items least
+  // often) over the rows of the pw warps that had items, in warp order, then
+  // lane order by a butterfly.  Deterministic.
+  auto reduce_block = [&](int ps, int pw) {
+    if (warp != kRunWarps - 1 - (ps & 3)) return;
+    T v = T(0);
+    if (pw > 0) {
+      const T* rr = red[ps & 1];
+      v = rr[lane];
+      for (int j = 1; j < pw; ++j) v += rr[32 * j + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    if (lane == 0) partial[(size_t)blk_of(ps) * pmax + blockIdx.x] = (double)v;
+  };
+  int pend_w = 0;  // warps with items in the previous block (its overlaps wait in red)
   for (int s = 0; s < nb; ++s) {
     uint32_t nxt = 0;
     if (s + 1 < nb && tid < kRunBlkWords)
       nxt = __ldg(reinterpret_cast<const uint32_t*>(blks + blk_of(s + 1)) + tid);
+    if (ADJ && s > 0) reduce_block(s - 1, pend_w);
     const RunBlk& B = sb[s & 1];
-    double acc = 0.0;
+    T acc = T(0);
     const int ke = P.ka - B.e0, ko = P.kb - B.o0;
     const uint64_t nitems = items_of(B);
     if (MODE == 3) logoff -= nitems;
@@ -352,13 +392,8 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       V* lg = ((MODE == 0 || MODE == 3) && log) ? log + P.logbase + logoff : nullptr;
       // the block's outside strings of sizes ke and ko, when tabulated
       const bool tab = strs && B.lsa != kNoStrings;
-      uint32_t sa0 = 0, sb0 = 0;
-      if (tab) {
-        sa0 = B.lsa;
-        for (int k = 0; k < ke; ++k) sa0 += C[B.ne][k];
-        sb0 = B.lsb;
-        for (int k = 0; k < ko; ++k) sb0 += C[B.no][k];
-      }
+      const uint32_t sa0 = tab ? B.lsa + Cs[B.ne][ke] : 0u;
+      const uint32_t sb0 = tab ? B.lsb + Cs[B.no][ko] : 0u;
       const float inv_co = 1.0f / (float)co;  // items < 2^24: the estimate is off by at most one
       for (uint32_t it = tid; it < items; it += kRunThreads) {
         uint32_t ie = (uint32_t)((float)it * inv_co);
@@ -373,7 +408,14 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
         // ranks of run-local strings: the general colex rank table
         const uint32_t i0 = (uint32_t)__ldg(cm.ra + (la | B.pu[0][0])) * P.cntb + __ldg(cm.ra + (lb | B.pu[0][1]));
         const uint32_t i1 = (uint32_t)__ldg(cm.ra + (la | B.pu[1][0])) * P.cntb + __ldg(cm.ra + (lb | B.pu[1][1]));
-        const T a00 = (T)B.m[cls][0][0], a01 = (T)B.m[cls][0][1], a10 = (T)B.m[cls][1][0], a11 = (T)B.m[cls][1][1];
+        T a00, a01, a10, a11, q01;
+        if constexpr (F32) {
+          a00 = B.mf[cls][0][0], a01 = B.mf[cls][0][1], a10 = B.mf[cls][1][0], a11 = B.mf[cls][1][1];
+          q01 = B.qf[cls];
+        } else {
+          a00 = B.m[cls][0][0], a01 = B.m[cls][0][1], a10 = B.m[cls][1][0], a11 = B.m[cls][1][1];
+          q01 = B.q[cls][0][1];
+        }
         if (MODE == 0) {
           const T v0 = ar[i0], v1 = ar[i1];
           const T o0 = fma(a00, v0, fma(a01, v1, v0)), o1 = fma(a10, v0, fma(a11, v1, v1));
@@ -388,22 +430,17 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
         } else if (MODE == 3) {
           const V pp = __ldcs(lg + it);  // psi on the pair after this block (forward log)
           const T w0 = ar[i0], w1 = ar[i1];
-          // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host); a
-          // complex64 state forms the pair's product in FP32
-          const double t01 = (sizeof(T) == 4) ? (double)fmaf((float)w0, (float)pp.y, -(float)w1 * (float)pp.x)
-                                              : fma((double)w0, (double)pp.y, -(double)w1 * (double)pp.x);
-          acc = fma(B.q[cls][0][1], t01, acc);
+          // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
+          acc = fma(q01, fma(w0, pp.y, -w1 * pp.x), acc);
           ar[i0] = fma(a00, w0, fma(a01, w1, w0));
           ar[i1] = fma(a10, w0, fma(a11, w1, w1));
         } else if (MODE == 4) {
           const V p0 = av[i0], p1 = av[i1];  // (psi, lambda)
-          const double t01 = (sizeof(T) == 4) ? (double)fmaf((float)p0.y, (float)p1.x, -(float)p1.y * (float)p0.x)
-                                              : fma((double)p0.y, (double)p1.x, -(double)p1.y * (double)p0.x);
-          acc = fma(B.q[cls][0][1], t01, acc);
+          acc = fma(q01, fma(p0.y, p1.x, -p1.y * p0.x), acc);
         } else if (MODE == 1) {
           const V p0 = av[i0], p1 = av[i1];  // (psi, lambda)
           // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
-          acc = fma(B.q[cls][0][1], fma((double)p0.y, (double)p1.x, -(double)p1.y * (double)p0.x), acc);
+          acc = fma(q01, fma(p0.y, p1.x, -p1.y * p0.x), acc);
           V o0, o1;
           o0.x = fma(a00, p0.x, fma(a01, p1.x, p0.x));
           o0.y = fma(a00, p0.y, fma(a01, p1.y, p0.y));
@@ -413,9 +450,11 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
           av[i1] = o1;
         } else {
           const V v0 = av[i0], v1 = av[i1], w0 = lv[i0], w1 = lv[i1];
-          const double q00 = B.q[cls][0][0], q01 = B.q[cls][0][1], q10 = B.q[cls][1][0], q11 = B.q[cls][1][1];
-          acc += (double)w0.x * (q00 * v0.x + q01 * v1.x) + (double)w0.y * (q00 * v0.y + q01 * v1.y);
-          acc += (double)w1.x * (q10 * v0.x + q11 * v1.x) + (double)w1.y * (q10 * v0.y + q11 * v1.y);
+          const double q00 = B.q[cls][0][0], q10 = B.q[cls][1][0], q11 = B.q[cls][1][1];
+          const double qq01 = B.q[cls][0][1];
+          double t = (double)w0.x * (q00 * v0.x + qq01 * v1.x) + (double)w0.y * (q00 * v0.y + qq01 * v1.y);
+          t += (double)w1.x * (q10 * v0.x + q11 * v1.x) + (double)w1.y * (q10 * v0.y + q11 * v1.y);
+          acc += (T)t;
           V o0, o1;
           o0.x = fma(a00, w0.x, fma(a01, w1.x, w0.x));
           o0.y = fma(a00, w0.y, fma(a01, w1.y, w0.y));
@@ -434,20 +473,13 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     }
     if (MODE == 0) logoff += nitems;
     if (ADJ) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if ((tid & 31) == 0) ws[s & 1][tid >> 5] = acc;
+      red[s & 1][tid] = acc;
+      pend_w = nitems >= (uint64_t)kRunThreads ? kRunWarps : (int)((nitems + 31) / 32);
     }
     if (s + 1 < nb && tid < kRunBlkWords) reinterpret_cast<uint32_t*>(&sb[(s + 1) & 1])[tid] = nxt;
     __syncthreads();
-    // this part's overlap with block s: its warps' sums in warp order (ws[s & 1] is
-    // rewritten only after the next barrier)
-    if (ADJ && tid == kRunThreads - 1) {
-      double v = 0.0;
-      for (int w = 0; w < kRunWarps; ++w) v += ws[s & 1][w];
-      partial[(size_t)blk_of(s) * pmax + blockIdx.x] = v;
-    }
   }
+  if (ADJ && nb > 0) reduce_block(nb - 1, pend_w);
   if (MODE == 4) return;  // read only
   T* pw = reinterpret_cast<T*>(psi);
   for (uint32_t m = tid; m < size; m += kRunThreads) {
@@ -771,26 +803,34 @@ cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBl
   return e;
 }
 
+// Dynamic shared memory a k_sector_run instantiation may take: the opt-in
+// maximum less its static shared memory (binomial tables, descriptors, overlaps).
+template <int MODE, typename T>
 static size_t run_smem_max() {
   static const int v = [] {  // thread-safe one-time initialisation
     int dev = 0, bytes = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return bytes;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_sector_run<MODE, T>) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return std::max(0, bytes - (int)fa.sharedSizeBytes - 256);
   }();
-  // the kernel's static shared memory (binomials, two descriptors, run, part) and a margin
-  return (size_t)std::max(0, v - 4096);
+  return (size_t)v;
 }
 
 template <int MODE, typename T>
 static size_t run_smem_bytes(uint32_t maxsize) {
-  const size_t amp = align16((run_member_bytes<MODE, T>() - sizeof(uint32_t)) * maxsize);
-  return align16(amp + sizeof(uint32_t) * maxsize);
+  constexpr size_t idx = MODE == 4 ? 0 : sizeof(uint32_t);
+  const size_t amp = align16((run_member_bytes<MODE, T>() - idx) * maxsize);
+  return align16(amp + idx * maxsize);
 }
 
 template <int MODE, typename T>
 static uint32_t run_capacity_t() {
-  const size_t avail = run_smem_max();
+  const size_t avail = run_smem_max<MODE, T>();
   const size_t fixed = 64;
   return avail > fixed ? (uint32_t)((avail - fixed) / run_member_bytes<MODE, T>()) : 0u;
 }
@@ -813,13 +853,13 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
     attr = cudaFuncSetAttribute(k_sector_run<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)run_smem_max());
+                                (int)run_smem_max<MODE, T>());
   });
   if (attr != cudaSuccess) return attr;
   for (int r = 0; r < nruns; ++r) {
     const RunInfo& R = runs[MODE != 0 ? nruns - 1 - r : r];
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
-    if (smem > run_smem_max() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
+    if (smem > run_smem_max<MODE, T>() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
     k_sector_run<MODE, T><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
                                                               blks, partial, pmax, cm, static_cast<V*>(log), strs);
     count_launch();
