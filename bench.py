@@ -119,7 +119,7 @@ def measured_traffic(kernel: str):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path)).get(kernel.replace("k_sector_hpsi", "k_sector_hpsi"))
+    rec = json.load(open(path)).get(kernel)
     if not rec:
         return None
     src = os.path.join(ROOT, rec["source"])

@@ -373,10 +373,22 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     if (lane == 0) partial[(size_t)blk_of(ps) * pmax + blockIdx.x] = (double)v;
   };
   int pend_w = 0;  // warps with items in the previous block (its overlaps wait in red)
+  // MODE 3: the log pair of item tid of the current block, loaded during the
+  // previous block so that its DRAM latency overlaps that block's barrier
+  V pre{};
+  bool pre_ok = false;
   for (int s = 0; s < nb; ++s) {
     uint32_t nxt = 0;
     if (s + 1 < nb && tid < kRunBlkWords)
       nxt = __ldg(reinterpret_cast<const uint32_t*>(blks + blk_of(s + 1)) + tid);
+    int ne1 = 0, no1 = 0, e01 = 0, o01 = 0;  // MODE 3: the next block's item geometry
+    if (MODE == 3 && s + 1 < nb) {
+      const RunBlk* Bn = blks + blk_of(s + 1);
+      ne1 = __ldg(&Bn->ne);
+      no1 = __ldg(&Bn->no);
+      e01 = __ldg(&Bn->e0);
+      o01 = __ldg(&Bn->o0);
+    }
     if (ADJ && s > 0) reduce_block(s - 1, pend_w);
     const RunBlk& B = sb[s & 1];
     T acc = T(0);
@@ -428,7 +440,8 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
             __stcs(lg + it, w);  // streamed: read back once by the reverse sweep
           }
         } else if (MODE == 3) {
-          const V pp = __ldcs(lg + it);  // psi on the pair after this block (forward log)
+          // psi on the pair after this block (forward log)
+          const V pp = (pre_ok && it == (uint32_t)tid) ? pre : __ldcs(lg + it);
           const T w0 = ar[i0], w1 = ar[i1];
           // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
           acc = fma(q01, fma(w0, pp.y, -w1 * pp.x), acc);
@@ -472,6 +485,17 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       }
     }
     if (MODE == 0) logoff += nitems;
+    if (MODE == 3) {  // the next block's log starts its item count before this one's
+      pre_ok = false;
+      const int ke1 = P.ka - e01, ko1 = P.kb - o01;
+      if (log && s + 1 < nb && ke1 >= 0 && ke1 <= ne1 && ko1 >= 0 && ko1 <= no1) {
+        const uint64_t n1 = (uint64_t)C[ne1][ke1] * C[no1][ko1];
+        if ((uint64_t)tid < n1) {
+          pre = __ldcs(log + P.logbase + (logoff - n1) + tid);
+          pre_ok = true;
+        }
+      }
+    }
     if (ADJ) {
       red[s & 1][tid] = acc;
       pend_w = nitems >= (uint64_t)kRunThreads ? kRunWarps : (int)((nitems + 31) / 32);
@@ -530,18 +554,14 @@ __device__ __forceinline__ unsigned real_index(const RealChunk* __restrict__ R, 
 }
 
 // FP32 partial sums of a complex64 state's H|psi>, folded into the FP64 sum
-// every kFoldTerms terms.
-constexpr int kFoldTerms = 32;
+// after each innermost enumeration loop (at most C(17, 2) = 136 terms at 34
+// qubits, 15 to 36 at 24).
 struct F32Acc {
   float s = 0.0f;
-  int k = 0;
-  __device__ __forceinline__ void add(float w, float v, double& lx) {
-    s = fmaf(w, v, s);
-    if (++k == kFoldTerms) {
-      lx += (double)s;
-      s = 0.0f;
-      k = 0;
-    }
+  __device__ __forceinline__ void add(float w, float v) { s = fmaf(w, v, s); }
+  __device__ __forceinline__ void fold(double& lx) {
+    lx += (double)s;
+    s = 0.0f;
   }
 };
 
@@ -558,7 +578,7 @@ __device__ __forceinline__ void sector_term(const typename SCx<T>::V* __restrict
       const RealChunk* R = rch + chunk0;
       const unsigned idx = real_index(R, (uint32_t)b);
       if (sizeof(T) == 4)  // complex64: FP32 products, folded into the FP64 sum
-        fac.add(__ldg(&R->tf[idx]), (float)vt, lx);
+        fac.add(__ldg(&R->tf[idx]), (float)vt);
       else
         lx = fma(__ldg(&R->t[idx]), (double)vt, lx);
     } else {
@@ -627,26 +647,13 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
     const uint32_t i32 = (uint32_t)it;
     const uint32_t ie = i32 / ssp.cnt_o, io = i32 - ie * ssp.cnt_o;
     const uint64_t c = unrank(ie, ssp.epos, ssp.ne, ssp.ke, C) | unrank(io, ssp.opos, ssp.no, ssp.ko, C);
-    // occupied / empty spin orbitals of each parity, as local indices (qubit 2i -> i, 2i+1 -> i)
-    uint8_t oa[kSecMaxPos], va[kSecMaxPos], ob[kSecMaxPos], vb[kSecMaxPos];
-    int noa = 0, nva = 0, nob = 0, nvb = 0;
+    // occupied spin orbitals of each parity as local masks (alpha orbital q is
+    // qubit 2q, beta orbital q is qubit 2q + 1), and the empty ones; the loops
+    // below visit set bits in ascending order, held in registers
     uint32_t la = 0, lb = 0;  // local alpha / beta strings (compact addressing)
-    for (int q = 0; q < ssp.ne; ++q) {
-      if ((c >> ssp.epos[q]) & 1ull) {
-        oa[noa++] = (uint8_t)q;
-        la |= 1u << q;
-      } else {
-        va[nva++] = (uint8_t)q;
-      }
-    }
-    for (int q = 0; q < ssp.no; ++q) {
-      if ((c >> ssp.opos[q]) & 1ull) {
-        ob[nob++] = (uint8_t)q;
-        lb |= 1u << q;
-      } else {
-        vb[nvb++] = (uint8_t)q;
-      }
-    }
+    for (int q = 0; q < ssp.ne; ++q) la |= (uint32_t)((c >> ssp.epos[q]) & 1ull) << q;
+    for (int q = 0; q < ssp.no; ++q) lb |= (uint32_t)((c >> ssp.opos[q]) & 1ull) << q;
+    const uint32_t va = ((1u << ssp.ne) - 1u) & ~la, vb = ((1u << ssp.no) - 1u) & ~lb;
     double lx = 0.0, ly = 0.0, lxs = 0.0;
     F32Acc fac;
     // one connected group: flip x (qubits), xa / xb (local alpha / beta orbitals)
@@ -659,57 +666,97 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
     auto visit = [&](int code, uint64_t x, uint32_t xa, uint32_t xb) {
       if (code >= 0) term(code & 0xFFFFFF, code >> 24, x, xa, xb);
     };
-    // alpha orbital q is qubit 2q, beta orbital q is qubit 2q + 1
     auto qa = [](int q) { return 1ull << (2 * q); };
     auto qb = [](int q) { return 1ull << (2 * q + 1); };
     visit(rk.diag, 0ull, 0u, 0u);
     const int ne = rk.ne, no = rk.no;
     const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
-    for (int x1 = 0; x1 < noa; ++x1)
-      for (int y1 = 0; y1 < nva; ++y1)
-        visit(__ldg(rk.sa + oa[x1] * ne + va[y1]), qa(oa[x1]) | qa(va[y1]), (1u << oa[x1]) | (1u << va[y1]), 0u);
-    for (int x1 = 0; x1 < nob; ++x1)
-      for (int y1 = 0; y1 < nvb; ++y1)
-        visit(__ldg(rk.sb + ob[x1] * no + vb[y1]), qb(ob[x1]) | qb(vb[y1]), 0u, (1u << ob[x1]) | (1u << vb[y1]));
-    for (int x2 = 1; x2 < noa; ++x2)
-      for (int x1 = 0; x1 < x2; ++x1) {
-        const int rij = oa[x1] + oa[x2] * (oa[x2] - 1) / 2;
-        const uint64_t xo = qa(oa[x1]) | qa(oa[x2]);
-        const uint32_t lo = (1u << oa[x1]) | (1u << oa[x2]);
-        for (int y2 = 1; y2 < nva; ++y2)
-          for (int y1 = 0; y1 < y2; ++y1)
-            visit(__ldg(rk.aa + rij * pe + va[y1] + va[y2] * (va[y2] - 1) / 2), xo | qa(va[y1]) | qa(va[y2]),
-                  lo | (1u << va[y1]) | (1u << va[y2]), 0u);
+    // (complex64: fold the FP32 partial sum after every innermost loop)
+    auto fold = [&]() {
+      if (sizeof(T) == 4) fac.fold(lx);
+    };
+    auto low = [](uint32_t m) { return __ffs((int)m) - 1; };  // lowest set bit of m != 0
+    for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
+      const int o = low(m1);
+      for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
+        const int v = low(n1);
+        visit(__ldg(rk.sa + o * ne + v), qa(o) | qa(v), (1u << o) | (1u << v), 0u);
       }
-    for (int x2 = 1; x2 < nob; ++x2)
-      for (int x1 = 0; x1 < x2; ++x1) {
-        const int rij = ob[x1] + ob[x2] * (ob[x2] - 1) / 2;
-        const uint64_t xo = qb(ob[x1]) | qb(ob[x2]);
-        const uint32_t lo = (1u << ob[x1]) | (1u << ob[x2]);
-        for (int y2 = 1; y2 < nvb; ++y2)
-          for (int y1 = 0; y1 < y2; ++y1)
-            visit(__ldg(rk.bb + rij * po + vb[y1] + vb[y2] * (vb[y2] - 1) / 2), xo | qb(vb[y1]) | qb(vb[y2]), 0u,
-                  lo | (1u << vb[y1]) | (1u << vb[y2]));
+      fold();
+    }
+    for (uint32_t m1 = lb; m1; m1 &= m1 - 1) {
+      const int o = low(m1);
+      for (uint32_t n1 = vb; n1; n1 &= n1 - 1) {
+        const int v = low(n1);
+        visit(__ldg(rk.sb + o * no + v), qb(o) | qb(v), 0u, (1u << o) | (1u << v));
       }
-    for (int x1 = 0; x1 < noa; ++x1)
-      for (int y1 = 0; y1 < nva; ++y1) {
-        const int ia = (oa[x1] * ne + va[y1]) * no;
-        const uint64_t xa_q = qa(oa[x1]) | qa(va[y1]);
-        const uint32_t xa_l = (1u << oa[x1]) | (1u << va[y1]);
-        for (int x2 = 0; x2 < nob; ++x2) {
-          const int iab = (ia + ob[x2]) * no;
-          for (int y2 = 0; y2 < nvb; ++y2)
-            visit(__ldg(rk.ab + iab + vb[y2]), xa_q | qb(ob[x2]) | qb(vb[y2]), xa_l, (1u << ob[x2]) | (1u << vb[y2]));
+      fold();
+    }
+    // same-spin doubles: occupied pairs o1 < o2 (by o2, then o1), empty pairs v1 < v2 likewise
+    for (uint32_t m2 = la; m2; m2 &= m2 - 1) {
+      const int o2 = low(m2);
+      for (uint32_t m1 = la & ((1u << o2) - 1u); m1; m1 &= m1 - 1) {
+        const int o1 = low(m1);
+        const int rij = o1 + o2 * (o2 - 1) / 2;
+        const uint64_t xo = qa(o1) | qa(o2);
+        const uint32_t lo = (1u << o1) | (1u << o2);
+        for (uint32_t n2 = va; n2; n2 &= n2 - 1) {
+          const int v2 = low(n2);
+          const int base = rij * pe + v2 * (v2 - 1) / 2;
+          for (uint32_t n1 = va & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
+            const int v1 = low(n1);
+            visit(__ldg(rk.aa + base + v1), xo | qa(v1) | qa(v2), lo | (1u << v1) | (1u << v2), 0u);
+          }
         }
+        fold();
       }
+    }
+    for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
+      const int o2 = low(m2);
+      for (uint32_t m1 = lb & ((1u << o2) - 1u); m1; m1 &= m1 - 1) {
+        const int o1 = low(m1);
+        const int rij = o1 + o2 * (o2 - 1) / 2;
+        const uint64_t xo = qb(o1) | qb(o2);
+        const uint32_t lo = (1u << o1) | (1u << o2);
+        for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
+          const int v2 = low(n2);
+          const int base = rij * po + v2 * (v2 - 1) / 2;
+          for (uint32_t n1 = vb & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
+            const int v1 = low(n1);
+            visit(__ldg(rk.bb + base + v1), xo | qb(v1) | qb(v2), 0u, lo | (1u << v1) | (1u << v2));
+          }
+        }
+        fold();
+      }
+    }
+    // opposite-spin doubles: alpha single (o -> v), then beta single (ob -> vb')
+    for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
+      const int o = low(m1);
+      for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
+        const int v = low(n1);
+        const int ia = (o * ne + v) * no;
+        const uint64_t xa_q = qa(o) | qa(v);
+        const uint32_t xa_l = (1u << o) | (1u << v);
+        for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
+          const int o2 = low(m2);
+          const int iab = (ia + o2) * no;
+          for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
+            const int v2 = low(n2);
+            visit(__ldg(rk.ab + iab + v2), xa_q | qb(o2) | qb(v2), xa_l, (1u << o2) | (1u << v2));
+          }
+        }
+        fold();
+      }
+    }
     // groups flipping more than four qubits: test each
     for (int gi = 0; gi < nlarge; ++gi) {
       const SecGroup G = large[gi];
       if (2 * __popcll(c & G.x & EVEN) != G.xe || 2 * __popcll(c & G.x & ODD) != G.xo) continue;
       term(G.chunk0, G.nchunk, G.x, G.xa, G.xb);
+      fold();
     }
     const uint64_t self = COMPACT ? it : c;
-    lx += (double)fac.s;
+    fold();  // what is left (a member with no flips)
     if (REALST) lx = fma(lxs, rk.inv_fix, lx);
     if (REALST) {  // real parts only: with LAMY the imaginary slots are lambda's
       const double ux = (double)reinterpret_cast<const T*>(psi)[2 * self];
