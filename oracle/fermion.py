@@ -16,6 +16,9 @@
   the first one acting first on the reference.
 * The Jordan-Wigner image is built here by multiplying single-qubit Pauli
   letters (a route independent of the bit-mask algebra used elsewhere).
+* PQE: the residuals of Eq. 23, their three-energy form (Eq. 24-25), and the
+  quasi-Newton iteration of Eq. 26 with Moller-Plesset denominators from the
+  determinant's Fock diagonal; ADAPT operator gradients (Eq. 21).
 """
 from __future__ import annotations
 
@@ -324,6 +327,53 @@ def pqe_residuals_from_energies(n_orb, n_el, h, g, t, exs=None):
         omega = ucc_factor_apply(phi0, n, ex, np.pi / 4)
         out.append(ubar_energy(omega) - 0.5 * e0 - 0.5 * ubar_energy(excited_state(n, n_el, ex)))
     return np.array(out)
+
+
+def orbital_energies(h, g, n_el):
+    """Hartree-Fock orbital energies of the determinant filling spin orbitals
+    0..n_el-1, one per spin orbital P (spatial p = P // 2, spin P % 2): the
+    diagonal Fock element
+        eps_P = h_pp + sum over occupied J of [(pp|jj) - delta_{s_P s_J} (pj|jp)],
+    whose differences form the Moller-Plesset denominators of Eq. 26."""
+    n = 2 * h.shape[0]
+    eps = np.zeros(n)
+    for P in range(n):
+        p = P // 2
+        e = h[p, p]
+        for J in range(n_el):
+            j = J // 2
+            e += g[p, p, j, j]
+            if P % 2 == J % 2:
+                e -= g[p, j, j, p]
+        eps[P] = e
+    return eps
+
+
+def mp_denominators(eps, exs):
+    """Delta_mu = eps_i + eps_j + ... - eps_a - eps_b - ... (Eq. 26)."""
+    return np.array([sum(eps[i] for i in occ) - sum(eps[a] for a in vir) for occ, vir in exs])
+
+
+def pqe_solve(n_orb, n_el, h, g, exs=None, t0=None, tol=1e-10, max_iter=200):
+    """PQE by the quasi-Newton iteration of Eq. 26,
+        t_mu <- t_mu + r_mu(t) / Delta_mu,
+    with the residuals of Eq. 23 (`pqe_residuals`) and the denominators of the
+    Hartree-Fock orbital energies, from t0 (zeros by default) until every
+    |r_mu| < tol.  Returns (t, E, history): history lists (E, max |r|) at each
+    evaluated t, and E and t are those of the last evaluation."""
+    if exs is None:
+        exs = excitations(n_orb, n_el)
+    delta = mp_denominators(orbital_energies(h, g, n_el), exs)
+    t = np.zeros(len(exs)) if t0 is None else np.array(t0, dtype=float)
+    history = []
+    for _ in range(max_iter):
+        e, r = pqe_residuals(n_orb, n_el, h, g, t, exs)
+        r = r.real
+        history.append((e, float(np.abs(r).max())))
+        if history[-1][1] < tol:
+            break
+        t = t + r / delta
+    return t, e, history
 
 
 # ----------------------------------------------------------------------------

@@ -7,6 +7,8 @@
   of the excited determinant's integer value.
 * Random Pauli-exponential circuits and random Hermitian Pauli sums built from
   the seeded draws of `workloads`.
+* The excited determinants of PQE's residuals (Eq. 23) and the Moller-Plesset
+  denominators of its quasi-Newton update (Eq. 26).
 
 Pauli algebra used here: an operator is sum c X^x Z^z ("raw" form, Z applied
 first), with (X^x1 Z^z1)(X^x2 Z^z2) = (-1)^{popc(z1 & x2)} X^{x1^x2} Z^{z1^z2}.
@@ -190,6 +192,31 @@ def excited_determinants(excitations, det: int):
         idx[k] = d
         sgn[k] = s
     return idx, sgn
+
+
+def orbital_energies(h: np.ndarray, g: np.ndarray, det: int) -> np.ndarray:
+    """Diagonal Fock elements of the determinant det, one per spin orbital
+    (qubit 2p is alpha, 2p + 1 beta of spatial orbital p):
+        eps[2p + s] = h_pp + sum over occupied J of (pp|jj) - sum over occupied J
+                      of spin s of (pj|jp).
+    These are the Hartree-Fock orbital energies of the Moller-Plesset
+    denominators in PQE's quasi-Newton update (Eq. 26)."""
+    n_orb = h.shape[0]
+    occ = np.array([q for q in range(2 * n_orb) if (int(det) >> q) & 1], dtype=np.int64)
+    j, sj = occ // 2, occ % 2
+    p = np.arange(n_orb)
+    coulomb = g[p[:, None], p[:, None], j[None, :], j[None, :]].sum(axis=1)
+    exch = g[p[:, None], j[None, :], j[None, :], p[:, None]]
+    eps = np.empty(2 * n_orb)
+    for s in (0, 1):
+        eps[s::2] = np.diag(h) + coulomb - exch[:, sj == s].sum(axis=1)
+    return eps
+
+
+def mp_denominators(excitations, eps: np.ndarray) -> np.ndarray:
+    """Moller-Plesset denominators Delta_mu = (sum of eps over the excitation's
+    occupied spin orbitals) - (sum over its virtual ones), Eq. 26."""
+    return np.array([float(np.sum(eps[list(occ)]) - np.sum(eps[list(vir)])) for occ, vir in excitations])
 
 
 def bind_thetas(ansatz: np.ndarray, t) -> np.ndarray:

@@ -457,6 +457,31 @@ def test_residuals_invalid_determinant_rejected():
         st.residuals(15, A, t, T, np.array([1 << cfg["n_qubits"]], dtype=np.uint64))
 
 
+@pytest.mark.parametrize("dtype,tol,etol", [("c128", 1e-10, 1e-10), ("c64", 1e-5, 5e-5)])
+def test_pqe_solve_matches_oracle(dtype, tol, etol):
+    """PQE's quasi-Newton iteration (Eq. 26), each step one qf_residuals call,
+    reaches the oracle iteration's fixed point (8 qubits, orbitals ordered so
+    that the denominators are negative).  complex64 stops at max |r| < 1e-5; its
+    energy then carries that convergence error on top of its rounding."""
+    from paper_2108_04413_gb300 import pqe
+
+    n_orb, ne = 4, 4
+    h, g = integrals(n_orb, 0)
+    o = np.argsort(np.diag(h))
+    h, g = h[np.ix_(o, o)], g[np.ix_(o, o, o, o)]
+    A, exs = prep.uccsd_ansatz(n_orb, ne)
+    T = prep.molecular_hamiltonian(h, g)
+    det = (1 << ne) - 1
+    delta = prep.mp_denominators(exs, prep.orbital_energies(h, g, det))
+    st = qf.State(2 * n_orb, dtype)
+    res = pqe.solve(st, det, A, exs, T, delta, tol=tol, max_iter=200)
+    t_o, e_o, hist_o = fermion.pqe_solve(n_orb, ne, h, g, tol=1e-10)
+    assert res.converged and hist_o[-1][1] < 1e-10
+    assert abs(res.energy - e_o) < etol
+    if dtype == "c128":
+        np.testing.assert_allclose(res.t, t_o, rtol=0, atol=1e-8)
+
+
 @pytest.mark.parametrize("cfg_id,dtype", [(0, "c128"), (1, "c128"), (0, "c64"), (1, "c64")])
 def test_pool_gradients_match_oracle(cfg_id, dtype):
     """ADAPT pool gradients (Eq. 21) of every spin-conserving single and double

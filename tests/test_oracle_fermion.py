@@ -292,3 +292,73 @@ def test_adapt_gradients_dense_commutator_and_pauli_route():
     _, g0 = fermion.adapt_gradients(n_orb, ne, h, g, np.zeros(len(exs)), exs, exs)
     _, gref = fermion.ucc_gradient_adjoint(n_orb, ne, h, g, np.zeros(len(exs)), exs)
     np.testing.assert_allclose(g0, gref, atol=1e-12)
+
+
+def _gapped_integrals(n_orb, seed):
+    """Seeded integrals with the orbitals relabelled by ascending h_pp, so that
+    the determinant's occupied orbitals lie lowest (negative Moller-Plesset
+    denominators, as for a Hartree-Fock reference)."""
+    h, g = integrals(n_orb, seed)
+    o = np.argsort(np.diag(h))
+    return h[np.ix_(o, o)], g[np.ix_(o, o, o, o)]
+
+
+def _sector_ground_energy(H, n_orb, ne):
+    b = np.arange(1 << (2 * n_orb))
+    na = np.array([bin(v & int("01" * n_orb, 2)).count("1") for v in b])
+    nb = np.array([bin(v & int("10" * n_orb, 2)).count("1") for v in b])
+    sec = np.flatnonzero((na == (ne + 1) // 2) & (nb == ne // 2))
+    return np.linalg.eigvalsh(H[np.ix_(sec, sec)].real)[0]
+
+
+def test_orbital_energies_koopmans():
+    """The orbital energies of Eq. 26 against determinant energies of the dense
+    fermionic Hamiltonian (frozen orbitals): taking occupied spin orbital i out
+    of Phi_0 changes <Phi|H|Phi> by -eps_i, putting virtual a in changes it by
+    +eps_a."""
+    n_orb, ne = 4, 4
+    h, g = integrals(n_orb, 0)
+    H = fermion.hamiltonian_dense(n_orb, h, g)
+    d0 = fermion.hf_det(ne)
+    eps = fermion.orbital_energies(h, g, ne)
+    for q in range(2 * n_orb):
+        d = d0 ^ (1 << q)
+        want = -eps[q] if q < ne else eps[q]
+        assert abs((H[d, d] - H[d0, d0]).real - want) < 1e-12
+
+
+def test_pqe_solve_two_electrons_reaches_the_exact_ground_state():
+    """Two electrons: the singles and doubles span the whole sector, so at the
+    fixed point of Eq. 26 (every residual of Eq. 23 zero) U Phi_0 is an
+    eigenvector of H, here the lowest of the two-electron S_z = 0 block."""
+    n_orb, ne = 3, 2
+    h, g = _gapped_integrals(n_orb, 5)
+    t, e, hist = fermion.pqe_solve(n_orb, ne, h, g, tol=1e-11)
+    assert hist[-1][1] < 1e-11 and hist[-1][1] < hist[0][1]
+    H = fermion.hamiltonian_dense(n_orb, h, g)
+    assert abs(e - _sector_ground_energy(H, n_orb, ne)) < 1e-10
+
+
+def test_pqe_solve_four_electrons_converges_above_the_ground_state():
+    """Four electrons: the iteration converges (every |r_mu| < 1e-10) to a state
+    whose energy, an expectation value, lies at or above the sector's lowest
+    eigenvalue, and close to it (dUCCSD)."""
+    n_orb, ne = 4, 4
+    h, g = _gapped_integrals(n_orb, 0)
+    t, e, hist = fermion.pqe_solve(n_orb, ne, h, g, tol=1e-10)
+    assert hist[-1][1] < 1e-10
+    efci = _sector_ground_energy(fermion.hamiltonian_dense(n_orb, h, g), n_orb, ne)
+    assert efci - 1e-12 <= e < efci + 1e-6
+
+
+@pytest.mark.parametrize("n_orb,ne,seed", [(4, 4, 0), (5, 6, 3), (4, 3, 7)])
+def test_prep_orbital_energies_and_denominators_match_oracle(n_orb, ne, seed):
+    """Host prep's orbital energies (vectorised) and denominators against the oracle's."""
+    from paper_2108_04413_gb300 import prep
+
+    h, g = integrals(n_orb, seed)
+    eps = prep.orbital_energies(h, g, fermion.hf_det(ne))
+    np.testing.assert_allclose(eps, fermion.orbital_energies(h, g, ne), rtol=0, atol=1e-14)
+    exs = fermion.excitations(n_orb, ne)
+    np.testing.assert_allclose(prep.mp_denominators(exs, eps), fermion.mp_denominators(eps, exs), rtol=0,
+                               atol=1e-14)
