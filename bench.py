@@ -14,7 +14,8 @@ exponentials), t ~ N(0, 0.05), complex128.  Each step rewrites the handle's
 Under torchrun each rank evaluates its own copy of the workload (independent
 problems, no collective); the value is the evaluations of all ranks divided by
 the slowest rank's time.  `--impl reference` times the CPU oracle (the
-reference for this build) on a bounded sample of the same workload.
+plain restatement of the paper's definitions that the tests compare against) on
+a bounded sample of the same workload.
 """
 from __future__ import annotations
 
