@@ -1,5 +1,6 @@
 """Pins of the oracle's fermionic pieces: JW (Eq. 15-16), the Hamiltonian (Eq. 1-2),
-dUCC factors (Eq. 19), the PQE identity (Eq. 25) and Tab. 1's CNOT count."""
+dUCC factors (Eq. 19), PQE (Eq. 23-26), ADAPT gradients (Eq. 21) and Tab. 1's
+parameter and CNOT counts."""
 import itertools
 import json
 import os
@@ -119,6 +120,30 @@ def test_tab1_pduccd_cnot_count():
             npar += 1
     assert npar == gold["n_par"]
     assert total == gold["value"]
+
+
+def test_tab1_duccsd_parameter_and_cnot_counts():
+    """Tab. 1: dUCCSD for linear H4 (8 qubits, 4 electrons) has 14 parameters and
+    736 CNOTs.  The chain's orbitals alternate sigma_g / sigma_u, so the
+    totally symmetric excitations are those with an even number of sigma_u
+    orbitals; each JW string of weight w costs 2(w-1) CNOTs (Fig. 4).  Checked
+    for the oracle's strings and for host prep's ansatz."""
+    from paper_2108_04413_gb300 import prep
+
+    gold = GOLD["dUCCSD_H4"]
+    n, ne = gold["n_qubits"], gold["n_el"]
+    irrep = gold["orbital_symmetry"]
+    exs = fermion.excitations(n // 2, ne)
+    keep = [k for k, (occ, vir) in enumerate(exs) if sum(irrep[q // 2] for q in occ + vir) % 2 == 0]
+    assert len(keep) == gold["n_par"]
+    cnot = sum(2 * (bin(int(x) | int(z)).count("1") - 1)
+               for k in keep for x, z, _ in fermion.jw_kappa_rotations(n, exs[k]))
+    assert cnot == gold["n_cnot"]
+    A, exs_p = prep.uccsd_ansatz(n // 2, ne)
+    assert [tuple(map(tuple, e)) for e in exs_p] == [tuple(map(tuple, e)) for e in exs]
+    rows = np.isin(A["param"], keep)
+    w = np.array([bin(int(x) | int(z)).count("1") for x, z in zip(A["x"][rows], A["z"][rows])])
+    assert int(np.sum(2 * (w - 1))) == gold["n_cnot"]
 
 
 @pytest.mark.parametrize("n_orb", [2, 3])
