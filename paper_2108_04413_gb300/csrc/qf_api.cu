@@ -182,7 +182,8 @@ struct qf_state {
   struct Blk {
     size_t i, j;
     bool sparse;
-    qf::SparseArgs fwd, inv;
+    qf::SparseArgs fwd, inv;  // filled by build_sparse (which clears them) when sparse
+    Blk() {}                  // no zeroing: a plan holds thousands of ~16 KB blocks
   };
   struct AnsatzPlan {
     std::vector<Blk> blocks;
@@ -666,6 +667,7 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
   const int D = 1 << u;
   const uint64_t xl = (uint64_t)D - 1;
   std::vector<std::vector<cplx>> Ms(ncls, std::vector<cplx>(D * D)), Qs(ncls, std::vector<cplx>(D * D));
+  std::vector<cplx> pr(D);
   const cplx iu(0, 1);
   for (int c = 0; c < ncls; ++c) {
     std::vector<cplx>& M = Ms[c];
@@ -681,21 +683,24 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
       const uint64_t zin = compress(r[k].z & x);
       const int y = popc(x & r[k].z) & 3;
       const cplx iy = (y == 0) ? cplx(1, 0) : (y == 1) ? cplx(0, 1) : (y == 2) ? cplx(-1, 0) : cplx(0, -1);
-      // P|col> = iy (-1)^{popc(zin & col)} |col ^ xl>, times the class sign.
-      auto pel = [&](int row) {  // coefficient of P in (row, row ^ xl)
-        const int col = row ^ (int)xl;
-        return iy * sig * ((popc(zin & (uint64_t)col) & 1) ? -1.0 : 1.0);
-      };
+      // P|col> = iy (-1)^{popc(zin & col)} |col ^ xl>, times the class sign:
+      // pr[row] is the coefficient of P in (row, row ^ xl)
+      for (int row = 0; row < D; ++row)
+        pr[row] = iy * sig * ((popc(zin & (uint64_t)(row ^ (int)xl)) & 1) ? -1.0 : 1.0);
       const double th = inverse ? -r[k].th : r[k].th;
       const double cs = std::cos(th), sn = std::sin(th);
-      std::vector<cplx> N2(D * D);
-      for (int row = 0; row < D; ++row) {
-        const cplx pr = pel(row);
-        const int prow = row ^ (int)xl;
-        for (int col = 0; col < D; ++col) N2[row * D + col] = cs * M[row * D + col] - iu * sn * pr * M[prow * D + col];
+      // Every rotation of the block pairs row with row ^ xl, so M stays block
+      // diagonal in those pairs: only the 2x2 block of each pair changes.
+      for (int r0 = 0; r0 < D; ++r0) {
+        const int r1 = r0 ^ (int)xl;
+        if (r1 < r0) continue;
+        const cplx m00 = M[r0 * D + r0], m01 = M[r0 * D + r1], m10 = M[r1 * D + r0], m11 = M[r1 * D + r1];
+        M[r0 * D + r0] = cs * m00 - iu * sn * pr[r0] * m10;
+        M[r0 * D + r1] = cs * m01 - iu * sn * pr[r0] * m11;
+        M[r1 * D + r0] = cs * m10 - iu * sn * pr[r1] * m00;
+        M[r1 * D + r1] = cs * m11 - iu * sn * pr[r1] * m01;
       }
-      M.swap(N2);
-      for (int row = 0; row < D; ++row) Q[row * D + (row ^ (int)xl)] += r[k].coeff * pel(row);
+      for (int row = 0; row < D; ++row) Q[row * D + (row ^ (int)xl)] += r[k].coeff * pr[row];
     }
   }
   // For the inverse the product above is R_m(-th_m)...R_1(-th_1); it equals the inverse of the
@@ -708,7 +713,8 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
       for (int col = 0; col < D && !a2; ++col) {
         const cplx d = Ms[c][row * D + col] - ((row == col) ? 1.0 : 0.0);
         const cplx d2 = Ms[c][col * D + row] - ((row == col) ? 1.0 : 0.0);
-        if (std::abs(d) > tol || std::abs(d2) > tol)
+        // (exact zeros, every entry outside the pair blocks, skip the modulus)
+        if ((d != 0.0 && std::abs(d) > tol) || (d2 != 0.0 && std::abs(d2) > tol))
           a2 = true;
         else if (with_gen && (Qs[c][row * D + col] != 0.0 || Qs[c][col * D + row] != 0.0))
           a2 = true;
@@ -1543,8 +1549,12 @@ std::vector<qf_state::Blk> plan_blocks(const RotIn* r, const int32_t* par, size_
   } else {
     work(0, 1);
   }
+  // every run a sparse block (a UCC ansatz): the candidates are the plan (a
+  // block carries two composites of about 8 KB each; copying them dominated)
+  if (std::all_of(ok.begin(), ok.end(), [](char v) { return v != 0; })) return cand;
   // assemble in order; a run that is not a sparse block is walked rotation by rotation
   std::vector<Blk> bl;
+  bl.reserve(runs.size());
   for (size_t k = 0; k < runs.size(); ++k) {
     if (ok[k]) {
       bl.push_back(cand[k]);
