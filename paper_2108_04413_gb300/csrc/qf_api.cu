@@ -291,30 +291,47 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     *out = &it->second;
     return QF_OK;
   }
-  std::map<uint64_t, std::vector<size_t>> byx;
-  for (size_t i = 0; i < nt; ++i) byx[terms[i].x].push_back(i);
+  // terms grouped by X mask: ascending x, each group's terms in input order
+  std::vector<size_t> order(nt);
+  for (size_t i = 0; i < nt; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return terms[a].x < terms[b].x; });
   std::vector<qf::ExpGroup> groups;
   std::vector<qf::ExpChunk> ech, hch;
-  for (auto& kv : byx) {
+  ech.reserve(nt);  // at most one chunk per term: the tables are built in place
+  hch.reserve(nt);
+  // scratch reused across groups
+  std::vector<size_t> idx;
+  std::vector<std::vector<size_t>> parts;
+  std::vector<std::vector<uint32_t>> coords;
+  std::vector<std::vector<uint64_t>> bases;
+  std::vector<uint64_t> B, E;
+  std::vector<uint32_t> Cb, a;
+  std::vector<double> addh, adde;  // a term's exact table addend (real or imaginary part) before its sign
+  std::vector<char> odd;           // the addend is imaginary (odd number of Y)
+  for (size_t q0 = 0; q0 < nt;) {
+    size_t q1 = q0 + 1;
+    while (q1 < nt && terms[order[q1]].x == terms[order[q0]].x) ++q1;
+    idx.assign(order.begin() + q0, order.begin() + q1);
+    q0 = q1;
     qf::ExpGroup g{};
-    g.x = kv.first;
-    g.h = hibit(kv.first);
+    g.x = terms[idx[0]].x;
+    g.h = hibit(g.x);
     g.chunk0 = (int)ech.size();
     g.flags = 0;
-    const std::vector<size_t>& idx = kv.second;
     for (size_t i : idx) g.flags |= (popc(terms[i].x & terms[i].z) & 1) ? 2 : 1;
     // A chunk holds terms whose Z masks are combinations (over GF(2)) of at most
     // kChunkTerms basis masks: the table entry for the basis parities `pat` sums
     // the terms with the sign (-1)^{popc(a_t & pat)}, a_t the term's coordinates.
     // When the whole group spans at most kChunkTerms dimensions it is one chunk;
     // otherwise each chunk takes kChunkTerms terms as its own basis.
-    std::vector<std::vector<size_t>> parts;
-    std::vector<std::vector<uint32_t>> coords;
-    std::vector<std::vector<uint64_t>> bases;
+    parts.clear();
+    coords.clear();
+    bases.clear();
     {
-      std::vector<uint64_t> B, E;  // basis (term masks), echelon copies (pivot = highest bit, descending)
-      std::vector<uint32_t> Cb;    // E[i] as a combination of B
-      std::vector<uint32_t> a(idx.size());
+      B.clear();  // basis (term masks)
+      E.clear();  // echelon copies (pivot = highest bit, descending)
+      Cb.clear(); // E[i] as a combination of B
+      a.assign(idx.size(), 0u);
       bool fits = true;
       for (size_t t = 0; t < idx.size() && fits; ++t) {
         uint64_t v = terms[idx[t]].z;
@@ -362,22 +379,40 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     }
     g.nchunk = (int)parts.size();
     for (size_t c = 0; c < parts.size(); ++c) {
-      qf::ExpChunk ce{}, ch{};
+      qf::ExpChunk& ce = ech.emplace_back();
+      qf::ExpChunk& ch = hch.emplace_back();
       for (int t = 0; t < qf::kChunkTerms; ++t) ce.z[t] = ch.z[t] = (t < (int)bases[c].size()) ? bases[c][t] : 0ull;
+      // per term: i^y c (real for even y, imaginary for odd y) and the expectation
+      // weight (1 for x = 0, else 2 for the two pair members; odd y: 2 c (-1)^{(y+1)/2});
+      // each is exact up to the sign the pattern gives it
+      const size_t nterm = parts[c].size();
+      addh.resize(nterm);
+      adde.resize(nterm);
+      odd.resize(nterm);
+      for (size_t t = 0; t < nterm; ++t) {
+        const qf_term& T = terms[parts[c][t]];
+        const int y = popc(T.x & T.z) & 3;
+        odd[t] = (char)(y & 1);
+        if ((y & 1) == 0) {
+          const double ph = (y == 2) ? -1.0 : 1.0;  // i^y
+          addh[t] = T.coeff * ph;
+          adde[t] = (g.x == 0 ? 1.0 : 2.0) * T.coeff * ph;
+        } else {
+          addh[t] = T.coeff * ((y == 3) ? -1.0 : 1.0);           // i^y = +-i
+          adde[t] = 2.0 * T.coeff * ((y == 1) ? -1.0 : 1.0);     // 2 c (-1)^{(y+1)/2}
+        }
+      }
       for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat) {
         double ex = 0, ey = 0, hx = 0, hy = 0;
-        for (size_t t = 0; t < parts[c].size(); ++t) {
-          const qf_term& T = terms[parts[c][t]];
-          const int y = popc(T.x & T.z) & 3;
-          const double sg = (popc(coords[c][t] & (uint32_t)pat) & 1) ? -1.0 : 1.0;
-          const double cf = T.coeff * sg;
-          if ((y & 1) == 0) {
-            const double ph = (y == 2) ? -1.0 : 1.0;  // i^y
-            hx += cf * ph;
-            ex += (g.x == 0 ? 1.0 : 2.0) * cf * ph;
+        for (size_t t = 0; t < nterm; ++t) {
+          const bool neg = popc(coords[c][t] & (uint32_t)pat) & 1;
+          const double h = neg ? -addh[t] : addh[t], e = neg ? -adde[t] : adde[t];
+          if (!odd[t]) {
+            hx += h;
+            ex += e;
           } else {
-            hy += cf * ((y == 3) ? -1.0 : 1.0);        // i^y = +-i
-            ey += 2.0 * cf * ((y == 1) ? -1.0 : 1.0);  // 2 c (-1)^{(y+1)/2}
+            hy += h;
+            ey += e;
           }
         }
         ce.tab[pat] = make_double2(ex, ey);
@@ -385,8 +420,6 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
         ce.ftab[pat] = make_float2((float)ex, (float)ey);
         ch.ftab[pat] = make_float2((float)hx, (float)hy);
       }
-      ech.push_back(ce);
-      hch.push_back(ch);
     }
     groups.push_back(g);
   }
@@ -648,7 +681,12 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
   const uint64_t x = r[0].x;
   const int u = popc(x);
   if (u == 0 || u > qf::kSparseMaxSupp) return false;
-  std::vector<int> supp;
+  // scratch kept per thread (plan_blocks builds thousands of blocks in parallel)
+  thread_local std::vector<int> supp, act;
+  thread_local std::vector<uint64_t> zc;
+  thread_local std::vector<std::vector<cplx>> Ms, Qs;
+  thread_local std::vector<cplx> pr;
+  supp.clear();
   for (int i = 0; i < n; ++i)
     if ((x >> i) & 1) supp.push_back(i);
   auto compress = [&](uint64_t v) {
@@ -657,7 +695,7 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
       if ((v >> supp[i]) & 1) o |= 1ull << i;
     return o;
   };
-  std::vector<uint64_t> zc;
+  zc.clear();
   for (int k = 0; k < m; ++k) {
     const uint64_t zo = r[k].z & ~x;
     if (zo && std::find(zc.begin(), zc.end(), zo) == zc.end()) zc.push_back(zo);
@@ -666,8 +704,15 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
   const int ncls = 1 << zc.size();
   const int D = 1 << u;
   const uint64_t xl = (uint64_t)D - 1;
-  std::vector<std::vector<cplx>> Ms(ncls, std::vector<cplx>(D * D)), Qs(ncls, std::vector<cplx>(D * D));
-  std::vector<cplx> pr(D);
+  if ((int)Ms.size() < ncls) {
+    Ms.resize(ncls);
+    Qs.resize(ncls);
+  }
+  for (int c = 0; c < ncls; ++c) {
+    Ms[c].assign(D * D, cplx(0.0, 0.0));
+    Qs[c].assign(D * D, cplx(0.0, 0.0));
+  }
+  pr.assign(D, cplx(0.0, 0.0));
   const cplx iu(0, 1);
   for (int c = 0; c < ncls; ++c) {
     std::vector<cplx>& M = Ms[c];
@@ -706,7 +751,7 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
   // For the inverse the product above is R_m(-th_m)...R_1(-th_1); it equals the inverse of the
   // forward composite because the block's rotations commute.
   const double tol = 1e-14;
-  std::vector<int> act;
+  act.clear();
   for (int row = 0; row < D; ++row) {
     bool a2 = false;
     for (int c = 0; c < ncls && !a2; ++c)
