@@ -740,10 +740,11 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
         const int r1 = r0 ^ (int)xl;
         if (r1 < r0) continue;
         const cplx m00 = M[r0 * D + r0], m01 = M[r0 * D + r1], m10 = M[r1 * D + r0], m11 = M[r1 * D + r1];
-        M[r0 * D + r0] = cs * m00 - iu * sn * pr[r0] * m10;
-        M[r0 * D + r1] = cs * m01 - iu * sn * pr[r0] * m11;
-        M[r1 * D + r0] = cs * m10 - iu * sn * pr[r1] * m00;
-        M[r1 * D + r1] = cs * m11 - iu * sn * pr[r1] * m01;
+        const cplx f0 = iu * sn * pr[r0], f1 = iu * sn * pr[r1];
+        M[r0 * D + r0] = cs * m00 - f0 * m10;
+        M[r0 * D + r1] = cs * m01 - f0 * m11;
+        M[r1 * D + r0] = cs * m10 - f1 * m00;
+        M[r1 * D + r1] = cs * m11 - f1 * m01;
       }
       for (int row = 0; row < D; ++row) Q[row * D + (row ^ (int)xl)] += r[k].coeff * pr[row];
     }
@@ -866,11 +867,25 @@ void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
   }
 }
 
-uint32_t binom(int m, int k) {
+uint32_t binom_loop(int m, int k) {
   if (k < 0 || k > m) return 0;
   uint64_t c = 1;
   for (int j = 1; j <= k; ++j) c = c * (uint64_t)(m - k + j) / (uint64_t)j;
   return (uint32_t)c;
+}
+
+// C(m, k) as 32 bits; a table (filled once by the same loop) for m < 64
+uint32_t binom(int m, int k) {
+  struct Table {
+    uint32_t v[64][64];
+    Table() {
+      for (int i = 0; i < 64; ++i)
+        for (int j = 0; j < 64; ++j) v[i][j] = binom_loop(i, j);
+    }
+  };
+  static const Table t;  // thread-safe one-time initialisation
+  if (m >= 0 && m < 64 && k >= 0 && k < 64) return t.v[m][k];
+  return binom_loop(m, k);
 }
 
 // The real composite-minus-identity m and, for an inverse block, the real Qi of
