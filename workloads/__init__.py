@@ -98,6 +98,19 @@ def random_state(n_qubits: int, seed: int) -> np.ndarray:
     return v / np.linalg.norm(v)
 
 
+def probe_vectors(count: int, length: int, seed: int) -> np.ndarray:
+    """`count` seeded N(0, 1) vectors of the given length (random projections that
+    compare two long vectors through a few numbers)."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(count, length))
+
+
+def sample_indices(length: int, count: int, seed: int) -> np.ndarray:
+    """`count` distinct seeded indices in [0, length), ascending."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(length, size=min(count, length), replace=False))
+
+
 def poisson_arrivals(rate_per_s: float, count: int, seed: int) -> np.ndarray:
     """Arrival times (seconds from 0) of a Poisson stream."""
     rng = np.random.default_rng(seed)
