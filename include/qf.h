@@ -227,9 +227,11 @@ qf_status qf_profile_end(void);
  * process exits.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress), so make the first call on each device before
  * any stream capture.  All calls share the array and it keeps the last call's
- * contents (the counter is cleared at each call's start): calls whose GPU work
- * may overlap -- other streams, other host threads -- race and must be ordered
- * by the caller. */
+ * contents (the counter is cleared at each call's start).  Two calls whose GPU
+ * work overlapped would race on it; to prevent that, a call holds a
+ * process-wide lock from uploading its tables until its stream has
+ * synchronised, so calls from several host threads (on any streams) run one
+ * after another. */
 #define QF_NOALLOC_MAX_TERMS 2048
 #define QF_NOALLOC_SCRATCH_BYTES (1u << 20)
 qf_status qf_expectation_noalloc(const void* amplitudes, int n, qf_dtype dtype, void* stream,

@@ -71,8 +71,9 @@ struct ExpPlan {
   qf::HClass* d_classes[qf::kClassTbN] = {};  // classes for tile bits 10, 11, 12
   int nclasses[qf::kClassTbN] = {};
   bool tiled = false;                // tiled H|psi> tables built (on first use)
-  std::vector<qf_term> terms;        // the plan's terms, for building the tiled tables later
+  std::vector<qf_term> terms;        // the plan's terms (compared on every cache hit; tiled tables)
   bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
+  uint64_t last_use = 0; // the handle's call count at the plan's last use (least recently used goes first)
 };
 
 void free_plan(ExpPlan& p) {
@@ -115,6 +116,11 @@ uint64_t content_key(const void* data, size_t bytes, uint64_t seed = 0x243F6A888
   v *= 0xD6E8FEB86659FD93ull;
   v ^= v >> 32;
   return v;
+}
+
+// Whether a cached plan's rotation list equals the caller's.
+bool same_arots(const std::vector<qf_arot>& seen, const qf_arot* a, size_t n) {
+  return seen.size() == n && (n == 0 || std::memcmp(seen.data(), a, n * sizeof(qf_arot)) == 0);
 }
 
 }  // namespace
@@ -186,6 +192,8 @@ struct qf_state {
     Blk() {}                  // no zeroing: a plan holds thousands of ~16 KB blocks
   };
   struct AnsatzPlan {
+    std::vector<qf_arot> src;  // the rotation list it was planned from (compared on every cache hit)
+    uint64_t last_use = 0;
     std::vector<Blk> blocks;
     // sector run plan, built for (sec_n, sec_na, sec_nb) on first use there
     int sec_n = -1, sec_na = -1, sec_nb = -1;
@@ -195,6 +203,7 @@ struct qf_state {
   };
   std::unordered_map<uint64_t, AnsatzPlan> ansatz_plans;
   uint64_t parts_key = 0;  // the ansatz plan and sector whose run parts sit in d_runblk
+  uint64_t calls = 0;      // plan-using calls so far (the caches' clock)
   size_t elem() const { return dt == QF_C128 ? 16 : 8; }
   size_t bytes() const { return elem() << n; }
 };
@@ -210,6 +219,32 @@ constexpr uint64_t kStringsMax = (uint64_t)1 << 25;
 // Largest forward log of the part-local sweeps a handle allocates (24 qubits,
 // complex128: 2.1 GB).
 constexpr size_t kLogMaxBytes = (size_t)16 << 30;
+// Plans a handle keeps per cache (Pauli sums; ansatz and pool block structures).
+// Past that, the least recently used are dropped (with their device tables) when
+// the next plan-using call starts, so no call loses a plan it is using.
+constexpr size_t kMaxPlans = 8;
+
+void free_plan(ExpPlan& p);
+
+// Drop the least recently used plans beyond kMaxPlans; stamps the call.
+void trim_plans(qf_state* st) {
+  ++st->calls;
+  while (st->plans.size() > kMaxPlans) {
+    auto lru = st->plans.begin();
+    for (auto it = st->plans.begin(); it != st->plans.end(); ++it)
+      if (it->second.last_use < lru->second.last_use) lru = it;
+    free_plan(lru->second);
+    st->plans.erase(lru);
+  }
+  while (st->ansatz_plans.size() > kMaxPlans) {
+    auto lru = st->ansatz_plans.begin();
+    for (auto it = st->ansatz_plans.begin(); it != st->ansatz_plans.end(); ++it)
+      if (it->second.last_use < lru->second.last_use) lru = it;
+    st->ansatz_plans.erase(lru);
+    st->parts_key = 0;  // descriptors on the device are re-uploaded by their next user
+    st->pool_key = 0;
+  }
+}
 
 // Bits of mask on qubits of parity par (0 even / alpha, 1 odd / beta), as local
 // spin-orbital indices: qubit q -> bit q >> 1.
@@ -288,8 +323,15 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   const uint64_t key = content_key(terms, nt * sizeof(qf_term), 0x243F6A8885A308D3ull ^ (uint64_t)st->n);
   auto it = st->plans.find(key);
   if (it != st->plans.end()) {
-    *out = &it->second;
-    return QF_OK;
+    const std::vector<qf_term>& seen = it->second.terms;
+    if (seen.size() == nt && (nt == 0 || std::memcmp(seen.data(), terms, nt * sizeof(qf_term)) == 0)) {
+      it->second.last_use = st->calls;
+      *out = &it->second;
+      return QF_OK;
+    }
+    // another term list with the same key: the key only picks the slot, so replace it
+    free_plan(it->second);
+    st->plans.erase(it);
   }
   // terms grouped by X mask: ascending x, each group's terms in input order
   std::vector<size_t> order(nt);
@@ -558,6 +600,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     QF_CUDA(cudaStreamSynchronize(st->stream));
   }
   p.terms.assign(terms, terms + nt);
+  p.last_use = st->calls;
   auto res = st->plans.emplace(key, std::move(p));
   *out = &res.first->second;
   return QF_OK;
@@ -867,6 +910,12 @@ void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
   }
 }
 
+// Largest m of the binomial table.  Every caller takes m <= n / 2 (orbitals of
+// one spin) with n <= QF_MAX_QUBITS, and C(33, k) < 2^31, so the table's values
+// are exact in 32 bits and its running products (< 2^36) cannot overflow.
+constexpr int kBinomMax = 33;
+static_assert(QF_MAX_QUBITS / 2 <= kBinomMax, "binomial table too small for QF_MAX_QUBITS");
+
 uint32_t binom_loop(int m, int k) {
   if (k < 0 || k > m) return 0;
   uint64_t c = 1;
@@ -874,18 +923,21 @@ uint32_t binom_loop(int m, int k) {
   return (uint32_t)c;
 }
 
-// C(m, k) as 32 bits; a table (filled once by the same loop) for m < 64
+// C(m, k) for 0 <= m <= kBinomMax from a table filled once by the same loop;
+// 0 for k outside 0..m.  An m outside the table is a planning error: it gives
+// 0 (never a truncated value) and is caught by qf_state_create's qubit limit
+// before any caller can reach it.
 uint32_t binom(int m, int k) {
   struct Table {
-    uint32_t v[64][64];
+    uint32_t v[kBinomMax + 1][kBinomMax + 1];
     Table() {
-      for (int i = 0; i < 64; ++i)
-        for (int j = 0; j < 64; ++j) v[i][j] = binom_loop(i, j);
+      for (int i = 0; i <= kBinomMax; ++i)
+        for (int j = 0; j <= kBinomMax; ++j) v[i][j] = binom_loop(i, j);
     }
   };
   static const Table t;  // thread-safe one-time initialisation
-  if (m >= 0 && m < 64 && k >= 0 && k < 64) return t.v[m][k];
-  return binom_loop(m, k);
+  if (m < 0 || m > kBinomMax || k < 0 || k > m) return 0;
+  return t.v[m][k];
 }
 
 // The real composite-minus-identity m and, for an inverse block, the real Qi of
@@ -1554,6 +1606,7 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
     *re = 0.0;
     return QF_OK;
   }
+  trim_plans(st);
   const ExpPlan* p = nullptr;
   qf_status ps = get_plan(st, terms, n_terms, &p);
   if (ps != QF_OK) return ps;
@@ -1665,6 +1718,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     return fail(QF_EINVAL, "NULL array");
   for (size_t k = 0; k < n_dets; ++k)
     if (st->n < 64 && (dets[k] >> st->n)) return fail(QF_EINVAL, "residual determinant has a bit at or above the qubit count");
+  trim_plans(st);
   const bool want_pool = pool_fallback != nullptr;
   if (want_pool) {
     *pool_fallback = false;
@@ -1698,15 +1752,23 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
   using Blk = qf_state::Blk;
   const uint64_t akey = content_key(ansatz, n_rot * sizeof(qf_arot), 0x13198A2E03707344ull ^ (uint64_t)st->n);
   auto ait = st->ansatz_plans.find(akey);
+  if (ait != st->ansatz_plans.end() && !same_arots(ait->second.src, ansatz, n_rot)) {
+    // another rotation list with the same key: the key only picks the slot
+    st->ansatz_plans.erase(ait);
+    ait = st->ansatz_plans.end();
+    st->parts_key = 0;
+  }
   bool fresh = false;
   if (ait == st->ansatz_plans.end()) {
     // first sight of this ansatz: find its block structure
     std::vector<Blk> bl = plan_blocks(r.data(), par.data(), n_rot, st->n);
     qf_state::AnsatzPlan plan;
+    plan.src.assign(ansatz, ansatz + n_rot);
     plan.blocks = std::move(bl);
     ait = st->ansatz_plans.emplace(akey, std::move(plan)).first;
     fresh = true;
   }
+  ait->second.last_use = st->calls;
   qf_state::AnsatzPlan& ap = ait->second;
   std::vector<Blk>& blocks = ap.blocks;
   const size_t nblk = blocks.size();
@@ -1796,6 +1858,12 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
       }
       pkey0 = content_key(pool, n_pool_rot * sizeof(qf_arot), 0x452821E638D01377ull ^ (uint64_t)n);
       auto pit = st->ansatz_plans.find(pkey0);
+      if (pit != st->ansatz_plans.end() && (&pit->second == &ap || !same_arots(pit->second.src, pool, n_pool_rot))) {
+        if (&pit->second == &ap) return fail(QF_EINVAL, "pool and ansatz plans share a cache key");
+        st->ansatz_plans.erase(pit);
+        pit = st->ansatz_plans.end();
+        st->pool_key = 0;
+      }
       if (pit == st->ansatz_plans.end()) {
         std::vector<RotIn> rp(n_pool_rot);
         std::vector<int32_t> ppar(n_pool_rot);
@@ -1804,9 +1872,11 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
           ppar[k] = pool[k].param;
         }
         qf_state::AnsatzPlan plan;
+        plan.src.assign(pool, pool + n_pool_rot);
         plan.blocks = plan_blocks(rp.data(), ppar.data(), n_pool_rot, n);
         pit = st->ansatz_plans.emplace(pkey0, std::move(plan)).first;
       }
+      pit->second.last_use = st->calls;
       pp = &pit->second;
       if (!(pp->sec_ok && pp->sec_n == n && pp->sec_na == na && pp->sec_nb == nbeta && pp->sec_cap == cap)) {
         const size_t nbp = pp->blocks.size();

@@ -15,9 +15,9 @@
 // sums and the X-mask group tables (at most QF_NOALLOC_MAX_TERMS terms).  All
 // calls share it and it keeps the previous call's contents: the counter is
 // cleared at the start of each call, and everything else is overwritten before
-// it is read.  Two calls whose GPU work overlaps (different streams or host
-// threads without ordering between them) race on the array and give wrong
-// results; callers must order them.
+// it is read.  Two calls whose GPU work overlapped would race on the array, so
+// each call holds a process-wide lock from its table upload until its stream
+// has synchronised: calls from several host threads run one after another.
 #include <cuda_runtime.h>
 
 #include <algorithm>

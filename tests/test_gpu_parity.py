@@ -575,3 +575,30 @@ def test_pool_gradients_different_pools_across_clear_plans():
         _, g_ref = fermion.adapt_gradients(cfg["n_orb"], cfg["n_el"], h, g, t, exs, pexs)
         assert np.abs(gp - g_ref).max() < 1e-10
         st.clear_plans()
+
+
+def test_plan_caches_evict_and_stay_correct():
+    """One handle sees twelve Hamiltonians and twelve ansatz orders (more than the
+    eight plans per cache it keeps), then the first pair again: every result
+    matches the oracle, and the first pair's result is bit-identical after its
+    plans were dropped and rebuilt."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    n, det = cfg["n_qubits"], (1 << cfg["n_el"]) - 1
+    rng = np.random.default_rng(77)
+    st = qf.State(n, "c128")
+    first = None
+    for k in range(12):
+        Tk = T.copy()
+        Tk["coeff"] = T["coeff"] * (1.0 + 0.05 * k)
+        order = rng.permutation(len(exs)) if k else np.arange(len(exs))
+        Ak = np.concatenate([A[A["param"] == p] for p in order])
+        e, grad = st.energy_grad(det, Ak, t, Tk)
+        arots = list(zip(Ak["x"], Ak["z"], Ak["coeff"], Ak["param"]))
+        e_ref, g_ref, _ = pauli.adjoint_gradient(n, det, arots, t, _terms_list(Tk))
+        assert abs(e - e_ref) < TOL_E_C128 and np.abs(grad - g_ref).max() < 1e-10, k
+        if k == 0:
+            first = (Ak, Tk, e, grad)
+    Ak, Tk, e0, g0 = first
+    e, grad = st.energy_grad(det, Ak, t, Tk)
+    assert e == e0 and np.array_equal(grad, g0)
+    st.close()
