@@ -74,6 +74,11 @@ struct ExpPlan {
   std::vector<qf_term> terms;        // the plan's terms (compared on every cache hit; tiled tables)
   bool has_odd = false;  // some term has an odd number of Y letters (imaginary phase)
   uint64_t last_use = 0; // the handle's call count at the plan's last use (least recently used goes first)
+  // direct sector H|psi> tables (qf::SecDirect): 0 not tried yet, 1 built, -1 the
+  // terms do not take that form (the chunk-table kernel runs instead)
+  int direct = 0;
+  void* d_direct = nullptr;
+  qf::SecDirect dtab{};
 };
 
 void free_plan(ExpPlan& p) {
@@ -88,6 +93,7 @@ void free_plan(ExpPlan& p) {
   cudaFree(p.d_wchunks_s);
   cudaFree(p.d_seclarge);
   cudaFree(p.d_rk);
+  cudaFree(p.d_direct);
   for (int v = 0; v < qf::kClassTbN; ++v) cudaFree(p.d_classes[v]);
   p = ExpPlan();
 }
@@ -603,6 +609,195 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   p.last_use = st->calls;
   auto res = st->plans.emplace(key, std::move(p));
   *out = &res.first->second;
+  return QF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Direct sector tables (qf::SecDirect) of a real Pauli sum on n <= 32 qubits.
+// Every group that can link two members of one sector must take the form the
+// direct kernel evaluates: all strings with an even number of Y letters; for a
+// flip set S of two or four qubits, Z letters off S equal to the Jordan-Wigner
+// chains of S (open intervals between the 1st and 2nd and between the 3rd and
+// 4th support qubits), a two-qubit flip may add one more Z; the x = 0 group has
+// Z strings of weight at most two.  A molecular Hamiltonian (Eq. 1 through
+// Eq. 15-16) takes this form.  Returns false otherwise.
+struct DirectHost {
+  std::vector<double> wab, waa, wbb;  // doubles' weights
+  std::vector<double> s1a, s1b;       // singles' A and B (before fixed point)
+  std::vector<double> dg;             // K, U, V (before fixed point)
+};
+
+bool build_direct(const std::vector<qf_term>& T, int n, DirectHost* h) {
+  if (n < 2 || n > 32) return false;
+  const int ne = (n + 1) / 2, no = n / 2, pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
+  h->wab.assign((size_t)ne * ne * no * no, 0.0);
+  h->waa.assign((size_t)std::max(1, pe * pe), 0.0);
+  h->wbb.assign((size_t)std::max(1, po * po), 0.0);
+  h->s1a.assign((size_t)ne * ne * (n + 1), 0.0);
+  h->s1b.assign((size_t)no * no * (n + 1), 0.0);
+  h->dg.assign((size_t)1 + n + (size_t)n * n, 0.0);
+  std::vector<size_t> order(T.size());
+  for (size_t i = 0; i < T.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return T[a].x < T[b].x; });
+  auto pr = [](int i, int j) { return i + j * (j - 1) / 2; };  // i < j
+  std::vector<double> wr(n);
+  for (size_t q0 = 0; q0 < order.size();) {
+    size_t q1 = q0 + 1;
+    const uint64_t x = T[order[q0]].x;
+    while (q1 < order.size() && T[order[q1]].x == x) ++q1;
+    const int xe = popc(x & kEvenMask), xo = popc(x & ~kEvenMask);
+    if ((xe & 1) || (xo & 1)) {  // never links two members of one sector
+      q0 = q1;
+      continue;
+    }
+    for (size_t k = q0; k < q1; ++k)
+      if (popc(T[order[k]].x & T[order[k]].z) & 1) return false;  // imaginary weight
+    if (x == 0) {
+      for (size_t k = q0; k < q1; ++k) {
+        const qf_term& t = T[order[k]];
+        std::vector<int> zb;
+        for (int q = 0; q < n; ++q)
+          if ((t.z >> q) & 1ull) zb.push_back(q);
+        if (zb.size() > 2) return false;
+        // (-1)^{c_r} = 1 - 2 c_r on occupation bits c_r
+        h->dg[0] += t.coeff;
+        for (int r : zb) h->dg[1 + r] -= 2.0 * t.coeff;
+        if (zb.size() == 2) h->dg[1 + n + (size_t)zb[0] * n + zb[1]] += 4.0 * t.coeff;
+      }
+      q0 = q1;
+      continue;
+    }
+    std::vector<int> sq;
+    for (int q = 0; q < n; ++q)
+      if ((x >> q) & 1ull) sq.push_back(q);
+    if (sq.size() != 2 && sq.size() != 4) return false;
+    uint64_t zc = 0;  // the chains
+    for (size_t i = 0; i < sq.size(); i += 2)
+      for (int q = sq[i] + 1; q < sq[i + 1]; ++q) zc |= 1ull << q;
+    for (size_t k = q0; k < q1; ++k) {
+      const uint64_t extra = (T[order[k]].z & ~x) ^ zc;
+      if (extra && (sq.size() == 4 || popc(extra) > 1)) return false;
+    }
+    // every flip direction: c occupies half the support, as many alpha and beta
+    // qubits as it leaves empty
+    const int ns = (int)sq.size();
+    for (int m = 0; m < (1 << ns); ++m) {
+      uint64_t cd = 0;
+      for (int i = 0; i < ns; ++i)
+        if ((m >> i) & 1) cd |= 1ull << sq[i];
+      if (2 * popc(cd & kEvenMask) != xe || 2 * popc(cd & ~kEvenMask) != xo) continue;
+      // D(c) = (-1)^{xor of PP_c over S} * (-1)^{c_s1 ^ c_s3} * sum_t c_t i^y_t (-1)^{popc(z_t & S & ~c)} * ...
+      const double pref = ((((cd >> sq[0]) ^ (ns == 4 ? (cd >> sq[2]) : 0ull)) & 1ull) ? -1.0 : 1.0);
+      double w0 = 0.0;
+      std::fill(wr.begin(), wr.end(), 0.0);
+      for (size_t k = q0; k < q1; ++k) {
+        const qf_term& t = T[order[k]];
+        const int y = popc(t.x & t.z) & 3;  // 0 or 2
+        double val = t.coeff * (y == 2 ? -1.0 : 1.0) * ((popc(t.z & x & ~cd) & 1) ? -1.0 : 1.0) * pref;
+        const uint64_t extra = (t.z & ~x) ^ zc;
+        if (!extra)
+          w0 += val;
+        else
+          wr[__builtin_ctzll(extra)] += val;
+      }
+      std::vector<int> oc, em;  // occupied / empty support qubits of c
+      for (int q : sq) ((cd >> q) & 1ull ? oc : em).push_back(q);
+      if (ns == 2) {
+        const bool beta = oc[0] & 1;
+        const int lo = oc[0] >> 1, lv = em[0] >> 1, nn = beta ? no : ne;
+        double* row = (beta ? h->s1b.data() : h->s1a.data()) + (size_t)(lo * nn + lv) * (n + 1);
+        double a = w0;
+        for (int r = 0; r < n; ++r) {
+          a += wr[r];
+          row[1 + r] += -2.0 * wr[r];
+        }
+        row[0] += a;
+      } else if (xe == 2) {
+        int oa = -1, va = -1, ob = -1, vb = -1;
+        for (int q : oc) (q & 1 ? ob : oa) = q >> 1;
+        for (int q : em) (q & 1 ? vb : va) = q >> 1;
+        h->wab[(((size_t)oa * ne + va) * no + ob) * no + vb] += w0;
+      } else {
+        const int P = xe == 4 ? pe : po;
+        (xe == 4 ? h->waa : h->wbb)[(size_t)pr(oc[0] >> 1, oc[1] >> 1) * P + pr(em[0] >> 1, em[1] >> 1)] += w0;
+      }
+    }
+    q0 = q1;
+  }
+  return true;
+}
+
+// Builds and uploads a plan's direct tables on first use.
+qf_status ensure_direct(qf_state* st, ExpPlan* p) {
+  if (p->direct != 0) return QF_OK;
+  DirectHost h;
+  if (!build_direct(p->terms, st->n, &h)) {
+    p->direct = -1;
+    return QF_OK;
+  }
+  const int n = st->n;
+  // fixed point: the largest sum of magnitudes any member can add stays below 2^61
+  double bound = 0.0;
+  for (double v : h.dg) bound += std::fabs(v);
+  for (const std::vector<double>* t : {&h.s1a, &h.s1b})
+    for (size_t r = 0; r < t->size(); r += n + 1) {
+      double b = 0.0;
+      for (int k = 0; k <= n; ++k) b += std::fabs((*t)[r + k]);
+      bound = std::max(bound, b);
+    }
+  int e = 0;
+  if (bound > 0.0) e = std::min(1000, 61 - (int)std::ceil(std::log2(bound)));
+  auto to_fix = [&](const std::vector<double>& v) {
+    std::vector<long long> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = std::llrint(std::ldexp(v[i], e));
+    return o;
+  };
+  const std::vector<long long> f1a = to_fix(h.s1a), f1b = to_fix(h.s1b), fdg = to_fix(h.dg);
+  auto f32 = [](const std::vector<double>& v) {
+    std::vector<float> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+    return o;
+  };
+  const std::vector<float> fab = f32(h.wab), faa = f32(h.waa), fbb = f32(h.wbb);
+  // one buffer: doubles, floats, fixed point (each part 256-byte aligned)
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t o_wab = 0, o_waa = o_wab + al(h.wab.size() * 8), o_wbb = o_waa + al(h.waa.size() * 8),
+               o_fab = o_wbb + al(h.wbb.size() * 8), o_faa = o_fab + al(fab.size() * 4),
+               o_fbb = o_faa + al(faa.size() * 4), o_s1a = o_fbb + al(fbb.size() * 4),
+               o_s1b = o_s1a + al(f1a.size() * 8), o_dg = o_s1b + al(f1b.size() * 8), total = o_dg + al(fdg.size() * 8);
+  std::vector<char> buf(total, 0);
+  std::memcpy(buf.data() + o_wab, h.wab.data(), h.wab.size() * 8);
+  std::memcpy(buf.data() + o_waa, h.waa.data(), h.waa.size() * 8);
+  std::memcpy(buf.data() + o_wbb, h.wbb.data(), h.wbb.size() * 8);
+  std::memcpy(buf.data() + o_fab, fab.data(), fab.size() * 4);
+  std::memcpy(buf.data() + o_faa, faa.data(), faa.size() * 4);
+  std::memcpy(buf.data() + o_fbb, fbb.data(), fbb.size() * 4);
+  std::memcpy(buf.data() + o_s1a, f1a.data(), f1a.size() * 8);
+  std::memcpy(buf.data() + o_s1b, f1b.data(), f1b.size() * 8);
+  std::memcpy(buf.data() + o_dg, fdg.data(), fdg.size() * 8);
+  if (cudaMalloc(&p->d_direct, total) != cudaSuccess) {
+    cudaGetLastError();
+    p->d_direct = nullptr;
+    return fail(QF_ENOMEM, "cudaMalloc(direct H tables) failed");
+  }
+  QF_CUDA(h2d(p->d_direct, buf.data(), total, st->stream));
+  QF_CUDA(cudaStreamSynchronize(st->stream));  // the staging buffer is freed on return
+  char* b = static_cast<char*>(p->d_direct);
+  qf::SecDirect& d = p->dtab;
+  d.n = n;
+  d.ne = (n + 1) / 2;
+  d.no = n / 2;
+  d.wab = reinterpret_cast<const double*>(b + o_wab);
+  d.waa = reinterpret_cast<const double*>(b + o_waa);
+  d.wbb = reinterpret_cast<const double*>(b + o_wbb);
+  d.fab = reinterpret_cast<const float*>(b + o_fab);
+  d.faa = reinterpret_cast<const float*>(b + o_faa);
+  d.fbb = reinterpret_cast<const float*>(b + o_fbb);
+  d.s1a = reinterpret_cast<const long long*>(b + o_s1a);
+  d.s1b = reinterpret_cast<const long long*>(b + o_s1b);
+  d.dg = reinterpret_cast<const long long*>(b + o_dg);
+  d.inv_fix = std::ldexp(1.0, -e);
+  p->direct = 1;
   return QF_OK;
 }
 
@@ -1952,9 +2147,19 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
                                    (int)nblk, nullptr, rs.pmax, nullptr, cm, log, d_strs, st->stream));
     double* d_e = st->d_out + nblk;
-    QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_seclarge,
-                                   p->nseclarge, p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
-                                   st->stream));
+    // a real state with a Hamiltonian of molecular form takes the direct tables
+    ExpPlan* pm = const_cast<ExpPlan*>(p);
+    if (lreal && st->n <= 32) {
+      qf_status ds = ensure_direct(st, pm);
+      if (ds != QF_OK) return ds;
+    }
+    if (lreal && pm->direct == 1)
+      QF_CUDA(qf::launch_sector_hpsi_direct(cpsi, st->dt, sp, pm->dtab, cm, st->d_partials, st->d_counter, d_e,
+                                            kPartials / 2, st->stream));
+    else
+      QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_seclarge, p->nseclarge,
+                                     p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
+                                     st->stream));
     const size_t npool_blk = pp ? pp->blocks.size() : 0;
     double* d_pool = st->d_out + nblk + 2 + 2 * n_dets;
     if (pp) {  // every pool operator's overlap with the final (psi, lambda): nothing rotated

@@ -233,6 +233,33 @@ struct SecRank {
   const RealChunk* rch;         // the chunks as RealChunk (n <= 32), else NULL
 };
 
+// Direct tables of a real molecular-type Hamiltonian on a sector (n <= 32),
+// for the compact-layout H|psi>.  For a member c and a group with support S
+// (the qubits its strings flip), PP_c(q) is the parity of c's occupied qubits
+// below q.  When every string of the group has the Jordan-Wigner chains of S as
+// its Z letters off S -- the open intervals between the 1st and 2nd and between
+// the 3rd and 4th support qubits -- the group's weight on the pair (c, c ^ x) is
+//     D(c) = (-1)^{xor over q in S of PP_c(q)} * W,
+// with W fixed by which support qubits c occupies (the flip direction).  Single
+// flips may also carry one number-operator Z_r: W = A + sum over c's occupied
+// qubits r outside S of B[r].  The x = 0 group is a sum of Z strings of weight
+// at most two: K + sum over occupied r of U[r] + sum over occupied r < s of
+// V[r][s].  A, B, K, U, V are 64-bit fixed point (value * 2^e, inv_fix = 2^-e),
+// so their sums are exact.  Local orbital q is qubit 2q (alpha) or 2q + 1 (beta).
+struct SecDirect {
+  int n, ne, no;               // qubits, alpha orbitals, beta orbitals
+  const double* wab;           // [((o * ne + v) * no + o2) * no + v2]: c occupies alpha o, beta o2
+  const double* waa;           // [pr(o1, o2) * C(ne, 2) + pr(v1, v2)]: c occupies o1 < o2, not v1 < v2
+  const double* wbb;           // likewise for beta (C(no, 2))
+  const float* fab;            // FP32 copies (complex64)
+  const float* faa;
+  const float* fbb;
+  const long long* s1a;        // alpha single o -> v: A at [(o * ne + v) * (n + 1)], B[r] at + 1 + r
+  const long long* s1b;        // beta single likewise ((o * no + v) * (n + 1))
+  const long long* dg;         // K, then U[r] at 1 + r, then V[r][s] at 1 + n + r * n + s (r < s)
+  double inv_fix;
+};
+
 // Kernel launchers (qf_kernels.cu).  All return cudaGetLastError() after launch.
 cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cudaStream_t s);
 // count amplitudes set to the unit vector e_idx.
@@ -305,6 +332,12 @@ cudaError_t launch_sector_overlaps(void* psi, qf_dtype dt, const RunInfo* runs, 
 uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged);
 // With cm.ra != NULL psi and lam are in the compact layout.  nblocks: the
 // most CTAs the reduction may use (partials holds 2 * nblocks doubles).
+// lambda = H psi on the compact layout of a real state through the direct tables
+// (lambda packed into psi's imaginary slots); out[0] = <psi|lambda>,
+// out[1] = <psi|psi>, partials holds 2 * nblocks doubles.
+cudaError_t launch_sector_hpsi_direct(void* cpsi, qf_dtype dt, const SecSpace& sp, const SecDirect& d,
+                                      const SecCompact& cm, double* partials, unsigned* counter, double* out,
+                                      int nblocks, cudaStream_t s);
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
                                const SecRank& rk, const SecGroup* large, int nlarge,
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,

@@ -804,6 +804,240 @@ __global__ void __launch_bounds__(256) k_sector_hpsi(const typename SCx<T>::V* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Sector H|psi> through the direct tables (SecDirect), compact layout, real
+// state with lambda packed into psi's imaginary slots.  Per member: the
+// prefix-parity bits PP_c at every qubit, then every single and double flip of
+// c -- each costs one table weight, its sign from four (two) PP bits, the
+// partner's rank and one multiply-add.  The diagonal and the singles' number-
+// operator parts are summed exactly in fixed point.
+
+// The r-th k-subset (colex order) of positions 0..m-1 as a bit mask.
+__device__ __forceinline__ uint32_t unrank_mask(uint32_t r, int m, int k, const uint32_t (*C)[kBinom]) {
+  uint32_t bits = 0;
+  for (int j = m - 1; j >= 0 && k > 0; --j) {
+    const uint32_t c = C[j][k];
+    if (r >= c) {
+      bits |= 1u << j;
+      r -= c;
+      --k;
+    }
+  }
+  return bits;
+}
+
+// Bit q of x (q < 16) to bit 2q.
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+// Bit 2q of x to bit q.
+__device__ __forceinline__ uint32_t gather_even(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+  x = (x | (x >> 4)) & 0x00FF00FFu;
+  x = (x | (x >> 8)) & 0x0000FFFFu;
+  return x;
+}
+
+// w with its sign flipped when s (0 or 1) is set.
+__device__ __forceinline__ double flip_sign(double w, uint32_t s) {
+  return __longlong_as_double(__double_as_longlong(w) ^ ((long long)s << 63));
+}
+__device__ __forceinline__ float flip_sign(float w, uint32_t s) {
+  return __int_as_float(__float_as_int(w) ^ (int)(s << 31));
+}
+
+// Pair products of one member: FP64 multiply-adds into the member's sum
+// (complex128), or FP32 ones folded into it after each innermost loop
+// (complex64; at most C(16, 2) products between folds).
+template <typename T> struct PairAcc {
+  float s = 0.0f;
+  __device__ __forceinline__ void add(float w, float v, double&) { s = fmaf(w, v, s); }
+  __device__ __forceinline__ void fold(double& lx) {
+    lx += (double)s;
+    s = 0.0f;
+  }
+};
+template <> struct PairAcc<double> {
+  __device__ __forceinline__ void add(double w, double v, double& lx) { lx = fma(w, v, lx); }
+  __device__ __forceinline__ void fold(double&) {}
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, uint32_t cnt_e, uint32_t cnt_o,
+                                                            int ke, int ko, const uint16_t* __restrict__ ra,
+                                                            const uint16_t* __restrict__ rb, double* partials,
+                                                            unsigned* counter, double* out) {
+  __shared__ uint32_t C[kBinom][kBinom];
+  fill_binom(C);
+  __syncthreads();
+  const int n = d.n, ne = d.ne, no = d.no;
+  const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
+  const T* wab = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.wab : (const void*)d.fab);
+  const T* waa = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.waa : (const void*)d.faa);
+  const T* wbb = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.wbb : (const void*)d.fbb);
+  const T* ps = st;  // psi of member m at ps[2 m]; lambda goes to st[2 m + 1]
+  const uint64_t items = (uint64_t)cnt_e * cnt_o;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc_e = 0.0, acc_n = 0.0;
+  for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items; it += stride) {
+    const uint32_t i32 = (uint32_t)it;
+    const uint32_t ie = i32 / cnt_o, io = i32 - ie * cnt_o;
+    const uint32_t la = unrank_mask(ie, ne, ke, C), lb = unrank_mask(io, no, ko, C);
+    const uint32_t c = spread16(la) | (spread16(lb) << 1);  // the member in qubit order
+    uint32_t p = c;  // prefix parities: bit q = parity of c's bits below q
+    p ^= p << 1;
+    p ^= p << 2;
+    p ^= p << 4;
+    p ^= p << 8;
+    p ^= p << 16;
+    p <<= 1;
+    const uint32_t ppa = gather_even(p), ppb = gather_even(p >> 1);
+    const uint32_t va = ((1u << ne) - 1u) & ~la, vb = ((1u << no) - 1u) & ~lb;
+    const size_t rowself = (size_t)ie * cnt_o;
+    const double self = (double)ps[2 * (size_t)it];
+    double lx = 0.0, lxs = 0.0;  // lxs: fixed-point weights times psi (units of 2^-e)
+    PairAcc<T> pa;
+    // x = 0: K + sum U[r] + sum V[r][s] over occupied r < s
+    long long dsum = __ldg(d.dg);
+    for (uint32_t m = c; m; m &= m - 1) {
+      const int r = __ffs((int)m) - 1;
+      dsum += __ldg(d.dg + 1 + r);
+      const long long* vr = d.dg + 1 + n + r * n - 1;
+      for (uint32_t m2 = m & (m - 1); m2; m2 &= m2 - 1) dsum += __ldg(vr + __ffs((int)m2));
+    }
+    lxs = fma(__ll2double_rn(dsum), self, lxs);
+    // singles: A + sum of B[r] over c's occupied qubits other than the one it gives up
+    for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
+      const int o = __ffs((int)m1) - 1;
+      const uint32_t rest = c & ~(1u << (2 * o));
+      for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
+        const int v = __ffs((int)n1) - 1;
+        const long long* row = d.s1a + (size_t)(o * ne + v) * (n + 1);
+        long long w = __ldg(row);
+        for (uint32_t m2 = rest; m2; m2 &= m2 - 1) w += __ldg(row + __ffs((int)m2));
+        if (((ppa >> o) ^ (ppa >> v)) & 1u) w = -w;
+        const size_t idx = (size_t)__ldg(ra + (la ^ (1u << o) ^ (1u << v))) * cnt_o + io;
+        lxs = fma(__ll2double_rn(w), (double)ps[2 * idx], lxs);
+      }
+    }
+    for (uint32_t m1 = lb; m1; m1 &= m1 - 1) {
+      const int o = __ffs((int)m1) - 1;
+      const uint32_t rest = c & ~(1u << (2 * o + 1));
+      for (uint32_t n1 = vb; n1; n1 &= n1 - 1) {
+        const int v = __ffs((int)n1) - 1;
+        const long long* row = d.s1b + (size_t)(o * no + v) * (n + 1);
+        long long w = __ldg(row);
+        for (uint32_t m2 = rest; m2; m2 &= m2 - 1) w += __ldg(row + __ffs((int)m2));
+        if (((ppb >> o) ^ (ppb >> v)) & 1u) w = -w;
+        const size_t idx = rowself + __ldg(rb + (lb ^ (1u << o) ^ (1u << v)));
+        lxs = fma(__ll2double_rn(w), (double)ps[2 * idx], lxs);
+      }
+    }
+    // opposite-spin doubles: alpha o -> v, beta o2 -> v2
+    for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
+      const int o = __ffs((int)m1) - 1;
+      for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
+        const int v = __ffs((int)n1) - 1;
+        const uint32_t sa = ((ppa >> o) ^ (ppa >> v)) & 1u;
+        const size_t rowa = (size_t)__ldg(ra + (la ^ (1u << o) ^ (1u << v))) * cnt_o;
+        const T* wrow = wab + (size_t)(o * ne + v) * (no * no);
+        for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
+          const int o2 = __ffs((int)m2) - 1;
+          const uint32_t s3 = sa ^ ((ppb >> o2) & 1u);
+          const uint32_t lbo = lb ^ (1u << o2);
+          const T* w2 = wrow + o2 * no;
+          for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
+            const int v2 = __ffs((int)n2) - 1;
+            const T w = flip_sign(__ldg(w2 + v2), s3 ^ ((ppb >> v2) & 1u));
+            pa.add(w, ps[2 * (rowa + __ldg(rb + (lbo | (1u << v2))))], lx);
+          }
+        }
+        pa.fold(lx);
+      }
+    }
+    // same-spin doubles: occupied o1 < o2 -> empty v1 < v2
+    for (uint32_t m2 = la; m2; m2 &= m2 - 1) {
+      const int o2 = __ffs((int)m2) - 1;
+      for (uint32_t m1 = la & ((1u << o2) - 1u); m1; m1 &= m1 - 1) {
+        const int o1 = __ffs((int)m1) - 1;
+        const uint32_t so = ((ppa >> o1) ^ (ppa >> o2)) & 1u;
+        const uint32_t lao = la ^ (1u << o1) ^ (1u << o2);
+        const T* wrow = waa + (size_t)(o1 + o2 * (o2 - 1) / 2) * pe;
+        for (uint32_t n2 = va; n2; n2 &= n2 - 1) {
+          const int v2 = __ffs((int)n2) - 1;
+          const uint32_t s2 = so ^ ((ppa >> v2) & 1u);
+          const T* w2 = wrow + v2 * (v2 - 1) / 2;
+          const uint32_t lav = lao | (1u << v2);
+          for (uint32_t n1 = va & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
+            const int v1 = __ffs((int)n1) - 1;
+            const T w = flip_sign(__ldg(w2 + v1), s2 ^ ((ppa >> v1) & 1u));
+            pa.add(w, ps[2 * ((size_t)__ldg(ra + (lav | (1u << v1))) * cnt_o + io)], lx);
+          }
+        }
+        pa.fold(lx);
+      }
+    }
+    for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
+      const int o2 = __ffs((int)m2) - 1;
+      for (uint32_t m1 = lb & ((1u << o2) - 1u); m1; m1 &= m1 - 1) {
+        const int o1 = __ffs((int)m1) - 1;
+        const uint32_t so = ((ppb >> o1) ^ (ppb >> o2)) & 1u;
+        const uint32_t lbo = lb ^ (1u << o1) ^ (1u << o2);
+        const T* wrow = wbb + (size_t)(o1 + o2 * (o2 - 1) / 2) * po;
+        for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
+          const int v2 = __ffs((int)n2) - 1;
+          const uint32_t s2 = so ^ ((ppb >> v2) & 1u);
+          const T* w2 = wrow + v2 * (v2 - 1) / 2;
+          const uint32_t lbv = lbo | (1u << v2);
+          for (uint32_t n1 = vb & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
+            const int v1 = __ffs((int)n1) - 1;
+            const T w = flip_sign(__ldg(w2 + v1), s2 ^ ((ppb >> v1) & 1u));
+            pa.add(w, ps[2 * (rowself + __ldg(rb + (lbv | (1u << v1))))], lx);
+          }
+        }
+        pa.fold(lx);
+      }
+    }
+    lx = fma(lxs, d.inv_fix, lx);
+    acc_e = fma(self, lx, acc_e);
+    acc_n = fma(self, self, acc_n);
+    st[2 * (size_t)it + 1] = (T)lx;
+  }
+  // deterministic two-value grid reduction
+  __shared__ bool last;
+  const double b0 = block_sum_s(acc_e);
+  const double b1 = block_sum_s(acc_n);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = b0;
+    partials[2 * blockIdx.x + 1] = b1;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+      s0 += __ldcg(partials + 2 * i);
+      s1 += __ldcg(partials + 2 * i + 1);
+    }
+    s0 = block_sum_s(s0);
+    s1 = block_sum_s(s1);
+    if (threadIdx.x == 0) {
+      out[0] = s0;
+      out[1] = s1;
+      *counter = 0u;
+    }
+  }
+}
+
 }  // namespace
 
 // Grid of the cooperative sweep: about one item per thread for a typical block,
@@ -1021,6 +1255,27 @@ static cudaError_t hpsi_dispatch(const void* psi, void* lam, bool realst, bool n
     hpsi_t<T, false, false, true>(psi, lam, narrow, g, sp, rk, large, nlarge, chunks, partials, counter, out,
                                   cm, s);
   return cudaGetLastError();
+}
+
+cudaError_t launch_sector_hpsi_direct(void* cpsi, qf_dtype dt, const SecSpace& sp, const SecDirect& d,
+                                      const SecCompact& cm, double* partials, unsigned* counter, double* out,
+                                      int nblocks, cudaStream_t s) {
+  if (d.n > 32 || d.ne != sp.ne || d.no != sp.no || sp.ne > 16) return cudaErrorInvalidValue;
+  const int prof_slot_ = prof_pre(QF_K_HPSI, s);
+  const uint64_t items = (uint64_t)sp.cnt_e * sp.cnt_o;
+  if (dt == QF_C128) {
+    const auto k = k_sector_hpsi_direct<double>;
+    k<<<hpsi_grid(k, items, nblocks), 256, 0, s>>>(static_cast<double*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke,
+                                                    sp.ko, cm.ra, cm.rb, partials, counter, out);
+  } else {
+    const auto k = k_sector_hpsi_direct<float>;
+    k<<<hpsi_grid(k, items, nblocks), 256, 0, s>>>(static_cast<float*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke, sp.ko,
+                                                    cm.ra, cm.rb, partials, counter, out);
+  }
+  const cudaError_t e = cudaGetLastError();
+  prof_post(prof_slot_, s);
+  count_launch();
+  return e;
 }
 
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,

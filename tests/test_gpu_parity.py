@@ -602,3 +602,26 @@ def test_plan_caches_evict_and_stay_correct():
     e, grad = st.energy_grad(det, Ak, t, Tk)
     assert e == e0 and np.array_equal(grad, g0)
     st.close()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_sector_hpsi_chunk_tables_for_non_molecular_terms(dtype):
+    """A real Hamiltonian outside the molecular form (here a Z string of weight
+    three and a double flip with extra Z letters) keeps the chunk-table sector
+    H|psi>; the molecular part alone takes the direct tables.  Both against the
+    oracle's adjoint gradient."""
+    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    n, det = cfg["n_qubits"], (1 << cfg["n_el"]) - 1
+    extra = qf.as_terms(np.array([0, 0b00110011], dtype=np.uint64), np.array([0b10101, 0b10000000], dtype=np.uint64),
+                        np.array([0.11, -0.07]))
+    arots = list(zip(A["x"], A["z"], A["coeff"], A["param"]))
+    st = qf.State(n, dtype)
+    for TT in (T, np.concatenate([T, extra])):
+        e, grad = st.energy_grad(det, A, t, TT)
+        e_ref, g_ref, _ = pauli.adjoint_gradient(n, det, arots, t, _terms_list(TT))
+        if dtype == "c128":
+            assert abs(e - e_ref) < TOL_E_C128 and np.abs(grad - g_ref).max() < 1e-10
+        else:
+            assert abs(e - e_ref) < TOL_E_C64
+            assert np.linalg.norm(grad - g_ref) <= TOL_G_C64 * np.linalg.norm(g_ref)
+    st.close()
