@@ -142,6 +142,10 @@ struct SectorRuns {
   uint64_t logitems = 0;         // (member pair, block) items of one sweep: the forward log's length
   std::vector<uint16_t> strs;    // the blocks' outside strings (RunBlk::lsa / lsb); empty when not tabulated
   bool log_ok = true;            // every inverse block lists its two patterns in the forward order
+  // item maps (RunPart::mapbase): words of all classes; map_ok when every part fits
+  // a map word and the inverse blocks share the forward blocks' item geometry
+  uint64_t mapwords = 0;
+  bool map_ok = false;
 };
 
 struct qf_state {
@@ -179,6 +183,9 @@ struct qf_state {
   void* d_poolblk = nullptr; // operator-pool run descriptors (blocks, parts, strings)
   size_t poolblk_cap = 0;
   uint64_t pool_key = 0;     // the pool plan and sector whose descriptors sit in d_poolblk
+  void* d_map = nullptr;     // item maps of the part-local sweeps (RunPart::mapbase)
+  size_t map_cap = 0;
+  uint64_t map_key = 0;      // the plan and sector whose maps sit in d_map
   void* d_log = nullptr;     // forward log of the part-local sweeps (psi pairs after each block)
   size_t log_cap = 0;
   bool log_failed = false;   // the log did not fit: later calls un-rotate psi instead
@@ -225,6 +232,8 @@ constexpr uint64_t kStringsMax = (uint64_t)1 << 25;
 // Largest forward log of the part-local sweeps a handle allocates (24 qubits,
 // complex128: 2.1 GB).
 constexpr size_t kLogMaxBytes = (size_t)16 << 30;
+// Largest item-map table a handle allocates (words; 1 GB).
+constexpr uint64_t kMapMaxWords = (uint64_t)1 << 28;
 // Plans a handle keeps per cache (Pauli sums; ansatz and pool block structures).
 // Past that, the least recently used are dropped (with their device tables) when
 // the next plan-using call starts, so no call loses a plan it is using.
@@ -248,6 +257,7 @@ void trim_plans(qf_state* st) {
       if (it->second.last_use < lru->second.last_use) lru = it;
     st->ansatz_plans.erase(lru);
     st->parts_key = 0;  // descriptors on the device are re-uploaded by their next user
+    st->map_key = 0;
     st->pool_key = 0;
   }
 }
@@ -1411,6 +1421,7 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
       const qf::RunBlk& B = out->blks[b];
       ++shapes[{B.ne, B.no, B.e0, B.o0}];
     }
+    std::map<std::pair<int, int>, uint64_t> classes;  // (ka, kb) -> map base
     for (int k = 0; k < R.nparts; ++k) {
       qf::RunPart& P = out->parts[R.part0 + k];
       uint64_t tot = 0;
@@ -1420,9 +1431,30 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
       }
       P.logbase = out->logitems;
       out->logitems += tot;
+      // parts with the same electron counts on U share one item map
+      const auto seen = classes.find({P.ka, P.kb});
+      P.maprep = seen == classes.end();
+      P.mapbase = P.maprep ? out->mapwords : seen->second;
+      if (P.maprep) {
+        classes.emplace(std::make_pair(P.ka, P.kb), P.mapbase);
+        out->mapwords += tot;
+      }
     }
     out->runs.push_back(R);
     b0 = b1;
+  }
+  // maps serve the reverse sweep too when each inverse block has its forward
+  // block's item geometry (outside orbitals, patterns, class masks)
+  out->map_ok = out->log_ok;
+  for (const qf::RunInfo& R : out->runs)
+    if (R.maxsize > qf::kMapMaxPart) out->map_ok = false;
+  for (size_t b = 0; b < nblk && out->map_ok; ++b) {
+    const qf::RunBlk& F = out->blks[b];
+    const qf::RunBlk& I = out->blks[nblk + b];
+    out->map_ok = F.ne == I.ne && F.no == I.no && F.e0 == I.e0 && F.o0 == I.o0 && F.nzc == I.nzc &&
+                  std::memcmp(F.epos, I.epos, sizeof(F.epos)) == 0 && std::memcmp(F.opos, I.opos, sizeof(F.opos)) == 0 &&
+                  std::memcmp(F.pu, I.pu, sizeof(F.pu)) == 0 && std::memcmp(F.zu, I.zu, sizeof(F.zu)) == 0 &&
+                  std::memcmp(F.zg, I.zg, sizeof(F.zg)) == 0;
   }
   // outside strings of every block: all subsets of its outside positions, by size,
   // each size in colex order (= increasing mask), as run-local masks; shared by a
@@ -1721,6 +1753,7 @@ qf_status qf_state_destroy(qf_state* st) {
   cudaFree(st->d_cstate);
   cudaFree(st->d_runblk);
   cudaFree(st->d_log);
+  cudaFree(st->d_map);
   cudaFree(st->d_idx);
   cudaFree(st->d_poolblk);
   cudaFree(st->d_partials);
@@ -1952,6 +1985,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     st->ansatz_plans.erase(ait);
     ait = st->ansatz_plans.end();
     st->parts_key = 0;
+    st->map_key = 0;
   }
   bool fresh = false;
   if (ait == st->ansatz_plans.end()) {
@@ -2143,9 +2177,22 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
         rs.strs.empty() ? nullptr
                         : reinterpret_cast<const uint16_t*>(static_cast<const char*>(st->d_runblk) + blk_bytes +
                                                             part_bytes);
+    // item maps of the sweeps, built on the device whenever the parts change
+    const uint32_t* d_map = nullptr;
+    if (rs.map_ok && rs.mapwords > 0 && rs.mapwords <= kMapMaxWords) {
+      const void* mbefore = st->d_map;
+      if (ensure_buf(&st->d_map, &st->map_cap, (size_t)rs.mapwords * sizeof(uint32_t), "sweep item maps") == QF_OK) {
+        if (st->map_key != pkey || st->d_map != mbefore) {
+          QF_CUDA(qf::launch_run_itemmaps(rs.runs.data(), nruns, d_parts, d_blks, cm, d_strs,
+                                          static_cast<uint32_t*>(st->d_map), st->stream));
+          st->map_key = pkey;
+        }
+        d_map = static_cast<const uint32_t*>(st->d_map);
+      }
+    }
     QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
     QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
-                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, d_strs, st->stream));
+                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, d_strs, d_map, st->stream));
     double* d_e = st->d_out + nblk;
     // a real state with a Hamiltonian of molecular form takes the direct tables
     ExpPlan* pm = const_cast<ExpPlan*>(p);
@@ -2186,7 +2233,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     }
     if (need_reverse)
       QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
-                                     (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, d_strs,
+                                     (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, d_strs, d_map,
                                      st->stream));
     if (n_dets) {  // residuals: lambda after the reverse sweep is U^dagger H psi
       std::vector<int64_t> idx(n_dets);
@@ -2392,7 +2439,7 @@ qf_status qf_state_clear_plans(qf_state* st) {
   for (auto& kv : st->plans) free_plan(kv.second);
   st->plans.clear();
   st->ansatz_plans.clear();
-  st->parts_key = st->pool_key = 0;  // descriptors on the device belong to no plan now
+  st->parts_key = st->pool_key = st->map_key = 0;  // descriptors on the device belong to no plan now
   return QF_OK;
 }
 

@@ -189,7 +189,16 @@ struct RunPart {                    // one occupation pattern of G
   int ka, kb;                       // electrons left for U's alpha / beta orbitals
   uint32_t cnta, cntb;              // C(ua, ka), C(ub, kb): size = cnta * cntb
   uint64_t logbase;                 // first forward-log item of this part (its blocks' items follow in order)
+  // Item map of the part's class (the run's parts with the same ka, kb share every
+  // block's item geometry): one word per item in sweep order, laid out like the
+  // log, from mapbase.  maprep: this part builds its class's map.
+  uint64_t mapbase;
+  int maprep;
+  int pad_;
 };
+// An item-map word: the item's two members inside the part (12 bits each) and
+// the sign-class bits its U strings give (bits 24-25).
+constexpr uint32_t kMapMaxPart = 4096;
 struct RunInfo {
   int b0, b1;                       // blocks [b0, b1)
   int part0, nparts;                // parts [part0, part0 + nparts), largest first
@@ -320,7 +329,7 @@ cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBl
 // when a part does not fit in shared memory.
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
-                               int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
+                               int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs, const uint32_t* map,
                                cudaStream_t s);
 // Overlaps only: out[b] = Im <lam|Q_b|psi> of every block b on the same compact
 // state (psi real parts, lam real parts in psi's imaginary slots); nothing is
@@ -328,6 +337,10 @@ cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool
 cudaError_t launch_sector_overlaps(void* psi, qf_dtype dt, const RunInfo* runs, int nruns, const RunPart* parts,
                                   const RunBlk* blks, int nblk, double* partial, int pmax, double* out,
                                   const SecCompact& cm, const uint16_t* strs, cudaStream_t s);
+// Builds the item maps (RunPart::mapbase) of every run's classes from the forward
+// blocks; map holds the plan's map words.
+cudaError_t launch_run_itemmaps(const RunInfo* runs, int nruns, const RunPart* parts, const RunBlk* blks,
+                                const SecCompact& cm, const uint16_t* strs, uint32_t* map, cudaStream_t s);
 // Largest part (members) launch_sector_runs accepts for this dtype, direction and log use.
 uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged);
 // With cm.ra != NULL psi and lam are in the compact layout.  nblocks: the

@@ -243,9 +243,65 @@ __device__ __forceinline__ uint32_t unrank_m(uint32_t r, const uint8_t* pos, int
   return bits;
 }
 
+// Sums of FP64 values on the integer pipes (GB300 runs FP64 at 1/64 of FP32, and
+// a reduction tree is a serial chain of FP64 adds).  A double is its 53-bit
+// integer significand times 2^(e - 1075), e its biased exponent.  Lanes align
+// their significands on the warp's largest e, dropping bits below 2^-52 of the
+// largest value, and the aligned integers are added exactly in three 21-bit
+// slices by single-instruction warp reductions.
+
+// Exact warp sum of m (|m| < 2^58 on every lane).
+__device__ __forceinline__ long long warp_add_i64(long long m) {
+  const unsigned lo = (unsigned)(m & 0x1FFFFFll), mid = (unsigned)((m >> 21) & 0x1FFFFFll);
+  const int hi = (int)(m >> 42);
+  const unsigned slo = __reduce_add_sync(0xffffffffu, lo);
+  const unsigned smid = __reduce_add_sync(0xffffffffu, mid);
+  const int shi = __reduce_add_sync(0xffffffffu, hi);
+  return (long long)shi * (1ll << 42) + (long long)smid * (1ll << 21) + (long long)slo;
+}
+
+// The warp's sum of v as t * 2^(*e - 1075), |t| < 2^58 (zero and subnormal lanes
+// add nothing; the error is at most 32 units of 2^(*e - 1075)).
+__device__ __forceinline__ long long warp_sum_fixed(double v, int* e) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)ex);
+  long long m = (ex == 0) ? 0ll : ((b & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll);
+  const int sh = emax - ex;
+  m = sh > 62 ? 0ll : (m >> sh);
+  if (b < 0) m = -m;
+  *e = emax;
+  return warp_add_i64(m);
+}
+
+// d * 2^k for -2044 <= k <= 1023, exact unless the result is subnormal.
+__device__ __forceinline__ double scale_pow2(double d, int k) {
+  if (k < -1022) {
+    d *= __longlong_as_double(1ll << 52);  // 2^-1022
+    k += 1022;
+  }
+  return d * __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// Sum of the lanes' (t, e) pairs from warp_sum_fixed (at most 8 lanes nonzero) as
+// one double: aligned on the largest e, added exactly, converted once.
+__device__ __forceinline__ double warp_fixed_to_double(long long t, int e) {
+  const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)(t != 0 ? e : 0));
+  const int sh = emax - e;
+  const long long m = (t == 0 || sh > 62) ? 0ll : (t >> sh);
+  const long long tot = warp_add_i64(m);
+  return tot == 0 ? 0.0 : scale_pow2((double)tot, emax - 1075);
+}
+
 constexpr int kRunThreads = 256;
 constexpr int kRunWarps = kRunThreads / 32;
 constexpr int kRunBlkWords = sizeof(RunBlk) / 4;
+// Coefficient words a mapped sweep step copies: m then q (FP64) or mf then qf (FP32).
+constexpr int kCoefWordsMax = 64;
+static_assert(offsetof(RunBlk, q) == offsetof(RunBlk, m) + sizeof(double) * 16 &&
+                  offsetof(RunBlk, qf) == offsetof(RunBlk, mf) + sizeof(float) * 16 && kSparseMaxCls == 4 &&
+                  offsetof(RunBlk, m) % 8 == 0,
+              "coefficient layout of RunBlk");
 static_assert(sizeof(RunBlk) % 4 == 0 && kRunBlkWords <= kRunThreads, "run descriptor copy layout");
 
 // Shared-memory bytes per member: psi real parts (forward), (psi, lam) packed
@@ -289,7 +345,8 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
                                                              RunInfo run, const RunPart* __restrict__ parts,
                                                              const RunBlk* __restrict__ blks, double* partial,
                                                              int pmax, SecCompact cm, typename SCx<T>::V* log,
-                                                             const uint16_t* __restrict__ strs) {
+                                                             const uint16_t* __restrict__ strs,
+                                                             const uint32_t* __restrict__ map) {
   using V = typename SCx<T>::V;
   constexpr bool ADJ = MODE != 0;
   constexpr bool F32 = sizeof(T) == 4;
@@ -323,6 +380,8 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   const size_t amp_bytes = align16((run_member_bytes<MODE, T>() - idx_bytes) * cap);
   uint32_t* gi = reinterpret_cast<uint32_t*>(dsm + amp_bytes);
   const uint32_t size = P.cnta * P.cntb;
+  // item-map words of this part's class (forward and logged reverse sweeps)
+  const uint32_t* mp = (MODE == 0 || MODE == 3) && map ? map + P.mapbase : nullptr;
   // the real slot each member moves: psi's real part (MODE 0), lam's in psi's imaginary slot (MODE 3)
   const int slot = MODE == 3 ? 1 : 0;
   const T* pr = reinterpret_cast<const T*>(psi);
@@ -347,7 +406,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   };
   // log offset of the current block within this part's log
   uint64_t logoff = 0;
-  if (MODE == 3) {  // the reverse starts past the part's last block
+  if (MODE == 3 && !mp) {  // the reverse starts past the part's last block
     for (int s = 0; s < nb; ++s) {
       const RunBlk* Bg = blks + run.b0 + s;
       const int ne = __ldg(&Bg->ne), no = __ldg(&Bg->no);
@@ -374,9 +433,150 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   };
   int pend_w = 0;  // warps with items in the previous block (its overlaps wait in red)
   // MODE 3: the log pair of item tid of the current block, loaded during the
-  // previous block so that its DRAM latency overlaps that block's barrier
+  // previous block so that its DRAM latency overlaps that block's barrier; the
+  // item-map word of item tid likewise (MODE 0 and 3)
   V pre{};
   bool pre_ok = false;
+  if (mp) {
+    // Mapped sweep (forward, and reverse with the log): each step runs its items
+    // from the class's map with its block's coefficients.  Item counts, offsets and
+    // G class bits of every step are tabulated first; the coefficients, map words
+    // and log pairs of a step are loaded two steps ahead, so no load latency sits
+    // between two barriers.  A complex128 reverse sums each step's overlaps on the
+    // integer pipes (warp_sum_fixed), one step later, with no FP64 chain.
+    __shared__ uint32_t stn[kRunMaxBlocks], sto[kRunMaxBlocks];
+    __shared__ uint8_t stc[kRunMaxBlocks];
+    __shared__ __align__(16) uint32_t cw[3][kCoefWordsMax];
+    __shared__ long long wtot[2][kRunWarps];  // per-warp overlap sums of the last two steps
+    __shared__ int wexp[2][kRunWarps];
+    constexpr int kCw = F32 ? (MODE == 3 ? 20 : 16) : (MODE == 3 ? 64 : 32);
+    constexpr size_t kCoff = F32 ? offsetof(RunBlk, mf) : offsetof(RunBlk, m);
+    constexpr bool IRED = MODE == 3 && !F32;  // integer overlap reduction
+    auto coef_word = [&](int st) {
+      return __ldg(reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(blks + blk_of(st)) + kCoff) + tid);
+    };
+    for (int f = tid; f < nb; f += kRunThreads) {  // f: the block's position in forward order
+      const RunBlk* Bg = blks + run.b0 + f;
+      const int ne = __ldg(&Bg->ne), no = __ldg(&Bg->no), nzc = __ldg(&Bg->nzc);
+      const int ke = P.ka - __ldg(&Bg->e0), ko = P.kb - __ldg(&Bg->o0);
+      stn[f] = (ke >= 0 && ke <= ne && ko >= 0 && ko <= no) ? C[ne][ke] * C[no][ko] : 0u;
+      unsigned cg = 0;
+      if (nzc > 0) cg = par32s(__ldg(&Bg->zg[0][0]) & P.ga) ^ par32s(__ldg(&Bg->zg[0][1]) & P.gb);
+      if (nzc > 1) cg |= (par32s(__ldg(&Bg->zg[1][0]) & P.ga) ^ par32s(__ldg(&Bg->zg[1][1]) & P.gb)) << 1;
+      stc[f] = (uint8_t)cg;
+    }
+    if (tid < kCw) {
+      cw[0][tid] = coef_word(0);
+      if (nb > 1) cw[1][tid] = coef_word(1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t a = 0;
+      for (int f = 0; f < nb; ++f) {
+        sto[f] = a;
+        a += stn[f];
+      }
+    }
+    __syncthreads();
+    V* lgp = log ? log + P.logbase : nullptr;
+    auto pos = [&](int st) { return MODE == 3 ? nb - 1 - st : st; };  // a step's forward position
+    // item tid of step s (wq0, lq0) and of step s + 1 (wq1, lq1): map word and
+    // (reverse) log pair
+    uint32_t wq0 = 0u, wq1 = 0u;
+    V lq0{}, lq1{};
+    if ((uint32_t)tid < stn[pos(0)]) {
+      wq0 = __ldg(mp + sto[pos(0)] + tid);
+      if (MODE == 3) lq0 = __ldcs(lgp + sto[pos(0)] + tid);
+    }
+    if (nb > 1 && (uint32_t)tid < stn[pos(1)]) {
+      wq1 = __ldg(mp + sto[pos(1)] + tid);
+      if (MODE == 3) lq1 = __ldcs(lgp + sto[pos(1)] + tid);
+    }
+    uint32_t nxtc = 0;  // coefficient word of step s + 2, stored at step s + 1
+    if (nb > 2 && tid < kCw) nxtc = coef_word(2);
+    // the previous step's per-warp sums, combined by one warp into the block's partial
+    auto reduce_fixed = [&](int ps, int pw) {
+      if (warp != kRunWarps - 1 - (ps & 3)) return;
+      const long long t = lane < pw ? wtot[ps & 1][lane] : 0ll;
+      const int e = lane < pw ? wexp[ps & 1][lane] : 0;
+      const double v = warp_fixed_to_double(t, e);
+      if (lane == 0) partial[(size_t)blk_of(ps) * pmax + blockIdx.x] = v;
+    };
+    for (int s = 0; s < nb; ++s) {
+      const int f = pos(s);
+      if (s >= 1 && s + 1 < nb && tid < kCw) {  // step s + 1's coefficients, loaded during step s - 1
+        cw[(s + 1) % 3][tid] = nxtc;
+        nxtc = (s + 2 < nb) ? coef_word(s + 2) : 0u;
+      }
+      if (ADJ && s > 0) {
+        if (IRED) reduce_fixed(s - 1, pend_w);
+        else reduce_block(s - 1, pend_w);
+      }
+      const uint32_t n_s = stn[f], o_s = sto[f];
+      const unsigned cg = stc[f];
+      const T* cf = reinterpret_cast<const T*>(cw[s % 3]);  // m[cls][i][j] at 4 cls + 2 i + j, then q or qf
+      const uint32_t wnow = wq0;
+      const V lnow = lq0;
+      T acc = T(0);
+      for (uint32_t it = tid; it < n_s; it += kRunThreads) {
+        const bool first = it == (uint32_t)tid;
+        const uint32_t w = first ? wnow : __ldg(mp + o_s + it);
+        const uint32_t i0 = w & 0xFFFu, i1 = (w >> 12) & 0xFFFu;
+        const unsigned cls = cg ^ (w >> 24);
+        const T a00 = cf[4 * cls], a01 = cf[4 * cls + 1], a10 = cf[4 * cls + 2], a11 = cf[4 * cls + 3];
+        if (MODE == 0) {
+          const T v0 = ar[i0], v1 = ar[i1];
+          const T o0 = fma(a00, v0, fma(a01, v1, v0)), o1 = fma(a10, v0, fma(a11, v1, v1));
+          ar[i0] = o0;
+          ar[i1] = o1;
+          if (lgp) {
+            V wv;
+            wv.x = o0;
+            wv.y = o1;
+            __stcs(lgp + o_s + it, wv);  // streamed: read back once by the reverse sweep
+          }
+        } else {
+          const T q01 = F32 ? cf[16 + cls] : cf[16 + 4 * cls + 1];
+          const V pp = first ? lnow : __ldcs(lgp + o_s + it);
+          const T w0 = ar[i0], w1 = ar[i1];
+          // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
+          acc = fma(q01, fma(w0, pp.y, -w1 * pp.x), acc);
+          ar[i0] = fma(a00, w0, fma(a01, w1, w0));
+          ar[i1] = fma(a10, w0, fma(a11, w1, w1));
+        }
+      }
+      if (ADJ) {
+        pend_w = n_s >= (uint32_t)kRunThreads ? kRunWarps : (int)((n_s + 31) / 32);
+        if (IRED) {
+          if (warp < pend_w) {  // warps past pend_w hold no items this step
+            int e;
+            const long long t = warp_sum_fixed((double)acc, &e);
+            if (lane == 0) {
+              wtot[s & 1][warp] = t;
+              wexp[s & 1][warp] = e;
+            }
+          }
+        } else {
+          red[s & 1][tid] = acc;
+        }
+      }
+      wq0 = wq1;
+      lq0 = lq1;
+      if (s + 2 < nb) {  // item tid of step s + 2
+        const int f2 = pos(s + 2);
+        if ((uint32_t)tid < stn[f2]) {
+          wq1 = __ldg(mp + sto[f2] + tid);
+          if (MODE == 3) lq1 = __ldcs(lgp + sto[f2] + tid);
+        }
+      }
+      __syncthreads();
+    }
+    if (ADJ && nb > 0) {
+      if (IRED) reduce_fixed(nb - 1, pend_w);
+      else reduce_block(nb - 1, pend_w);
+    }
+
+  } else
   for (int s = 0; s < nb; ++s) {
     uint32_t nxt = 0;
     if (s + 1 < nb && tid < kRunBlkWords)
@@ -406,7 +606,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       const bool tab = strs && B.lsa != kNoStrings;
       const uint32_t sa0 = tab ? B.lsa + Cs[B.ne][ke] : 0u;
       const uint32_t sb0 = tab ? B.lsb + Cs[B.no][ko] : 0u;
-      const float inv_co = 1.0f / (float)co;  // items < 2^24: the estimate is off by at most one
+      const float inv_co = __frcp_rn((float)co);  // items < 2^24: the estimate is off by at most one
       for (uint32_t it = tid; it < items; it += kRunThreads) {
         uint32_t ie = (uint32_t)((float)it * inv_co);
         if (ie * co > it) --ie;
@@ -503,7 +703,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     if (s + 1 < nb && tid < kRunBlkWords) reinterpret_cast<uint32_t*>(&sb[(s + 1) & 1])[tid] = nxt;
     __syncthreads();
   }
-  if (ADJ && nb > 0) reduce_block(nb - 1, pend_w);
+  if (ADJ && nb > 0 && !mp) reduce_block(nb - 1, pend_w);
   if (MODE == 4) return;  // read only
   T* pw = reinterpret_cast<T*>(psi);
   for (uint32_t m = tid; m < size; m += kRunThreads) {
@@ -514,6 +714,45 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       __stcg(psi + g, av[m]);
       if (MODE == 2) __stcg(lam + g, lv[m]);
     }
+  }
+}
+
+// Item maps (RunPart::mapbase): for the part representing each class, every
+// forward block's items in sweep order, one word each -- the item's two
+// members inside the part and the sign-class bits of its U strings -- computed
+// as the sweep itself would (outside strings, colex ranks, class masks).
+__global__ void __launch_bounds__(kRunThreads) k_run_itemmap(RunInfo run, const RunPart* __restrict__ parts,
+                                                             const RunBlk* __restrict__ blks, SecCompact cm,
+                                                             const uint16_t* __restrict__ strs, uint32_t* map) {
+  __shared__ uint32_t C[kBinom][kBinom];
+  __shared__ uint32_t Cs[kBinom][kBinom];
+  fill_binom(C);
+  fill_binom_prefix(Cs);
+  __syncthreads();
+  const RunPart P = parts[run.part0 + blockIdx.x];
+  if (!P.maprep) return;
+  uint64_t off = 0;
+  for (int b = run.b0; b < run.b1; ++b) {
+    const RunBlk& B = blks[b];
+    const int ke = P.ka - B.e0, ko = P.kb - B.o0;
+    if (ke < 0 || ke > B.ne || ko < 0 || ko > B.no) continue;
+    const uint32_t co = C[B.no][ko];
+    const uint32_t items = C[B.ne][ke] * co;
+    const bool tab = strs && B.lsa != kNoStrings;
+    const uint32_t sa0 = tab ? B.lsa + Cs[B.ne][ke] : 0u;
+    const uint32_t sb0 = tab ? B.lsb + Cs[B.no][ko] : 0u;
+    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+      const uint32_t ie = it / co, io = it - ie * co;
+      const uint32_t la = tab ? (uint32_t)__ldg(strs + sa0 + ie) : unrank_m(ie, B.epos, B.ne, ke, C);
+      const uint32_t lb = tab ? (uint32_t)__ldg(strs + sb0 + io) : unrank_m(io, B.opos, B.no, ko, C);
+      unsigned cls = 0;
+      if (B.nzc > 0) cls ^= par32s(B.zu[0][0] & la) ^ par32s(B.zu[0][1] & lb);
+      if (B.nzc > 1) cls ^= (par32s(B.zu[1][0] & la) ^ par32s(B.zu[1][1] & lb)) << 1;
+      const uint32_t i0 = (uint32_t)__ldg(cm.ra + (la | B.pu[0][0])) * P.cntb + __ldg(cm.ra + (lb | B.pu[0][1]));
+      const uint32_t i1 = (uint32_t)__ldg(cm.ra + (la | B.pu[1][0])) * P.cntb + __ldg(cm.ra + (lb | B.pu[1][1]));
+      map[P.mapbase + off + it] = i0 | (i1 << 12) | (cls << 24);
+    }
+    off += items;
   }
 }
 
@@ -1128,7 +1367,7 @@ uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged) {
 template <int MODE, typename T>
 static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, const RunPart* parts,
                           const RunBlk* blks, double* partial, int pmax, const SecCompact& cm, void* log,
-                          const uint16_t* strs, cudaStream_t s) {
+                          const uint16_t* strs, const uint32_t* map, cudaStream_t s) {
   using V = typename SCx<T>::V;
   static std::once_flag once;  // allow the opt-in shared memory size, once per process
   static cudaError_t attr = cudaSuccess;
@@ -1142,7 +1381,8 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
     if (smem > run_smem_max<MODE, T>() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
     k_sector_run<MODE, T><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
-                                                              blks, partial, pmax, cm, static_cast<V*>(log), strs);
+                                                              blks, partial, pmax, cm, static_cast<V*>(log), strs,
+                                                              (MODE == 0 || MODE == 3) ? map : nullptr);
     count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1153,22 +1393,22 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
                                int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
-                               cudaStream_t s) {
+                               const uint32_t* map, cudaStream_t s) {
   if (nblk <= 0 || nruns <= 0) return cudaSuccess;
   if (!cm.ra || (log && !realst)) return cudaErrorInvalidValue;
   const int prof_slot_ = prof_pre(adj ? QF_K_ADJ_SPARSE : QF_K_SPARSE, s);
   const int mode = !adj ? 0 : !realst ? 2 : log ? 3 : 1;
   cudaError_t e;
   if (dt == QF_C128)
-    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
-      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
-      : mode == 2 ? runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
-                  : runs_t<3, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s);
+    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
+      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
+      : mode == 2 ? runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
+                  : runs_t<3, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s);
   else
-    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
-      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
-      : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s)
-                  : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, s);
+    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
+      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
+      : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
+                  : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s);
   if (e == cudaSuccess && adj) {
     k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
@@ -1178,6 +1418,20 @@ cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool
   return e;
 }
 
+cudaError_t launch_run_itemmaps(const RunInfo* runs, int nruns, const RunPart* parts, const RunBlk* blks,
+                                const SecCompact& cm, const uint16_t* strs, uint32_t* map, cudaStream_t s) {
+  if (!cm.ra || !map) return cudaErrorInvalidValue;
+  for (int r = 0; r < nruns; ++r) {
+    if (runs[r].nparts <= 0) continue;
+    if (runs[r].maxsize > kMapMaxPart) return cudaErrorInvalidValue;
+    k_run_itemmap<<<runs[r].nparts, kRunThreads, 0, s>>>(runs[r], parts, blks, cm, strs, map);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_sector_overlaps(void* psi, qf_dtype dt, const RunInfo* runs, int nruns, const RunPart* parts,
                                   const RunBlk* blks, int nblk, double* partial, int pmax, double* out,
                                   const SecCompact& cm, const uint16_t* strs, cudaStream_t s) {
@@ -1185,8 +1439,8 @@ cudaError_t launch_sector_overlaps(void* psi, qf_dtype dt, const RunInfo* runs, 
   if (!cm.ra) return cudaErrorInvalidValue;
   const int prof_slot_ = prof_pre(QF_K_ADJ_SPARSE, s);
   cudaError_t e = (dt == QF_C128)
-                      ? runs_t<4, double>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, s)
-                      : runs_t<4, float>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, s);
+                      ? runs_t<4, double>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, nullptr, s)
+                      : runs_t<4, float>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, nullptr, s);
   if (e == cudaSuccess) {
     k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
