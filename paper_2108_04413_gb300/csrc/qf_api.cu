@@ -769,12 +769,23 @@ qf_status ensure_direct(qf_state* st, ExpPlan* p) {
     return o;
   };
   const std::vector<float> fab = f32(h.wab), faa = f32(h.waa), fbb = f32(h.wbb);
+  auto ds = [](const std::vector<double>& v) {  // (hi, lo) float pairs
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float hi = (float)v[i];
+      o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+    }
+    return o;
+  };
+  const std::vector<float2> dab = ds(h.wab), daa = ds(h.waa), dbb = ds(h.wbb);
   // one buffer: doubles, floats, fixed point (each part 256-byte aligned)
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t o_wab = 0, o_waa = o_wab + al(h.wab.size() * 8), o_wbb = o_waa + al(h.waa.size() * 8),
                o_fab = o_wbb + al(h.wbb.size() * 8), o_faa = o_fab + al(fab.size() * 4),
                o_fbb = o_faa + al(faa.size() * 4), o_s1a = o_fbb + al(fbb.size() * 4),
-               o_s1b = o_s1a + al(f1a.size() * 8), o_dg = o_s1b + al(f1b.size() * 8), total = o_dg + al(fdg.size() * 8);
+               o_s1b = o_s1a + al(f1a.size() * 8), o_dg = o_s1b + al(f1b.size() * 8),
+               o_dab = o_dg + al(fdg.size() * 8), o_daa = o_dab + al(dab.size() * 8), o_dbb = o_daa + al(daa.size() * 8),
+               total = o_dbb + al(dbb.size() * 8);
   std::vector<char> buf(total, 0);
   std::memcpy(buf.data() + o_wab, h.wab.data(), h.wab.size() * 8);
   std::memcpy(buf.data() + o_waa, h.waa.data(), h.waa.size() * 8);
@@ -785,6 +796,9 @@ qf_status ensure_direct(qf_state* st, ExpPlan* p) {
   std::memcpy(buf.data() + o_s1a, f1a.data(), f1a.size() * 8);
   std::memcpy(buf.data() + o_s1b, f1b.data(), f1b.size() * 8);
   std::memcpy(buf.data() + o_dg, fdg.data(), fdg.size() * 8);
+  std::memcpy(buf.data() + o_dab, dab.data(), dab.size() * 8);
+  std::memcpy(buf.data() + o_daa, daa.data(), daa.size() * 8);
+  std::memcpy(buf.data() + o_dbb, dbb.data(), dbb.size() * 8);
   if (cudaMalloc(&p->d_direct, total) != cudaSuccess) {
     cudaGetLastError();
     p->d_direct = nullptr;
@@ -806,6 +820,9 @@ qf_status ensure_direct(qf_state* st, ExpPlan* p) {
   d.s1a = reinterpret_cast<const long long*>(b + o_s1a);
   d.s1b = reinterpret_cast<const long long*>(b + o_s1b);
   d.dg = reinterpret_cast<const long long*>(b + o_dg);
+  d.dab = reinterpret_cast<const float2*>(b + o_dab);
+  d.daa = reinterpret_cast<const float2*>(b + o_daa);
+  d.dbb = reinterpret_cast<const float2*>(b + o_dbb);
   d.inv_fix = std::ldexp(1.0, -e);
   p->direct = 1;
   return QF_OK;
@@ -2200,9 +2217,14 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
       qf_status ds = ensure_direct(st, pm);
       if (ds != QF_OK) return ds;
     }
+    // double-single pair products (complex128, QF_HPSI_DS): the amplitudes' float
+    // split sits in the compact buffer's second half, unused by a packed real lambda
+    float2* split = (st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS)
+                        ? reinterpret_cast<float2*>(static_cast<char*>(cpsi) + members * st->elem())
+                        : nullptr;
     if (lreal && pm->direct == 1)
       QF_CUDA(qf::launch_sector_hpsi_direct(cpsi, st->dt, sp, pm->dtab, cm, st->d_partials, st->d_counter, d_e,
-                                            kPartials / 2, st->stream));
+                                            kPartials / 2, split, st->stream));
     else
       QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_seclarge, p->nseclarge,
                                      p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,

@@ -263,6 +263,9 @@ struct SecDirect {
   const float* fab;            // FP32 copies (complex64)
   const float* faa;
   const float* fbb;
+  const float2* dab;           // double-single copies (hi, lo) (complex128, QF_HPSI_DS)
+  const float2* daa;
+  const float2* dbb;
   const long long* s1a;        // alpha single o -> v: A at [(o * ne + v) * (n + 1)], B[r] at + 1 + r
   const long long* s1b;        // beta single likewise ((o * no + v) * (n + 1))
   const long long* dg;         // K, then U[r] at 1 + r, then V[r][s] at 1 + n + r * n + s (r < s)
@@ -347,10 +350,12 @@ uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged);
 // most CTAs the reduction may use (partials holds 2 * nblocks doubles).
 // lambda = H psi on the compact layout of a real state through the direct tables
 // (lambda packed into psi's imaginary slots); out[0] = <psi|lambda>,
-// out[1] = <psi|psi>, partials holds 2 * nblocks doubles.
+// out[1] = <psi|psi>, partials holds 2 * nblocks doubles.  split: for a
+// QF_C128 state, scratch of one float2 per member that turns on double-single
+// pair products (QF_HPSI_DS); NULL keeps them in FP64.
 cudaError_t launch_sector_hpsi_direct(void* cpsi, qf_dtype dt, const SecSpace& sp, const SecDirect& d,
                                       const SecCompact& cm, double* partials, unsigned* counter, double* out,
-                                      int nblocks, cudaStream_t s);
+                                      int nblocks, float2* split, cudaStream_t s);
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
                                const SecRank& rk, const SecGroup* large, int nlarge,
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,

@@ -1108,12 +1108,55 @@ template <> struct PairAcc<double> {
   __device__ __forceinline__ void fold(double&) {}
 };
 
-template <typename T>
+// Double-single pair products (complex128, QF_HPSI_DS): a weight and an amplitude
+// each as a float pair hi + lo (about 48 significant bits); the product keeps the
+// exact error of hi * hi and both cross terms, the float-pair sum takes it through
+// an error-free TwoSum, and the sum is folded into the member's FP64 sum after each
+// innermost loop (at most C(16, 2)^2 / 16 products in between).  The rounded
+// operations are explicit so that no multiply is fused into the TwoSum.
+struct DsAcc {
+  float sh = 0.0f, sl = 0.0f;
+  __device__ __forceinline__ void add(float2 w, float2 v) {
+    const float ph = __fmul_rn(w.x, v.x);
+    float pl = fmaf(w.x, v.x, -ph);
+    pl = fmaf(w.x, v.y, pl);
+    pl = fmaf(w.y, v.x, pl);
+    const float s = __fadd_rn(sh, ph);
+    const float bp = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(ph, bp));
+    sl = __fadd_rn(sl, __fadd_rn(err, pl));
+    sh = s;
+  }
+  __device__ __forceinline__ void fold(double& lx) {
+    lx += (double)sh + (double)sl;
+    sh = 0.0f;
+    sl = 0.0f;
+  }
+};
+__device__ __forceinline__ float2 flip_sign2(float2 w, uint32_t s) {
+  return make_float2(flip_sign(w.x, s), flip_sign(w.y, s));
+}
+
+// (hi, lo) float split of every member's real amplitude (packed state: psi at 2 m).
+__global__ void k_split_real(const double* __restrict__ st, float2* __restrict__ out, uint64_t members) {
+  for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < members;
+       m += (uint64_t)gridDim.x * blockDim.x) {
+    const double v = st[2 * m];
+    const float hi = __double2float_rn(v);
+    out[m] = make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+}
+
+template <typename T, bool DS>
 __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, uint32_t cnt_e, uint32_t cnt_o,
                                                             int ke, int ko, const uint16_t* __restrict__ ra,
                                                             const uint16_t* __restrict__ rb, double* partials,
-                                                            unsigned* counter, double* out) {
+                                                            unsigned* counter, double* out,
+                                                            const float2* __restrict__ split) {
   __shared__ uint32_t C[kBinom][kBinom];
+  // each thread's beta singles (entry k of thread t at bsl[k * 256 + t]): the
+  // flipped string's rank | weight column o2 * no + v2 << 14 | sign bit << 31
+  extern __shared__ uint32_t bsl[];
   fill_binom(C);
   __syncthreads();
   const int n = d.n, ne = d.ne, no = d.no;
@@ -1143,6 +1186,7 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
     const double self = (double)ps[2 * (size_t)it];
     double lx = 0.0, lxs = 0.0;  // lxs: fixed-point weights times psi (units of 2^-e)
     PairAcc<T> pa;
+    DsAcc da;
     // x = 0: K + sum U[r] + sum V[r][s] over occupied r < s
     long long dsum = __ldg(d.dg);
     for (uint32_t m = c; m; m &= m - 1) {
@@ -1179,26 +1223,40 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
         lxs = fma(__ll2double_rn(w), (double)ps[2 * idx], lxs);
       }
     }
-    // opposite-spin doubles: alpha o -> v, beta o2 -> v2
+    // opposite-spin doubles: alpha o -> v, beta o2 -> v2; the member's beta singles
+    // are listed once and reused under each of its alpha singles
+    uint32_t* bl = bsl + threadIdx.x;
+    int nbs = 0;
+    for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
+      const int o2 = __ffs((int)m2) - 1;
+      const uint32_t lbo = lb ^ (1u << o2);
+      const uint32_t so = (ppb >> o2) & 1u;
+      for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
+        const int v2 = __ffs((int)n2) - 1;
+        bl[256 * nbs++] = (uint32_t)__ldg(rb + (lbo | (1u << v2))) | ((uint32_t)(o2 * no + v2) << 14) |
+                          ((so ^ ((ppb >> v2) & 1u)) << 31);
+      }
+    }
     for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
       const int o = __ffs((int)m1) - 1;
       for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
         const int v = __ffs((int)n1) - 1;
         const uint32_t sa = ((ppa >> o) ^ (ppa >> v)) & 1u;
         const size_t rowa = (size_t)__ldg(ra + (la ^ (1u << o) ^ (1u << v))) * cnt_o;
-        const T* wrow = wab + (size_t)(o * ne + v) * (no * no);
-        for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
-          const int o2 = __ffs((int)m2) - 1;
-          const uint32_t s3 = sa ^ ((ppb >> o2) & 1u);
-          const uint32_t lbo = lb ^ (1u << o2);
-          const T* w2 = wrow + o2 * no;
-          for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
-            const int v2 = __ffs((int)n2) - 1;
-            const T w = flip_sign(__ldg(w2 + v2), s3 ^ ((ppb >> v2) & 1u));
-            pa.add(w, ps[2 * (rowa + __ldg(rb + (lbo | (1u << v2))))], lx);
-          }
+        const size_t wo = (size_t)(o * ne + v) * (no * no);
+        const T* wrow = wab + wo;
+        const float2* drow = d.dab + wo;
+        for (int k = 0; k < nbs; ++k) {
+          const uint32_t e = bl[256 * k];
+          const size_t idx = rowa + (e & 0x3FFFu);
+          const uint32_t col = (e >> 14) & 0xFFu, sg = sa ^ (e >> 31);
+          if (DS)
+            da.add(flip_sign2(__ldg(drow + col), sg), __ldg(split + idx));
+          else
+            pa.add(flip_sign(__ldg(wrow + col), sg), ps[2 * idx], lx);
         }
-        pa.fold(lx);
+        if (DS) da.fold(lx);
+        else pa.fold(lx);
       }
     }
     // same-spin doubles: occupied o1 < o2 -> empty v1 < v2
@@ -1208,19 +1266,24 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
         const int o1 = __ffs((int)m1) - 1;
         const uint32_t so = ((ppa >> o1) ^ (ppa >> o2)) & 1u;
         const uint32_t lao = la ^ (1u << o1) ^ (1u << o2);
-        const T* wrow = waa + (size_t)(o1 + o2 * (o2 - 1) / 2) * pe;
+        const size_t wo = (size_t)(o1 + o2 * (o2 - 1) / 2) * pe;
         for (uint32_t n2 = va; n2; n2 &= n2 - 1) {
           const int v2 = __ffs((int)n2) - 1;
           const uint32_t s2 = so ^ ((ppa >> v2) & 1u);
-          const T* w2 = wrow + v2 * (v2 - 1) / 2;
+          const size_t w2 = wo + v2 * (v2 - 1) / 2;
           const uint32_t lav = lao | (1u << v2);
           for (uint32_t n1 = va & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
             const int v1 = __ffs((int)n1) - 1;
-            const T w = flip_sign(__ldg(w2 + v1), s2 ^ ((ppa >> v1) & 1u));
-            pa.add(w, ps[2 * ((size_t)__ldg(ra + (lav | (1u << v1))) * cnt_o + io)], lx);
+            const uint32_t sg = s2 ^ ((ppa >> v1) & 1u);
+            const size_t idx = (size_t)__ldg(ra + (lav | (1u << v1))) * cnt_o + io;
+            if (DS)
+              da.add(flip_sign2(__ldg(d.daa + w2 + v1), sg), __ldg(split + idx));
+            else
+              pa.add(flip_sign(__ldg(waa + w2 + v1), sg), ps[2 * idx], lx);
           }
         }
-        pa.fold(lx);
+        if (DS) da.fold(lx);
+        else pa.fold(lx);
       }
     }
     for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
@@ -1229,19 +1292,24 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
         const int o1 = __ffs((int)m1) - 1;
         const uint32_t so = ((ppb >> o1) ^ (ppb >> o2)) & 1u;
         const uint32_t lbo = lb ^ (1u << o1) ^ (1u << o2);
-        const T* wrow = wbb + (size_t)(o1 + o2 * (o2 - 1) / 2) * po;
+        const size_t wo = (size_t)(o1 + o2 * (o2 - 1) / 2) * po;
         for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
           const int v2 = __ffs((int)n2) - 1;
           const uint32_t s2 = so ^ ((ppb >> v2) & 1u);
-          const T* w2 = wrow + v2 * (v2 - 1) / 2;
+          const size_t w2 = wo + v2 * (v2 - 1) / 2;
           const uint32_t lbv = lbo | (1u << v2);
           for (uint32_t n1 = vb & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
             const int v1 = __ffs((int)n1) - 1;
-            const T w = flip_sign(__ldg(w2 + v1), s2 ^ ((ppb >> v1) & 1u));
-            pa.add(w, ps[2 * (rowself + __ldg(rb + (lbv | (1u << v1))))], lx);
+            const uint32_t sg = s2 ^ ((ppb >> v1) & 1u);
+            const size_t idx = rowself + __ldg(rb + (lbv | (1u << v1)));
+            if (DS)
+              da.add(flip_sign2(__ldg(d.dbb + w2 + v1), sg), __ldg(split + idx));
+            else
+              pa.add(flip_sign(__ldg(wbb + w2 + v1), sg), ps[2 * idx], lx);
           }
         }
-        pa.fold(lx);
+        if (DS) da.fold(lx);
+        else pa.fold(lx);
       }
     }
     lx = fma(lxs, d.inv_fix, lx);
@@ -1513,18 +1581,42 @@ static cudaError_t hpsi_dispatch(const void* psi, void* lam, bool realst, bool n
 
 cudaError_t launch_sector_hpsi_direct(void* cpsi, qf_dtype dt, const SecSpace& sp, const SecDirect& d,
                                       const SecCompact& cm, double* partials, unsigned* counter, double* out,
-                                      int nblocks, cudaStream_t s) {
+                                      int nblocks, float2* split, cudaStream_t s) {
   if (d.n > 32 || d.ne != sp.ne || d.no != sp.no || sp.ne > 16) return cudaErrorInvalidValue;
+  // the beta-single lists: ko (no - ko) entries per thread (at most 64 at 32 qubits);
+  // partner ranks must fit 14 bits
+  if (sp.cnt_o > (1u << 14)) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)std::max(1, sp.ko * (sp.no - sp.ko)) * 256 * sizeof(uint32_t);
   const int prof_slot_ = prof_pre(QF_K_HPSI, s);
   const uint64_t items = (uint64_t)sp.cnt_e * sp.cnt_o;
-  if (dt == QF_C128) {
-    const auto k = k_sector_hpsi_direct<double>;
-    k<<<hpsi_grid(k, items, nblocks), 256, 0, s>>>(static_cast<double*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke,
-                                                    sp.ko, cm.ra, cm.rb, partials, counter, out);
+  auto grid = [&](auto kernel) {  // every CTA the SMs hold at this shared-memory size
+    static std::once_flag once;
+    std::call_once(once, [&] {
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * (int)sizeof(uint32_t));
+    });
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
+    const uint64_t want = (items + 255) / 256;
+    const uint64_t res = (uint64_t)std::max(1, sms) * (uint64_t)std::max(1, per_sm);
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, std::min<uint64_t>(res, (uint64_t)nblocks)));
+  };
+  if (dt == QF_C128 && split) {
+    k_split_real<<<(unsigned)std::min<uint64_t>((items + 255) / 256, 4096), 256, 0, s>>>(
+        static_cast<const double*>(cpsi), split, items);
+    count_launch();
+    const auto k = k_sector_hpsi_direct<double, true>;
+    k<<<grid(k), 256, smem, s>>>(static_cast<double*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke, sp.ko, cm.ra, cm.rb,
+                                 partials, counter, out, split);
+  } else if (dt == QF_C128) {
+    const auto k = k_sector_hpsi_direct<double, false>;
+    k<<<grid(k), 256, smem, s>>>(static_cast<double*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke, sp.ko, cm.ra, cm.rb,
+                                 partials, counter, out, nullptr);
   } else {
-    const auto k = k_sector_hpsi_direct<float>;
-    k<<<hpsi_grid(k, items, nblocks), 256, 0, s>>>(static_cast<float*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke, sp.ko,
-                                                    cm.ra, cm.rb, partials, counter, out);
+    const auto k = k_sector_hpsi_direct<float, false>;
+    k<<<grid(k), 256, smem, s>>>(static_cast<float*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke, sp.ko, cm.ra, cm.rb,
+                                 partials, counter, out, nullptr);
   }
   const cudaError_t e = cudaGetLastError();
   prof_post(prof_slot_, s);
