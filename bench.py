@@ -34,8 +34,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-FP64_FMA_PER_CLK_PER_SM = 2  # GB300: 1.25 TFLOP/s nominal FP64 = 152 SMs * 2 FMA * 2 flop * ~2.06 GHz
-N_SMS = 152
+FP64_FMA_PER_CLK_PER_SM = 2  # GB300 CUDA cores: 2 FP64 FMA per clock per SM (nominal, for context)
 
 
 def parse_args():
@@ -50,7 +49,13 @@ def parse_args():
     return ap.parse_args()
 
 
+_FP64 = {}  # FP64 peaks measured once per process by the library's probe
+
+
 def peaks():
+    """Roofline denominators: HBM and bf16 from MEASURED_PEAKS.json (else the
+    fallback figures); FP64 FMA and FP64 MMA measured in this process on this GPU
+    (qf_probe_fp64_peaks), with the derived nominal FMA figure for context."""
     p = {"hbm_gbs": 6782.8, "bf16_tflops": 1939.0, "sm_max_mhz": 2070.0, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -58,8 +63,21 @@ def peaks():
             m = json.load(f)
         p.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz") if k in m})
         p["source"] = "measured"
-    p["fp64_tflops"] = N_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    if not _FP64:
+        import torch
+
+        from paper_2108_04413_gb300 import qf
+        fma, dmma = qf.probe_fp64_peaks(torch.cuda.current_stream().cuda_stream)
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        _FP64.update({"fma_tflops": fma / 1e12, "dmma_tflops": dmma / 1e12, "sms": sms,
+                      "nominal_fma_tflops": sms * FP64_FMA_PER_CLK_PER_SM * 2 * p["sm_max_mhz"] * 1e6 / 1e12})
+    p["fp64_tflops"] = _FP64["fma_tflops"]
+    p["fp64"] = dict(_FP64)
     return p
+
+
+FP64_NOTE = ("FP64 FMA throughput measured in this run by qf_probe_fp64_peaks (independent FMA chains on every "
+             "SM, CUDA events)")
 
 
 # ----------------------------------------------------------------------------- workloads
@@ -371,7 +389,7 @@ def run_gpu(args, rank, world, local, pg):
                 "algorithmic": (f"{fl:.4g} FP64 flop per sweep: {items} (member pair, excitation) items x "
                                 + ("(4 multiply-adds rotating lambda + 2 for the overlap; psi read from the "
                                    "forward log)" if rev else "4 multiply-adds rotating psi") + " x 2 flop"),
-                "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock (derived)",
+                "peak_note": FP64_NOTE,
                 "note": "one launch per run of excitations; the compact sector state stays in L2"}
     if dom == "hpsi":
         # the dUCC state stays in one (alpha, beta) sector, where H|psi> runs on members only
@@ -379,11 +397,14 @@ def run_gpu(args, rank, world, local, pg):
         pairs, members = sector_pairs(w["terms"], n, na, bin(w["det"]).count("1") - na)
         avg_s = per_kind[dom]["ms"] / per_kind[dom]["launches"] / 1e3
         fl = 2 * pairs + 4 * members
-        roof = {"kernel": "k_sector_hpsi", "bound": "alu", "achieved": fl / avg_s / 1e12, "peak": pk["fp64_tflops"],
+        roof = {"kernel": "k_sector_hpsi_direct", "bound": "alu", "achieved": fl / avg_s / 1e12,
+                "peak": pk["fp64_tflops"],
                 "unit": "TFLOP/s", "frac": fl / avg_s / 1e12 / pk["fp64_tflops"], "traffic": None,
                 "algorithmic": (f"{fl:.4g} FP64 flop per launch: one multiply-add per connected (sector member, "
                                 f"X group) pair ({pairs} pairs, {members} members)"),
-                "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock (derived)"}
+                "peak_note": FP64_NOTE + (("; in the default double-single mode the pair products run on the FP32 "
+                                           "pipe, so frac compares with the native-FP64 roofline of the same work")
+                                          if args.dtype == "c128" else "")}
 
     roof["traffic"] = measured_traffic(roof.get("kernel", ""))
     out = {
@@ -397,8 +418,9 @@ def run_gpu(args, rank, world, local, pg):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f64 (sector H|psi> weight sums in exact 64-bit fixed point)"
-                  if args.dtype == "c128" else "f32 state, f64 reductions"),
+        "dtype": ("f64 (amplitudes, rotations, reductions; sector H|psi> pair products in double-single, "
+                  "about 48-bit, on the FP32 pipe: the library's default QF_HPSI_DS mode; hpsi_fp64_mode times "
+                  "FP64 products)" if args.dtype == "c128" else "f32 state, f64 reductions"),
         "data": "synthetic (seeded integrals, dUCCSD amplitudes)",
         "config": {
             "workload": f"{n}-qubit dUCCSD energy + adjoint gradient ({args.workload})",
@@ -414,6 +436,7 @@ def run_gpu(args, rank, world, local, pg):
         "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": clk,
+        "fp64_peaks": pk["fp64"],
     }
     if rank == 0 and not args.no_extras:
         out["e2e"] = e2e_leg(st, w, args, stats, stream)
@@ -442,9 +465,8 @@ def roofline_for(kind, rec, w, stats, n, S, pk, dtype):
         return {"kernel": "k_hpsi", "bound": "alu", "achieved": ach, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                 "frac": ach / pk["fp64_tflops"], "traffic": None,
                 "algorithmic": f"{fl:.4g} FP64-equivalent flop per launch (one multiply-add per X group and amplitude)",
-                "peak_note": ("FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock (derived); the default "
-                              "double-single kernel runs these multiply-adds on the FP32 pipe, so frac is measured "
-                              "against the native-FP64 roofline of the same work")}
+                "peak_note": (FP64_NOTE + "; the default double-single kernel runs these multiply-adds on the FP32 "
+                              "pipe, so frac is measured against the native-FP64 roofline of the same work")}
     if kind in ("hpsi",):
         by = (len(stats) + 2) * N * S
         ach = by / avg_s / 1e9

@@ -237,6 +237,17 @@ qf_status qf_profile_end(void);
 qf_status qf_expectation_noalloc(const void* amplitudes, int n, qf_dtype dtype, void* stream,
                                  const qf_term* terms, size_t n_terms, double* re, double* im);
 
+/* Measured FP64 arithmetic peaks of the current device (the paper has no
+ * counterpart: a measurement helper for roofline denominators; GB300 runs FP64 at
+ * a small fraction of its FP32 rate, so these bound the complex128 kernels).
+ *   fma_flops: FP64 fused multiply-add throughput of the CUDA cores;
+ *   dmma_flops: FP64 matrix multiply-accumulate throughput (mma.sync m8n8k4);
+ * both in flop/s (one multiply-add = 2 flop), from kernels of independent
+ * operations on every SM, each timed with CUDA events on `stream` after a
+ * warm-up launch.  Either pointer may be NULL.  Allocates a few KB of scratch,
+ * takes tens of milliseconds and synchronises the stream. */
+qf_status qf_probe_fp64_peaks(void* stream, double* fma_flops, double* dmma_flops);
+
 /* Self-test of the bounded device wait used by the grid barriers of the
  * persistent kernels: one thread waits up to limit_s seconds (0 < limit_s <= 10)
  * on a word that nothing changes.  Returns QF_ETIMEOUT when the wait gave up as

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqf.so")
-SOURCES = ["qf_kernels.cu", "qf_api.cu", "qf_noalloc.cu", "qf_sector.cu"]
+SOURCES = ["qf_kernels.cu", "qf_api.cu", "qf_noalloc.cu", "qf_sector.cu", "qf_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

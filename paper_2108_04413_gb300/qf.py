@@ -55,6 +55,7 @@ _SIGS = {
     "qf_profile_end": (ctypes.c_int, []),
     "qf_expectation_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _sz, _dp, _dp]),
     "qf_selftest_bounded_wait": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "qf_probe_fp64_peaks": (ctypes.c_int, [_vp, _dp, _dp]),
     "qf_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -109,6 +110,13 @@ KIND_NAMES = {K_SET: "set", K_ROT: "rot", K_TILE: "tile", K_SPARSE: "sparse", K_
 def selftest_bounded_wait(stream_ptr: int, limit_s: float) -> int:
     """Runs the bounded-wait self-test; returns the status (QF_ETIMEOUT expected)."""
     return int(_lib.qf_selftest_bounded_wait(_vp(stream_ptr), float(limit_s)))
+
+
+def probe_fp64_peaks(stream_ptr: int):
+    """(FP64 FMA flop/s, FP64 MMA flop/s) measured on the current device."""
+    a, b = _d(), _d()
+    _check(_lib.qf_probe_fp64_peaks(_vp(stream_ptr), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def profile_begin(mask: int = K_ALL) -> None:

@@ -625,3 +625,14 @@ def test_sector_hpsi_chunk_tables_for_non_molecular_terms(dtype):
             assert abs(e - e_ref) < TOL_E_C64
             assert np.linalg.norm(grad - g_ref) <= TOL_G_C64 * np.linalg.norm(g_ref)
     st.close()
+
+
+def test_fp64_peak_probe():
+    """The roofline probe returns the FP64 FMA rate of the CUDA cores within a
+    plausible range for this part (2 FMA per clock per SM, nominal 1.26 TFLOP/s
+    at 2070 MHz on 152 SMs) and a positive FP64 MMA rate."""
+    fma, dmma = qf.probe_fp64_peaks(torch.cuda.current_stream().cuda_stream)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 2 * 2 * 2.1e9
+    assert 0.2 * nominal < fma < 1.2 * nominal, (fma, nominal)
+    assert dmma > 0.0
