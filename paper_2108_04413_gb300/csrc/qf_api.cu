@@ -377,6 +377,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     g.chunk0 = (int)ech.size();
     g.flags = 0;
     for (size_t i : idx) g.flags |= (popc(terms[i].x & terms[i].z) & 1) ? 2 : 1;
+    if (idx.size() == 1) g.flags |= 4;  // one term: its table is +-tab[0] (k_expect_tiled)
     // A chunk holds terms whose Z masks are combinations (over GF(2)) of at most
     // kChunkTerms basis masks: the table entry for the basis parities `pat` sums
     // the terms with the sign (-1)^{popc(a_t & pat)}, a_t the term's coordinates.

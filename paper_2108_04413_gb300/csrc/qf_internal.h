@@ -73,7 +73,7 @@ struct ExpGroup {
   int h;        // highest set bit of x, -1 for the diagonal (x = 0) group
   int nchunk;
   int chunk0;   // first chunk index
-  int flags;    // bit0: has even-y terms, bit1: has odd-y terms
+  int flags;    // bit0: has even-y terms, bit1: has odd-y terms, bit2: a single term
 };
 
 struct ExpChunk {

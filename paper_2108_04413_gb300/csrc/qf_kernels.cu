@@ -493,6 +493,116 @@ __global__ void __launch_bounds__(256) k_expect(const typename Cx<T>::V* __restr
   grid_finish(acc, partials, counter, out);
 }
 
+// Tiled form for n > 10: a CTA takes tiles of 256 x P pairs of one X group
+// (P = 4; 8 was slower for complex64 at 28 qubits), reads the group's descriptor
+// once per tile, and every thread issues the loads of its P pairs before using
+// them (P times the loads in flight of the flat loop).  A group of one term
+// (flags bit 2: its table is +-tab[0]) puts the sign on the amplitude and the
+// weight on the tile's sum, so a pair costs two multiply-adds.
+template <typename T> struct ExpTile {
+  static constexpr int P = 4;
+  static constexpr int LOG = 10;  // log2(256 P)
+};
+constexpr int kExpTileLogMax = 10;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_expect_tiled(const typename Cx<T>::V* __restrict__ psi, int n,
+                                                      const ExpGroup* __restrict__ groups, int ngroups,
+                                                      const ExpChunk* __restrict__ chunks, double* partials,
+                                                      unsigned* counter, double* out) {
+  using V = typename Cx<T>::V;
+  constexpr int kExpPairs = ExpTile<T>::P, kExpTileLog = ExpTile<T>::LOG;
+  const int tb = n - 1 - kExpTileLog;  // log2(tiles per group)
+  const uint64_t ntiles = (uint64_t)ngroups << tb;
+  double acc = 0.0;
+  float facc = 0.f;  // complex64: FP32 sums folded into acc once per tile
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int g = (int)(tile >> tb);
+    const uint64_t p0 = ((tile & ((1ull << tb) - 1)) << kExpTileLog) + threadIdx.x;
+    const ExpGroup G = groups[g];
+    if (G.h < 0) {  // x = 0: |psi_b|^2 of both amplitudes of each pair
+#pragma unroll
+      for (int k = 0; k < kExpPairs; ++k) {
+        const uint64_t b0 = (p0 + 256 * k) << 1;
+        const V u0 = psi[b0], u1 = psi[b0 | 1ull];
+        for (int c = 0; c < G.nchunk; ++c) {
+          const ExpChunk* C = chunks + G.chunk0 + c;
+          unsigned i0 = 0, i1 = 0;
+#pragma unroll
+          for (int t = 0; t < kChunkTerms; ++t) {
+            const uint64_t zt = C->z[t];
+            const unsigned pb = par64(zt & b0);
+            i0 |= pb << t;
+            i1 |= (pb ^ (unsigned)(zt & 1ull)) << t;
+          }
+          if constexpr (sizeof(T) == 4) {
+            facc = fmaf(C->ftab[i0].x, fmaf(u0.x, u0.x, u0.y * u0.y), facc);
+            facc = fmaf(C->ftab[i1].x, fmaf(u1.x, u1.x, u1.y * u1.y), facc);
+          } else {
+            acc = fma(C->tab[i0].x, fma((double)u0.x, u0.x, (double)u0.y * u0.y), acc);
+            acc = fma(C->tab[i1].x, fma((double)u1.x, u1.x, (double)u1.y * u1.y), acc);
+          }
+        }
+      }
+    } else {
+      uint64_t b[kExpPairs];
+      V u[kExpPairs], v[kExpPairs];
+#pragma unroll
+      for (int k = 0; k < kExpPairs; ++k) {
+        b[k] = ins0(p0 + 256 * k, G.h);
+        u[k] = psi[b[k]];
+        v[k] = psi[b[k] ^ G.x];
+      }
+      if (G.flags & 4) {  // one term: D = (-1)^{popc(z & b)} tab[0]
+        const ExpChunk* C = chunks + G.chunk0;
+        const uint64_t z = C->z[0];
+        T gr = T(0), gi = T(0);
+#pragma unroll
+        for (int k = 0; k < kExpPairs; ++k) {
+          const unsigned sg = par64(z & b[k]);
+          const T ux = sg ? -u[k].x : u[k].x, uy = sg ? -u[k].y : u[k].y;
+          if (G.flags & 1) gr = fma(ux, v[k].x, fma(uy, v[k].y, gr));
+          if (G.flags & 2) gi = fma(uy, v[k].x, fma(-ux, v[k].y, gi));
+        }
+        if constexpr (sizeof(T) == 4) {
+          const float2 D = C->ftab[0];
+          facc = fmaf(D.x, gr, fmaf(D.y, gi, facc));
+        } else {
+          const double2 D = C->tab[0];
+          acc = fma(D.x, gr, fma(D.y, gi, acc));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kExpPairs; ++k) {
+          T rew = 0, imw = 0;
+          if (G.flags & 1) rew = fma(u[k].x, v[k].x, u[k].y * v[k].y);
+          if (G.flags & 2) imw = fma(u[k].y, v[k].x, -u[k].x * v[k].y);
+          for (int c = 0; c < G.nchunk; ++c) {
+            const ExpChunk* C = chunks + G.chunk0 + c;
+            unsigned idx = 0;
+#pragma unroll
+            for (int t = 0; t < kChunkTerms; ++t) idx |= par64(C->z[t] & b[k]) << t;
+            if constexpr (sizeof(T) == 4) {
+              const float2 D = C->ftab[idx];
+              if (G.flags & 1) facc = fmaf(D.x, rew, facc);
+              if (G.flags & 2) facc = fmaf(D.y, imw, facc);
+            } else {
+              const double2 D = C->tab[idx];
+              if (G.flags & 1) acc = fma(D.x, rew, acc);
+              if (G.flags & 2) acc = fma(D.y, imw, acc);
+            }
+          }
+        }
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      acc += (double)facc;
+      facc = 0.f;
+    }
+  }
+  grid_finish(acc, partials, counter, out);
+}
+
 // ---------------------------------------------------------------------------
 // lam = H psi (gather form) fused with out[0] = Re <psi|lam>, out[1] = <psi|psi>
 //
@@ -1240,12 +1350,22 @@ cudaError_t launch_expect(const void* psi, int n, qf_dtype dt, const ExpGroup* g
                           const ExpChunk* chunks, double* partials, unsigned* counter, double* out, int nblocks,
                           cudaStream_t s) {
   const int prof_slot_ = prof_pre(QF_K_EXPECT, s);
-  if (dt == QF_C128)
-    k_expect<double><<<nblocks, 256, 0, s>>>(static_cast<const double2*>(psi), n, groups, ngroups, chunks,
-                                             partials, counter, out);
-  else
-    k_expect<float><<<nblocks, 256, 0, s>>>(static_cast<const float2*>(psi), n, groups, ngroups, chunks, partials,
-                                            counter, out);
+  const bool tiled = n > kExpTileLogMax;  // at least one whole tile per group
+  if (dt == QF_C128) {
+    if (tiled)
+      k_expect_tiled<double><<<nblocks, 256, 0, s>>>(static_cast<const double2*>(psi), n, groups, ngroups, chunks,
+                                                     partials, counter, out);
+    else
+      k_expect<double><<<nblocks, 256, 0, s>>>(static_cast<const double2*>(psi), n, groups, ngroups, chunks,
+                                               partials, counter, out);
+  } else {
+    if (tiled)
+      k_expect_tiled<float><<<nblocks, 256, 0, s>>>(static_cast<const float2*>(psi), n, groups, ngroups, chunks,
+                                                    partials, counter, out);
+    else
+      k_expect<float><<<nblocks, 256, 0, s>>>(static_cast<const float2*>(psi), n, groups, ngroups, chunks,
+                                              partials, counter, out);
+  }
   prof_post(prof_slot_, s);
   count_launch();
   return cudaGetLastError();

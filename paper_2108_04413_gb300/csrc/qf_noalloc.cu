@@ -125,6 +125,7 @@ void build_tables(const qf_term* terms, size_t nt, int* ngroups, int* nchunks) {
         g.flags |= (popc(T.x & T.z) & 1) ? 2 : 1;
       }
     }
+    if (j - i == 1) g.flags |= 4;  // a single term (the same flag as the state path's plans)
     i = j;
   }
   *ngroups = ng;
