@@ -2209,8 +2209,13 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
       }
     }
     QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
+    // complex128 in QF_HPSI_DS mode: the mapped sweeps run in double-single arithmetic;
+    // the reverse must agree with the forward, whose log it reads
+    const bool sweep_ds = st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS && d_map != nullptr &&
+                          (log != nullptr || !need_reverse);
     QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
-                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, d_strs, d_map, st->stream));
+                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, d_strs, d_map, sweep_ds,
+                                   st->stream));
     double* d_e = st->d_out + nblk;
     // a real state with a Hamiltonian of molecular form takes the direct tables
     ExpPlan* pm = const_cast<ExpPlan*>(p);
@@ -2257,7 +2262,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     if (need_reverse)
       QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
                                      (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, d_strs, d_map,
-                                     st->stream));
+                                     sweep_ds, st->stream));
     if (n_dets) {  // residuals: lambda after the reverse sweep is U^dagger H psi
       std::vector<int64_t> idx(n_dets);
       for (size_t k = 0; k < n_dets; ++k) idx[k] = (int64_t)compact_of(dets[k], sp);

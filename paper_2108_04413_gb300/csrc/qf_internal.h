@@ -173,13 +173,27 @@ struct RunBlk {                     // one excitation block inside its run
   double q[kSparseMaxCls][2][2];    // Qi with generator Q = i Qi (reverse)
   float mf[kSparseMaxCls][2][2];    // m rounded to FP32 (complex64 sweeps)
   float qf[kSparseMaxCls];          // q[c][0][1] rounded to FP32 (complex64 overlaps)
+  float2 md[kSparseMaxCls][2][2];   // m as double-single (hi, lo) pairs (complex128, QF_HPSI_DS)
+  float2 qd[kSparseMaxCls];         // q[c][0][1] as (hi, lo)
 };
-// Fills a run block's FP32 coefficients from its FP64 ones.
+// (hi, lo) float pair of v: hi = v rounded to FP32, lo = the rest rounded.
+inline float2 ds_split(double v) {
+  const float hi = (float)v;
+  float2 r;
+  r.x = hi;
+  r.y = (float)(v - (double)hi);
+  return r;
+}
+// Fills a run block's FP32 and double-single coefficients from its FP64 ones.
 inline void runblk_f32(RunBlk& B) {
   for (int c = 0; c < kSparseMaxCls; ++c) {
     for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) B.mf[c][i][j] = (float)B.m[c][i][j];
+      for (int j = 0; j < 2; ++j) {
+        B.mf[c][i][j] = (float)B.m[c][i][j];
+        B.md[c][i][j] = ds_split(B.m[c][i][j]);
+      }
     B.qf[c] = (float)B.q[c][0][1];
+    B.qd[c] = ds_split(B.q[c][0][1]);
   }
 }
 constexpr uint32_t kNoStrings = 0xFFFFFFFFu;
@@ -328,12 +342,16 @@ cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBl
 // there (RunPart::logbase) and the reverse reads psi back from it instead of
 // un-rotating psi; both sweeps of one evaluation must use the same log.
 // strs: the blocks' outside strings (RunBlk::lsa / lsb), or NULL to unrank them.
+// map: the plan's item maps (RunPart::mapbase), used by the forward and by the
+// logged reverse, or NULL.  ds: a complex128 forward and logged reverse with maps
+// run in double-single arithmetic (members and log as hi + lo float pairs, about
+// 48 bits; RunBlk::md / qd); both sweeps of one evaluation must agree on it.
 // runs is a host array; parts and blks are device arrays.  Returns an error
 // when a part does not fit in shared memory.
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
-                               int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs, const uint32_t* map,
-                               cudaStream_t s);
+                               int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
+                               const uint32_t* map, bool ds, cudaStream_t s);
 // Overlaps only: out[b] = Im <lam|Q_b|psi> of every block b on the same compact
 // state (psi real parts, lam real parts in psi's imaginary slots); nothing is
 // rotated.  Same descriptors as launch_sector_runs.

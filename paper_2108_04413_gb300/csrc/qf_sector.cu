@@ -293,6 +293,36 @@ __device__ __forceinline__ double warp_fixed_to_double(long long t, int e) {
   return tot == 0 ? 0.0 : scale_pow2((double)tot, emax - 1075);
 }
 
+// Double-single arithmetic of the part-local sweeps (complex128 in QF_HPSI_DS
+// mode): a value is a float pair hi + lo with |lo| <= ulp(hi) / 2, about 48
+// significant bits.  Every rounding step is explicit, so that no multiply is
+// fused into an error-free transformation.
+__device__ __forceinline__ float2 ds_renorm(float s, float e) {  // Fast2Sum (|s| >= |e| or s == 0)
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 ds_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);  // the exact error of hi * hi
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return ds_renorm(p, e);
+}
+__device__ __forceinline__ float2 ds_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);  // TwoSum of the high parts
+  const float bp = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bp)), __fsub_rn(b.x, bp));
+  return ds_renorm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+// c + a x + b y (one output of a 2x2 block rotation, m = composite - identity)
+__device__ __forceinline__ float2 ds_rot(float2 a, float2 x, float2 b, float2 y, float2 c) {
+  return ds_add(c, ds_add(ds_mul(a, x), ds_mul(b, y)));
+}
+__device__ __forceinline__ float2 ds_of(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 constexpr int kRunThreads = 256;
 constexpr int kRunWarps = kRunThreads / 32;
 constexpr int kRunBlkWords = sizeof(RunBlk) / 4;
@@ -340,7 +370,7 @@ __device__ void fill_binom_prefix(uint32_t (*Cs)[kBinom]) {
 // the same (psi, lam), nothing rotated or written back (operator-pool gradients).
 // Overlaps accumulate in the state's precision (FP64 for complex128, FP32 for
 // complex64); each part's overlap with a block is written to partial in FP64.
-template <int MODE, typename T>
+template <int MODE, typename T, bool DSW = false>
 __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
                                                              RunInfo run, const RunPart* __restrict__ parts,
                                                              const RunBlk* __restrict__ blks, double* partial,
@@ -374,6 +404,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   // shared memory: amplitudes, then compact indices
   const uint32_t cap = R.maxsize;
   T* ar = reinterpret_cast<T*>(dsm);   // MODE 0 (psi), MODE 3 (lam)
+  float2* ad = reinterpret_cast<float2*>(dsm);  // the same, double-single (DSW)
   V* av = reinterpret_cast<V*>(dsm);   // MODE 1, 2, 4 (psi)
   V* lv = av + cap;                    // MODE 2 (lam)
   constexpr size_t idx_bytes = MODE == 4 ? 0 : sizeof(uint32_t);
@@ -391,7 +422,9 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     const uint32_t sbm = unrank_m(ib, R.bpos, R.ub, P.kb, C) | P.gb;
     const uint32_t g = (uint32_t)compact_index(cm, sa, sbm);
     if (MODE != 4) gi[m] = g;
-    if (MODE == 0 || MODE == 3) {
+    if (DSW) {
+      ad[m] = ds_of(__ldcg(pr + 2 * (size_t)g + slot));
+    } else if (MODE == 0 || MODE == 3) {
       ar[m] = __ldcg(pr + 2 * (size_t)g + slot);
     } else {
       av[m] = __ldcg(psi + g);
@@ -449,8 +482,9 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     __shared__ __align__(16) uint32_t cw[3][kCoefWordsMax];
     __shared__ long long wtot[2][kRunWarps];  // per-warp overlap sums of the last two steps
     __shared__ int wexp[2][kRunWarps];
-    constexpr int kCw = F32 ? (MODE == 3 ? 20 : 16) : (MODE == 3 ? 64 : 32);
-    constexpr size_t kCoff = F32 ? offsetof(RunBlk, mf) : offsetof(RunBlk, m);
+    constexpr int kCw = DSW ? (MODE == 3 ? 40 : 32) : F32 ? (MODE == 3 ? 20 : 16) : (MODE == 3 ? 64 : 32);
+    constexpr size_t kCoff = DSW ? offsetof(RunBlk, md) : F32 ? offsetof(RunBlk, mf) : offsetof(RunBlk, m);
+    using LV = typename std::conditional<DSW, float4, V>::type;  // a log pair
     constexpr bool IRED = MODE == 3 && !F32;  // integer overlap reduction
     auto coef_word = [&](int st) {
       return __ldg(reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(blks + blk_of(st)) + kCoff) + tid);
@@ -478,12 +512,12 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       }
     }
     __syncthreads();
-    V* lgp = log ? log + P.logbase : nullptr;
+    LV* lgp = log ? reinterpret_cast<LV*>(log + P.logbase) : nullptr;
     auto pos = [&](int st) { return MODE == 3 ? nb - 1 - st : st; };  // a step's forward position
     // item tid of step s (wq0, lq0) and of step s + 1 (wq1, lq1): map word and
     // (reverse) log pair
     uint32_t wq0 = 0u, wq1 = 0u;
-    V lq0{}, lq1{};
+    LV lq0{}, lq1{};
     if ((uint32_t)tid < stn[pos(0)]) {
       wq0 = __ldg(mp + sto[pos(0)] + tid);
       if (MODE == 3) lq0 = __ldcs(lgp + sto[pos(0)] + tid);
@@ -516,41 +550,60 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       const unsigned cg = stc[f];
       const T* cf = reinterpret_cast<const T*>(cw[s % 3]);  // m[cls][i][j] at 4 cls + 2 i + j, then q or qf
       const uint32_t wnow = wq0;
-      const V lnow = lq0;
+      const LV lnow = lq0;
       T acc = T(0);
+      float2 dacc = make_float2(0.0f, 0.0f);  // DSW overlap
       for (uint32_t it = tid; it < n_s; it += kRunThreads) {
         const bool first = it == (uint32_t)tid;
         const uint32_t w = first ? wnow : __ldg(mp + o_s + it);
         const uint32_t i0 = w & 0xFFFu, i1 = (w >> 12) & 0xFFFu;
         const unsigned cls = cg ^ (w >> 24);
-        const T a00 = cf[4 * cls], a01 = cf[4 * cls + 1], a10 = cf[4 * cls + 2], a11 = cf[4 * cls + 3];
-        if (MODE == 0) {
-          const T v0 = ar[i0], v1 = ar[i1];
-          const T o0 = fma(a00, v0, fma(a01, v1, v0)), o1 = fma(a10, v0, fma(a11, v1, v1));
-          ar[i0] = o0;
-          ar[i1] = o1;
-          if (lgp) {
-            V wv;
-            wv.x = o0;
-            wv.y = o1;
-            __stcs(lgp + o_s + it, wv);  // streamed: read back once by the reverse sweep
+        if constexpr (DSW) {
+          const float2* cd = reinterpret_cast<const float2*>(cw[s % 3]);  // md, then qd
+          const float2 d00 = cd[4 * cls], d01 = cd[4 * cls + 1], d10 = cd[4 * cls + 2], d11 = cd[4 * cls + 3];
+          const float2 x0 = ad[i0], x1 = ad[i1];
+          if (MODE == 3) {
+            const float4 pq = first ? lnow : __ldcs(lgp + o_s + it);  // psi pair after this block
+            const float2 p0 = make_float2(pq.x, pq.y), p1 = make_float2(pq.z, pq.w);
+            // Im <lam|Q|psi> on the pair: q01 (lam0 psi1 - lam1 psi0)
+            const float2 t = ds_add(ds_mul(x0, p1), ds_mul(make_float2(-x1.x, -x1.y), p0));
+            dacc = ds_add(dacc, ds_mul(cd[16 + cls], t));
           }
+          const float2 o0 = ds_rot(d00, x0, d01, x1, x0), o1 = ds_rot(d10, x0, d11, x1, x1);
+          ad[i0] = o0;
+          ad[i1] = o1;
+          if (MODE == 0 && lgp) __stcs(lgp + o_s + it, make_float4(o0.x, o0.y, o1.x, o1.y));
         } else {
-          const T q01 = F32 ? cf[16 + cls] : cf[16 + 4 * cls + 1];
-          const V pp = first ? lnow : __ldcs(lgp + o_s + it);
-          const T w0 = ar[i0], w1 = ar[i1];
-          // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
-          acc = fma(q01, fma(w0, pp.y, -w1 * pp.x), acc);
-          ar[i0] = fma(a00, w0, fma(a01, w1, w0));
-          ar[i1] = fma(a10, w0, fma(a11, w1, w1));
-        }
+          const T a00 = cf[4 * cls], a01 = cf[4 * cls + 1], a10 = cf[4 * cls + 2], a11 = cf[4 * cls + 3];
+          if (MODE == 0) {
+            const T v0 = ar[i0], v1 = ar[i1];
+            const T o0 = fma(a00, v0, fma(a01, v1, v0)), o1 = fma(a10, v0, fma(a11, v1, v1));
+            ar[i0] = o0;
+            ar[i1] = o1;
+            if (lgp) {
+              V wv;
+              wv.x = o0;
+              wv.y = o1;
+              __stcs(lgp + o_s + it, wv);  // streamed: read back once by the reverse sweep
+            }
+          } else {
+            const T q01 = F32 ? cf[16 + cls] : cf[16 + 4 * cls + 1];
+            const V pp = first ? lnow : __ldcs(lgp + o_s + it);
+            const T w0 = ar[i0], w1 = ar[i1];
+            // Im <lam|Q|psi> on the pair, Qi = [[0, q01], [-q01, 0]] (checked on the host)
+            acc = fma(q01, fma(w0, pp.y, -w1 * pp.x), acc);
+            ar[i0] = fma(a00, w0, fma(a01, w1, w0));
+            ar[i1] = fma(a10, w0, fma(a11, w1, w1));
+          }
+        }  // DSW
       }
       if (ADJ) {
         pend_w = n_s >= (uint32_t)kRunThreads ? kRunWarps : (int)((n_s + 31) / 32);
         if (IRED) {
           if (warp < pend_w) {  // warps past pend_w hold no items this step
             int e;
-            const long long t = warp_sum_fixed((double)acc, &e);
+            const double av_ = DSW ? (double)dacc.x + (double)dacc.y : (double)acc;
+            const long long t = warp_sum_fixed(av_, &e);
             if (lane == 0) {
               wtot[s & 1][warp] = t;
               wexp[s & 1][warp] = e;
@@ -708,7 +761,10 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   T* pw = reinterpret_cast<T*>(psi);
   for (uint32_t m = tid; m < size; m += kRunThreads) {
     const uint32_t g = gi[m];
-    if (MODE == 0 || MODE == 3) {
+    if (DSW) {
+      const float2 d = ad[m];
+      __stcg(pw + 2 * (size_t)g + slot, (T)((double)d.x + (double)d.y));
+    } else if (MODE == 0 || MODE == 3) {
       __stcg(pw + 2 * (size_t)g + slot, ar[m]);
     } else {
       __stcg(psi + g, av[m]);
@@ -1432,15 +1488,18 @@ uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged) {
        : mode == 2 ? run_capacity_t<2, float>() : run_capacity_t<3, float>();
 }
 
-template <int MODE, typename T>
+template <int MODE, typename T, bool DSW = false>
 static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, const RunPart* parts,
                           const RunBlk* blks, double* partial, int pmax, const SecCompact& cm, void* log,
                           const uint16_t* strs, const uint32_t* map, cudaStream_t s) {
+  static_assert(!DSW || ((MODE == 0 || MODE == 3) && sizeof(T) == 8), "double-single sweeps: complex128 forward "
+                                                                      "and logged reverse");
+  if (DSW && !map) return cudaErrorInvalidValue;  // the double-single path is the mapped step loop
   using V = typename SCx<T>::V;
   static std::once_flag once;  // allow the opt-in shared memory size, once per process
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_sector_run<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr = cudaFuncSetAttribute(k_sector_run<MODE, T, DSW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)run_smem_max<MODE, T>());
   });
   if (attr != cudaSuccess) return attr;
@@ -1448,7 +1507,7 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
     const RunInfo& R = runs[MODE != 0 ? nruns - 1 - r : r];
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
     if (smem > run_smem_max<MODE, T>() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
-    k_sector_run<MODE, T><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
+    k_sector_run<MODE, T, DSW><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
                                                               blks, partial, pmax, cm, static_cast<V*>(log), strs,
                                                               (MODE == 0 || MODE == 3) ? map : nullptr);
     count_launch();
@@ -1461,13 +1520,16 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
                                int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
-                               const uint32_t* map, cudaStream_t s) {
+                               const uint32_t* map, bool ds, cudaStream_t s) {
   if (nblk <= 0 || nruns <= 0) return cudaSuccess;
   if (!cm.ra || (log && !realst)) return cudaErrorInvalidValue;
   const int prof_slot_ = prof_pre(adj ? QF_K_ADJ_SPARSE : QF_K_SPARSE, s);
   const int mode = !adj ? 0 : !realst ? 2 : log ? 3 : 1;
   cudaError_t e;
-  if (dt == QF_C128)
+  if (dt == QF_C128 && ds && map && (mode == 0 || mode == 3))
+    e = mode == 0 ? runs_t<0, double, true>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
+                  : runs_t<3, double, true>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s);
+  else if (dt == QF_C128)
     e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
       : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
       : mode == 2 ? runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
