@@ -274,6 +274,26 @@ __device__ __forceinline__ long long warp_sum_fixed(double v, int* e) {
   return warp_add_i64(m);
 }
 
+// The same for a double-single value hi + lo held as two floats: a float is its
+// 24-bit significand times 2^(e - 150); both parts are aligned, with 29 guard
+// bits, on the warp's largest hi exponent (lo keeps its leading bits down to
+// 2^-53 of the largest value) and added exactly.  The sum is t * 2^(*e - 179),
+// |t| < 2^59, so eight warps' sums stay below 2^62.
+__device__ __forceinline__ long long f_aligned(float v, int emax) {
+  const int b = __float_as_int(v);
+  const int ex = (b >> 23) & 0xFF;
+  if (ex == 0) return 0ll;  // zero or subnormal
+  const long long m = (long long)((b & 0x7FFFFF) | 0x800000) << 29;
+  const int sh = emax - ex;
+  const long long a = sh > 62 ? 0ll : (m >> sh);
+  return b < 0 ? -a : a;
+}
+__device__ __forceinline__ long long warp_sum_fixed_ds(float2 v, int* e) {
+  const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)((__float_as_int(v.x) >> 23) & 0xFF));
+  *e = emax - 179 + 1075;  // on the double scale of warp_fixed_to_double: t * 2^(*e - 1075)
+  return warp_add_i64(f_aligned(v.x, emax) + f_aligned(v.y, emax));
+}
+
 // d * 2^k for -2044 <= k <= 1023, exact unless the result is subnormal.
 __device__ __forceinline__ double scale_pow2(double d, int k) {
   if (k < -1022) {
@@ -602,8 +622,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
         if (IRED) {
           if (warp < pend_w) {  // warps past pend_w hold no items this step
             int e;
-            const double av_ = DSW ? (double)dacc.x + (double)dacc.y : (double)acc;
-            const long long t = warp_sum_fixed(av_, &e);
+            const long long t = DSW ? warp_sum_fixed_ds(dacc, &e) : warp_sum_fixed((double)acc, &e);
             if (lane == 0) {
               wtot[s & 1][warp] = t;
               wexp[s & 1][warp] = e;
