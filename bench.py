@@ -130,9 +130,13 @@ def sector_pairs(terms, n: int, na: int, nb: int):
     return total, comb(ne, na) * comb(no, nb)
 
 
-def measured_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
-    or None when the kernel's source changed since the capture."""
+def measured_traffic(kernel: str, run_items=None):
+    """(DRAM bytes per roofline unit, how they were taken) from the committed ncu summary
+    (profiles/traffic.json), or None when the kernel's source changed since the
+    capture.  A sweep's record holds the bytes of a few of its run launches and
+    their run indices; it is scaled to the whole sweep by the items the runs
+    process (run_items, from the library's plan), since the forward log that
+    dominates the traffic grows with the items."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -146,7 +150,16 @@ def measured_traffic(kernel: str):
         return None
     if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["sha256_prefix"]:
         return None
-    return rec["bytes"]
+    if "runs" not in rec:
+        return rec["bytes"], "one ncu capture of one launch, cold caches"
+    if run_items is None or len(run_items) != rec.get("n_runs") or max(rec["runs"]) >= len(run_items):
+        return None
+    sampled = sum(int(run_items[r]) for r in rec["runs"])
+    total = int(sum(int(v) for v in run_items))
+    if not sampled:
+        return None
+    return rec["bytes"] * total / sampled, (
+        f"ncu DRAM bytes of runs {rec['runs']} ({sampled} items, cold caches) scaled to the sweep's {total} items")
 
 
 def hpsi_flops(stats, n, real: bool):
@@ -406,7 +419,14 @@ def run_gpu(args, rank, world, local, pg):
                                            "pipe, so frac compares with the native-FP64 roofline of the same work")
                                           if args.dtype == "c128" else "")}
 
-    roof["traffic"] = measured_traffic(roof.get("kernel", ""))
+    try:
+        run_items = st.sweep_run_items()
+    except qf.QFError:
+        run_items = None
+    mt = measured_traffic(roof.get("kernel", ""), run_items)
+    roof["traffic"] = mt[0] if mt else None
+    if mt:
+        roof["traffic_note"] = mt[1]
     out = {
         "metric": "energy+grad evals/s",
         "value": value,

@@ -207,6 +207,17 @@ qf_status qf_profile_begin(unsigned kind_mask);
 qf_status qf_profile_read(unsigned kind_mask, uint64_t* launches, double* total_ms);
 qf_status qf_profile_end(void);
 
+/* Plan introspection for measurement (the paper has no counterpart).  For the
+ * last qf_energy_grad / qf_residuals call on st that ran its sweeps as
+ * part-local runs of the compact sector layout (one kernel launch per run and
+ * sweep): the number of runs into *n_runs and, for the first min(cap, runs)
+ * runs in plan order, the (sector member pair, excitation) items one sweep
+ * processes in that run into items (host array of cap entries; may be NULL when
+ * cap = 0).  The forward sweep launches the runs in plan order, the reverse
+ * sweep last to first.  The items of all runs sum to the forward log's pair
+ * count.  QF_EINVAL when no such sweep has run on st. */
+qf_status qf_sweep_run_items(const qf_state* st, uint64_t* items, size_t cap, size_t* n_runs);
+
 /* Allocation-free expectation value.  The paper has no counterpart: this call
  * exists for callers that cannot allocate device memory -- for instance when
  * all of the GPU's memory is already reserved by another allocator (a

@@ -140,6 +140,7 @@ struct SectorRuns {
   std::vector<qf::RunBlk> blks;  // forward blocks, then inverse blocks (m, q refilled per call)
   int pmax = 0;
   uint64_t logitems = 0;         // (member pair, block) items of one sweep: the forward log's length
+  std::vector<uint64_t> run_items;  // the items of each run (they sum to logitems)
   std::vector<uint16_t> strs;    // the blocks' outside strings (RunBlk::lsa / lsb); empty when not tabulated
   bool log_ok = true;            // every inverse block lists its two patterns in the forward order
   // item maps (RunPart::mapbase): words of all classes; map_ok when every part fits
@@ -216,6 +217,7 @@ struct qf_state {
   };
   std::unordered_map<uint64_t, AnsatzPlan> ansatz_plans;
   uint64_t parts_key = 0;  // the ansatz plan and sector whose run parts sit in d_runblk
+  std::vector<uint64_t> run_items;  // items of each run of the last part-local sweep (launch order)
   uint64_t calls = 0;      // plan-using calls so far (the caches' clock)
   size_t elem() const { return dt == QF_C128 ? 16 : 8; }
   size_t bytes() const { return elem() << n; }
@@ -1322,6 +1324,7 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
   out->blks.assign(2 * nblk, qf::RunBlk{});
   out->pmax = 0;
   out->logitems = 0;
+  out->run_items.clear();
   out->strs.clear();
   out->log_ok = true;
   for (size_t b = 0; b < nblk; ++b)
@@ -1440,6 +1443,7 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
       ++shapes[{B.ne, B.no, B.e0, B.o0}];
     }
     std::map<std::pair<int, int>, uint64_t> classes;  // (ka, kb) -> map base
+    const uint64_t items0 = out->logitems;
     for (int k = 0; k < R.nparts; ++k) {
       qf::RunPart& P = out->parts[R.part0 + k];
       uint64_t tot = 0;
@@ -1459,6 +1463,7 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
       }
     }
     out->runs.push_back(R);
+    out->run_items.push_back(out->logitems - items0);
     b0 = b1;
   }
   // maps serve the reverse sweep too when each inverse block has its forward
@@ -1528,13 +1533,13 @@ qf_status ensure_buf(void** p, size_t* cap, size_t bytes, const char* what) {
 }
 
 // Residual read-out: out[2k], out[2k + 1] = the amplitude of lam at idx[k].
-cudaError_t gather_residuals(qf_state* st, const void* lam, bool packed, const std::vector<int64_t>& idx,
+cudaError_t gather_residuals(qf_state* st, const void* lam, bool packed, bool ds, const std::vector<int64_t>& idx,
                              double* out) {
   if (ensure_buf(&st->d_idx, &st->idx_cap, idx.size() * sizeof(int64_t), "residual indices") != QF_OK)
     return cudaErrorMemoryAllocation;
   cudaError_t e = h2d(st->d_idx, idx.data(), idx.size() * sizeof(int64_t), st->stream);
   if (e != cudaSuccess) return e;
-  return qf::launch_gather(lam, st->dt, static_cast<const int64_t*>(st->d_idx), (int)idx.size(), packed, out,
+  return qf::launch_gather(lam, st->dt, static_cast<const int64_t*>(st->d_idx), (int)idx.size(), packed, ds, out,
                            st->stream);
 }
 
@@ -2208,29 +2213,41 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
         d_map = static_cast<const uint32_t*>(st->d_map);
       }
     }
-    QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, compact_of(det, sp), st->stream));
-    // complex128 in QF_HPSI_DS mode: the mapped sweeps run in double-single arithmetic;
-    // the reverse must agree with the forward, whose log it reads
-    const bool sweep_ds = st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS && d_map != nullptr &&
-                          (log != nullptr || !need_reverse);
-    QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
-                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, d_strs, d_map, sweep_ds,
-                                   st->stream));
-    double* d_e = st->d_out + nblk;
+    st->run_items = rs.run_items;
     // a real state with a Hamiltonian of molecular form takes the direct tables
     ExpPlan* pm = const_cast<ExpPlan*>(p);
     if (lreal && st->n <= 32) {
       qf_status ds = ensure_direct(st, pm);
       if (ds != QF_OK) return ds;
     }
+    const bool hdirect = lreal && pm->direct == 1;
+    // complex128 in QF_HPSI_DS mode: the mapped sweeps run in double-single arithmetic;
+    // the reverse must agree with the forward, whose log it reads
+    const bool sweep_ds = st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS && d_map != nullptr &&
+                          (log != nullptr || !need_reverse);
+    // and the compact state stays in double-single form from the reset to the end
+    // of the reverse when the sweeps, the direct H|psi> and the residual gather are
+    // all that touch it (the pool overlaps read FP64 members)
+    const bool dss = sweep_ds && hdirect && !pp;
+    const uint64_t c0 = compact_of(det, sp);
+    if (dss)  // member c0 = (1, 0, 0, 0) as floats: element 2 c0 of 2 * members float pairs
+      QF_CUDA(qf::launch_zero_and_set_count(cpsi, 2 * members, QF_C64, 2 * c0, st->stream));
+    else
+      QF_CUDA(qf::launch_zero_and_set_count(cpsi, members, st->dt, c0, st->stream));
+    QF_CUDA(qf::launch_sector_runs(cpsi, nullptr, st->dt, false, true, rs.runs.data(), nruns, d_parts, d_blks,
+                                   (int)nblk, nullptr, rs.pmax, nullptr, cm, log, d_strs, d_map, sweep_ds, dss,
+                                   st->stream));
+    double* d_e = st->d_out + nblk;
     // double-single pair products (complex128, QF_HPSI_DS): the amplitudes' float
-    // split sits in the compact buffer's second half, unused by a packed real lambda
+    // split sits in the compact buffer's second half, unused by a packed real lambda,
+    // followed (double-single state) by psi's FP64 values
     float2* split = (st->dt == QF_C128 && st->hpsi_mode == QF_HPSI_DS)
                         ? reinterpret_cast<float2*>(static_cast<char*>(cpsi) + members * st->elem())
                         : nullptr;
-    if (lreal && pm->direct == 1)
+    double* psid = split ? reinterpret_cast<double*>(split + members) : nullptr;
+    if (hdirect)
       QF_CUDA(qf::launch_sector_hpsi_direct(cpsi, st->dt, sp, pm->dtab, cm, st->d_partials, st->d_counter, d_e,
-                                            kPartials / 2, split, st->stream));
+                                            kPartials / 2, split, psid, dss, st->stream));
     else
       QF_CUDA(qf::launch_sector_hpsi(cpsi, clam, st->dt, lreal, sp, p->rk, p->d_seclarge, p->nseclarge,
                                      p->d_hchunks, st->d_partials, st->d_counter, d_e, kPartials / 2, cm,
@@ -2262,11 +2279,11 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     if (need_reverse)
       QF_CUDA(qf::launch_sector_runs(cpsi, clam, st->dt, true, lreal, rs.runs.data(), nruns, d_parts, d_blks + nblk,
                                      (int)nblk, st->d_sec_partial, rs.pmax, st->d_out, cm, log, d_strs, d_map,
-                                     sweep_ds, st->stream));
+                                     sweep_ds, dss, st->stream));
     if (n_dets) {  // residuals: lambda after the reverse sweep is U^dagger H psi
       std::vector<int64_t> idx(n_dets);
       for (size_t k = 0; k < n_dets; ++k) idx[k] = (int64_t)compact_of(dets[k], sp);
-      QF_CUDA(gather_residuals(st, lreal ? cpsi : clam, lreal, idx, st->d_out + nblk + 2));
+      QF_CUDA(gather_residuals(st, lreal ? cpsi : clam, lreal, dss, idx, st->d_out + nblk + 2));
     }
     QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
     QF_CUDA(d2h(st->h_out, st->d_out, (nblk + 2 + 2 * n_dets + npool_blk) * sizeof(double), st->stream));
@@ -2362,7 +2379,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
   st->real = both_real;
   if (n_dets) {  // residuals: lambda after the reverse sweep is U^dagger H psi (scale sc)
     std::vector<int64_t> idx(dets, dets + n_dets);
-    QF_CUDA(gather_residuals(st, st->lam, false, idx, st->d_out + blocks.size() + 2));
+    QF_CUDA(gather_residuals(st, st->lam, false, false, idx, st->d_out + blocks.size() + 2));
   }
   QF_CUDA(d2h(st->h_out, st->d_out, (blocks.size() + 2 + 2 * n_dets) * sizeof(double), st->stream));
   QF_CUDA(cudaStreamSynchronize(st->stream));
@@ -2468,6 +2485,15 @@ qf_status qf_state_clear_plans(qf_state* st) {
   st->plans.clear();
   st->ansatz_plans.clear();
   st->parts_key = st->pool_key = st->map_key = 0;  // descriptors on the device belong to no plan now
+  return QF_OK;
+}
+
+qf_status qf_sweep_run_items(const qf_state* st, uint64_t* items, size_t cap, size_t* n_runs) {
+  if (!st || !n_runs) return fail(QF_EINVAL, "NULL argument");
+  if (cap && !items) return fail(QF_EINVAL, "items is NULL with cap > 0");
+  if (st->run_items.empty()) return fail(QF_EINVAL, "no part-local sweep has run on this state");
+  *n_runs = st->run_items.size();
+  for (size_t r = 0; r < std::min(cap, st->run_items.size()); ++r) items[r] = st->run_items[r];
   return QF_OK;
 }
 

@@ -291,8 +291,10 @@ cudaError_t launch_zero_and_set(void* psi, int n, qf_dtype dt, uint64_t det, cud
 // count amplitudes set to the unit vector e_idx.
 cudaError_t launch_zero_and_set_count(void* psi, uint64_t count, qf_dtype dt, uint64_t idx, cudaStream_t s);
 // out[2k], out[2k + 1] = (re, im) of src[idx[k]] (zeros where idx[k] < 0); packed: a
-// real value kept in the imaginary slot.
-cudaError_t launch_gather(const void* src, qf_dtype dt, const int64_t* idx, int count, bool packed, double* out,
+// real value kept in the imaginary slot.  ds (QF_C128, packed): that slot holds a
+// double-single (hi, lo) float pair (launch_sector_runs' dss layout).
+cudaError_t launch_gather(const void* src, qf_dtype dt, const int64_t* idx, int count, bool packed, bool ds,
+                          double* out,
                           cudaStream_t s);
 cudaError_t launch_scale(void* psi, int n, qf_dtype dt, double scale, cudaStream_t s);
 cudaError_t launch_rot(void* psi, int n, qf_dtype dt, const RotArgs& a, cudaStream_t s);
@@ -346,12 +348,15 @@ cudaError_t launch_sector_sweep(void* psi, qf_dtype dt, bool realst, const SecBl
 // logged reverse, or NULL.  ds: a complex128 forward and logged reverse with maps
 // run in double-single arithmetic (members and log as hi + lo float pairs, about
 // 48 bits; RunBlk::md / qd); both sweeps of one evaluation must agree on it.
+// dss (with ds only): the compact state itself is kept in double-single form, each
+// member's slots holding (psi hi, psi lo, lam hi, lam lo) floats in place of
+// (psi, lam) doubles, so that no sweep converts between the two.
 // runs is a host array; parts and blks are device arrays.  Returns an error
 // when a part does not fit in shared memory.
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
                                int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
-                               const uint32_t* map, bool ds, cudaStream_t s);
+                               const uint32_t* map, bool ds, bool dss, cudaStream_t s);
 // Overlaps only: out[b] = Im <lam|Q_b|psi> of every block b on the same compact
 // state (psi real parts, lam real parts in psi's imaginary slots); nothing is
 // rotated.  Same descriptors as launch_sector_runs.
@@ -370,10 +375,13 @@ uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged);
 // (lambda packed into psi's imaginary slots); out[0] = <psi|lambda>,
 // out[1] = <psi|psi>, partials holds 2 * nblocks doubles.  split: for a
 // QF_C128 state, scratch of one float2 per member that turns on double-single
-// pair products (QF_HPSI_DS); NULL keeps them in FP64.
+// pair products (QF_HPSI_DS); NULL keeps them in FP64.  dss (with split): the
+// state is in the sweeps' double-single layout (launch_sector_runs); psid,
+// scratch of one double per member, receives psi, and lambda is written as a
+// (hi, lo) float pair.
 cudaError_t launch_sector_hpsi_direct(void* cpsi, qf_dtype dt, const SecSpace& sp, const SecDirect& d,
                                       const SecCompact& cm, double* partials, unsigned* counter, double* out,
-                                      int nblocks, float2* split, cudaStream_t s);
+                                      int nblocks, float2* split, double* psid, bool dss, cudaStream_t s);
 cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool realst, const SecSpace& sp,
                                const SecRank& rk, const SecGroup* large, int nlarge,
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,

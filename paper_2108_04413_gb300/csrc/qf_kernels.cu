@@ -155,6 +155,21 @@ __global__ void k_zero_and_set(V* psi, uint64_t N, uint64_t det) {
 
 // out[2k], out[2k + 1] = the amplitude at idx[k] (0 where idx[k] < 0); packed:
 // the real value stored in the imaginary slot, imaginary part 0.
+// The same for a packed double-single state: (re hi, re lo, packed hi, packed lo).
+__global__ void k_gather_ds(const float4* __restrict__ src, const int64_t* __restrict__ idx, int count,
+                            double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int64_t i = idx[k];
+  double re = 0.0;
+  if (i >= 0) {
+    const float4 v = src[i];
+    re = (double)v.z + (double)v.w;
+  }
+  out[2 * k] = re;
+  out[2 * k + 1] = 0.0;
+}
+
 template <typename V>
 __global__ void k_gather(const V* __restrict__ src, const int64_t* __restrict__ idx, int count, int packed,
                          double* __restrict__ out) {
@@ -1161,11 +1176,14 @@ cudaError_t launch_zero_and_set_count(void* psi, uint64_t N, qf_dtype dt, uint64
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const void* src, qf_dtype dt, const int64_t* idx, int count, bool packed, double* out,
-                          cudaStream_t s) {
+cudaError_t launch_gather(const void* src, qf_dtype dt, const int64_t* idx, int count, bool packed, bool ds,
+                          double* out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (ds && (dt != QF_C128 || !packed)) return cudaErrorInvalidValue;
   const unsigned g = (unsigned)((count + 255) / 256);
-  if (dt == QF_C128)
+  if (ds)
+    k_gather_ds<<<g, 256, 0, s>>>(static_cast<const float4*>(src), idx, count, out);
+  else if (dt == QF_C128)
     k_gather<double2><<<g, 256, 0, s>>>(static_cast<const double2*>(src), idx, count, packed ? 1 : 0, out);
   else
     k_gather<float2><<<g, 256, 0, s>>>(static_cast<const float2*>(src), idx, count, packed ? 1 : 0, out);

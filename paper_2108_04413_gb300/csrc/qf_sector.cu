@@ -39,14 +39,36 @@ constexpr int kBinom = 18;  // C(m, k) for m, k < 18 (up to 34 qubits: 17 per pa
 
 __device__ __forceinline__ unsigned par64s(uint64_t v) { return (unsigned)__popcll(v) & 1u; }
 
-__device__ void fill_binom(uint32_t (*C)[kBinom]) {
-  for (int i = threadIdx.x; i < kBinom * kBinom; i += blockDim.x) {
-    const int m = i / kBinom, k = i % kBinom;
-    // C(m, k) by the multiplicative formula (exact in 64-bit for m < 18)
-    uint64_t c = (k > m) ? 0 : 1;
-    for (int j = 1; j <= k && k <= m; ++j) c = c * (uint64_t)(m - k + j) / (uint64_t)j;
-    C[m][k] = (uint32_t)c;
+// Binomial tables, built at compile time: c[m][k] = C(m, k) (Pascal's rule; 0
+// for k > m) and cs[m][k] = sum of C(m, k') over k' < k, where the size-k group
+// of the subsets of m positions starts in a strings table ordered by size.
+struct BinomTables {
+  uint32_t c[kBinom][kBinom];
+  uint32_t cs[kBinom][kBinom];
+};
+constexpr BinomTables make_binom_tables() {
+  BinomTables t{};
+  for (int m = 0; m < kBinom; ++m)
+    for (int k = 0; k < kBinom; ++k)
+      t.c[m][k] = k == 0 ? 1u : (m == 0 ? 0u : t.c[m - 1][k - 1] + t.c[m - 1][k]);
+  for (int m = 0; m < kBinom; ++m) {
+    uint32_t s = 0;
+    for (int k = 0; k < kBinom; ++k) {
+      t.cs[m][k] = s;
+      s += t.c[m][k];
+    }
   }
+  return t;
+}
+constexpr BinomTables kBinomTables = make_binom_tables();
+static_assert(kBinomTables.c[17][8] == 24310u && kBinomTables.c[5][7] == 0u && kBinomTables.cs[4][2] == 5u,
+              "binomial tables");
+__constant__ BinomTables c_binom = kBinomTables;
+
+// Copies of the tables in shared memory (per-thread indices differ, which
+// constant memory would serialise).
+__device__ void fill_binom(uint32_t (*C)[kBinom]) {
+  for (int i = threadIdx.x; i < kBinom * kBinom; i += blockDim.x) (&C[0][0])[i] = (&c_binom.c[0][0])[i];
 }
 
 // The r-th k-subset (colex order) of the m positions pos[0..m), as a bit mask.
@@ -365,18 +387,8 @@ __host__ __device__ constexpr size_t run_member_bytes() {
 }
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// Cs[m][k] = sum of C(m, k') over k' < k: where the size-k group of the subsets
-// of m positions starts in a strings table ordered by size.
 __device__ void fill_binom_prefix(uint32_t (*Cs)[kBinom]) {
-  for (int i = threadIdx.x; i < kBinom * kBinom; i += blockDim.x) {
-    const int m = i / kBinom, k = i % kBinom;
-    uint64_t s = 0, c = 1;  // c = C(m, j), exact in 64-bit for m < 18
-    for (int j = 0; j < k && j <= m; ++j) {
-      s += c;
-      c = c * (uint64_t)(m - j) / (uint64_t)(j + 1);
-    }
-    Cs[m][k] = (uint32_t)s;
-  }
+  for (int i = threadIdx.x; i < kBinom * kBinom; i += blockDim.x) (&Cs[0][0])[i] = (&c_binom.cs[0][0])[i];
 }
 
 // MODE 0: forward, psi real; with a log, each item's rotated pair (psi_i0,
@@ -396,7 +408,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
                                                              const RunBlk* __restrict__ blks, double* partial,
                                                              int pmax, SecCompact cm, typename SCx<T>::V* log,
                                                              const uint16_t* __restrict__ strs,
-                                                             const uint32_t* __restrict__ map) {
+                                                             const uint32_t* __restrict__ map, bool dss) {
   using V = typename SCx<T>::V;
   constexpr bool ADJ = MODE != 0;
   constexpr bool F32 = sizeof(T) == 4;
@@ -442,8 +454,9 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     const uint32_t sbm = unrank_m(ib, R.bpos, R.ub, P.kb, C) | P.gb;
     const uint32_t g = (uint32_t)compact_index(cm, sa, sbm);
     if (MODE != 4) gi[m] = g;
-    if (DSW) {
-      ad[m] = ds_of(__ldcg(pr + 2 * (size_t)g + slot));
+    if (DSW) {  // double-single state layout (dss): the slot already holds the (hi, lo) pair
+      ad[m] = dss ? __ldcg(reinterpret_cast<const float2*>(psi) + 2 * (size_t)g + slot)
+                  : ds_of(__ldcg(pr + 2 * (size_t)g + slot));
     } else if (MODE == 0 || MODE == 3) {
       ar[m] = __ldcg(pr + 2 * (size_t)g + slot);
     } else {
@@ -782,7 +795,10 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     const uint32_t g = gi[m];
     if (DSW) {
       const float2 d = ad[m];
-      __stcg(pw + 2 * (size_t)g + slot, (T)((double)d.x + (double)d.y));
+      if (dss)
+        __stcg(reinterpret_cast<float2*>(psi) + 2 * (size_t)g + slot, d);
+      else
+        __stcg(pw + 2 * (size_t)g + slot, (T)((double)d.x + (double)d.y));
     } else if (MODE == 0 || MODE == 3) {
       __stcg(pw + 2 * (size_t)g + slot, ar[m]);
     } else {
@@ -1213,12 +1229,21 @@ __device__ __forceinline__ float2 flip_sign2(float2 w, uint32_t s) {
 }
 
 // (hi, lo) float split of every member's real amplitude (packed state: psi at 2 m).
-__global__ void k_split_real(const double* __restrict__ st, float2* __restrict__ out, uint64_t members) {
+// dss: the state is already in double-single form, (psi hi, psi lo, lam hi, lam
+// lo) floats per member; the split is copied out and psid[m] gets psi as a double.
+__global__ void k_split_real(const double* __restrict__ st, float2* __restrict__ out, double* __restrict__ psid,
+                             uint64_t members, bool dss) {
   for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < members;
        m += (uint64_t)gridDim.x * blockDim.x) {
-    const double v = st[2 * m];
-    const float hi = __double2float_rn(v);
-    out[m] = make_float2(hi, __double2float_rn(v - (double)hi));
+    if (dss) {
+      const float2 v = __ldcg(reinterpret_cast<const float2*>(st) + 2 * m);
+      out[m] = v;
+      psid[m] = (double)v.x + (double)v.y;
+    } else {
+      const double v = st[2 * m];
+      const float hi = __double2float_rn(v);
+      out[m] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
   }
 }
 
@@ -1227,7 +1252,8 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
                                                             int ke, int ko, const uint16_t* __restrict__ ra,
                                                             const uint16_t* __restrict__ rb, double* partials,
                                                             unsigned* counter, double* out,
-                                                            const float2* __restrict__ split) {
+                                                            const float2* __restrict__ split,
+                                                            const double* __restrict__ psid, bool dss) {
   __shared__ uint32_t C[kBinom][kBinom];
   // each thread's beta singles (entry k of thread t at bsl[k * 256 + t]): the
   // flipped string's rank | weight column o2 * no + v2 << 14 | sign bit << 31
@@ -1240,6 +1266,9 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
   const T* waa = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.waa : (const void*)d.faa);
   const T* wbb = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.wbb : (const void*)d.fbb);
   const T* ps = st;  // psi of member m at ps[2 m]; lambda goes to st[2 m + 1]
+  // psi of member m as a double: pd[pst * m] (double-single state layout: psid, from the split)
+  const double* pd = (DS && dss) ? psid : reinterpret_cast<const double*>(ps);
+  const int pst = (DS && dss) ? 1 : 2;
   const uint64_t items = (uint64_t)cnt_e * cnt_o;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   double acc_e = 0.0, acc_n = 0.0;
@@ -1258,7 +1287,7 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
     const uint32_t ppa = gather_even(p), ppb = gather_even(p >> 1);
     const uint32_t va = ((1u << ne) - 1u) & ~la, vb = ((1u << no) - 1u) & ~lb;
     const size_t rowself = (size_t)ie * cnt_o;
-    const double self = (double)ps[2 * (size_t)it];
+    const double self = (sizeof(T) == 8) ? pd[pst * (size_t)it] : (double)ps[2 * (size_t)it];
     double lx = 0.0, lxs = 0.0;  // lxs: fixed-point weights times psi (units of 2^-e)
     PairAcc<T> pa;
     DsAcc da;
@@ -1282,7 +1311,7 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
         for (uint32_t m2 = rest; m2; m2 &= m2 - 1) w += __ldg(row + __ffs((int)m2));
         if (((ppa >> o) ^ (ppa >> v)) & 1u) w = -w;
         const size_t idx = (size_t)__ldg(ra + (la ^ (1u << o) ^ (1u << v))) * cnt_o + io;
-        lxs = fma(__ll2double_rn(w), (double)ps[2 * idx], lxs);
+        lxs = fma(__ll2double_rn(w), (sizeof(T) == 8) ? pd[pst * idx] : (double)ps[2 * idx], lxs);
       }
     }
     for (uint32_t m1 = lb; m1; m1 &= m1 - 1) {
@@ -1295,7 +1324,7 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
         for (uint32_t m2 = rest; m2; m2 &= m2 - 1) w += __ldg(row + __ffs((int)m2));
         if (((ppb >> o) ^ (ppb >> v)) & 1u) w = -w;
         const size_t idx = rowself + __ldg(rb + (lb ^ (1u << o) ^ (1u << v)));
-        lxs = fma(__ll2double_rn(w), (double)ps[2 * idx], lxs);
+        lxs = fma(__ll2double_rn(w), (sizeof(T) == 8) ? pd[pst * idx] : (double)ps[2 * idx], lxs);
       }
     }
     // opposite-spin doubles: alpha o -> v, beta o2 -> v2; the member's beta singles
@@ -1390,7 +1419,10 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
     lx = fma(lxs, d.inv_fix, lx);
     acc_e = fma(self, lx, acc_e);
     acc_n = fma(self, self, acc_n);
-    st[2 * (size_t)it + 1] = (T)lx;
+    if (DS && dss)
+      reinterpret_cast<float2*>(st)[2 * (size_t)it + 1] = ds_of(lx);
+    else
+      st[2 * (size_t)it + 1] = (T)lx;
   }
   // deterministic two-value grid reduction
   __shared__ bool last;
@@ -1510,7 +1542,7 @@ uint32_t sector_run_capacity(qf_dtype dt, bool adj, bool realst, bool logged) {
 template <int MODE, typename T, bool DSW = false>
 static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, const RunPart* parts,
                           const RunBlk* blks, double* partial, int pmax, const SecCompact& cm, void* log,
-                          const uint16_t* strs, const uint32_t* map, cudaStream_t s) {
+                          const uint16_t* strs, const uint32_t* map, bool dss, cudaStream_t s) {
   static_assert(!DSW || ((MODE == 0 || MODE == 3) && sizeof(T) == 8), "double-single sweeps: complex128 forward "
                                                                       "and logged reverse");
   if (DSW && !map) return cudaErrorInvalidValue;  // the double-single path is the mapped step loop
@@ -1528,7 +1560,8 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
     if (smem > run_smem_max<MODE, T>() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
     k_sector_run<MODE, T, DSW><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
                                                               blks, partial, pmax, cm, static_cast<V*>(log), strs,
-                                                              (MODE == 0 || MODE == 3) ? map : nullptr);
+                                                              (MODE == 0 || MODE == 3) ? map : nullptr,
+                                                              DSW && dss);
     count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1539,25 +1572,27 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
 cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool realst, const RunInfo* runs,
                                int nruns, const RunPart* parts, const RunBlk* blks, int nblk, double* partial,
                                int pmax, double* out, const SecCompact& cm, void* log, const uint16_t* strs,
-                               const uint32_t* map, bool ds, cudaStream_t s) {
+                               const uint32_t* map, bool ds, bool dss, cudaStream_t s) {
   if (nblk <= 0 || nruns <= 0) return cudaSuccess;
   if (!cm.ra || (log && !realst)) return cudaErrorInvalidValue;
+  const bool dsw = dt == QF_C128 && ds && map && (!adj || (realst && log));
+  if (dss && !dsw) return cudaErrorInvalidValue;  // the double-single layout needs the double-single sweeps
   const int prof_slot_ = prof_pre(adj ? QF_K_ADJ_SPARSE : QF_K_SPARSE, s);
   const int mode = !adj ? 0 : !realst ? 2 : log ? 3 : 1;
   cudaError_t e;
-  if (dt == QF_C128 && ds && map && (mode == 0 || mode == 3))
-    e = mode == 0 ? runs_t<0, double, true>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
-                  : runs_t<3, double, true>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s);
+  if (dsw)
+    e = mode == 0 ? runs_t<0, double, true>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s)
+                  : runs_t<3, double, true>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s);
   else if (dt == QF_C128)
-    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
-      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
-      : mode == 2 ? runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
-                  : runs_t<3, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s);
+    e = mode == 0 ? runs_t<0, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s)
+      : mode == 1 ? runs_t<1, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s)
+      : mode == 2 ? runs_t<2, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s)
+                  : runs_t<3, double>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s);
   else
-    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
-      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
-      : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s)
-                  : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, s);
+    e = mode == 0 ? runs_t<0, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s)
+      : mode == 1 ? runs_t<1, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s)
+      : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s)
+                  : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s);
   if (e == cudaSuccess && adj) {
     k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
@@ -1588,8 +1623,8 @@ cudaError_t launch_sector_overlaps(void* psi, qf_dtype dt, const RunInfo* runs, 
   if (!cm.ra) return cudaErrorInvalidValue;
   const int prof_slot_ = prof_pre(QF_K_ADJ_SPARSE, s);
   cudaError_t e = (dt == QF_C128)
-                      ? runs_t<4, double>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, nullptr, s)
-                      : runs_t<4, float>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, nullptr, s);
+                      ? runs_t<4, double>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, nullptr, false, s)
+                      : runs_t<4, float>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, nullptr, false, s);
   if (e == cudaSuccess) {
     k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
@@ -1662,8 +1697,9 @@ static cudaError_t hpsi_dispatch(const void* psi, void* lam, bool realst, bool n
 
 cudaError_t launch_sector_hpsi_direct(void* cpsi, qf_dtype dt, const SecSpace& sp, const SecDirect& d,
                                       const SecCompact& cm, double* partials, unsigned* counter, double* out,
-                                      int nblocks, float2* split, cudaStream_t s) {
+                                      int nblocks, float2* split, double* psid, bool dss, cudaStream_t s) {
   if (d.n > 32 || d.ne != sp.ne || d.no != sp.no || sp.ne > 16) return cudaErrorInvalidValue;
+  if (dss && (dt != QF_C128 || !split || !psid)) return cudaErrorInvalidValue;
   // the beta-single lists: ko (no - ko) entries per thread (at most 64 at 32 qubits);
   // partner ranks must fit 14 bits
   if (sp.cnt_o > (1u << 14)) return cudaErrorInvalidValue;
@@ -1685,19 +1721,19 @@ cudaError_t launch_sector_hpsi_direct(void* cpsi, qf_dtype dt, const SecSpace& s
   };
   if (dt == QF_C128 && split) {
     k_split_real<<<(unsigned)std::min<uint64_t>((items + 255) / 256, 4096), 256, 0, s>>>(
-        static_cast<const double*>(cpsi), split, items);
+        static_cast<const double*>(cpsi), split, psid, items, dss);
     count_launch();
     const auto k = k_sector_hpsi_direct<double, true>;
     k<<<grid(k), 256, smem, s>>>(static_cast<double*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke, sp.ko, cm.ra, cm.rb,
-                                 partials, counter, out, split);
+                                 partials, counter, out, split, psid, dss);
   } else if (dt == QF_C128) {
     const auto k = k_sector_hpsi_direct<double, false>;
     k<<<grid(k), 256, smem, s>>>(static_cast<double*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke, sp.ko, cm.ra, cm.rb,
-                                 partials, counter, out, nullptr);
+                                 partials, counter, out, nullptr, nullptr, false);
   } else {
     const auto k = k_sector_hpsi_direct<float, false>;
     k<<<grid(k), 256, smem, s>>>(static_cast<float*>(cpsi), d, sp.cnt_e, sp.cnt_o, sp.ke, sp.ko, cm.ra, cm.rb,
-                                 partials, counter, out, nullptr);
+                                 partials, counter, out, nullptr, nullptr, false);
   }
   const cudaError_t e = cudaGetLastError();
   prof_post(prof_slot_, s);

@@ -53,6 +53,7 @@ _SIGS = {
     "qf_profile_begin": (ctypes.c_int, [ctypes.c_uint]),
     "qf_profile_read": (ctypes.c_int, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint64), _dp]),
     "qf_profile_end": (ctypes.c_int, []),
+    "qf_sweep_run_items": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), _sz, ctypes.POINTER(_sz)]),
     "qf_expectation_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _sz, _dp, _dp]),
     "qf_selftest_bounded_wait": (ctypes.c_int, [_vp, ctypes.c_double]),
     "qf_probe_fp64_peaks": (ctypes.c_int, [_vp, _dp, _dp]),
@@ -246,6 +247,16 @@ class State:
 
     def clear_plans(self):
         _check(_lib.qf_state_clear_plans(self._h))
+
+    def sweep_run_items(self) -> np.ndarray:
+        """Items of each part-local run of the last sector sweep, in plan order (the
+        forward sweep's launch order; the reverse launches them last to first)."""
+        n = _sz()
+        _check(_lib.qf_sweep_run_items(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.uint64)
+        _check(_lib.qf_sweep_run_items(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n.value,
+                                       ctypes.byref(n)))
+        return out
 
     def fold_scale(self):
         _check(_lib.qf_state_fold_scale(self._h))

@@ -636,3 +636,29 @@ def test_fp64_peak_probe():
     nominal = sms * 2 * 2 * 2.1e9
     assert 0.2 * nominal < fma < 1.2 * nominal, (fma, nominal)
     assert dmma > 0.0
+
+
+def test_sweep_run_items_count_the_sector_pairs():
+    """The part-local sweep's per-run item counts (the units its traffic and flops
+    are scaled by) add up to the brute-force count of (determinant, excitation)
+    pairs: the sector determinants with the excitation's occupied orbitals filled
+    and its virtual orbitals empty (Eq. 19's factors act on exactly these)."""
+    from oracle import sector
+
+    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    det = (1 << cfg["n_el"]) - 1
+    st = qf.State(cfg["n_qubits"], "c128")
+    with pytest.raises(qf.QFError):
+        st.sweep_run_items()
+    st.energy_grad(det, A, t, T)
+    items = st.sweep_run_items()
+    na, nb = sector.counts_of(det)
+    dets = sector.sector_dets(cfg["n_orb"], na, nb)
+    expect = 0
+    for occ, vir in exs:
+        om = sum(1 << q for q in occ)
+        vm = sum(1 << q for q in vir)
+        expect += int(np.count_nonzero(((dets & np.uint64(om)) == np.uint64(om)) & ((dets & np.uint64(vm)) == 0)))
+    assert len(items) >= 1 and (items > 0).all()
+    assert int(items.sum()) == expect
+    st.close()
