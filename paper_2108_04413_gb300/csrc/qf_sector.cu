@@ -343,22 +343,40 @@ __device__ __forceinline__ float2 ds_renorm(float s, float e) {  // Fast2Sum (|s
   const float h = __fadd_rn(s, e);
   return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
-__device__ __forceinline__ float2 ds_mul(float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float e = fmaf(a.x, b.x, -p);  // the exact error of hi * hi
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  return ds_renorm(p, e);
+// a * b as an unnormalised pair: the rounded product of the high parts and, in
+// the low part, its exact error plus both cross terms.
+__device__ __forceinline__ float2 ds_prod(float2 a, float2 b) {
+  const float ph = __fmul_rn(a.x, b.x);
+  float pl = fmaf(a.x, b.x, -ph);
+  pl = fmaf(a.x, b.y, pl);
+  pl = fmaf(a.y, b.x, pl);
+  return make_float2(ph, pl);
 }
-__device__ __forceinline__ float2 ds_add(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);  // TwoSum of the high parts
-  const float bp = __fsub_rn(s, a.x);
-  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bp)), __fsub_rn(b.x, bp));
-  return ds_renorm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+// TwoSum: s + *e == a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float* e) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  *e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return s;
+}
+// x + p + q for p, q from ds_prod: the high parts through two TwoSums, the low
+// parts and both errors summed in float, one renormalisation (27 operations per
+// output; normalising each product and partial sum would take 36).
+__device__ __forceinline__ float2 ds_sum3(float2 x, float2 p, float2 q) {
+  float e1, e2;
+  const float s1 = two_sum(x.x, p.x, &e1);
+  const float s2 = two_sum(s1, q.x, &e2);
+  return ds_renorm(s2, __fadd_rn(__fadd_rn(__fadd_rn(x.y, p.y), __fadd_rn(q.y, e1)), e2));
 }
 // c + a x + b y (one output of a 2x2 block rotation, m = composite - identity)
 __device__ __forceinline__ float2 ds_rot(float2 a, float2 x, float2 b, float2 y, float2 c) {
-  return ds_add(c, ds_add(ds_mul(a, x), ds_mul(b, y)));
+  return ds_sum3(c, ds_prod(a, x), ds_prod(b, y));
+}
+// p + q for p, q from ds_prod (or normalised pairs), renormalised.
+__device__ __forceinline__ float2 ds_sum2(float2 p, float2 q) {
+  float e;
+  const float s = two_sum(p.x, q.x, &e);
+  return ds_renorm(s, __fadd_rn(e, __fadd_rn(p.y, q.y)));
 }
 __device__ __forceinline__ float2 ds_of(double v) {
   const float hi = __double2float_rn(v);
@@ -593,14 +611,17 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
         const unsigned cls = cg ^ (w >> 24);
         if constexpr (DSW) {
           const float2* cd = reinterpret_cast<const float2*>(cw[s % 3]);  // md, then qd
-          const float2 d00 = cd[4 * cls], d01 = cd[4 * cls + 1], d10 = cd[4 * cls + 2], d11 = cd[4 * cls + 3];
+          const float4 da = reinterpret_cast<const float4*>(cd)[2 * cls];      // md[cls][0][0..1]
+          const float4 db = reinterpret_cast<const float4*>(cd)[2 * cls + 1];  // md[cls][1][0..1]
+          const float2 d00 = make_float2(da.x, da.y), d01 = make_float2(da.z, da.w);
+          const float2 d10 = make_float2(db.x, db.y), d11 = make_float2(db.z, db.w);
           const float2 x0 = ad[i0], x1 = ad[i1];
           if (MODE == 3) {
             const float4 pq = first ? lnow : __ldcs(lgp + o_s + it);  // psi pair after this block
             const float2 p0 = make_float2(pq.x, pq.y), p1 = make_float2(pq.z, pq.w);
             // Im <lam|Q|psi> on the pair: q01 (lam0 psi1 - lam1 psi0)
-            const float2 t = ds_add(ds_mul(x0, p1), ds_mul(make_float2(-x1.x, -x1.y), p0));
-            dacc = ds_add(dacc, ds_mul(cd[16 + cls], t));
+            const float2 t = ds_sum2(ds_prod(x0, p1), ds_prod(make_float2(-x1.x, -x1.y), p0));
+            dacc = ds_sum2(dacc, ds_prod(cd[16 + cls], t));
           }
           const float2 o0 = ds_rot(d00, x0, d01, x1, x0), o1 = ds_rot(d10, x0, d11, x1, x1);
           ad[i0] = o0;
