@@ -9,6 +9,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -133,11 +134,48 @@ bool same_arots(const std::vector<qf_arot>& seen, const qf_arot* a, size_t n) {
 
 void qf::set_last_error(const std::string& msg) { t_err = msg; }
 
+// Host allocator of page-locked memory (cudaMallocHost), so that an array
+// refilled and uploaded on every call goes to the device by an asynchronous DMA
+// instead of a staged pageable copy.  Falls back to ordinary memory when the
+// page-locked allocation fails; a 16-byte header records which one it is.
+template <typename T>
+struct PinnedAlloc {
+  using value_type = T;
+  PinnedAlloc() = default;
+  template <typename U>
+  PinnedAlloc(const PinnedAlloc<U>&) {}
+  T* allocate(size_t n) {
+    const size_t bytes = n * sizeof(T) + 16;
+    void* p = nullptr;
+    unsigned char tag = 1;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = std::malloc(bytes);
+      tag = 0;
+      if (!p) throw std::bad_alloc();
+    }
+    static_cast<unsigned char*>(p)[0] = tag;
+    return reinterpret_cast<T*>(static_cast<unsigned char*>(p) + 16);
+  }
+  void deallocate(T* q, size_t) {
+    unsigned char* p = reinterpret_cast<unsigned char*>(q) - 16;
+    if (p[0])
+      cudaFreeHost(p);
+    else
+      std::free(p);
+  }
+  template <typename U>
+  bool operator==(const PinnedAlloc<U>&) const { return true; }
+  template <typename U>
+  bool operator!=(const PinnedAlloc<U>&) const { return false; }
+};
+
 // The part-local run plan of an ansatz in one sector (see build_runs).
 struct SectorRuns {
   std::vector<qf::RunInfo> runs;
   std::vector<qf::RunPart> parts;
-  std::vector<qf::RunBlk> blks;  // forward blocks, then inverse blocks (m, q refilled per call)
+  // forward blocks, then inverse blocks (m, q refilled and uploaded per call)
+  std::vector<qf::RunBlk, PinnedAlloc<qf::RunBlk>> blks;
   int pmax = 0;
   uint64_t logitems = 0;         // (member pair, block) items of one sweep: the forward log's length
   std::vector<uint64_t> run_items;  // the items of each run (they sum to logitems)
@@ -217,6 +255,8 @@ struct qf_state {
   };
   std::unordered_map<uint64_t, AnsatzPlan> ansatz_plans;
   uint64_t parts_key = 0;  // the ansatz plan and sector whose run parts sit in d_runblk
+  // keys of the last Pauli-sum and ansatz plans used: compared first, without hashing
+  uint64_t last_plan_key = 0, last_ansatz_key = 0;
   std::vector<uint64_t> run_items;  // items of each run of the last part-local sweep (launch order)
   uint64_t calls = 0;      // plan-using calls so far (the caches' clock)
   size_t elem() const { return dt == QF_C128 ? 16 : 8; }
@@ -338,11 +378,21 @@ qf_status validate_masks(const qf_state* st, uint64_t x, uint64_t z) {
 // tables (Eq. 18 evaluated pair by pair).
 
 qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan** out) {
+  auto same_terms = [&](const std::vector<qf_term>& seen) {
+    return seen.size() == nt && (nt == 0 || std::memcmp(seen.data(), terms, nt * sizeof(qf_term)) == 0);
+  };
+  // a loop over one Hamiltonian finds its plan with one comparison, no hashing
+  auto last = st->plans.find(st->last_plan_key);
+  if (last != st->plans.end() && same_terms(last->second.terms)) {
+    last->second.last_use = st->calls;
+    *out = &last->second;
+    return QF_OK;
+  }
   const uint64_t key = content_key(terms, nt * sizeof(qf_term), 0x243F6A8885A308D3ull ^ (uint64_t)st->n);
   auto it = st->plans.find(key);
   if (it != st->plans.end()) {
-    const std::vector<qf_term>& seen = it->second.terms;
-    if (seen.size() == nt && (nt == 0 || std::memcmp(seen.data(), terms, nt * sizeof(qf_term)) == 0)) {
+    if (same_terms(it->second.terms)) {
+      st->last_plan_key = key;
       it->second.last_use = st->calls;
       *out = &it->second;
       return QF_OK;
@@ -351,6 +401,13 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     free_plan(it->second);
     st->plans.erase(it);
   }
+  // a term list not seen before: its masks are checked once, here (a cached plan's
+  // terms were checked when it was built)
+  for (size_t k = 0; k < nt; ++k) {
+    qf_status v = validate_masks(st, terms[k].x, terms[k].z);
+    if (v != QF_OK) return v;
+  }
+  st->last_plan_key = key;
   // terms grouped by X mask: ascending x, each group's terms in input order
   std::vector<size_t> order(nt);
   for (size_t i = 0; i < nt; ++i) order[i] = i;
@@ -1135,6 +1192,25 @@ void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
   }
 }
 
+// The inverse block's composites as the adjoints of the forward block's (the
+// composites are unitary), when both blocks list the same rows and sign classes:
+// inv.M[c] = (f.M[c] + I)^dagger - I.  Returns false (nothing written) otherwise.
+bool adjoint_composite(const qf::SparseArgs& f, qf::SparseArgs* inv) {
+  if (f.nr != inv->nr || f.nzc != inv->nzc) return false;
+  for (int i = 0; i < f.nr; ++i)
+    if (f.pat[i] != inv->pat[i]) return false;
+  for (int j = 0; j < f.nzc; ++j)
+    if (f.zc[j] != inv->zc[j]) return false;
+  const int ncls = 1 << f.nzc;
+  for (int c = 0; c < ncls; ++c)
+    for (int i = 0; i < f.nr; ++i)
+      for (int j = 0; j < f.nr; ++j) {
+        const double2 a = f.M[c][j][i];  // the identity's diagonal is real: M - I keeps its shape
+        inv->M[c][i][j] = make_double2(a.x, -a.y);
+      }
+  return true;
+}
+
 // Largest m of the binomial table.  Every caller takes m <= n / 2 (orbitals of
 // one spin) with n <= QF_MAX_QUBITS, and C(33, k) < 2^31, so the table's values
 // are exact in 32 bits and its running products (< 2^36) cannot overflow.
@@ -1848,10 +1924,6 @@ qf_status qf_trotter(qf_state* st, const qf_term* terms, size_t n_terms, double 
 qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, double* re, double* im) {
   if (!st || !re) return fail(QF_EINVAL, "NULL argument");
   if (n_terms && !terms) return fail(QF_EINVAL, "term list is NULL");
-  for (size_t k = 0; k < n_terms; ++k) {
-    qf_status v = validate_masks(st, terms[k].x, terms[k].z);
-    if (v != QF_OK) return v;
-  }
   if (im) *im = 0.0;
   if (n_terms == 0) {
     *re = 0.0;
@@ -1983,11 +2055,31 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     }
   }
   if (st->n < 64 && (det >> st->n)) return fail(QF_EINVAL, "determinant has a bit at or above the qubit count");
+  // block structure: sparse composite blocks (same X, same parameter, commuting) or single rotations
+  using Blk = qf_state::Blk;
+  // the last ansatz plan first (one comparison, no hashing), then by content key
+  uint64_t akey = st->last_ansatz_key;
+  auto ait = st->ansatz_plans.find(akey);
+  if (ait == st->ansatz_plans.end() || !same_arots(ait->second.src, ansatz, n_rot)) {
+    akey = content_key(ansatz, n_rot * sizeof(qf_arot), 0x13198A2E03707344ull ^ (uint64_t)st->n);
+    ait = st->ansatz_plans.find(akey);
+    if (ait != st->ansatz_plans.end() && !same_arots(ait->second.src, ansatz, n_rot)) {
+      // another rotation list with the same key: the key only picks the slot
+      st->ansatz_plans.erase(ait);
+      ait = st->ansatz_plans.end();
+      st->parts_key = 0;
+      st->map_key = 0;
+    }
+  }
+  // a cached plan's rotations had their masks checked when it was built
+  const bool known = ait != st->ansatz_plans.end();
   std::vector<RotIn> r(n_rot);
   std::vector<int32_t> par(n_rot);
   for (size_t k = 0; k < n_rot; ++k) {
-    qf_status v = validate_masks(st, ansatz[k].x, ansatz[k].z);
-    if (v != QF_OK) return v;
+    if (!known) {
+      qf_status v = validate_masks(st, ansatz[k].x, ansatz[k].z);
+      if (v != QF_OK) return v;
+    }
     if (ansatz[k].param < 0 || (size_t)ansatz[k].param >= n_par)
       return fail(QF_EINVAL, "ansatz parameter index out of range");
     const double th = ansatz[k].coeff * t[ansatz[k].param];
@@ -1995,21 +2087,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     r[k] = RotIn{ansatz[k].x, ansatz[k].z, th, ansatz[k].coeff};
     par[k] = ansatz[k].param;
   }
-  for (size_t k = 0; k < n_terms; ++k) {
-    qf_status v = validate_masks(st, terms[k].x, terms[k].z);
-    if (v != QF_OK) return v;
-  }
-  // block structure: sparse composite blocks (same X, same parameter, commuting) or single rotations
-  using Blk = qf_state::Blk;
-  const uint64_t akey = content_key(ansatz, n_rot * sizeof(qf_arot), 0x13198A2E03707344ull ^ (uint64_t)st->n);
-  auto ait = st->ansatz_plans.find(akey);
-  if (ait != st->ansatz_plans.end() && !same_arots(ait->second.src, ansatz, n_rot)) {
-    // another rotation list with the same key: the key only picks the slot
-    st->ansatz_plans.erase(ait);
-    ait = st->ansatz_plans.end();
-    st->parts_key = 0;
-    st->map_key = 0;
-  }
+  st->last_ansatz_key = akey;
   bool fresh = false;
   if (ait == st->ansatz_plans.end()) {
     // first sight of this ansatz: find its block structure
@@ -2050,7 +2128,7 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
       if (!b.sparse) return;
       if (!fresh) {
         refill_sparse(&r[b.i], (int)(b.j - b.i), false, &b.fwd);
-        refill_sparse(&r[b.i], (int)(b.j - b.i), true, &b.inv);
+        if (!adjoint_composite(b.fwd, &b.inv)) refill_sparse(&r[b.i], (int)(b.j - b.i), true, &b.inv);
       }
       if (sec_cached) {
         qf::RunBlk& F = ap.runs.blks[k];
