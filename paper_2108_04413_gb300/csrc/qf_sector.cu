@@ -300,7 +300,8 @@ __device__ __forceinline__ long long warp_sum_fixed(double v, int* e) {
 // 24-bit significand times 2^(e - 150); both parts are aligned, with 29 guard
 // bits, on the warp's largest hi exponent (lo keeps its leading bits down to
 // 2^-53 of the largest value) and added exactly.  The sum is t * 2^(*e - 179),
-// |t| < 2^59, so eight warps' sums stay below 2^62.
+// |t| < 2^59, so the sums of up to twelve warps (a run CTA has at most 384
+// threads) stay below 1.5 * 2^62.
 __device__ __forceinline__ long long f_aligned(float v, int emax) {
   const int b = __float_as_int(v);
   const int ex = (b >> 23) & 0xFF;
@@ -325,7 +326,7 @@ __device__ __forceinline__ double scale_pow2(double d, int k) {
   return d * __longlong_as_double((long long)(k + 1023) << 52);
 }
 
-// Sum of the lanes' (t, e) pairs from warp_sum_fixed (at most 8 lanes nonzero) as
+// Sum of the lanes' (t, e) pairs from warp_sum_fixed (one lane per warp of the CTA nonzero, at most 12) as
 // one double: aligned on the largest e, added exactly, converted once.
 __device__ __forceinline__ double warp_fixed_to_double(long long t, int e) {
   const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)(t != 0 ? e : 0));
@@ -383,16 +384,25 @@ __device__ __forceinline__ float2 ds_of(double v) {
   return make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
-constexpr int kRunThreads = 256;
-constexpr int kRunWarps = kRunThreads / 32;
+constexpr int kRunThreads = 256;  // threads of a part-local run CTA (item maps, FP64 and FP32 sweeps)
 constexpr int kRunBlkWords = sizeof(RunBlk) / 4;
+// Threads of a run CTA.  A run's time is that of its largest parts, whose block
+// steps take ceil(items / threads) item rounds each, so the double-single sweeps
+// take as many threads as still leave every part of a run resident at once
+// (512 parts on 152 SMs: 4 CTAs per SM): 384 for the forward (40 registers), 288
+// for the reverse (56 registers).
+template <int MODE, bool DSW>
+__host__ __device__ constexpr int run_threads() {
+  return !DSW ? kRunThreads : MODE == 0 ? 384 : 288;
+}
 // Coefficient words a mapped sweep step copies: m then q (FP64) or mf then qf (FP32).
 constexpr int kCoefWordsMax = 64;
 static_assert(offsetof(RunBlk, q) == offsetof(RunBlk, m) + sizeof(double) * 16 &&
                   offsetof(RunBlk, qf) == offsetof(RunBlk, mf) + sizeof(float) * 16 && kSparseMaxCls == 4 &&
                   offsetof(RunBlk, m) % 8 == 0,
               "coefficient layout of RunBlk");
-static_assert(sizeof(RunBlk) % 4 == 0 && kRunBlkWords <= kRunThreads, "run descriptor copy layout");
+static_assert(sizeof(RunBlk) % 4 == 0 && kRunBlkWords <= kRunThreads && kRunBlkWords <= 288,
+              "run descriptor copy layout");
 
 // Shared-memory bytes per member: psi real parts (forward), (psi, lam) packed
 // real pairs (reverse, real), psi and lam complex (reverse, complex), or lam's
@@ -420,14 +430,14 @@ __device__ void fill_binom_prefix(uint32_t (*Cs)[kBinom]) {
 // the same (psi, lam), nothing rotated or written back (operator-pool gradients).
 // Overlaps accumulate in the state's precision (FP64 for complex128, FP32 for
 // complex64); each part's overlap with a block is written to partial in FP64.
-template <int MODE, typename T, bool DSW = false>
-__global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* psi, typename SCx<T>::V* lam,
-                                                             RunInfo run, const RunPart* __restrict__ parts,
-                                                             const RunBlk* __restrict__ blks, double* partial,
-                                                             int pmax, SecCompact cm, typename SCx<T>::V* log,
-                                                             const uint16_t* __restrict__ strs,
-                                                             const uint32_t* __restrict__ map, bool dss) {
+template <int MODE, typename T, bool DSW>
+__device__ __forceinline__ void sector_run_body(typename SCx<T>::V* psi, typename SCx<T>::V* lam, RunInfo run,
+                                                const RunPart* __restrict__ parts, const RunBlk* __restrict__ blks,
+                                                double* partial, int pmax, SecCompact cm, typename SCx<T>::V* log,
+                                                const uint16_t* __restrict__ strs,
+                                                const uint32_t* __restrict__ map, bool dss) {
   using V = typename SCx<T>::V;
+  constexpr int NT = run_threads<MODE, DSW>(), NW = NT / 32;
   constexpr bool ADJ = MODE != 0;
   constexpr bool F32 = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -438,7 +448,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   __shared__ RunPart P;
   // every thread's overlap with the last two blocks: block s's values are summed
   // by one warp during block s + 1 and rewritten after block s + 1's barrier
-  __shared__ T red[ADJ ? 2 : 1][kRunThreads];
+  __shared__ T red[ADJ ? 2 : 1][(ADJ && !DSW) ? NT : 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   fill_binom(C);
   fill_binom_prefix(Cs);
@@ -466,7 +476,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   // the real slot each member moves: psi's real part (MODE 0), lam's in psi's imaginary slot (MODE 3)
   const int slot = MODE == 3 ? 1 : 0;
   const T* pr = reinterpret_cast<const T*>(psi);
-  for (uint32_t m = tid; m < size; m += kRunThreads) {
+  for (uint32_t m = tid; m < size; m += NT) {
     const uint32_t ia = m / P.cntb, ib = m - ia * P.cntb;
     const uint32_t sa = unrank_m(ia, R.apos, R.ua, P.ka, C) | P.ga;
     const uint32_t sbm = unrank_m(ib, R.bpos, R.ub, P.kb, C) | P.gb;
@@ -504,7 +514,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   // often) over the rows of the pw warps that had items, in warp order, then
   // lane order by a butterfly.  Deterministic.
   auto reduce_block = [&](int ps, int pw) {
-    if (warp != kRunWarps - 1 - (ps & 3)) return;
+    if (warp != NW - 1 - (ps & 3)) return;
     T v = T(0);
     if (pw > 0) {
       const T* rr = red[ps & 1];
@@ -531,8 +541,8 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     __shared__ uint32_t stn[kRunMaxBlocks], sto[kRunMaxBlocks];
     __shared__ uint8_t stc[kRunMaxBlocks];
     __shared__ __align__(16) uint32_t cw[3][kCoefWordsMax];
-    __shared__ long long wtot[2][kRunWarps];  // per-warp overlap sums of the last two steps
-    __shared__ int wexp[2][kRunWarps];
+    __shared__ long long wtot[2][NW];  // per-warp overlap sums of the last two steps
+    __shared__ int wexp[2][NW];
     constexpr int kCw = DSW ? (MODE == 3 ? 40 : 32) : F32 ? (MODE == 3 ? 20 : 16) : (MODE == 3 ? 64 : 32);
     constexpr size_t kCoff = DSW ? offsetof(RunBlk, md) : F32 ? offsetof(RunBlk, mf) : offsetof(RunBlk, m);
     using LV = typename std::conditional<DSW, float4, V>::type;  // a log pair
@@ -540,7 +550,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     auto coef_word = [&](int st) {
       return __ldg(reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(blks + blk_of(st)) + kCoff) + tid);
     };
-    for (int f = tid; f < nb; f += kRunThreads) {  // f: the block's position in forward order
+    for (int f = tid; f < nb; f += NT) {  // f: the block's position in forward order
       const RunBlk* Bg = blks + run.b0 + f;
       const int ne = __ldg(&Bg->ne), no = __ldg(&Bg->no), nzc = __ldg(&Bg->nzc);
       const int ke = P.ka - __ldg(&Bg->e0), ko = P.kb - __ldg(&Bg->o0);
@@ -581,7 +591,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     if (nb > 2 && tid < kCw) nxtc = coef_word(2);
     // the previous step's per-warp sums, combined by one warp into the block's partial
     auto reduce_fixed = [&](int ps, int pw) {
-      if (warp != kRunWarps - 1 - (ps & 3)) return;
+      if (warp != NW - 1 - (ps & 3)) return;
       const long long t = lane < pw ? wtot[ps & 1][lane] : 0ll;
       const int e = lane < pw ? wexp[ps & 1][lane] : 0;
       const double v = warp_fixed_to_double(t, e);
@@ -604,7 +614,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       const LV lnow = lq0;
       T acc = T(0);
       float2 dacc = make_float2(0.0f, 0.0f);  // DSW overlap
-      for (uint32_t it = tid; it < n_s; it += kRunThreads) {
+      for (uint32_t it = tid; it < n_s; it += NT) {
         const bool first = it == (uint32_t)tid;
         const uint32_t w = first ? wnow : __ldg(mp + o_s + it);
         const uint32_t i0 = w & 0xFFFu, i1 = (w >> 12) & 0xFFFu;
@@ -652,7 +662,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
         }  // DSW
       }
       if (ADJ) {
-        pend_w = n_s >= (uint32_t)kRunThreads ? kRunWarps : (int)((n_s + 31) / 32);
+        pend_w = n_s >= (uint32_t)NT ? NW : (int)((n_s + 31) / 32);
         if (IRED) {
           if (warp < pend_w) {  // warps past pend_w hold no items this step
             int e;
@@ -713,7 +723,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       const uint32_t sa0 = tab ? B.lsa + Cs[B.ne][ke] : 0u;
       const uint32_t sb0 = tab ? B.lsb + Cs[B.no][ko] : 0u;
       const float inv_co = __frcp_rn((float)co);  // items < 2^24: the estimate is off by at most one
-      for (uint32_t it = tid; it < items; it += kRunThreads) {
+      for (uint32_t it = tid; it < items; it += NT) {
         uint32_t ie = (uint32_t)((float)it * inv_co);
         if (ie * co > it) --ie;
         else if ((ie + 1) * co <= it) ++ie;
@@ -804,7 +814,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
     }
     if (ADJ) {
       red[s & 1][tid] = acc;
-      pend_w = nitems >= (uint64_t)kRunThreads ? kRunWarps : (int)((nitems + 31) / 32);
+      pend_w = nitems >= (uint64_t)NT ? NW : (int)((nitems + 31) / 32);
     }
     if (s + 1 < nb && tid < kRunBlkWords) reinterpret_cast<uint32_t*>(&sb[(s + 1) & 1])[tid] = nxt;
     __syncthreads();
@@ -812,7 +822,7 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
   if (ADJ && nb > 0 && !mp) reduce_block(nb - 1, pend_w);
   if (MODE == 4) return;  // read only
   T* pw = reinterpret_cast<T*>(psi);
-  for (uint32_t m = tid; m < size; m += kRunThreads) {
+  for (uint32_t m = tid; m < size; m += NT) {
     const uint32_t g = gi[m];
     if (DSW) {
       const float2 d = ad[m];
@@ -827,6 +837,29 @@ __global__ void __launch_bounds__(kRunThreads) k_sector_run(typename SCx<T>::V* 
       if (MODE == 2) __stcg(lam + g, lv[m]);
     }
   }
+}
+
+// The sweeps in FP64 / FP32 (256 threads) and in double-single arithmetic
+// (run_threads threads).
+#define QF_RUN_ARGS                                                                                              \
+  typename SCx<T>::V *psi, typename SCx<T>::V *lam, RunInfo run, const RunPart *__restrict__ parts,               \
+      const RunBlk *__restrict__ blks, double *partial, int pmax, SecCompact cm, typename SCx<T>::V *log,         \
+      const uint16_t *__restrict__ strs, const uint32_t *__restrict__ map, bool dss
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kRunThreads) k_sector_run(QF_RUN_ARGS) {
+  sector_run_body<MODE, T, false>(psi, lam, run, parts, blks, partial, pmax, cm, log, strs, map, dss);
+}
+template <int MODE, typename T>
+__global__ void __launch_bounds__(run_threads<MODE, true>()) k_sector_run_ds(QF_RUN_ARGS) {
+  sector_run_body<MODE, T, true>(psi, lam, run, parts, blks, partial, pmax, cm, log, strs, map, dss);
+}
+#undef QF_RUN_ARGS
+template <int MODE, typename T, bool DSW>
+constexpr auto run_kernel() {
+  if constexpr (DSW)
+    return k_sector_run_ds<MODE, T>;
+  else
+    return k_sector_run<MODE, T>;
 }
 
 // Item maps (RunPart::mapbase): for the part representing each class, every
@@ -1571,7 +1604,7 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
   static std::once_flag once;  // allow the opt-in shared memory size, once per process
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_sector_run<MODE, T, DSW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr = cudaFuncSetAttribute(run_kernel<MODE, T, DSW>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)run_smem_max<MODE, T>());
   });
   if (attr != cudaSuccess) return attr;
@@ -1579,10 +1612,9 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
     const RunInfo& R = runs[MODE != 0 ? nruns - 1 - r : r];
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
     if (smem > run_smem_max<MODE, T>() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
-    k_sector_run<MODE, T, DSW><<<R.nparts, kRunThreads, smem, s>>>(static_cast<V*>(psi), static_cast<V*>(lam), R, parts,
-                                                              blks, partial, pmax, cm, static_cast<V*>(log), strs,
-                                                              (MODE == 0 || MODE == 3) ? map : nullptr,
-                                                              DSW && dss);
+    run_kernel<MODE, T, DSW>()<<<R.nparts, run_threads<MODE, DSW>(), smem, s>>>(
+        static_cast<V*>(psi), static_cast<V*>(lam), R, parts, blks, partial, pmax, cm, static_cast<V*>(log), strs,
+        (MODE == 0 || MODE == 3) ? map : nullptr, DSW && dss);
     count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
