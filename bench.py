@@ -563,11 +563,16 @@ def serving_systems(qubit_counts=(10, 12, 14, 16, 18, 20, 22)):
 
 def serving_leg(args, count: int = 240, rate: float = 200.0, saturate: int = 960):
     """Poisson stream (seeded, `rate` requests/s) of energy+gradient requests with
-    qubit counts uniform in {10,...,22}, t ~ N(0, 0.1): the complex64 continuous-
-    batching server (4 workers, resident states, HBM-budget admission) against
-    one-at-a-time complex128 solves of the same stream (one worker).  Each mode is
-    also driven closed-loop -- `saturate` requests of the same mix all queued at
-    once -- for its saturated throughput; throughput_multiple compares those."""
+    qubit counts uniform in {10,...,22}, t ~ N(0, 0.1), served three ways: the
+    complex64 continuous-batching server (8 workers, up to 4 resident handles per
+    system, HBM-budget admission), the same with small systems (<= 16 qubits)
+    grouped up to 32 requests per qf_energy_grad_multi call (one launch, one CTA
+    per request), and one-at-a-time complex128 solves (one worker, one handle per
+    system).  Each mode is also driven
+    closed-loop -- `saturate` requests of the same mix all queued at once -- for
+    its saturated throughput; throughput_multiple compares the best complex64
+    mode with one-at-a-time complex128.  A second closed-loop stream of small
+    systems only ({10, 12, 14} qubits) isolates the grouped launch."""
     from paper_2108_04413_gb300.serving import GpuExecutor, Request, Server, latency_stats, replay
     from workloads import poisson_arrivals
 
@@ -581,27 +586,51 @@ def serving_leg(args, count: int = 240, rate: float = 200.0, saturate: int = 960
     def stream(m, timed):
         return [Request(i, keys[picks[i]], ts[i], float(arrivals[i]) if timed else 0.0) for i in range(m)]
 
-    out = {"requests": count, "arrival_rate_rps": rate, "qubits": "uniform in {10,...,22}",
-           "saturated_requests": saturate}
-    for label, dtype, workers in (("continuous_batching_c64", "c64", 4), ("one_at_a_time_c128", "c128", 1)):
-        srv = Server(systems, GpuExecutor(dtype), workers=workers, hbm_budget=32 << 30, dtype=dtype)
-        replay(srv, [Request(-1 - i, k, np.zeros(npar[k]), 0.0) for i, k in enumerate(keys)], realtime=False)
+    def serve(dtype, workers, batch, reqs_timed, reqs_sat, warm_keys, replicas=1):
+        srv = Server(systems, GpuExecutor(dtype), workers=workers, hbm_budget=32 << 30, dtype=dtype,
+                     batch=batch, batch_qubits=16, replicas=replicas)
+        replay(srv, [Request(-1 - i, k, np.zeros(npar[k]), 0.0) for i, k in enumerate(warm_keys)], realtime=False)
         srv.done.clear()  # warm-up: one request per system plans and allocates its state
+        st = {}
+        if reqs_timed:
+            srv.t0 = srv.clock()
+            st = latency_stats(replay(srv, reqs_timed))
+            st["max_concurrent"] = srv.max_concurrent
+            srv.done.clear()
         srv.t0 = srv.clock()
-        st = latency_stats(replay(srv, stream(count, True)))
-        st["max_concurrent"] = srv.max_concurrent
-        srv.done.clear()
-        srv.t0 = srv.clock()
-        sat = latency_stats(replay(srv, stream(saturate, False), realtime=False))
-        srv.close()
+        sat = latency_stats(replay(srv, reqs_sat, realtime=False))
         st["saturated_throughput_rps"] = sat["throughput_rps"]
         st["saturated_failed"] = sat["failed"]
-        out[label] = st
-    b = out["one_at_a_time_c128"]
-    c = out["continuous_batching_c64"]
-    out["throughput_multiple"] = (c["saturated_throughput_rps"] / b["saturated_throughput_rps"]
-                                  if b["saturated_throughput_rps"] else None)
-    out["throughput_multiple_note"] = "saturated (closed-loop) throughputs; at 200 req/s both keep up"
+        st["grouped_calls"] = srv.batches
+        srv.close()
+        return st
+
+    out = {"requests": count, "arrival_rate_rps": rate, "qubits": "uniform in {10,...,22}",
+           "saturated_requests": saturate}
+    for label, dtype, workers, batch, replicas in (("continuous_batching_c64", "c64", 8, 1, 4),
+                                                   ("grouped_small_c64", "c64", 8, 32, 4),
+                                                   ("one_at_a_time_c128", "c128", 1, 1, 1)):
+        out[label] = serve(dtype, workers, batch, stream(count, True), stream(saturate, False), keys, replicas)
+        out[label]["server"] = {"workers": workers, "replicas": replicas, "group": batch}
+    b = out["one_at_a_time_c128"]["saturated_throughput_rps"]
+    best = max(out["continuous_batching_c64"]["saturated_throughput_rps"],
+               out["grouped_small_c64"]["saturated_throughput_rps"])
+    out["throughput_multiple"] = best / b if b else None
+    out["throughput_multiple_note"] = ("best complex64 mode over one-at-a-time complex128, saturated (closed-loop) "
+                                       "throughputs; at 200 req/s every mode keeps up")
+    # small systems only: the grouped launch against one call per request
+    small = [k for k in keys if systems[k].n <= 14]
+    spick = rng.integers(0, len(small), saturate)
+    tsmall = [rng.normal(0.0, 0.1, npar[small[k]]) for k in spick]
+    sreqs = lambda: [Request(i, small[spick[i]], tsmall[i], 0.0) for i in range(saturate)]  # noqa: E731
+    one = serve("c64", 8, 1, None, sreqs(), small, 4)
+    grp = serve("c64", 8, 32, None, sreqs(), small, 4)
+    out["small_systems"] = {"qubits": sorted({systems[k].n for k in small}), "requests": saturate,
+                            "per_request_calls_rps": one["saturated_throughput_rps"],
+                            "grouped_calls_rps": grp["saturated_throughput_rps"],
+                            "grouped_calls": grp["grouped_calls"],
+                            "grouped_multiple": (grp["saturated_throughput_rps"] / one["saturated_throughput_rps"]
+                                                 if one["saturated_throughput_rps"] else None)}
     return out
 
 

@@ -109,6 +109,24 @@ qf_status qf_expectation(qf_state* st, const qf_term* terms, size_t n_terms, dou
 qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
                          size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad);
 
+/* Energy and gradient for n_req parameter vectors of one system (the paper has
+ * no counterpart: a serving path for many small requests).  t holds n_req rows
+ * of n_par parameters; energies[q] and, when grads is not NULL, grads[q * n_par ..]
+ * are those qf_energy_grad gives for row q (equal within rounding: the
+ * summation order differs).  Once the handle has planned this ansatz and
+ * Hamiltonian for this sector (a qf_energy_grad call does; the first call here
+ * runs its first row through qf_energy_grad to do so), and when every block is
+ * a real two-row sector block, H has direct sector tables and the sector's
+ * psi and lambda fit in one CTA's shared memory (about 6000 members in
+ * QF_C128, 12000 in QF_C64: up to 16 qubits at half filling), all rows run in
+ * ONE kernel launch, one CTA per row, each holding its state in shared memory
+ * through the forward blocks, H|psi> and the reverse blocks.  Otherwise the rows
+ * run one after another through qf_energy_grad.  Errors as qf_energy_grad.
+ * Synchronises the stream; leaves the state holding |det>. */
+qf_status qf_energy_grad_multi(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                               size_t n_par, size_t n_req, const qf_term* terms, size_t n_terms, double* energies,
+                               double* grads);
+
 /* PQE residuals (Sec. PQE, Eq. 23): for each of the n_dets basis determinants b,
  * res[2k] + i res[2k+1] = <b| U(t)^+ H U(t) |det> / |U(t) det|, with the energy
  * and, when grad is not NULL, the gradient of qf_energy_grad (same arguments,

@@ -229,6 +229,19 @@ struct qf_state {
   size_t log_cap = 0;
   bool log_failed = false;   // the log did not fit: later calls un-rotate psi instead
   int hpsi_mode = QF_HPSI_DS;
+  // several parameter sets in one launch (qf_energy_grad_multi): the plan's block
+  // geometries for one sector (small_key), per-request coefficients and results
+  void* d_small = nullptr;
+  size_t small_cap = 0;
+  uint64_t small_key = 0;
+  void* d_scoef = nullptr;
+  size_t scoef_cap = 0;
+  void* h_scoef = nullptr;  // page-locked
+  size_t h_scoef_cap = 0;
+  void* d_sout = nullptr;
+  size_t sout_cap = 0;
+  void* h_sout = nullptr;  // page-locked
+  size_t h_sout_cap = 0;
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
   double* d_out = nullptr;
@@ -1122,7 +1135,13 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
 // r ^ x, and the active rows are a union of such pairs, so each rotation maps
 // the active rows onto themselves and the composite restricted to them is the
 // product of the restricted rotations.
-void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
+// The composites of a block's rotations r[0..m) (inverse: of the inverse rotations;
+// a block's rotations commute) for its rows and sign classes in a: store(c, i, j, d)
+// receives entry (i, j) of class c's composite minus the identity.  Reads only
+// a's structure (rows, support, classes).
+template <typename Store>
+void compose_sparse(const RotIn* r, int m, bool inverse, const qf::SparseArgs& sa, Store&& store) {
+  const qf::SparseArgs* a = &sa;
   const int u = a->u, nr = a->nr;
   const uint64_t x = r[0].x;
   const int xl = (1 << u) - 1;
@@ -1164,8 +1183,9 @@ void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
     snv[k] = std::sin(th);
   }
   for (int c = 0; c < ncls; ++c) {
-    cplx M[qf::kSparseMaxRows][qf::kSparseMaxRows] = {};
-    for (int i = 0; i < nr; ++i) M[i][i] = 1.0;
+    cplx M[qf::kSparseMaxRows][qf::kSparseMaxRows];
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < nr; ++j) M[i][j] = (i == j) ? 1.0 : 0.0;
     for (int k = 0; k < m; ++k) {
       const uint64_t zo = r[k].z & ~x;
       double sig = 1.0;
@@ -1185,11 +1205,13 @@ void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
         for (int j = 0; j < nr; ++j) M[i][j] = N2[i][j];
     }
     for (int i = 0; i < nr; ++i)
-      for (int j = 0; j < nr; ++j) {
-        const cplx d = M[i][j] - ((i == j) ? 1.0 : 0.0);
-        a->M[c][i][j] = make_double2(d.real(), d.imag());
-      }
+      for (int j = 0; j < nr; ++j) store(c, i, j, M[i][j] - ((i == j) ? 1.0 : 0.0));
   }
+}
+
+void refill_sparse(const RotIn* r, int m, bool inverse, qf::SparseArgs* a) {
+  compose_sparse(r, m, inverse, *a,
+                 [a](int c, int i, int j, cplx d) { a->M[c][i][j] = make_double2(d.real(), d.imag()); });
 }
 
 // The inverse block's composites as the adjoints of the forward block's (the
@@ -1855,6 +1877,11 @@ qf_status qf_state_destroy(qf_state* st) {
   cudaFree(st->d_map);
   cudaFree(st->d_idx);
   cudaFree(st->d_poolblk);
+  cudaFree(st->d_small);
+  cudaFree(st->d_scoef);
+  cudaFree(st->d_sout);
+  cudaFreeHost(st->h_scoef);
+  cudaFreeHost(st->h_sout);
   cudaFree(st->d_partials);
   cudaFree(st->d_counter);
   cudaFree(st->d_out);
@@ -2487,6 +2514,217 @@ qf_status qf_energy_grad(qf_state* st, uint64_t det, const qf_arot* ansatz, size
                          size_t n_par, const qf_term* terms, size_t n_terms, double* energy, double* grad) {
   if (n_par && !grad) return fail(QF_EINVAL, "NULL array");
   return energy_grad_impl(st, det, ansatz, n_rot, t, n_par, terms, n_terms, energy, grad, nullptr, 0, nullptr);
+}
+
+namespace {
+
+qf_status ensure_host(void** p, size_t* cap, size_t bytes, const char* what) {
+  if (bytes <= *cap) return QF_OK;
+  cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMallocHost(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(QF_ENOMEM, std::string("cudaMallocHost(") + what + ") failed");
+  }
+  *cap = bytes;
+  return QF_OK;
+}
+
+// Requests r0 .. n_req - 1 of qf_energy_grad_multi in one launch (qf::SmallEval),
+// when the handle's cached plans allow it: the ansatz and the Hamiltonian planned
+// before for this sector, every block a real two-row sector block, the direct
+// H|psi> tables, and a sector small enough for one CTA's shared memory.
+// Otherwise returns QF_OK with *done = false and touches nothing.
+qf_status multi_small(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                      size_t n_par, size_t r0, size_t n_req, const qf_term* terms, size_t n_terms,
+                      double* energies, double* grads, bool* done) {
+  *done = false;
+  const int n = st->n;
+  if (n > 32 || n_terms == 0 || n_rot == 0 || r0 >= n_req) return QF_OK;
+  auto ait = st->ansatz_plans.find(st->last_ansatz_key);
+  if (ait == st->ansatz_plans.end() || !same_arots(ait->second.src, ansatz, n_rot)) {
+    ait = st->ansatz_plans.find(content_key(ansatz, n_rot * sizeof(qf_arot), 0x13198A2E03707344ull ^ (uint64_t)n));
+    if (ait == st->ansatz_plans.end() || !same_arots(ait->second.src, ansatz, n_rot)) return QF_OK;
+  }
+  auto same_terms = [&](const std::vector<qf_term>& seen) {
+    return seen.size() == n_terms && std::memcmp(seen.data(), terms, n_terms * sizeof(qf_term)) == 0;
+  };
+  auto pit = st->plans.find(st->last_plan_key);
+  if (pit == st->plans.end() || !same_terms(pit->second.terms)) {
+    pit = st->plans.find(content_key(terms, n_terms * sizeof(qf_term), 0x243F6A8885A308D3ull ^ (uint64_t)n));
+    if (pit == st->plans.end() || !same_terms(pit->second.terms)) return QF_OK;
+  }
+  qf_state::AnsatzPlan& ap = ait->second;
+  ExpPlan& hp = pit->second;
+  if (hp.has_odd || hp.direct != 1) return QF_OK;
+  const int na = popc(det & kEvenMask), nbeta = popc(det & ~kEvenMask);
+  const uint64_t cap = std::min<uint64_t>(
+      kRunPartTarget, std::min(qf::sector_run_capacity(st->dt, false, true, false),
+                               qf::sector_run_capacity(st->dt, true, true, false)));
+  if (!(ap.sec_ok && ap.sec_n == n && ap.sec_na == na && ap.sec_nb == nbeta && ap.sec_cap == cap)) return QF_OK;
+  const qf::SecSpace sp = sector_space(n, na, nbeta);
+  const uint32_t members = sp.cnt_e * sp.cnt_o;
+  if (qf::small_eval_smem(st->dt, members, sp.ko, sp.no) == 0) return QF_OK;
+  const std::vector<qf_state::Blk>& blocks = ap.blocks;
+  const size_t nblk = blocks.size();
+  for (const auto& b : blocks) {  // the reverse reads the forward geometry with the inverse's coefficients
+    if (!b.sparse || b.fwd.nr != 2 || b.inv.nr != 2 || b.fwd.nzc != b.inv.nzc) return QF_OK;
+    if (b.fwd.pat[0] != b.inv.pat[0] || b.fwd.pat[1] != b.inv.pat[1]) return QF_OK;
+    for (int j = 0; j < b.fwd.nzc; ++j)
+      if (b.fwd.zc[j] != b.inv.zc[j]) return QF_OK;
+  }
+  // parameters: indices and angles of every request
+  for (size_t k = 0; k < n_rot; ++k)
+    if (ansatz[k].param < 0 || (size_t)ansatz[k].param >= n_par)
+      return fail(QF_EINVAL, "ansatz parameter index out of range");
+  for (size_t q = r0; q < n_req; ++q)
+    for (size_t k = 0; k < n_rot; ++k)
+      if (!std::isfinite(ansatz[k].coeff * t[q * n_par + ansatz[k].param]))
+        return fail(QF_EINVAL, "theta is not finite");
+  // the forward blocks' geometry for this sector, on the device once
+  const uint64_t skey = content_key(nullptr, 0, ait->first ^ ((uint64_t)na << 40) ^ ((uint64_t)nbeta << 48)) | 1ull;
+  if (st->small_key != skey) {
+    std::vector<qf::SecBlk> g(nblk);
+    for (size_t b = 0; b < nblk; ++b)
+      if (!to_secblk(blocks[b].fwd, n, na, nbeta, false, &g[b])) return QF_OK;
+    qf_status bs = ensure_buf(&st->d_small, &st->small_cap, nblk * sizeof(qf::SecBlk), "small-request blocks");
+    if (bs != QF_OK) return bs;
+    QF_CUDA(h2d(st->d_small, g.data(), nblk * sizeof(qf::SecBlk), st->stream));
+    QF_CUDA(cudaStreamSynchronize(st->stream));  // g is freed on return
+    st->small_key = skey;
+  }
+  qf::SecCompact cm{};
+  qf_status cs = ensure_compact(st, sp, na, nbeta, &cm);
+  if (cs != QF_OK) return cs;
+  ap.last_use = hp.last_use = st->calls;
+  st->last_ansatz_key = ait->first;
+  st->last_plan_key = pit->first;
+  // per request and block: the forward composite minus I, its transpose (the
+  // inverse's, the composite being real orthogonal), and the inverse's generator
+  // entry q01 (angle independent), in the state's real type
+  const size_t nr = n_req - r0;
+  const bool c128 = st->dt == QF_C128;
+  const size_t rec = (size_t)qf::kSmallCoef * (c128 ? sizeof(double) : sizeof(float));
+  qf_status hs = ensure_host(&st->h_scoef, &st->h_scoef_cap, nr * nblk * rec, "small-request coefficients");
+  if (hs != QF_OK) return hs;
+  std::atomic<bool> real(true);
+  qf::HostPool::get().parallel_for(nr * nblk, 64, [&](size_t k) {
+    const size_t q = k / nblk, b = k - q * nblk;
+    const qf_state::Blk& B = blocks[b];
+    const double* tq = t + (r0 + q) * n_par;
+    const int len = (int)(B.j - B.i);
+    RotIn rb_buf[16];
+    std::vector<RotIn> rb_heap;
+    RotIn* rr = rb_buf;
+    if (len > 16) {
+      rb_heap.resize(len);
+      rr = rb_heap.data();
+    }
+    for (int u = 0; u < len; ++u) {
+      const qf_arot& a = ansatz[B.i + u];
+      rr[u] = RotIn{a.x, a.z, a.coeff * tq[a.param], a.coeff};
+    }
+    double m[4][2][2] = {};
+    bool ok = true;
+    compose_sparse(rr, len, false, B.fwd, [&](int c, int i, int j, cplx d) {
+      m[c][i][j] = d.real();
+      if (d.imag() != 0.0) ok = false;
+    });
+    double mi[4][2][2], qi[4][2][2];
+    if (!sector_mq(B.inv, true, mi, qi)) ok = false;
+    if (!ok) real = false;
+    const int ncls = 1 << B.fwd.nzc;
+    double v[qf::kSmallCoef];
+    for (int c = 0; c < 4; ++c) {
+      const int cc = c < ncls ? c : 0;
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          v[4 * c + 2 * i + j] = m[cc][i][j];
+          v[16 + 4 * c + 2 * i + j] = m[cc][j][i];
+        }
+      v[32 + c] = qi[c][0][1];
+    }
+    unsigned char* dst = static_cast<unsigned char*>(st->h_scoef) + k * rec;
+    if (c128) {
+      std::memcpy(dst, v, sizeof(v));
+    } else {
+      float f[qf::kSmallCoef];
+      for (int u = 0; u < qf::kSmallCoef; ++u) f[u] = (float)v[u];
+      std::memcpy(dst, f, sizeof(f));
+    }
+  });
+  if (!real.load()) return QF_OK;
+  const size_t outn = nr * (nblk + 2);
+  qf_status bs = ensure_buf(&st->d_scoef, &st->scoef_cap, nr * nblk * rec, "small-request coefficients");
+  if (bs == QF_OK) bs = ensure_buf(&st->d_sout, &st->sout_cap, outn * sizeof(double), "small-request results");
+  if (bs == QF_OK) bs = ensure_host(&st->h_sout, &st->h_sout_cap, outn * sizeof(double), "small-request results");
+  if (bs != QF_OK) return bs;
+  QF_CUDA(h2d(st->d_scoef, st->h_scoef, nr * nblk * rec, st->stream));
+  qf::SmallEval a{};
+  a.blks = static_cast<const qf::SecBlk*>(st->d_small);
+  a.nblk = (int)nblk;
+  a.coef = st->d_scoef;
+  a.d = hp.dtab;
+  a.cnt_e = sp.cnt_e;
+  a.cnt_o = sp.cnt_o;
+  a.ke = sp.ke;
+  a.ko = sp.ko;
+  a.ra = cm.ra;
+  a.rb = cm.rb;
+  a.c0 = (uint32_t)compact_of(det, sp);
+  a.out = static_cast<double*>(st->d_sout);
+  QF_CUDA(qf::launch_small_eval(a, st->dt, (int)nr, st->stream));
+  st->scale = 1.0;
+  st->real = true;
+  st->sec_a = na;
+  st->sec_b = nbeta;
+  QF_CUDA(qf::launch_zero_and_set(st->psi, n, st->dt, det, st->stream));
+  QF_CUDA(d2h(st->h_sout, st->d_sout, outn * sizeof(double), st->stream));
+  QF_CUDA(cudaStreamSynchronize(st->stream));
+  const double* ho = static_cast<const double*>(st->h_sout);
+  for (size_t q = 0; q < nr; ++q) {
+    const double* o = ho + q * (nblk + 2);
+    double nrm = o[nblk + 1];
+    if (!(nrm > 0.0)) nrm = 1.0;
+    energies[r0 + q] = o[nblk] / nrm;
+    if (grads) {
+      double* gq = grads + (r0 + q) * n_par;
+      for (size_t k = 0; k < n_par; ++k) gq[k] = 0.0;
+      for (size_t b = 0; b < nblk; ++b) gq[ansatz[blocks[b].i].param] += 2.0 * o[b] / nrm;
+    }
+  }
+  *done = true;
+  return QF_OK;
+}
+
+}  // namespace
+
+qf_status qf_energy_grad_multi(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,
+                               size_t n_par, size_t n_req, const qf_term* terms, size_t n_terms, double* energies,
+                               double* grads) {
+  if (!st || (n_req && !energies)) return fail(QF_EINVAL, "NULL argument");
+  if (n_req && n_par && !t) return fail(QF_EINVAL, "NULL array");
+  if (n_req == 0) return QF_OK;
+  trim_plans(st);
+  bool done = false;
+  size_t r0 = 0;
+  qf_status s = multi_small(st, det, ansatz, n_rot, t, n_par, 0, n_req, terms, n_terms, energies, grads, &done);
+  if (s != QF_OK || done) return s;
+  // not planned yet on this handle (or not the small form): the first request
+  // through qf_energy_grad, which validates and plans, then the rest at once
+  s = energy_grad_impl(st, det, ansatz, n_rot, t, n_par, terms, n_terms, &energies[0], grads, nullptr, 0, nullptr);
+  if (s != QF_OK) return s;
+  r0 = 1;
+  s = multi_small(st, det, ansatz, n_rot, t, n_par, r0, n_req, terms, n_terms, energies, grads, &done);
+  if (s != QF_OK || done) return s;
+  for (size_t q = r0; q < n_req; ++q) {
+    s = energy_grad_impl(st, det, ansatz, n_rot, t + q * n_par, n_par, terms, n_terms, &energies[q],
+                         grads ? grads + q * n_par : nullptr, nullptr, 0, nullptr);
+    if (s != QF_OK) return s;
+  }
+  return QF_OK;
 }
 
 qf_status qf_pool_gradients(qf_state* st, uint64_t det, const qf_arot* ansatz, size_t n_rot, const double* t,

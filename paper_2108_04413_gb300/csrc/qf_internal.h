@@ -387,6 +387,28 @@ cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool rea
                                const ExpChunk* chunks, double* partials, unsigned* counter, double* out,
                                int nblocks, const SecCompact& cm, cudaStream_t s);
 
+// Energy and gradient of several parameter sets of one small system in one
+// launch, one CTA per request, the request's compact sector state (psi and
+// lambda, real) held in shared memory for the whole evaluation: the forward
+// blocks, lambda = H psi through the direct tables with <psi|H|psi> and
+// <psi|psi>, then the reverse blocks with their gradient overlaps.
+constexpr int kSmallCoef = 36;  // per request and block: forward m[4][2][2], inverse m[4][2][2], q01[4]
+struct SmallEval {
+  const SecBlk* blks;  // the forward blocks' geometry (pat, zc, nzc, outside positions and counts)
+  int nblk;
+  const void* coef;  // per request, nblk records of kSmallCoef values of the state's real type
+  SecDirect d;       // the Hamiltonian's direct tables
+  uint32_t cnt_e, cnt_o;
+  int ke, ko;        // the sector's alpha / beta electrons
+  const uint16_t* ra;
+  const uint16_t* rb;  // colex rank tables of the compact layout
+  uint32_t c0;         // compact index of the reference determinant
+  double* out;         // per request: the nblk block overlaps, then <psi|H|psi> and <psi|psi>
+};
+// Dynamic shared memory of one request's CTA (0 when it exceeds the limit).
+size_t small_eval_smem(qf_dtype dt, uint32_t members, int ko, int no);
+cudaError_t launch_small_eval(const SmallEval& a, qf_dtype dt, int n_req, cudaStream_t s);
+
 // Bounded-wait self-test: words (3 device words, zeroed) -- waits on words[1]
 // for limit_s seconds, then raises words[2].
 cudaError_t launch_wait_selftest(unsigned* words, double limit_s, cudaStream_t s);

@@ -1301,8 +1301,166 @@ __global__ void k_split_real(const double* __restrict__ st, float2* __restrict__
   }
 }
 
+// lambda of one member (it: its compact index) through the direct tables:
+// the diagonal, the singles (fixed-point weights), then the opposite- and
+// same-spin doubles as pair products.  amp(idx): psi of member idx as a double
+// (the diagonal and singles); pair(idx): its pair-product operand -- T in FP64
+// or FP32, the (hi, lo) float split with DS.  bl: this thread's beta-single list,
+// entry k at bl[k * BSTRIDE].
+template <typename T, bool DS, int BSTRIDE, typename AmpF, typename PairF>
+__device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d, uint32_t cnt_o, int ke, int ko,
+                                                const uint16_t* __restrict__ ra, const uint16_t* __restrict__ rb,
+                                                const uint32_t (*C)[kBinom], uint32_t* bl, AmpF amp, PairF pair) {
+  const int n = d.n, ne = d.ne, no = d.no;
+  const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
+  const T* wab = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.wab : (const void*)d.fab);
+  const T* waa = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.waa : (const void*)d.faa);
+  const T* wbb = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.wbb : (const void*)d.fbb);
+  const uint32_t ie = it / cnt_o, io = it - ie * cnt_o;
+  const uint32_t la = unrank_mask(ie, ne, ke, C), lb = unrank_mask(io, no, ko, C);
+  const uint32_t c = spread16(la) | (spread16(lb) << 1);  // the member in qubit order
+  uint32_t p = c;  // prefix parities: bit q = parity of c's bits below q
+  p ^= p << 1;
+  p ^= p << 2;
+  p ^= p << 4;
+  p ^= p << 8;
+  p ^= p << 16;
+  p <<= 1;
+  const uint32_t ppa = gather_even(p), ppb = gather_even(p >> 1);
+  const uint32_t va = ((1u << ne) - 1u) & ~la, vb = ((1u << no) - 1u) & ~lb;
+  const size_t rowself = (size_t)ie * cnt_o;
+  double lx = 0.0, lxs = 0.0;  // lxs: fixed-point weights times psi (units of 2^-e)
+  PairAcc<T> pa;
+  DsAcc da;
+  // x = 0: K + sum U[r] + sum V[r][s] over occupied r < s
+  long long dsum = __ldg(d.dg);
+  for (uint32_t m = c; m; m &= m - 1) {
+    const int r = __ffs((int)m) - 1;
+    dsum += __ldg(d.dg + 1 + r);
+    const long long* vr = d.dg + 1 + n + r * n - 1;
+    for (uint32_t m2 = m & (m - 1); m2; m2 &= m2 - 1) dsum += __ldg(vr + __ffs((int)m2));
+  }
+  lxs = fma(__ll2double_rn(dsum), amp(it), lxs);
+  // singles: A + sum of B[r] over c's occupied qubits other than the one it gives up
+  for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
+    const int o = __ffs((int)m1) - 1;
+    const uint32_t rest = c & ~(1u << (2 * o));
+    for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
+      const int v = __ffs((int)n1) - 1;
+      const long long* row = d.s1a + (size_t)(o * ne + v) * (n + 1);
+      long long w = __ldg(row);
+      for (uint32_t m2 = rest; m2; m2 &= m2 - 1) w += __ldg(row + __ffs((int)m2));
+      if (((ppa >> o) ^ (ppa >> v)) & 1u) w = -w;
+      const size_t idx = (size_t)__ldg(ra + (la ^ (1u << o) ^ (1u << v))) * cnt_o + io;
+      lxs = fma(__ll2double_rn(w), amp(idx), lxs);
+    }
+  }
+  for (uint32_t m1 = lb; m1; m1 &= m1 - 1) {
+    const int o = __ffs((int)m1) - 1;
+    const uint32_t rest = c & ~(1u << (2 * o + 1));
+    for (uint32_t n1 = vb; n1; n1 &= n1 - 1) {
+      const int v = __ffs((int)n1) - 1;
+      const long long* row = d.s1b + (size_t)(o * no + v) * (n + 1);
+      long long w = __ldg(row);
+      for (uint32_t m2 = rest; m2; m2 &= m2 - 1) w += __ldg(row + __ffs((int)m2));
+      if (((ppb >> o) ^ (ppb >> v)) & 1u) w = -w;
+      const size_t idx = rowself + __ldg(rb + (lb ^ (1u << o) ^ (1u << v)));
+      lxs = fma(__ll2double_rn(w), amp(idx), lxs);
+    }
+  }
+  // opposite-spin doubles: alpha o -> v, beta o2 -> v2; the member's beta singles
+  // are listed once and reused under each of its alpha singles
+  int nbs = 0;
+  for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
+    const int o2 = __ffs((int)m2) - 1;
+    const uint32_t lbo = lb ^ (1u << o2);
+    const uint32_t so = (ppb >> o2) & 1u;
+    for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
+      const int v2 = __ffs((int)n2) - 1;
+      bl[BSTRIDE * nbs++] = (uint32_t)__ldg(rb + (lbo | (1u << v2))) | ((uint32_t)(o2 * no + v2) << 14) |
+                            ((so ^ ((ppb >> v2) & 1u)) << 31);
+    }
+  }
+  for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
+    const int o = __ffs((int)m1) - 1;
+    for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
+      const int v = __ffs((int)n1) - 1;
+      const uint32_t sa = ((ppa >> o) ^ (ppa >> v)) & 1u;
+      const size_t rowa = (size_t)__ldg(ra + (la ^ (1u << o) ^ (1u << v))) * cnt_o;
+      const size_t wo = (size_t)(o * ne + v) * (no * no);
+      const T* wrow = wab + wo;
+      const float2* drow = d.dab + wo;
+      for (int k = 0; k < nbs; ++k) {
+        const uint32_t e = bl[BSTRIDE * k];
+        const size_t idx = rowa + (e & 0x3FFFu);
+        const uint32_t col = (e >> 14) & 0xFFu, sg = sa ^ (e >> 31);
+        if constexpr (DS)
+          da.add(flip_sign2(__ldg(drow + col), sg), pair(idx));
+        else
+          pa.add(flip_sign(__ldg(wrow + col), sg), pair(idx), lx);
+      }
+      if constexpr (DS) da.fold(lx);
+      else pa.fold(lx);
+    }
+  }
+  // same-spin doubles: occupied o1 < o2 -> empty v1 < v2
+  for (uint32_t m2 = la; m2; m2 &= m2 - 1) {
+    const int o2 = __ffs((int)m2) - 1;
+    for (uint32_t m1 = la & ((1u << o2) - 1u); m1; m1 &= m1 - 1) {
+      const int o1 = __ffs((int)m1) - 1;
+      const uint32_t so = ((ppa >> o1) ^ (ppa >> o2)) & 1u;
+      const uint32_t lao = la ^ (1u << o1) ^ (1u << o2);
+      const size_t wo = (size_t)(o1 + o2 * (o2 - 1) / 2) * pe;
+      for (uint32_t n2 = va; n2; n2 &= n2 - 1) {
+        const int v2 = __ffs((int)n2) - 1;
+        const uint32_t s2 = so ^ ((ppa >> v2) & 1u);
+        const size_t w2 = wo + v2 * (v2 - 1) / 2;
+        const uint32_t lav = lao | (1u << v2);
+        for (uint32_t n1 = va & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
+          const int v1 = __ffs((int)n1) - 1;
+          const uint32_t sg = s2 ^ ((ppa >> v1) & 1u);
+          const size_t idx = (size_t)__ldg(ra + (lav | (1u << v1))) * cnt_o + io;
+          if constexpr (DS)
+            da.add(flip_sign2(__ldg(d.daa + w2 + v1), sg), pair(idx));
+          else
+            pa.add(flip_sign(__ldg(waa + w2 + v1), sg), pair(idx), lx);
+        }
+      }
+      if constexpr (DS) da.fold(lx);
+      else pa.fold(lx);
+    }
+  }
+  for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
+    const int o2 = __ffs((int)m2) - 1;
+    for (uint32_t m1 = lb & ((1u << o2) - 1u); m1; m1 &= m1 - 1) {
+      const int o1 = __ffs((int)m1) - 1;
+      const uint32_t so = ((ppb >> o1) ^ (ppb >> o2)) & 1u;
+      const uint32_t lbo = lb ^ (1u << o1) ^ (1u << o2);
+      const size_t wo = (size_t)(o1 + o2 * (o2 - 1) / 2) * po;
+      for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
+        const int v2 = __ffs((int)n2) - 1;
+        const uint32_t s2 = so ^ ((ppb >> v2) & 1u);
+        const size_t w2 = wo + v2 * (v2 - 1) / 2;
+        const uint32_t lbv = lbo | (1u << v2);
+        for (uint32_t n1 = vb & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
+          const int v1 = __ffs((int)n1) - 1;
+          const uint32_t sg = s2 ^ ((ppb >> v1) & 1u);
+          const size_t idx = rowself + __ldg(rb + (lbv | (1u << v1)));
+          if constexpr (DS)
+            da.add(flip_sign2(__ldg(d.dbb + w2 + v1), sg), pair(idx));
+          else
+            pa.add(flip_sign(__ldg(wbb + w2 + v1), sg), pair(idx), lx);
+        }
+      }
+      if constexpr (DS) da.fold(lx);
+      else pa.fold(lx);
+    }
+  }
+  return fma(lxs, d.inv_fix, lx);
+}
+
 template <typename T, bool DS>
-__global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, uint32_t cnt_e, uint32_t cnt_o,
+__global__ void __launch_bounds__(256, 4) k_sector_hpsi_direct(T* st, SecDirect d, uint32_t cnt_e, uint32_t cnt_o,
                                                             int ke, int ko, const uint16_t* __restrict__ ra,
                                                             const uint16_t* __restrict__ rb, double* partials,
                                                             unsigned* counter, double* out,
@@ -1314,163 +1472,24 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
   extern __shared__ uint32_t bsl[];
   fill_binom(C);
   __syncthreads();
-  const int n = d.n, ne = d.ne, no = d.no;
-  const int pe = ne * (ne - 1) / 2, po = no * (no - 1) / 2;
-  const T* wab = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.wab : (const void*)d.fab);
-  const T* waa = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.waa : (const void*)d.faa);
-  const T* wbb = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.wbb : (const void*)d.fbb);
   const T* ps = st;  // psi of member m at ps[2 m]; lambda goes to st[2 m + 1]
   // psi of member m as a double: pd[pst * m] (double-single state layout: psid, from the split)
   const double* pd = (DS && dss) ? psid : reinterpret_cast<const double*>(ps);
   const int pst = (DS && dss) ? 1 : 2;
+  auto amp = [&](size_t m) -> double { return (sizeof(T) == 8) ? pd[pst * m] : (double)ps[2 * m]; };
+  auto pair_op = [&](size_t m) {
+    if constexpr (DS)
+      return __ldg(split + m);
+    else
+      return ps[2 * m];
+  };
   const uint64_t items = (uint64_t)cnt_e * cnt_o;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   double acc_e = 0.0, acc_n = 0.0;
   for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items; it += stride) {
-    const uint32_t i32 = (uint32_t)it;
-    const uint32_t ie = i32 / cnt_o, io = i32 - ie * cnt_o;
-    const uint32_t la = unrank_mask(ie, ne, ke, C), lb = unrank_mask(io, no, ko, C);
-    const uint32_t c = spread16(la) | (spread16(lb) << 1);  // the member in qubit order
-    uint32_t p = c;  // prefix parities: bit q = parity of c's bits below q
-    p ^= p << 1;
-    p ^= p << 2;
-    p ^= p << 4;
-    p ^= p << 8;
-    p ^= p << 16;
-    p <<= 1;
-    const uint32_t ppa = gather_even(p), ppb = gather_even(p >> 1);
-    const uint32_t va = ((1u << ne) - 1u) & ~la, vb = ((1u << no) - 1u) & ~lb;
-    const size_t rowself = (size_t)ie * cnt_o;
-    const double self = (sizeof(T) == 8) ? pd[pst * (size_t)it] : (double)ps[2 * (size_t)it];
-    double lx = 0.0, lxs = 0.0;  // lxs: fixed-point weights times psi (units of 2^-e)
-    PairAcc<T> pa;
-    DsAcc da;
-    // x = 0: K + sum U[r] + sum V[r][s] over occupied r < s
-    long long dsum = __ldg(d.dg);
-    for (uint32_t m = c; m; m &= m - 1) {
-      const int r = __ffs((int)m) - 1;
-      dsum += __ldg(d.dg + 1 + r);
-      const long long* vr = d.dg + 1 + n + r * n - 1;
-      for (uint32_t m2 = m & (m - 1); m2; m2 &= m2 - 1) dsum += __ldg(vr + __ffs((int)m2));
-    }
-    lxs = fma(__ll2double_rn(dsum), self, lxs);
-    // singles: A + sum of B[r] over c's occupied qubits other than the one it gives up
-    for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
-      const int o = __ffs((int)m1) - 1;
-      const uint32_t rest = c & ~(1u << (2 * o));
-      for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
-        const int v = __ffs((int)n1) - 1;
-        const long long* row = d.s1a + (size_t)(o * ne + v) * (n + 1);
-        long long w = __ldg(row);
-        for (uint32_t m2 = rest; m2; m2 &= m2 - 1) w += __ldg(row + __ffs((int)m2));
-        if (((ppa >> o) ^ (ppa >> v)) & 1u) w = -w;
-        const size_t idx = (size_t)__ldg(ra + (la ^ (1u << o) ^ (1u << v))) * cnt_o + io;
-        lxs = fma(__ll2double_rn(w), (sizeof(T) == 8) ? pd[pst * idx] : (double)ps[2 * idx], lxs);
-      }
-    }
-    for (uint32_t m1 = lb; m1; m1 &= m1 - 1) {
-      const int o = __ffs((int)m1) - 1;
-      const uint32_t rest = c & ~(1u << (2 * o + 1));
-      for (uint32_t n1 = vb; n1; n1 &= n1 - 1) {
-        const int v = __ffs((int)n1) - 1;
-        const long long* row = d.s1b + (size_t)(o * no + v) * (n + 1);
-        long long w = __ldg(row);
-        for (uint32_t m2 = rest; m2; m2 &= m2 - 1) w += __ldg(row + __ffs((int)m2));
-        if (((ppb >> o) ^ (ppb >> v)) & 1u) w = -w;
-        const size_t idx = rowself + __ldg(rb + (lb ^ (1u << o) ^ (1u << v)));
-        lxs = fma(__ll2double_rn(w), (sizeof(T) == 8) ? pd[pst * idx] : (double)ps[2 * idx], lxs);
-      }
-    }
-    // opposite-spin doubles: alpha o -> v, beta o2 -> v2; the member's beta singles
-    // are listed once and reused under each of its alpha singles
-    uint32_t* bl = bsl + threadIdx.x;
-    int nbs = 0;
-    for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
-      const int o2 = __ffs((int)m2) - 1;
-      const uint32_t lbo = lb ^ (1u << o2);
-      const uint32_t so = (ppb >> o2) & 1u;
-      for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
-        const int v2 = __ffs((int)n2) - 1;
-        bl[256 * nbs++] = (uint32_t)__ldg(rb + (lbo | (1u << v2))) | ((uint32_t)(o2 * no + v2) << 14) |
-                          ((so ^ ((ppb >> v2) & 1u)) << 31);
-      }
-    }
-    for (uint32_t m1 = la; m1; m1 &= m1 - 1) {
-      const int o = __ffs((int)m1) - 1;
-      for (uint32_t n1 = va; n1; n1 &= n1 - 1) {
-        const int v = __ffs((int)n1) - 1;
-        const uint32_t sa = ((ppa >> o) ^ (ppa >> v)) & 1u;
-        const size_t rowa = (size_t)__ldg(ra + (la ^ (1u << o) ^ (1u << v))) * cnt_o;
-        const size_t wo = (size_t)(o * ne + v) * (no * no);
-        const T* wrow = wab + wo;
-        const float2* drow = d.dab + wo;
-        for (int k = 0; k < nbs; ++k) {
-          const uint32_t e = bl[256 * k];
-          const size_t idx = rowa + (e & 0x3FFFu);
-          const uint32_t col = (e >> 14) & 0xFFu, sg = sa ^ (e >> 31);
-          if (DS)
-            da.add(flip_sign2(__ldg(drow + col), sg), __ldg(split + idx));
-          else
-            pa.add(flip_sign(__ldg(wrow + col), sg), ps[2 * idx], lx);
-        }
-        if (DS) da.fold(lx);
-        else pa.fold(lx);
-      }
-    }
-    // same-spin doubles: occupied o1 < o2 -> empty v1 < v2
-    for (uint32_t m2 = la; m2; m2 &= m2 - 1) {
-      const int o2 = __ffs((int)m2) - 1;
-      for (uint32_t m1 = la & ((1u << o2) - 1u); m1; m1 &= m1 - 1) {
-        const int o1 = __ffs((int)m1) - 1;
-        const uint32_t so = ((ppa >> o1) ^ (ppa >> o2)) & 1u;
-        const uint32_t lao = la ^ (1u << o1) ^ (1u << o2);
-        const size_t wo = (size_t)(o1 + o2 * (o2 - 1) / 2) * pe;
-        for (uint32_t n2 = va; n2; n2 &= n2 - 1) {
-          const int v2 = __ffs((int)n2) - 1;
-          const uint32_t s2 = so ^ ((ppa >> v2) & 1u);
-          const size_t w2 = wo + v2 * (v2 - 1) / 2;
-          const uint32_t lav = lao | (1u << v2);
-          for (uint32_t n1 = va & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
-            const int v1 = __ffs((int)n1) - 1;
-            const uint32_t sg = s2 ^ ((ppa >> v1) & 1u);
-            const size_t idx = (size_t)__ldg(ra + (lav | (1u << v1))) * cnt_o + io;
-            if (DS)
-              da.add(flip_sign2(__ldg(d.daa + w2 + v1), sg), __ldg(split + idx));
-            else
-              pa.add(flip_sign(__ldg(waa + w2 + v1), sg), ps[2 * idx], lx);
-          }
-        }
-        if (DS) da.fold(lx);
-        else pa.fold(lx);
-      }
-    }
-    for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
-      const int o2 = __ffs((int)m2) - 1;
-      for (uint32_t m1 = lb & ((1u << o2) - 1u); m1; m1 &= m1 - 1) {
-        const int o1 = __ffs((int)m1) - 1;
-        const uint32_t so = ((ppb >> o1) ^ (ppb >> o2)) & 1u;
-        const uint32_t lbo = lb ^ (1u << o1) ^ (1u << o2);
-        const size_t wo = (size_t)(o1 + o2 * (o2 - 1) / 2) * po;
-        for (uint32_t n2 = vb; n2; n2 &= n2 - 1) {
-          const int v2 = __ffs((int)n2) - 1;
-          const uint32_t s2 = so ^ ((ppb >> v2) & 1u);
-          const size_t w2 = wo + v2 * (v2 - 1) / 2;
-          const uint32_t lbv = lbo | (1u << v2);
-          for (uint32_t n1 = vb & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
-            const int v1 = __ffs((int)n1) - 1;
-            const uint32_t sg = s2 ^ ((ppb >> v1) & 1u);
-            const size_t idx = rowself + __ldg(rb + (lbv | (1u << v1)));
-            if (DS)
-              da.add(flip_sign2(__ldg(d.dbb + w2 + v1), sg), __ldg(split + idx));
-            else
-              pa.add(flip_sign(__ldg(wbb + w2 + v1), sg), ps[2 * idx], lx);
-          }
-        }
-        if (DS) da.fold(lx);
-        else pa.fold(lx);
-      }
-    }
-    lx = fma(lxs, d.inv_fix, lx);
+    const double self = amp(it);
+    const double lx = direct_member<T, DS, 256>((uint32_t)it, d, cnt_o, ke, ko, ra, rb, C, bsl + threadIdx.x, amp,
+                                                pair_op);
     acc_e = fma(self, lx, acc_e);
     acc_n = fma(self, self, acc_n);
     if (DS && dss)
@@ -1503,6 +1522,102 @@ __global__ void __launch_bounds__(256) k_sector_hpsi_direct(T* st, SecDirect d, 
       out[1] = s1;
       *counter = 0u;
     }
+  }
+}
+
+// Small systems, several requests per launch (SmallEval): CTA r evaluates request
+// r alone.  Its compact state (psi, then lambda: members real values each) and
+// the H psi step's beta-single lists live in shared memory; the block
+// geometries, tables and rank tables are shared by every CTA and stay in L1/L2.
+constexpr int kSmallThreads = 256;
+
+// The two compact indices and the sign class of item `it` of block B (the item's
+// outside string in colex order, as the full-layout sweep enumerates it).
+__device__ __forceinline__ void small_item(const SecBlk& B, uint32_t it, const uint32_t (*C)[kBinom],
+                                           const uint16_t* __restrict__ ra, const uint16_t* __restrict__ rb,
+                                           uint32_t cnt_o, uint32_t* i0, uint32_t* i1, unsigned* cls) {
+  const uint32_t ie = it / B.cnt_o, io = it - ie * B.cnt_o;
+  const uint64_t base = unrank(ie, B.epos, B.ne, B.ke, C) | unrank(io, B.opos, B.no, B.ko, C);
+  unsigned c = 0;
+  if (B.nzc > 0) c = par64s(B.zc[0] & base);
+  if (B.nzc > 1) c |= par64s(B.zc[1] & base) << 1;
+  const uint32_t q0 = (uint32_t)(base | B.pat[0]), q1 = (uint32_t)(base | B.pat[1]);
+  *i0 = (uint32_t)__ldg(ra + gather_even(q0)) * cnt_o + __ldg(rb + gather_even(q0 >> 1));
+  *i1 = (uint32_t)__ldg(ra + gather_even(q1)) * cnt_o + __ldg(rb + gather_even(q1 >> 1));
+  *cls = c;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads, 2) k_small_eval(SmallEval a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ uint32_t C[kBinom][kBinom];
+  const int tid = threadIdx.x;
+  const uint32_t M = a.cnt_e * a.cnt_o;
+  T* ps = reinterpret_cast<T*>(dsm);
+  T* lm = ps + M;
+  uint32_t* bsl = reinterpret_cast<uint32_t*>(dsm + align16(2 * (size_t)M * sizeof(T)));
+  const T* cf = static_cast<const T*>(a.coef) + (size_t)blockIdx.x * a.nblk * kSmallCoef;
+  double* out = a.out + (size_t)blockIdx.x * (a.nblk + 2);
+  fill_binom(C);
+  for (uint32_t m = tid; m < M; m += kSmallThreads) ps[m] = (m == a.c0) ? T(1) : T(0);
+  __syncthreads();
+  // forward: psi <- psi + (M - I) psi on every item of each block in turn
+  for (int b = 0; b < a.nblk; ++b) {
+    const SecBlk& B = a.blks[b];
+    const T* mf = cf + (size_t)b * kSmallCoef;
+    const uint32_t items = B.cnt_e * B.cnt_o;
+    for (uint32_t it = tid; it < items; it += kSmallThreads) {
+      uint32_t i0, i1;
+      unsigned cls;
+      small_item(B, it, C, a.ra, a.rb, a.cnt_o, &i0, &i1, &cls);
+      const T* m = mf + 4 * cls;
+      const T v0 = ps[i0], v1 = ps[i1];
+      ps[i0] = fma(m[0], v0, fma(m[1], v1, v0));
+      ps[i1] = fma(m[2], v0, fma(m[3], v1, v1));
+    }
+    __syncthreads();
+  }
+  // lambda = H psi with <psi|lambda> and <psi|psi>
+  double acc_e = 0.0, acc_n = 0.0;
+  auto amp = [&](size_t m) -> double { return (double)ps[m]; };
+  auto pair_op = [&](size_t m) { return ps[m]; };
+  for (uint32_t m = tid; m < M; m += kSmallThreads) {
+    const double self = (double)ps[m];
+    const double lx = direct_member<T, false, kSmallThreads>(m, a.d, a.cnt_o, a.ke, a.ko, a.ra, a.rb, C, bsl + tid,
+                                                             amp, pair_op);
+    lm[m] = (T)lx;
+    acc_e = fma(self, lx, acc_e);
+    acc_n = fma(self, self, acc_n);
+  }
+  acc_e = block_sum_s(acc_e);
+  acc_n = block_sum_s(acc_n);
+  if (tid == 0) {
+    out[a.nblk] = acc_e;
+    out[a.nblk + 1] = acc_n;
+  }
+  __syncthreads();
+  // reverse: block b's overlap Im <lambda|Q_b|psi> = q01 (lambda0 psi1 - lambda1 psi0)
+  // summed over its items, then psi and lambda un-rotated by its inverse
+  for (int b = a.nblk - 1; b >= 0; --b) {
+    const SecBlk& B = a.blks[b];
+    const T* mi = cf + (size_t)b * kSmallCoef + 16;
+    const T* q = cf + (size_t)b * kSmallCoef + 32;
+    const uint32_t items = B.cnt_e * B.cnt_o;
+    double acc = 0.0;
+    for (uint32_t it = tid; it < items; it += kSmallThreads) {
+      uint32_t i0, i1;
+      unsigned cls;
+      small_item(B, it, C, a.ra, a.rb, a.cnt_o, &i0, &i1, &cls);
+      const T* m = mi + 4 * cls;
+      const T p0 = ps[i0], p1 = ps[i1], w0 = lm[i0], w1 = lm[i1];
+      acc += (double)(q[cls] * fma(w0, p1, -w1 * p0));
+      ps[i0] = fma(m[0], p0, fma(m[1], p1, p0));
+      ps[i1] = fma(m[2], p0, fma(m[3], p1, p1));
+      lm[i0] = fma(m[0], w0, fma(m[1], w1, w0));
+      lm[i1] = fma(m[2], w0, fma(m[3], w1, w1));
+    }
+    acc = block_sum_s(acc);  // its first barrier also ends this block's updates
+    if (tid == 0) out[b] = acc;
   }
 }
 
@@ -1809,6 +1924,38 @@ cudaError_t launch_sector_hpsi(const void* psi, void* lam, qf_dtype dt, bool rea
                                  out, cm, s);
   prof_post(prof_slot_, s);
   count_launch();
+  return e;
+}
+
+size_t small_eval_smem(qf_dtype dt, uint32_t members, int ko, int no) {
+  const size_t real = dt == QF_C128 ? sizeof(double) : sizeof(float);
+  const size_t b = align16(2 * (size_t)members * real) +
+                   (size_t)std::max(1, ko * (no - ko)) * kSmallThreads * sizeof(uint32_t);
+  return b <= 200u * 1024u ? b : 0;
+}
+
+cudaError_t launch_small_eval(const SmallEval& a, qf_dtype dt, int n_req, cudaStream_t s) {
+  if (n_req <= 0 || a.nblk < 0) return cudaSuccess;
+  const size_t smem = small_eval_smem(dt, a.cnt_e * a.cnt_o, a.ko, a.d.no);
+  if (smem == 0 || a.d.n > 32 || a.cnt_o > (1u << 14)) return cudaErrorInvalidValue;
+  const auto k = dt == QF_C128 ? k_small_eval<double> : k_small_eval<float>;
+  static std::once_flag once_d, once_f;  // allow the opt-in shared memory size, once per process
+  static cudaError_t attr_d = cudaSuccess, attr_f = cudaSuccess;
+  if (dt == QF_C128)
+    std::call_once(once_d, [&] {
+      attr_d = cudaFuncSetAttribute(k_small_eval<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+  else
+    std::call_once(once_f, [&] {
+      attr_f = cudaFuncSetAttribute(k_small_eval<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+  const cudaError_t attr = dt == QF_C128 ? attr_d : attr_f;
+  if (attr != cudaSuccess) return attr;
+  const int prof_slot_ = prof_pre(QF_K_SPARSE, s);
+  k<<<n_req, kSmallThreads, smem, s>>>(a);
+  count_launch();
+  const cudaError_t e = cudaGetLastError();
+  prof_post(prof_slot_, s);
   return e;
 }
 

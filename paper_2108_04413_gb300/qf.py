@@ -38,6 +38,7 @@ _SIGS = {
     "qf_apply_circuit": (ctypes.c_int, [_vp, _vp, _sz]),
     "qf_expectation": (ctypes.c_int, [_vp, _vp, _sz, _dp, _dp]),
     "qf_energy_grad": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _dp, _vp]),
+    "qf_energy_grad_multi": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _sz, _vp, _sz, _vp, _vp]),
     "qf_residuals": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _dp, _vp, _vp]),
     "qf_pool_gradients": (ctypes.c_int, [_vp, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _sz, _sz, _dp, _vp]),
     "qf_trotter": (ctypes.c_int, [_vp, _vp, _sz, _d, ctypes.c_int]),
@@ -207,6 +208,19 @@ class State:
         _check(_lib.qf_energy_grad(self._h, int(det), _ptr(ansatz), len(ansatz), _ptr(t), len(t), _ptr(terms),
                                    len(terms), ctypes.byref(e), _ptr(grad)))
         return e.value, grad
+
+    def energy_grad_multi(self, det: int, ansatz: np.ndarray, t, terms: np.ndarray):
+        """Energy and gradient for each row of t (n_req x n_par): qf_energy_grad_multi,
+        one launch for all rows when the system is small enough."""
+        ansatz = np.ascontiguousarray(ansatz, dtype=AROT_DTYPE)
+        terms = np.ascontiguousarray(terms, dtype=TERM_DTYPE)
+        t = np.ascontiguousarray(np.atleast_2d(t), dtype=np.float64)
+        n_req, n_par = t.shape
+        energies = np.zeros(n_req, dtype=np.float64)
+        grads = np.zeros((n_req, n_par), dtype=np.float64)
+        _check(_lib.qf_energy_grad_multi(self._h, int(det), _ptr(ansatz), len(ansatz), _ptr(t), n_par, n_req,
+                                         _ptr(terms), len(terms), _ptr(energies), _ptr(grads)))
+        return energies, grads
 
     def residuals(self, det: int, ansatz: np.ndarray, t, terms: np.ndarray, dets, grad: bool = False):
         """PQE residuals <b|U^dagger H U|det> for the basis indices dets (complex

@@ -3,17 +3,22 @@
 Requests (system, parameters) arrive over time.  A dispatcher admits them as
 worker slots free up and as device memory allows: every system keeps its state
 resident (psi, lambda or the sector path's compact copy and forward log, plus its
-cached plans; see footprint_bytes) so
-repeated-parameter requests skip all planning, and admission charges a system's
-footprint against an HBM budget, evicting idle resident systems (least
-recently used first) when a new one does not fit.  Admitted requests run on
-worker threads, each call on its system's own CUDA stream; libqf calls release
-the GIL, so the device work of several requests overlaps.  Requests for the
-same system are serialised (one handle is never used by two threads at once).
+cached plans; see footprint_bytes) so repeated-parameter requests skip all
+planning, and admission charges each resident handle's footprint against an HBM
+budget, evicting idle handles (least recently used first) when a new one does
+not fit.  A system may hold up to `replicas` handles, so requests of one busy
+system can run side by side; one handle is never used by two threads at once.
+Admitted requests run on worker threads, each call on its handle's own CUDA
+stream; libqf calls release the GIL, so the device work of several requests
+overlaps.
 
-Latency = completion time - arrival time; the server reports throughput and
-p50/p99 latency.  The executor is pluggable so the scheduling logic can be
-tested without a GPU.
+Small systems are also batched: when a worker takes a request for a system of
+at most `batch_qubits` qubits, it takes up to `batch` - 1 more pending requests
+for the same system and runs them all in one qf_energy_grad_multi call (one
+kernel launch, one CTA per request, each request's sector state in shared
+memory).  Latency = completion time - arrival time; the server reports
+throughput and p50/p99 latency.  The executor is pluggable so the scheduling
+logic can be tested without a GPU.
 """
 from __future__ import annotations
 
@@ -103,23 +108,39 @@ class GpuExecutor:
         self.torch.cuda.set_device(self.device)
         return handle.energy_grad(sysm.det, sysm.ansatz, t, sysm.terms)
 
+    def run_multi(self, handle, sysm: System, ts: List[np.ndarray]):
+        """Several requests of one system in one qf_energy_grad_multi call."""
+        self.torch.cuda.set_device(self.device)
+        e, g = handle.energy_grad_multi(sysm.det, sysm.ansatz, np.stack(ts), sysm.terms)
+        return [(float(e[k]), g[k]) for k in range(len(ts))]
+
     def release(self, handle):
         handle.close()
 
 
 class Server:
     def __init__(self, systems: Dict[str, System], executor, workers: int = 4, hbm_budget: int = 8 << 30,
-                 dtype: str = "c64", clock: Callable[[], float] = time.perf_counter):
+                 dtype: str = "c64", clock: Callable[[], float] = time.perf_counter, batch: int = 1,
+                 batch_qubits: int = 16, replicas: int = 1):
         self.systems = systems
         self.ex = executor
+        self.batch = batch if hasattr(executor, "run_multi") else 1
+        self.batch_qubits = batch_qubits
+        self.batches = 0  # calls that served more than one request
+        # resident handles a system may hold at once (each charged its footprint):
+        # requests of one busy system run side by side on different handles
+        self.replicas = max(1, replicas)
         self.workers = workers
         self.budget = hbm_budget
         self.dtype = dtype
         self.clock = clock
         self._lock = threading.Condition()
         self._pending: collections.deque = collections.deque()
-        self._resident: "collections.OrderedDict[str, object]" = collections.OrderedDict()
-        self._busy: Dict[str, bool] = {}
+        # (system, slot) -> handle, least recently used first; busy or idle
+        self._resident: "collections.OrderedDict[tuple, object]" = collections.OrderedDict()
+        self._busy: Dict[tuple, bool] = {}
+        self._slots: Dict[str, int] = {}  # handles of each system (resident or being created)
+        self._next_slot = 0
         self._used = 0
         self._active = 0
         self._closed = False
@@ -136,7 +157,7 @@ class Server:
         return self.clock() - self.t0
 
     def _footprint(self, key: str) -> int:
-        """Device bytes charged for a resident system (cached per system)."""
+        """Device bytes charged for a resident handle of a system (cached per system)."""
         fp = self._fp.get(key)
         if fp is None:
             sysm = self.systems[key]
@@ -155,21 +176,24 @@ class Server:
             self._lock.notify_all()
         for th in self._threads:
             th.join()
-        for key, h in list(self._resident.items()):
+        for h in list(self._resident.values()):
             self.ex.release(h)
         self._resident.clear()
 
-    # -- admission (called with the lock held): first pending request whose
-    # system is idle and whose state is resident or fits after evictions
+    # -- admission (called with the lock held): the first pending request that has
+    # an idle resident handle of its system, or room for a new one (within the
+    # system's replica count and, after evicting idle handles least recently used
+    # first, the HBM budget)
     def _admit(self):
         for i, req in enumerate(self._pending):
             key = req.system
-            if self._busy.get(key):
-                continue
-            if key in self._resident:
+            idle = next((rk for rk in self._resident if rk[0] == key and not self._busy.get(rk)), None)
+            if idle is not None:
                 del self._pending[i]
-                self._resident.move_to_end(key)
-                return req, self._resident[key], False
+                self._resident.move_to_end(idle)
+                return self._group(req), self._resident[idle], False, idle
+            if self._slots.get(key, 0) >= self.replicas:
+                continue  # wait for one of its handles
             need = self._footprint(key)
             if need > self.budget:
                 del self._pending[i]
@@ -179,23 +203,43 @@ class Server:
                 return None
             victims = []
             free = self.budget - self._used
-            for k in self._resident:  # least recently used first
+            for rk in self._resident:  # least recently used first
                 if free >= need:
                     break
-                if not self._busy.get(k):
-                    victims.append(k)
-                    free += self._footprint(k)
+                if not self._busy.get(rk):
+                    victims.append(rk)
+                    free += self._footprint(rk[0])
             if free < need:
-                continue  # wait for a busy system to finish
-            for k in victims:
-                h = self._resident.pop(k)
-                self._used -= self._footprint(k)
+                continue  # wait for a busy handle to finish
+            for rk in victims:
+                h = self._resident.pop(rk)
+                self._busy.pop(rk, None)
+                self._slots[rk[0]] -= 1
+                self._used -= self._footprint(rk[0])
                 self.evictions += 1
                 self.ex.release(h)
             del self._pending[i]
             self._used += need
-            return req, None, True
+            self._slots[key] = self._slots.get(key, 0) + 1
+            rk = (key, self._next_slot)
+            self._next_slot += 1
+            return self._group(req), None, True, rk
         return None
+
+    def _group(self, req: Request) -> List[Request]:
+        """req and, for a small system, up to batch - 1 more pending requests of
+        the same system (earliest first), taken off the queue (lock held)."""
+        group = [req]
+        if self.batch > 1 and self.systems[req.system].n <= self.batch_qubits:
+            rest = collections.deque()
+            while self._pending:
+                r = self._pending.popleft()
+                if r.system == req.system and len(group) < self.batch:
+                    group.append(r)
+                else:
+                    rest.append(r)
+            self._pending = rest
+        return group
 
     def _worker(self):
         while True:
@@ -207,30 +251,42 @@ class Server:
                     if self._closed and not self._pending:
                         return
                     self._lock.wait(timeout=0.05)
-                req, handle, fresh = got
-                key = req.system
-                self._busy[key] = True
+                group, handle, fresh, rk = got
+                key = rk[0]
+                self._busy[rk] = True
                 self._active += 1
                 self.max_concurrent = max(self.max_concurrent, self._active)
+                if len(group) > 1:
+                    self.batches += 1
             sysm = self.systems[key]
             try:
                 if fresh:
                     handle = self.ex.create(sysm)
-                req.start = self.now()
-                e, g = self.ex.run(handle, sysm, req.t)
-                req.energy, req.grad = float(e), np.asarray(g)
-            except Exception as exc:  # the request fails, the server keeps going
-                req.error = repr(exc)
-            req.done = self.now()
+                t0 = self.now()
+                for req in group:
+                    req.start = t0
+                if len(group) > 1:
+                    results = self.ex.run_multi(handle, sysm, [req.t for req in group])
+                else:
+                    results = [self.ex.run(handle, sysm, group[0].t)]
+                for req, (e, g) in zip(group, results):
+                    req.energy, req.grad = float(e), np.asarray(g)
+            except Exception as exc:  # the requests fail, the server keeps going
+                for req in group:
+                    req.error = repr(exc)
+            t1 = self.now()
+            for req in group:
+                req.done = t1
             with self._lock:
                 if fresh and handle is not None:
-                    self._resident[key] = handle
-                    self._resident.move_to_end(key)
-                elif fresh:
-                    self._used -= self._footprint(sysm.key)
-                self._busy[key] = False
+                    self._resident[rk] = handle
+                    self._resident.move_to_end(rk)
+                elif fresh:  # the handle was never created
+                    self._used -= self._footprint(key)
+                    self._slots[key] -= 1
+                self._busy[rk] = False
                 self._active -= 1
-                self.done.append(req)
+                self.done.extend(group)
                 self._lock.notify_all()
 
 

@@ -127,3 +127,69 @@ def test_footprint_counts_sector_log_items_by_brute_force():
         assert base == 2 * (size << n)
         got = footprint_bytes(n, dtype, det, A) - base
         assert got == 2 * len(members) * size + items * size
+
+
+class BatchingExecutor(FakeExecutor):
+    """FakeExecutor with a multi-request call (one call serves a group)."""
+
+    def __init__(self, budget, dtype):
+        super().__init__(budget, dtype)
+        self.groups = []
+
+    def run_multi(self, handle, sysm, ts):
+        with self.lock:
+            self.groups.append((sysm.key, len(ts)))
+        time.sleep(0.002 * (sysm.n - 6))
+        return [(float(np.sum(np.sin(t)) + sysm.n), np.cos(t)) for t in ts]
+
+
+def test_small_systems_batched_and_results_unchanged():
+    """A closed-loop burst: requests of one small system are served together (at
+    most `batch` per call); larger systems never are; every result equals the
+    one-at-a-time result."""
+    systems = _systems()
+    systems["n20"] = System("n20", 20, (1 << 10) - 1, np.zeros(0), np.zeros(0))
+    reqs = _requests(systems, 80, 4)
+    ex = BatchingExecutor(1 << 34, "c64")
+    srv = Server(systems, ex, workers=2, hbm_budget=1 << 34, batch=6, batch_qubits=12)
+    done = replay(srv, reqs, realtime=False)
+    srv.close()
+    assert len(done) == 80 and all(r.error is None for r in done)
+    for r in done:
+        e, g = FakeExecutor(0, "c64").run(None, systems[r.system], r.t)
+        assert r.energy == e and np.array_equal(r.grad, g)
+    assert srv.batches > 0 and ex.groups
+    assert all(2 <= k <= 6 and systems[key].n <= 12 for key, k in ex.groups)
+    assert sum(k for _, k in ex.groups) <= 80
+
+
+def test_no_batching_without_multi_call():
+    systems = _systems()
+    reqs = _requests(systems, 30, 5)
+    ex = FakeExecutor(1 << 30, "c64")
+    srv = Server(systems, ex, workers=2, hbm_budget=1 << 30, batch=8)
+    done = replay(srv, reqs, realtime=False)
+    srv.close()
+    assert len(done) == 30 and all(r.error is None for r in done)
+    assert srv.batches == 0
+
+
+def test_replicas_run_one_system_side_by_side():
+    """One system, a burst of requests: with three replicas its requests overlap
+    on three handles (each charged against the budget), results unchanged; with
+    one they run one at a time."""
+    systems = {"n12": System("n12", 12, (1 << 6) - 1, np.zeros(0), np.zeros(0))}
+    rng = np.random.default_rng(6)
+    reqs = [Request(i, "n12", rng.normal(size=5), 0.0) for i in range(24)]
+    fp = footprint_bytes(12, "c64")
+    for replicas, expect_overlap in ((3, True), (1, False)):
+        ex = FakeExecutor(1 << 30, "c64")
+        srv = Server(systems, ex, workers=4, hbm_budget=3 * fp, replicas=replicas)
+        done = replay(srv, [Request(r.rid, r.system, r.t, 0.0) for r in reqs], realtime=False)
+        srv.close()
+        assert len(done) == 24 and all(r.error is None for r in done)
+        for r in done:
+            e, g = FakeExecutor(0, "c64").run(None, systems[r.system], r.t)
+            assert r.energy == e and np.array_equal(r.grad, g)
+        assert (ex.max_active > 1) == expect_overlap
+        assert len(ex.created) == replicas and ex.max_used <= 3 * fp and ex.used == 0
