@@ -386,14 +386,14 @@ __device__ __forceinline__ float2 ds_of(double v) {
 
 constexpr int kRunThreads = 256;  // threads of a part-local run CTA (item maps, FP64 and FP32 sweeps)
 constexpr int kRunBlkWords = sizeof(RunBlk) / 4;
-// Threads of a run CTA.  A run's time is that of its largest parts, whose block
-// steps take ceil(items / threads) item rounds each, so the double-single sweeps
-// take as many threads as still leave every part of a run resident at once
-// (512 parts on 152 SMs: 4 CTAs per SM): 384 for the forward (40 registers), 288
-// for the reverse (56 registers).
-template <int MODE, bool DSW>
-__host__ __device__ constexpr int run_threads() {
-  return !DSW ? kRunThreads : MODE == 0 ? 384 : 288;
+// Threads of a mapped sweep CTA (forward, and logged reverse).  A run's time is
+// that of its largest parts, whose block steps take ceil(items / threads) item
+// rounds each, so these take as many threads as still leave every part of a run
+// resident at once (512 parts on 152 SMs: 4 CTAs per SM): 384 for the forward
+// (40 registers), 288 for the reverse (56 registers).
+template <int MODE>
+__host__ __device__ constexpr int wide_threads() {
+  return MODE == 0 ? 384 : 288;
 }
 // Coefficient words a mapped sweep step copies: m then q (FP64) or mf then qf (FP32).
 constexpr int kCoefWordsMax = 64;
@@ -430,14 +430,15 @@ __device__ void fill_binom_prefix(uint32_t (*Cs)[kBinom]) {
 // the same (psi, lam), nothing rotated or written back (operator-pool gradients).
 // Overlaps accumulate in the state's precision (FP64 for complex128, FP32 for
 // complex64); each part's overlap with a block is written to partial in FP64.
-template <int MODE, typename T, bool DSW>
+template <int MODE, typename T, bool DSW, int NT>
 __device__ __forceinline__ void sector_run_body(typename SCx<T>::V* psi, typename SCx<T>::V* lam, RunInfo run,
                                                 const RunPart* __restrict__ parts, const RunBlk* __restrict__ blks,
                                                 double* partial, int pmax, SecCompact cm, typename SCx<T>::V* log,
                                                 const uint16_t* __restrict__ strs,
                                                 const uint32_t* __restrict__ map, bool dss) {
   using V = typename SCx<T>::V;
-  constexpr int NT = run_threads<MODE, DSW>(), NW = NT / 32;
+  constexpr int NW = NT / 32;
+  static_assert(NT % 32 == 0 && NT >= kRunBlkWords && NT <= 384, "run CTA size");
   constexpr bool ADJ = MODE != 0;
   constexpr bool F32 = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -839,28 +840,22 @@ __device__ __forceinline__ void sector_run_body(typename SCx<T>::V* psi, typenam
   }
 }
 
-// The sweeps in FP64 / FP32 (256 threads) and in double-single arithmetic
-// (run_threads threads).
+// The sweeps: kRunThreads threads, or wide_threads for the mapped forward and
+// logged reverse (every double-single sweep is one).
 #define QF_RUN_ARGS                                                                                              \
   typename SCx<T>::V *psi, typename SCx<T>::V *lam, RunInfo run, const RunPart *__restrict__ parts,               \
       const RunBlk *__restrict__ blks, double *partial, int pmax, SecCompact cm, typename SCx<T>::V *log,         \
       const uint16_t *__restrict__ strs, const uint32_t *__restrict__ map, bool dss
 template <int MODE, typename T>
 __global__ void __launch_bounds__(kRunThreads) k_sector_run(QF_RUN_ARGS) {
-  sector_run_body<MODE, T, false>(psi, lam, run, parts, blks, partial, pmax, cm, log, strs, map, dss);
+  sector_run_body<MODE, T, false, kRunThreads>(psi, lam, run, parts, blks, partial, pmax, cm, log, strs, map, dss);
 }
-template <int MODE, typename T>
-__global__ void __launch_bounds__(run_threads<MODE, true>()) k_sector_run_ds(QF_RUN_ARGS) {
-  sector_run_body<MODE, T, true>(psi, lam, run, parts, blks, partial, pmax, cm, log, strs, map, dss);
+template <int MODE, typename T, bool DSW>
+__global__ void __launch_bounds__(wide_threads<MODE>()) k_sector_run_wide(QF_RUN_ARGS) {
+  sector_run_body<MODE, T, DSW, wide_threads<MODE>()>(psi, lam, run, parts, blks, partial, pmax, cm, log, strs, map,
+                                                       dss);
 }
 #undef QF_RUN_ARGS
-template <int MODE, typename T, bool DSW>
-constexpr auto run_kernel() {
-  if constexpr (DSW)
-    return k_sector_run_ds<MODE, T>;
-  else
-    return k_sector_run<MODE, T>;
-}
 
 // Item maps (RunPart::mapbase): for the part representing each class, every
 // forward block's items in sweep order, one word each -- the item's two
@@ -1716,20 +1711,36 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
                                                                       "and logged reverse");
   if (DSW && !map) return cudaErrorInvalidValue;  // the double-single path is the mapped step loop
   using V = typename SCx<T>::V;
+  // the mapped step loop runs wide CTAs (not the FP64 logged reverse: at 64
+  // registers four of its wide CTAs would not fit an SM)
+  constexpr bool kWide = MODE == 0 || (MODE == 3 && (DSW || sizeof(T) == 4));
+  const bool wide = kWide && map != nullptr;
   static std::once_flag once;  // allow the opt-in shared memory size, once per process
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(run_kernel<MODE, T, DSW>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)run_smem_max<MODE, T>());
+    const int bytes = (int)run_smem_max<MODE, T>();
+    if (!DSW) attr = cudaFuncSetAttribute(k_sector_run<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if constexpr (kWide)
+      if (attr == cudaSuccess)
+        attr = cudaFuncSetAttribute(k_sector_run_wide<MODE, T, DSW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    bytes);
   });
   if (attr != cudaSuccess) return attr;
   for (int r = 0; r < nruns; ++r) {
     const RunInfo& R = runs[MODE != 0 ? nruns - 1 - r : r];
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
     if (smem > run_smem_max<MODE, T>() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
-    run_kernel<MODE, T, DSW>()<<<R.nparts, run_threads<MODE, DSW>(), smem, s>>>(
-        static_cast<V*>(psi), static_cast<V*>(lam), R, parts, blks, partial, pmax, cm, static_cast<V*>(log), strs,
-        (MODE == 0 || MODE == 3) ? map : nullptr, DSW && dss);
+    if constexpr (kWide) {
+      if (wide)
+        k_sector_run_wide<MODE, T, DSW><<<R.nparts, wide_threads<MODE>(), smem, s>>>(
+            static_cast<V*>(psi), static_cast<V*>(lam), R, parts, blks, partial, pmax, cm, static_cast<V*>(log),
+            strs, map, DSW && dss);
+    }
+    if constexpr (!DSW)
+      if (!wide)
+        k_sector_run<MODE, T><<<R.nparts, kRunThreads, smem, s>>>(
+            static_cast<V*>(psi), static_cast<V*>(lam), R, parts, blks, partial, pmax, cm, static_cast<V*>(log),
+            strs, (MODE == 0 || MODE == 3) ? map : nullptr, false);
     count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
