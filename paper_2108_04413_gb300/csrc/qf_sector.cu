@@ -1385,17 +1385,33 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
       const size_t wo = (size_t)(o * ne + v) * (no * no);
       const T* wrow = wab + wo;
       const float2* drow = d.dab + wo;
-      for (int k = 0; k < nbs; ++k) {
-        const uint32_t e = bl[BSTRIDE * k];
-        const size_t idx = rowa + (e & 0x3FFFu);
-        const uint32_t col = (e >> 14) & 0xFFu, sg = sa ^ (e >> 31);
-        if constexpr (DS)
-          da.add(flip_sign2(__ldg(drow + col), sg), pair(idx));
-        else
+      if constexpr (DS) {
+        // two independent accumulators (even and odd entries), so that two
+        // TwoSum chains and their loads are in flight at once
+        DsAcc db;
+        int k = 0;
+        for (; k + 1 < nbs; k += 2) {
+          const uint32_t e0 = bl[BSTRIDE * k], e1 = bl[BSTRIDE * (k + 1)];
+          const float2 w0 = __ldg(drow + ((e0 >> 14) & 0xFFu)), w1 = __ldg(drow + ((e1 >> 14) & 0xFFu));
+          const float2 v0 = pair(rowa + (e0 & 0x3FFFu)), v1 = pair(rowa + (e1 & 0x3FFFu));
+          da.add(flip_sign2(w0, sa ^ (e0 >> 31)), v0);
+          db.add(flip_sign2(w1, sa ^ (e1 >> 31)), v1);
+        }
+        if (k < nbs) {
+          const uint32_t e = bl[BSTRIDE * k];
+          da.add(flip_sign2(__ldg(drow + ((e >> 14) & 0xFFu)), sa ^ (e >> 31)), pair(rowa + (e & 0x3FFFu)));
+        }
+        da.fold(lx);
+        db.fold(lx);
+      } else {
+        for (int k = 0; k < nbs; ++k) {
+          const uint32_t e = bl[BSTRIDE * k];
+          const size_t idx = rowa + (e & 0x3FFFu);
+          const uint32_t col = (e >> 14) & 0xFFu, sg = sa ^ (e >> 31);
           pa.add(flip_sign(__ldg(wrow + col), sg), pair(idx), lx);
+        }
+        pa.fold(lx);
       }
-      if constexpr (DS) da.fold(lx);
-      else pa.fold(lx);
     }
   }
   // same-spin doubles: occupied o1 < o2 -> empty v1 < v2
