@@ -1166,6 +1166,52 @@ void compose_sparse(const RotIn* r, int m, bool inverse, const qf::SparseArgs& s
   };
   const cplx iu(0, 1);
   const int ncls = 1 << a->nzc;
+  // phase pe of rotation k on row i in class c: P_k maps row i to its partner
+  // with this factor (Y phase, outside-Z class sign, inside-Z parity)
+  auto phase = [&](int k, int c, int i) {
+    const uint64_t zo = r[k].z & ~x;
+    double sig = 1.0;
+    for (int j = 0; j < a->nzc; ++j)
+      if (zo == a->zc[j] && ((c >> j) & 1)) sig = -1.0;
+    const uint64_t zin = compress(r[k].z & x);
+    const int y = popc(x & r[k].z) & 3;
+    const cplx iy = (y == 0) ? cplx(1, 0) : (y == 1) ? cplx(0, 1) : (y == 2) ? cplx(-1, 0) : cplx(0, -1);
+    const int col = loc[i] ^ xl;
+    return iy * sig * ((popc(zin & (uint64_t)col) & 1) ? -1.0 : 1.0);
+  };
+  // Two rows: each rotation is cos(th) I - i sin(th) P_k on the pair.  When every
+  // P_k is +-P_0 there (same phases up to one common sign per rotation), they
+  // compose to cos(phi) I - i sin(phi) P_0 with phi the signed sum of the angles:
+  // one sine and cosine per class instead of one per rotation and a product each.
+  if (nr == 2 && partner[0] == 1 && partner[1] == 0) {
+    bool closed = true;
+    double phi[4] = {0.0, 0.0, 0.0, 0.0};
+    cplx p0[4], p1[4];
+    for (int c = 0; c < ncls && closed; ++c) {
+      p0[c] = phase(0, c, 0);
+      p1[c] = phase(0, c, 1);
+      for (int k = 0; k < m && closed; ++k) {
+        const cplx q0 = phase(k, c, 0), q1 = phase(k, c, 1);
+        const double th = inverse ? -r[k].th : r[k].th;
+        if (q0 == p0[c] && q1 == p1[c])
+          phi[c] += th;
+        else if (q0 == -p0[c] && q1 == -p1[c])
+          phi[c] -= th;
+        else
+          closed = false;
+      }
+    }
+    if (closed) {
+      for (int c = 0; c < ncls; ++c) {
+        const double cs = std::cos(phi[c]), sn = std::sin(phi[c]);
+        store(c, 0, 0, cplx(cs - 1.0, 0.0));
+        store(c, 0, 1, -iu * sn * p0[c]);
+        store(c, 1, 0, -iu * sn * p1[c]);
+        store(c, 1, 1, cplx(cs - 1.0, 0.0));
+      }
+      return;
+    }
+  }
   // one sine and cosine per rotation (a block's runs are short; longer ones spill to the heap)
   double cs_buf[32], sn_buf[32];
   std::vector<double> cs_heap, sn_heap;
@@ -2115,7 +2161,6 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     par[k] = ansatz[k].param;
   }
   st->last_ansatz_key = akey;
-  bool fresh = false;
   if (ait == st->ansatz_plans.end()) {
     // first sight of this ansatz: find its block structure
     std::vector<Blk> bl = plan_blocks(r.data(), par.data(), n_rot, st->n);
@@ -2123,7 +2168,6 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
     plan.src.assign(ansatz, ansatz + n_rot);
     plan.blocks = std::move(bl);
     ait = st->ansatz_plans.emplace(akey, std::move(plan)).first;
-    fresh = true;
   }
   ait->second.last_use = st->calls;
   qf_state::AnsatzPlan& ap = ait->second;
@@ -2149,14 +2193,14 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
   // new angles: refill every block's composites (and, with a cached run plan, its
   // sector form), spread over the host pool
   std::atomic<bool> sec_good(true);
-  if (!fresh || sec_cached) {
+  // (a fresh plan's composites are refilled too, so that the first call and
+  // every later call with the same angles give bit-identical results)
+  {
     qf::HostPool::get().parallel_for(nblk, 32, [&](size_t k) {
       Blk& b = blocks[k];
       if (!b.sparse) return;
-      if (!fresh) {
-        refill_sparse(&r[b.i], (int)(b.j - b.i), false, &b.fwd);
-        if (!adjoint_composite(b.fwd, &b.inv)) refill_sparse(&r[b.i], (int)(b.j - b.i), true, &b.inv);
-      }
+      refill_sparse(&r[b.i], (int)(b.j - b.i), false, &b.fwd);
+      if (!adjoint_composite(b.fwd, &b.inv)) refill_sparse(&r[b.i], (int)(b.j - b.i), true, &b.inv);
       if (sec_cached) {
         qf::RunBlk& F = ap.runs.blks[k];
         qf::RunBlk& I = ap.runs.blks[nblk + k];
