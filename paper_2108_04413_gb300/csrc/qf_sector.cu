@@ -1404,13 +1404,21 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
         da.fold(lx);
         db.fold(lx);
       } else {
-        for (int k = 0; k < nbs; ++k) {
+        PairAcc<T> pb;
+        int k = 0;
+        for (; k + 1 < nbs; k += 2) {
+          const uint32_t e0 = bl[BSTRIDE * k], e1 = bl[BSTRIDE * (k + 1)];
+          const T w0 = __ldg(wrow + ((e0 >> 14) & 0xFFu)), w1 = __ldg(wrow + ((e1 >> 14) & 0xFFu));
+          const T v0 = pair(rowa + (e0 & 0x3FFFu)), v1 = pair(rowa + (e1 & 0x3FFFu));
+          pa.add(flip_sign(w0, sa ^ (e0 >> 31)), v0, lx);
+          pb.add(flip_sign(w1, sa ^ (e1 >> 31)), v1, lx);
+        }
+        if (k < nbs) {
           const uint32_t e = bl[BSTRIDE * k];
-          const size_t idx = rowa + (e & 0x3FFFu);
-          const uint32_t col = (e >> 14) & 0xFFu, sg = sa ^ (e >> 31);
-          pa.add(flip_sign(__ldg(wrow + col), sg), pair(idx), lx);
+          pa.add(flip_sign(__ldg(wrow + ((e >> 14) & 0xFFu)), sa ^ (e >> 31)), pair(rowa + (e & 0x3FFFu)), lx);
         }
         pa.fold(lx);
+        pb.fold(lx);
       }
     }
   }
