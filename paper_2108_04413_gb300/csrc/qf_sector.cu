@@ -430,6 +430,17 @@ __device__ void fill_binom_prefix(uint32_t (*Cs)[kBinom]) {
 // the same (psi, lam), nothing rotated or written back (operator-pool gradients).
 // Overlaps accumulate in the state's precision (FP64 for complex128, FP32 for
 // complex64); each part's overlap with a block is written to partial in FP64.
+// Programmatic dependent launch: a sweep launch may start while the previous
+// kernel of the stream finishes; it reads only plan data (descriptors, parts,
+// coefficients) before grid_dep_wait, which returns once that kernel has
+// completed and its writes are visible.  A kernel lets the next launch start
+// only after its own wait (so it never overlaps one two places before it).  Both
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int MODE, typename T, bool DSW, int NT>
 __device__ __forceinline__ void sector_run_body(typename SCx<T>::V* psi, typename SCx<T>::V* lam, RunInfo run,
                                                 const RunPart* __restrict__ parts, const RunBlk* __restrict__ blks,
@@ -474,6 +485,42 @@ __device__ __forceinline__ void sector_run_body(typename SCx<T>::V* psi, typenam
   const uint32_t size = P.cnta * P.cntb;
   // item-map words of this part's class (forward and logged reverse sweeps)
   const uint32_t* mp = (MODE == 0 || MODE == 3) && map ? map + P.mapbase : nullptr;
+  // Mapped sweep tables (plan data only): every step's item count, offset and G
+  // class bits, and the first two steps' coefficients.
+  __shared__ uint32_t stn[kRunMaxBlocks], sto[kRunMaxBlocks];
+  __shared__ uint8_t stc[kRunMaxBlocks];
+  __shared__ __align__(16) uint32_t cw[3][kCoefWordsMax];
+  constexpr int kCw = DSW ? (MODE == 3 ? 40 : 32) : F32 ? (MODE == 3 ? 20 : 16) : (MODE == 3 ? 64 : 32);
+  constexpr size_t kCoff = DSW ? offsetof(RunBlk, md) : F32 ? offsetof(RunBlk, mf) : offsetof(RunBlk, m);
+  auto coef_word = [&](int st) {
+    return __ldg(reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(blks + blk_of(st)) + kCoff) + tid);
+  };
+  if (mp) {
+    for (int f = tid; f < nb; f += NT) {  // f: the block's position in forward order
+      const RunBlk* Bg = blks + run.b0 + f;
+      const int ne = __ldg(&Bg->ne), no = __ldg(&Bg->no), nzc = __ldg(&Bg->nzc);
+      const int ke = P.ka - __ldg(&Bg->e0), ko = P.kb - __ldg(&Bg->o0);
+      stn[f] = (ke >= 0 && ke <= ne && ko >= 0 && ko <= no) ? C[ne][ke] * C[no][ko] : 0u;
+      unsigned cg = 0;
+      if (nzc > 0) cg = par32s(__ldg(&Bg->zg[0][0]) & P.ga) ^ par32s(__ldg(&Bg->zg[0][1]) & P.gb);
+      if (nzc > 1) cg |= (par32s(__ldg(&Bg->zg[1][0]) & P.ga) ^ par32s(__ldg(&Bg->zg[1][1]) & P.gb)) << 1;
+      stc[f] = (uint8_t)cg;
+    }
+    if (tid < kCw) {
+      cw[0][tid] = coef_word(0);
+      if (nb > 1) cw[1][tid] = coef_word(1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t a = 0;
+      for (int f = 0; f < nb; ++f) {
+        sto[f] = a;
+        a += stn[f];
+      }
+    }
+  }
+  // the state (and the maps, the log) come from earlier kernels of the stream
+  grid_dep_wait();
   // the real slot each member moves: psi's real part (MODE 0), lam's in psi's imaginary slot (MODE 3)
   const int slot = MODE == 3 ? 1 : 0;
   const T* pr = reinterpret_cast<const T*>(psi);
@@ -539,41 +586,10 @@ __device__ __forceinline__ void sector_run_body(typename SCx<T>::V* psi, typenam
     // and log pairs of a step are loaded two steps ahead, so no load latency sits
     // between two barriers.  A complex128 reverse sums each step's overlaps on the
     // integer pipes (warp_sum_fixed), one step later, with no FP64 chain.
-    __shared__ uint32_t stn[kRunMaxBlocks], sto[kRunMaxBlocks];
-    __shared__ uint8_t stc[kRunMaxBlocks];
-    __shared__ __align__(16) uint32_t cw[3][kCoefWordsMax];
     __shared__ long long wtot[2][NW];  // per-warp overlap sums of the last two steps
     __shared__ int wexp[2][NW];
-    constexpr int kCw = DSW ? (MODE == 3 ? 40 : 32) : F32 ? (MODE == 3 ? 20 : 16) : (MODE == 3 ? 64 : 32);
-    constexpr size_t kCoff = DSW ? offsetof(RunBlk, md) : F32 ? offsetof(RunBlk, mf) : offsetof(RunBlk, m);
     using LV = typename std::conditional<DSW, float4, V>::type;  // a log pair
     constexpr bool IRED = MODE == 3 && !F32;  // integer overlap reduction
-    auto coef_word = [&](int st) {
-      return __ldg(reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(blks + blk_of(st)) + kCoff) + tid);
-    };
-    for (int f = tid; f < nb; f += NT) {  // f: the block's position in forward order
-      const RunBlk* Bg = blks + run.b0 + f;
-      const int ne = __ldg(&Bg->ne), no = __ldg(&Bg->no), nzc = __ldg(&Bg->nzc);
-      const int ke = P.ka - __ldg(&Bg->e0), ko = P.kb - __ldg(&Bg->o0);
-      stn[f] = (ke >= 0 && ke <= ne && ko >= 0 && ko <= no) ? C[ne][ke] * C[no][ko] : 0u;
-      unsigned cg = 0;
-      if (nzc > 0) cg = par32s(__ldg(&Bg->zg[0][0]) & P.ga) ^ par32s(__ldg(&Bg->zg[0][1]) & P.gb);
-      if (nzc > 1) cg |= (par32s(__ldg(&Bg->zg[1][0]) & P.ga) ^ par32s(__ldg(&Bg->zg[1][1]) & P.gb)) << 1;
-      stc[f] = (uint8_t)cg;
-    }
-    if (tid < kCw) {
-      cw[0][tid] = coef_word(0);
-      if (nb > 1) cw[1][tid] = coef_word(1);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t a = 0;
-      for (int f = 0; f < nb; ++f) {
-        sto[f] = a;
-        a += stn[f];
-      }
-    }
-    __syncthreads();
     LV* lgp = log ? reinterpret_cast<LV*>(log + P.logbase) : nullptr;
     auto pos = [&](int st) { return MODE == 3 ? nb - 1 - st : st; };  // a step's forward position
     // item tid of step s (wq0, lq0) and of step s + 1 (wq1, lq1): map word and
@@ -821,6 +837,9 @@ __device__ __forceinline__ void sector_run_body(typename SCx<T>::V* psi, typenam
     __syncthreads();
   }
   if (ADJ && nb > 0 && !mp) reduce_block(nb - 1, pend_w);
+  // the next run may launch once every CTA is here (its CTAs then take the SMs as
+  // this run's scatters finish, so that they spread over the SMs)
+  grid_dep_launch_dependents();
   if (MODE == 4) return;  // read only
   T* pw = reinterpret_cast<T*>(psi);
   for (uint32_t m = tid; m < size; m += NT) {
@@ -1755,10 +1774,22 @@ static cudaError_t runs_t(void* psi, void* lam, const RunInfo* runs, int nruns, 
     const size_t smem = run_smem_bytes<MODE, T>(R.maxsize);
     if (smem > run_smem_max<MODE, T>() || R.b1 - R.b0 > kRunMaxBlocks || R.nparts <= 0) return cudaErrorInvalidValue;
     if constexpr (kWide) {
-      if (wide)
-        k_sector_run_wide<MODE, T, DSW><<<R.nparts, wide_threads<MODE>(), smem, s>>>(
-            static_cast<V*>(psi), static_cast<V*>(lam), R, parts, blks, partial, pmax, cm, static_cast<V*>(log),
-            strs, map, DSW && dss);
+      if (wide) {  // programmatic dependent launch: its table prologue overlaps the previous kernel's tail
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)R.nparts);
+        cfg.blockDim = dim3(wide_threads<MODE>());
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t le = cudaLaunchKernelEx(&cfg, k_sector_run_wide<MODE, T, DSW>, static_cast<V*>(psi),
+                                                  static_cast<V*>(lam), R, parts, blks, partial, pmax, cm,
+                                                  static_cast<V*>(log), strs, map, DSW && dss);
+        if (le != cudaSuccess) return le;
+      }
     }
     if constexpr (!DSW)
       if (!wide)
