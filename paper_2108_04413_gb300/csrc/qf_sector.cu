@@ -1270,9 +1270,10 @@ template <> struct PairAcc<double> {
 // Double-single pair products (complex128, QF_HPSI_DS): a weight and an amplitude
 // each as a float pair hi + lo (about 48 significant bits); the product keeps the
 // exact error of hi * hi and both cross terms, the float-pair sum takes it through
-// an error-free TwoSum, and the sum is folded into the member's FP64 sum after each
-// innermost loop (at most C(16, 2)^2 / 16 products in between).  The rounded
-// operations are explicit so that no multiply is fused into the TwoSum.
+// an error-free TwoSum, and after each innermost loop (at most C(16, 2)^2 / 16
+// products) the sum is added into the member's double-single total, which is
+// converted to FP64 once.  The rounded operations are explicit so that no
+// multiply is fused into the TwoSum.
 struct DsAcc {
   float sh = 0.0f, sl = 0.0f;
   __device__ __forceinline__ void add(float2 w, float2 v) {
@@ -1288,6 +1289,19 @@ struct DsAcc {
   }
   __device__ __forceinline__ void fold(double& lx) {
     lx += (double)sh + (double)sl;
+    sh = 0.0f;
+    sl = 0.0f;
+  }
+  // this sum added into o as a double-single value (TwoSum of the high parts, the
+  // low parts and the error summed, one renormalisation): no FP64 operation
+  __device__ __forceinline__ void fold_into(DsAcc& o) {
+    const float s = __fadd_rn(o.sh, sh);
+    const float bp = __fsub_rn(s, o.sh);
+    const float err = __fadd_rn(__fsub_rn(o.sh, __fsub_rn(s, bp)), __fsub_rn(sh, bp));
+    const float lo = __fadd_rn(__fadd_rn(o.sl, sl), err);
+    const float h = __fadd_rn(s, lo);
+    o.sl = __fsub_rn(lo, __fsub_rn(h, s));
+    o.sh = h;
     sh = 0.0f;
     sl = 0.0f;
   }
@@ -1345,7 +1359,7 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
   const size_t rowself = (size_t)ie * cnt_o;
   double lx = 0.0, lxs = 0.0;  // lxs: fixed-point weights times psi (units of 2^-e)
   PairAcc<T> pa;
-  DsAcc da;
+  DsAcc da, dt;  // dt: the member's double-single total, converted to FP64 once
   // x = 0: K + sum U[r] + sum V[r][s] over occupied r < s
   long long dsum = __ldg(d.dg);
   for (uint32_t m = c; m; m &= m - 1) {
@@ -1420,8 +1434,8 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
           const uint32_t e = bl[BSTRIDE * k];
           da.add(flip_sign2(__ldg(drow + ((e >> 14) & 0xFFu)), sa ^ (e >> 31)), pair(rowa + (e & 0x3FFFu)));
         }
-        da.fold(lx);
-        db.fold(lx);
+        da.fold_into(dt);
+        db.fold_into(dt);
       } else {
         PairAcc<T> pb;
         int k = 0;
@@ -1464,7 +1478,7 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
             pa.add(flip_sign(__ldg(waa + w2 + v1), sg), pair(idx), lx);
         }
       }
-      if constexpr (DS) da.fold(lx);
+      if constexpr (DS) da.fold_into(dt);
       else pa.fold(lx);
     }
   }
@@ -1490,10 +1504,11 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
             pa.add(flip_sign(__ldg(wbb + w2 + v1), sg), pair(idx), lx);
         }
       }
-      if constexpr (DS) da.fold(lx);
+      if constexpr (DS) da.fold_into(dt);
       else pa.fold(lx);
     }
   }
+  if constexpr (DS) dt.fold(lx);
   return fma(lxs, d.inv_fix, lx);
 }
 
