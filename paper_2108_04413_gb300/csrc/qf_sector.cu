@@ -1252,19 +1252,25 @@ __device__ __forceinline__ float flip_sign(float w, uint32_t s) {
 }
 
 // Pair products of one member: FP64 multiply-adds into the member's sum
-// (complex128), or FP32 ones folded into it after each innermost loop
-// (complex64; at most C(16, 2) products between folds).
+// (complex128), or FP32 ones added after each innermost loop (at most C(16, 2)
+// products) into a float-pair total that is converted to FP64 once (complex64).
 template <typename T> struct PairAcc {
   float s = 0.0f;
   __device__ __forceinline__ void add(float w, float v, double&) { s = fmaf(w, v, s); }
-  __device__ __forceinline__ void fold(double& lx) {
-    lx += (double)s;
+  // s added into the float-pair total (hi, lo) by a TwoSum: no FP64 operation
+  __device__ __forceinline__ void fold_into(float& hi, float& lo) {
+    const float t = __fadd_rn(hi, s);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(s, bp));
+    const float l = __fadd_rn(lo, err);
+    hi = __fadd_rn(t, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, t));
     s = 0.0f;
   }
 };
 template <> struct PairAcc<double> {
   __device__ __forceinline__ void add(double w, double v, double& lx) { lx = fma(w, v, lx); }
-  __device__ __forceinline__ void fold(double&) {}
+  __device__ __forceinline__ void fold_into(float&, float&) {}
 };
 
 // Double-single pair products (complex128, QF_HPSI_DS): a weight and an amplitude
@@ -1359,7 +1365,7 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
   const size_t rowself = (size_t)ie * cnt_o;
   double lx = 0.0, lxs = 0.0;  // lxs: fixed-point weights times psi (units of 2^-e)
   PairAcc<T> pa;
-  DsAcc da, dt;  // dt: the member's double-single total, converted to FP64 once
+  DsAcc da, dt;  // dt: the member's float-pair total of the pair products, converted to FP64 once
   // x = 0: K + sum U[r] + sum V[r][s] over occupied r < s
   long long dsum = __ldg(d.dg);
   for (uint32_t m = c; m; m &= m - 1) {
@@ -1450,8 +1456,8 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
           const uint32_t e = bl[BSTRIDE * k];
           pa.add(flip_sign(__ldg(wrow + ((e >> 14) & 0xFFu)), sa ^ (e >> 31)), pair(rowa + (e & 0x3FFFu)), lx);
         }
-        pa.fold(lx);
-        pb.fold(lx);
+        pa.fold_into(dt.sh, dt.sl);
+        pb.fold_into(dt.sh, dt.sl);
       }
     }
   }
@@ -1479,7 +1485,7 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
         }
       }
       if constexpr (DS) da.fold_into(dt);
-      else pa.fold(lx);
+      else pa.fold_into(dt.sh, dt.sl);
     }
   }
   for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
@@ -1505,10 +1511,10 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
         }
       }
       if constexpr (DS) da.fold_into(dt);
-      else pa.fold(lx);
+      else pa.fold_into(dt.sh, dt.sl);
     }
   }
-  if constexpr (DS) dt.fold(lx);
+  dt.fold(lx);  // the pair products' float-pair total (zero for FP64 products)
   return fma(lxs, d.inv_fix, lx);
 }
 
