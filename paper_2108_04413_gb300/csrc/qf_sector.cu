@@ -1425,10 +1425,22 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
       const T* wrow = wab + wo;
       const float2* drow = d.dab + wo;
       if constexpr (DS) {
-        // two independent accumulators (even and odd entries), so that two
-        // TwoSum chains and their loads are in flight at once
+        // two independent accumulators (alternate entries), so that two TwoSum
+        // chains are in flight, and four entries' loads issued together
         DsAcc db;
         int k = 0;
+        for (; k + 3 < nbs; k += 4) {
+          const uint32_t e0 = bl[BSTRIDE * k], e1 = bl[BSTRIDE * (k + 1)];
+          const uint32_t e2 = bl[BSTRIDE * (k + 2)], e3 = bl[BSTRIDE * (k + 3)];
+          const float2 w0 = __ldg(drow + ((e0 >> 14) & 0xFFu)), w1 = __ldg(drow + ((e1 >> 14) & 0xFFu));
+          const float2 w2 = __ldg(drow + ((e2 >> 14) & 0xFFu)), w3 = __ldg(drow + ((e3 >> 14) & 0xFFu));
+          const float2 v0 = pair(rowa + (e0 & 0x3FFFu)), v1 = pair(rowa + (e1 & 0x3FFFu));
+          const float2 v2 = pair(rowa + (e2 & 0x3FFFu)), v3 = pair(rowa + (e3 & 0x3FFFu));
+          da.add(flip_sign2(w0, sa ^ (e0 >> 31)), v0);
+          db.add(flip_sign2(w1, sa ^ (e1 >> 31)), v1);
+          da.add(flip_sign2(w2, sa ^ (e2 >> 31)), v2);
+          db.add(flip_sign2(w3, sa ^ (e3 >> 31)), v3);
+        }
         for (; k + 1 < nbs; k += 2) {
           const uint32_t e0 = bl[BSTRIDE * k], e1 = bl[BSTRIDE * (k + 1)];
           const float2 w0 = __ldg(drow + ((e0 >> 14) & 0xFFu)), w1 = __ldg(drow + ((e1 >> 14) & 0xFFu));
@@ -1445,6 +1457,18 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
       } else {
         PairAcc<T> pb;
         int k = 0;
+        for (; k + 3 < nbs; k += 4) {
+          const uint32_t e0 = bl[BSTRIDE * k], e1 = bl[BSTRIDE * (k + 1)];
+          const uint32_t e2 = bl[BSTRIDE * (k + 2)], e3 = bl[BSTRIDE * (k + 3)];
+          const T w0 = __ldg(wrow + ((e0 >> 14) & 0xFFu)), w1 = __ldg(wrow + ((e1 >> 14) & 0xFFu));
+          const T w2 = __ldg(wrow + ((e2 >> 14) & 0xFFu)), w3 = __ldg(wrow + ((e3 >> 14) & 0xFFu));
+          const T v0 = pair(rowa + (e0 & 0x3FFFu)), v1 = pair(rowa + (e1 & 0x3FFFu));
+          const T v2 = pair(rowa + (e2 & 0x3FFFu)), v3 = pair(rowa + (e3 & 0x3FFFu));
+          pa.add(flip_sign(w0, sa ^ (e0 >> 31)), v0, lx);
+          pb.add(flip_sign(w1, sa ^ (e1 >> 31)), v1, lx);
+          pa.add(flip_sign(w2, sa ^ (e2 >> 31)), v2, lx);
+          pb.add(flip_sign(w3, sa ^ (e3 >> 31)), v3, lx);
+        }
         for (; k + 1 < nbs; k += 2) {
           const uint32_t e0 = bl[BSTRIDE * k], e1 = bl[BSTRIDE * (k + 1)];
           const T w0 = __ldg(wrow + ((e0 >> 14) & 0xFFu)), w1 = __ldg(wrow + ((e1 >> 14) & 0xFFu));
