@@ -916,14 +916,18 @@ __global__ void __launch_bounds__(kRunThreads) k_run_itemmap(RunInfo run, const 
 }
 
 // out[b] = sum over the parts of block b's run of partial[b * pmax + part], in part order.
+// One warp per block: lane l sums parts l, l + 32, ... in order, then a fixed
+// butterfly combines the lanes (deterministic).
 __global__ void k_sector_reduce_parts(const double* __restrict__ partial, int pmax, const RunBlk* __restrict__ blks,
                                       int nblk, double* out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nblk) return;
+  const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (b >= nblk) return;  // whole warps leave together
   const int np = blks[b].np;
   double s = 0.0;
-  for (int p = 0; p < np; ++p) s += partial[(size_t)b * pmax + p];
-  out[b] = s;
+  for (int p = lane; p < np; p += 32) s += partial[(size_t)b * pmax + p];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) out[b] = s;
 }
 
 
@@ -1873,7 +1877,7 @@ cudaError_t launch_sector_runs(void* psi, void* lam, qf_dtype dt, bool adj, bool
       : mode == 2 ? runs_t<2, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s)
                   : runs_t<3, float>(psi, lam, runs, nruns, parts, blks, partial, pmax, cm, log, strs, map, dss, s);
   if (e == cudaSuccess && adj) {
-    k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
+    k_sector_reduce_parts<<<(nblk + 7) / 8, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
     count_launch();
   }
@@ -1905,7 +1909,7 @@ cudaError_t launch_sector_overlaps(void* psi, qf_dtype dt, const RunInfo* runs, 
                       ? runs_t<4, double>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, nullptr, false, s)
                       : runs_t<4, float>(psi, psi, runs, nruns, parts, blks, partial, pmax, cm, nullptr, strs, nullptr, false, s);
   if (e == cudaSuccess) {
-    k_sector_reduce_parts<<<(nblk + 255) / 256, 256, 0, s>>>(partial, pmax, blks, nblk, out);
+    k_sector_reduce_parts<<<(nblk + 7) / 8, 256, 0, s>>>(partial, pmax, blks, nblk, out);
     e = cudaGetLastError();
     count_launch();
   }
