@@ -1368,8 +1368,8 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
   const uint32_t va = ((1u << ne) - 1u) & ~la, vb = ((1u << no) - 1u) & ~lb;
   const size_t rowself = (size_t)ie * cnt_o;
   double lx = 0.0, lxs = 0.0;  // lxs: fixed-point weights times psi (units of 2^-e)
-  PairAcc<T> pa;
-  DsAcc da, dt;  // dt: the member's float-pair total of the pair products, converted to FP64 once
+  PairAcc<T> pa, pb;  // two accumulators, so that two chains are in flight
+  DsAcc da, db, dt;   // dt: the member's float-pair total of the pair products, converted to FP64 once
   // x = 0: K + sum U[r] + sum V[r][s] over occupied r < s
   long long dsum = __ldg(d.dg);
   for (uint32_t m = c; m; m &= m - 1) {
@@ -1431,7 +1431,6 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
       if constexpr (DS) {
         // two independent accumulators (alternate entries), so that two TwoSum
         // chains are in flight, and four entries' loads issued together
-        DsAcc db;
         int k = 0;
         for (; k + 3 < nbs; k += 4) {
           const uint32_t e0 = bl[BSTRIDE * k], e1 = bl[BSTRIDE * (k + 1)];
@@ -1459,7 +1458,6 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
         da.fold_into(dt);
         db.fold_into(dt);
       } else {
-        PairAcc<T> pb;
         int k = 0;
         for (; k + 3 < nbs; k += 4) {
           const uint32_t e0 = bl[BSTRIDE * k], e1 = bl[BSTRIDE * (k + 1)];
@@ -1502,18 +1500,36 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
         const uint32_t s2 = so ^ ((ppa >> v2) & 1u);
         const size_t w2 = wo + v2 * (v2 - 1) / 2;
         const uint32_t lav = lao | (1u << v2);
-        for (uint32_t n1 = va & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
+        // two entries per round (the second into db / pb), so that two chains and
+        // their loads are in flight
+        for (uint32_t n1 = va & ((1u << v2) - 1u); n1;) {
           const int v1 = __ffs((int)n1) - 1;
-          const uint32_t sg = s2 ^ ((ppa >> v1) & 1u);
+          n1 &= n1 - 1;
           const size_t idx = (size_t)__ldg(ra + (lav | (1u << v1))) * cnt_o + io;
+          const uint32_t sg = s2 ^ ((ppa >> v1) & 1u);
+          if (n1) {
+            const int u1 = __ffs((int)n1) - 1;
+            n1 &= n1 - 1;
+            const size_t jdx = (size_t)__ldg(ra + (lav | (1u << u1))) * cnt_o + io;
+            const uint32_t tg = s2 ^ ((ppa >> u1) & 1u);
+            if constexpr (DS)
+              db.add(flip_sign2(__ldg(d.daa + w2 + u1), tg), pair(jdx));
+            else
+              pb.add(flip_sign(__ldg(waa + w2 + u1), tg), pair(jdx), lx);
+          }
           if constexpr (DS)
             da.add(flip_sign2(__ldg(d.daa + w2 + v1), sg), pair(idx));
           else
             pa.add(flip_sign(__ldg(waa + w2 + v1), sg), pair(idx), lx);
         }
       }
-      if constexpr (DS) da.fold_into(dt);
-      else pa.fold_into(dt.sh, dt.sl);
+      if constexpr (DS) {
+        da.fold_into(dt);
+        db.fold_into(dt);
+      } else {
+        pa.fold_into(dt.sh, dt.sl);
+        pb.fold_into(dt.sh, dt.sl);
+      }
     }
   }
   for (uint32_t m2 = lb; m2; m2 &= m2 - 1) {
@@ -1528,18 +1544,34 @@ __device__ __forceinline__ double direct_member(uint32_t it, const SecDirect& d,
         const uint32_t s2 = so ^ ((ppb >> v2) & 1u);
         const size_t w2 = wo + v2 * (v2 - 1) / 2;
         const uint32_t lbv = lbo | (1u << v2);
-        for (uint32_t n1 = vb & ((1u << v2) - 1u); n1; n1 &= n1 - 1) {
+        for (uint32_t n1 = vb & ((1u << v2) - 1u); n1;) {
           const int v1 = __ffs((int)n1) - 1;
-          const uint32_t sg = s2 ^ ((ppb >> v1) & 1u);
+          n1 &= n1 - 1;
           const size_t idx = rowself + __ldg(rb + (lbv | (1u << v1)));
+          const uint32_t sg = s2 ^ ((ppb >> v1) & 1u);
+          if (n1) {
+            const int u1 = __ffs((int)n1) - 1;
+            n1 &= n1 - 1;
+            const size_t jdx = rowself + __ldg(rb + (lbv | (1u << u1)));
+            const uint32_t tg = s2 ^ ((ppb >> u1) & 1u);
+            if constexpr (DS)
+              db.add(flip_sign2(__ldg(d.dbb + w2 + u1), tg), pair(jdx));
+            else
+              pb.add(flip_sign(__ldg(wbb + w2 + u1), tg), pair(jdx), lx);
+          }
           if constexpr (DS)
             da.add(flip_sign2(__ldg(d.dbb + w2 + v1), sg), pair(idx));
           else
             pa.add(flip_sign(__ldg(wbb + w2 + v1), sg), pair(idx), lx);
         }
       }
-      if constexpr (DS) da.fold_into(dt);
-      else pa.fold_into(dt.sh, dt.sl);
+      if constexpr (DS) {
+        da.fold_into(dt);
+        db.fold_into(dt);
+      } else {
+        pa.fold_into(dt.sh, dt.sl);
+        pb.fold_into(dt.sh, dt.sl);
+      }
     }
   }
   dt.fold(lx);  // the pair products' float-pair total (zero for FP64 products)
