@@ -1629,21 +1629,26 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
   uint64_t total = 0;
   for (size_t b = 0; b < nblk; ++b) total += (1ull << out->blks[b].ne) + (1ull << out->blks[b].no);
   const bool tab = total <= kStringsMax;
-  if (tab) out->strs.reserve(total);
+  if (!tab) {
+    for (size_t b = 0; b < 2 * nblk; ++b) out->blks[b].lsa = out->blks[b].lsb = qf::kNoStrings;
+    return true;
+  }
+  // each block's two tables start where the previous blocks' end; filled in parallel
+  std::vector<uint32_t> base(2 * nblk + 1, 0);
   for (size_t b = 0; b < nblk; ++b) {
+    base[2 * b + 1] = base[2 * b] + (1u << out->blks[b].ne);
+    base[2 * b + 2] = base[2 * b + 1] + (1u << out->blks[b].no);
+  }
+  out->strs.assign(base[2 * nblk], 0);
+  qf::HostPool::get().parallel_for(nblk, 16, [&](size_t b) {
     qf::RunBlk& F = out->blks[b];
     qf::RunBlk& I = out->blks[nblk + b];
-    if (!tab) {
-      F.lsa = F.lsb = I.lsa = I.lsb = qf::kNoStrings;
-      continue;
-    }
     for (int spin = 0; spin < 2; ++spin) {
       const int m = spin ? F.no : F.ne;
       const uint8_t* pos = spin ? F.opos : F.epos;
-      const uint32_t base = (uint32_t)out->strs.size();
-      out->strs.resize(base + (1u << m));
+      const uint32_t b0 = base[2 * b + spin];
       uint32_t next[qf::kSecMaxPos + 1];  // next slot of each size
-      uint32_t acc = base;
+      uint32_t acc = b0;
       for (int k = 0; k <= m; ++k) {
         next[k] = acc;
         acc += binom(m, k);
@@ -1654,10 +1659,10 @@ bool build_runs(const qf::SecBlk* sec, size_t nblk, int n, int na, int nb, uint6
           if ((mask >> j) & 1u) dep |= 1u << pos[j];
         out->strs[next[popc(mask)]++] = (uint16_t)dep;
       }
-      (spin ? F.lsb : F.lsa) = base;
-      (spin ? I.lsb : I.lsa) = base;
+      (spin ? F.lsb : F.lsa) = b0;
+      (spin ? I.lsb : I.lsa) = b0;
     }
-  }
+  });
   return true;
 }
 
@@ -2038,26 +2043,16 @@ std::vector<qf_state::Blk> plan_blocks(const RotIn* r, const int32_t* par, size_
   }
   std::vector<Blk> cand(runs.size());
   std::vector<char> ok(runs.size(), 0);
-  auto work = [&](size_t t0, size_t step) {
-    for (size_t k = t0; k < runs.size(); k += step) {
-      const size_t i = runs[k].first;
-      const int run = runs[k].second;
-      Blk& b = cand[k];
-      b.i = i;
-      b.j = i + run;
-      b.sparse = run >= 2 && build_sparse(r + i, run, n, false, true, &b.fwd) &&
-                 build_sparse(r + i, run, n, true, true, &b.inv) && b.fwd.nr == b.inv.nr;
-      ok[k] = b.sparse;
-    }
-  };
-  const size_t nth = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
-  if (runs.size() >= 64 && nth > 1) {
-    std::vector<std::thread> th;
-    for (size_t t = 0; t < nth; ++t) th.emplace_back(work, t, nth);
-    for (auto& x : th) x.join();
-  } else {
-    work(0, 1);
-  }
+  qf::HostPool::get().parallel_for(runs.size(), 16, [&](size_t k) {
+    const size_t i = runs[k].first;
+    const int run = runs[k].second;
+    Blk& b = cand[k];
+    b.i = i;
+    b.j = i + run;
+    b.sparse = run >= 2 && build_sparse(r + i, run, n, false, true, &b.fwd) &&
+               build_sparse(r + i, run, n, true, true, &b.inv) && b.fwd.nr == b.inv.nr;
+    ok[k] = b.sparse;
+  });
   // every run a sparse block (a UCC ansatz): the candidates are the plan (a
   // block carries two composites of about 8 KB each; copying them dominated)
   if (std::all_of(ok.begin(), ok.end(), [](char v) { return v != 0; })) return cand;
@@ -2302,6 +2297,13 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
       if (po != QF_OK) return po;
     }
     const SectorRuns& rs = ap.runs;
+    // a real state with a Hamiltonian of molecular form takes the direct tables
+    // (built before this call queues any kernel: their upload synchronises the stream)
+    ExpPlan* pm = const_cast<ExpPlan*>(p);
+    if (lreal && st->n <= 32) {
+      qf_status ds = ensure_direct(st, pm);
+      if (ds != QF_OK) return ds;
+    }
     const qf::SecSpace sp = sector_space(n, na, nbeta);
     qf::SecCompact cm{};
     qf_status cs = ensure_compact(st, sp, na, nbeta, &cm);
@@ -2363,12 +2365,6 @@ static qf_status energy_grad_impl(qf_state* st, uint64_t det, const qf_arot* ans
       }
     }
     st->run_items = rs.run_items;
-    // a real state with a Hamiltonian of molecular form takes the direct tables
-    ExpPlan* pm = const_cast<ExpPlan*>(p);
-    if (lreal && st->n <= 32) {
-      qf_status ds = ensure_direct(st, pm);
-      if (ds != QF_OK) return ds;
-    }
     const bool hdirect = lreal && pm->direct == 1;
     // complex128 in QF_HPSI_DS mode: the mapped sweeps run in double-single arithmetic;
     // the reverse must agree with the forward, whose log it reads
