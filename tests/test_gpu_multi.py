@@ -43,7 +43,7 @@ def _close(dtype, e, g, e_ref, g_ref):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("n_orb,n_el", [(4, 4), (5, 5), (7, 7)])
+@pytest.mark.parametrize("n_orb,n_el", [(4, 4), (5, 5), (7, 7), (8, 8)])
 def test_multi_rows_match_single_calls(n_orb, n_el, dtype):
     h, g, A, exs, T, det = _system(n_orb, n_el, 40 + n_orb)
     t = _rows(len(exs), 9, 1000 + n_orb)
@@ -73,6 +73,24 @@ def test_multi_rows_match_oracle(dtype):
         e_ref, g_ref = fermion.ucc_gradient_adjoint(n_orb, n_el, h, g, t[k], exs)
         _close(dtype, e_m[k], g_m[k], e_ref, g_ref)
     st.close()
+
+
+def test_multi_largest_sector_in_shared_memory_is_one_launch():
+    """16 qubits at half filling (4900 members, psi and lambda 78 KB in complex128)
+    is the largest sector a CTA holds: its rows still take one launch."""
+    h, g, A, exs, T, det = _system(8, 8, 21)
+    t = _rows(len(exs), 4, 31)
+    st = qf.State(16, "c128")
+    st.energy_grad_multi(det, A, t[:1], T)
+    qf.kernel_launches(reset=True)
+    e, gr = st.energy_grad_multi(det, A, t, T)
+    assert qf.kernel_launches(reset=True) == 2
+    ref = qf.State(16, "c128")
+    for k in range(len(t)):
+        e1, g1 = ref.energy_grad(det, A, t[k], T)
+        _close("c128", e[k], gr[k], e1, g1)
+    st.close()
+    ref.close()
 
 
 def test_multi_is_one_launch_for_all_rows():
