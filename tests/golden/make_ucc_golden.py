@@ -26,14 +26,14 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import numpy as np  # noqa: E402
 
 from oracle import fermion, sector  # noqa: E402
-from workloads import CONFIGS, amplitudes, integrals, probe_vectors, sample_indices  # noqa: E402
+from workloads import WORKLOADS, amplitudes, integrals, probe_vectors, sample_indices  # noqa: E402
 
 PROBE_SEED = 2024
 SAMPLE_SEED = 2025
 
 
 def main(out=os.path.join(HERE, "ucc24_oracle.json")):
-    cfg = CONFIGS[2]
+    cfg = WORKLOADS["ucc24"]
     t0 = time.time()
     h, g = integrals(cfg["n_orb"], cfg["seed"])
     exs = fermion.excitations(cfg["n_orb"], cfg["n_el"])

@@ -19,12 +19,12 @@ __graft_entry__.build()
 
 from oracle import fermion, pauli  # noqa: E402
 from paper_2108_04413_gb300 import prep, qf  # noqa: E402
-from workloads import CONFIGS, amplitudes, integrals  # noqa: E402
+from workloads import WORKLOADS, amplitudes, integrals  # noqa: E402
 
 
 @pytest.fixture(scope="module")
 def ucc24():
-    cfg = CONFIGS[2]
+    cfg = WORKLOADS["ucc24"]
     h, g = integrals(cfg["n_orb"], cfg["seed"])
     T = prep.molecular_hamiltonian(h, g)
     A, exs = prep.uccsd_ansatz(cfg["n_orb"], cfg["n_el"])

@@ -36,7 +36,7 @@ __graft_entry__.build()
 
 from oracle import fermion, sector, sparse  # noqa: E402
 from paper_2108_04413_gb300 import prep, qf  # noqa: E402
-from workloads import (CONFIGS, amplitudes, integrals, probe_vectors, random_angles,  # noqa: E402
+from workloads import (WORKLOADS, amplitudes, integrals, probe_vectors, random_angles,  # noqa: E402
                        random_coefficients, random_pauli_masks)
 
 TOL_AMP = {"c128": 1e-12, "c64": 2e-5}
@@ -107,7 +107,7 @@ def test_ucc20_apply_circuit_state_matches_oracle(ucc20, dtype):
 @pytest.fixture(scope="module")
 def ucc24():
     gold = json.load(open(GOLDEN))
-    cfg = CONFIGS[2]
+    cfg = WORKLOADS["ucc24"]
     assert (gold["n_orb"], gold["n_el"], gold["seed"], gold["t_sigma"]) == \
         (cfg["n_orb"], cfg["n_el"], cfg["seed"], cfg["t_sigma"])
     h, g = integrals(cfg["n_orb"], cfg["seed"])
@@ -158,7 +158,7 @@ def test_ucc24_apply_circuit_state_matches_oracle_golden(ucc24, dtype):
 def _config3_prefix(k_rot, k_terms):
     """The first rotations and terms of the 28-qubit random workload, drawn from
     the seeded generators with the seeds the library-side helpers use."""
-    n, seed = 28, CONFIGS[3]["seed"]
+    n, seed = 28, WORKLOADS["sweep28"]["seed"]
     x, z = random_pauli_masks(n, 500, seed)
     th = random_angles(500, seed + 1000)
     tx, tz = random_pauli_masks(n, 20000, seed + 2000)
@@ -172,8 +172,8 @@ def test_sweep28_prefix_matches_oracle(dtype):
     rots, terms = _config3_prefix(20, 200)
     idx, amp = sparse.apply_rotations(*sparse.basis(det), rots)
     e_ref = sparse.expectation(idx, amp, terms)
-    R = prep.random_circuit(n, 500, CONFIGS[3]["seed"])[:20]
-    T = prep.random_hamiltonian(n, 20000, CONFIGS[3]["seed"])[:200]
+    R = prep.random_circuit(n, 500, WORKLOADS["sweep28"]["seed"])[:20]
+    T = prep.random_hamiltonian(n, 20000, WORKLOADS["sweep28"]["seed"])[:200]
     assert [(int(a), int(b)) for a, b, _ in rots] == list(zip(R["x"].tolist(), R["z"].tolist()))
     f = torch.float64 if dtype == "c128" else torch.float32
     ref = torch.zeros(1 << n, dtype=torch.complex128 if dtype == "c128" else torch.complex64, device="cuda")

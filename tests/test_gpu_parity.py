@@ -19,7 +19,7 @@ __graft_entry__.build()
 
 from oracle import fermion, pauli  # noqa: E402
 from paper_2108_04413_gb300 import prep, qf  # noqa: E402
-from workloads import CONFIGS, amplitudes, integrals, random_state  # noqa: E402
+from workloads import WORKLOADS, amplitudes, integrals, random_state  # noqa: E402
 
 TOL_AMP_C128 = 1e-12
 TOL_E_C128 = 1e-10
@@ -97,8 +97,8 @@ def test_scale_renormalisation_long_circuit():
     assert np.abs(out - ref).max() < 1e-11
 
 
-def _ucc_problem(cfg_id):
-    cfg = CONFIGS[cfg_id]
+def _ucc_problem(name):
+    cfg = WORKLOADS[name]
     h, g = integrals(cfg["n_orb"], cfg["seed"])
     T = prep.molecular_hamiltonian(h, g)
     A, exs = prep.uccsd_ansatz(cfg["n_orb"], cfg["n_el"])
@@ -106,9 +106,9 @@ def _ucc_problem(cfg_id):
     return cfg, h, g, T, A, exs, t
 
 
-@pytest.mark.parametrize("cfg_id", [0, 1])
-def test_ucc_state_and_energy_c128(cfg_id):
-    cfg, h, g, T, A, exs, t = _ucc_problem(cfg_id)
+@pytest.mark.parametrize("workload", ["ucc8", "ucc16"])
+def test_ucc_state_and_energy_c128(workload):
+    cfg, h, g, T, A, exs, t = _ucc_problem(workload)
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], "c128")
     st.set_basis(det)
@@ -122,9 +122,9 @@ def test_ucc_state_and_energy_c128(cfg_id):
     assert im == 0.0
 
 
-@pytest.mark.parametrize("cfg_id", [0, 1])
-def test_ucc_energy_c64(cfg_id):
-    cfg, h, g, T, A, exs, t = _ucc_problem(cfg_id)
+@pytest.mark.parametrize("workload", ["ucc8", "ucc16"])
+def test_ucc_energy_c64(workload):
+    cfg, h, g, T, A, exs, t = _ucc_problem(workload)
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], "c64")
     st.set_basis(det)
@@ -406,13 +406,13 @@ def test_bounded_wait_times_out_and_context_survives():
     assert np.abs(st.to_numpy() - ref).max() < 1e-15
 
 
-@pytest.mark.parametrize("cfg_id,dtype", [(0, "c128"), (1, "c128"), (0, "c64"), (1, "c64")])
-def test_pqe_residuals_match_oracle(cfg_id, dtype):
+@pytest.mark.parametrize("workload,dtype", [("ucc8", "c128"), ("ucc16", "c128"), ("ucc8", "c64"), ("ucc16", "c64")])
+def test_pqe_residuals_match_oracle(workload, dtype):
     """PQE residuals r_mu = <Phi_mu|U^dagger H U|Phi_0> (Eq. 23) of every dUCCSD
     excitation, through qf_residuals on the compact sector path, against the
     oracle's fermionic route; the energy and gradient that come along match
     qf_energy_grad."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(cfg_id)
+    cfg, h, g, T, A, exs, t = _ucc_problem(workload)
     det = (1 << cfg["n_el"]) - 1
     idx, sgn = prep.excited_determinants(exs, det)
     st = qf.State(cfg["n_qubits"], dtype)
@@ -482,12 +482,12 @@ def test_pqe_solve_matches_oracle(dtype, tol, etol):
         np.testing.assert_allclose(res.t, t_o, rtol=0, atol=1e-8)
 
 
-@pytest.mark.parametrize("cfg_id,dtype", [(0, "c128"), (1, "c128"), (0, "c64"), (1, "c64")])
-def test_pool_gradients_match_oracle(cfg_id, dtype):
+@pytest.mark.parametrize("workload,dtype", [("ucc8", "c128"), ("ucc16", "c128"), ("ucc8", "c64"), ("ucc16", "c64")])
+def test_pool_gradients_match_oracle(workload, dtype):
     """ADAPT pool gradients (Eq. 21) of every spin-conserving single and double
     excitation at the dUCCSD state: the overlap pass on the compact sector path,
     against the oracle's fermionic commutator route."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(cfg_id)
+    cfg, h, g, T, A, exs, t = _ucc_problem(workload)
     det = (1 << cfg["n_el"]) - 1
     pool = A.copy()
     pool["param"] = len(exs) - 1 - A["param"]  # operators numbered in reverse

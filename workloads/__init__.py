@@ -126,12 +126,12 @@ def serving_choices(count: int, seed: int, qubit_counts=(10, 12, 14, 16, 18, 20,
     return ns.astype(int), sys_idx.astype(int), t_seeds.astype(int)
 
 
-# Sizes of the five workloads (qubits, spatial orbitals, electrons, seeds).
-CONFIGS = {
-    0: dict(name="8q UCCSD", n_qubits=8, n_orb=4, n_el=4, seed=0, t_sigma=0.1),
-    1: dict(name="16q UCCSD", n_qubits=16, n_orb=8, n_el=8, seed=1, t_sigma=0.1),
-    2: dict(name="24q UCCSD", n_qubits=24, n_orb=12, n_el=12, seed=2, t_sigma=0.05),
-    3: dict(name="28q random Pauli exponentials", n_qubits=28, n_el=14, seed=3,
+# Sizes of the five workloads (qubits, spatial orbitals, electrons, seeds), by name.
+WORKLOADS = {
+    "ucc8": dict(name="8q UCCSD", n_qubits=8, n_orb=4, n_el=4, seed=0, t_sigma=0.1),
+    "ucc16": dict(name="16q UCCSD", n_qubits=16, n_orb=8, n_el=8, seed=1, t_sigma=0.1),
+    "ucc24": dict(name="24q UCCSD", n_qubits=24, n_orb=12, n_el=12, seed=2, t_sigma=0.05),
+    "sweep28": dict(name="28q random Pauli exponentials", n_qubits=28, n_el=14, seed=3,
             n_rot=500, n_terms=20000),
-    4: dict(name="serving", rate=200.0, qubit_counts=(10, 12, 14, 16, 18, 20, 22), seed=4),
+    "serving": dict(name="serving", rate=200.0, qubit_counts=(10, 12, 14, 16, 18, 20, 22), seed=4),
 }
