@@ -155,7 +155,7 @@ def test_ucc24_apply_circuit_state_matches_oracle_golden(ucc24, dtype):
     assert np.abs(proj.imag).max() == 0.0
 
 
-def _config3_prefix(k_rot, k_terms):
+def _sweep28_prefix(k_rot, k_terms):
     """The first rotations and terms of the 28-qubit random workload, drawn from
     the seeded generators with the seeds the library-side helpers use."""
     n, seed = 28, WORKLOADS["sweep28"]["seed"]
@@ -169,7 +169,7 @@ def _config3_prefix(k_rot, k_terms):
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_sweep28_prefix_matches_oracle(dtype):
     n, det = 28, (1 << 14) - 1
-    rots, terms = _config3_prefix(20, 200)
+    rots, terms = _sweep28_prefix(20, 200)
     idx, amp = sparse.apply_rotations(*sparse.basis(det), rots)
     e_ref = sparse.expectation(idx, amp, terms)
     R = prep.random_circuit(n, 500, WORKLOADS["sweep28"]["seed"])[:20]
