@@ -380,6 +380,17 @@ qf_status ensure_out(qf_state* st, size_t n) {
   return QF_OK;
 }
 
+// Term indices ordered by X mask, equal masks in input order (a stable sort by
+// x), through (x, index) pairs: contiguous keys, no indirection per comparison.
+std::vector<size_t> order_by_x(const qf_term* T, size_t nt) {
+  std::vector<std::pair<uint64_t, size_t>> key(nt);
+  for (size_t i = 0; i < nt; ++i) key[i] = {T[i].x, i};
+  std::sort(key.begin(), key.end());
+  std::vector<size_t> order(nt);
+  for (size_t i = 0; i < nt; ++i) order[i] = key[i].second;
+  return order;
+}
+
 qf_status validate_masks(const qf_state* st, uint64_t x, uint64_t z) {
   const uint64_t lim = (st->n >= 64) ? ~0ull : ((1ull << st->n) - 1ull);
   if ((x & ~lim) || (z & ~lim)) return fail(QF_EINVAL, "Pauli mask has a bit at or above the qubit count");
@@ -422,9 +433,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   }
   st->last_plan_key = key;
   // terms grouped by X mask: ascending x, each group's terms in input order
-  std::vector<size_t> order(nt);
-  for (size_t i = 0; i < nt; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return terms[a].x < terms[b].x; });
+  const std::vector<size_t> order = order_by_x(terms, nt);
   std::vector<qf::ExpGroup> groups;
   std::vector<qf::ExpChunk> ech, hch;
   ech.reserve(nt);  // at most one chunk per term: the tables are built in place
@@ -719,9 +728,7 @@ bool build_direct(const std::vector<qf_term>& T, int n, DirectHost* h) {
   h->s1a.assign((size_t)ne * ne * (n + 1), 0.0);
   h->s1b.assign((size_t)no * no * (n + 1), 0.0);
   h->dg.assign((size_t)1 + n + (size_t)n * n, 0.0);
-  std::vector<size_t> order(T.size());
-  for (size_t i = 0; i < T.size(); ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return T[a].x < T[b].x; });
+  const std::vector<size_t> order = order_by_x(T.data(), T.size());
   auto pr = [](int i, int j) { return i + j * (j - 1) / 2; };  // i < j
   std::vector<double> wr(n);
   for (size_t q0 = 0; q0 < order.size();) {
@@ -1022,8 +1029,7 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
   // scratch kept per thread (plan_blocks builds thousands of blocks in parallel)
   thread_local std::vector<int> supp, act;
   thread_local std::vector<uint64_t> zc;
-  thread_local std::vector<std::vector<cplx>> Ms, Qs;
-  thread_local std::vector<cplx> pr;
+  thread_local std::vector<cplx> dg, of, qg, pr;
   supp.clear();
   for (int i = 0; i < n; ++i)
     if ((x >> i) & 1) supp.push_back(i);
@@ -1042,20 +1048,20 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
   const int ncls = 1 << zc.size();
   const int D = 1 << u;
   const uint64_t xl = (uint64_t)D - 1;
-  if ((int)Ms.size() < ncls) {
-    Ms.resize(ncls);
-    Qs.resize(ncls);
-  }
-  for (int c = 0; c < ncls; ++c) {
-    Ms[c].assign(D * D, cplx(0.0, 0.0));
-    Qs[c].assign(D * D, cplx(0.0, 0.0));
-  }
+  // Every rotation of the block pairs row with row ^ xl, so the composite M stays
+  // block diagonal in those pairs and the generator Q only links a row to its
+  // partner.  Per class, dg[row] = M[row][row], of[row] = M[row][row ^ xl] and
+  // qg[row] = Q[row][row ^ xl] are the only entries that can differ from the
+  // identity (every other entry of M - I and of Q stays exactly zero).
+  dg.assign((size_t)ncls * D, cplx(1.0, 0.0));
+  of.assign((size_t)ncls * D, cplx(0.0, 0.0));
+  qg.assign((size_t)ncls * D, cplx(0.0, 0.0));
   pr.assign(D, cplx(0.0, 0.0));
   const cplx iu(0, 1);
   for (int c = 0; c < ncls; ++c) {
-    std::vector<cplx>& M = Ms[c];
-    std::vector<cplx>& Q = Qs[c];
-    for (int i = 0; i < D; ++i) M[i * D + i] = 1.0;
+    cplx* M0 = &dg[(size_t)c * D];
+    cplx* M1 = &of[(size_t)c * D];
+    cplx* Q = &qg[(size_t)c * D];
     for (int k = 0; k < m; ++k) {
       const uint64_t zo = r[k].z & ~x;
       double sig = 1.0;
@@ -1072,37 +1078,39 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
         pr[row] = iy * sig * ((popc(zin & (uint64_t)(row ^ (int)xl)) & 1) ? -1.0 : 1.0);
       const double th = inverse ? -r[k].th : r[k].th;
       const double cs = std::cos(th), sn = std::sin(th);
-      // Every rotation of the block pairs row with row ^ xl, so M stays block
-      // diagonal in those pairs: only the 2x2 block of each pair changes.
+      // only the 2x2 block of each pair changes
       for (int r0 = 0; r0 < D; ++r0) {
         const int r1 = r0 ^ (int)xl;
         if (r1 < r0) continue;
-        const cplx m00 = M[r0 * D + r0], m01 = M[r0 * D + r1], m10 = M[r1 * D + r0], m11 = M[r1 * D + r1];
+        const cplx m00 = M0[r0], m01 = M1[r0], m10 = M1[r1], m11 = M0[r1];
         const cplx f0 = iu * sn * pr[r0], f1 = iu * sn * pr[r1];
-        M[r0 * D + r0] = cs * m00 - f0 * m10;
-        M[r0 * D + r1] = cs * m01 - f0 * m11;
-        M[r1 * D + r0] = cs * m10 - f1 * m00;
-        M[r1 * D + r1] = cs * m11 - f1 * m01;
+        M0[r0] = cs * m00 - f0 * m10;
+        M1[r0] = cs * m01 - f0 * m11;
+        M1[r1] = cs * m10 - f1 * m00;
+        M0[r1] = cs * m11 - f1 * m01;
       }
-      for (int row = 0; row < D; ++row) Q[row * D + (row ^ (int)xl)] += r[k].coeff * pr[row];
+      for (int row = 0; row < D; ++row) Q[row] += r[k].coeff * pr[row];
     }
   }
   // For the inverse the product above is R_m(-th_m)...R_1(-th_1); it equals the inverse of the
   // forward composite because the block's rotations commute.
+  // A row is active when its row or column of M - I or of Q (every class) has an
+  // entry: on the diagonal, or linking it to its partner.
   const double tol = 1e-14;
+  auto off_identity = [&](const cplx& d) { return d != 0.0 && std::abs(d) > tol; };
   act.clear();
   for (int row = 0; row < D; ++row) {
+    const int rp = row ^ (int)xl;
     bool a2 = false;
-    for (int c = 0; c < ncls && !a2; ++c)
-      for (int col = 0; col < D && !a2; ++col) {
-        const cplx d = Ms[c][row * D + col] - ((row == col) ? 1.0 : 0.0);
-        const cplx d2 = Ms[c][col * D + row] - ((row == col) ? 1.0 : 0.0);
-        // (exact zeros, every entry outside the pair blocks, skip the modulus)
-        if ((d != 0.0 && std::abs(d) > tol) || (d2 != 0.0 && std::abs(d2) > tol))
-          a2 = true;
-        else if (with_gen && (Qs[c][row * D + col] != 0.0 || Qs[c][col * D + row] != 0.0))
-          a2 = true;
-      }
+    for (int c = 0; c < ncls && !a2; ++c) {
+      const cplx* M0 = &dg[(size_t)c * D];
+      const cplx* M1 = &of[(size_t)c * D];
+      const cplx* Q = &qg[(size_t)c * D];
+      if (off_identity(M0[row] - 1.0) || off_identity(M1[row]) || off_identity(M1[rp]))
+        a2 = true;
+      else if (with_gen && (Q[row] != 0.0 || Q[rp] != 0.0))
+        a2 = true;
+    }
     if (a2) act.push_back(row);
   }
   const int nr = (int)act.size();
@@ -1123,7 +1131,11 @@ bool build_sparse(const RotIn* r, int m, int n, bool inverse, bool with_gen, qf:
   for (int c = 0; c < ncls; ++c)
     for (int i = 0; i < nr; ++i)
       for (int j = 0; j < nr; ++j) {
-        const cplx mv = Ms[c][act[i] * D + act[j]] - ((i == j) ? 1.0 : 0.0), qv = Qs[c][act[i] * D + act[j]];
+        const int ri = act[i], rj = act[j];
+        const bool pair = rj == (ri ^ (int)xl);
+        const cplx me = (rj == ri) ? dg[(size_t)c * D + ri] : pair ? of[(size_t)c * D + ri] : cplx(0.0, 0.0);
+        const cplx mv = me - ((i == j) ? 1.0 : 0.0);
+        const cplx qv = pair ? qg[(size_t)c * D + ri] : cplx(0.0, 0.0);
         a->M[c][i][j] = make_double2(mv.real(), mv.imag());
         a->Q[c][i][j] = make_double2(qv.real(), qv.imag());
       }
