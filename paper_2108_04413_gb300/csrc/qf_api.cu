@@ -440,9 +440,11 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
   hch.reserve(nt);
   // scratch reused across groups
   std::vector<size_t> idx;
-  std::vector<std::vector<size_t>> parts;
-  std::vector<std::vector<uint32_t>> coords;
-  std::vector<std::vector<uint64_t>> bases;
+  // the group's chunks, flat: chunk c holds terms pterm[poff[c] .. poff[c + 1])
+  // with coordinates pcrd (same range) over the basis pbas[boff[c] .. boff[c + 1])
+  std::vector<size_t> pterm, poff, boff;
+  std::vector<uint32_t> pcrd;
+  std::vector<uint64_t> pbas;
   std::vector<uint64_t> B, E;
   std::vector<uint32_t> Cb, a;
   std::vector<double> addh, adde;  // a term's exact table addend (real or imaginary part) before its sign
@@ -464,9 +466,11 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
     // the terms with the sign (-1)^{popc(a_t & pat)}, a_t the term's coordinates.
     // When the whole group spans at most kChunkTerms dimensions it is one chunk;
     // otherwise each chunk takes kChunkTerms terms as its own basis.
-    parts.clear();
-    coords.clear();
-    bases.clear();
+    pterm.clear();
+    pcrd.clear();
+    pbas.clear();
+    poff.assign(1, 0);
+    boff.assign(1, 0);
     {
       B.clear();  // basis (term masks)
       E.clear();  // echelon copies (pivot = highest bit, descending)
@@ -498,39 +502,43 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
         a[t] = 1u << j;
       }
       if (fits) {
-        parts.push_back(idx);
-        coords.push_back(a);
-        bases.push_back(B);
+        pterm.assign(idx.begin(), idx.end());
+        pcrd.assign(a.begin(), a.end());
+        pbas.assign(B.begin(), B.end());
+        poff.push_back(pterm.size());
+        boff.push_back(pbas.size());
       } else {
         for (size_t k = 0; k < idx.size(); k += qf::kChunkTerms) {
           const size_t cnt = std::min<size_t>(qf::kChunkTerms, idx.size() - k);
-          std::vector<size_t> ps(idx.begin() + k, idx.begin() + k + cnt);
-          std::vector<uint32_t> cs(cnt);
-          std::vector<uint64_t> bs(cnt);
           for (size_t t = 0; t < cnt; ++t) {
-            cs[t] = 1u << t;
-            bs[t] = terms[ps[t]].z;
+            pterm.push_back(idx[k + t]);
+            pcrd.push_back(1u << t);
+            pbas.push_back(terms[idx[k + t]].z);
           }
-          parts.push_back(ps);
-          coords.push_back(cs);
-          bases.push_back(bs);
+          poff.push_back(pterm.size());
+          boff.push_back(pbas.size());
         }
       }
     }
-    g.nchunk = (int)parts.size();
-    for (size_t c = 0; c < parts.size(); ++c) {
+    const size_t nch = poff.size() - 1;
+    g.nchunk = (int)nch;
+    for (size_t c = 0; c < nch; ++c) {
       qf::ExpChunk& ce = ech.emplace_back();
       qf::ExpChunk& ch = hch.emplace_back();
-      for (int t = 0; t < qf::kChunkTerms; ++t) ce.z[t] = ch.z[t] = (t < (int)bases[c].size()) ? bases[c][t] : 0ull;
+      const size_t* cterm = pterm.data() + poff[c];
+      const uint32_t* ccrd = pcrd.data() + poff[c];
+      const uint64_t* cbas = pbas.data() + boff[c];
+      const int nbas = (int)(boff[c + 1] - boff[c]);
+      for (int t = 0; t < qf::kChunkTerms; ++t) ce.z[t] = ch.z[t] = (t < nbas) ? cbas[t] : 0ull;
       // per term: i^y c (real for even y, imaginary for odd y) and the expectation
       // weight (1 for x = 0, else 2 for the two pair members; odd y: 2 c (-1)^{(y+1)/2});
       // each is exact up to the sign the pattern gives it
-      const size_t nterm = parts[c].size();
+      const size_t nterm = poff[c + 1] - poff[c];
       addh.resize(nterm);
       adde.resize(nterm);
       odd.resize(nterm);
       for (size_t t = 0; t < nterm; ++t) {
-        const qf_term& T = terms[parts[c][t]];
+        const qf_term& T = terms[cterm[t]];
         const int y = popc(T.x & T.z) & 3;
         odd[t] = (char)(y & 1);
         if ((y & 1) == 0) {
@@ -545,7 +553,7 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
       for (int pat = 0; pat < (1 << qf::kChunkTerms); ++pat) {
         double ex = 0, ey = 0, hx = 0, hy = 0;
         for (size_t t = 0; t < nterm; ++t) {
-          const bool neg = popc(coords[c][t] & (uint32_t)pat) & 1;
+          const bool neg = popc(ccrd[t] & (uint32_t)pat) & 1;
           const double h = neg ? -addh[t] : addh[t], e = neg ? -adde[t] : adde[t];
           if (!odd[t]) {
             hx += h;
@@ -616,31 +624,34 @@ qf_status get_plan(qf_state* st, const qf_term* terms, size_t nt, const ExpPlan*
       continue;
     }
     const int code = sg[gi].chunk0 | (sg[gi].nchunk << 24);
-    std::vector<int> ev, od;
+    int ev[32], od[32], nev = 0, nod = 0;  // flipped alpha / beta orbitals (n <= 64)
     for (int q = 0; q < nq; ++q)
-      if ((x >> q) & 1) ((q & 1) ? od : ev).push_back(q >> 1);
+      if ((x >> q) & 1) {
+        if (q & 1) od[nod++] = q >> 1;
+        else ev[nev++] = q >> 1;
+      }
     if (w == 0) {
       diag = code;
       continue;
     }
     // each flip set is recorded under every occupied/empty split that a member can present
-    if (w == 2 && ev.size() == 2) {
+    if (w == 2 && nev == 2) {
       rkt[o_sa + ev[0] * ne + ev[1]] = code;
       rkt[o_sa + ev[1] * ne + ev[0]] = code;
-    } else if (w == 2 && od.size() == 2) {
+    } else if (w == 2 && nod == 2) {
       rkt[o_sb + od[0] * no + od[1]] = code;
       rkt[o_sb + od[1] * no + od[0]] = code;
-    } else if (w == 4 && (ev.size() == 4 || od.size() == 4)) {
-      const std::vector<int>& v = ev.size() == 4 ? ev : od;
-      const size_t off = ev.size() == 4 ? o_aa : o_bb;
-      const int P = ev.size() == 4 ? pe : po;
+    } else if (w == 4 && (nev == 4 || nod == 4)) {
+      const int* v = nev == 4 ? ev : od;
+      const size_t off = nev == 4 ? o_aa : o_bb;
+      const int P = nev == 4 ? pe : po;
       const int pairs[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
       for (const auto& q : pairs) {
         const int r1 = pr(v[q[0]], v[q[1]]), r2 = pr(v[q[2]], v[q[3]]);
         rkt[off + (size_t)r1 * P + r2] = code;
         rkt[off + (size_t)r2 * P + r1] = code;
       }
-    } else if (w == 4 && ev.size() == 2) {
+    } else if (w == 4 && nev == 2) {
       for (int s0 = 0; s0 < 2; ++s0)
         for (int s1 = 0; s1 < 2; ++s1)
           rkt[o_ab + (((size_t)ev[s0] * ne + ev[1 - s0]) * no + od[s1]) * no + od[1 - s1]] = code;
@@ -745,32 +756,31 @@ bool build_direct(const std::vector<qf_term>& T, int n, DirectHost* h) {
     if (x == 0) {
       for (size_t k = q0; k < q1; ++k) {
         const qf_term& t = T[order[k]];
-        std::vector<int> zb;
+        int zb[32], nz = 0;  // n <= 32
         for (int q = 0; q < n; ++q)
-          if ((t.z >> q) & 1ull) zb.push_back(q);
-        if (zb.size() > 2) return false;
+          if ((t.z >> q) & 1ull) zb[nz++] = q;
+        if (nz > 2) return false;
         // (-1)^{c_r} = 1 - 2 c_r on occupation bits c_r
         h->dg[0] += t.coeff;
-        for (int r : zb) h->dg[1 + r] -= 2.0 * t.coeff;
-        if (zb.size() == 2) h->dg[1 + n + (size_t)zb[0] * n + zb[1]] += 4.0 * t.coeff;
+        for (int i = 0; i < nz; ++i) h->dg[1 + zb[i]] -= 2.0 * t.coeff;
+        if (nz == 2) h->dg[1 + n + (size_t)zb[0] * n + zb[1]] += 4.0 * t.coeff;
       }
       q0 = q1;
       continue;
     }
-    std::vector<int> sq;
+    int sq[32], ns = 0;  // support qubits (n <= 32)
     for (int q = 0; q < n; ++q)
-      if ((x >> q) & 1ull) sq.push_back(q);
-    if (sq.size() != 2 && sq.size() != 4) return false;
+      if ((x >> q) & 1ull) sq[ns++] = q;
+    if (ns != 2 && ns != 4) return false;
     uint64_t zc = 0;  // the chains
-    for (size_t i = 0; i < sq.size(); i += 2)
+    for (int i = 0; i < ns; i += 2)
       for (int q = sq[i] + 1; q < sq[i + 1]; ++q) zc |= 1ull << q;
     for (size_t k = q0; k < q1; ++k) {
       const uint64_t extra = (T[order[k]].z & ~x) ^ zc;
-      if (extra && (sq.size() == 4 || popc(extra) > 1)) return false;
+      if (extra && (ns == 4 || popc(extra) > 1)) return false;
     }
     // every flip direction: c occupies half the support, as many alpha and beta
     // qubits as it leaves empty
-    const int ns = (int)sq.size();
     for (int m = 0; m < (1 << ns); ++m) {
       uint64_t cd = 0;
       for (int i = 0; i < ns; ++i)
@@ -790,8 +800,11 @@ bool build_direct(const std::vector<qf_term>& T, int n, DirectHost* h) {
         else
           wr[__builtin_ctzll(extra)] += val;
       }
-      std::vector<int> oc, em;  // occupied / empty support qubits of c
-      for (int q : sq) ((cd >> q) & 1ull ? oc : em).push_back(q);
+      int oc[2], em[2], noc = 0, nem = 0;  // occupied / empty support qubits of c (ns / 2 each)
+      for (int i = 0; i < ns; ++i) {
+        if ((cd >> sq[i]) & 1ull) oc[noc++] = sq[i];
+        else em[nem++] = sq[i];
+      }
       if (ns == 2) {
         const bool beta = oc[0] & 1;
         const int lo = oc[0] >> 1, lv = em[0] >> 1, nn = beta ? no : ne;
@@ -804,8 +817,8 @@ bool build_direct(const std::vector<qf_term>& T, int n, DirectHost* h) {
         row[0] += a;
       } else if (xe == 2) {
         int oa = -1, va = -1, ob = -1, vb = -1;
-        for (int q : oc) (q & 1 ? ob : oa) = q >> 1;
-        for (int q : em) (q & 1 ? vb : va) = q >> 1;
+        for (int i = 0; i < noc; ++i) (oc[i] & 1 ? ob : oa) = oc[i] >> 1;
+        for (int i = 0; i < nem; ++i) (em[i] & 1 ? vb : va) = em[i] >> 1;
         h->wab[(((size_t)oa * ne + va) * no + ob) * no + vb] += w0;
       } else {
         const int P = xe == 4 ? pe : po;
