@@ -139,7 +139,7 @@ def test_ucc_energy_c64(workload):
 def test_ucc_general_sparse_path_unknown_sector(dtype):
     """A determinant loaded from the host has no tracked sector, so the dUCC
     blocks run on the general sparse kernels; same state and energy as the oracle."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc16")
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], dtype)
     st.from_numpy(pauli.basis_state(cfg["n_qubits"], det))
@@ -203,7 +203,7 @@ def test_expectation_random_terms_mixed(dtype):
 
 
 def test_energy_grad_ucc_c128_matches_oracle_adjoint():
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], "c128")
     e, grad = st.energy_grad(det, A, t, T)
@@ -222,7 +222,7 @@ def test_energy_grad_ucc_c128_matches_oracle_adjoint():
 def test_energy_grad_repeated_calls_new_angles(dtype):
     """The ansatz structure is planned once per handle; later calls refill the
     composites for new angles.  Each call must match the oracle."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], dtype)
     for k, tt in enumerate((t, 3 * t[::-1].copy(), amplitudes(len(exs), 99, 0.4))):
@@ -242,7 +242,7 @@ def test_energy_grad_repeated_calls_new_angles(dtype):
 def test_energy_grad_ucc_16q_matches_oracle_both_hpsi_modes(mode):
     """16-qubit dUCCSD energy and full gradient with the H|psi> step in FP64 and
     in double-single arithmetic, against the oracle's fermionic adjoint."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc16")
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], "c128")
     st.set_hpsi_mode(qf.QF_HPSI_FP64 if mode == "fp64" else qf.QF_HPSI_DS)
@@ -253,7 +253,7 @@ def test_energy_grad_ucc_16q_matches_oracle_both_hpsi_modes(mode):
 
 
 def test_energy_grad_ucc_16q_fd():
-    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc16")
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], "c128")
     e, grad = st.energy_grad(det, A, t, T)
@@ -274,7 +274,7 @@ def test_energy_grad_same_ansatz_across_sectors(dtype):
     """One handle evaluates one dUCC ansatz from determinants in different
     (alpha, beta) sectors and back: the cached part-local run plan of each
     sector must be rebuilt or reused correctly (oracle: plain Pauli adjoint)."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     n = cfg["n_qubits"]
     hf = (1 << cfg["n_el"]) - 1
     # sectors (2, 2); (3, 2) and (1, 2), where the alpha-alpha doubles touch no
@@ -339,7 +339,7 @@ def test_energy_grad_generic_complex_tiled(n, dtype):
 
 
 def test_energy_grad_c64_relative():
-    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc16")
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], "c64")
     e, grad = st.energy_grad(det, A, t, T)
@@ -436,7 +436,7 @@ def test_residuals_general_path_match_oracle(dtype):
     rng = np.random.default_rng(31)
     T = qf.as_terms(rng.integers(0, 256, 50), rng.integers(0, 256, 50), rng.normal(size=50))
     terms = _terms_list(T)
-    cfg, h, g, Tu, A, exs, t = _ucc_problem(0)
+    cfg, h, g, Tu, A, exs, t = _ucc_problem("ucc8")
     det = (1 << cfg["n_el"]) - 1
     dets = np.arange(256, dtype=np.uint64)
     tol = 1e-10 if dtype == "c128" else 1e-5
@@ -451,7 +451,7 @@ def test_residuals_general_path_match_oracle(dtype):
 
 
 def test_residuals_invalid_determinant_rejected():
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     st = qf.State(cfg["n_qubits"], "c128")
     with pytest.raises(qf.QFError):
         st.residuals(15, A, t, T, np.array([1 << cfg["n_qubits"]], dtype=np.uint64))
@@ -513,7 +513,7 @@ def test_pool_gradients_general_route_match_oracle(dtype):
     with odd-Y terms go through the appended-at-zero route; against the Pauli oracle."""
     n = 8
     rng = np.random.default_rng(41)
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     det = (1 << cfg["n_el"]) - 1
     pool = qf.as_arots(rng.integers(1, 256, 12), rng.integers(0, 256, 12), rng.normal(size=12), rng.integers(0, 5, 12))
     arots = list(zip(A["x"], A["z"], A["coeff"], A["param"]))
@@ -547,7 +547,7 @@ def test_trotter_molecular_hamiltonian_from_reference():
     """The molecular Hamiltonian's evolution of the Hartree-Fock determinant (the
     time-evolved basis states of the quantum Krylov method): against the oracle,
     and the energy is conserved up to the Trotter error."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     n = cfg["n_qubits"]
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(n, "c128")
@@ -562,7 +562,7 @@ def test_trotter_molecular_hamiltonian_from_reference():
 def test_pool_gradients_different_pools_across_clear_plans():
     """Two different pools on one handle, with the plans cleared in between: each
     call must use its own pool's descriptors (oracle: fermionic commutators)."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], "c128")
     doubles = [k for k, ex in enumerate(exs) if len(ex[0]) == 2]
@@ -582,7 +582,7 @@ def test_plan_caches_evict_and_stay_correct():
     eight plans per cache it keeps), then the first pair again: every result
     matches the oracle, and the first pair's result is bit-identical after its
     plans were dropped and rebuilt."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     n, det = cfg["n_qubits"], (1 << cfg["n_el"]) - 1
     rng = np.random.default_rng(77)
     st = qf.State(n, "c128")
@@ -610,7 +610,7 @@ def test_sector_hpsi_chunk_tables_for_non_molecular_terms(dtype):
     three and a double flip with extra Z letters) keeps the chunk-table sector
     H|psi>; the molecular part alone takes the direct tables.  Both against the
     oracle's adjoint gradient."""
-    cfg, h, g, T, A, exs, t = _ucc_problem(0)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc8")
     n, det = cfg["n_qubits"], (1 << cfg["n_el"]) - 1
     extra = qf.as_terms(np.array([0, 0b00110011], dtype=np.uint64), np.array([0b10101, 0b10000000], dtype=np.uint64),
                         np.array([0.11, -0.07]))
@@ -645,7 +645,7 @@ def test_sweep_run_items_count_the_sector_pairs():
     and its virtual orbitals empty (Eq. 19's factors act on exactly these)."""
     from oracle import sector
 
-    cfg, h, g, T, A, exs, t = _ucc_problem(1)
+    cfg, h, g, T, A, exs, t = _ucc_problem("ucc16")
     det = (1 << cfg["n_el"]) - 1
     st = qf.State(cfg["n_qubits"], "c128")
     with pytest.raises(qf.QFError):
