@@ -1,0 +1,243 @@
+// Test double of the CUDA runtime and of the kernel launchers, so that the C
+// ABI's host code (grouping, plan tables, block composites, sweep plans) can run
+// on a machine without a GPU.  Device memory is host memory and no kernel runs;
+// every host-to-device copy and the plain-data arguments of the launchers that
+// take them by value are hashed into one digest, so two runs of the planner can
+// be compared byte for byte.  With QF_STUB_DUMP_DIR set, the sparse composite
+// blocks handed to the forward and adjoint launchers are appended to
+// fwd.bin / adj.bin there, for comparison with the dense products.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "qf_internal.h"
+
+namespace stub {
+std::mutex mu;
+uint64_t digest = 1469598103934665603ull;
+size_t copies = 0, h2d_bytes = 0;
+
+void mix(const void* p, size_t n) {  // FNV-1a over the bytes, folded into the digest
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  std::lock_guard<std::mutex> l(mu);
+  digest ^= h + 0x9e3779b97f4a7c15ull + (digest << 6) + (digest >> 2);
+  ++copies;
+}
+template <typename T> void mixv(const T& v) { mix(&v, sizeof(T)); }
+void reset() {
+  std::lock_guard<std::mutex> l(mu);
+  digest = 1469598103934665603ull;
+  copies = h2d_bytes = 0;
+}
+void dump(const char* file, const qf::SparseArgs& a) {
+  const char* dir = std::getenv("QF_STUB_DUMP_DIR");
+  if (!dir) return;
+  FILE* f = std::fopen((std::string(dir) + "/" + file).c_str(), "ab");
+  if (!f) return;
+  std::fwrite(&a, sizeof(a), 1, f);
+  std::fclose(f);
+}
+void mix_rot(const qf::RotArgs& a) {
+  mixv(a.x), mixv(a.z), mixv(a.h), mixv(a.y), mixv(a.form), mixv(a.A), mixv(a.B);
+}
+}  // namespace stub
+
+extern "C" {
+cudaError_t cudaMalloc(void** p, size_t n) {
+  const size_t m = (n + 255) & ~(size_t)255;
+  *p = std::aligned_alloc(256, m ? m : 256);
+  if (*p && m < ((size_t)1 << 20)) std::memset(*p, 0, m);  // small buffers (flags, partials) are read back
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+cudaError_t cudaFree(void* p) {
+  std::free(p);
+  return cudaSuccess;
+}
+cudaError_t cudaHostAlloc(void** p, size_t n, unsigned int) {
+  *p = std::aligned_alloc(64, (n + 63) & ~(size_t)63);
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+cudaError_t cudaMallocHost(void** p, size_t n) { return cudaHostAlloc(p, n, 0); }
+cudaError_t cudaFreeHost(void* p) {
+  std::free(p);
+  return cudaSuccess;
+}
+cudaError_t cudaGetLastError(void) { return cudaSuccess; }
+const char* cudaGetErrorString(cudaError_t) { return "CUDA stub"; }
+cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t) {
+  if (n < ((size_t)1 << 20)) std::memset(p, v, n);
+  return cudaSuccess;
+}
+cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t n, cudaMemcpyKind k, cudaStream_t) {
+  if (k == cudaMemcpyHostToDevice) {
+    stub::mix(s, n);
+    std::lock_guard<std::mutex> l(stub::mu);
+    stub::h2d_bytes += n;
+  }
+  // large uploads are never read back on the host: skip the copy a DMA engine would make
+  if (k != cudaMemcpyHostToDevice || n < ((size_t)1 << 20)) std::memcpy(d, s, n);
+  return cudaSuccess;
+}
+}  // extern "C"
+
+namespace qf {
+using stub::mixv;
+cudaError_t launch_zero_and_set(void*, int n, qf_dtype, uint64_t det, cudaStream_t) {
+  mixv(n), mixv(det);
+  return cudaSuccess;
+}
+cudaError_t launch_zero_and_set_count(void*, uint64_t count, qf_dtype, uint64_t idx, cudaStream_t) {
+  mixv(count), mixv(idx);
+  return cudaSuccess;
+}
+cudaError_t launch_gather(const void*, qf_dtype, const int64_t*, int count, bool packed, bool ds, double*,
+                          cudaStream_t) {
+  mixv(count), mixv(packed), mixv(ds);
+  return cudaSuccess;
+}
+cudaError_t launch_scale(void*, int n, qf_dtype, double scale, cudaStream_t) {
+  mixv(n), mixv(scale);
+  return cudaSuccess;
+}
+cudaError_t launch_rot(void*, int n, qf_dtype, const RotArgs& a, cudaStream_t) {
+  mixv(n);
+  stub::mix_rot(a);
+  return cudaSuccess;
+}
+cudaError_t launch_tile(void*, int n, qf_dtype, const TileArgs& a, cudaStream_t) {
+  mixv(n), mixv(a.m), mixv(a.s), mixv(a.l), mixv(a.nhi);
+  stub::mix(a.pos, sizeof(int) * a.nhi);
+  stub::mix(a.sbits, sizeof(int) * a.s);
+  for (int i = 0; i < a.m; ++i) {
+    const TileRot& r = a.r[i];
+    mixv(r.xl), mixv(r.zl), mixv(r.zout), mixv(r.hl), mixv(r.y), mixv(r.form), mixv(r.A), mixv(r.B);
+  }
+  return cudaSuccess;
+}
+cudaError_t launch_sparse(void*, int n, qf_dtype, const SparseArgs& a, bool realst, cudaStream_t) {
+  mixv(n), mixv(a), mixv(realst);
+  stub::dump("fwd.bin", a);
+  return cudaSuccess;
+}
+// a block's composite is real when every entry of M has a zero imaginary part
+bool sparse_m_real(const SparseArgs& a) {
+  for (int c = 0; c < a.ncls; ++c)
+    for (int i = 0; i < a.nr; ++i)
+      for (int j = 0; j < a.nr; ++j)
+        if (a.M[c][i][j].y != 0.0) return false;
+  return true;
+}
+bool sparse_q_imag(const SparseArgs& a) {
+  for (int c = 0; c < a.ncls; ++c)
+    for (int i = 0; i < a.nr; ++i)
+      for (int j = 0; j < a.nr; ++j)
+        if (a.Q[c][i][j].x != 0.0) return false;
+  return true;
+}
+cudaError_t launch_expect(const void*, int n, qf_dtype, const ExpGroup*, int ngroups, const ExpChunk*, double*,
+                          unsigned*, double*, int nblocks, cudaStream_t) {
+  mixv(n), mixv(ngroups), mixv(nblocks);
+  return cudaSuccess;
+}
+cudaError_t launch_hpsi(const void*, void*, int n, qf_dtype, const ExpGroup*, int ngroups, const ExpChunk*, double*,
+                        unsigned*, double*, int nblocks, cudaStream_t) {
+  mixv(n), mixv(ngroups), mixv(nblocks);
+  return cudaSuccess;
+}
+cudaError_t launch_hpsi_tiled(const void*, void*, int n, qf_dtype, int tb, bool realst, const HClass*, int nclasses,
+                              const HGroup*, const void*, double*, unsigned*, double*, int nblocks, cudaStream_t) {
+  mixv(n), mixv(tb), mixv(realst), mixv(nclasses), mixv(nblocks);
+  return cudaSuccess;
+}
+cudaError_t launch_hpsi_ds(const void*, void*, void*, int n, const HClass*, int nclasses, const HGroup*,
+                           const WChunkS*, double*, unsigned*, double*, int nblocks, cudaStream_t) {
+  mixv(n), mixv(nclasses), mixv(nblocks);
+  return cudaSuccess;
+}
+cudaError_t launch_adj_rot(void*, void*, int n, qf_dtype, const RotArgs& a, double*, unsigned*, double*, int nblocks,
+                           cudaStream_t) {
+  mixv(n), mixv(nblocks);
+  stub::mix_rot(a);
+  return cudaSuccess;
+}
+cudaError_t launch_adj_sparse(void*, void*, int n, qf_dtype, const SparseArgs& a, bool realst, double*, unsigned*,
+                              double*, int nblocks, cudaStream_t) {
+  mixv(n), mixv(a), mixv(realst), mixv(nblocks);
+  stub::dump("adj.bin", a);
+  return cudaSuccess;
+}
+int sector_sweep_grid(uint64_t) { return 152; }
+cudaError_t launch_sector_sweep(void*, qf_dtype, bool realst, const SecBlk*, int nblk, unsigned*, int grid,
+                                cudaStream_t) {
+  mixv(realst), mixv(nblk), mixv(grid);
+  return cudaSuccess;
+}
+cudaError_t launch_sector_runs(void*, void*, qf_dtype, bool adj, bool realst, const RunInfo* runs, int nruns,
+                               const RunPart*, const RunBlk*, int nblk, double*, int pmax, double*,
+                               const SecCompact& cm, void* log, const uint16_t* strs, const uint32_t* map, bool ds,
+                               bool dss, cudaStream_t) {
+  const bool has_log = log, has_strs = strs, has_map = map;
+  mixv(adj), mixv(realst), mixv(nruns), mixv(nblk), mixv(pmax), mixv(cm.cnt_o);
+  mixv(has_log), mixv(has_strs), mixv(has_map), mixv(ds), mixv(dss);
+  for (int r = 0; r < nruns; ++r) {
+    const RunInfo& R = runs[r];
+    mixv(R.b0), mixv(R.b1), mixv(R.part0), mixv(R.nparts), mixv(R.ua), mixv(R.ub), mixv(R.maxsize);
+    stub::mix(R.apos, R.ua);
+    stub::mix(R.bpos, R.ub);
+  }
+  return cudaSuccess;
+}
+cudaError_t launch_sector_overlaps(void*, qf_dtype, const RunInfo*, int nruns, const RunPart*, const RunBlk*, int nblk,
+                                  double*, int pmax, double*, const SecCompact&, const uint16_t*, cudaStream_t) {
+  mixv(nruns), mixv(nblk), mixv(pmax);
+  return cudaSuccess;
+}
+cudaError_t launch_run_itemmaps(const RunInfo*, int nruns, const RunPart*, const RunBlk*, const SecCompact&,
+                                const uint16_t*, uint32_t*, cudaStream_t) {
+  mixv(nruns);
+  return cudaSuccess;
+}
+// Shared-memory capacity of a part-local run CTA, as on the GB300 (227 KB opt-in).
+uint32_t sector_run_capacity(qf_dtype, bool, bool, bool) { return 18000; }
+cudaError_t launch_sector_hpsi_direct(void*, qf_dtype, const SecSpace& sp, const SecDirect&, const SecCompact&,
+                                      double*, unsigned*, double*, int nblocks, float2*, double*, bool dss,
+                                      cudaStream_t) {
+  mixv(sp.cnt_e), mixv(sp.cnt_o), mixv(sp.ne), mixv(sp.no), mixv(sp.ke), mixv(sp.ko), mixv(nblocks), mixv(dss);
+  return cudaSuccess;
+}
+cudaError_t launch_sector_hpsi(const void*, void*, qf_dtype, bool realst, const SecSpace& sp, const SecRank&,
+                               const SecGroup*, int nlarge, const ExpChunk*, double*, unsigned*, double*,
+                               int nblocks, const SecCompact&, cudaStream_t) {
+  mixv(realst), mixv(sp.cnt_e), mixv(sp.cnt_o), mixv(nlarge), mixv(nblocks);
+  return cudaSuccess;
+}
+// A request's sector state in shared memory: psi and lambda plus the block tables.
+size_t small_eval_smem(qf_dtype dt, uint32_t members, int, int) {
+  return (size_t)members * (dt == QF_C128 ? 32 : 16) + 4096;
+}
+cudaError_t launch_small_eval(const SmallEval& a, qf_dtype, int n_req, cudaStream_t) {
+  mixv(a.nblk), mixv(a.cnt_e), mixv(a.cnt_o), mixv(a.ke), mixv(a.ko), mixv(a.c0), mixv(n_req);
+  return cudaSuccess;
+}
+cudaError_t launch_wait_selftest(unsigned*, double, cudaStream_t) { return cudaSuccess; }
+// Reduction grid as the device code sizes it: one block per 512 amplitudes, at most four per SM of 152.
+int reduce_blocks(int n, qf_dtype) {
+  const uint64_t g = ((1ull << n) / 2 + 255) / 256;
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(g, 4 * 152));
+}
+int prof_pre(unsigned, cudaStream_t) { return -1; }
+void prof_post(int, cudaStream_t) {}
+void count_launch() {}
+int profile_begin(unsigned) { return 0; }
+cudaError_t profile_read(unsigned, uint64_t*, double*) { return cudaSuccess; }
+void profile_end() {}
+}  // namespace qf

@@ -1,0 +1,138 @@
+// Runs the C ABI's calls on the CUDA test double (cuda_stub.cpp) and prints, per
+// call, its status and the digest of everything it would have sent to the
+// device.  Inputs are raw arrays written by tests/test_hostplan_cpu.py:
+//   plan_suite <dir>          every case, one line each
+//   plan_suite <dir> layout   sizeof and field offsets of qf::SparseArgs
+#include <cstddef>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "qf.h"
+#include "qf_internal.h"
+
+namespace stub {
+extern uint64_t digest;
+extern size_t copies, h2d_bytes;
+void reset();
+}  // namespace stub
+
+static std::string g_dir;
+
+template <typename T>
+static std::vector<T> load(const char* name) {
+  const std::string path = g_dir + "/" + name;
+  FILE* f = std::fopen(path.c_str(), "rb");
+  if (!f) {
+    std::fprintf(stderr, "missing input %s\n", path.c_str());
+    std::exit(2);
+  }
+  std::fseek(f, 0, SEEK_END);
+  const long n = std::ftell(f);
+  std::fseek(f, 0, SEEK_SET);
+  std::vector<T> v((size_t)n / sizeof(T));
+  if (std::fread(v.data(), sizeof(T), v.size(), f) != v.size()) std::exit(2);
+  std::fclose(f);
+  return v;
+}
+
+static void report(const std::string& name, qf_status s) {
+  std::printf("%s %d %zu %zu %016llx\n", name.c_str(), (int)s, stub::copies, stub::h2d_bytes,
+              (unsigned long long)stub::digest);
+  if (s != QF_OK) std::printf("#error %s: %s\n", name.c_str(), qf_last_error());
+  stub::reset();
+}
+
+static qf_state* make(int n, qf_dtype dt) {
+  qf_state* st = nullptr;
+  if (qf_state_create(n, dt, nullptr, nullptr, 0, &st) != QF_OK) {
+    std::printf("#error create: %s\n", qf_last_error());
+    std::exit(3);
+  }
+  return st;
+}
+
+int main(int argc, char** argv) {
+  if (argc < 2) return 1;
+  g_dir = argv[1];
+  if (argc > 2 && std::string(argv[2]) == "layout") {
+    using qf::SparseArgs;
+    std::printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d %d %d\n", sizeof(SparseArgs), offsetof(SparseArgs, u),
+                offsetof(SparseArgs, nr), offsetof(SparseArgs, ncls), offsetof(SparseArgs, nzc),
+                offsetof(SparseArgs, supp), offsetof(SparseArgs, pat), offsetof(SparseArgs, zc),
+                offsetof(SparseArgs, M), offsetof(SparseArgs, Q), qf::kSparseMaxSupp, qf::kSparseMaxRows,
+                qf::kSparseMaxCls);
+    return 0;
+  }
+  const auto T16 = load<qf_term>("terms16.bin");
+  const auto A16 = load<qf_arot>("ansatz16.bin");
+  auto t16 = load<double>("t16.bin");
+  const auto R16 = load<qf_rot>("rot16.bin");
+  const auto P16 = load<qf_arot>("pool16.bin");
+  const auto D16 = load<uint64_t>("dets16.bin");
+  const auto A10 = load<qf_arot>("ansatz10.bin");
+  const auto t10 = load<double>("t10.bin");
+  const auto T10 = load<qf_term>("terms10.bin");
+  const auto R10 = load<qf_rot>("rot10.bin");
+  const auto H10 = load<qf_term>("ham10.bin");
+  const auto A8 = load<qf_arot>("ansatz8.bin");
+  const auto t8 = load<double>("t8.bin");
+  const auto T8 = load<qf_term>("terms8.bin");
+  const std::string only = argc > 2 ? argv[2] : "";
+  std::vector<double> g(4096), r(4096), gp(4096), es(16);
+  double e = 0, re = 0, im = 0;
+  stub::reset();
+  if (only.empty() || only == "sector16") {
+    qf_state* st = make(16, QF_C128);
+    report("energy_grad.16q.cold", qf_energy_grad(st, 255, A16.data(), A16.size(), t16.data(), t16.size(),
+                                                  T16.data(), T16.size(), &e, g.data()));
+    // the first call also sets up the handle (compact layout, tables kept across plans);
+    // from then on every rebuilt plan must send the device the same bytes
+    for (const char* name : {"energy_grad.16q.rebuilt", "energy_grad.16q.rebuilt_again"}) {
+      qf_state_clear_plans(st);
+      stub::reset();
+      report(name, qf_energy_grad(st, 255, A16.data(), A16.size(), t16.data(), t16.size(), T16.data(), T16.size(),
+                                  &e, g.data()));
+    }
+    t16[0] += 0.01;
+    report("energy_grad.16q.warm", qf_energy_grad(st, 255, A16.data(), A16.size(), t16.data(), t16.size(),
+                                                  T16.data(), T16.size(), &e, g.data()));
+    t16[0] -= 0.01;
+    report("pool_gradients.16q", qf_pool_gradients(st, 255, A16.data(), A16.size(), t16.data(), t16.size(),
+                                                   T16.data(), T16.size(), P16.data(), P16.size(), t16.size(), &e,
+                                                   gp.data()));
+    report("residuals.16q", qf_residuals(st, 255, A16.data(), A16.size(), t16.data(), t16.size(), T16.data(),
+                                         T16.size(), D16.data(), D16.size(), &e, g.data(), r.data()));
+    qf_set_basis(st, 255);
+    stub::reset();
+    report("apply_circuit.16q.ucc", qf_apply_circuit(st, R16.data(), R16.size()));
+    report("expectation.16q", qf_expectation(st, T16.data(), T16.size(), &re, &im));
+    qf_state_destroy(st);
+  }
+  if (only.empty() || only == "general10") {
+    qf_state* st = make(10, QF_C128);
+    report("energy_grad.10q.general", qf_energy_grad(st, 31, A10.data(), A10.size(), t10.data(), t10.size(),
+                                                     T10.data(), T10.size(), &e, g.data()));
+    qf_state_destroy(st);
+  }
+  if (only.empty()) {
+    for (int d = 0; d < 2; ++d) {
+      const qf_dtype dt = d ? QF_C64 : QF_C128;
+      const std::string sfx = d ? ".c64" : ".c128";
+      qf_state* st = make(10, dt);
+      qf_set_basis(st, 0x155);
+      stub::reset();
+      report("apply_circuit.10q.random" + sfx, qf_apply_circuit(st, R10.data(), R10.size()));
+      report("expectation.10q.random" + sfx, qf_expectation(st, H10.data(), H10.size(), &re, &im));
+      report("trotter.10q.random" + sfx, qf_trotter(st, H10.data(), H10.size(), 0.25, 2));
+      qf_state_destroy(st);
+      st = make(8, dt);
+      report("energy_grad_multi.8q" + sfx,
+             qf_energy_grad_multi(st, 15, A8.data(), A8.size(), t8.data(), t8.size() / 4, 4, T8.data(), T8.size(),
+                                  es.data(), g.data()));
+      qf_state_destroy(st);
+    }
+  }
+  return 0;
+}

@@ -1,0 +1,185 @@
+"""The C ABI's host planning, run without a GPU.
+
+qf_api.cu is compiled with g++ against a test double of the CUDA runtime and of
+the kernel launchers (tests/hostplan/cuda_stub.cpp): device memory is host
+memory, no kernel runs, and everything a call would send to the device (uploads
+and the plain-data launch arguments) is hashed.  This covers the planner -- X-mask
+grouping and its tables, the direct sector tables, block composites, the
+part-local run plan, grouped small requests -- on every ABI path, and checks:
+  * every path plans without error;
+  * plans are deterministic, and every plan rebuilt after qf_state_clear_plans
+    sends the device the same bytes;
+  * a call with new angles on a kept plan uploads only the new composites;
+  * each fused block's composite (Eq. 19's excitation factors, applied as one
+    2^u x 2^u block on its active rows) and generator equal the dense products
+    of its rotations computed by the oracle.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HERE = os.path.join(ROOT, "tests", "hostplan")
+CUDA_INC = "/usr/local/cuda/include"
+
+
+def _have_toolchain():
+    return shutil.which("g++") is not None and os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h"))
+
+
+@pytest.fixture(scope="module")
+def suite(tmp_path_factory):
+    if not _have_toolchain():
+        pytest.skip("needs g++ and the CUDA headers")
+    d = tmp_path_factory.mktemp("hostplan")
+    exe = str(d / "plan_suite")
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_2108_04413_gb300", "csrc"),
+           "-I", CUDA_INC]
+    cmd = (["g++", "-O1", "-std=c++17", "-w"] + inc +
+           ["-x", "c++", os.path.join(ROOT, "paper_2108_04413_gb300", "csrc", "qf_api.cu"), "-x", "none",
+            os.path.join(HERE, "cuda_stub.cpp"), os.path.join(HERE, "plan_suite.cpp"), "-o", exe, "-lpthread"])
+    subprocess.run(cmd, check=True, capture_output=True, timeout=600)
+    _write_inputs(str(d))
+    return exe, str(d)
+
+
+def _write_inputs(d):
+    from paper_2108_04413_gb300 import prep
+    from paper_2108_04413_gb300.abi import AROT_DTYPE
+    from workloads import amplitudes, integrals
+
+    def save(name, a):
+        np.ascontiguousarray(a).tofile(os.path.join(d, name))
+
+    # 16 qubits, half filling: the compact sector path
+    h, g = integrals(8, 1)
+    T16 = prep.molecular_hamiltonian(h, g)
+    A16, ex16 = prep.uccsd_ansatz(8, 8)
+    t16 = amplitudes(len(ex16), 1, 0.1)
+    pool = A16.copy()
+    pool["param"] = len(ex16) - 1 - A16["param"]
+    idx, _ = prep.excited_determinants(ex16, 255)
+    save("terms16.bin", T16), save("ansatz16.bin", A16), save("t16.bin", np.asarray(t16, np.float64))
+    save("rot16.bin", prep.bind_thetas(A16, t16)), save("pool16.bin", pool)
+    save("dets16.bin", np.asarray(idx, np.uint64))
+    # 10 qubits: a particle-number-changing rotation first, so the dUCCSD factors
+    # that follow run as general sparse blocks (their composites are checked)
+    h, g = integrals(5, 3)
+    A, ex10 = prep.uccsd_ansatz(5, 5)
+    A10 = np.zeros(len(A) + 1, dtype=AROT_DTYPE)
+    A10[0] = (1, 0, 1.0, 0, 0)
+    A10[1:] = A
+    A10["param"][1:] += 1
+    save("ansatz10.bin", A10), save("t10.bin", amplitudes(len(ex10) + 1, 5, 0.2))
+    save("terms10.bin", prep.molecular_hamiltonian(h, g))
+    save("rot10.bin", prep.random_circuit(10, 200, 7)), save("ham10.bin", prep.random_hamiltonian(10, 300, 9))
+    # 8 qubits, four parameter vectors in one grouped call
+    h, g = integrals(4, 0)
+    A8, ex8 = prep.uccsd_ansatz(4, 4)
+    save("ansatz8.bin", A8), save("terms8.bin", prep.molecular_hamiltonian(h, g))
+    save("t8.bin", np.stack([amplitudes(len(ex8), 20 + k, 0.15) for k in range(4)]).astype(np.float64))
+
+
+def _run(suite, *args, env=None):
+    exe, d = suite
+    out = subprocess.run([exe, d, *args], check=True, capture_output=True, text=True, timeout=600,
+                         env=dict(os.environ, **(env or {}))).stdout
+    assert "#error" not in out, out
+    rows = {}
+    for line in out.splitlines():
+        name, status, copies, h2d, digest = line.split()
+        rows[name] = (int(status), int(copies), int(h2d), digest)
+    return rows
+
+
+def test_every_abi_path_plans_on_the_host(suite):
+    rows = _run(suite)
+    assert len(rows) == 17
+    for name, (status, copies, _, _) in rows.items():
+        assert status == 0, name
+        assert copies > 0, name
+    assert rows["energy_grad.16q.cold"][2] > 0 and rows["energy_grad.10q.general"][2] > 0
+
+
+def test_plans_are_deterministic_and_rebuilt_identically(suite):
+    a, b = _run(suite), _run(suite)
+    assert a == b
+    assert a["energy_grad.16q.rebuilt"] == a["energy_grad.16q.rebuilt_again"]
+
+
+def test_new_angles_upload_only_the_composites(suite):
+    rows = _run(suite, "sector16")
+    cold, warm = rows["energy_grad.16q.rebuilt_again"], rows["energy_grad.16q.warm"]
+    assert 0 < warm[2] < cold[2] / 2
+    assert warm[3] != cold[3]
+
+
+def _sparse_args(raw, layout):
+    size, o_u, o_nr, o_ncls, o_nzc, o_supp, o_pat, o_zc, o_m, o_q, max_supp, max_rows, max_cls = layout
+    assert len(raw) % size == 0
+    out = []
+    for k in range(len(raw) // size):
+        b = raw[k * size:(k + 1) * size]
+        i32 = lambda off, cnt=1: np.frombuffer(b, np.int32, cnt, off)  # noqa: E731
+        u, nr, ncls, nzc = (int(i32(o)[0]) for o in (o_u, o_nr, o_ncls, o_nzc))
+        cmat = np.frombuffer(b, np.float64, 2 * max_cls * max_rows * max_rows, o_m).view(np.complex128)
+        qmat = np.frombuffer(b, np.float64, 2 * max_cls * max_rows * max_rows, o_q).view(np.complex128)
+        out.append(dict(u=u, nr=nr, ncls=ncls, nzc=nzc, supp=i32(o_supp, u).tolist(),
+                        pat=np.frombuffer(b, np.uint64, nr, o_pat).tolist(),
+                        zc=np.frombuffer(b, np.uint64, nzc, o_zc).tolist(),
+                        M=cmat.reshape(max_cls, max_rows, max_rows)[:ncls, :nr, :nr],
+                        Q=qmat.reshape(max_cls, max_rows, max_rows)[:ncls, :nr, :nr]))
+    return out
+
+
+def test_sparse_composites_match_dense_products(suite, tmp_path):
+    """Every fused dUCCSD factor of the general path: M + I on the active rows is
+    the product of the factor's rotations (adjoint sweep: its inverse), and Q is
+    sum_k coeff_k P_k, for every sign class of the Z strings outside the support;
+    rows outside the active set are left unchanged."""
+    from oracle import pauli
+
+    exe, d = suite
+    layout = [int(v) for v in subprocess.run([exe, d, "layout"], check=True, capture_output=True,
+                                             text=True).stdout.split()]
+    _run(suite, "general10", env={"QF_STUB_DUMP_DIR": str(tmp_path)})
+    n = 10
+    A = np.fromfile(os.path.join(d, "ansatz10.bin"), dtype=__import__(
+        "paper_2108_04413_gb300.abi", fromlist=["AROT_DTYPE"]).AROT_DTYPE)
+    t = np.fromfile(os.path.join(d, "t10.bin"), dtype=np.float64)
+    runs = {}
+    for x, z, c, p in zip(A["x"].tolist(), A["z"].tolist(), A["coeff"].tolist(), A["param"].tolist()):
+        runs.setdefault(int(x), []).append((int(z), float(c), int(p)))
+    fwd = _sparse_args((tmp_path / "fwd.bin").read_bytes(), layout)
+    adj = _sparse_args((tmp_path / "adj.bin").read_bytes(), layout)
+    assert len(fwd) == len(runs) - 1 == len(adj)  # every factor but the single X rotation
+    assert {a["ncls"] for a in fwd} == {1, 2}  # factors with and without Z strings outside the support
+    for blocks, inverse in ((fwd, False), (adj, True)):
+        for a in blocks:
+            x = sum(1 << q for q in a["supp"])
+            rots = [(x, z, c * t[p]) for z, c, p in runs[x]]
+            assert 0 <= a["nzc"] <= 2 and a["ncls"] == 1 << a["nzc"]
+            for cls in range(a["ncls"]):
+                # a basis state off the support whose outside-Z parities give this class
+                b0 = next(b for b in range(1 << n) if not (b & x) and all(
+                    (bin(zc & b).count("1") & 1) == ((cls >> j) & 1) for j, zc in enumerate(a["zc"])))
+                rows = [b0 ^ p for p in a["pat"]]
+                for j, rj in enumerate(rows):
+                    col = pauli.apply_rotations(pauli.basis_state(n, rj), n, rots)
+                    gen = sum(c * pauli.apply(pauli.basis_state(n, rj), n, x, z) for z, c, _ in runs[x])
+                    assert abs(np.linalg.norm(col[rows]) - 1.0) < 1e-13  # no amplitude leaves the active rows
+                    for i, ri in enumerate(rows):
+                        u = np.conj(pauli.apply_rotations(pauli.basis_state(n, ri), n, rots)[rj]) if inverse \
+                            else col[ri]
+                        assert abs(a["M"][cls, i, j] + (i == j) - u) < 1e-13
+                        assert abs(a["Q"][cls, i, j] - gen[ri]) < 1e-13
+                # a support pattern outside the active set is left unchanged
+                rest = [r for r in range(1 << a["u"]) if sum(((r >> k) & 1) << q for k, q in
+                                                             enumerate(a["supp"])) not in a["pat"]]
+                if rest:
+                    r0 = b0 ^ sum(((rest[0] >> k) & 1) << q for k, q in enumerate(a["supp"]))
+                    col = pauli.apply_rotations(pauli.basis_state(n, r0), n, rots)
+                    assert abs(col[r0] - 1.0) < 1e-13
