@@ -3,6 +3,8 @@
 // device.  Inputs are raw arrays written by tests/test_hostplan_cpu.py:
 //   plan_suite <dir>          every case, one line each
 //   plan_suite <dir> layout   sizeof and field offsets of qf::SparseArgs
+//   plan_suite <dir> runitems <n> <det>   the part-local sweep's items per run for
+//                             terms_ri.bin / ansatz_ri.bin / t_ri.bin
 #include <cstddef>
 #include <cstdio>
 #include <cstdlib>
@@ -63,6 +65,27 @@ int main(int argc, char** argv) {
                 offsetof(SparseArgs, supp), offsetof(SparseArgs, pat), offsetof(SparseArgs, zc),
                 offsetof(SparseArgs, M), offsetof(SparseArgs, Q), qf::kSparseMaxSupp, qf::kSparseMaxRows,
                 qf::kSparseMaxCls);
+    return 0;
+  }
+  if (argc > 4 && std::string(argv[2]) == "runitems") {
+    const auto T = load<qf_term>("terms_ri.bin");
+    const auto A = load<qf_arot>("ansatz_ri.bin");
+    const auto t = load<double>("t_ri.bin");
+    qf_state* st = make(std::atoi(argv[3]), QF_C128);
+    std::vector<double> grad(t.size());
+    double energy = 0;
+    const qf_status s = qf_energy_grad(st, std::strtoull(argv[4], nullptr, 0), A.data(), A.size(), t.data(),
+                                       t.size(), T.data(), T.size(), &energy, grad.data());
+    if (s != QF_OK) {
+      std::printf("#error runitems: %s\n", qf_last_error());
+      return 4;
+    }
+    size_t nr = 0;
+    qf_sweep_run_items(st, nullptr, 0, &nr);
+    std::vector<uint64_t> items(nr);
+    qf_sweep_run_items(st, items.data(), nr, &nr);
+    for (uint64_t v : items) std::printf("%llu\n", (unsigned long long)v);
+    qf_state_destroy(st);
     return 0;
   }
   const auto T16 = load<qf_term>("terms16.bin");

@@ -10,6 +10,8 @@ part-local run plan, grouped small requests -- on every ABI path, and checks:
   * plans are deterministic, and every plan rebuilt after qf_state_clear_plans
     sends the device the same bytes;
   * a call with new angles on a kept plan uploads only the new composites;
+  * the part-local sweep plan of the 24-qubit dUCCSD evaluation moves exactly
+    one item per (sector determinant, excitation) pair the excitation acts on;
   * each fused block's composite (Eq. 19's excitation factors, applied as one
     2^u x 2^u block on its active rows) and generator equal the dense products
     of its rotations computed by the oracle.
@@ -183,3 +185,35 @@ def test_sparse_composites_match_dense_products(suite, tmp_path):
                     r0 = b0 ^ sum(((rest[0] >> k) & 1) << q for k, q in enumerate(a["supp"]))
                     col = pauli.apply_rotations(pauli.basis_state(n, r0), n, rots)
                     assert abs(col[r0] - 1.0) < 1e-13
+
+
+def test_sweep_plan_items_at_24_qubits_count_the_sector_pairs(suite):
+    """The 24-qubit dUCCSD evaluation's run plan: its per-run items (the units the
+    sweeps' flops and log traffic are counted in) add up to the brute-force count
+    of (sector determinant, excitation) pairs with the excitation's occupied
+    orbitals filled and its virtual orbitals empty."""
+    from oracle import sector
+    from paper_2108_04413_gb300 import prep
+    from workloads import WORKLOADS, amplitudes, integrals
+
+    exe, d = suite
+    cfg = WORKLOADS["ucc24"]
+    h, g = integrals(cfg["n_orb"], cfg["seed"])
+    A, exs = prep.uccsd_ansatz(cfg["n_orb"], cfg["n_el"])
+    prep.molecular_hamiltonian(h, g).tofile(os.path.join(d, "terms_ri.bin"))
+    A.tofile(os.path.join(d, "ansatz_ri.bin"))
+    amplitudes(len(exs), cfg["seed"], cfg["t_sigma"]).astype(np.float64).tofile(os.path.join(d, "t_ri.bin"))
+    det = (1 << cfg["n_el"]) - 1
+    out = subprocess.run([exe, d, "runitems", str(cfg["n_qubits"]), str(det)], check=True, capture_output=True,
+                         text=True, timeout=600).stdout
+    items = np.array([int(v) for v in out.split()], dtype=np.int64)
+    na, nb = sector.counts_of(det)
+    dets = sector.sector_dets(cfg["n_orb"], na, nb)
+    expect = 0
+    for occ, vir in exs:
+        om = np.uint64(sum(1 << q for q in occ))
+        vm = np.uint64(sum(1 << q for q in vir))
+        expect += int(np.count_nonzero(((dets & om) == om) & ((dets & vm) == 0)))
+    assert len(exs) == 1818 and len(dets) == 853776
+    assert len(items) > 1 and (items > 0).all()
+    assert int(items.sum()) == expect == 128172240
