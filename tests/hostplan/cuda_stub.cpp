@@ -5,7 +5,9 @@
 // take them by value are hashed into one digest, so two runs of the planner can
 // be compared byte for byte.  With QF_STUB_DUMP_DIR set, the sparse composite
 // blocks handed to the forward and adjoint launchers are appended to
-// fwd.bin / adj.bin there, for comparison with the dense products.
+// fwd.bin / adj.bin there, and the X-mask groups and tables handed to the gather
+// H|psi> kernel are written to groups.bin / hchunks.bin, for comparison with the
+// plain definitions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +46,17 @@ void dump(const char* file, const qf::SparseArgs& a) {
   if (!f) return;
   std::fwrite(&a, sizeof(a), 1, f);
   std::fclose(f);
+}
+// the X-mask groups and their sign-pattern tables handed to the gather H|psi> kernel
+void dump_tables(const qf::ExpGroup* g, int ng, const qf::ExpChunk* c) {
+  const char* dir = std::getenv("QF_STUB_DUMP_DIR");
+  if (!dir) return;
+  int nc = 0;
+  for (int i = 0; i < ng; ++i) nc = std::max(nc, g[i].chunk0 + g[i].nchunk);
+  FILE* f = std::fopen((std::string(dir) + "/groups.bin").c_str(), "wb");
+  if (f) std::fwrite(g, sizeof(*g), ng, f), std::fclose(f);
+  f = std::fopen((std::string(dir) + "/hchunks.bin").c_str(), "wb");
+  if (f) std::fwrite(c, sizeof(*c), nc, f), std::fclose(f);
 }
 void mix_rot(const qf::RotArgs& a) {
   mixv(a.x), mixv(a.z), mixv(a.h), mixv(a.y), mixv(a.form), mixv(a.A), mixv(a.B);
@@ -148,9 +161,10 @@ cudaError_t launch_expect(const void*, int n, qf_dtype, const ExpGroup*, int ngr
   mixv(n), mixv(ngroups), mixv(nblocks);
   return cudaSuccess;
 }
-cudaError_t launch_hpsi(const void*, void*, int n, qf_dtype, const ExpGroup*, int ngroups, const ExpChunk*, double*,
-                        unsigned*, double*, int nblocks, cudaStream_t) {
+cudaError_t launch_hpsi(const void*, void*, int n, qf_dtype, const ExpGroup* groups, int ngroups,
+                        const ExpChunk* chunks, double*, unsigned*, double*, int nblocks, cudaStream_t) {
   mixv(n), mixv(ngroups), mixv(nblocks);
+  stub::dump_tables(groups, ngroups, chunks);
   return cudaSuccess;
 }
 cudaError_t launch_hpsi_tiled(const void*, void*, int n, qf_dtype, int tb, bool realst, const HClass*, int nclasses,

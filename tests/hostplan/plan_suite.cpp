@@ -3,6 +3,7 @@
 // device.  Inputs are raw arrays written by tests/test_hostplan_cpu.py:
 //   plan_suite <dir>          every case, one line each
 //   plan_suite <dir> layout   sizeof and field offsets of qf::SparseArgs
+//   plan_suite <dir> tables   the same for qf::ExpGroup and qf::ExpChunk
 //   plan_suite <dir> runitems <n> <det>   the part-local sweep's items per run for
 //                             terms_ri.bin / ansatz_ri.bin / t_ri.bin
 #include <cstddef>
@@ -65,6 +66,14 @@ int main(int argc, char** argv) {
                 offsetof(SparseArgs, supp), offsetof(SparseArgs, pat), offsetof(SparseArgs, zc),
                 offsetof(SparseArgs, M), offsetof(SparseArgs, Q), qf::kSparseMaxSupp, qf::kSparseMaxRows,
                 qf::kSparseMaxCls);
+    return 0;
+  }
+  if (argc > 2 && std::string(argv[2]) == "tables") {
+    using qf::ExpChunk;
+    using qf::ExpGroup;
+    std::printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(ExpGroup), offsetof(ExpGroup, x),
+                offsetof(ExpGroup, nchunk), offsetof(ExpGroup, chunk0), sizeof(ExpChunk), offsetof(ExpChunk, z),
+                offsetof(ExpChunk, tab), offsetof(ExpChunk, ftab), (size_t)(1 << qf::kChunkTerms), qf::kChunkTerms);
     return 0;
   }
   if (argc > 4 && std::string(argv[2]) == "runitems") {
@@ -131,6 +140,15 @@ int main(int argc, char** argv) {
     stub::reset();
     report("apply_circuit.16q.ucc", qf_apply_circuit(st, R16.data(), R16.size()));
     report("expectation.16q", qf_expectation(st, T16.data(), T16.size(), &re, &im));
+    qf_state_destroy(st);
+  }
+  if (only == "hpsi8") {  // a generic ansatz on 8 qubits: the gather H|psi> kernel and its tables
+    const auto A = load<qf_arot>("ansatz_h8.bin");
+    const auto t = load<double>("t_h8.bin");
+    const auto H = load<qf_term>("ham8.bin");
+    qf_state* st = make(8, QF_C128);
+    report("energy_grad.8q.generic", qf_energy_grad(st, 0x35, A.data(), A.size(), t.data(), t.size(), H.data(),
+                                                    H.size(), &e, g.data()));
     qf_state_destroy(st);
   }
   if (only.empty() || only == "general10") {

@@ -14,7 +14,9 @@ part-local run plan, grouped small requests -- on every ABI path, and checks:
     one item per (sector determinant, excitation) pair the excitation acts on;
   * each fused block's composite (Eq. 19's excitation factors, applied as one
     2^u x 2^u block on its active rows) and generator equal the dense products
-    of its rotations computed by the oracle.
+    of its rotations computed by the oracle;
+  * the X-mask groups' sign-pattern tables reproduce the oracle's Hamiltonian
+    matrix elements.
 """
 import os
 import shutil
@@ -217,3 +219,49 @@ def test_sweep_plan_items_at_24_qubits_count_the_sector_pairs(suite):
     assert len(exs) == 1818 and len(dets) == 853776
     assert len(items) > 1 and (items > 0).all()
     assert int(items.sum()) == expect == 128172240
+
+
+def test_xmask_group_tables_reproduce_the_hamiltonian(suite, tmp_path):
+    """The X-mask grouping (Eq. 18 evaluated group by group): for every group x and
+    every basis state b, the group's chunk tables read at b's sign patterns sum to
+    <b XOR x| H |b>.  The Hamiltonian mixes a group whose Z masks span three
+    dimensions (one chunk of combinations), a group spanning more than four (chunks
+    of four terms), the diagonal group, odd-Y terms and repeated terms."""
+    from oracle import pauli
+    from paper_2108_04413_gb300.abi import as_arots, as_terms
+
+    exe, d = suite
+    n = 8
+    rng = np.random.default_rng(18)
+    basis = rng.integers(0, 1 << n, 3)
+    span = [int(np.bitwise_xor.reduce(basis[[k for k in range(3) if (m >> k) & 1]], initial=0)) for m in range(8)]
+    xs = [0b00110101] * 12 + [0b11000011] * 10 + [0] * 15 + list(rng.integers(0, 1 << n, 150))
+    zs = [span[rng.integers(0, 8)] for _ in range(12)] + list(rng.integers(0, 1 << n, 10 + 15 + 150))
+    zs[40], xs[40] = zs[41], xs[41]  # a repeated term
+    T = as_terms(np.array(xs), np.array(zs), rng.normal(size=len(xs)))
+    A = as_arots(rng.integers(0, 1 << n, 30), rng.integers(0, 1 << n, 30), rng.normal(size=30), rng.integers(0, 6, 30))
+    T.tofile(os.path.join(d, "ham8.bin"))
+    A.tofile(os.path.join(d, "ansatz_h8.bin"))
+    rng.normal(size=6).tofile(os.path.join(d, "t_h8.bin"))
+    _run(suite, "hpsi8", env={"QF_STUB_DUMP_DIR": str(tmp_path)})
+    gsize, o_x, o_nchunk, o_chunk0, csize, o_z, o_tab, _, npat, kterms = (
+        int(v) for v in subprocess.run([exe, d, "tables"], check=True, capture_output=True, text=True).stdout.split())
+    graw, craw = (tmp_path / "groups.bin").read_bytes(), (tmp_path / "hchunks.bin").read_bytes()
+    H = pauli.dense_sum(n, [(int(x), int(z), float(c)) for x, z, c in zip(T["x"], T["z"], T["coeff"])])
+    seen = set()
+    b = np.arange(1 << n, dtype=np.uint64)
+    for k in range(len(graw) // gsize):
+        g = graw[k * gsize:(k + 1) * gsize]
+        x = int(np.frombuffer(g, np.uint64, 1, o_x)[0])
+        nchunk, chunk0 = (int(np.frombuffer(g, np.int32, 1, o)[0]) for o in (o_nchunk, o_chunk0))
+        seen.add(x)
+        D = np.zeros(1 << n, dtype=complex)
+        for c in range(chunk0, chunk0 + nchunk):
+            ch = craw[c * csize:(c + 1) * csize]
+            z = np.frombuffer(ch, np.uint64, kterms, o_z)
+            tab = np.frombuffer(ch, np.float64, 2 * npat, o_tab).view(np.complex128)
+            pat = sum(((pauli.popcount(z[j] & b) & 1).astype(np.int64) << j) for j in range(kterms))
+            D += tab[pat]
+        np.testing.assert_allclose(D, H[b.astype(np.int64) ^ x, b.astype(np.int64)], rtol=0, atol=1e-13)
+    assert seen == {int(v) for v in T["x"]}
+    assert len(seen) == len(graw) // gsize
