@@ -6,8 +6,8 @@
 // be compared byte for byte.  With QF_STUB_DUMP_DIR set, the sparse composite
 // blocks handed to the forward and adjoint launchers are appended to
 // fwd.bin / adj.bin there, and the X-mask groups and tables handed to the gather
-// H|psi> kernel are written to groups.bin / hchunks.bin, for comparison with the
-// plain definitions.
+// H|psi> kernel are written to groups.bin / hchunks.bin and the direct sector
+// tables to direct.bin, for comparison with the plain definitions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,6 +57,26 @@ void dump_tables(const qf::ExpGroup* g, int ng, const qf::ExpChunk* c) {
   if (f) std::fwrite(g, sizeof(*g), ng, f), std::fclose(f);
   f = std::fopen((std::string(dir) + "/hchunks.bin").c_str(), "wb");
   if (f) std::fwrite(c, sizeof(*c), nc, f), std::fclose(f);
+}
+// the direct sector tables of H: n, ne, no, inv_fix, then wab, waa, wbb (FP64) and
+// s1a, s1b, dg (fixed point), each at its full size
+void dump_direct(const qf::SecDirect& d) {
+  const char* dir = std::getenv("QF_STUB_DUMP_DIR");
+  if (!dir) return;
+  FILE* f = std::fopen((std::string(dir) + "/direct.bin").c_str(), "wb");
+  if (!f) return;
+  const int n = d.n, ne = d.ne, no = d.no;
+  const size_t pe = (size_t)ne * (ne - 1) / 2, po = (size_t)no * (no - 1) / 2;
+  const int32_t head[4] = {n, ne, no, 0};
+  std::fwrite(head, sizeof(head), 1, f);
+  std::fwrite(&d.inv_fix, sizeof(double), 1, f);
+  std::fwrite(d.wab, sizeof(double), (size_t)ne * ne * no * no, f);
+  std::fwrite(d.waa, sizeof(double), std::max<size_t>(1, pe * pe), f);
+  std::fwrite(d.wbb, sizeof(double), std::max<size_t>(1, po * po), f);
+  std::fwrite(d.s1a, sizeof(long long), (size_t)ne * ne * (n + 1), f);
+  std::fwrite(d.s1b, sizeof(long long), (size_t)no * no * (n + 1), f);
+  std::fwrite(d.dg, sizeof(long long), (size_t)1 + n + (size_t)n * n, f);
+  std::fclose(f);
 }
 void mix_rot(const qf::RotArgs& a) {
   mixv(a.x), mixv(a.z), mixv(a.h), mixv(a.y), mixv(a.form), mixv(a.A), mixv(a.B);
@@ -222,10 +242,11 @@ cudaError_t launch_run_itemmaps(const RunInfo*, int nruns, const RunPart*, const
 }
 // Shared-memory capacity of a part-local run CTA, as on the GB300 (227 KB opt-in).
 uint32_t sector_run_capacity(qf_dtype, bool, bool, bool) { return 18000; }
-cudaError_t launch_sector_hpsi_direct(void*, qf_dtype, const SecSpace& sp, const SecDirect&, const SecCompact&,
+cudaError_t launch_sector_hpsi_direct(void*, qf_dtype, const SecSpace& sp, const SecDirect& d, const SecCompact&,
                                       double*, unsigned*, double*, int nblocks, float2*, double*, bool dss,
                                       cudaStream_t) {
   mixv(sp.cnt_e), mixv(sp.cnt_o), mixv(sp.ne), mixv(sp.no), mixv(sp.ke), mixv(sp.ko), mixv(nblocks), mixv(dss);
+  stub::dump_direct(d);
   return cudaSuccess;
 }
 cudaError_t launch_sector_hpsi(const void*, void*, qf_dtype, bool realst, const SecSpace& sp, const SecRank&,

@@ -142,6 +142,21 @@ int main(int argc, char** argv) {
     report("expectation.16q", qf_expectation(st, T16.data(), T16.size(), &re, &im));
     qf_state_destroy(st);
   }
+  if (only == "direct8" || only == "direct10") {  // a molecular sector evaluation: the direct tables
+    const bool ten = only == "direct10";
+    const auto A = load<qf_arot>(ten ? "ansatz10.bin" : "ansatz8.bin");
+    const auto T = load<qf_term>(ten ? "terms10.bin" : "terms8.bin");
+    const auto t = load<double>(ten ? "t10.bin" : "t8.bin");
+    qf_state* st = make(ten ? 10 : 8, QF_C128);
+    // (the 10-qubit ansatz file starts with a particle-number-changing rotation: skip it)
+    const size_t skip = ten ? 1 : 0, npar = ten ? t.size() - 1 : t.size() / 4;
+    std::vector<qf_arot> A2(A.begin() + skip, A.end());
+    for (auto& a : A2) a.param -= (int32_t)skip;
+    report(only == "direct8" ? "energy_grad.8q.direct" : "energy_grad.10q.direct",
+           qf_energy_grad(st, ten ? 31 : 15, A2.data(), A2.size(), t.data() + skip, npar, T.data(), T.size(), &e,
+                          g.data()));
+    qf_state_destroy(st);
+  }
   if (only == "hpsi8") {  // a generic ansatz on 8 qubits: the gather H|psi> kernel and its tables
     const auto A = load<qf_arot>("ansatz_h8.bin");
     const auto t = load<double>("t_h8.bin");

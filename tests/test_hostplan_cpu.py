@@ -15,8 +15,8 @@ part-local run plan, grouped small requests -- on every ABI path, and checks:
   * each fused block's composite (Eq. 19's excitation factors, applied as one
     2^u x 2^u block on its active rows) and generator equal the dense products
     of its rotations computed by the oracle;
-  * the X-mask groups' sign-pattern tables reproduce the oracle's Hamiltonian
-    matrix elements.
+  * the X-mask groups' sign-pattern tables, and the direct sector tables of a
+    molecular Hamiltonian, reproduce the oracle's Hamiltonian matrix elements.
 """
 import os
 import shutil
@@ -265,3 +265,84 @@ def test_xmask_group_tables_reproduce_the_hamiltonian(suite, tmp_path):
         np.testing.assert_allclose(D, H[b.astype(np.int64) ^ x, b.astype(np.int64)], rtol=0, atol=1e-13)
     assert seen == {int(v) for v in T["x"]}
     assert len(seen) == len(graw) // gsize
+
+
+def _direct_tables(raw):
+    head = np.frombuffer(raw, np.int32, 4, 0)
+    n, ne, no = (int(v) for v in head[:3])
+    inv_fix = float(np.frombuffer(raw, np.float64, 1, 16)[0])
+    pe, po = ne * (ne - 1) // 2, no * (no - 1) // 2
+    sizes = [("wab", np.float64, ne * ne * no * no), ("waa", np.float64, max(1, pe * pe)),
+             ("wbb", np.float64, max(1, po * po)), ("s1a", np.int64, ne * ne * (n + 1)),
+             ("s1b", np.int64, no * no * (n + 1)), ("dg", np.int64, 1 + n + n * n)]
+    off, t = 24, dict(n=n, ne=ne, no=no, inv_fix=inv_fix)
+    for name, dt, cnt in sizes:
+        t[name] = np.frombuffer(raw, dt, cnt, off)
+        off += cnt * 8
+    assert off == len(raw)
+    return t
+
+
+def _h_from_direct(t, c, c2):
+    """<c|H|c2> as the direct tables state it: the diagonal K + sum U + sum V over
+    c's occupied qubits; a single o -> v (c occupies o) A + sum of B over c's other
+    occupied qubits; doubles one weight; each off-diagonal entry signed by the
+    parities of c's occupied qubits below each moved qubit."""
+    n, ne, no = t["n"], t["ne"], t["no"]
+    occ = [q for q in range(n) if (c >> q) & 1]
+    pp = lambda q: bin(c & ((1 << q) - 1)).count("1") & 1  # noqa: E731
+    pr = lambda i, j: i + j * (j - 1) // 2  # noqa: E731
+    d = c ^ c2
+    gone = [q for q in range(n) if (d >> q) & 1 and (c >> q) & 1]   # occupied in c, empty in c2
+    new = [q for q in range(n) if (d >> q) & 1 and (c2 >> q) & 1]
+    if d == 0:
+        dg = t["dg"]
+        v = int(dg[0]) + sum(int(dg[1 + r]) for r in occ)
+        v += sum(int(dg[1 + n + r * n + s]) for i, r in enumerate(occ) for s in occ[i + 1:])
+        return v * t["inv_fix"]
+    sign = (-1) ** (sum(pp(q) for q in gone + new) & 1)
+    if len(gone) == 1:
+        o, v = gone[0], new[0]
+        if (o & 1) != (v & 1):
+            return 0.0
+        tab, m = (t["s1a"], ne) if o % 2 == 0 else (t["s1b"], no)
+        row = tab[((o >> 1) * m + (v >> 1)) * (n + 1):][:n + 1]
+        w = int(row[0]) + sum(int(row[1 + r]) for r in occ if r != o)
+        return sign * w * t["inv_fix"]
+    if len(gone) == 2:
+        ga = [q >> 1 for q in gone if q % 2 == 0]
+        na_ = [q >> 1 for q in new if q % 2 == 0]
+        gb = [q >> 1 for q in gone if q % 2 == 1]
+        nb_ = [q >> 1 for q in new if q % 2 == 1]
+        if len(ga) != len(na_):
+            return 0.0
+        if len(ga) == 1:
+            return sign * t["wab"][((ga[0] * ne + na_[0]) * no + gb[0]) * no + nb_[0]]
+        if len(ga) == 2:
+            return sign * t["waa"][pr(*ga) * (ne * (ne - 1) // 2) + pr(*na_)]
+        return sign * t["wbb"][pr(*gb) * (no * (no - 1) // 2) + pr(*nb_)]
+    return 0.0
+
+
+@pytest.mark.parametrize("case", ["direct8", "direct10"])
+def test_direct_sector_tables_reproduce_the_hamiltonian(suite, tmp_path, case):
+    """The direct sector tables of a molecular Hamiltonian (Eq. 1 through the
+    Jordan-Wigner map of Eq. 15-16): every matrix element between two determinants
+    of the sector, as the tables state it, equals the oracle's dense Hamiltonian
+    (half filling at 8 qubits; 3 alpha and 2 beta electrons at 10)."""
+    from oracle import pauli, sector
+    from paper_2108_04413_gb300.abi import TERM_DTYPE
+
+    exe, d = suite
+    _run(suite, case, env={"QF_STUB_DUMP_DIR": str(tmp_path)})
+    t = _direct_tables((tmp_path / "direct.bin").read_bytes())
+    n = t["n"]
+    T = np.fromfile(os.path.join(d, "terms8.bin" if case == "direct8" else "terms10.bin"), dtype=TERM_DTYPE)
+    H = pauli.dense_sum(n, [(int(x), int(z), float(c)) for x, z, c in zip(T["x"], T["z"], T["coeff"])])
+    assert np.abs(H.imag).max() == 0.0
+    na, nb = sector.counts_of(15 if case == "direct8" else 31)
+    dets = [int(v) for v in sector.sector_dets(n // 2, na, nb)]
+    got = np.array([[_h_from_direct(t, c, c2) for c2 in dets] for c in dets])
+    want = H.real[np.ix_(dets, dets)]
+    assert np.abs(want).max() > 0.1
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
