@@ -6,8 +6,10 @@
 // be compared byte for byte.  With QF_STUB_DUMP_DIR set, the sparse composite
 // blocks handed to the forward and adjoint launchers are appended to
 // fwd.bin / adj.bin there, and the X-mask groups and tables handed to the gather
-// H|psi> kernel are written to groups.bin / hchunks.bin and the direct sector
-// tables to direct.bin, for comparison with the plain definitions.
+// H|psi> kernel are written to groups.bin / hchunks.bin, the direct sector
+// tables to direct.bin and the grouped small requests' blocks and coefficient
+// records to small_blks.bin / small_coef.bin, for comparison with the plain
+// definitions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -77,6 +79,17 @@ void dump_direct(const qf::SecDirect& d) {
   std::fwrite(d.s1b, sizeof(long long), (size_t)no * no * (n + 1), f);
   std::fwrite(d.dg, sizeof(long long), (size_t)1 + n + (size_t)n * n, f);
   std::fclose(f);
+}
+// the grouped small requests: the blocks' sector geometry and every request's
+// per-block coefficient records
+void dump_small(const qf::SmallEval& a, qf_dtype dt, int n_req) {
+  const char* dir = std::getenv("QF_STUB_DUMP_DIR");
+  if (!dir) return;
+  FILE* f = std::fopen((std::string(dir) + "/small_blks.bin").c_str(), "wb");
+  if (f) std::fwrite(a.blks, sizeof(qf::SecBlk), a.nblk, f), std::fclose(f);
+  const size_t rec = (size_t)qf::kSmallCoef * (dt == QF_C128 ? sizeof(double) : sizeof(float));
+  f = std::fopen((std::string(dir) + "/small_coef.bin").c_str(), "wb");
+  if (f) std::fwrite(a.coef, rec, (size_t)n_req * a.nblk, f), std::fclose(f);
 }
 void mix_rot(const qf::RotArgs& a) {
   mixv(a.x), mixv(a.z), mixv(a.h), mixv(a.y), mixv(a.form), mixv(a.A), mixv(a.B);
@@ -259,8 +272,9 @@ cudaError_t launch_sector_hpsi(const void*, void*, qf_dtype, bool realst, const 
 size_t small_eval_smem(qf_dtype dt, uint32_t members, int, int) {
   return (size_t)members * (dt == QF_C128 ? 32 : 16) + 4096;
 }
-cudaError_t launch_small_eval(const SmallEval& a, qf_dtype, int n_req, cudaStream_t) {
+cudaError_t launch_small_eval(const SmallEval& a, qf_dtype dt, int n_req, cudaStream_t) {
   mixv(a.nblk), mixv(a.cnt_e), mixv(a.cnt_o), mixv(a.ke), mixv(a.ko), mixv(a.c0), mixv(n_req);
+  stub::dump_small(a, dt, n_req);
   return cudaSuccess;
 }
 cudaError_t launch_wait_selftest(unsigned*, double, cudaStream_t) { return cudaSuccess; }

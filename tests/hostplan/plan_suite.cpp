@@ -4,6 +4,7 @@
 //   plan_suite <dir>          every case, one line each
 //   plan_suite <dir> layout   sizeof and field offsets of qf::SparseArgs
 //   plan_suite <dir> tables   the same for qf::ExpGroup and qf::ExpChunk
+//   plan_suite <dir> secblk   the same for qf::SecBlk, and the coefficient record length
 //   plan_suite <dir> runitems <n> <det>   the part-local sweep's items per run for
 //                             terms_ri.bin / ansatz_ri.bin / t_ri.bin
 #include <cstddef>
@@ -74,6 +75,12 @@ int main(int argc, char** argv) {
     std::printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(ExpGroup), offsetof(ExpGroup, x),
                 offsetof(ExpGroup, nchunk), offsetof(ExpGroup, chunk0), sizeof(ExpChunk), offsetof(ExpChunk, z),
                 offsetof(ExpChunk, tab), offsetof(ExpChunk, ftab), (size_t)(1 << qf::kChunkTerms), qf::kChunkTerms);
+    return 0;
+  }
+  if (argc > 2 && std::string(argv[2]) == "secblk") {
+    using qf::SecBlk;
+    std::printf("%zu %zu %zu %zu %d\n", sizeof(SecBlk), offsetof(SecBlk, pat), offsetof(SecBlk, zc),
+                offsetof(SecBlk, nzc), qf::kSmallCoef);
     return 0;
   }
   if (argc > 4 && std::string(argv[2]) == "runitems") {
@@ -155,6 +162,13 @@ int main(int argc, char** argv) {
     report(only == "direct8" ? "energy_grad.8q.direct" : "energy_grad.10q.direct",
            qf_energy_grad(st, ten ? 31 : 15, A2.data(), A2.size(), t.data() + skip, npar, T.data(), T.size(), &e,
                           g.data()));
+    qf_state_destroy(st);
+  }
+  if (only == "multi8") {  // four parameter vectors of one 8-qubit system in one grouped call
+    qf_state* st = make(8, QF_C128);
+    report("energy_grad_multi.8q.c128", qf_energy_grad_multi(st, 15, A8.data(), A8.size(), t8.data(),
+                                                             t8.size() / 4, 4, T8.data(), T8.size(), es.data(),
+                                                             g.data()));
     qf_state_destroy(st);
   }
   if (only == "hpsi8") {  // a generic ansatz on 8 qubits: the gather H|psi> kernel and its tables

@@ -14,7 +14,8 @@ part-local run plan, grouped small requests -- on every ABI path, and checks:
     one item per (sector determinant, excitation) pair the excitation acts on;
   * each fused block's composite (Eq. 19's excitation factors, applied as one
     2^u x 2^u block on its active rows) and generator equal the dense products
-    of its rotations computed by the oracle;
+    of its rotations computed by the oracle, and so do the grouped small
+    requests' per-request block records;
   * the X-mask groups' sign-pattern tables, and the direct sector tables of a
     molecular Hamiltonian, reproduce the oracle's Hamiltonian matrix elements.
 """
@@ -346,3 +347,55 @@ def test_direct_sector_tables_reproduce_the_hamiltonian(suite, tmp_path, case):
     want = H.real[np.ix_(dets, dets)]
     assert np.abs(want).max() > 0.1
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+def test_grouped_request_records_match_dense_products(suite, tmp_path):
+    """qf_energy_grad_multi's per-request block records (one CTA per request):
+    for every request and dUCCSD factor, the forward composite minus identity on
+    the factor's two active determinants, its inverse, and the generator's
+    coupling q01 (Q = i Qi), per sign class of the Z strings outside the support,
+    equal the oracle's dense products of the factor's rotations at that request's
+    angles."""
+    from oracle import pauli
+    from paper_2108_04413_gb300.abi import AROT_DTYPE
+
+    exe, d = suite
+    _run(suite, "multi8", env={"QF_STUB_DUMP_DIR": str(tmp_path)})
+    bsize, o_pat, o_zc, o_nzc, ncoef = (
+        int(v) for v in subprocess.run([exe, d, "secblk"], check=True, capture_output=True, text=True).stdout.split())
+    braw = (tmp_path / "small_blks.bin").read_bytes()
+    coef = np.frombuffer((tmp_path / "small_coef.bin").read_bytes(), np.float64)
+    A = np.fromfile(os.path.join(d, "ansatz8.bin"), dtype=AROT_DTYPE)
+    rows_t = np.fromfile(os.path.join(d, "t8.bin"), dtype=np.float64).reshape(4, -1)
+    n, nblk = 8, len(braw) // bsize
+    # a fresh handle plans with the first request (a single evaluation), then
+    # groups the rest in one launch
+    nreq = coef.size // (nblk * ncoef)
+    assert nblk == rows_t.shape[1] and coef.size == nreq * nblk * ncoef and nreq == 3
+    coef = coef.reshape(nreq, nblk, ncoef)
+    rows_t = rows_t[4 - nreq:]
+    runs = {}
+    for x, z, c, p in zip(A["x"].tolist(), A["z"].tolist(), A["coeff"].tolist(), A["param"].tolist()):
+        runs.setdefault(int(x), []).append((int(z), float(c), int(p)))
+    for b in range(nblk):
+        raw = braw[b * bsize:(b + 1) * bsize]
+        pat = [int(v) for v in np.frombuffer(raw, np.uint64, 2, o_pat)]
+        nzc = int(np.frombuffer(raw, np.int32, 1, o_nzc)[0])
+        zc = [int(v) for v in np.frombuffer(raw, np.uint64, nzc, o_zc)]
+        x = pat[0] ^ pat[1]
+        for k in range(nreq):
+            rots = [(x, z, c * rows_t[k, p]) for z, c, p in runs[x]]
+            v = coef[k, b]
+            for cls in range(1 << nzc):
+                b0 = next(s for s in range(1 << n) if not (s & x) and all(
+                    (bin(m & s).count("1") & 1) == ((cls >> j) & 1) for j, m in enumerate(zc)))
+                dets = [b0 ^ p for p in pat]
+                U = np.array([[pauli.apply_rotations(pauli.basis_state(n, cj), n, rots)[ci] for cj in dets]
+                              for ci in dets])
+                Q = np.array([[sum(c * pauli.apply(pauli.basis_state(n, cj), n, x, z)[ci] for z, c, _ in runs[x])
+                               for cj in dets] for ci in dets])
+                assert np.abs(U.imag).max() < 1e-15
+                np.testing.assert_allclose(v[4 * cls:4 * cls + 4].reshape(2, 2), U.real - np.eye(2), atol=1e-13)
+                np.testing.assert_allclose(v[16 + 4 * cls:20 + 4 * cls].reshape(2, 2), U.real.T - np.eye(2),
+                                           atol=1e-13)
+                assert abs(v[32 + cls] - (Q[0, 1] / 1j)) < 1e-13
