@@ -8,8 +8,8 @@
 // fwd.bin / adj.bin there, and the X-mask groups and tables handed to the gather
 // H|psi> kernel are written to groups.bin / hchunks.bin, the direct sector
 // tables to direct.bin and the grouped small requests' blocks and coefficient
-// records to small_blks.bin / small_coef.bin, for comparison with the plain
-// definitions.
+// records to small_blks.bin / small_coef.bin and the full-layout sector sweep's
+// blocks to sweep_blks.bin, for comparison with the plain definitions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -223,9 +223,15 @@ cudaError_t launch_adj_sparse(void*, void*, int n, qf_dtype, const SparseArgs& a
   return cudaSuccess;
 }
 int sector_sweep_grid(uint64_t) { return 152; }
-cudaError_t launch_sector_sweep(void*, qf_dtype, bool realst, const SecBlk*, int nblk, unsigned*, int grid,
+cudaError_t launch_sector_sweep(void*, qf_dtype, bool realst, const SecBlk* blks, int nblk, unsigned*, int grid,
                                 cudaStream_t) {
   mixv(realst), mixv(nblk), mixv(grid);
+  if (const char* dir = std::getenv("QF_STUB_DUMP_DIR")) {  // the sweep's blocks, appended per flush
+    if (FILE* f = std::fopen((std::string(dir) + "/sweep_blks.bin").c_str(), "ab")) {
+      std::fwrite(blks, sizeof(SecBlk), nblk, f);
+      std::fclose(f);
+    }
+  }
   return cudaSuccess;
 }
 cudaError_t launch_sector_runs(void*, void*, qf_dtype, bool adj, bool realst, const RunInfo* runs, int nruns,

@@ -79,8 +79,8 @@ int main(int argc, char** argv) {
   }
   if (argc > 2 && std::string(argv[2]) == "secblk") {
     using qf::SecBlk;
-    std::printf("%zu %zu %zu %zu %d\n", sizeof(SecBlk), offsetof(SecBlk, pat), offsetof(SecBlk, zc),
-                offsetof(SecBlk, nzc), qf::kSmallCoef);
+    std::printf("%zu %zu %zu %zu %d %zu\n", sizeof(SecBlk), offsetof(SecBlk, pat), offsetof(SecBlk, zc),
+                offsetof(SecBlk, nzc), qf::kSmallCoef, offsetof(SecBlk, m));
     return 0;
   }
   if (argc > 4 && std::string(argv[2]) == "runitems") {
@@ -162,6 +162,14 @@ int main(int argc, char** argv) {
     report(only == "direct8" ? "energy_grad.8q.direct" : "energy_grad.10q.direct",
            qf_energy_grad(st, ten ? 31 : 15, A2.data(), A2.size(), t.data() + skip, npar, T.data(), T.size(), &e,
                           g.data()));
+    qf_state_destroy(st);
+  }
+  if (only == "sweep8") {  // an 8-qubit dUCCSD circuit on its sector state: the full-layout sector sweep
+    const auto R = load<qf_rot>("rot8.bin");
+    qf_state* st = make(8, QF_C128);
+    qf_set_basis(st, 15);
+    stub::reset();
+    report("apply_circuit.8q.ucc", qf_apply_circuit(st, R.data(), R.size()));
     qf_state_destroy(st);
   }
   if (only == "multi8") {  // four parameter vectors of one 8-qubit system in one grouped call

@@ -15,7 +15,7 @@ part-local run plan, grouped small requests -- on every ABI path, and checks:
   * each fused block's composite (Eq. 19's excitation factors, applied as one
     2^u x 2^u block on its active rows) and generator equal the dense products
     of its rotations computed by the oracle, and so do the grouped small
-    requests' per-request block records;
+    requests' per-request block records and the sector sweep's blocks;
   * the X-mask groups' sign-pattern tables, and the direct sector tables of a
     molecular Hamiltonian, reproduce the oracle's Hamiltonian matrix elements.
 """
@@ -361,7 +361,7 @@ def test_grouped_request_records_match_dense_products(suite, tmp_path):
 
     exe, d = suite
     _run(suite, "multi8", env={"QF_STUB_DUMP_DIR": str(tmp_path)})
-    bsize, o_pat, o_zc, o_nzc, ncoef = (
+    bsize, o_pat, o_zc, o_nzc, ncoef, _ = (
         int(v) for v in subprocess.run([exe, d, "secblk"], check=True, capture_output=True, text=True).stdout.split())
     braw = (tmp_path / "small_blks.bin").read_bytes()
     coef = np.frombuffer((tmp_path / "small_coef.bin").read_bytes(), np.float64)
@@ -399,3 +399,43 @@ def test_grouped_request_records_match_dense_products(suite, tmp_path):
                 np.testing.assert_allclose(v[16 + 4 * cls:20 + 4 * cls].reshape(2, 2), U.real.T - np.eye(2),
                                            atol=1e-13)
                 assert abs(v[32 + cls] - (Q[0, 1] / 1j)) < 1e-13
+
+
+def test_sector_sweep_blocks_match_dense_products(suite, tmp_path):
+    """qf_apply_circuit of an 8-qubit dUCCSD circuit on its sector state runs the
+    full-layout sector sweep: every block's real composite minus identity on its
+    two active determinants, per sign class of the Z strings outside the support,
+    equals the oracle's dense product of the excitation's rotations."""
+    from oracle import pauli
+    from paper_2108_04413_gb300 import prep
+    from paper_2108_04413_gb300.abi import AROT_DTYPE
+
+    exe, d = suite
+    A = np.fromfile(os.path.join(d, "ansatz8.bin"), dtype=AROT_DTYPE)
+    t = np.fromfile(os.path.join(d, "t8.bin"), dtype=np.float64).reshape(4, -1)[0]
+    R = prep.bind_thetas(A, t)
+    R.tofile(os.path.join(d, "rot8.bin"))
+    _run(suite, "sweep8", env={"QF_STUB_DUMP_DIR": str(tmp_path)})
+    bsize, o_pat, o_zc, o_nzc, _, o_m = (
+        int(v) for v in subprocess.run([exe, d, "secblk"], check=True, capture_output=True, text=True).stdout.split())
+    braw = (tmp_path / "sweep_blks.bin").read_bytes()
+    runs = {}
+    for x, z, th in zip(R["x"].tolist(), R["z"].tolist(), R["theta"].tolist()):
+        runs.setdefault(int(x), []).append((int(x), int(z), float(th)))
+    n, nblk = 8, len(braw) // bsize
+    assert nblk == len(runs) == t.size
+    for b in range(nblk):
+        raw = braw[b * bsize:(b + 1) * bsize]
+        pat = [int(v) for v in np.frombuffer(raw, np.uint64, 2, o_pat)]
+        nzc = int(np.frombuffer(raw, np.int32, 1, o_nzc)[0])
+        zc = [int(v) for v in np.frombuffer(raw, np.uint64, nzc, o_zc)]
+        m = np.frombuffer(raw, np.float64, 16, o_m).reshape(4, 2, 2)
+        rots = runs[pat[0] ^ pat[1]]
+        for cls in range(1 << nzc):
+            b0 = next(s for s in range(1 << n) if not (s & (pat[0] ^ pat[1])) and all(
+                (bin(mz & s).count("1") & 1) == ((cls >> j) & 1) for j, mz in enumerate(zc)))
+            dets = [b0 ^ p for p in pat]
+            U = np.array([[pauli.apply_rotations(pauli.basis_state(n, cj), n, rots)[ci] for cj in dets]
+                          for ci in dets])
+            assert np.abs(U.imag).max() < 1e-15
+            np.testing.assert_allclose(m[cls], U.real - np.eye(2), atol=1e-13)
