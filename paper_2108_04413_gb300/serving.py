@@ -57,17 +57,30 @@ def _popc(v: int) -> int:
     return bin(v).count("1")
 
 
-def footprint_bytes(n: int, dtype: str, det: Optional[int] = None, ansatz: Optional[np.ndarray] = None) -> int:
-    """Device bytes a resident system holds: psi and lambda (2 * 2^n amplitudes).
-    Given the determinant and the ansatz, also the sector path's compact copy
-    (2 * members amplitudes) and forward log (one amplitude pair per (member
-    pair, excitation) item, at most 16 GB): an excitation whose flips cover sa
-    alpha and sb beta spin orbitals, half of each occupied, moves
-    C(ne - sa, na - sa/2) * C(no - sb, nb - sb/2) items.  Plan tables are small."""
+# Per-handle device memory beyond the amplitudes (upper bounds of what the
+# library allocates): work buffers, Pauli-sum plan tables per term, sweep
+# descriptors per excitation, and the limits of the forward log and item maps.
+FIXED_BYTES = 128 << 10
+TABLE_BYTES_PER_TERM = 512
+RUN_BYTES_PER_EXCITATION = 1536
+LOG_MAX_BYTES = 16 << 30
+MAP_MAX_BYTES = 1 << 30
+
+
+def footprint_bytes(n: int, dtype: str, det: Optional[int] = None, ansatz: Optional[np.ndarray] = None,
+                    n_terms: int = 0) -> int:
+    """Device bytes a resident system holds, an upper bound: psi and lambda
+    (2 * 2^n amplitudes), the handle's work buffers and its Pauli-sum plan tables
+    (n_terms terms).  Given the determinant and the ansatz, also the sector
+    path's compact copy (2 * members amplitudes), its forward log (one amplitude
+    pair per (member pair, excitation) item, at most 16 GB), its item maps (at
+    most one 4-byte word per item, at most 1 GB) and its run descriptors: an
+    excitation whose flips cover sa alpha and sb beta spin orbitals, half of each
+    occupied, moves C(ne - sa, na - sa/2) * C(no - sb, nb - sb/2) items."""
     from math import comb
 
     size = 16 if dtype == "c128" else 8
-    total = 2 * (size << n)
+    total = 2 * (size << n) + FIXED_BYTES + TABLE_BYTES_PER_TERM * int(n_terms)
     if det is None or ansatz is None or len(ansatz) == 0:
         return total
     ne, no = (n + 1) // 2, n // 2
@@ -83,7 +96,8 @@ def footprint_bytes(n: int, dtype: str, det: Optional[int] = None, ansatz: Optio
         ka, kb = na - sa // 2, nb - sb // 2
         if 0 <= ka <= ne - sa and 0 <= kb <= no - sb:
             items += comb(ne - sa, ka) * comb(no - sb, kb)
-    return total + 2 * members * size + min(items * size, 16 << 30)
+    return (total + 2 * members * size + min(items * size, LOG_MAX_BYTES) + min(items * 4, MAP_MAX_BYTES) +
+            RUN_BYTES_PER_EXCITATION * len(flips))
 
 
 class GpuExecutor:
@@ -161,7 +175,7 @@ class Server:
         fp = self._fp.get(key)
         if fp is None:
             sysm = self.systems[key]
-            fp = self._fp[key] = footprint_bytes(sysm.n, self.dtype, sysm.det, sysm.ansatz)
+            fp = self._fp[key] = footprint_bytes(sysm.n, self.dtype, sysm.det, sysm.ansatz, len(sysm.terms))
         return fp
 
     # -- submission

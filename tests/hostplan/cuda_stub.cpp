@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -26,6 +27,17 @@ namespace stub {
 std::mutex mu;
 uint64_t digest = 1469598103934665603ull;
 size_t copies = 0, h2d_bytes = 0;
+std::map<const void*, size_t> live;  // device allocations and their sizes
+void dump_live() {
+  std::lock_guard<std::mutex> l(mu);
+  for (const auto& kv : live) std::printf("#live %zu\n", kv.second);
+}
+size_t live_bytes() {
+  std::lock_guard<std::mutex> l(mu);
+  size_t t = 0;
+  for (const auto& kv : live) t += kv.second;
+  return t;
+}
 
 void mix(const void* p, size_t n) {  // FNV-1a over the bytes, folded into the digest
   const unsigned char* b = static_cast<const unsigned char*>(p);
@@ -101,9 +113,17 @@ cudaError_t cudaMalloc(void** p, size_t n) {
   const size_t m = (n + 255) & ~(size_t)255;
   *p = std::aligned_alloc(256, m ? m : 256);
   if (*p && m < ((size_t)1 << 20)) std::memset(*p, 0, m);  // small buffers (flags, partials) are read back
+  if (*p) {
+    std::lock_guard<std::mutex> l(stub::mu);
+    stub::live[*p] = n;
+  }
   return *p ? cudaSuccess : cudaErrorMemoryAllocation;
 }
 cudaError_t cudaFree(void* p) {
+  {
+    std::lock_guard<std::mutex> l(stub::mu);
+    stub::live.erase(p);
+  }
   std::free(p);
   return cudaSuccess;
 }

@@ -20,6 +20,8 @@ namespace stub {
 extern uint64_t digest;
 extern size_t copies, h2d_bytes;
 void reset();
+size_t live_bytes();
+void dump_live();
 }  // namespace stub
 
 static std::string g_dir;
@@ -81,6 +83,26 @@ int main(int argc, char** argv) {
     using qf::SecBlk;
     std::printf("%zu %zu %zu %zu %d %zu\n", sizeof(SecBlk), offsetof(SecBlk, pat), offsetof(SecBlk, zc),
                 offsetof(SecBlk, nzc), qf::kSmallCoef, offsetof(SecBlk, m));
+    return 0;
+  }
+  if (argc > 5 && std::string(argv[2]) == "footprint") {
+    // device bytes a handle holds after one evaluation of terms_fp.bin / ansatz_fp.bin / t_fp.bin
+    const auto T = load<qf_term>("terms_fp.bin");
+    const auto A = load<qf_arot>("ansatz_fp.bin");
+    const auto t = load<double>("t_fp.bin");
+    const size_t before = stub::live_bytes();
+    qf_state* st = make(std::atoi(argv[3]), std::string(argv[4]) == "c64" ? QF_C64 : QF_C128);
+    std::vector<double> grad(t.size());
+    double energy = 0;
+    const qf_status s = qf_energy_grad(st, std::strtoull(argv[5], nullptr, 0), A.data(), A.size(), t.data(),
+                                       t.size(), T.data(), T.size(), &energy, grad.data());
+    if (s != QF_OK) {
+      std::printf("#error footprint: %s\n", qf_last_error());
+      return 4;
+    }
+    std::printf("%zu\n", stub::live_bytes() - before);
+    if (std::getenv("QF_STUB_LIST")) stub::dump_live();
+    qf_state_destroy(st);
     return 0;
   }
   if (argc > 4 && std::string(argv[2]) == "runitems") {

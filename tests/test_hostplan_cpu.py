@@ -439,3 +439,30 @@ def test_sector_sweep_blocks_match_dense_products(suite, tmp_path):
                           for ci in dets])
             assert np.abs(U.imag).max() < 1e-15
             np.testing.assert_allclose(m[cls], U.real - np.eye(2), atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [10, 12, 14, 16, 18])
+def test_serving_footprint_bounds_the_handle_memory(suite, n):
+    """Serving admits a system by serving.footprint_bytes: it must bound the
+    device bytes a handle really holds after an evaluation (the state, the
+    compact sector copy, the forward log, item maps, run descriptors, plan
+    tables and work buffers), without overstating them more than 2.5 times."""
+    from paper_2108_04413_gb300 import prep
+    from paper_2108_04413_gb300.serving import footprint_bytes
+    from workloads import amplitudes, integrals
+
+    exe, d = suite
+    h, g = integrals(n // 2, 100 + n)
+    T = prep.molecular_hamiltonian(h, g)
+    A, exs = prep.uccsd_ansatz(n // 2, n // 2)
+    T.tofile(os.path.join(d, "terms_fp.bin"))
+    A.tofile(os.path.join(d, "ansatz_fp.bin"))
+    np.asarray(amplitudes(len(exs), n, 0.1), np.float64).tofile(os.path.join(d, "t_fp.bin"))
+    det = (1 << (n // 2)) - 1
+    for dtype in ("c128", "c64"):
+        out = subprocess.run([exe, d, "footprint", str(n), dtype, str(det)], check=True, capture_output=True,
+                             text=True, timeout=600).stdout
+        assert "#error" not in out, out
+        held = int(out.split()[0])
+        bound = footprint_bytes(n, dtype, det, A, len(T))
+        assert held <= bound <= 2.5 * held, (n, dtype, held, bound)

@@ -105,9 +105,10 @@ def test_oversized_system_fails_alone():
 
 def test_footprint_counts_sector_log_items_by_brute_force():
     """The sector part of footprint_bytes: 2 * members amplitudes for the compact
-    copy plus one amplitude pair per (member pair, excitation) for the forward
-    log.  A pair is a sector member carrying the excitation's annihilated
-    orbitals on its support; count those directly."""
+    copy, one amplitude pair per (member pair, excitation) for the forward log and
+    one map word per pair, plus the run descriptors.  A pair is a sector member
+    carrying the excitation's annihilated orbitals on its support; count those
+    directly."""
     from paper_2108_04413_gb300 import prep
 
     n_orb, n_el = 4, 4
@@ -122,11 +123,15 @@ def test_footprint_counts_sector_log_items_by_brute_force():
         p0 = sum(1 << q for q in occ)
         sup = p0 | sum(1 << q for q in vir)
         items += sum(1 for c in members if c & sup == p0)
+    from paper_2108_04413_gb300 import serving
+
     for dtype, size in (("c128", 16), ("c64", 8)):
         base = footprint_bytes(n, dtype)
-        assert base == 2 * (size << n)
+        assert base == 2 * (size << n) + serving.FIXED_BYTES
+        assert footprint_bytes(n, dtype, n_terms=100) == base + 100 * serving.TABLE_BYTES_PER_TERM
         got = footprint_bytes(n, dtype, det, A) - base
-        assert got == 2 * len(members) * size + items * size
+        assert got == (2 * len(members) * size + items * size + items * 4 +
+                       len(exs) * serving.RUN_BYTES_PER_EXCITATION)
 
 
 class BatchingExecutor(FakeExecutor):
