@@ -186,6 +186,18 @@ int main(int argc, char** argv) {
                           g.data()));
     qf_state_destroy(st);
   }
+  if (only == "plancache") {  // one handle, 14 Hamiltonians in turn: device bytes after each call
+    qf_state* st = make(16, QF_C128);
+    std::vector<qf_term> T(T16);
+    for (int k = 0; k < 14; ++k) {
+      T[0].coeff = T16[0].coeff + 1e-3 * (k + 1);  // a different term list each call
+      const qf_status s = qf_energy_grad(st, 255, A16.data(), A16.size(), t16.data(), t16.size(), T.data(),
+                                         T.size(), &e, g.data());
+      std::printf("#plancache %d %d %zu\n", k, (int)s, stub::live_bytes());
+    }
+    qf_state_destroy(st);
+    std::printf("#plancache_after_destroy %zu\n", stub::live_bytes());
+  }
   if (only == "sweep8") {  // an 8-qubit dUCCSD circuit on its sector state: the full-layout sector sweep
     const auto R = load<qf_rot>("rot8.bin");
     qf_state* st = make(8, QF_C128);
@@ -234,5 +246,6 @@ int main(int argc, char** argv) {
       qf_state_destroy(st);
     }
   }
+  std::printf("#live_at_exit %zu\n", stub::live_bytes());  // every handle destroyed: nothing left
   return 0;
 }

@@ -6,7 +6,8 @@ memory, no kernel runs, and everything a call would send to the device (uploads
 and the plain-data launch arguments) is hashed.  This covers the planner -- X-mask
 grouping and its tables, the direct sector tables, block composites, the
 part-local run plan, grouped small requests -- on every ABI path, and checks:
-  * every path plans without error;
+  * every path plans without error, and destroying the handles releases every
+    device allocation; the plan cache stays bounded;
   * plans are deterministic, and every plan rebuilt after qf_state_clear_plans
     sends the device the same bytes;
   * a call with new angles on a kept plan uploads only the new composites;
@@ -95,6 +96,9 @@ def _run(suite, *args, env=None):
     assert "#error" not in out, out
     rows = {}
     for line in out.splitlines():
+        if line.startswith("#live_at_exit"):
+            assert int(line.split()[1]) == 0, "device memory left after every handle was destroyed"
+            continue
         name, status, copies, h2d, digest = line.split()
         rows[name] = (int(status), int(copies), int(h2d), digest)
     return rows
@@ -466,3 +470,17 @@ def test_serving_footprint_bounds_the_handle_memory(suite, n):
         held = int(out.split()[0])
         bound = footprint_bytes(n, dtype, det, A, len(T))
         assert held <= bound <= 2.5 * held, (n, dtype, held, bound)
+
+
+def test_plan_cache_is_bounded_and_released(suite):
+    """A handle that receives new Hamiltonians keeps at most a fixed number of
+    plans (least recently used evicted with their device tables): its device
+    bytes stop growing, and destroying it releases everything."""
+    exe, d = suite
+    out = subprocess.run([exe, d, "plancache"], check=True, capture_output=True, text=True, timeout=600).stdout
+    rows = [line.split() for line in out.splitlines() if line.startswith("#plancache ")]
+    assert [int(r[2]) for r in rows] == [0] * 14
+    held = [int(r[3]) for r in rows]
+    assert held[1] > held[0]  # a second plan is kept
+    assert max(held[8:]) == held[8] == held[-1]  # from the ninth on, each new plan replaces the oldest
+    assert int(out.split("#plancache_after_destroy")[1].split()[0]) == 0
