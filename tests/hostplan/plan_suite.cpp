@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstdlib>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -184,6 +185,35 @@ int main(int argc, char** argv) {
     report(only == "direct8" ? "energy_grad.8q.direct" : "energy_grad.10q.direct",
            qf_energy_grad(st, ten ? 31 : 15, A2.data(), A2.size(), t.data() + skip, npar, T.data(), T.size(), &e,
                           g.data()));
+    qf_state_destroy(st);
+  }
+  if (only == "errors") {  // rejected calls: their status, then a valid call on the same handle
+    const size_t base = stub::live_bytes();
+    qf_state* ref = make(16, QF_C128);
+    qf_energy_grad(ref, 255, A16.data(), A16.size(), t16.data(), t16.size(), T16.data(), T16.size(), &e, g.data());
+    const size_t clean = stub::live_bytes() - base;
+    qf_state_destroy(ref);
+    qf_state* st = make(16, QF_C128);
+    std::vector<qf_term> Tbad(T16);
+    Tbad[7].z |= 1ull << 16;  // a Pauli letter on a qubit the state does not have
+    std::printf("#status mask %d\n", (int)qf_energy_grad(st, 255, A16.data(), A16.size(), t16.data(), t16.size(),
+                                                         Tbad.data(), Tbad.size(), &e, g.data()));
+    std::vector<qf_arot> Abad(A16);
+    Abad[3].param = (int32_t)t16.size();  // a parameter index past the vector
+    std::printf("#status param %d\n", (int)qf_energy_grad(st, 255, Abad.data(), Abad.size(), t16.data(),
+                                                          t16.size(), T16.data(), T16.size(), &e, g.data()));
+    std::vector<double> tbad(t16);
+    tbad[5] = std::numeric_limits<double>::quiet_NaN();
+    std::printf("#status angle %d\n", (int)qf_energy_grad(st, 255, A16.data(), A16.size(), tbad.data(),
+                                                          tbad.size(), T16.data(), T16.size(), &e, g.data()));
+    std::printf("#status det %d\n", (int)qf_energy_grad(st, 255ull | (1ull << 20), A16.data(), A16.size(),
+                                                        t16.data(), t16.size(), T16.data(), T16.size(), &e,
+                                                        g.data()));
+    std::printf("#status null %d\n", (int)qf_energy_grad(st, 255, A16.data(), A16.size(), nullptr, t16.size(),
+                                                         T16.data(), T16.size(), &e, g.data()));
+    std::printf("#status valid %d\n", (int)qf_energy_grad(st, 255, A16.data(), A16.size(), t16.data(),
+                                                          t16.size(), T16.data(), T16.size(), &e, g.data()));
+    std::printf("#held %zu %zu\n", clean, stub::live_bytes() - base);
     qf_state_destroy(st);
   }
   if (only == "plancache") {  // one handle, 14 Hamiltonians in turn: device bytes after each call

@@ -484,3 +484,18 @@ def test_plan_cache_is_bounded_and_released(suite):
     assert held[1] > held[0]  # a second plan is kept
     assert max(held[8:]) == held[8] == held[-1]  # from the ninth on, each new plan replaces the oldest
     assert int(out.split("#plancache_after_destroy")[1].split()[0]) == 0
+
+
+def test_rejected_calls_leave_the_handle_working(suite):
+    """Invalid inputs (a Pauli letter past the register, a parameter index past
+    the vector, a non-finite angle, a determinant past the register, a NULL
+    array) are rejected with QF_EINVAL before anything is planned or sent; the
+    handle then evaluates normally and holds what a fresh handle would."""
+    exe, d = suite
+    out = subprocess.run([exe, d, "errors"], check=True, capture_output=True, text=True, timeout=600).stdout
+    status = {l.split()[1]: int(l.split()[2]) for l in out.splitlines() if l.startswith("#status")}
+    QF_OK, QF_EINVAL = 0, 1
+    assert status == {"mask": QF_EINVAL, "param": QF_EINVAL, "angle": QF_EINVAL, "det": QF_EINVAL,
+                      "null": QF_EINVAL, "valid": QF_OK}
+    clean, held = (int(v) for v in out.split("#held")[1].split()[:2])
+    assert held == clean
