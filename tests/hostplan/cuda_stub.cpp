@@ -25,8 +25,9 @@
 
 namespace stub {
 std::mutex mu;
-uint64_t digest = 1469598103934665603ull;
-size_t copies = 0, h2d_bytes = 0;
+// each host thread hashes its own calls (handles used from several threads)
+thread_local uint64_t digest = 1469598103934665603ull;
+thread_local size_t copies = 0, h2d_bytes = 0;
 std::map<const void*, size_t> live;  // device allocations and their sizes
 void dump_live() {
   std::lock_guard<std::mutex> l(mu);
@@ -43,13 +44,11 @@ void mix(const void* p, size_t n) {  // FNV-1a over the bytes, folded into the d
   const unsigned char* b = static_cast<const unsigned char*>(p);
   uint64_t h = 1469598103934665603ull;
   for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
-  std::lock_guard<std::mutex> l(mu);
   digest ^= h + 0x9e3779b97f4a7c15ull + (digest << 6) + (digest >> 2);
   ++copies;
 }
 template <typename T> void mixv(const T& v) { mix(&v, sizeof(T)); }
 void reset() {
-  std::lock_guard<std::mutex> l(mu);
   digest = 1469598103934665603ull;
   copies = h2d_bytes = 0;
 }
@@ -146,7 +145,6 @@ cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t) {
 cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t n, cudaMemcpyKind k, cudaStream_t) {
   if (k == cudaMemcpyHostToDevice) {
     stub::mix(s, n);
-    std::lock_guard<std::mutex> l(stub::mu);
     stub::h2d_bytes += n;
   }
   // large uploads are never read back on the host: skip the copy a DMA engine would make

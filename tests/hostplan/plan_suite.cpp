@@ -12,14 +12,15 @@
 #include <cstdlib>
 #include <limits>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "qf.h"
 #include "qf_internal.h"
 
 namespace stub {
-extern uint64_t digest;
-extern size_t copies, h2d_bytes;
+extern thread_local uint64_t digest;
+extern thread_local size_t copies, h2d_bytes;
 void reset();
 size_t live_bytes();
 void dump_live();
@@ -215,6 +216,28 @@ int main(int argc, char** argv) {
                                                           t16.size(), T16.data(), T16.size(), &e, g.data()));
     std::printf("#held %zu %zu\n", clean, stub::live_bytes() - base);
     qf_state_destroy(st);
+  }
+  if (only == "threads") {  // one 16-qubit handle per host thread, evaluated at once
+    auto one = [&](uint64_t* out, double scale) {
+      stub::reset();
+      std::vector<double> t(t16), gg(t16.size());
+      for (double& v : t) v *= scale;
+      double en = 0;
+      qf_state* st = make(16, QF_C128);
+      for (int rep = 0; rep < 3; ++rep)
+        if (qf_energy_grad(st, 255, A16.data(), A16.size(), t.data(), t.size(), T16.data(), T16.size(), &en,
+                           gg.data()) != QF_OK)
+          std::printf("#error thread: %s\n", qf_last_error());
+      qf_state_destroy(st);
+      *out = stub::digest;
+    };
+    uint64_t serial[4], conc[4];
+    for (int k = 0; k < 4; ++k) one(&serial[k], 1.0 + 0.1 * k);
+    std::vector<std::thread> th;
+    for (int k = 0; k < 4; ++k) th.emplace_back(one, &conc[k], 1.0 + 0.1 * k);
+    for (auto& x : th) x.join();
+    for (int k = 0; k < 4; ++k)
+      std::printf("#thread %d %016llx %016llx\n", k, (unsigned long long)serial[k], (unsigned long long)conc[k]);
   }
   if (only == "plancache") {  // one handle, 14 Hamiltonians in turn: device bytes after each call
     qf_state* st = make(16, QF_C128);

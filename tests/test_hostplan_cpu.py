@@ -7,7 +7,8 @@ and the plain-data launch arguments) is hashed.  This covers the planner -- X-ma
 grouping and its tables, the direct sector tables, block composites, the
 part-local run plan, grouped small requests -- on every ABI path, and checks:
   * every path plans without error, and destroying the handles releases every
-    device allocation; the plan cache stays bounded;
+    device allocation; the plan cache stays bounded; handles planned from
+    several host threads at once do not interfere;
   * plans are deterministic, and every plan rebuilt after qf_state_clear_plans
     sends the device the same bytes;
   * a call with new angles on a kept plan uploads only the new composites;
@@ -499,3 +500,16 @@ def test_rejected_calls_leave_the_handle_working(suite):
                       "null": QF_EINVAL, "valid": QF_OK}
     clean, held = (int(v) for v in out.split("#held")[1].split()[:2])
     assert held == clean
+
+
+def test_handles_plan_independently_on_concurrent_threads(suite):
+    """Serving evaluates several handles from several host threads at once (the
+    planner's worker pool is shared): four handles planned and evaluated
+    concurrently send the device exactly what each sends alone."""
+    exe, d = suite
+    out = subprocess.run([exe, d, "threads"], check=True, capture_output=True, text=True, timeout=600).stdout
+    assert "#error" not in out, out
+    rows = [line.split() for line in out.splitlines() if line.startswith("#thread")]
+    assert len(rows) == 4
+    assert all(r[2] == r[3] for r in rows)
+    assert len({r[2] for r in rows}) == 4  # different angles, different uploads
