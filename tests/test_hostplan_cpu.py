@@ -151,14 +151,14 @@ def test_sparse_composites_match_dense_products(suite, tmp_path):
     sum_k coeff_k P_k, for every sign class of the Z strings outside the support;
     rows outside the active set are left unchanged."""
     from oracle import pauli
+    from paper_2108_04413_gb300.abi import AROT_DTYPE
 
     exe, d = suite
     layout = [int(v) for v in subprocess.run([exe, d, "layout"], check=True, capture_output=True,
                                              text=True).stdout.split()]
     _run(suite, "general10", env={"QF_STUB_DUMP_DIR": str(tmp_path)})
     n = 10
-    A = np.fromfile(os.path.join(d, "ansatz10.bin"), dtype=__import__(
-        "paper_2108_04413_gb300.abi", fromlist=["AROT_DTYPE"]).AROT_DTYPE)
+    A = np.fromfile(os.path.join(d, "ansatz10.bin"), dtype=AROT_DTYPE)
     t = np.fromfile(os.path.join(d, "t10.bin"), dtype=np.float64)
     runs = {}
     for x, z, c, p in zip(A["x"].tolist(), A["z"].tolist(), A["coeff"].tolist(), A["param"].tolist()):
