@@ -156,7 +156,7 @@ def measured_traffic(kernel: str, run_items=None):
         return None
     sampled = sum(int(run_items[r]) for r in rec["runs"])
     total = int(sum(int(v) for v in run_items))
-    if not sampled:
+    if not sampled or sampled != rec.get("items", sampled):  # the plan's runs changed since the capture
         return None
     return rec["bytes"] * total / sampled, (
         f"ncu DRAM bytes of runs {rec['runs']} ({sampled} items, cold caches) scaled to the sweep's {total} items")

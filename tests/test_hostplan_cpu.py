@@ -225,6 +225,15 @@ def test_sweep_plan_items_at_24_qubits_count_the_sector_pairs(suite):
     assert len(exs) == 1818 and len(dets) == 853776
     assert len(items) > 1 and (items > 0).all()
     assert int(items.sum()) == expect == 128172240
+    # the committed DRAM captures of the sweeps are scaled by these runs' items:
+    # they must be the runs the captures measured
+    import json
+
+    traffic = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for key in ("k_sector_run (forward)", "k_sector_run (reverse)"):
+        rec = traffic[key]
+        assert rec["n_runs"] == len(items)
+        assert sum(int(items[r]) for r in rec["runs"]) == rec["items"], key
 
 
 def test_xmask_group_tables_reproduce_the_hamiltonian(suite, tmp_path):
