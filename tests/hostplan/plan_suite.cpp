@@ -217,6 +217,19 @@ int main(int argc, char** argv) {
     std::printf("#held %zu %zu\n", clean, stub::live_bytes() - base);
     qf_state_destroy(st);
   }
+  if (only == "big28") {  // the 28-qubit random workload: a 4 GiB register, 500 rotations, 20000 terms
+    const auto R = load<qf_rot>("rot28.bin");
+    const auto H = load<qf_term>("ham28.bin");
+    for (int d = 0; d < 2; ++d) {
+      qf_state* st = make(28, d ? QF_C64 : QF_C128);
+      qf_set_basis(st, (1ull << 14) - 1);
+      stub::reset();
+      report(std::string("apply_circuit.28q") + (d ? ".c64" : ".c128"), qf_apply_circuit(st, R.data(), R.size()));
+      report(std::string("expectation.28q") + (d ? ".c64" : ".c128"),
+             qf_expectation(st, H.data(), H.size(), &re, &im));
+      qf_state_destroy(st);
+    }
+  }
   if (only == "threads") {  // one 16-qubit handle per host thread, evaluated at once
     auto one = [&](uint64_t* out, double scale) {
       stub::reset();

@@ -522,3 +522,21 @@ def test_handles_plan_independently_on_concurrent_threads(suite):
     assert len(rows) == 4
     assert all(r[2] == r[3] for r in rows)
     assert len({r[2] for r in rows}) == 4  # different angles, different uploads
+
+
+def test_28_qubit_workload_plans_deterministically(suite):
+    """The largest workload: 500 random Pauli exponentials and the 20000-term sum
+    on a 28-qubit register (4 GiB of complex128) plan without error, the same way
+    twice, and release their memory."""
+    from paper_2108_04413_gb300 import prep
+    from workloads import WORKLOADS
+
+    exe, d = suite
+    seed = WORKLOADS["sweep28"]["seed"]
+    prep.random_circuit(28, 500, seed).tofile(os.path.join(d, "rot28.bin"))
+    prep.random_hamiltonian(28, 20000, seed).tofile(os.path.join(d, "ham28.bin"))
+    a, b = _run(suite, "big28"), _run(suite, "big28")
+    assert a == b and len(a) == 4
+    for name, (status, copies, _, _) in a.items():
+        assert status == 0 and copies > 0, name
+    assert a["expectation.28q.c128"][2] > 0
