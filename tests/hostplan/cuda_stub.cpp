@@ -102,6 +102,17 @@ void dump_small(const qf::SmallEval& a, qf_dtype dt, int n_req) {
   f = std::fopen((std::string(dir) + "/small_coef.bin").c_str(), "wb");
   if (f) std::fwrite(a.coef, rec, (size_t)n_req * a.nblk, f), std::fclose(f);
 }
+// The op log (ops.bin): every launch that changes the state, in launch order, as
+// a record the test replays on a dense vector.  A record is an int32 kind and its
+// payload: 1 basis (u64 det); 2 rotation A*I - i*B*P (u64 x, u64 z, f64 A, f64 B);
+// 3 tile (i32 m, i32 s, i32 sbits[s], then per rotation u32 xl, u32 zl, u64 zout,
+// f64 A, f64 B); 4 sparse block (the raw SparseArgs); 5 sector sweep (i32 nblk,
+// then the raw SecBlks); 6 scale (f64).
+FILE* op_log() {
+  const char* dir = std::getenv("QF_STUB_DUMP_DIR");
+  return dir ? std::fopen((std::string(dir) + "/ops.bin").c_str(), "ab") : nullptr;
+}
+template <typename T> void put(FILE* f, const T& v) { std::fwrite(&v, sizeof(T), 1, f); }
 void mix_rot(const qf::RotArgs& a) {
   mixv(a.x), mixv(a.z), mixv(a.h), mixv(a.y), mixv(a.form), mixv(a.A), mixv(a.B);
 }
@@ -157,6 +168,7 @@ namespace qf {
 using stub::mixv;
 cudaError_t launch_zero_and_set(void*, int n, qf_dtype, uint64_t det, cudaStream_t) {
   mixv(n), mixv(det);
+  if (FILE* f = stub::op_log()) stub::put(f, (int32_t)1), stub::put(f, det), std::fclose(f);
   return cudaSuccess;
 }
 cudaError_t launch_zero_and_set_count(void*, uint64_t count, qf_dtype, uint64_t idx, cudaStream_t) {
@@ -170,11 +182,15 @@ cudaError_t launch_gather(const void*, qf_dtype, const int64_t*, int count, bool
 }
 cudaError_t launch_scale(void*, int n, qf_dtype, double scale, cudaStream_t) {
   mixv(n), mixv(scale);
+  if (FILE* f = stub::op_log()) stub::put(f, (int32_t)6), stub::put(f, scale), std::fclose(f);
   return cudaSuccess;
 }
 cudaError_t launch_rot(void*, int n, qf_dtype, const RotArgs& a, cudaStream_t) {
   mixv(n);
   stub::mix_rot(a);
+  if (FILE* f = stub::op_log())
+    stub::put(f, (int32_t)2), stub::put(f, a.x), stub::put(f, a.z), stub::put(f, a.A), stub::put(f, a.B),
+        std::fclose(f);
   return cudaSuccess;
 }
 cudaError_t launch_tile(void*, int n, qf_dtype, const TileArgs& a, cudaStream_t) {
@@ -185,11 +201,20 @@ cudaError_t launch_tile(void*, int n, qf_dtype, const TileArgs& a, cudaStream_t)
     const TileRot& r = a.r[i];
     mixv(r.xl), mixv(r.zl), mixv(r.zout), mixv(r.hl), mixv(r.y), mixv(r.form), mixv(r.A), mixv(r.B);
   }
+  if (FILE* f = stub::op_log()) {
+    stub::put(f, (int32_t)3), stub::put(f, (int32_t)a.m), stub::put(f, (int32_t)a.s);
+    for (int q = 0; q < a.s; ++q) stub::put(f, (int32_t)a.sbits[q]);
+    for (int i = 0; i < a.m; ++i)
+      stub::put(f, a.r[i].xl), stub::put(f, a.r[i].zl), stub::put(f, a.r[i].zout), stub::put(f, a.r[i].A),
+          stub::put(f, a.r[i].B);
+    std::fclose(f);
+  }
   return cudaSuccess;
 }
 cudaError_t launch_sparse(void*, int n, qf_dtype, const SparseArgs& a, bool realst, cudaStream_t) {
   mixv(n), mixv(a), mixv(realst);
   stub::dump("fwd.bin", a);
+  if (FILE* f = stub::op_log()) stub::put(f, (int32_t)4), stub::put(f, a), std::fclose(f);
   return cudaSuccess;
 }
 // a block's composite is real when every entry of M has a zero imaginary part
@@ -244,6 +269,11 @@ int sector_sweep_grid(uint64_t) { return 152; }
 cudaError_t launch_sector_sweep(void*, qf_dtype, bool realst, const SecBlk* blks, int nblk, unsigned*, int grid,
                                 cudaStream_t) {
   mixv(realst), mixv(nblk), mixv(grid);
+  if (FILE* f = stub::op_log()) {
+    stub::put(f, (int32_t)5), stub::put(f, (int32_t)nblk);
+    std::fwrite(blks, sizeof(SecBlk), nblk, f);
+    std::fclose(f);
+  }
   if (const char* dir = std::getenv("QF_STUB_DUMP_DIR")) {  // the sweep's blocks, appended per flush
     if (FILE* f = std::fopen((std::string(dir) + "/sweep_blks.bin").c_str(), "ab")) {
       std::fwrite(blks, sizeof(SecBlk), nblk, f);

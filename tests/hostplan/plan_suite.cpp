@@ -107,6 +107,26 @@ int main(int argc, char** argv) {
     qf_state_destroy(st);
     return 0;
   }
+  if (argc > 5 && std::string(argv[2]) == "circuit") {
+    // rot_c.bin applied to |det> (or, with "trotter", terms_c.bin evolved for time 0.3 in 3 steps);
+    // prints the scale the state keeps aside
+    const int n = std::atoi(argv[3]);
+    qf_state* st = make(n, std::string(argv[5]) == "c64" ? QF_C64 : QF_C128);
+    qf_set_basis(st, std::strtoull(argv[4], nullptr, 0));
+    qf_status s;
+    if (argc > 6 && std::string(argv[6]) == "trotter") {
+      const auto H = load<qf_term>("terms_c.bin");
+      s = qf_trotter(st, H.data(), H.size(), 0.3, 3);
+    } else {
+      const auto R = load<qf_rot>("rot_c.bin");
+      s = qf_apply_circuit(st, R.data(), R.size());
+    }
+    double scale = 0;
+    qf_state_info(st, nullptr, nullptr, nullptr, &scale);
+    std::printf("%d %.17g\n", (int)s, scale);
+    qf_state_destroy(st);
+    return 0;
+  }
   if (argc > 4 && std::string(argv[2]) == "runitems") {
     const auto T = load<qf_term>("terms_ri.bin");
     const auto A = load<qf_arot>("ansatz_ri.bin");

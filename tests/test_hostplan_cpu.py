@@ -19,7 +19,9 @@ part-local run plan, grouped small requests -- on every ABI path, and checks:
     of its rotations computed by the oracle, and so do the grouped small
     requests' per-request block records and the sector sweep's blocks;
   * the X-mask groups' sign-pattern tables, and the direct sector tables of a
-    molecular Hamiltonian, reproduce the oracle's Hamiltonian matrix elements.
+    molecular Hamiltonian, reproduce the oracle's Hamiltonian matrix elements;
+  * the launches qf_apply_circuit and qf_trotter plan, replayed on a dense
+    vector, give the oracle's state.
 """
 import os
 import shutil
@@ -540,3 +542,134 @@ def test_28_qubit_workload_plans_deterministically(suite):
     for name, (status, copies, _, _) in a.items():
         assert status == 0 and copies > 0, name
     assert a["expectation.28q.c128"][2] > 0
+
+
+def _replay(raw, n, sparse_layout, secblk_layout):
+    """The dense state the logged launches produce (the stored values; the kept
+    scale is applied by the caller).  A rotation record applies A*I - i*B*P with
+    P|b> = i^popc(x&z) (-1)^popc(z&b) |b^x> (the oracle's convention)."""
+    from oracle import pauli
+
+    ssize, o_u, o_nr, o_ncls, o_nzc, o_supp, o_pat, o_zc, o_m, _, _, max_rows, max_cls = sparse_layout
+    bsize, b_pat, b_zc, b_nzc, _, b_m = secblk_layout
+    psi = None
+    off, nops = 0, 0
+    b = np.arange(1 << n, dtype=np.int64)
+
+    def take(dt, cnt=1):
+        nonlocal off
+        v = np.frombuffer(raw, dt, cnt, off)
+        off += v.nbytes
+        return v
+
+    def rot(x, z, A, B):
+        return A * psi - 1j * B * pauli.apply(psi, n, x, z)
+
+    def block(x, pat, zc, mats):  # (M_c + I) on the active rows of every outside configuration
+        out = psi.copy()
+        for s0 in range(1 << n):
+            if s0 & x:
+                continue
+            cls = sum(((bin(zc[j] & s0).count("1") & 1) << j) for j in range(len(zc)))
+            rows = [s0 | p for p in pat]
+            out[rows] = psi[rows] + mats[cls] @ psi[rows]
+        return out
+
+    while off < len(raw):
+        kind = int(take(np.int32)[0])
+        nops += 1
+        if kind == 1:
+            psi = pauli.basis_state(n, int(take(np.uint64)[0]))
+        elif kind == 2:
+            x, z = (int(v) for v in take(np.uint64, 2))
+            A, B = take(np.float64, 2)
+            psi = rot(x, z, A, B)
+        elif kind == 3:
+            m, s = (int(v) for v in take(np.int32, 2))
+            sbits = [int(v) for v in take(np.int32, s)]
+            expand = lambda v: sum(1 << sbits[q] for q in range(s) if (v >> q) & 1)  # noqa: E731
+            for _ in range(m):
+                xl, zl = (int(v) for v in take(np.uint32, 2))
+                zout = int(take(np.uint64)[0])
+                A, B = take(np.float64, 2)
+                psi = rot(expand(xl), expand(zl) | zout, A, B)
+        elif kind == 4:
+            a = _sparse_args(raw[off:off + ssize], sparse_layout)[0]
+            off += ssize
+            psi = block(sum(1 << q for q in a["supp"]), a["pat"], a["zc"], a["M"])
+        elif kind == 5:
+            nblk = int(take(np.int32)[0])
+            for _ in range(nblk):
+                rec = raw[off:off + bsize]
+                off += bsize
+                pat = [int(v) for v in np.frombuffer(rec, np.uint64, 2, b_pat)]
+                nzc = int(np.frombuffer(rec, np.int32, 1, b_nzc)[0])
+                zc = [int(v) for v in np.frombuffer(rec, np.uint64, nzc, b_zc)]
+                mats = np.frombuffer(rec, np.float64, 16, b_m).reshape(4, 2, 2)
+                psi = block(pat[0] ^ pat[1], pat, zc, mats)
+        elif kind == 6:
+            psi = psi * float(take(np.float64)[0])
+        else:
+            raise AssertionError(f"unknown op {kind}")
+    return psi, nops
+
+
+def _layouts(exe, d):
+    run = lambda mode: [int(v) for v in subprocess.run([exe, d, mode], check=True, capture_output=True,  # noqa: E731
+                                                        text=True).stdout.split()]
+    return run("layout"), run("secblk")
+
+
+@pytest.mark.parametrize("case", ["random13", "ucc10_general", "ucc8_sector", "trotter10"])
+def test_circuit_plans_replay_to_the_oracle_state(suite, tmp_path, case):
+    """qf_apply_circuit and qf_trotter as planned: the launches they would make
+    (unfused rotations, fused tiles with their tile-local bit maps, sparse blocks,
+    sector sweeps) and the scale the state keeps aside, replayed on a dense
+    vector, give the oracle's state.  Cases: random weight-2..8 exponentials on 13
+    qubits (tile fusion, diagonal and single-flip rotations); a dUCCSD circuit on
+    10 qubits after a particle-number-changing rotation (general sparse blocks);
+    a dUCCSD circuit on its 8-qubit sector state (one sector sweep); a first-order
+    Trotter evolution of a random Hamiltonian on 10 qubits."""
+    from oracle import pauli
+    from paper_2108_04413_gb300 import prep
+    from paper_2108_04413_gb300.abi import AROT_DTYPE, ROT_DTYPE, TERM_DTYPE
+    from workloads import amplitudes
+
+    exe, d = suite
+    extra = []
+    if case == "random13":
+        n, det = 13, 0b1010110100101
+        R = prep.random_circuit(n, 150, 13)
+    elif case == "ucc10_general":
+        n, det = 10, 31
+        A10 = np.fromfile(os.path.join(d, "ansatz10.bin"), dtype=AROT_DTYPE)
+        t10 = np.fromfile(os.path.join(d, "t10.bin"), dtype=np.float64)
+        R = prep.bind_thetas(A10, t10)
+    elif case == "ucc8_sector":
+        n, det = 8, 15
+        A8, ex8 = prep.uccsd_ansatz(4, 4)
+        R = prep.bind_thetas(A8, amplitudes(len(ex8), 3, 0.3))
+    else:
+        n, det = 10, 0b0101010101
+        T = prep.random_hamiltonian(n, 40, 21)
+        T.tofile(os.path.join(d, "terms_c.bin"))
+        extra = ["trotter"]
+        R = np.zeros(0, dtype=ROT_DTYPE)
+        for _ in range(3):  # the oracle's own Trotter steps, written out as rotations
+            R = np.concatenate([R, np.array([(x, z, c * 0.3 / 3) for x, z, c in zip(T["x"], T["z"], T["coeff"])],
+                                            dtype=ROT_DTYPE)])
+        assert T.dtype == TERM_DTYPE
+    R.tofile(os.path.join(d, "rot_c.bin"))
+    sl, bl = _layouts(exe, d)
+    for dtype in ("c128", "c64"):
+        dump = tmp_path / dtype
+        dump.mkdir()
+        out = subprocess.run([exe, d, "circuit", str(n), str(det), dtype, *extra], check=True, capture_output=True,
+                             text=True, timeout=600, env=dict(os.environ, QF_STUB_DUMP_DIR=str(dump))).stdout.split()
+        assert int(out[0]) == 0
+        psi, nops = _replay((dump / "ops.bin").read_bytes(), n, sl, bl)
+        psi = psi * float(out[1])
+        ref = pauli.apply_rotations(pauli.basis_state(n, det), n, [(int(x), int(z), float(t)) for x, z, t in
+                                                                    zip(R["x"], R["z"], R["theta"])])
+        assert nops >= 2
+        np.testing.assert_allclose(psi, ref, rtol=0, atol=1e-11)
